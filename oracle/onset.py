@@ -1,0 +1,129 @@
+"""Linear onset of convection (Section 6.1, Eq. lin), solved with the
+Chebyshev-integration operators of this oracle.
+
+Test infrastructure only (see the package docstring).
+
+For one azimuthal wavenumber m, normal modes f ~ exp(i m phi + lambda t) of the
+linearised equations satisfy the generalised eigenproblem
+    lambda A^I Psi = B^I Psi + (Ra/Pr)(i m/s_o) C^I theta
+    lambda D^I theta = (1/Pr) F^I theta - (alpha/ln eta) i m G^I Psi
+with the tau rows of the boundary conditions (zero mass).  Reading: the printed
+Eq. lin omits the 1/Pr of the diffusion term that Eq. temp carries; the paper's own
+eigenvalues (tau = 6.149994e2, omega_d = -9.536952e3 at E = 3e-6, Pr = 0.025,
+Ra = 1e7, m = 12) are reproduced only with 1/Pr, so 1/Pr is kept.
+
+lambda = tau + i omega_d.  The tau method adds spurious eigenvalues of huge
+modulus; they are discarded (|lambda| > 1e8) and the leading eigenvalue is then
+refined by shift-and-invert around the QZ estimate.
+"""
+import numpy as np
+import scipy.linalg as sl
+from scipy.optimize import brentq
+
+from .operators import IntegrationOperators
+
+
+def pencil(E, Pr, Ra, eta, m, n_c):
+    n_r = int(1.5 * n_c) + 2
+    op = IntegrationOperators(n_r, n_c, eta, E, Pr, Ra)
+    n = n_c
+    L = np.zeros((2 * n, 2 * n), complex)
+    M = np.zeros((2 * n, 2 * n), complex)
+    M[:n, :n] = op.A(m)
+    L[:n, :n] = op.B(m)
+    L[:n, n:] = (Ra / Pr) * (1j * m / op.ann.s_o) * op.C
+    M[n:, n:] = op.D
+    L[n:, n:] = op.F(m) / Pr
+    L[n:, :n] = -op.tc_coef * 1j * m * op.G
+    M[:4, :] = 0.0
+    L[:4, :] = 0.0
+    L[:4, :n] = op.bc_psi
+    M[n:n + 2, :] = 0.0
+    L[n:n + 2, :] = 0.0
+    L[n:n + 2, n:] = op.bc_dir
+    return L, M
+
+
+def leading_eigenvalue(E, Pr, Ra, eta, m, n_c, guess=None):
+    L, M = pencil(E, Pr, Ra, eta, m, n_c)
+    if guess is None:
+        w = sl.eig(L, M, right=False)
+        w = w[np.isfinite(w) & (np.abs(w) < 1e8)]
+        guess = w[np.argmax(w.real)]
+    lu = sl.lu_factor(L - guess * M)
+    mu = sl.eigvals(sl.lu_solve(lu, M))
+    mu = mu[np.abs(mu) > 1e-300]
+    lam = guess + 1.0 / mu
+    lam = lam[np.abs(lam) < 1e8]
+    return lam[np.argmin(np.abs(lam - guess))]
+
+
+def critical_rayleigh_m(E, Pr, eta, m, n_c, ra_lo, ra_hi, rtol=1e-9):
+    """Ra at which the leading growth rate of mode m crosses zero."""
+    f = lambda ra: leading_eigenvalue(E, Pr, ra, eta, m, n_c).real
+    ra = brentq(f, ra_lo, ra_hi, rtol=rtol)
+    return ra, leading_eigenvalue(E, Pr, ra, eta, m, n_c)
+
+
+def critical_rayleigh(E, Pr, eta, m_values, n_c, ra_lo, ra_hi):
+    """Minimum over m of the marginal Ra: returns (Ra_c, m_c, omega_d)."""
+    best = None
+    for m in m_values:
+        ra, lam = critical_rayleigh_m(E, Pr, eta, m, n_c, ra_lo, ra_hi)
+        if best is None or ra < best[0]:
+            best = (ra, m, lam.imag)
+    return best
+
+
+def leading_eigenvalue_arnoldi(E, Pr, Ra, eta, m, n_c, guess, k=6):
+    """Eigenvalues nearest ``guess`` by Arnoldi iteration on (L - guess M)^{-1} M;
+    returns the one of largest real part among them."""
+    from scipy.sparse.linalg import LinearOperator, eigs
+    L, M = pencil(E, Pr, Ra, eta, m, n_c)
+    lu = sl.lu_factor(L - guess * M)
+    n = L.shape[0]
+    op = LinearOperator((n, n), matvec=lambda x: sl.lu_solve(lu, M @ x), dtype=complex)
+    mu = eigs(op, k=k, return_eigenvectors=False, tol=1e-13)
+    lam = guess + 1.0 / mu
+    lam = lam[np.abs(lam) < 1e8]
+    return lam[np.argmax(lam.real)]
+
+
+def marginal_rayleigh(E, Pr, eta, m, n_c, ra0, guess=None, rtol=1e-10):
+    """Ra at which the leading growth rate of mode m vanishes, by bracketing from
+    ra0 with factor-2 steps and then Brent's method; returns (Ra, lambda)."""
+    state = {"g": guess}
+    memo = {}
+
+    def tau(ra):
+        if ra in memo:
+            return memo[ra]
+        lam = None
+        if state["g"] is not None:
+            lam = leading_eigenvalue_arnoldi(E, Pr, ra, eta, m, n_c, state["g"])
+            # accept only a continuation of the same branch
+            if abs(lam.imag - state["g"].imag) > 0.2 * abs(state["g"].imag) + 1.0:
+                lam = None
+        if lam is None:
+            lam = leading_eigenvalue(E, Pr, ra, eta, m, n_c)
+        state["g"] = 1j * lam.imag
+        memo[ra] = lam.real
+        return lam.real
+
+    lo = hi = ra0
+    t0 = tau(ra0)
+    if t0 < 0:
+        while True:
+            hi *= 2.0
+            if tau(hi) > 0:
+                break
+            lo = hi
+    else:
+        while True:
+            lo /= 2.0
+            if tau(lo) < 0:
+                break
+            hi = lo
+    ra = brentq(tau, lo, hi, rtol=rtol)
+    lam = leading_eigenvalue(E, Pr, ra, eta, m, n_c, guess=state["g"])
+    return ra, lam
