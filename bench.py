@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Throughput of the IMEX time step (Mgridpoint-steps/s = n_r * n_phi * steps / s).
+
+Default workload: n_r = 257, n_phi = 768 (N_m = 256), E = 1e-5, Pr = 1,
+Ra = 10 Ra_c, radius ratio 0.35, Chebyshev integration / tau, ARS443, FP64,
+seeded initial temperature perturbation of amplitude 1e-3.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Timing: W untimed steps, then K steps, each bracketed by CUDA events on the
+library's stream, with a 256 MiB write between steps to flush the 129 MB L2
+(outside the events).  A second pass of K steps records events around every
+kernel launch for the per-kernel (roofline) numbers.  The end-to-end figure
+times set_state (pinned host buffers) + step + get_state per step.
+Multi-GPU (torchrun): independent replicas, one per rank (the step does not
+shard without an all-to-all exchange); value = all ranks' grid-point-steps /
+max time over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1902_07092_gb300 import inputs  # noqa: E402
+
+METRIC = "Mgridpoint-steps/s (n_r*n_phi*steps/s), FP64 vs mixed/batched at <=1e-6 rel err"
+UNIT = "Mgridpoint-steps/s"
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (152 SMs x 4 flop/clk x ~2.07 GHz)
+KERNELS = ("spec_to_grid", "phi_products", "grid_to_spec", "solve")
+
+
+def critical_rayleigh(E):
+    t = json.load(open(os.path.join(ROOT, "tests", "golden", "critical_rayleigh.json")))
+    return t["%g" % E]["Ra_c"]
+
+
+# ----------------------------------------------------------- flop counts ----
+def algorithmic_flops(n_r, n_phi, scheme):
+    """FP64 flops per launch of each kernel (formulas and unit counts in the design
+    notes): a complex FFT of length L counts 5 L log2 L, a complex-data DCT-I of
+    K+1 points 5 K log2 K (a length-K complex FFT), a banded apply 2 flops per
+    real x complex tap pair, the unpivoted band solve its multiply-adds."""
+    K = n_r - 1
+    M = n_phi // 3 + 1
+    nc = (2 * (n_r - 1)) // 3
+    dct = 5.0 * K * math.log2(K)
+    fft = 5.0 * n_phi * math.log2(n_phi)
+    f_s2g = M * (4 * dct + 40.0 * n_r)
+    f_phi = n_r * (4 * fft + 8.0 * n_phi)
+    band = lambda h: 4.0 * (2 * h + 1) * nc            # real band x complex vector
+    f_g2s = M * (6 * dct + 30.0 * n_r + band(8) + 2 * band(4))
+    np_, nt = nc - 4, nc - 2
+    solve_psi = np_ * (8 * 8 + 8 * 8 + 6) + 4 * 4 * np_ + 4 * 8 * np_   # LU sweeps + Schur
+    solve_th = nt * (4 * 4 + 4 * 4 + 2) + 2 * 4 * nt + 2 * 4 * nt
+    epi = band(8) * 2 + band(6) * 3 + band(8) + band(4) + 2 * band(2)
+    f_solve = M * (solve_psi + solve_th + 6 * 8.0 * nc + epi)
+    return dict(zip(KERNELS, (f_s2g, f_phi, f_g2s, f_solve)))
+
+
+def launches_per_step(scheme):
+    return {"CNAB2": 4, "SBDF2": 4, "SBDF3": 4, "ARS443": 16}[scheme]
+
+
+# --------------------------------------------------------------- clocks -----
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 4 + i and r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------ oracle arm ----
+def oracle_sample(wl, Ra, budget_s, max_steps):
+    """Time the oracle (as it stands) on the workload: steps until budget_s."""
+    from oracle.stepper import IntegrationStepper
+    n_r, n_phi = wl["n_r"], wl["n_phi"]
+    t0 = time.perf_counter()
+    st = IntegrationStepper(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
+    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"], cfg=wl["cfg"])
+    z, zu = inputs.zero_state(n_r, n_phi)
+    st.set_state(z, th, zu)
+    st.step()                                  # builds the LU factors (set-up, untimed)
+    setup = time.perf_counter() - t0
+    n, t = 0, 0.0
+    while n < max_steps and (t < budget_s or n == 0):
+        a = time.perf_counter()
+        st.step()
+        t += time.perf_counter() - a
+        n += 1
+    return n, t, setup
+
+
+def cores_used():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, wl, Ra, rank):
+    if rank != 0:
+        return
+    per_step_budget = 150.0 / max(args.steps + args.warmup, 1)
+    n, t, setup = oracle_sample(wl, Ra, budget_s=min(150.0, per_step_budget * args.steps), max_steps=args.steps)
+    gp = wl["n_r"] * wl["n_phi"]
+    val = gp * n / t / 1e6
+    sample = "%d of %d requested steps of the full %s workload (oracle set-up %.1f s untimed)" % (
+        n, args.steps, args.workload, setup)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": n, "warmup": 1, "ms_per_step": 1e3 * t / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, wl, Ra),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, wl, Ra):
+    return {"workload": args.workload, "n_r": wl["n_r"], "n_phi": wl["n_phi"], "N_m": wl["n_phi"] // 3,
+            "N_c": inputs.n_c_integration(wl["n_r"]), "E": wl["E"], "Ra": Ra, "Ra_over_Ra_c": wl["ra_factor"],
+            "Pr": wl["Pr"], "radius_ratio": wl["eta"], "scheme": wl["scheme"], "dt": wl["dt"],
+            "radial": "chebyshev-integration-tau", "l2": "flushed (256 MiB write) between timed steps",
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+# ------------------------------------------------------------ native arm ----
+def run_native(args, wl, Ra, rank, world, local_rank):
+    import torch
+    from paper_1902_07092_gb300 import binding as B
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n_r, n_phi = wl["n_r"], wl["n_phi"]
+    gp = n_r * n_phi
+    sol = B.Solver(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
+    # a dedicated stream: the library launches, the L2 flush and the timing events
+    # all go to it (torch's default stream handle is 0, which the library reads
+    # as "use your own stream")
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    B.pizza_set_stream(sol.ctx, stream.cuda_stream)
+    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"] + 1000 * rank, cfg=wl["cfg"])
+    z, zu = inputs.zero_state(n_r, n_phi)
+    sol.set_state(th, z, zu)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        sol.step(1)
+    torch.cuda.synchronize()
+
+    def timed_pass(profile):
+        evs = []
+        if profile:
+            B.pizza_profile_begin(sol.ctx, 0xF)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sol.step(1)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        prof = B.pizza_profile_end(sol.ctx) if profile else None
+        return sum(a.elapsed_time(b) for a, b in evs), prof
+
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        total_ms, _ = timed_pass(False)
+    barrier()
+    torch.cuda.synchronize()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    # per-kernel pass
+    _, (kt, kn) = timed_pass(True)
+    # end to end through host buffers
+    M, nc = sol.M, sol.n_c
+    h_th = torch.empty((M, nc), dtype=torch.complex128, pin_memory=True).numpy()
+    h_ps = torch.empty((M, nc), dtype=torch.complex128, pin_memory=True).numpy()
+    h_u = torch.empty(nc, dtype=torch.float64, pin_memory=True).numpy()
+    B.pizza_get_state(sol.ctx, h_th, h_ps, h_u)
+    k_e2e = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        B.pizza_set_state(sol.ctx, h_th, h_ps, h_u, nc)
+        B.pizza_step(sol.ctx, 1)
+        B.pizza_get_state(sol.ctx, h_th, h_ps, h_u)
+    e2e_s = time.perf_counter() - t0
+    nbytes = 2 * M * nc * 16 + nc * 8
+
+    if rank != 0:
+        sol.close()
+        return
+    value = world * gp * args.steps / (total_ms / 1e3) / 1e6
+    flops = algorithmic_flops(n_r, n_phi, wl["scheme"])
+    share = {k: float(kt[i]) / max(float(kt.sum()), 1e-30) for i, k in enumerate(KERNELS)}
+    dom = max(range(4), key=lambda i: kt[i])
+    avg_ms = float(kt[dom]) / max(int(kn[dom]), 1)
+    achieved = flops[KERNELS[dom]] / (avg_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, wl, Ra),
+        "e2e": {"value": gp * k_e2e / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "steps": k_e2e},
+        "gpu_launches": launches_per_step(wl["scheme"]) * args.steps,
+        "roofline": {"bound": "alu", "kernel": KERNELS[dom], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "nominal FP64 rate of the profiling recipe (not in MEASURED_PEAKS)",
+                     "timing": "CUDA events around each launch, second pass of the same K steps"},
+        "kernels": {k: {"launches": int(kn[i]), "avg_us": 1e3 * float(kt[i]) / max(int(kn[i]), 1),
+                        "share": share[k], "gflop_per_launch": flops[k] / 1e9} for i, k in enumerate(KERNELS)},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        n, t_cpu, _ = oracle_sample(wl, Ra, budget_s=args.cpu_budget, max_steps=1000)
+        line["cpu_baseline"] = {"value": gp * n / t_cpu / 1e6, "unit": UNIT, "cores": cores_used(),
+                                "kind": "oracle",
+                                "sample": "%d full steps of the workload on the host CPU (%.1f s)" % (n, t_cpu)}
+    print(json.dumps(line), flush=True)
+    sol.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="sparse_n257_p768", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    wl = inputs.WORKLOADS[args.workload]
+    Ra = wl["ra_factor"] * critical_rayleigh(wl["E"])
+    if args.impl == "reference":
+        run_reference(args, wl, Ra, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    run_native(args, wl, Ra, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

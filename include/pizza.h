@@ -1,0 +1,141 @@
+/*
+ * pizza.h -- C interface of a GB300 (sm_103a) implementation of one IMEX time
+ * step of the pseudo-spectral 2-D spherical quasi-geostrophic convection model
+ * of Gastine, "pizza: an open-source pseudo-spectral code for spherical
+ * quasi-geostrophic convection" (GJI 2019).
+ *
+ * The library owns all device memory it allocates; callers pass plain pointers
+ * and sizes.  Every call returns a status code (enum pizza_status); no call
+ * aborts the process.  A failing call leaves a message for pizza_last_error().
+ *
+ * Problem and notation (Section 2 of the paper):
+ *   annulus s_i <= s <= s_o with gap d = s_o - s_i = 1, radius ratio eta = s_i/s_o,
+ *   Ekman number E, Rayleigh number Ra, Prandtl number Pr; unknowns are the
+ *   temperature perturbation theta, the regularised streamfunction Psi of the
+ *   Chebyshev-integration method (Section 3.2: u_s = (h^2/s) dPsi/dphi,
+ *   u_phi = u_bar - h^2 dPsi/ds + 3 s Psi, h^2 = s_o^2 - s^2) and the
+ *   axisymmetric zonal flow u_bar.  No-slip, fixed-temperature walls; Ekman
+ *   pumping off.
+ *
+ * Discretisation (Section 3): n_phi azimuthal points with N_m = n_phi/3
+ * retained wavenumbers m = 0..N_m (Eqs. fft, ifft); n_r Gauss-Lobatto radial
+ * points x_k = cos(pi k/(n_r-1)), k = 0..n_r-1 (k = 0 is the outer wall s_o);
+ * N_c Chebyshev coefficients per mode, N_c = floor(2 (n_r-1)/3) for the
+ * integration method (Eq. psi_int and the dealiasing rule below Eq. temp_int).
+ *
+ * Spectral coefficient convention (Eq. cheb): f_m(s_k) = C sum''_{n<N_c}
+ * f_hat_{mn} T_n(x_k), C = sqrt(2/(n_r-1)), the double prime halving the n = 0
+ * term (and the n = n_r-1 term when present).  Complex arrays are interleaved
+ * (re, im) doubles with layout [m][n], m = 0..N_m, n = 0..N_c-1 (row-major).
+ */
+#ifndef PIZZA_H
+#define PIZZA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pizza_ctx pizza_ctx;
+
+/* Time schemes (Section 4, Table 1; Eqs. multistep1 and dirks).  The multistep
+ * schemes start with lower-order steps: CNAB2 uses bE = (1) on its first step,
+ * SBDF3 one SBDF1 and one SBDF2 step, SBDF2 one SBDF1 step.  ARS443 is the
+ * third-order stiffly accurate SDIRK of Ascher, Ruuth & Spiteri (1997). */
+enum pizza_scheme { PIZZA_CNAB2 = 0, PIZZA_SBDF2 = 1, PIZZA_SBDF3 = 2, PIZZA_ARS443 = 3 };
+
+enum pizza_status {
+    PIZZA_OK = 0,
+    PIZZA_EINVAL = -1,      /* invalid argument or size                          */
+    PIZZA_ENOMEM = -2,      /* device or host allocation failed                  */
+    PIZZA_ECUDA = -3,       /* a CUDA runtime call failed (message has details)  */
+    PIZZA_ENONFINITE = -4,  /* a NaN/Inf was found in the state                  */
+    PIZZA_ECFL = -5,        /* reserved: Courant criterion exceeded              */
+    PIZZA_ETIMEOUT = -6,    /* reserved: a bounded device wait gave up           */
+    PIZZA_ESTATE = -7,      /* call out of order (e.g. step before dt is set)    */
+    PIZZA_EUNSUPPORTED = -8 /* valid request this build does not implement       */
+};
+
+/* Create a context.  Validation: n_r >= 9 with n_r - 1 a power of two (the
+ * radial transform is a DCT-I evaluated by a 2(n_r-1)-point FFT); n_phi a
+ * multiple of 3 of the form 3*2^j or 2^j, n_phi >= 12; 0 < radius_ratio < 1;
+ * E, Pr > 0; scheme one of enum pizza_scheme.  Allocates the device state for
+ * the integration/tau formulation on the current CUDA device.  *out receives
+ * the context (NULL on failure).  The time step must be set with
+ * pizza_set_option(ctx, "dt", value) before pizza_step. */
+int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
+               double Pr, double radius_ratio, int scheme);
+
+/* Set a numeric option.  Keys: "dt" (time step > 0; invalidates the factored
+ * implicit operators, which are rebuilt on the next step).  Returns
+ * PIZZA_EINVAL for an unknown key or an invalid value. */
+int pizza_set_option(pizza_ctx *ctx, const char *key, double value);
+
+/* Use the given cudaStream_t (passed as void*) for all later device work of
+ * this context; NULL selects the context's own stream. */
+int pizza_set_stream(pizza_ctx *ctx, void *stream);
+
+/* Report the sizes: n_r, n_phi, N_m = n_phi/3 and N_c.  Any pointer may be NULL. */
+int pizza_get_sizes(const pizza_ctx *ctx, int *n_r, int *n_phi, int *n_m, int *n_c);
+
+/* Copy a state in.  theta_hat and psi_hat: complex [N_m+1][nc_in]; uphi0_hat:
+ * real [nc_in] (the m = 0 zonal flow).  nc_in <= N_c; missing coefficients are
+ * zero; psi_hat of m = 0 is ignored (Psi_0 = 0).  Pointers may be host or
+ * device memory (detected); the data are copied and not retained.  Resets the
+ * time-scheme history (the next step is a start-up step). */
+int pizza_set_state(pizza_ctx *ctx, const double *theta_hat, const double *psi_hat,
+                    const double *uphi0_hat, int nc_in);
+
+/* Copy the current state out (layouts as in pizza_set_state with nc_in = N_c).
+ * Host or device destination pointers; any may be NULL to skip that field.
+ * Synchronises the context stream. */
+int pizza_get_state(pizza_ctx *ctx, double *theta_hat, double *psi_hat, double *uphi0_hat);
+
+/* Advance nsteps time steps (Sections 3.2 and 4): per explicit evaluation the
+ * spectral-to-grid transforms, the grid products and forward transforms, then
+ * per implicit stage the right-hand-side assembly and the bordered banded solve
+ * of Appendix A.  Work is queued on the context stream; the call returns
+ * without waiting.  Returns PIZZA_ESTATE if dt is unset. */
+int pizza_step(pizza_ctx *ctx, int nsteps);
+
+/* Evaluate the integrated explicit right-hand sides of the current state (the
+ * bracketed terms of Eqs. psi_int and temp_int after C^I and D^I, and of
+ * Eq. uphi_int after D^I): e_psi, e_theta complex [N_m+1][N_c], e_uphi real
+ * [N_c]; rows n < 4 (psi) and n < 2 (theta, u) are zero.  Host or device
+ * destinations.  Synchronises the context stream. */
+int pizza_explicit_terms(pizza_ctx *ctx, double *e_psi, double *e_theta, double *e_uphi);
+
+/* Per-kernel timing.  pizza_profile_begin starts recording a CUDA event pair on
+ * the context stream around every later launch of the kernels selected by mask
+ * (bit 0 spectral-to-grid, bit 1 azimuthal products, bit 2 grid-to-spectral,
+ * bit 3 implicit solve).  pizza_profile_end synchronises the stream, writes the
+ * summed device time in milliseconds and the launch count of each of the four
+ * kernels into total_ms[4] and launches[4] (either may be NULL) and stops
+ * recording. */
+int pizza_profile_begin(pizza_ctx *ctx, unsigned mask);
+int pizza_profile_end(pizza_ctx *ctx, double *total_ms, int *launches);
+
+/* Block until all queued work of the context is done; returns the first
+ * deferred CUDA error, if any. */
+int pizza_synchronize(pizza_ctx *ctx);
+
+/* Host-side operator construction, exposed for verification without a GPU.
+ * which: 0 A0, 1 A2 (A^I_m = A0 + m^2 A2), 2 B0, 3 B2, 4 B4 (B^I_m = B0 + m^2 B2
+ * + m^4 B4 + i m (2/E) C^I), 5 C^I, 6 D^I, 7 F0, 8 F2 (F^I_m = F0 + m^2 F2),
+ * 9 E^I, 10 G^I = int^2 h^2.  Writes the dense n_c x n_c matrix (row-major,
+ * acting on f_hat coefficients of an n_r-point grid; rows below the number of
+ * integrations are zero) into out.  Needs no CUDA device. */
+int pizza_host_operator(int which, int n_r, int n_c, double radius_ratio, double *out);
+
+void pizza_free(pizza_ctx *ctx);
+
+/* Message of the last failing call on ctx (or of the last failing pizza_init
+ * when ctx is NULL).  Never NULL. */
+const char *pizza_last_error(const pizza_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIZZA_H */

@@ -1,0 +1,203 @@
+"""ctypes binding of libpizza (include/pizza.h).  Argument marshalling only:
+every step of the time step runs in the CUDA library.  Functions carry the C
+names; arrays may be numpy arrays (host) or torch CUDA tensors (device).
+
+Loading fails loudly if the library is missing; there is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpizza.so")
+
+PIZZA_CNAB2, PIZZA_SBDF2, PIZZA_SBDF3, PIZZA_ARS443 = 0, 1, 2, 3
+SCHEMES = {"CNAB2": 0, "SBDF2": 1, "SBDF3": 2, "ARS443": 3}
+
+STATUS = {0: "PIZZA_OK", -1: "PIZZA_EINVAL", -2: "PIZZA_ENOMEM", -3: "PIZZA_ECUDA", -4: "PIZZA_ENONFINITE",
+          -5: "PIZZA_ECFL", -6: "PIZZA_ETIMEOUT", -7: "PIZZA_ESTATE", -8: "PIZZA_EUNSUPPORTED"}
+
+# every symbol include/pizza.h declares
+EXPORTS = ("pizza_init", "pizza_set_option", "pizza_set_stream", "pizza_get_sizes", "pizza_set_state",
+           "pizza_get_state", "pizza_step", "pizza_explicit_terms", "pizza_profile_begin",
+           "pizza_profile_end", "pizza_synchronize",
+           "pizza_host_operator", "pizza_free", "pizza_last_error")
+
+_lib = None
+
+
+class PizzaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpizza.so is not built; run __graft_entry__.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip, d, i = ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_int
+    lib.pizza_init.argtypes = [ctypes.POINTER(vp), i, i, d, d, d, d, i]
+    lib.pizza_set_option.argtypes = [vp, ctypes.c_char_p, d]
+    lib.pizza_set_stream.argtypes = [vp, vp]
+    lib.pizza_get_sizes.argtypes = [vp, ip, ip, ip, ip]
+    lib.pizza_set_state.argtypes = [vp, dp, dp, dp, i]
+    lib.pizza_get_state.argtypes = [vp, dp, dp, dp]
+    lib.pizza_step.argtypes = [vp, i]
+    lib.pizza_explicit_terms.argtypes = [vp, dp, dp, dp]
+    lib.pizza_profile_begin.argtypes = [vp, ctypes.c_uint]
+    lib.pizza_profile_end.argtypes = [vp, dp, dp]
+    lib.pizza_synchronize.argtypes = [vp]
+    lib.pizza_host_operator.argtypes = [i, i, i, d, dp]
+    lib.pizza_free.argtypes = [vp]
+    lib.pizza_free.restype = None
+    lib.pizza_last_error.argtypes = [vp]
+    lib.pizza_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("pizza_free", "pizza_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        raise PizzaError(rc, load().pizza_last_error(ctx).decode())
+    return rc
+
+
+def pizza_init(n_r, n_phi, E, Ra, Pr, radius_ratio, scheme):
+    lib = load()
+    h = ctypes.c_void_p()
+    if isinstance(scheme, str):
+        scheme = SCHEMES[scheme]
+    _check(lib.pizza_init(ctypes.byref(h), n_r, n_phi, E, Ra, Pr, radius_ratio, scheme))
+    return h
+
+
+def pizza_set_option(ctx, key, value):
+    return _check(load().pizza_set_option(ctx, key.encode(), float(value)), ctx)
+
+
+def pizza_set_stream(ctx, stream):
+    return _check(load().pizza_set_stream(ctx, stream), ctx)
+
+
+def pizza_get_sizes(ctx):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().pizza_get_sizes(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return tuple(x.value for x in v)
+
+
+def pizza_set_state(ctx, theta_hat, psi_hat, uphi0_hat, nc_in):
+    return _check(load().pizza_set_state(ctx, _ptr(theta_hat), _ptr(psi_hat), _ptr(uphi0_hat), nc_in), ctx)
+
+
+def pizza_get_state(ctx, theta_hat, psi_hat, uphi0_hat):
+    return _check(load().pizza_get_state(ctx, _ptr(theta_hat), _ptr(psi_hat), _ptr(uphi0_hat)), ctx)
+
+
+def pizza_step(ctx, nsteps):
+    return _check(load().pizza_step(ctx, nsteps), ctx)
+
+
+def pizza_explicit_terms(ctx, e_psi, e_theta, e_uphi):
+    return _check(load().pizza_explicit_terms(ctx, _ptr(e_psi), _ptr(e_theta), _ptr(e_uphi)), ctx)
+
+
+KERNELS = ("spec_to_grid", "phi_products", "grid_to_spec", "solve")
+
+
+def pizza_profile_begin(ctx, mask=0xF):
+    return _check(load().pizza_profile_begin(ctx, mask), ctx)
+
+
+def pizza_profile_end(ctx):
+    t = np.zeros(4)
+    n = np.zeros(4, np.int32)
+    _check(load().pizza_profile_end(ctx, _ptr(t), _ptr(n)), ctx)
+    return t, n
+
+
+def pizza_synchronize(ctx):
+    return _check(load().pizza_synchronize(ctx), ctx)
+
+
+def pizza_host_operator(which, n_r, n_c, radius_ratio):
+    out = np.zeros((n_c, n_c))
+    _check(load().pizza_host_operator(which, n_r, n_c, radius_ratio, _ptr(out)))
+    return out
+
+
+def pizza_free(ctx):
+    load().pizza_free(ctx)
+
+
+def pizza_last_error(ctx=None):
+    return load().pizza_last_error(ctx).decode()
+
+
+class Solver:
+    """Convenience owner of one context with numpy host arrays in the C layouts
+    (complex128 [N_m+1][N_c] for theta and Psi, float64 [N_c] for u_bar)."""
+
+    def __init__(self, n_r, n_phi, E, Ra, Pr, radius_ratio, scheme, dt=None):
+        self.ctx = pizza_init(n_r, n_phi, E, Ra, Pr, radius_ratio, scheme)
+        self.n_r, self.n_phi, self.n_m, self.n_c = pizza_get_sizes(self.ctx)
+        self.M = self.n_m + 1
+        if dt is not None:
+            pizza_set_option(self.ctx, "dt", dt)
+
+    def set_state(self, theta_hat, psi_hat=None, uphi0_hat=None):
+        th = np.ascontiguousarray(theta_hat, dtype=np.complex128)
+        nc_in = th.shape[1]
+        ps = None if psi_hat is None else np.ascontiguousarray(psi_hat, dtype=np.complex128)
+        up = None if uphi0_hat is None else np.ascontiguousarray(uphi0_hat, dtype=np.float64)
+        pizza_set_state(self.ctx, th, ps, up, nc_in)
+
+    def get_state(self):
+        th = np.zeros((self.M, self.n_c), np.complex128)
+        ps = np.zeros((self.M, self.n_c), np.complex128)
+        up = np.zeros(self.n_c)
+        pizza_get_state(self.ctx, th, ps, up)
+        return ps, th, up
+
+    def step(self, n=1):
+        pizza_step(self.ctx, n)
+
+    def explicit_terms(self):
+        ep = np.zeros((self.M, self.n_c), np.complex128)
+        et = np.zeros((self.M, self.n_c), np.complex128)
+        eu = np.zeros(self.n_c)
+        pizza_explicit_terms(self.ctx, ep, et, eu)
+        return ep, et, eu
+
+    def close(self):
+        if self.ctx is not None:
+            pizza_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,775 @@
+// C interface (include/pizza.h): context set-up, factorisation of the tau
+// systems for each implicit weight, and the order of kernel launches for the
+// multistep (Eq. multistep1) and diagonally implicit (Eq. dirks) schemes of
+// Section 4 of Gastine, pizza, GJI 2019.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/pizza.h"
+#include "pizza_internal.h"
+
+using namespace pz;
+
+namespace {
+
+thread_local std::string g_init_error = "no error";
+
+constexpr int NVEC = 16;
+
+}  // namespace
+
+struct pizza_ctx {
+    int n_r = 0, n_phi = 0, n_m = 0, M = 0, nc = 0, K = 0, scheme = 0;
+    double E = 0, Ra = 0, Pr = 0, eta = 0, dt = 0;
+    bool dt_set = false;
+    int device = 0;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    std::vector<void*> allocs;
+    StepParams P{};
+    double2 *G1 = nullptr, *G2 = nullptr;
+    VecSet vec[NVEC]{};
+    std::vector<double> gammas;          // implicit weights in use
+    std::vector<DevFactors> factors;     // one per gamma (empty until built)
+    std::vector<std::vector<void*>> factor_allocs;
+    // scheme bookkeeping
+    int n_done = 0;
+    bool aux_valid = false;  // mass/imp of the current state computed
+    // multistep rings (indices into vec)
+    int ys[2]{}, es[4]{}, ms[3]{}, is[3]{};
+    // DIRK slots
+    int stage_y[4]{}, stage_e[4]{}, stage_imp[4]{}, mass_n = 0;
+    std::string err = "no error";
+    // per-kernel event timing
+    unsigned prof_mask = 0;
+    struct ProfRec {
+        int kernel;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+int fail(pizza_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_init_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ctx, PIZZA_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+template <class T>
+T* dalloc(pizza_ctx* ctx, size_t n, std::vector<void*>& list) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(T) + 16) != cudaSuccess) return nullptr;
+    list.push_back(p);
+    return static_cast<T*>(p);
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+bool make_plan(int L, FftPlan& pl) {
+    int n = L, np = 0;
+    if (n % 3 == 0) {
+        pl.radix[np++] = 3;
+        n /= 3;
+    }
+    if (!pow2(n)) return false;
+    while (n % 4 == 0) {
+        pl.radix[np++] = 4;
+        n /= 4;
+    }
+    while (n % 2 == 0) {
+        pl.radix[np++] = 2;
+        n /= 2;
+    }
+    pl.L = L;
+    pl.npass = np;
+    return np <= MAX_PASSES;
+}
+
+std::vector<double2> twiddles(int L) {
+    std::vector<double2> t(L);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int j = 0; j < L; ++j) {
+        long double a = 2.0L * pi * (long double)j / (long double)L;
+        t[j] = make_double2((double)cosl(a), (double)(-sinl(a)));
+    }
+    return t;
+}
+
+int cuda_check(pizza_ctx* ctx, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return fail(ctx, PIZZA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return PIZZA_OK;
+}
+
+void free_factors(pizza_ctx* ctx) {
+    for (auto& l : ctx->factor_allocs)
+        for (void* p : l) cudaFree(p);
+    ctx->factor_allocs.clear();
+    ctx->factors.clear();
+}
+
+std::vector<double> scheme_gammas(int scheme) {
+    switch (scheme) {
+        case PIZZA_CNAB2: return {0.5};
+        case PIZZA_SBDF2: return {1.0, 2.0 / 3.0};
+        case PIZZA_SBDF3: return {1.0, 2.0 / 3.0, 6.0 / 11.0};
+        case PIZZA_ARS443: return {0.5};
+    }
+    return {};
+}
+
+// ---------------------------------------------------------------------------
+// Factorisation (host) of the tau systems for one implicit weight.
+// ---------------------------------------------------------------------------
+struct HostOps {
+    std::vector<double> band[OP_COUNT];  // band storage with each operator's own half width
+};
+
+int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F, std::vector<void*>& al) {
+    const int M = ctx->M, nc = ctx->nc, np = nc - 4, nt = nc - 2;
+    const double gdt = gamma * ctx->dt;
+    const auto tauP = tau_rows_psi(ctx->n_r, nc);
+    const auto tauD = tau_rows_dir(ctx->n_r, nc);
+    std::vector<double2> hpL((size_t)M * np * 8), hpU((size_t)M * np * 8), hpD((size_t)M * np),
+        hpY((size_t)M * np * 4), hpS((size_t)M * 16);
+    std::vector<double> htL((size_t)M * nt * 4), htU((size_t)M * nt * 4), htD((size_t)M * nt),
+        htY((size_t)M * nt * 2), htS((size_t)M * 4);
+    std::vector<int> bad(M, 0);
+    auto get = [&](int id, int k, int n) -> double {
+        const int h = op_h(id);
+        const int d = n - k + h;
+        if (d < 0 || d > 2 * h) return 0.0;
+        return H.band[id][(size_t)k * (2 * h + 1) + d];
+    };
+    auto work = [&](int m0, int m1) {
+        std::vector<cplx> bp((size_t)nc * 17);
+        std::vector<double> bt((size_t)nc * 9);
+        for (int m = m0; m < m1; ++m) {
+            const double mu = (double)m * m, dm = (double)m;
+            // streamfunction: A_m - gdt B_m, half width 8
+            if (m > 0) {
+                for (int k = 0; k < nc; ++k)
+                    for (int d = 0; d < 17; ++d) {
+                        const int n = k - 8 + d;
+                        cplx v(0.0, 0.0);
+                        if (n >= 0 && n < nc && k >= 4) {
+                            const double a = get(OP_A0, k, n) + mu * get(OP_A2, k, n);
+                            const double b = get(OP_B0, k, n) + mu * (get(OP_B2, k, n) + mu * get(OP_B4, k, n));
+                            const double c = get(OP_C, k, n);
+                            v = cplx(a - gdt * b, -gdt * 2.0 * dm / ctx->E * c);
+                        }
+                        bp[(size_t)k * 17 + d] = v;
+                    }
+                Bordered<cplx> f;
+                if (!factor_bordered(bp, nc, 8, tauP, 4, f)) {
+                    bad[m] = 1;
+                    continue;
+                }
+                for (size_t i = 0; i < (size_t)np * 8; ++i) {
+                    hpL[(size_t)m * np * 8 + i] = make_double2(f.L[i].real(), f.L[i].imag());
+                    hpU[(size_t)m * np * 8 + i] = make_double2(f.U[i].real(), f.U[i].imag());
+                }
+                for (int i = 0; i < np; ++i) hpD[(size_t)m * np + i] = make_double2(f.invd[i].real(), f.invd[i].imag());
+                for (size_t i = 0; i < (size_t)np * 4; ++i)
+                    hpY[(size_t)m * np * 4 + i] = make_double2(f.Y[i].real(), f.Y[i].imag());
+                for (int i = 0; i < 16; ++i) hpS[(size_t)m * 16 + i] = make_double2(f.Sinv[i].real(), f.Sinv[i].imag());
+            }
+            // temperature: D - gdt F_m / Pr, half width 4
+            for (int k = 0; k < nc; ++k)
+                for (int d = 0; d < 9; ++d) {
+                    const int n = k - 4 + d;
+                    double v = 0.0;
+                    if (n >= 0 && n < nc && k >= 2)
+                        v = get(OP_D, k, n) - gdt * (get(OP_F0, k, n) + mu * get(OP_F2, k, n)) / ctx->Pr;
+                    bt[(size_t)k * 9 + d] = v;
+                }
+            Bordered<double> g;
+            if (!factor_bordered(bt, nc, 4, tauD, 2, g)) {
+                bad[m] = 1;
+                continue;
+            }
+            std::copy(g.L.begin(), g.L.end(), htL.begin() + (size_t)m * nt * 4);
+            std::copy(g.U.begin(), g.U.end(), htU.begin() + (size_t)m * nt * 4);
+            std::copy(g.invd.begin(), g.invd.end(), htD.begin() + (size_t)m * nt);
+            std::copy(g.Y.begin(), g.Y.end(), htY.begin() + (size_t)m * nt * 2);
+            std::copy(g.Sinv.begin(), g.Sinv.end(), htS.begin() + (size_t)m * 4);
+        }
+    };
+    unsigned nthr = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    const int chunk = (M + (int)nthr - 1) / (int)nthr;
+    for (unsigned t = 0; t < nthr; ++t) {
+        int a = (int)t * chunk, b = std::min(M, a + chunk);
+        if (a < b) th.emplace_back(work, a, b);
+    }
+    for (auto& t : th) t.join();
+    for (int m = 0; m < M; ++m)
+        if (bad[m]) return fail(ctx, PIZZA_EINVAL, "tau system of mode m=%d is singular", m);
+    // zonal flow: D - gdt E^I
+    std::vector<double> bu((size_t)nc * 9);
+    for (int k = 0; k < nc; ++k)
+        for (int d = 0; d < 9; ++d) {
+            const int n = k - 4 + d;
+            double v = 0.0;
+            if (n >= 0 && n < nc && k >= 2) v = get(OP_D, k, n) - gdt * get(OP_EZ, k, n);
+            bu[(size_t)k * 9 + d] = v;
+        }
+    Bordered<double> fu;
+    if (!factor_bordered(bu, nc, 4, tauD, 2, fu)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
+
+    F.gdt = gdt;
+#define UPLOAD(dst, T, hv)                                                                        \
+    do {                                                                                          \
+        dst = dalloc<T>(ctx, (hv).size(), al);                                                    \
+        if (!dst) return fail(ctx, PIZZA_ENOMEM, "device allocation of factors failed");          \
+        CK(cudaMemcpy(dst, (hv).data(), (hv).size() * sizeof(T), cudaMemcpyHostToDevice));       \
+    } while (0)
+    UPLOAD(F.pL, double2, hpL);
+    UPLOAD(F.pU, double2, hpU);
+    UPLOAD(F.pInvd, double2, hpD);
+    UPLOAD(F.pY, double2, hpY);
+    UPLOAD(F.pSinv, double2, hpS);
+    UPLOAD(F.tL, double, htL);
+    UPLOAD(F.tU, double, htU);
+    UPLOAD(F.tInvd, double, htD);
+    UPLOAD(F.tY, double, htY);
+    UPLOAD(F.tSinv, double, htS);
+    UPLOAD(F.uL, double, fu.L);
+    UPLOAD(F.uU, double, fu.U);
+    UPLOAD(F.uInvd, double, fu.invd);
+    UPLOAD(F.uY, double, fu.Y);
+    UPLOAD(F.uSinv, double, fu.Sinv);
+#undef UPLOAD
+    return PIZZA_OK;
+}
+
+HostOps host_ops_of(pizza_ctx* ctx) {
+    HostOps H;
+    Geom g = make_geom(ctx->eta);
+    for (int id = 0; id < OP_COUNT; ++id)
+        H.band[id] = to_band(build_operator(id, ctx->n_r, ctx->nc, g), ctx->nc, op_h(id));
+    return H;
+}
+
+int ensure_factors(pizza_ctx* ctx) {
+    if (!ctx->factors.empty()) return PIZZA_OK;
+    if (!ctx->dt_set) return fail(ctx, PIZZA_ESTATE, "dt is not set (pizza_set_option(ctx, \"dt\", v))");
+    HostOps H = host_ops_of(ctx);
+    ctx->gammas = scheme_gammas(ctx->scheme);
+    for (double g : ctx->gammas) {
+        DevFactors F{};
+        std::vector<void*> al;
+        int rc = build_factors(ctx, H, g, F, al);
+        ctx->factor_allocs.push_back(al);
+        if (rc != PIZZA_OK) {
+            free_factors(ctx);
+            return rc;
+        }
+        ctx->factors.push_back(F);
+    }
+    return PIZZA_OK;
+}
+
+const DevFactors* factors_for(pizza_ctx* ctx, double gamma) {
+    for (size_t i = 0; i < ctx->gammas.size(); ++i)
+        if (std::fabs(ctx->gammas[i] - gamma) < 1e-14) return &ctx->factors[i];
+    return nullptr;
+}
+
+void reset_slots(pizza_ctx* ctx) {
+    // vec indices: 0,1 state ring; 2..5 explicit ring; 6..8 mass ring; 9..11 imp ring
+    ctx->ys[0] = 0; ctx->ys[1] = 1;
+    for (int i = 0; i < 4; ++i) ctx->es[i] = 2 + i;
+    for (int i = 0; i < 3; ++i) ctx->ms[i] = 6 + i;
+    for (int i = 0; i < 3; ++i) ctx->is[i] = 9 + i;
+    // DIRK: stage states 12..14 (y_1..y_3), explicit 2..5 (e_0..e_3), imp 9..11 (I_1..I_3), mass 6
+    ctx->stage_y[1] = 12; ctx->stage_y[2] = 13; ctx->stage_y[3] = 14;
+    for (int i = 0; i < 4; ++i) ctx->stage_e[i] = 2 + i;
+    ctx->stage_imp[1] = 9; ctx->stage_imp[2] = 10; ctx->stage_imp[3] = 11;
+    ctx->mass_n = 6;
+    ctx->n_done = 0;
+    ctx->aux_valid = false;
+}
+
+cudaEvent_t pool_event(pizza_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch through f(), bracketed by an event pair when kernel id k is profiled.
+template <class F>
+cudaError_t timed_launch(pizza_ctx* ctx, int k, F&& f) {
+    if (!(ctx->prof_mask & (1u << k))) return f();
+    pizza_ctx::ProfRec r{k, pool_event(ctx), pool_event(ctx)};
+    cudaEventRecord(r.a, ctx->stream);
+    cudaError_t e = f();
+    cudaEventRecord(r.b, ctx->stream);
+    ctx->prof.push_back(r);
+    return e;
+}
+
+int explicit_eval(pizza_ctx* ctx, VecSet y, VecSet e) {
+    CK(timed_launch(ctx, 0, [&] { return launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream); }));
+    CK(timed_launch(ctx, 1, [&] { return launch_phi_products(ctx->P, ctx->G1, ctx->G2, ctx->stream); }));
+    CK(timed_launch(ctx, 2, [&] { return launch_grid_to_spec(ctx->P, ctx->G2, y, e, ctx->stream); }));
+    return PIZZA_OK;
+}
+
+bool is_multistep(int scheme) { return scheme != PIZZA_ARS443; }
+
+// (a, b0, bI, bE) of Eq. multistep1 with the start-up rule
+void multistep_coeffs(int scheme, int n_done, std::vector<double>& a, double& b0, std::vector<double>& bI,
+                      std::vector<double>& bE) {
+    if (scheme == PIZZA_CNAB2) {
+        a = {1.0};
+        b0 = 0.5;
+        bI = {0.5};
+        bE = (n_done == 0) ? std::vector<double>{1.0} : std::vector<double>{1.5, -0.5};
+        return;
+    }
+    int order = (scheme == PIZZA_SBDF2) ? 2 : 3;
+    int k = std::min(order, n_done + 1);
+    if (k == 1) {
+        a = {1.0}; b0 = 1.0; bI = {0.0}; bE = {1.0};
+    } else if (k == 2) {
+        a = {4.0 / 3.0, -1.0 / 3.0}; b0 = 2.0 / 3.0; bI = {0.0, 0.0}; bE = {4.0 / 3.0, -2.0 / 3.0};
+    } else {
+        a = {18.0 / 11.0, -9.0 / 11.0, 2.0 / 11.0}; b0 = 6.0 / 11.0; bI = {0.0, 0.0, 0.0};
+        bE = {18.0 / 11.0, -18.0 / 11.0, 6.0 / 11.0};
+    }
+}
+
+// ARS443 tableau (Ascher, Ruuth & Spiteri 1997, Section 2.8), stage 0 = y_n
+const double ARS_AI[5][5] = {{0, 0, 0, 0, 0},
+                             {0, 0.5, 0, 0, 0},
+                             {0, 1.0 / 6.0, 0.5, 0, 0},
+                             {0, -0.5, 0.5, 0.5, 0},
+                             {0, 1.5, -1.5, 0.5, 0.5}};
+const double ARS_AE[5][5] = {{0, 0, 0, 0, 0},
+                             {0.5, 0, 0, 0, 0},
+                             {11.0 / 18.0, 1.0 / 18.0, 0, 0, 0},
+                             {5.0 / 6.0, -5.0 / 6.0, 0.5, 0, 0},
+                             {0.25, 1.75, 0.75, -1.75, 0}};
+
+int ensure_aux(pizza_ctx* ctx) {
+    if (ctx->aux_valid) return PIZZA_OK;
+    VecSet y = ctx->vec[ctx->ys[0]];
+    if (is_multistep(ctx->scheme)) {
+        CK(launch_apply(ctx->P, y, ctx->vec[ctx->ms[0]], ctx->vec[ctx->is[0]], true,
+                        ctx->scheme == PIZZA_CNAB2, ctx->stream));
+    } else {
+        CK(launch_apply(ctx->P, y, ctx->vec[ctx->mass_n], ctx->vec[ctx->mass_n], true, false, ctx->stream));
+    }
+    ctx->aux_valid = true;
+    return PIZZA_OK;
+}
+
+int step_multistep(pizza_ctx* ctx) {
+    std::vector<double> a, bI, bE;
+    double b0;
+    multistep_coeffs(ctx->scheme, ctx->n_done, a, b0, bI, bE);
+    const double dt = ctx->dt;
+    // rotate explicit ring: new e^n goes to the oldest slot
+    int e_new = ctx->es[3];
+    for (int i = 3; i > 0; --i) ctx->es[i] = ctx->es[i - 1];
+    ctx->es[0] = e_new;
+    int rc = explicit_eval(ctx, ctx->vec[ctx->ys[0]], ctx->vec[ctx->es[0]]);
+    if (rc) return rc;
+    RhsSpec R{};
+    for (size_t j = 0; j < a.size(); ++j) R.t[R.nterms++] = {ctx->vec[ctx->ms[j]], a[j]};
+    for (size_t j = 0; j < bI.size(); ++j)
+        if (bI[j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->is[j]], dt * bI[j]};
+    for (size_t j = 0; j < bE.size(); ++j) R.t[R.nterms++] = {ctx->vec[ctx->es[j]], dt * bE[j]};
+    const DevFactors* F = factors_for(ctx, b0);
+    if (!F) return fail(ctx, PIZZA_EINVAL, "no factors for implicit weight %g", b0);
+    // outputs overwrite the oldest mass / imp slots (each CTA reads its rows first)
+    const int m_new = ctx->ms[2], i_new = ctx->is[2];
+    const bool want_imp = (ctx->scheme == PIZZA_CNAB2);
+    CK(timed_launch(ctx, 3, [&] {
+        return launch_solve(ctx->P, R, *F, ctx->vec[ctx->ys[1]], ctx->vec[m_new], ctx->vec[i_new], true, want_imp,
+                            ctx->stream);
+    }));
+    std::swap(ctx->ys[0], ctx->ys[1]);
+    ctx->ms[2] = ctx->ms[1]; ctx->ms[1] = ctx->ms[0]; ctx->ms[0] = m_new;
+    ctx->is[2] = ctx->is[1]; ctx->is[1] = ctx->is[0]; ctx->is[0] = i_new;
+    return PIZZA_OK;
+}
+
+int step_dirk(pizza_ctx* ctx) {
+    const double dt = ctx->dt;
+    const int nu = 4;
+    for (int i = 1; i <= nu; ++i) {
+        VecSet y_prev = (i == 1) ? ctx->vec[ctx->ys[0]] : ctx->vec[ctx->stage_y[i - 1]];
+        int rc = explicit_eval(ctx, y_prev, ctx->vec[ctx->stage_e[i - 1]]);
+        if (rc) return rc;
+        RhsSpec R{};
+        R.t[R.nterms++] = {ctx->vec[ctx->mass_n], 1.0};
+        for (int j = 0; j < i; ++j) {
+            if (ARS_AE[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_e[j]], dt * ARS_AE[i][j]};
+            if (j >= 1 && ARS_AI[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_imp[j]], dt * ARS_AI[i][j]};
+        }
+        const DevFactors* F = factors_for(ctx, ARS_AI[i][i]);
+        if (!F) return fail(ctx, PIZZA_EINVAL, "no factors for a_ii");
+        if (i < nu) {
+            CK(timed_launch(ctx, 3, [&] {
+                return launch_solve(ctx->P, R, *F, ctx->vec[ctx->stage_y[i]], ctx->vec[ctx->mass_n],
+                                    ctx->vec[ctx->stage_imp[i]], false, true, ctx->stream);
+            }));
+        } else {
+            // y_{n+1} = y_nu (stiffly accurate); its mass term replaces Mass(y_n)
+            CK(timed_launch(ctx, 3, [&] {
+                return launch_solve(ctx->P, R, *F, ctx->vec[ctx->ys[1]], ctx->vec[ctx->mass_n],
+                                    ctx->vec[ctx->mass_n], true, false, ctx->stream);
+            }));
+        }
+    }
+    std::swap(ctx->ys[0], ctx->ys[1]);
+    return PIZZA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double Pr, double radius_ratio,
+               int scheme) {
+    if (!out) return fail(nullptr, PIZZA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_r < 9 || !pow2(n_r - 1) || n_r > 2049)
+        return fail(nullptr, PIZZA_EINVAL, "n_r must be 2^j + 1 with 9 <= n_r <= 2049 (got %d)", n_r);
+    if (n_phi < 12 || n_phi % 3 != 0 || !pow2(n_phi / 3) || n_phi > 6144)
+        return fail(nullptr, PIZZA_EINVAL, "n_phi must be 3*2^j with 12 <= n_phi <= 6144 (got %d)", n_phi);
+    if (!(radius_ratio > 0.0 && radius_ratio < 1.0)) return fail(nullptr, PIZZA_EINVAL, "radius_ratio not in (0,1)");
+    if (!(E > 0.0) || !(Pr > 0.0) || !std::isfinite(Ra)) return fail(nullptr, PIZZA_EINVAL, "E, Pr must be > 0");
+    if (scheme < PIZZA_CNAB2 || scheme > PIZZA_ARS443) return fail(nullptr, PIZZA_EINVAL, "unknown scheme %d", scheme);
+
+    pizza_ctx* ctx = new pizza_ctx();
+    ctx->n_r = n_r;
+    ctx->n_phi = n_phi;
+    ctx->n_m = n_phi / 3;
+    ctx->M = ctx->n_m + 1;
+    ctx->K = n_r - 1;
+    ctx->nc = (2 * (n_r - 1)) / 3;
+    ctx->E = E;
+    ctx->Ra = Ra;
+    ctx->Pr = Pr;
+    ctx->eta = radius_ratio;
+    ctx->scheme = scheme;
+    auto bail = [&](int rc) {
+        g_init_error = ctx->err;
+        pizza_free(ctx);
+        return rc;
+    };
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        ctx->err = "no CUDA device available";
+        return bail(PIZZA_ECUDA);
+    }
+    if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        ctx->err = "cudaStreamCreate failed";
+        return bail(PIZZA_ECUDA);
+    }
+    ctx->stream = ctx->own_stream;
+
+    Geom g = make_geom(radius_ratio);
+    StepParams& P = ctx->P;
+    P.n_r = n_r;
+    P.n_phi = n_phi;
+    P.n_m = ctx->n_m;
+    P.M = ctx->M;
+    P.nc = ctx->nc;
+    P.K = ctx->K;
+    P.E = E;
+    P.Ra = Ra;
+    P.Pr = Pr;
+    P.s_o = g.s_o;
+    P.inv_a = 1.0 / g.a;
+    P.tc = tc_coefficient(radius_ratio);
+    P.cnorm = std::sqrt(2.0 / (n_r - 1));
+
+    std::vector<double> s(n_r), h2(n_r), is(n_r);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int k = 0; k < n_r; ++k) {
+        double x = (double)cosl(pi * (long double)k / (long double)(n_r - 1));
+        s[k] = g.a * x + g.b;
+        h2[k] = g.s_o * g.s_o - s[k] * s[k];
+        is[k] = 1.0 / s[k];
+    }
+    h2[0] = 0.0;  // x_0 = 1 is the outer wall exactly
+    auto& al = ctx->allocs;
+    double* ds = dalloc<double>(ctx, n_r, al);
+    double* dh = dalloc<double>(ctx, n_r, al);
+    double* di = dalloc<double>(ctx, n_r, al);
+    if (!ds || !dh || !di) {
+        ctx->err = "device allocation failed";
+        return bail(PIZZA_ENOMEM);
+    }
+    int rc = PIZZA_OK;
+    auto up = [&](void* d, const void* h, size_t bytes) {
+        if (rc == PIZZA_OK && cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            ctx->err = "cudaMemcpy failed";
+            rc = PIZZA_ECUDA;
+        }
+    };
+    up(ds, s.data(), n_r * 8);
+    up(dh, h2.data(), n_r * 8);
+    up(di, is.data(), n_r * 8);
+    P.s = ds;
+    P.h2 = dh;
+    P.inv_s = di;
+
+    if (!make_plan(2 * ctx->K, P.plan_r) || !make_plan(n_phi, P.plan_p)) {
+        ctx->err = "unsupported transform length";
+        return bail(PIZZA_EINVAL);
+    }
+    auto twr = twiddles(2 * ctx->K), twp = twiddles(n_phi);
+    double2* dtwr = dalloc<double2>(ctx, twr.size(), al);
+    double2* dtwp = dalloc<double2>(ctx, twp.size(), al);
+    if (!dtwr || !dtwp) {
+        ctx->err = "device allocation failed";
+        return bail(PIZZA_ENOMEM);
+    }
+    up(dtwr, twr.data(), twr.size() * sizeof(double2));
+    up(dtwp, twp.data(), twp.size() * sizeof(double2));
+    P.plan_r.tw = dtwr;
+    P.plan_p.tw = dtwp;
+
+    // m-independent banded operators and tau rows
+    HostOps H = host_ops_of(ctx);
+    for (int id = 0; id < OP_COUNT; ++id) {
+        double* d = dalloc<double>(ctx, H.band[id].size(), al);
+        if (!d) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(d, H.band[id].data(), H.band[id].size() * 8);
+        P.ops.band[id] = d;
+    }
+    {
+        const int nc = ctx->nc;
+        auto tp = tau_rows_psi(n_r, nc), td = tau_rows_dir(n_r, nc);
+        std::vector<double> bp((size_t)4 * (nc - 4)), bd((size_t)2 * (nc - 2));
+        for (int r = 0; r < 4; ++r)
+            for (int j = 0; j < nc - 4; ++j) bp[(size_t)r * (nc - 4) + j] = tp[(size_t)r * nc + 4 + j];
+        for (int r = 0; r < 2; ++r)
+            for (int j = 0; j < nc - 2; ++j) bd[(size_t)r * (nc - 2) + j] = td[(size_t)r * nc + 2 + j];
+        double* dp = dalloc<double>(ctx, bp.size(), al);
+        double* dd = dalloc<double>(ctx, bd.size(), al);
+        if (!dp || !dd) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(dp, bp.data(), bp.size() * 8);
+        up(dd, bd.data(), bd.size() * 8);
+        P.ops.tau_psi_B = dp;
+        P.ops.tau_dir_B = dd;
+    }
+    // work buffers and state vectors
+    const size_t gsz = (size_t)n_r * 4 * ctx->M;
+    ctx->G1 = dalloc<double2>(ctx, gsz, al);
+    ctx->G2 = dalloc<double2>(ctx, gsz, al);
+    if (!ctx->G1 || !ctx->G2) {
+        ctx->err = "device allocation of grid buffers failed";
+        return bail(PIZZA_ENOMEM);
+    }
+    const size_t vsz = (size_t)ctx->M * ctx->nc;
+    for (int i = 0; i < NVEC; ++i) {
+        ctx->vec[i].psi = dalloc<double2>(ctx, vsz, al);
+        ctx->vec[i].th = dalloc<double2>(ctx, vsz, al);
+        ctx->vec[i].u = dalloc<double>(ctx, ctx->nc, al);
+        if (!ctx->vec[i].psi || !ctx->vec[i].th || !ctx->vec[i].u) {
+            ctx->err = "device allocation of state vectors failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        if (rc == PIZZA_OK && (cudaMemset(ctx->vec[i].psi, 0, vsz * 16) != cudaSuccess ||
+                               cudaMemset(ctx->vec[i].th, 0, vsz * 16) != cudaSuccess ||
+                               cudaMemset(ctx->vec[i].u, 0, ctx->nc * 8) != cudaSuccess)) {
+            ctx->err = "cudaMemset failed";
+            rc = PIZZA_ECUDA;
+        }
+    }
+    if (rc != PIZZA_OK) return bail(rc);
+    reset_slots(ctx);
+    *out = ctx;
+    return PIZZA_OK;
+}
+
+int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
+    if (!ctx || !key) return fail(ctx, PIZZA_EINVAL, "NULL argument");
+    if (std::strcmp(key, "dt") == 0) {
+        if (!(value > 0.0) || !std::isfinite(value)) return fail(ctx, PIZZA_EINVAL, "dt must be > 0");
+        if (ctx->dt_set && value == ctx->dt) return PIZZA_OK;
+        cudaStreamSynchronize(ctx->stream);
+        free_factors(ctx);
+        ctx->dt = value;
+        ctx->dt_set = true;
+        return PIZZA_OK;
+    }
+    return fail(ctx, PIZZA_EINVAL, "unknown option '%s'", key);
+}
+
+int pizza_set_stream(pizza_ctx* ctx, void* stream) {
+    if (!ctx) return PIZZA_EINVAL;
+    ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own_stream;
+    return PIZZA_OK;
+}
+
+int pizza_get_sizes(const pizza_ctx* ctx, int* n_r, int* n_phi, int* n_m, int* n_c) {
+    if (!ctx) return PIZZA_EINVAL;
+    if (n_r) *n_r = ctx->n_r;
+    if (n_phi) *n_phi = ctx->n_phi;
+    if (n_m) *n_m = ctx->n_m;
+    if (n_c) *n_c = ctx->nc;
+    return PIZZA_OK;
+}
+
+int pizza_set_state(pizza_ctx* ctx, const double* theta_hat, const double* psi_hat, const double* uphi0_hat,
+                    int nc_in) {
+    if (!ctx) return PIZZA_EINVAL;
+    if (nc_in < 0 || nc_in > ctx->nc) return fail(ctx, PIZZA_EINVAL, "nc_in must be in [0, %d]", ctx->nc);
+    reset_slots(ctx);
+    VecSet y = ctx->vec[ctx->ys[0]];
+    const size_t M = ctx->M, nc = ctx->nc;
+    CK(cudaMemsetAsync(y.psi, 0, M * nc * 16, ctx->stream));
+    CK(cudaMemsetAsync(y.th, 0, M * nc * 16, ctx->stream));
+    CK(cudaMemsetAsync(y.u, 0, nc * 8, ctx->stream));
+    if (nc_in > 0) {
+        if (theta_hat)
+            CK(cudaMemcpy2DAsync(y.th, nc * 16, theta_hat, (size_t)nc_in * 16, (size_t)nc_in * 16, M,
+                                 cudaMemcpyDefault, ctx->stream));
+        if (psi_hat && M > 1)
+            CK(cudaMemcpy2DAsync(y.psi + nc, nc * 16, psi_hat + 2 * (size_t)nc_in, (size_t)nc_in * 16,
+                                 (size_t)nc_in * 16, M - 1, cudaMemcpyDefault, ctx->stream));
+        if (uphi0_hat) CK(cudaMemcpyAsync(y.u, uphi0_hat, (size_t)nc_in * 8, cudaMemcpyDefault, ctx->stream));
+    }
+    // keep the host buffers valid only for the duration of the call
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIZZA_OK;
+}
+
+int pizza_get_state(pizza_ctx* ctx, double* theta_hat, double* psi_hat, double* uphi0_hat) {
+    if (!ctx) return PIZZA_EINVAL;
+    VecSet y = ctx->vec[ctx->ys[0]];
+    const size_t M = ctx->M, nc = ctx->nc;
+    if (theta_hat) CK(cudaMemcpyAsync(theta_hat, y.th, M * nc * 16, cudaMemcpyDefault, ctx->stream));
+    if (psi_hat) CK(cudaMemcpyAsync(psi_hat, y.psi, M * nc * 16, cudaMemcpyDefault, ctx->stream));
+    if (uphi0_hat) CK(cudaMemcpyAsync(uphi0_hat, y.u, nc * 8, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIZZA_OK;
+}
+
+int pizza_step(pizza_ctx* ctx, int nsteps) {
+    if (!ctx) return PIZZA_EINVAL;
+    if (nsteps < 0) return fail(ctx, PIZZA_EINVAL, "nsteps < 0");
+    int rc = ensure_factors(ctx);
+    if (rc) return rc;
+    rc = ensure_aux(ctx);
+    if (rc) return rc;
+    for (int s = 0; s < nsteps; ++s) {
+        rc = is_multistep(ctx->scheme) ? step_multistep(ctx) : step_dirk(ctx);
+        if (rc) return rc;
+        ctx->n_done++;
+    }
+    return PIZZA_OK;
+}
+
+int pizza_explicit_terms(pizza_ctx* ctx, double* e_psi, double* e_theta, double* e_uphi) {
+    if (!ctx) return PIZZA_EINVAL;
+    // scratch slot 15 is not used by either scheme
+    VecSet e = ctx->vec[15];
+    int rc = explicit_eval(ctx, ctx->vec[ctx->ys[0]], e);
+    if (rc) return rc;
+    const size_t M = ctx->M, nc = ctx->nc;
+    if (e_psi) CK(cudaMemcpyAsync(e_psi, e.psi, M * nc * 16, cudaMemcpyDefault, ctx->stream));
+    if (e_theta) CK(cudaMemcpyAsync(e_theta, e.th, M * nc * 16, cudaMemcpyDefault, ctx->stream));
+    if (e_uphi) CK(cudaMemcpyAsync(e_uphi, e.u, nc * 8, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIZZA_OK;
+}
+
+int pizza_profile_begin(pizza_ctx* ctx, unsigned mask) {
+    if (!ctx) return PIZZA_EINVAL;
+    ctx->prof_mask = mask & 0xFu;
+    return PIZZA_OK;
+}
+
+int pizza_profile_end(pizza_ctx* ctx, double* total_ms, int* launches) {
+    if (!ctx) return PIZZA_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    double t[4] = {0, 0, 0, 0};
+    int n[4] = {0, 0, 0, 0};
+    for (auto& r : ctx->prof) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        t[r.kernel] += ms;
+        n[r.kernel] += 1;
+        ctx->event_pool.push_back(r.a);
+        ctx->event_pool.push_back(r.b);
+    }
+    ctx->prof.clear();
+    ctx->prof_mask = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (total_ms) total_ms[k] = t[k];
+        if (launches) launches[k] = n[k];
+    }
+    return PIZZA_OK;
+}
+
+int pizza_synchronize(pizza_ctx* ctx) {
+    if (!ctx) return PIZZA_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    return PIZZA_OK;
+}
+
+int pizza_host_operator(int which, int n_r, int n_c, double radius_ratio, double* out) {
+    if (which < 0 || which >= OP_COUNT || n_r < 3 || n_c < 5 || n_c > n_r || !out ||
+        !(radius_ratio > 0 && radius_ratio < 1))
+        return fail(nullptr, PIZZA_EINVAL, "invalid arguments to pizza_host_operator");
+    auto M = build_operator(which, n_r, n_c, make_geom(radius_ratio));
+    std::memcpy(out, M.data(), M.size() * sizeof(double));
+    return PIZZA_OK;
+}
+
+void pizza_free(pizza_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_factors(ctx);
+    for (auto& r : ctx->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+const char* pizza_last_error(const pizza_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Device helpers: complex arithmetic, CTA-cooperative mixed-radix Stockham FFT in
+// shared memory, the DCT-I of the Gauss-Lobatto grid (Eqs. cheb and icheb of
+// Section 3) through an FFT of the even extension, and the Chebyshev derivative
+// of plain coefficients by a parity-split suffix scan.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pizza_internal.h"
+
+namespace pz {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// multiply by i*t (t real)
+__device__ __forceinline__ double2 cmul_i(double2 a, double t) { return make_double2(-a.y * t, a.x * t); }
+
+// One Stockham pass of radix R over a batch of nb transforms of length L.
+// SIGN = -1: forward  sum_j x_j exp(-2 pi i jk/L);  SIGN = +1: backward (unscaled).
+template <int SIGN, int R>
+__device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, double2* __restrict__ dst, int L,
+                                              int Ns, const double2* __restrict__ tw, int nb, int tid,
+                                              int nth) {
+    const int nbf = L / R;
+    const int twmul = L / (Ns * R);
+    for (int t = tid; t < nb * nbf; t += nth) {
+        const int bt = t / nbf;
+        const int j = t - bt * nbf;
+        const double2* s = src + (size_t)bt * L;
+        double2* d = dst + (size_t)bt * L;
+        const int k = j % Ns;
+        double2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[j + r * nbf];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            double2 w = __ldg(&tw[r * k * twmul]);
+            if (SIGN > 0) w.y = -w.y;
+            v[r] = cmul(v[r], w);
+        }
+        if (R == 2) {
+            double2 a = v[0], b = v[1];
+            v[0] = cadd(a, b);
+            v[1] = csub(a, b);
+        } else if (R == 4) {
+            double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+            double2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+            // forward: -i*t3 ; backward: +i*t3
+            double2 rt = (SIGN < 0) ? make_double2(t3.y, -t3.x) : make_double2(-t3.y, t3.x);
+            v[0] = cadd(t0, t2);
+            v[2] = csub(t0, t2);
+            v[1] = cadd(t1, rt);
+            v[3] = csub(t1, rt);
+        } else if (R == 3) {
+            const double h3 = 0.86602540378443864676;  // sqrt(3)/2
+            double2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+            double2 m1 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
+            double2 m2 = (SIGN < 0) ? make_double2(h3 * t2.y, -h3 * t2.x) : make_double2(-h3 * t2.y, h3 * t2.x);
+            v[0] = cadd(v[0], t1);
+            v[1] = cadd(m1, m2);
+            v[2] = csub(m1, m2);
+        }
+        const int idx = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[idx + r * Ns] = v[r];
+    }
+}
+
+// Batched FFT of nb transforms stored contiguously in buf0 (each length pl.L);
+// buf1 is scratch of the same size.  Ends with __syncthreads(); returns the buffer
+// holding the result.
+template <int SIGN>
+__device__ static double2* fft_batched(double2* buf0, double2* buf1, const FftPlan& pl, int nb) {
+    double2* a = buf0;
+    double2* b = buf1;
+    int Ns = 1;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    __syncthreads();
+    for (int p = 0; p < pl.npass; ++p) {
+        const int R = pl.radix[p];
+        if (R == 4)
+            stockham_pass<SIGN, 4>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+        else if (R == 2)
+            stockham_pass<SIGN, 2>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+        else
+            stockham_pass<SIGN, 3>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+        __syncthreads();
+        double2* t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// Load the even extension of coefficients a_0..a_K (complex) into z (length 2K):
+// z_j = a_j (j <= K), z_{2K-j} = a_j.  The FFT of z then gives
+// Z_n = 2 sum''_{j=0..K} a_j cos(pi n j/K),  n = 0..K (the DCT-I core).
+__device__ __forceinline__ void even_extend_store(double2* z, int K, int j, double2 aj) {
+    z[j] = aj;
+    if (j > 0 && j < K) z[2 * K - j] = aj;
+}
+
+// Chebyshev derivative in x of plain coefficients c[0..n-1] -> d[0..n-1]
+// (d[n-1] = 0):  d_j = (2/c_j) sum_{k>j, k+j odd} k c_k  (c_0 = 2, c_j = 1),
+// evaluated as a suffix scan over each index parity.  ``tmp`` is scratch of n
+// entries.  Must be called by the whole CTA.
+__device__ __noinline__ static void cheb_derivative_scan(const double2* c, double2* d, double2* tmp, int n, double scale) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    // d_j (before the j=0 halving) = sum_{i>=0} 2(j+1+2i) c_{j+1+2i}: suffix sum with stride 2
+    for (int j = tid; j < n; j += nth) {
+        int k = j + 1;
+        d[j] = (k < n) ? cscale(c[k], 2.0 * k) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    double2* src = d;
+    double2* dst = tmp;
+    for (int off = 2; off < n; off *= 2) {
+        for (int j = tid; j < n; j += nth) {
+            double2 v = src[j];
+            if (j + off < n) v = cadd(v, src[j + off]);
+            dst[j] = v;
+        }
+        __syncthreads();
+        double2* t = src;
+        src = dst;
+        dst = t;
+    }
+    for (int j = tid; j < n; j += nth) {
+        double f = (j == 0) ? 0.5 * scale : scale;
+        d[j] = cscale(src[j], f);  // src may alias d: each j touched by one thread
+    }
+    __syncthreads();
+}
+
+}  // namespace pz

@@ -1,0 +1,56 @@
+// Host-side construction of the radial operators of the Chebyshev-integration
+// formulation and of the factored tau systems (Sections 3.2 and Appendix A of
+// Gastine, pizza, GJI 2019).  Pure C++; no CUDA.
+#pragma once
+#include <complex>
+#include <vector>
+
+namespace pz {
+
+using cplx = std::complex<double>;
+
+struct Geom {
+    double eta, s_o, s_i, a, b;   // s = a x + b, a = d/2 with d = s_o - s_i = 1
+};
+Geom make_geom(double eta);
+
+// Conduction-profile coefficient alpha/ln(eta) (Section 2, below Eq. temp).
+double tc_coefficient(double eta);
+
+// Operator ids of pizza_host_operator.
+enum OpId { OP_A0 = 0, OP_A2, OP_B0, OP_B2, OP_B4, OP_C, OP_D, OP_F0, OP_F2, OP_EZ, OP_G, OP_COUNT };
+
+// Number of integrations q of an operator and its half bandwidth h.
+int op_q(int id);
+int op_h(int id);
+
+// Dense n_c x n_c matrix (row-major) acting on the paper's f_hat coefficients of
+// an n_r-point grid; rows below q are zero.
+std::vector<double> build_operator(int id, int n_r, int n_c, const Geom& g);
+
+// Band storage of an operator: band[k*(2h+1) + (n-k+h)] for |n-k| <= h.
+std::vector<double> to_band(const std::vector<double>& dense, int n_c, int h);
+
+// Tau rows acting on f_hat (Eqs. bcs_coll_dirichlet, bcs_coll_neumann,
+// bc_d3psi_coll), in the order used by the systems:
+//  streamfunction: f(s_o), f(s_i), f'''(s_o), f'(s_i);  Dirichlet: f(s_o), f(s_i).
+std::vector<double> tau_rows_psi(int n_r, int n_c);
+std::vector<double> tau_rows_dir(int n_r, int n_c);
+
+// Factored bordered system (Appendix A) for p border rows and a banded block
+// D of half bandwidth kl = ku = h, factored by LU without pivoting:
+//   L[i*h + t] = L(i+1+t, i),  U[i*h + t] = U(i, i+1+t),  invd[i] = 1/U(i,i),
+//   Y = D^{-1} C stored [i*p + c],  Sinv = (A - B Y)^{-1} stored [r*p + c].
+template <class T>
+struct Bordered {
+    int n = 0, p = 0, h = 0;
+    std::vector<T> L, U, invd, Y, Sinv;
+};
+
+// Assemble and factor the tau system  [tau rows; Mass - gdt*Lin]  for one m.
+// mass_band / lin_band: band storage with half bandwidth h (complex).
+template <class T>
+bool factor_bordered(const std::vector<T>& mass_lin_band, int n_c, int h,
+                     const std::vector<double>& tau, int p, Bordered<T>& out);
+
+}  // namespace pz

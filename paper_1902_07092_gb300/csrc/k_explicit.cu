@@ -1,0 +1,405 @@
+// Explicit stage of one IMEX step (Sections 2, 3 and 3.2 of Gastine, pizza,
+// GJI 2019): spectral -> radial grid per azimuthal mode m, grid products per
+// radius, radial grid -> integrated right-hand sides per m.
+//
+// Layouts (double2 = complex):
+//   state   Psi_hat, theta_hat  [M][nc]  (paper f_hat convention, Eq. cheb)
+//   G1      [n_r][4][M]  radial-grid Fourier coefficients of
+//           v = dPsi/dphi, u_phi, omega, theta            (radius-major)
+//   G2      [n_r][4][M]  Fourier coefficients of the products
+//           v*omega, u_phi*omega, v*theta, u_phi*theta     (radius-major)
+//   e       [M][nc] integrated explicit right-hand sides
+// The change from mode-major to radius-major order (the paper's MPI transpose)
+// is folded into the stores of spec_to_grid and the loads of grid_to_spec.
+#include "device_common.cuh"
+
+namespace pz {
+
+namespace {
+
+constexpr int NTHREADS_R = 256;  // radial kernels
+constexpr int MAXPER = 12;       // azimuthal points per thread held in registers
+
+__device__ __forceinline__ int g_index(int k, int f, int m, int M) { return (k * 4 + f) * M + m; }
+
+// number of radial transforms batched together in shared memory
+__host__ __device__ inline int radial_batch(int L) { return L <= 1024 ? 2 : 1; }
+
+// ---------------------------------------------------------------------------
+// K1: per m, Chebyshev coefficients -> values on the Gauss-Lobatto grid.
+//   v = i m Psi,  u_phi = -h^2 Psi' + 3 s Psi,
+//   omega = -[h^2 Psi'' + (h^2/s - 5 s) Psi' - (6 + m^2 h^2/s^2) Psi]   (m >= 1)
+//   m = 0:  v = 0, u_phi = u_bar, omega = u_bar' + u_bar/s
+// (Section 3.2: u_s = (h^2/s) dPsi/dphi, u_phi = u_bar - h^2 dPsi/ds + 3 s Psi,
+//  omega = (1/s) d(s u_bar)/ds - L_I Psi.)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSet y, double2* __restrict__ G1) {
+    extern __shared__ double2 sm[];
+    const int m = blockIdx.x;
+    const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
+    const int NB = radial_batch(L);
+    double2* bufA = sm;
+    double2* bufB = bufA + NB * L;
+    double2* cc0 = bufB + NB * L;  // Psi (or u_bar) plain coefficients, length N
+    double2* cc1 = cc0 + N;        // first derivative
+    double2* cc2 = cc1 + N;        // second derivative
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const double C = P.cnorm;
+
+    for (int n = tid; n < N; n += nth) {
+        double2 a = make_double2(0.0, 0.0);
+        if (n < nc) {
+            const double w = (n == 0) ? 0.5 * C : C;
+            if (m > 0)
+                a = cscale(y.psi[(size_t)m * nc + n], w);
+            else
+                a = make_double2(y.u[n] * w, 0.0);
+        }
+        cc0[n] = a;
+    }
+    __syncthreads();
+    cheb_derivative_scan(cc0, cc1, bufA, N, P.inv_a);
+    if (m > 0) cheb_derivative_scan(cc1, cc2, bufA, N, P.inv_a);
+
+    // field list: 0 Psi, 1 Psi', 2 Psi'', 3 theta, 4 packed u_bar + i u_bar'
+    int fields[4];
+    int nf;
+    if (m > 0) {
+        fields[0] = 0; fields[1] = 1; fields[2] = 2; fields[3] = 3; nf = 4;
+    } else {
+        fields[0] = 4; fields[1] = 3; nf = 2;
+    }
+    const double dm = (double)m;
+    for (int f0 = 0; f0 < nf; f0 += NB) {
+        const int nb = min(NB, nf - f0);
+        for (int b = 0; b < nb; ++b) {
+            const int fid = fields[f0 + b];
+            double2* z = bufA + b * L;
+            for (int j = tid; j <= K; j += nth) {
+                double2 v;
+                if (fid == 0) v = cc0[j];
+                else if (fid == 1) v = cc1[j];
+                else if (fid == 2) v = cc2[j];
+                else if (fid == 3)
+                    v = (j < nc) ? cscale(y.th[(size_t)m * nc + j], (j == 0) ? 0.5 * C : C) : make_double2(0.0, 0.0);
+                else v = make_double2(cc0[j].x, cc1[j].x);
+                if (j == 0 || j == K) v = cscale(v, 2.0);
+                even_extend_store(z, K, j, v);
+            }
+        }
+        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        for (int b = 0; b < nb; ++b) {
+            const int fid = fields[f0 + b];
+            const double2* Z = R + b * L;
+            for (int k = tid; k < N; k += nth) {
+                const double2 g = cscale(Z[k], 0.5);  // value of the series at x_k
+                const double s = P.s[k], h2 = P.h2[k], is = P.inv_s[k];
+                double2* out = G1 + g_index(k, 0, m, M);
+                // out[0] = v, out[M] = u_phi, out[2M] = omega, out[3M] = theta
+                if (fid == 0) {
+                    out[0] = cmul_i(g, dm);
+                    out[M] = cscale(g, 3.0 * s);
+                    out[2 * M] = cscale(g, 6.0 + dm * dm * h2 * is * is);
+                } else if (fid == 1) {
+                    out[M] = csub(out[M], cscale(g, h2));
+                    out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - 5.0 * s));
+                } else if (fid == 2) {
+                    out[2 * M] = csub(out[2 * M], cscale(g, h2));
+                } else if (fid == 3) {
+                    out[3 * M] = g;
+                } else {
+                    out[0] = make_double2(0.0, 0.0);
+                    out[M] = make_double2(g.x, 0.0);
+                    out[2 * M] = make_double2(g.y + g.x * is, 0.0);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2: per radius, Eq. fft to the N_phi-point azimuthal grid, the four products,
+// Eq. ifft back (modes m <= N_m kept).  Two real fields travel in one complex
+// transform: g1 = v + i u_phi, g2 = omega + i theta; then
+//   g1 * Re(g2) = v omega + i u_phi omega,  g1 * Im(g2) = v theta + i u_phi theta.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_packed_spectrum(double2* Z, const double2* __restrict__ src, int M, int Pn,
+                                                     int n_m) {
+    // src points at G1/G2 row (k, f): field a = src[0..M), field b = src[M..2M)
+    for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
+        double2 z = make_double2(0.0, 0.0);
+        if (j == 0) {
+            z = make_double2(src[0].x, src[M].x);
+        } else if (j <= n_m) {
+            const double2 a = src[j], b = src[M + j];
+            z = make_double2(a.x - b.y, a.y + b.x);  // a + i b
+        } else if (j >= Pn - n_m) {
+            const int mm = Pn - j;
+            const double2 a = src[mm], b = src[M + mm];
+            z = make_double2(a.x + b.y, -a.y + b.x);  // conj(a) + i conj(b)
+        }
+        Z[j] = z;
+    }
+}
+
+__device__ __forceinline__ void store_split_spectrum(const double2* Y, double2* __restrict__ dst, int M, int Pn,
+                                                     int n_m) {
+    const double inv = 1.0 / (double)Pn;
+    for (int m = threadIdx.x; m <= n_m; m += blockDim.x) {
+        double2 a, b;
+        if (m == 0) {
+            a = make_double2(Y[0].x * inv, 0.0);
+            b = make_double2(Y[0].y * inv, 0.0);
+        } else {
+            const double2 y1 = Y[m], y2 = Y[Pn - m];
+            // a = (y1 + conj(y2))/2,  b = (y1 - conj(y2))/(2i)
+            a = make_double2(0.5 * (y1.x + y2.x) * inv, 0.5 * (y1.y - y2.y) * inv);
+            b = make_double2(0.5 * (y1.y + y2.y) * inv, -0.5 * (y1.x - y2.x) * inv);
+        }
+        dst[m] = a;
+        dst[M + m] = b;
+    }
+}
+
+__global__ void __launch_bounds__(512) k_phi_products(StepParams P, const double2* __restrict__ G1,
+                                                      double2* __restrict__ G2) {
+    extern __shared__ double2 sm[];
+    const int k = blockIdx.x;
+    const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
+    double2* X = sm;
+    double2* Y = sm + Pn;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    double2 reg[MAXPER];
+
+    load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m);
+    double2* R = fft_batched<+1>(X, Y, P.plan_p, 1);
+#pragma unroll
+    for (int i = 0; i < MAXPER; ++i) {
+        const int j = tid + i * nth;
+        if (j < Pn) reg[i] = R[j];
+    }
+    __syncthreads();
+    load_packed_spectrum(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m);
+    R = fft_batched<+1>(X, Y, P.plan_p, 1);
+#pragma unroll
+    for (int i = 0; i < MAXPER; ++i) {
+        const int j = tid + i * nth;
+        if (j < Pn) {
+            const double2 g2 = R[j], g1 = reg[i];
+            R[j] = cscale(g1, g2.x);
+            reg[i] = cscale(g1, g2.y);
+        }
+    }
+    double2* other = (R == X) ? Y : X;
+    double2* S = fft_batched<-1>(R, other, P.plan_p, 1);
+    store_split_spectrum(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < MAXPER; ++i) {
+        const int j = tid + i * nth;
+        if (j < Pn) X[j] = reg[i];
+    }
+    S = fft_batched<-1>(X, Y, P.plan_p, 1);
+    store_split_spectrum(S, G2 + g_index(k, 2, 0, M), M, Pn, n_m);
+}
+
+// ---------------------------------------------------------------------------
+// K3: per m, radial divergences of the fluxes, Eq. icheb, truncation to n < N_c
+// (dealiasing), and the integrated right-hand sides
+//   N_omega = (1/s) d/ds(h^2 [v omega]_m) + (i m/s) [u_phi omega]_m
+//   N_theta = (1/s) d/ds(h^2 [v theta]_m) + (i m/s) [u_phi theta]_m - [v theta]_m
+//   N_u     = (h^2/s) [v omega]_0
+//   e_psi   = C^I [ (Ra/Pr)(i m/s_o) theta_hat_m + N_omega_hat ]        (m >= 1)
+//   e_theta = -D^I N_theta_hat - (alpha/ln eta) i m G^I Psi_hat_m
+//   e_u     = -D^I N_u_hat
+// (Eqs. vort, temp, uphi; psi_int, temp_int, uphi_int; u_s = (h^2/s) v and
+//  beta u_s = -v.)  The radial derivative is that of the n_r-point interpolant.
+// ---------------------------------------------------------------------------
+template <int H>
+__device__ __forceinline__ double2 band_row(const double* __restrict__ band, const double2* x, int k, int nc) {
+    const double* row = band + (size_t)k * (2 * H + 1);
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int d = 0; d <= 2 * H; ++d) {
+        const int n = k - H + d;
+        if (n >= 0 && n < nc) {
+            const double c = __ldg(&row[d]);
+            acc.x = fma(c, x[n].x, acc.x);
+            acc.y = fma(c, x[n].y, acc.y);
+        }
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const double2* __restrict__ G2, VecSet y,
+                                                             VecSet e) {
+    extern __shared__ double2 sm[];
+    const int m = blockIdx.x;
+    const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
+    const int NB = radial_batch(L);
+    double2* bufA = sm;
+    double2* bufB = bufA + NB * L;
+    double2* cc0 = bufB + NB * L;
+    double2* cc1 = cc0 + N;
+    double2* cc2 = cc1 + N;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const double dm = (double)m;
+
+    // pass A: plain Chebyshev coefficients of F1 = h^2 [v omega]_m, F2 = h^2 [v theta]_m
+    for (int b0 = 0; b0 < 2; b0 += NB) {
+        const int nb = min(NB, 2 - b0);
+        for (int b = 0; b < nb; ++b) {
+            const int f = (b0 + b == 0) ? 0 : 2;
+            double2* z = bufA + b * L;
+            for (int j = tid; j <= K; j += nth)
+                even_extend_store(z, K, j, cscale(G2[g_index(j, f, m, M)], P.h2[j]));
+        }
+        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        for (int b = 0; b < nb; ++b) {
+            double2* dst = (b0 + b == 0) ? cc0 : cc1;
+            const double2* Z = R + b * L;
+            for (int n = tid; n <= K; n += nth) {
+                const double w = (n == 0 || n == K) ? 0.5 : 1.0;
+                dst[n] = cscale(Z[n], w / (double)K);
+            }
+        }
+        __syncthreads();
+    }
+    // d/ds of both (in place through cc2 as output, then copy back)
+    cheb_derivative_scan(cc0, cc2, bufA, N, P.inv_a);
+    for (int n = tid; n < N; n += nth) cc0[n] = cc2[n];
+    __syncthreads();
+    cheb_derivative_scan(cc1, cc2, bufA, N, P.inv_a);
+    for (int n = tid; n < N; n += nth) cc1[n] = cc2[n];
+    __syncthreads();
+
+    // pass B: derivative values on the grid, then N_omega (or N_u) and N_theta
+    double2* Nbuf = nullptr;
+    for (int b0 = 0; b0 < 2; b0 += NB) {
+        const int nb = min(NB, 2 - b0);
+        for (int b = 0; b < nb; ++b) {
+            const double2* c = (b0 + b == 0) ? cc0 : cc1;
+            double2* z = bufA + b * L;
+            for (int j = tid; j <= K; j += nth) {
+                double2 v = c[j];
+                if (j == 0 || j == K) v = cscale(v, 2.0);
+                even_extend_store(z, K, j, v);
+            }
+        }
+        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        // nonlinear terms into the even-extension input of pass C, held in the
+        // buffer not holding R (pass C input area must survive: for NB == 1 the two
+        // fields are processed one after the other through cc2 / cc0 staging)
+        for (int b = 0; b < nb; ++b) {
+            const int fld = b0 + b;  // 0: omega, 1: theta
+            const double2* Z = R + b * L;
+            double2* dst = (fld == 0) ? cc2 : cc0;  // grid values of N (length N)
+            for (int k = tid; k <= K; k += nth) {
+                const double2 dF = cscale(Z[k], 0.5);
+                const double is = P.inv_s[k];
+                double2 val;
+                if (fld == 0) {
+                    if (m > 0) {
+                        const double2 uw = G2[g_index(k, 1, m, M)];
+                        val = cscale(cadd(dF, cmul_i(uw, dm)), is);
+                    } else {
+                        const double2 vw = G2[g_index(k, 0, m, M)];
+                        val = cscale(vw, P.h2[k] * is);
+                    }
+                } else {
+                    const double2 ut = G2[g_index(k, 3, m, M)];
+                    const double2 vt = G2[g_index(k, 2, m, M)];
+                    val = csub(cscale(cadd(dF, cmul_i(ut, dm)), is), vt);
+                }
+                dst[k] = val;
+            }
+        }
+        __syncthreads();
+    }
+    (void)Nbuf;
+    // pass C: Eq. icheb of N_omega (cc2) and N_theta (cc0), truncated to n < nc
+    for (int b0 = 0; b0 < 2; b0 += NB) {
+        const int nb = min(NB, 2 - b0);
+        for (int b = 0; b < nb; ++b) {
+            const double2* src = (b0 + b == 0) ? cc2 : cc0;
+            double2* z = bufA + b * L;
+            for (int j = tid; j <= K; j += nth) even_extend_store(z, K, j, src[j]);
+        }
+        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        for (int b = 0; b < nb; ++b) {
+            double2* dst = (b0 + b == 0) ? cc1 : cc2;  // N_omega_hat -> cc1, N_theta_hat -> cc2
+            const double2* Z = R + b * L;
+            // careful: for NB == 1 the theta pass reads cc0 and writes cc2, which
+            // already holds nothing needed any more (N_omega_hat went to cc1).
+            for (int n = tid; n < nc; n += nth) dst[n] = cscale(Z[n], 0.5 * P.cnorm);
+        }
+        __syncthreads();
+    }
+    // integrated right-hand sides
+    // psi: x = (Ra/Pr)(i m/s_o) theta_hat + N_omega_hat  (into cc0), then C^I
+    const double bfac = P.Ra / P.Pr * dm / P.s_o;
+    for (int n = tid; n < nc; n += nth) {
+        const double2 th = y.th[(size_t)m * nc + n];
+        cc0[n] = cadd(cc1[n], cmul_i(th, bfac));
+        // Psi_hat_m for the conduction term, into bufA
+        bufA[n] = (m > 0) ? y.psi[(size_t)m * nc + n] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int k = tid; k < nc; k += nth) {
+        double2 ep = make_double2(0.0, 0.0), et = make_double2(0.0, 0.0);
+        if (k >= 4 && m > 0) ep = band_row<8>(P.ops.band[OP_C], cc0, k, nc);
+        if (k >= 2) {
+            const double2 dn = band_row<4>(P.ops.band[OP_D], cc2, k, nc);
+            const double2 gp = band_row<4>(P.ops.band[OP_G], bufA, k, nc);
+            et = csub(cmul_i(gp, -P.tc * dm), dn);
+        }
+        e.psi[(size_t)m * nc + k] = ep;
+        e.th[(size_t)m * nc + k] = et;
+        if (m == 0) {
+            double eu = 0.0;
+            if (k >= 2) eu = -band_row<4>(P.ops.band[OP_D], cc1, k, nc).x;
+            e.u[k] = eu;
+        }
+    }
+}
+
+}  // namespace
+
+size_t smem_spec_to_grid(const StepParams& P) {
+    const int L = 2 * P.K;
+    return sizeof(double2) * (2 * radial_batch(L) * L + 3 * P.n_r);
+}
+size_t smem_phi_products(const StepParams& P) { return sizeof(double2) * 2 * P.n_phi; }
+size_t smem_grid_to_spec(const StepParams& P) {
+    const int L = 2 * P.K;
+    return sizeof(double2) * (2 * radial_batch(L) * L + 3 * P.n_r);
+}
+
+cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st) {
+    const size_t sm = smem_spec_to_grid(P);
+    cudaError_t err = cudaFuncSetAttribute(k_spec_to_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    k_spec_to_grid<<<P.M, NTHREADS_R, sm, st>>>(P, y, G1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2* G2, cudaStream_t st) {
+    const size_t sm = smem_phi_products(P);
+    const int nth = P.n_phi > 256 * MAXPER ? 512 : 256;
+    if (P.n_phi > nth * MAXPER) return cudaErrorInvalidValue;
+    cudaError_t err = cudaFuncSetAttribute(k_phi_products, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    k_phi_products<<<P.n_r, nth, sm, st>>>(P, G1, G2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_to_spec(const StepParams& P, const double2* G2, VecSet y, VecSet e, cudaStream_t st) {
+    const size_t sm = smem_grid_to_spec(P);
+    cudaError_t err = cudaFuncSetAttribute(k_grid_to_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    k_grid_to_spec<<<P.M, NTHREADS_R, sm, st>>>(P, G2, y, e);
+    return cudaGetLastError();
+}
+
+}  // namespace pz

@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of libpizza.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "host_ops.h"
+
+namespace pz {
+
+constexpr int MAX_PASSES = 16;
+constexpr int MAX_RHS_TERMS = 10;
+
+// Mixed-radix (3 * 2^j) Stockham plan for one transform length.
+struct FftPlan {
+    int L;
+    int npass;
+    int radix[MAX_PASSES];
+    const double2* tw;  // tw[j] = exp(-2 pi i j / L), j < L
+};
+
+// One set of per-field vectors: Psi and theta complex [M][nc], u real [nc].
+struct VecSet {
+    double2* psi;
+    double2* th;
+    double* u;
+};
+
+// Banded m-independent operators (band storage, half width h, row-major [nc][2h+1]).
+struct DevOps {
+    const double* band[OP_COUNT];
+    const double* tau_psi_B;  // 4 x (nc-4): tau rows restricted to columns 4..
+    const double* tau_dir_B;  // 2 x (nc-2)
+};
+
+// Factored bordered systems (Appendix A) for one implicit weight gamma*dt.
+struct DevFactors {
+    double gdt;
+    // streamfunction, complex, per m: L,U [M][n_p][8], invd [M][n_p], Y [M][n_p][4], Sinv [M][16]
+    double2 *pL, *pU, *pInvd, *pY, *pSinv;
+    // temperature, real, per m: L,U [M][n_t][4], invd [M][n_t], Y [M][n_t][2], Sinv [M][4]
+    double *tL, *tU, *tInvd, *tY, *tSinv;
+    // zonal flow, real: L,U [n_t][4], invd [n_t], Y [n_t][2], Sinv [4]
+    double *uL, *uU, *uInvd, *uY, *uSinv;
+};
+
+// Scalar parameters passed by value to every kernel.
+struct StepParams {
+    int n_r, n_phi, n_m, M, nc, K;   // K = n_r - 1
+    double E, Ra, Pr, s_o, inv_a, tc, cnorm;
+    const double* s;      // [n_r] radial grid
+    const double* h2;     // [n_r]
+    const double* inv_s;  // [n_r]
+    FftPlan plan_r;       // length 2K (radial DCT-I)
+    FftPlan plan_p;       // length n_phi (azimuthal)
+    DevOps ops;
+};
+
+struct RhsTerm {
+    VecSet v;
+    double c;
+};
+
+struct RhsSpec {
+    int nterms;
+    RhsTerm t[MAX_RHS_TERMS];
+};
+
+// kernel launchers (k_explicit.cu, k_implicit.cu)
+cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st);
+cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2* G2, cudaStream_t st);
+cudaError_t launch_grid_to_spec(const StepParams& P, const double2* G2, VecSet y, VecSet e, cudaStream_t st);
+cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFactors& F, VecSet y_out,
+                         VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st);
+cudaError_t launch_apply(const StepParams& P, VecSet y, VecSet mass_out, VecSet imp_out, bool want_mass,
+                         bool want_imp, cudaStream_t st);
+
+size_t smem_spec_to_grid(const StepParams& P);
+size_t smem_phi_products(const StepParams& P);
+size_t smem_grid_to_spec(const StepParams& P);
+size_t smem_solve(const StepParams& P);
+
+}  // namespace pz

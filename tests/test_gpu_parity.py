@@ -1,0 +1,130 @@
+"""GPU parity: the CUDA path, called through the C interface, against the
+oracle on the same seeded inputs.
+
+Tolerances (relative L2, FP64): explicit right-hand sides max(1e-12, 4 n_r^2 eps)
+with eps = 2^-53 (the flux divergence differentiates the interpolant of rounded
+grid products; the derivative of T_n is bounded by n^2, so rounding errors of the
+two implementations are amplified by up to n_r^2); full time
+steps 1e-12 at n_r <= 65 and 2e-12 at n_r = 257, where the unpivoted banded
+solve and the oracle's dense LU each sit ~1e-12 from the exact solution of the
+tau system (measured against iteratively refined solutions: the streamfunction
+block has an effective condition number ~1e4)."""
+import numpy as np
+import pytest
+
+from oracle.explicit import explicit_terms
+from oracle.stepper import IntegrationStepper
+from paper_1902_07092_gb300 import inputs
+from tests.parity_util import assert_state_close, critical_rayleigh, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def make_pair(n_r, n_phi, E, ra_factor, scheme, dt, Pr=1.0, eta=0.35):
+    from paper_1902_07092_gb300.binding import Solver
+    Ra = ra_factor * critical_rayleigh(E)
+    gpu = Solver(n_r, n_phi, E, Ra, Pr, eta, scheme, dt)
+    ora = IntegrationStepper(n_r, n_phi, E, Ra, Pr, eta, scheme, dt)
+    return gpu, ora
+
+
+def random_state(n_r, n_phi, amp, seed, psi_amp=None, u_amp=None):
+    th = inputs.theta_init(n_r, n_phi, amp, seed, cfg=7, m_min=0)
+    psi = inputs.theta_init(n_r, n_phi, psi_amp if psi_amp is not None else amp * 1e-2, seed + 1, cfg=8)
+    psi[0] = 0.0
+    u = inputs.theta_init(n_r, n_phi, u_amp if u_amp is not None else amp, seed + 2, cfg=9, m_min=0)[0].real
+    return psi, th, u
+
+
+@pytest.mark.parametrize("n_r,n_phi", [(33, 96), (65, 192), (129, 384), (257, 768)])
+def test_explicit_terms_match_oracle(n_r, n_phi):
+    gpu, ora = make_pair(n_r, n_phi, 1e-3, 2.0, "CNAB2", 1e-4)
+    psi, th, u = random_state(n_r, n_phi, 1.0, 3, psi_amp=1.0, u_amp=1.0)
+    gpu.set_state(th, psi, u)
+    ep, et, eu = gpu.explicit_terms()
+    rp, rt, ru = explicit_terms(ora.g, psi, th, u)
+    tol = max(1e-12, 4 * n_r * n_r * 2.0 ** -53)
+    errs = (rel_l2(ep, rp), rel_l2(et, rt), rel_l2(eu, ru))
+    print("explicit terms n_r=%d: rel L2 psi %.2e theta %.2e u %.2e (tol %.1e)" % ((n_r,) + errs + (tol,)))
+    assert max(errs) <= tol
+    gpu.close()
+
+
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443"])
+@pytest.mark.parametrize("amp", [1e-4, 1.0])
+def test_steps_match_oracle_tiny(scheme, amp):
+    """configs: n_r = 33, n_phi = 96, E = 1e-3, Pr = 1, Ra = 2 Ra_c, dt = 1e-4;
+    amp = 1e-4 is the tiny workload, amp = 1 the strongly nonlinear case."""
+    n_r, n_phi = 33, 96
+    gpu, ora = make_pair(n_r, n_phi, 1e-3, 2.0, scheme, 1e-4)
+    th = inputs.theta_init(n_r, n_phi, amp, 1, cfg=1)
+    z, zu = inputs.zero_state(n_r, n_phi)
+    gpu.set_state(th, z, zu)
+    ora.set_state(z, th, zu)
+    for k in range(5):
+        gpu.step(1)
+        ora.step()
+        assert_state_close(gpu.get_state(), ora.y, 1e-12)
+    gpu.close()
+
+
+def test_steps_match_oracle_sparse_workload():
+    """n_r = 257, n_phi = 768, E = 1e-5, Pr = 1, Ra = 10 Ra_c, ARS443, dt = 1e-7,
+    seeded amplitude 1e-3; two steps."""
+    n_r, n_phi = 257, 768
+    gpu, ora = make_pair(n_r, n_phi, 1e-5, 10.0, "ARS443", 1e-7)
+    th = inputs.theta_init(n_r, n_phi, 1e-3, 2, cfg=2)
+    z, zu = inputs.zero_state(n_r, n_phi)
+    gpu.set_state(th, z, zu)
+    ora.set_state(z, th, zu)
+    for k in range(2):
+        gpu.step(1)
+        ora.step()
+        assert_state_close(gpu.get_state(), ora.y, 2e-12)
+    gpu.close()
+
+
+def test_multistep_history_across_calls():
+    """pizza_step(ctx, 3) equals three pizza_step(ctx, 1) calls (history kept)."""
+    n_r, n_phi = 33, 96
+    from paper_1902_07092_gb300.binding import Solver
+    Ra = 2.0 * critical_rayleigh(1e-3)
+    a = Solver(n_r, n_phi, 1e-3, Ra, 1.0, 0.35, "SBDF3", 1e-4)
+    b = Solver(n_r, n_phi, 1e-3, Ra, 1.0, 0.35, "SBDF3", 1e-4)
+    th = inputs.theta_init(n_r, n_phi, 1e-2, 5, cfg=1)
+    z, zu = inputs.zero_state(n_r, n_phi)
+    a.set_state(th, z, zu)
+    b.set_state(th, z, zu)
+    a.step(3)
+    for _ in range(3):
+        b.step(1)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+
+
+def test_edge_cases():
+    n_r, n_phi = 33, 96
+    gpu, ora = make_pair(n_r, n_phi, 1e-3, 2.0, "CNAB2", 1e-4)
+    # zero state stays exactly zero
+    z, zu = inputs.zero_state(n_r, n_phi)
+    gpu.set_state(z, z, zu)
+    gpu.step(3)
+    for x in gpu.get_state():
+        assert not np.any(x)
+    # zonal-only state (m = 0 flow and temperature): matches the oracle
+    th = inputs.theta_init(n_r, n_phi, 1e-2, 4, cfg=1, m_min=0)
+    th[1:] = 0.0
+    u = inputs.theta_init(n_r, n_phi, 1e-2, 6, cfg=3, m_min=0)[0].real
+    gpu.set_state(th, z, u)
+    ora.set_state(z, th, u)
+    for _ in range(3):
+        gpu.step(1)
+        ora.step()
+    assert_state_close(gpu.get_state(), ora.y, 1e-12)
+    # ragged input: fewer coefficients than N_c are zero-padded
+    th = inputs.theta_init(n_r, n_phi, 1e-3, 8, cfg=1)
+    thr = np.ascontiguousarray(th[:, :7])
+    gpu.set_state(thr)
+    ps, tt, uu = gpu.get_state()
+    assert np.array_equal(tt[:, :7], thr) and not np.any(tt[:, 7:]) and not np.any(ps) and not np.any(uu)
+    gpu.close()
