@@ -210,3 +210,25 @@ def test_flux_divergences_match_analytic_evaluation():
         assert np.allclose(got, spec, rtol=0, atol=1e-10 * np.abs(spec).max()), key
     vals = np.asarray(fu(S, PH), dtype=complex).real.mean(axis=1)
     assert np.allclose(parts["Nu_grid"][1:], vals, rtol=0, atol=1e-10 * np.abs(vals).max())
+
+
+def test_tau_solve_is_accurate_against_extended_precision_refinement():
+    """The oracle's solve of the streamfunction tau system (n_r = 257, E = 1e-5,
+    dt = 1e-7) agrees with a solution iteratively refined with residuals in
+    extended precision."""
+    st = IntegrationStepper(257, 12, 1e-5, 1e8, 1.0, 0.35, "CNAB2", 1e-7)
+    rng = np.random.default_rng(12)
+    nc = st.n_c
+    for m in (1, 3):
+        L = st.ops.lhs_psi(m, 0.5e-7)
+        c = np.zeros(nc, complex)
+        c[:30] = (rng.standard_normal(30) + 1j * rng.standard_normal(30)) / (1 + np.arange(30)) ** 3
+        f = st.ops.A(m) @ c
+        f[:4] = 0
+        x = st._solve(st._factor(L), f)
+        xr = x.copy()
+        Ll = L.astype(np.clongdouble)
+        for _ in range(4):
+            r = (f.astype(np.clongdouble) - Ll @ xr.astype(np.clongdouble)).astype(complex)
+            xr = xr + st._solve(st._factor(L), r)
+        assert np.linalg.norm(x - xr) <= 1e-13 * np.linalg.norm(xr)
