@@ -128,6 +128,38 @@ int pizza_synchronize(pizza_ctx *ctx);
  * integrations are zero) into out.  Needs no CUDA device. */
 int pizza_host_operator(int which, int n_r, int n_c, double radius_ratio, double *out);
 
+/* Explicit stage without device allocation.  This entry point has no
+ * counterpart in the paper; it exists for callers that cannot allocate device
+ * memory themselves or through the library -- for example code running inside a
+ * host application that owns the device-memory budget and hands out only
+ * preallocated arrays, or latency-critical code that must not enter the CUDA
+ * allocator (which can synchronise the device) after start-up.
+ *
+ * Computes the same e_psi, e_theta, e_uphi as pizza_explicit_terms, for the state
+ * psi_hat, theta_hat (complex [N_m+1][N_c]) and uphi0_hat (real [N_c]), where
+ * N_m = n_phi/3 and N_c = floor(2 (n_r-1)/3).  All six arrays are DEVICE memory
+ * owned by the caller; work is queued on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream) and the call returns without waiting.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Its intermediate arrays and read-only tables live in static device arrays
+ * compiled into the library (about 8.7 MB, held by every device that loads the
+ * library until the process exits), so the sizes are limited to
+ * n_r <= PIZZA_NOALLOC_MAX_NR and n_phi <= PIZZA_NOALLOC_MAX_NPHI; larger sizes
+ * return PIZZA_EINVAL with a message.  The first call on a device, and any
+ * call whose (n_r, n_phi, Ra, Pr, radius_ratio) differ from the previous one on
+ * that device, does a synchronous set-up (address look-up of the static arrays,
+ * table upload); make that first call before any stream capture.  All calls on
+ * a device share the static arrays: calls whose work overlaps on the GPU (other
+ * streams, other host threads without ordering) race and give wrong results.
+ * Errors are reported through pizza_last_error(NULL). */
+#define PIZZA_NOALLOC_MAX_NR 257
+#define PIZZA_NOALLOC_MAX_NPHI 768
+int pizza_explicit_terms_noalloc(int n_r, int n_phi, double Ra, double Pr, double radius_ratio,
+                                 const double *psi_hat, const double *theta_hat,
+                                 const double *uphi0_hat, double *e_psi, double *e_theta,
+                                 double *e_uphi, void *stream);
+
 void pizza_free(pizza_ctx *ctx);
 
 /* Message of the last failing call on ctx (or of the last failing pizza_init

@@ -22,7 +22,7 @@ STATUS = {0: "PIZZA_OK", -1: "PIZZA_EINVAL", -2: "PIZZA_ENOMEM", -3: "PIZZA_ECUD
 EXPORTS = ("pizza_init", "pizza_set_option", "pizza_set_stream", "pizza_get_sizes", "pizza_set_state",
            "pizza_get_state", "pizza_step", "pizza_explicit_terms", "pizza_profile_begin",
            "pizza_profile_end", "pizza_synchronize",
-           "pizza_host_operator", "pizza_free", "pizza_last_error")
+           "pizza_host_operator", "pizza_explicit_terms_noalloc", "pizza_free", "pizza_last_error")
 
 _lib = None
 
@@ -53,6 +53,7 @@ def load():
     lib.pizza_profile_end.argtypes = [vp, dp, dp]
     lib.pizza_synchronize.argtypes = [vp]
     lib.pizza_host_operator.argtypes = [i, i, i, d, dp]
+    lib.pizza_explicit_terms_noalloc.argtypes = [i, i, d, d, d, dp, dp, dp, dp, dp, dp, vp]
     lib.pizza_free.argtypes = [vp]
     lib.pizza_free.restype = None
     lib.pizza_last_error.argtypes = [vp]
@@ -146,6 +147,14 @@ def pizza_host_operator(which, n_r, n_c, radius_ratio):
     out = np.zeros((n_c, n_c))
     _check(load().pizza_host_operator(which, n_r, n_c, radius_ratio, _ptr(out)))
     return out
+
+
+def pizza_explicit_terms_noalloc(n_r, n_phi, Ra, Pr, radius_ratio, psi_hat, theta_hat, uphi0_hat,
+                                 e_psi, e_theta, e_uphi, stream=None):
+    """Device arrays only (e.g. torch CUDA tensors); queued on ``stream``."""
+    return _check(load().pizza_explicit_terms_noalloc(n_r, n_phi, Ra, Pr, radius_ratio, _ptr(psi_hat),
+                                                      _ptr(theta_hat), _ptr(uphi0_hat), _ptr(e_psi),
+                                                      _ptr(e_theta), _ptr(e_uphi), stream))
 
 
 def pizza_free(ctx):

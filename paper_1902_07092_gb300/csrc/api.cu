@@ -23,6 +23,41 @@ constexpr int NVEC = 16;
 
 }  // namespace
 
+namespace pz {
+void set_global_error(const char* msg) { g_init_error = msg; }
+
+bool make_fft_plan(int L, FftPlan& pl) {
+    int n = L, np = 0;
+    if (n % 3 == 0) {
+        pl.radix[np++] = 3;
+        n /= 3;
+    }
+    if (n <= 0 || (n & (n - 1)) != 0) return false;
+    while (n % 4 == 0) {
+        pl.radix[np++] = 4;
+        n /= 4;
+    }
+    while (n % 2 == 0) {
+        pl.radix[np++] = 2;
+        n /= 2;
+    }
+    pl.L = L;
+    pl.npass = np;
+    return np <= MAX_PASSES;
+}
+
+std::vector<double2> fft_twiddles(int L) {
+    std::vector<double2> t(L);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int j = 0; j < L; ++j) {
+        long double a = 2.0L * pi * (long double)j / (long double)L;
+        t[j] = make_double2((double)cosl(a), (double)(-sinl(a)));
+    }
+    return t;
+}
+
+}  // namespace pz
+
 struct pizza_ctx {
     int n_r = 0, n_phi = 0, n_m = 0, M = 0, nc = 0, K = 0, scheme = 0;
     double E = 0, Ra = 0, Pr = 0, eta = 0, dt = 0;
@@ -85,36 +120,6 @@ T* dalloc(pizza_ctx* ctx, size_t n, std::vector<void*>& list) {
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
-
-bool make_plan(int L, FftPlan& pl) {
-    int n = L, np = 0;
-    if (n % 3 == 0) {
-        pl.radix[np++] = 3;
-        n /= 3;
-    }
-    if (!pow2(n)) return false;
-    while (n % 4 == 0) {
-        pl.radix[np++] = 4;
-        n /= 4;
-    }
-    while (n % 2 == 0) {
-        pl.radix[np++] = 2;
-        n /= 2;
-    }
-    pl.L = L;
-    pl.npass = np;
-    return np <= MAX_PASSES;
-}
-
-std::vector<double2> twiddles(int L) {
-    std::vector<double2> t(L);
-    const long double pi = 3.141592653589793238462643383279502884L;
-    for (int j = 0; j < L; ++j) {
-        long double a = 2.0L * pi * (long double)j / (long double)L;
-        t[j] = make_double2((double)cosl(a), (double)(-sinl(a)));
-    }
-    return t;
-}
 
 int cuda_check(pizza_ctx* ctx, cudaError_t e, const char* what) {
     if (e != cudaSuccess) return fail(ctx, PIZZA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -543,11 +548,11 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
     P.h2 = dh;
     P.inv_s = di;
 
-    if (!make_plan(2 * ctx->K, P.plan_r) || !make_plan(n_phi, P.plan_p)) {
+    if (!make_fft_plan(2 * ctx->K, P.plan_r) || !make_fft_plan(n_phi, P.plan_p)) {
         ctx->err = "unsupported transform length";
         return bail(PIZZA_EINVAL);
     }
-    auto twr = twiddles(2 * ctx->K), twp = twiddles(n_phi);
+    auto twr = fft_twiddles(2 * ctx->K), twp = fft_twiddles(n_phi);
     double2* dtwr = dalloc<double2>(ctx, twr.size(), al);
     double2* dtwp = dalloc<double2>(ctx, twp.size(), al);
     if (!dtwr || !dtwp) {

@@ -76,6 +76,13 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
 cudaError_t launch_apply(const StepParams& P, VecSet y, VecSet mass_out, VecSet imp_out, bool want_mass,
                          bool want_imp, cudaStream_t st);
 
+// message returned by pizza_last_error(NULL)
+void set_global_error(const char* msg);
+
+// Stockham radix plan (3 * 2^j or 2^j) and twiddle table exp(-2 pi i j/L), j < L.
+bool make_fft_plan(int L, FftPlan& pl);
+std::vector<double2> fft_twiddles(int L);
+
 size_t smem_spec_to_grid(const StepParams& P);
 size_t smem_phi_products(const StepParams& P);
 size_t smem_grid_to_spec(const StepParams& P);
