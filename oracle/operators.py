@@ -33,6 +33,7 @@ from math import comb
 
 import numpy as np
 import numpy.polynomial.polynomial as P
+import scipy.sparse as sp
 
 from . import chebyshev as ch
 from .geometry import Annulus, gauss_lobatto
@@ -114,11 +115,12 @@ def _poly_in_x(coeffs_s, ann):
 
 
 def _poly_matrix(coef_x, X):
-    """Q(X) for Q in the power basis (Horner)."""
+    """Q(X) for Q in the power basis (Horner); X sparse, result dense."""
     K = X.shape[0]
     R = np.zeros((K, K))
     for c in coef_x[::-1]:
-        R = X @ R + c * np.eye(K)
+        R = X @ R
+        R[np.diag_indices(K)] += c
     return R
 
 
@@ -138,11 +140,12 @@ def integrated_operator(op, q, ann, n_c, mu_power):
         return np.zeros((n_c, n_c))
     maxdeg = max(max(d) for d in by_p.values())
     Kp = n_c + 2 * (maxdeg + q) + 8
-    X = ch.xmul_matrix(Kp)
-    J = ch.int_matrix(Kp)
-    Jpow = [np.eye(Kp)]
+    # x-multiplication and integration are tri-/bidiagonal: stored sparse
+    X = sp.csr_matrix(ch.xmul_matrix(Kp))
+    J = sp.csr_matrix(ch.int_matrix(Kp))
+    Jpow = [sp.identity(Kp, format="csr")]
     for _ in range(q):
-        Jpow.append(J @ Jpow[-1])
+        Jpow.append((J @ Jpow[-1]).tocsr())
     M = np.zeros((Kp, Kp))
     for p, cs in by_p.items():
         if p > q:

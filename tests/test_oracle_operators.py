@@ -125,7 +125,7 @@ def test_integrated_operators_equal_exact_integrals(mu):
                     g = pint(g)
                 ref = np.array([float(v) for v in s_poly_to_plain_cheb(g, n_c)])
             got = mat[:, n]
-            scale = max(np.abs(ref[q:]).max(), np.abs(mat[q:]).max() * 1e-3)
+            scale = max(np.abs(ref[q:]).max(), np.abs(mat[q:]).max())  # operator magnitude
             assert np.allclose(got[q:], ref[q:], rtol=0, atol=1e-13 * scale), (name, n)
 
 
