@@ -155,10 +155,11 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
     const double gdt = gamma * ctx->dt;
     const auto tauP = tau_rows_psi(ctx->n_r, nc);
     const auto tauD = tau_rows_dir(ctx->n_r, nc);
-    std::vector<double2> hpL((size_t)M * np * 8), hpU((size_t)M * np * 8), hpD((size_t)M * np),
-        hpY((size_t)M * np * 4), hpS((size_t)M * 16);
-    std::vector<double> htL((size_t)M * nt * 4), htU((size_t)M * nt * 4), htD((size_t)M * nt),
-        htY((size_t)M * nt * 2), htS((size_t)M * 4);
+    const int nbp = (np + 7) / 8, nbt = (nt + 3) / 4;
+    std::vector<double2> hpK((size_t)M * nbp * 3 * 64), hpY((size_t)M * np * 4), hpS((size_t)M * 16),
+        hpB((size_t)M * np * 17);
+    std::vector<double> htK((size_t)M * nbt * 3 * 16), htY((size_t)M * nt * 2), htS((size_t)M * 4),
+        htB((size_t)M * nt * 9);
     std::vector<int> bad(M, 0);
     auto get = [&](int id, int k, int n) -> double {
         const int h = op_h(id);
@@ -185,16 +186,20 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
                         }
                         bp[(size_t)k * 17 + d] = v;
                     }
+                for (size_t i = 0; i < (size_t)np * 17; ++i)
+                    hpB[(size_t)m * np * 17 + i] = make_double2(bp[4 * 17 + i].real(), bp[4 * 17 + i].imag());
                 Bordered<cplx> f;
                 if (!factor_bordered(bp, nc, 8, tauP, 4, f)) {
                     bad[m] = 1;
                     continue;
                 }
-                for (size_t i = 0; i < (size_t)np * 8; ++i) {
-                    hpL[(size_t)m * np * 8 + i] = make_double2(f.L[i].real(), f.L[i].imag());
-                    hpU[(size_t)m * np * 8 + i] = make_double2(f.U[i].real(), f.U[i].imag());
+                std::vector<cplx> blk;
+                if (!block_lu(bp, nc, 8, 4, blk)) {
+                    bad[m] = 1;
+                    continue;
                 }
-                for (int i = 0; i < np; ++i) hpD[(size_t)m * np + i] = make_double2(f.invd[i].real(), f.invd[i].imag());
+                for (size_t i = 0; i < blk.size(); ++i)
+                    hpK[(size_t)m * nbp * 192 + i] = make_double2(blk[i].real(), blk[i].imag());
                 for (size_t i = 0; i < (size_t)np * 4; ++i)
                     hpY[(size_t)m * np * 4 + i] = make_double2(f.Y[i].real(), f.Y[i].imag());
                 for (int i = 0; i < 16; ++i) hpS[(size_t)m * 16 + i] = make_double2(f.Sinv[i].real(), f.Sinv[i].imag());
@@ -213,9 +218,13 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
                 bad[m] = 1;
                 continue;
             }
-            std::copy(g.L.begin(), g.L.end(), htL.begin() + (size_t)m * nt * 4);
-            std::copy(g.U.begin(), g.U.end(), htU.begin() + (size_t)m * nt * 4);
-            std::copy(g.invd.begin(), g.invd.end(), htD.begin() + (size_t)m * nt);
+            std::copy(bt.begin() + 2 * 9, bt.end(), htB.begin() + (size_t)m * nt * 9);
+            std::vector<double> tb;
+            if (!block_lu(bt, nc, 4, 2, tb)) {
+                bad[m] = 1;
+                continue;
+            }
+            std::copy(tb.begin(), tb.end(), htK.begin() + (size_t)m * nbt * 48);
             std::copy(g.Y.begin(), g.Y.end(), htY.begin() + (size_t)m * nt * 2);
             std::copy(g.Sinv.begin(), g.Sinv.end(), htS.begin() + (size_t)m * 4);
         }
@@ -249,19 +258,22 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         if (!dst) return fail(ctx, PIZZA_ENOMEM, "device allocation of factors failed");          \
         CK(cudaMemcpy(dst, (hv).data(), (hv).size() * sizeof(T), cudaMemcpyHostToDevice));       \
     } while (0)
-    UPLOAD(F.pL, double2, hpL);
-    UPLOAD(F.pU, double2, hpU);
-    UPLOAD(F.pInvd, double2, hpD);
+    std::vector<double> ub;
+    if (!block_lu(bu, nc, 4, 2, ub)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
+    UPLOAD(F.pBlk, double2, hpK);
     UPLOAD(F.pY, double2, hpY);
     UPLOAD(F.pSinv, double2, hpS);
-    UPLOAD(F.tL, double, htL);
-    UPLOAD(F.tU, double, htU);
-    UPLOAD(F.tInvd, double, htD);
+    UPLOAD(F.pBand, double2, hpB);
+    UPLOAD(F.tBlk, double, htK);
     UPLOAD(F.tY, double, htY);
     UPLOAD(F.tSinv, double, htS);
-    UPLOAD(F.uL, double, fu.L);
-    UPLOAD(F.uU, double, fu.U);
-    UPLOAD(F.uInvd, double, fu.invd);
+    UPLOAD(F.tBand, double, htB);
+    {
+        std::vector<double> ubd(bu.begin() + 2 * 9, bu.end());
+        UPLOAD(F.uBand, double, ubd);
+    }
+    F.refine_t = (nc > 600) ? 1 : 0;
+    UPLOAD(F.uBlk, double, ub);
     UPLOAD(F.uY, double, fu.Y);
     UPLOAD(F.uSinv, double, fu.Sinv);
 #undef UPLOAD
@@ -585,14 +597,20 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
             for (int j = 0; j < nc - 2; ++j) bd[(size_t)r * (nc - 2) + j] = td[(size_t)r * nc + 2 + j];
         double* dp = dalloc<double>(ctx, bp.size(), al);
         double* dd = dalloc<double>(ctx, bd.size(), al);
-        if (!dp || !dd) {
+        double* dfull = dalloc<double>(ctx, tp.size(), al);
+        double* dfull2 = dalloc<double>(ctx, td.size(), al);
+        if (!dp || !dd || !dfull || !dfull2) {
             ctx->err = "device allocation failed";
             return bail(PIZZA_ENOMEM);
         }
         up(dp, bp.data(), bp.size() * 8);
         up(dd, bd.data(), bd.size() * 8);
+        up(dfull, tp.data(), tp.size() * 8);
+        up(dfull2, td.data(), td.size() * 8);
+        P.ops.tau_dir = dfull2;
         P.ops.tau_psi_B = dp;
         P.ops.tau_dir_B = dd;
+        P.ops.tau_psi = dfull;
     }
     // work buffers and state vectors
     const size_t gsz = (size_t)n_r * 4 * ctx->M;

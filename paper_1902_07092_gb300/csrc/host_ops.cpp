@@ -378,6 +378,92 @@ bool factor_bordered(const std::vector<T>& band, int n_c, int h,
     return true;
 }
 
+namespace {
+template <class T>
+bool invert_small(std::vector<T> A, int h, std::vector<T>& inv) {
+    inv.assign((size_t)h * h, T(0));
+    for (int i = 0; i < h; ++i) inv[(size_t)i * h + i] = T(1);
+    for (int k = 0; k < h; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < h; ++i)
+            if (std::abs(A[(size_t)i * h + k]) > std::abs(A[(size_t)piv * h + k])) piv = i;
+        if (A[(size_t)piv * h + k] == T(0)) return false;
+        if (piv != k)
+            for (int j = 0; j < h; ++j) {
+                std::swap(A[(size_t)k * h + j], A[(size_t)piv * h + j]);
+                std::swap(inv[(size_t)k * h + j], inv[(size_t)piv * h + j]);
+            }
+        const T d = T(1) / A[(size_t)k * h + k];
+        for (int j = 0; j < h; ++j) {
+            A[(size_t)k * h + j] *= d;
+            inv[(size_t)k * h + j] *= d;
+        }
+        for (int i = 0; i < h; ++i) {
+            if (i == k) continue;
+            const T f = A[(size_t)i * h + k];
+            if (f == T(0)) continue;
+            for (int j = 0; j < h; ++j) {
+                A[(size_t)i * h + j] -= f * A[(size_t)k * h + j];
+                inv[(size_t)i * h + j] -= f * inv[(size_t)k * h + j];
+            }
+        }
+    }
+    return true;
+}
+}  // namespace
+
+template <class T>
+bool block_lu(const std::vector<T>& band, int n_c, int h, int p, std::vector<T>& out) {
+    const int W = 2 * h + 1;
+    const int n = n_c - p;
+    const int nb = (n + h - 1) / h;
+    // entry (i, j) of D (0-based within the block), identity beyond n
+    auto Dat = [&](int i, int j) -> T {
+        if (i >= n || j >= n) return (i == j) ? T(1) : T(0);
+        const int d = j - i + h;
+        if (d < 0 || d >= W) return T(0);
+        return band[(size_t)(i + p) * W + d];
+    };
+    const size_t hh = (size_t)h * h;
+    out.assign((size_t)nb * 3 * hh, T(0));
+    std::vector<T> U(hh), Uinv_prev(hh), Uinv(hh), Lk(hh);
+    for (int k = 0; k < nb; ++k) {
+        const int r0 = k * h;
+        for (int i = 0; i < h; ++i)
+            for (int j = 0; j < h; ++j) U[(size_t)i * h + j] = Dat(r0 + i, r0 + j);
+        if (k > 0) {
+            // L = D_{k,k-1} Uinv_{k-1};  U_kk -= L D_{k-1,k}
+            for (int i = 0; i < h; ++i)
+                for (int j = 0; j < h; ++j) {
+                    T acc = T(0);
+                    for (int t = 0; t < h; ++t) acc += Dat(r0 + i, r0 - h + t) * Uinv_prev[(size_t)t * h + j];
+                    Lk[(size_t)i * h + j] = acc;
+                }
+            for (int i = 0; i < h; ++i)
+                for (int j = 0; j < h; ++j) {
+                    T acc = T(0);
+                    for (int t = 0; t < h; ++t) acc += Lk[(size_t)i * h + t] * Dat(r0 - h + t, r0 + j);
+                    U[(size_t)i * h + j] -= acc;
+                }
+            std::copy(Lk.begin(), Lk.end(), out.begin() + (size_t)k * 3 * hh);
+        }
+        if (!invert_small(U, h, Uinv)) return false;
+        std::copy(Uinv.begin(), Uinv.end(), out.begin() + (size_t)k * 3 * hh + hh);
+        if (k < nb - 1)
+            for (int i = 0; i < h; ++i)
+                for (int j = 0; j < h; ++j) {
+                    T acc = T(0);
+                    for (int t = 0; t < h; ++t) acc += Uinv[(size_t)i * h + t] * Dat(r0 + t, r0 + h + j);
+                    out[(size_t)k * 3 * hh + 2 * hh + (size_t)i * h + j] = acc;
+                }
+        Uinv_prev = Uinv;
+    }
+    return true;
+}
+
+template bool block_lu<double>(const std::vector<double>&, int, int, int, std::vector<double>&);
+template bool block_lu<cplx>(const std::vector<cplx>&, int, int, int, std::vector<cplx>&);
+
 template bool factor_bordered<double>(const std::vector<double>&, int, int, const std::vector<double>&, int,
                                       Bordered<double>&);
 template bool factor_bordered<cplx>(const std::vector<cplx>&, int, int, const std::vector<double>&, int,

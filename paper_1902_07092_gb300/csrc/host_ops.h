@@ -47,6 +47,18 @@ struct Bordered {
     std::vector<T> L, U, invd, Y, Sinv;
 };
 
+// Block-tridiagonal LU of the banded block D (rows and columns p..n_c-1 of the
+// band storage, half width h) with blocks of h rows (nb = ceil(n/h), padding
+// rows identity):  D = L U with L unit block-lower-bidiagonal, U block upper
+// bidiagonal;  U_kk = D_kk - L_{k,k-1} D_{k-1,k},  L_{k,k-1} = D_{k,k-1} U_{k-1,k-1}^{-1}.
+// The diagonal blocks are inverted by Gauss-Jordan with partial pivoting.
+//   D x = b  <=>  z_k = b_k - L_{k,k-1} z_{k-1}  (k = 0..nb-1),
+//                 x_k = Uinv_k z_k - H_k x_{k+1}  (k = nb-1..0),  H_k = Uinv_k D_{k,k+1}.
+// Stored per block k as three row-major h x h matrices [k][0] L_{k,k-1},
+// [k][1] Uinv_k, [k][2] H_k.  Returns false if a diagonal block is singular.
+template <class T>
+bool block_lu(const std::vector<T>& band, int n_c, int h, int p, std::vector<T>& out);
+
 // Assemble and factor the tau system  [tau rows; Mass - gdt*Lin]  for one m.
 // mass_band / lin_band: band storage with half bandwidth h (complex).
 template <class T>

@@ -1,29 +1,34 @@
 // Implicit stage of one IMEX step: right-hand-side assembly (Eqs. multistep1
 // and dirks of Section 4) and the bordered banded solve of Appendix A of
-// Gastine, pizza, GJI 2019, one CTA per azimuthal mode m.
+// Gastine, pizza, GJI 2019.
 //
 // For each mode the tau system  [tau rows; Mass - gamma dt Lin] y = [0; r]  is
-//   (A B; C D)(y1; y2) = (0; h),   D banded (half width 8 for Psi, 4 for theta
+//   (A B; C D)(y1; y2) = (g; h),   D banded (half width 8 for Psi, 4 for theta
 //   and u_bar), factored at set-up without pivoting,
-//   x = D^{-1} h,  y1 = S^{-1}(0 - B x) with S = A - B D^{-1} C,  y2 = x - Y y1,
+//   x = D^{-1} h,  y1 = S^{-1}(g - B x) with S = A - B D^{-1} C,  y2 = x - Y y1,
 //   Y = D^{-1} C precomputed.
-// Warp 0 solves Psi_m, warp 1 theta_m, warp 2 u_bar (m = 0).  The epilogue
-// applies the banded mass (A^I_m, D^I) and implicit (B^I_m, F^I_m/Pr, E^I)
-// operators to the new state for later stages.
+// The unpivoted factorisation of the streamfunction block loses digits as n_r
+// grows, so its solution is refined once: the residual of the assembled system
+// is formed in FP64 and solved again with the same factors.
+//
+// The banded block is solved through its block-tridiagonal LU (blocks of 8 rows
+// for the streamfunction, 4 for temperature and zonal flow; host_ops.h): the
+// sequential part is one lane-parallel H x H mat-vec per block forward and one
+// fused pair of them per block backward.  On GB300 a
+// dependent FP64 FMA costs ~64 cycles, so this cuts the sequential chain of a
+// row-by-row substitution (two to four dependent FMAs per row) several-fold.
+// One warp per system: lane (r, c) = (lane/4, lane%4) owns row r of a block and
+// columns c, c+4.  A CTA handles MB consecutive modes; the right-hand side,
+// Schur updates, residual and the banded mass/implicit applies for later stages
+// use the whole CTA.
 #include "device_common.cuh"
 
 namespace pz {
 
 namespace {
 
-constexpr int NTHREADS_S = 128;
-constexpr int PF = 8;  // factor rows prefetched ahead by the solving warp
+constexpr int NTHREADS_S = 256;
 
-__device__ __forceinline__ double2 mul(double2 a, double2 b) { return cmul(a, b); }
-__device__ __forceinline__ double2 mul(double a, double2 b) { return cscale(b, a); }
-__device__ __forceinline__ double mul(double a, double b) { return a * b; }
-__device__ __forceinline__ double2 sub(double2 a, double2 b) { return csub(a, b); }
-__device__ __forceinline__ double sub(double a, double b) { return a - b; }
 template <class T>
 __device__ __forceinline__ T zero();
 template <>
@@ -31,86 +36,156 @@ __device__ __forceinline__ double2 zero<double2>() { return make_double2(0.0, 0.
 template <>
 __device__ __forceinline__ double zero<double>() { return 0.0; }
 
-// Unpivoted banded LU solve by one warp.  x (shared memory) has n entries;
-// L[j*H + t] = L(j+1+t, j), U[j*H + t] = U(j, j+1+t), invd[j] = 1/U(j,j).
+// x - a*z in fused form
+__device__ __forceinline__ double2 fms(double2 x, double2 a, double2 z) {
+    return make_double2(fma(-a.x, z.x, fma(a.y, z.y, x.x)), fma(-a.x, z.y, fma(-a.y, z.x, x.y)));
+}
+__device__ __forceinline__ double2 fms(double2 x, double a, double2 z) {
+    return make_double2(fma(-a, z.x, x.x), fma(-a, z.y, x.y));
+}
+__device__ __forceinline__ double2 mul(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ double2 mul(double a, double2 b) { return cscale(b, a); }
+
+template <class TX>
+__device__ __forceinline__ TX shfl_idx(TX v, int src);
+template <>
+__device__ __forceinline__ double shfl_idx<double>(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <>
+__device__ __forceinline__ double2 shfl_idx<double2>(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+// sum over the four lanes of a row (lanes 4r .. 4r+3); every lane gets the sum
+__device__ __forceinline__ double reduce4(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+__device__ __forceinline__ double2 reduce4(double2 v) { return make_double2(reduce4(v.x), reduce4(v.y)); }
+// acc + a*b
+__device__ __forceinline__ double2 fma_x(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 fma_x(double a, double2 b, double2 acc) {
+    return make_double2(fma(a, b.x, acc.x), fma(a, b.y, acc.y));
+}
+__device__ __forceinline__ double fma_x(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ double2 sub_x(double2 a, double2 b) { return csub(a, b); }
+__device__ __forceinline__ double sub_x(double a, double b) { return a - b; }
+
+__device__ __forceinline__ double2 fms_x(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 fms_x(double a, double2 b, double2 acc) {
+    return make_double2(fma(-a, b.x, acc.x), fma(-a, b.y, acc.y));
+}
+__device__ __forceinline__ double fms_x(double a, double b, double acc) { return fma(-a, b, acc); }
+
+constexpr int PFB = 2;  // blocks of coefficients prefetched ahead in the chains
+
+// Solve D x = b with the block-tridiagonal LU (blocks of H rows; per block
+// [0] L_{k,k-1}, [1] Uinv_k, [2] H_k) by one warp.  Lane (r, c) = (lane/4,
+// lane%4) owns row r of a block and columns c + 4q, q < H/4; the four lanes of a
+// row reduce by shuffles.
+//   forward:  z_k = b_k - L_{k,k-1} z_{k-1}          (Z: nb*H entries)
+//   backward: x_k = Uinv_k z_k - H_k x_{k+1}         (x: n entries)
+// Rows of b at or beyond n read as zero.
 template <int H, class TF, class TX>
-__device__ void warp_band_solve(TX* x, int n, const TF* __restrict__ Lf, const TF* __restrict__ Uf,
-                                const TF* __restrict__ invd) {
+__device__ void warp_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __restrict__ blk, bool act) {
+    constexpr int CPL = H / 4;
+    constexpr int HH = H * H;
     const int lane = threadIdx.x & 31;
-    const bool act = lane < H;
-    // forward: L z = h
-    TF cur[PF], nxt[PF];
-#pragma unroll
-    for (int i = 0; i < PF; ++i) {
-        const int j = i;
-        cur[i] = (act && j < n) ? Lf[(size_t)j * H + lane] : zero<TF>();
-    }
-    for (int j0 = 0; j0 < n; j0 += PF) {
-#pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            const int j = j0 + PF + i;
-            nxt[i] = (act && j < n) ? Lf[(size_t)j * H + lane] : zero<TF>();
-        }
-#pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            const int j = j0 + i;
-            if (j < n) {
-                const TX z = x[j];
-                if (act && j + 1 + lane < n) x[j + 1 + lane] = sub(x[j + 1 + lane], mul(cur[i], z));
-                __syncwarp();
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PF; ++i) cur[i] = nxt[i];
-    }
-    // backward: U x = z  (column oriented)
-    TF dcur = zero<TF>(), dnxt = zero<TF>();
+    const int r = lane >> 2, c = lane & 3;
+    const bool ra = act && r < H;
+    const int nb = (n + H - 1) / H;
+    auto coef = [&](int k, int which, int q) -> TF {
+        return (ra && k >= 0 && k < nb) ? blk[(size_t)k * 3 * HH + which * HH + r * H + c + 4 * q] : zero<TF>();
+    };
+    // forward chain
     {
-        // cur[i] holds U(j-1-lane, j) for j = top - i; lane < PF also holds invd
-        const int top = n - 1;
+        TX prev[CPL];
+        TF cur[PFB][CPL], nxt[PFB][CPL];
 #pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            const int j = top - i, r = j - 1 - lane;
-            cur[i] = (act && r >= 0) ? Uf[(size_t)r * H + lane] : zero<TF>();
-        }
-        dcur = (lane < PF && top - lane >= 0) ? invd[top - lane] : zero<TF>();
-    }
-    for (int j0 = n - 1; j0 >= 0; j0 -= PF) {
+        for (int q = 0; q < CPL; ++q) prev[q] = zero<TX>();
 #pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            const int j = j0 - PF - i, r = j - 1 - lane;
-            nxt[i] = (act && j >= 0 && r >= 0) ? Uf[(size_t)r * H + lane] : zero<TF>();
-        }
-        {
-            const int j = j0 - PF - lane;
-            dnxt = (lane < PF && j >= 0) ? invd[j] : zero<TF>();
-        }
+        for (int i = 0; i < PFB; ++i)
 #pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            const int j = j0 - i;
-            if (j >= 0) {
-                TF di;
-                if constexpr (sizeof(TF) == sizeof(double2)) {
-                    double2 dd = *reinterpret_cast<double2*>(&dcur);
-                    dd.x = __shfl_sync(0xffffffffu, dd.x, i);
-                    dd.y = __shfl_sync(0xffffffffu, dd.y, i);
-                    di = *reinterpret_cast<TF*>(&dd);
-                } else {
-                    double dd = *reinterpret_cast<double*>(&dcur);
-                    dd = __shfl_sync(0xffffffffu, dd, i);
-                    di = *reinterpret_cast<TF*>(&dd);
+            for (int q = 0; q < CPL; ++q) cur[i][q] = coef(i, 0, q);
+        for (int k0 = 0; k0 < nb; k0 += PFB) {
+#pragma unroll
+            for (int i = 0; i < PFB; ++i)
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) nxt[i][q] = coef(k0 + PFB + i, 0, q);
+#pragma unroll
+            for (int i = 0; i < PFB; ++i) {
+                const int k = k0 + i;
+                if (k < nb) {
+                    const int row = k * H + r;
+                    const TX bv = (ra && row < n) ? b[row] : zero<TX>();
+                    TX p = zero<TX>();
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) p = fma_x(cur[i][q], prev[q], p);
+                    p = reduce4(p);
+                    const TX zv = sub_x(bv, p);
+                    if (ra && c == 0) Z[row] = zv;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(zv, 4 * (c + 4 * q));
                 }
-                const TX xj = mul(di, x[j]);
-                __syncwarp();
-                if (lane == 0) x[j] = xj;
-                if (act && j - 1 - lane >= 0) x[j - 1 - lane] = sub(x[j - 1 - lane], mul(cur[i], xj));
-                __syncwarp();
             }
-        }
 #pragma unroll
-        for (int i = 0; i < PF; ++i) cur[i] = nxt[i];
-        dcur = dnxt;
+            for (int i = 0; i < PFB; ++i)
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) cur[i][q] = nxt[i][q];
+        }
     }
+    __syncwarp();
+    // backward chain
+    {
+        TX prev[CPL];
+        TF cu[PFB][CPL], ch[PFB][CPL], nu[PFB][CPL], nh[PFB][CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) prev[q] = zero<TX>();
+#pragma unroll
+        for (int i = 0; i < PFB; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                cu[i][q] = coef(nb - 1 - i, 1, q);
+                ch[i][q] = coef(nb - 1 - i, 2, q);
+            }
+        for (int i0 = 0; i0 < nb; i0 += PFB) {
+#pragma unroll
+            for (int i = 0; i < PFB; ++i)
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    nu[i][q] = coef(nb - 1 - (i0 + PFB + i), 1, q);
+                    nh[i][q] = coef(nb - 1 - (i0 + PFB + i), 2, q);
+                }
+#pragma unroll
+            for (int i = 0; i < PFB; ++i) {
+                const int k = nb - 1 - (i0 + i);
+                if (k >= 0) {
+                    TX p = zero<TX>();
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) {
+                        const TX zq = ra ? Z[k * H + c + 4 * q] : zero<TX>();
+                        p = fma_x(cu[i][q], zq, p);
+                        p = fms_x(ch[i][q], prev[q], p);
+                    }
+                    p = reduce4(p);
+                    const int row = k * H + r;
+                    if (ra && c == 0 && row < n) x[row] = p;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(p, 4 * (c + 4 * q));
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < PFB; ++i)
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    cu[i][q] = nu[i][q];
+                    ch[i][q] = nh[i][q];
+                }
+        }
+    }
+    __syncwarp();
 }
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
@@ -122,18 +197,18 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
     return v;
 }
 
-// Schur step of Appendix A for one field, by one warp: x holds the full vector of
-// length n_c; on entry x[p..] = D^{-1} h; on exit the solution.  B: p x (n_c-p)
-// real tau rows; Sinv: p x p; Y: (n_c-p) x p.
+// Schur step of Appendix A by one warp: sol[PB..] = D^{-1} h on entry;
+// sol[0..PB) = S^{-1}(g - B sol[PB..]) on exit.  B: PB x (nc-PB) real tau rows.
 template <int PB, class TF>
-__device__ void warp_schur(double2* x, int nc, const double* __restrict__ B, const TF* __restrict__ Sinv) {
+__device__ void warp_schur(double2* sol, const double2* g, int nc, const double* __restrict__ B,
+                           const TF* __restrict__ Sinv) {
     const int lane = threadIdx.x & 31;
     const int n = nc - PB;
     double2 t[PB];
 #pragma unroll
     for (int r = 0; r < PB; ++r) t[r] = make_double2(0.0, 0.0);
     for (int j = lane; j < n; j += 32) {
-        const double2 xv = x[PB + j];
+        const double2 xv = sol[PB + j];
 #pragma unroll
         for (int r = 0; r < PB; ++r) {
             const double b = __ldg(&B[(size_t)r * n + j]);
@@ -142,27 +217,28 @@ __device__ void warp_schur(double2* x, int nc, const double* __restrict__ B, con
         }
     }
 #pragma unroll
-    for (int r = 0; r < PB; ++r) t[r] = warp_sum(t[r]);
+    for (int r = 0; r < PB; ++r) t[r] = csub(g ? g[r] : make_double2(0.0, 0.0), warp_sum(t[r]));
     if (lane < PB) {
         double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
-        for (int c = 0; c < PB; ++c) acc = csub(acc, mul(Sinv[lane * PB + c], t[c]));
-        x[lane] = acc;
+        for (int c = 0; c < PB; ++c) acc = cadd(acc, mul(Sinv[lane * PB + c], t[c]));
+        sol[lane] = acc;
     }
     __syncwarp();
 }
 
+// y2 -= Y y1 over the rows of one system, threads [t0, t0 + nt)
 template <int PB, class TF>
-__device__ void block_schur_update(double2* x, int nc, const TF* __restrict__ Y) {
+__device__ void schur_update(double2* sol, int nc, const TF* __restrict__ Y, int t0, int nt) {
     const int n = nc - PB;
     double2 y1[PB];
 #pragma unroll
-    for (int c = 0; c < PB; ++c) y1[c] = x[c];
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double2 acc = x[PB + j];
+    for (int c = 0; c < PB; ++c) y1[c] = sol[c];
+    for (int j = threadIdx.x - t0; j < n; j += nt) {
+        double2 acc = sol[PB + j];
 #pragma unroll
-        for (int c = 0; c < PB; ++c) acc = csub(acc, mul(Y[(size_t)j * PB + c], y1[c]));
-        x[PB + j] = acc;
+        for (int c = 0; c < PB; ++c) acc = fms(acc, Y[(size_t)j * PB + c], y1[c]);
+        sol[PB + j] = acc;
     }
 }
 
@@ -182,81 +258,224 @@ __device__ __forceinline__ double2 band_row_c(const double* __restrict__ band, c
     return acc;
 }
 
-// mass / implicit operators applied to the state held in shared memory
-__device__ void apply_epilogue(const StepParams& P, int m, const double2* xp, const double2* xt, const double* xu,
-                               VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp) {
+// mass / implicit operators applied to one mode's new state
+__device__ void apply_row(const StepParams& P, int m, int k, const double2* xp, const double2* xt, const double* xu,
+                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp) {
     const int nc = P.nc;
     const double mu = (double)m * m;
     const double dm = (double)m;
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-        double2 mp = make_double2(0.0, 0.0), ip = make_double2(0.0, 0.0);
-        double2 mt = make_double2(0.0, 0.0), it = make_double2(0.0, 0.0);
-        if (m > 0 && k >= 4) {
-            if (want_mass) {
-                const double2 a0 = band_row_c<8>(P.ops.band[OP_A0], xp, k, nc);
-                const double2 a2 = band_row_c<8>(P.ops.band[OP_A2], xp, k, nc);
-                mp = make_double2(fma(mu, a2.x, a0.x), fma(mu, a2.y, a0.y));
-            }
-            if (want_imp) {
-                const double2 b0 = band_row_c<6>(P.ops.band[OP_B0], xp, k, nc);
-                const double2 b2 = band_row_c<6>(P.ops.band[OP_B2], xp, k, nc);
-                const double2 b4 = band_row_c<6>(P.ops.band[OP_B4], xp, k, nc);
-                const double2 c = band_row_c<8>(P.ops.band[OP_C], xp, k, nc);
-                const double ce = 2.0 * dm / P.E;
-                ip.x = b0.x + mu * (b2.x + mu * b4.x) - ce * c.y;
-                ip.y = b0.y + mu * (b2.y + mu * b4.y) + ce * c.x;
-            }
-        }
-        if (k >= 2) {
-            if (want_mass) mt = band_row_c<4>(P.ops.band[OP_D], xt, k, nc);
-            if (want_imp) {
-                const double2 f0 = band_row_c<2>(P.ops.band[OP_F0], xt, k, nc);
-                const double2 f2 = band_row_c<2>(P.ops.band[OP_F2], xt, k, nc);
-                const double ip_ = 1.0 / P.Pr;
-                it = make_double2((f0.x + mu * f2.x) * ip_, (f0.y + mu * f2.y) * ip_);
-            }
-        }
+    double2 mp = make_double2(0.0, 0.0), ip = make_double2(0.0, 0.0);
+    double2 mt = make_double2(0.0, 0.0), it = make_double2(0.0, 0.0);
+    if (m > 0 && k >= 4) {
         if (want_mass) {
-            mass_out.psi[(size_t)m * nc + k] = mp;
-            mass_out.th[(size_t)m * nc + k] = mt;
+            const double2 a0 = band_row_c<8>(P.ops.band[OP_A0], xp, k, nc);
+            const double2 a2 = band_row_c<8>(P.ops.band[OP_A2], xp, k, nc);
+            mp = make_double2(fma(mu, a2.x, a0.x), fma(mu, a2.y, a0.y));
         }
         if (want_imp) {
-            imp_out.psi[(size_t)m * nc + k] = ip;
-            imp_out.th[(size_t)m * nc + k] = it;
+            const double2 b0 = band_row_c<6>(P.ops.band[OP_B0], xp, k, nc);
+            const double2 b2 = band_row_c<6>(P.ops.band[OP_B2], xp, k, nc);
+            const double2 b4 = band_row_c<6>(P.ops.band[OP_B4], xp, k, nc);
+            const double2 c = band_row_c<8>(P.ops.band[OP_C], xp, k, nc);
+            const double ce = 2.0 * dm / P.E;
+            ip.x = b0.x + mu * (b2.x + mu * b4.x) - ce * c.y;
+            ip.y = b0.y + mu * (b2.y + mu * b4.y) + ce * c.x;
         }
-        if (m == 0) {
-            double mu_ = 0.0, iu = 0.0;
-            if (k >= 2) {
-                const double* rd = P.ops.band[OP_D] + (size_t)k * 9;
-                const double* re = P.ops.band[OP_EZ] + (size_t)k * 5;
-                for (int d = 0; d < 9; ++d) {
-                    const int n = k - 4 + d;
-                    if (n >= 0 && n < nc) mu_ = fma(__ldg(&rd[d]), xu[n], mu_);
-                }
-                for (int d = 0; d < 5; ++d) {
-                    const int n = k - 2 + d;
-                    if (n >= 0 && n < nc) iu = fma(__ldg(&re[d]), xu[n], iu);
-                }
+    }
+    if (k >= 2) {
+        if (want_mass) mt = band_row_c<4>(P.ops.band[OP_D], xt, k, nc);
+        if (want_imp) {
+            const double2 f0 = band_row_c<2>(P.ops.band[OP_F0], xt, k, nc);
+            const double2 f2 = band_row_c<2>(P.ops.band[OP_F2], xt, k, nc);
+            const double ip_ = 1.0 / P.Pr;
+            it = make_double2((f0.x + mu * f2.x) * ip_, (f0.y + mu * f2.y) * ip_);
+        }
+    }
+    if (want_mass) {
+        mass_out.psi[(size_t)m * nc + k] = mp;
+        mass_out.th[(size_t)m * nc + k] = mt;
+    }
+    if (want_imp) {
+        imp_out.psi[(size_t)m * nc + k] = ip;
+        imp_out.th[(size_t)m * nc + k] = it;
+    }
+    if (m == 0) {
+        double mu_ = 0.0, iu = 0.0;
+        if (k >= 2) {
+            const double* rd = P.ops.band[OP_D] + (size_t)k * 9;
+            const double* re = P.ops.band[OP_EZ] + (size_t)k * 5;
+            for (int d = 0; d < 9; ++d) {
+                const int n = k - 4 + d;
+                if (n >= 0 && n < nc) mu_ = fma(__ldg(&rd[d]), xu[n], mu_);
             }
-            if (want_mass) mass_out.u[k] = mu_;
-            if (want_imp) imp_out.u[k] = iu;
+            for (int d = 0; d < 5; ++d) {
+                const int n = k - 2 + d;
+                if (n >= 0 && n < nc) iu = fma(__ldg(&re[d]), xu[n], iu);
+            }
         }
+        if (want_mass) mass_out.u[k] = mu_;
+        if (want_imp) imp_out.u[k] = iu;
     }
 }
 
+// shared-memory layout of one CTA, per mode mi < MB:
+//   streamfunction: pf rhs (then the refinement residual), pw forward-chain
+//                   values, px solution, pd correction
+//   temperature:    tf rhs, tw forward-chain values, tx solution
+// and for the zonal flow (the CTA holding m = 0): uf rhs, ux solution (real); its
+// chain scratch is the temperature warp's, reused after the temperature solve.
+struct SolveSmem {
+    double2 *pf[2], *pw[2], *px[2], *pd[2], *tf[2], *tw[2], *tx[2];
+    double *uf, *ux;
+};
+
+__host__ __device__ inline int round8(int n) { return (n + 7) / 8 * 8; }
+
+__host__ __device__ inline size_t solve_smem_doubles(int nc, int MB) {
+    const int b = round8(nc);
+    return (size_t)MB * 2 * 7 * b + 2 * (size_t)b;
+}
+
+template <int MB>
+__device__ SolveSmem carve(double2* base, int nc) {
+    SolveSmem s;
+    const int b = round8(nc);
+    double2* p = base;
+    for (int i = 0; i < MB; ++i) {
+        s.pf[i] = p; p += b;
+        s.pw[i] = p; p += b;
+        s.px[i] = p; p += b;
+        s.pd[i] = p; p += b;
+        s.tf[i] = p; p += b;
+        s.tw[i] = p; p += b;
+        s.tx[i] = p; p += b;
+    }
+    double* d = reinterpret_cast<double*>(p);
+    s.uf = d; d += b;
+    s.ux = d;
+    return s;
+}
+
+// One refinement step of the temperature (and zonal-flow) solves, used for large
+// N_c: r = f - L x over the assembled rows and the tau rows, solved with the
+// same factors, x += correction.  The residual replaces the right-hand side and
+// the correction goes to the streamfunction's correction array (no longer needed).
+template <int MB>
+__device__ void refine_temperature(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u) {
+    const int nc = P.nc, M = P.M, nt = nc - 2, nbt = (nt + 3) / 4;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
+    for (int idx = tid; idx < MB * nc; idx += nth) {
+        const int mi = idx / nc, k = idx - mi * nc, m = m0 + mi;
+        if (m >= M || k < 2) continue;
+        const double* row = F.tBand + ((size_t)m * nt + (k - 2)) * 9;
+        const double2* x = s.tx[mi];
+        double2 acc = s.tf[mi][k];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+            const int n = k - 4 + d;
+            if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), x[n]);
+        }
+        s.tf[mi][k] = acc;
+    }
+    if (has_u)
+        for (int k = 2 + tid; k < nc; k += nth) {
+            const double* row = F.uBand + (size_t)(k - 2) * 9;
+            double acc = s.uf[k];
+            for (int d = 0; d < 9; ++d) {
+                const int n = k - 4 + d;
+                if (n >= 0 && n < nc) acc = fma(-__ldg(&row[d]), s.ux[n], acc);
+            }
+            s.uf[k] = acc;
+        }
+    if (warp < MB + (has_u ? 1 : 0)) {  // tau rows
+        const bool is_u = (warp == MB);
+        const int m = m0 + warp;
+        if (is_u || m < M) {
+            double2 t0 = make_double2(0.0, 0.0), t1 = make_double2(0.0, 0.0);
+            for (int j = lane; j < nc; j += 32) {
+                const double2 xv = is_u ? make_double2(s.ux[j], 0.0) : s.tx[warp][j];
+                const double b0 = __ldg(&P.ops.tau_dir[j]), b1 = __ldg(&P.ops.tau_dir[nc + j]);
+                t0.x = fma(b0, xv.x, t0.x);
+                t0.y = fma(b0, xv.y, t0.y);
+                t1.x = fma(b1, xv.x, t1.x);
+                t1.y = fma(b1, xv.y, t1.y);
+            }
+            t0 = warp_sum(t0);
+            t1 = warp_sum(t1);
+            if (lane < 2) {
+                const double2 t = lane ? t1 : t0;
+                if (is_u)
+                    s.uf[lane] = -t.x;
+                else
+                    s.tf[warp][lane] = make_double2(-t.x, -t.y);
+            }
+        }
+    }
+    __syncthreads();
+    double2* dt_[2] = {s.pd[0], s.pd[MB > 1 ? 1 : 0]};
+    double* du = reinterpret_cast<double*>(s.pw[0]);  // after the streamfunction solves
+    if (warp >= MB && warp < 2 * MB) {
+        const int mi = warp - MB, m = m0 + mi;
+        const bool act = m < M;
+        warp_block_solve<4>(s.tf[mi] + 2, s.tw[mi], dt_[mi] + 2, nt, F.tBlk + (size_t)(act ? m : 0) * nbt * 48, act);
+        if (act) warp_schur<2>(dt_[mi], s.tf[mi], nc, P.ops.tau_dir_B, F.tSinv + (size_t)m * 4);
+        if (has_u && mi == 0) {
+            warp_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.tw[0]), du + 2, nt, F.uBlk, true);
+            double t0 = 0.0, t1 = 0.0;
+            for (int j = lane; j < nt; j += 32) {
+                t0 = fma(__ldg(&P.ops.tau_dir_B[j]), du[2 + j], t0);
+                t1 = fma(__ldg(&P.ops.tau_dir_B[nt + j]), du[2 + j], t1);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+                t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+            }
+            const double g0 = s.uf[0], g1 = s.uf[1];
+            __syncwarp();
+            if (lane < 2) du[lane] = F.uSinv[lane * 2] * (g0 - t0) + F.uSinv[lane * 2 + 1] * (g1 - t1);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    {
+        const int per = nth / MB;
+        const int sys = tid / per, t0 = sys * per;
+        const int m = m0 + sys;
+        if (sys < MB && m < M) schur_update<2>(dt_[sys], nc, F.tY + (size_t)m * nt * 2, t0, per);
+        if (has_u) {
+            __syncthreads();
+            const double u0 = du[0], u1 = du[1];
+            for (int j = tid; j < nt; j += nth) du[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < MB * nc; idx += nth) {
+        const int mi = idx / nc, n = idx - mi * nc, m = m0 + mi;
+        if (m >= M) continue;
+        s.tx[mi][n] = cadd(s.tx[mi][n], dt_[mi][n]);
+        if (m == 0) s.ux[n] += du[n];
+    }
+    __syncthreads();
+}
+
+template <int MB>
 __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, DevFactors F, VecSet y_out,
                                                       VecSet mass_out, VecSet imp_out, int want_mass,
                                                       int want_imp) {
     extern __shared__ double2 sm[];
-    const int m = blockIdx.x;
-    const int nc = P.nc;
-    double2* xp = sm;
-    double2* xt = xp + nc;
-    double* xu = reinterpret_cast<double*>(xt + nc);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nc = P.nc, M = P.M;
+    const int m0 = blockIdx.x * MB;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
+    const int np = nc - 4, nt = nc - 2;
+    const int nbp = (np + 7) / 8, nbt = (nt + 3) / 4;
+    SolveSmem s = carve<MB>(sm, nc);
+    const bool has_u = (m0 == 0);
 
-    // right-hand side: sum_t c_t V_t, tau rows zero
-    for (int n = tid; n < nc; n += blockDim.x) {
+    // 1. right-hand side sum_t c_t V_t (tau rows zero)
+    for (int idx = tid; idx < MB * nc; idx += nth) {
+        const int mi = idx / nc, n = idx - mi * nc, m = m0 + mi;
+        if (m >= M) continue;
         double2 ap = make_double2(0.0, 0.0), at = make_double2(0.0, 0.0);
         double au = 0.0;
         for (int t = 0; t < R.nterms; ++t) {
@@ -269,52 +488,142 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
             at.y = fma(c, vt.y, at.y);
             if (m == 0) au = fma(c, R.t[t].v.u[n], au);
         }
-        xp[n] = (n < 4 || m == 0) ? make_double2(0.0, 0.0) : ap;
-        xt[n] = (n < 2) ? make_double2(0.0, 0.0) : at;
-        if (m == 0) xu[n] = (n < 2) ? 0.0 : au;
+        s.pf[mi][n] = (n < 4 || m == 0) ? make_double2(0.0, 0.0) : ap;
+        s.tf[mi][n] = (n < 2) ? make_double2(0.0, 0.0) : at;
+        if (m == 0) s.uf[n] = (n < 2) ? 0.0 : au;
     }
     __syncthreads();
-    const int np = nc - 4, nt = nc - 2;
-    if (warp == 0 && m > 0) {
-        warp_band_solve<8>(xp + 4, np, F.pL + (size_t)m * np * 8, F.pU + (size_t)m * np * 8,
-                           F.pInvd + (size_t)m * np);
-        warp_schur<4>(xp, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
-    } else if (warp == 1) {
-        warp_band_solve<4>(xt + 2, nt, F.tL + (size_t)m * nt * 4, F.tU + (size_t)m * nt * 4,
-                           F.tInvd + (size_t)m * nt);
-        warp_schur<2>(xt, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m * 4);
-    } else if (warp == 2 && m == 0) {
-        warp_band_solve<4>(xu + 2, nt, F.uL, F.uU, F.uInvd);
-        // real Schur step
-        const int lane = tid & 31;
+
+    // 2. banded solves: warp w < MB streamfunction of mode w, warps MB..2MB-1
+    //    temperature (the warp of mode m = 0 then also the zonal flow)
+    if (warp < MB) {
+        const int m = m0 + warp;
+        const bool act = m < M && m > 0;
+        warp_block_solve<8>(s.pf[warp] + 4, s.pw[warp], s.px[warp] + 4, np,
+                            F.pBlk + (size_t)(act ? m : 0) * nbp * 192, act);
+    } else if (warp < 2 * MB) {
+        const int mi = warp - MB, m = m0 + mi;
+        const bool act = m < M;
+        warp_block_solve<4>(s.tf[mi] + 2, s.tw[mi], s.tx[mi] + 2, nt,
+                            F.tBlk + (size_t)(act ? m : 0) * nbt * 48, act);
+        if (has_u && mi == 0)
+            warp_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.tw[0]), s.ux + 2, nt, F.uBlk, true);
+    }
+    __syncthreads();
+
+    // 3. Schur steps (same warp assignment)
+    if (warp < MB) {
+        const int m = m0 + warp;
+        if (m < M && m > 0) warp_schur<4>(s.px[warp], nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
+    } else if (warp < 2 * MB) {
+        const int mi = warp - MB, m = m0 + mi;
+        if (m < M) warp_schur<2>(s.tx[mi], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m * 4);
+    } else if (warp == 2 * MB && has_u) {
         double t0 = 0.0, t1 = 0.0;
         for (int j = lane; j < nt; j += 32) {
-            t0 = fma(__ldg(&P.ops.tau_dir_B[j]), xu[2 + j], t0);
-            t1 = fma(__ldg(&P.ops.tau_dir_B[nt + j]), xu[2 + j], t1);
+            t0 = fma(__ldg(&P.ops.tau_dir_B[j]), s.ux[2 + j], t0);
+            t1 = fma(__ldg(&P.ops.tau_dir_B[nt + j]), s.ux[2 + j], t1);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             t0 += __shfl_xor_sync(0xffffffffu, t0, o);
             t1 += __shfl_xor_sync(0xffffffffu, t1, o);
         }
-        if (lane < 2) xu[lane] = -(F.uSinv[lane * 2] * t0 + F.uSinv[lane * 2 + 1] * t1);
+        if (lane < 2) s.ux[lane] = -(F.uSinv[lane * 2] * t0 + F.uSinv[lane * 2 + 1] * t1);
         __syncwarp();
     }
     __syncthreads();
-    if (m > 0) block_schur_update<4>(xp, nc, F.pY + (size_t)m * np * 4);
-    block_schur_update<2>(xt, nc, F.tY + (size_t)m * nt * 2);
-    if (m == 0) {
-        const double u0 = xu[0], u1 = xu[1];
-        for (int j = tid; j < nt; j += blockDim.x)
-            xu[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
+    // 4. y2 -= Y y1 (threads split evenly over the systems of the CTA)
+    {
+        const int per = nth / (2 * MB);
+        const int sys = tid / per, t0 = sys * per;
+        if (sys < MB) {
+            const int m = m0 + sys;
+            if (m < M && m > 0) schur_update<4>(s.px[sys], nc, F.pY + (size_t)m * np * 4, t0, per);
+        } else if (sys < 2 * MB) {
+            const int mi = sys - MB, m = m0 + mi;
+            if (m < M) schur_update<2>(s.tx[mi], nc, F.tY + (size_t)m * nt * 2, t0, per);
+        }
+        if (has_u) {
+            __syncthreads();
+            const double u0 = s.ux[0], u1 = s.ux[1];
+            for (int j = tid; j < nt; j += nth) s.ux[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
+        }
     }
     __syncthreads();
-    for (int n = tid; n < nc; n += blockDim.x) {
-        y_out.psi[(size_t)m * nc + n] = xp[n];
-        y_out.th[(size_t)m * nc + n] = xt[n];
-        if (m == 0) y_out.u[n] = xu[n];
+
+    // 5. one refinement step of the streamfunction solve: r = f - L x (a second
+    //    step gains nothing: FP64 residuals limit the accuracy to ~cond * eps)
+    for (int it = 0; it < 1; ++it) {
+    for (int idx = tid; idx < MB * nc; idx += nth) {
+        const int mi = idx / nc, k = idx - mi * nc, m = m0 + mi;
+        if (m >= M || m == 0 || k < 4) continue;
+        const double2* row = F.pBand + ((size_t)m * np + (k - 4)) * 17;
+        // pass 0: r = f - L x; later passes: r <- r - L d (d: the last correction)
+        const double2* x = it ? s.pd[mi] : s.px[mi];
+        double2 acc = s.pf[mi][k];
+#pragma unroll
+        for (int d = 0; d < 17; ++d) {
+            const int n = k - 8 + d;
+            if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), x[n]);
+        }
+        s.pf[mi][k] = acc;  // the residual replaces the right-hand side
     }
-    if (want_mass || want_imp) apply_epilogue(P, m, xp, xt, xu, mass_out, imp_out, want_mass, want_imp);
+    if (warp < MB) {  // tau rows: r = 0 - tau x
+        const int m = m0 + warp;
+        if (m < M && m > 0) {
+            double2 t[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) t[r] = make_double2(0.0, 0.0);
+            for (int j = lane; j < nc; j += 32) {
+                const double2 xv = it ? s.pd[warp][j] : s.px[warp][j];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const double b = __ldg(&P.ops.tau_psi[(size_t)r * nc + j]);
+                    t[r].x = fma(b, xv.x, t[r].x);
+                    t[r].y = fma(b, xv.y, t[r].y);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) t[r] = warp_sum(t[r]);
+            if (lane < 4) s.pf[warp][lane] = csub(s.pf[warp][lane], t[lane]);
+        }
+    }
+    __syncthreads();
+    if (warp < MB) {
+        const int m = m0 + warp;
+        const bool act = m < M && m > 0;
+        warp_block_solve<8>(s.pf[warp] + 4, s.pw[warp], s.pd[warp] + 4, np,
+                            F.pBlk + (size_t)(act ? m : 0) * nbp * 192, act);
+        if (act) warp_schur<4>(s.pd[warp], s.pf[warp], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
+    }
+    __syncthreads();
+    {
+        const int per = nth / MB;
+        const int sys = tid / per, t0 = sys * per;
+        const int m = m0 + sys;
+        if (sys < MB && m < M && m > 0) schur_update<4>(s.pd[sys], nc, F.pY + (size_t)m * np * 4, t0, per);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < MB * nc; idx += nth) {
+        const int mi = idx / nc, n = idx - mi * nc, m = m0 + mi;
+        if (m >= M) continue;
+        s.px[mi][n] = (m == 0) ? make_double2(0.0, 0.0) : cadd(s.px[mi][n], s.pd[mi][n]);
+    }
+    __syncthreads();
+    }
+    if (F.refine_t) refine_temperature<MB>(P, F, s, m0, has_u);
+
+    // 6. store, then mass / implicit operators for later stages
+    for (int idx = tid; idx < MB * nc; idx += nth) {
+        const int mi = idx / nc, n = idx - mi * nc, m = m0 + mi;
+        if (m >= M) continue;
+        y_out.psi[(size_t)m * nc + n] = s.px[mi][n];
+        y_out.th[(size_t)m * nc + n] = s.tx[mi][n];
+        if (m == 0) y_out.u[n] = s.ux[n];
+        if (want_mass || want_imp)
+            apply_row(P, m, n, s.px[mi], s.tx[mi], s.ux, mass_out, imp_out, want_mass, want_imp);
+    }
 }
 
 __global__ void __launch_bounds__(NTHREADS_S) k_apply(StepParams P, VecSet y, VecSet mass_out, VecSet imp_out,
@@ -331,26 +640,40 @@ __global__ void __launch_bounds__(NTHREADS_S) k_apply(StepParams P, VecSet y, Ve
         if (m == 0) xu[n] = y.u[n];
     }
     __syncthreads();
-    apply_epilogue(P, m, xp, xt, xu, mass_out, imp_out, want_mass, want_imp);
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) apply_row(P, m, k, xp, xt, xu, mass_out, imp_out, want_mass, want_imp);
 }
+
+int modes_per_cta(const StepParams& P) { return P.nc <= 900 ? 2 : 1; }
+
+size_t smem_solve_mb(const StepParams& P, int MB) { return sizeof(double) * solve_smem_doubles(P.nc, MB); }
 
 }  // namespace
 
-size_t smem_solve(const StepParams& P) { return sizeof(double2) * 2 * P.nc + sizeof(double) * P.nc; }
+size_t smem_solve(const StepParams& P) { return smem_solve_mb(P, modes_per_cta(P)); }
 
 cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFactors& F, VecSet y_out,
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st) {
-    const size_t sm = smem_solve(P);
-    cudaError_t err = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    k_solve<<<P.M, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
-                                         want_imp ? 1 : 0);
+    const int MB = modes_per_cta(P);
+    const size_t sm = smem_solve_mb(P, MB);
+    const int grid = (P.M + MB - 1) / MB;
+    cudaError_t err;
+    if (MB == 2) {
+        err = cudaFuncSetAttribute(k_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_solve<2><<<grid, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+                                                  want_imp ? 1 : 0);
+    } else {
+        err = cudaFuncSetAttribute(k_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_solve<1><<<grid, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+                                                  want_imp ? 1 : 0);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const StepParams& P, VecSet y, VecSet mass_out, VecSet imp_out, bool want_mass,
                          bool want_imp, cudaStream_t st) {
-    const size_t sm = smem_solve(P);
+    const size_t sm = sizeof(double2) * 2 * P.nc + sizeof(double) * P.nc;
     cudaError_t err = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     k_apply<<<P.M, NTHREADS_S, sm, st>>>(P, y, mass_out, imp_out, want_mass ? 1 : 0, want_imp ? 1 : 0);

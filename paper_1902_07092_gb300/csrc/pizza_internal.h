@@ -32,17 +32,24 @@ struct DevOps {
     const double* band[OP_COUNT];
     const double* tau_psi_B;  // 4 x (nc-4): tau rows restricted to columns 4..
     const double* tau_dir_B;  // 2 x (nc-2)
+    const double* tau_psi;    // 4 x nc: the full streamfunction tau rows
+    const double* tau_dir;    // 2 x nc: the full Dirichlet tau rows
 };
 
-// Factored bordered systems (Appendix A) for one implicit weight gamma*dt.
+// Factored bordered systems (Appendix A) for one implicit weight gamma*dt.  The
+// banded block is held as a block-tridiagonal LU (host_ops.h, block_lu): per
+// block k of H rows three H x H matrices L_{k,k-1}, Uinv_k, H_k.
 struct DevFactors {
     double gdt;
-    // streamfunction, complex, per m: L,U [M][n_p][8], invd [M][n_p], Y [M][n_p][4], Sinv [M][16]
-    double2 *pL, *pU, *pInvd, *pY, *pSinv;
-    // temperature, real, per m: L,U [M][n_t][4], invd [M][n_t], Y [M][n_t][2], Sinv [M][4]
-    double *tL, *tU, *tInvd, *tY, *tSinv;
-    // zonal flow, real: L,U [n_t][4], invd [n_t], Y [n_t][2], Sinv [4]
-    double *uL, *uU, *uInvd, *uY, *uSinv;
+    // streamfunction, complex, H = 8: blocks [M][nb_p][3][64], Y [M][n_p][4],
+    // Sinv [M][16], assembled rows 4..nc-1 of A^I_m - gamma dt B^I_m [M][n_p][17]
+    double2 *pBlk, *pY, *pSinv, *pBand;
+    // temperature, real, H = 4: blocks [M][nb_t][3][16], Y [M][n_t][2], Sinv [M][4],
+    // assembled rows 2..nc-1 of D^I - gamma dt F^I_m/Pr [M][n_t][9]
+    double *tBlk, *tY, *tSinv, *tBand;
+    // zonal flow, real, H = 4: blocks [nb_t][3][16], Y [n_t][2], Sinv [4], band [n_t][9]
+    double *uBlk, *uY, *uSinv, *uBand;
+    int refine_t;  // also refine the temperature and zonal-flow solves
 };
 
 // Scalar parameters passed by value to every kernel.

@@ -47,9 +47,10 @@ def state_errors(gpu, ref):
 U_FACTOR = 20.0
 
 
-def assert_state_close(gpu, ref, tol, floor=1e-9):
+def assert_state_close(gpu, ref, tol, floor=1e-3):
     """Whole-state relative L2 <= tol; per field <= tol (u_bar: U_FACTOR * tol) for
-    fields carrying more than ``floor`` of the state norm."""
+    fields carrying more than ``floor`` of the state norm (a smaller field's error
+    is bounded, relative to the state, by the whole-state check)."""
     e = state_errors(gpu, ref)
     total = np.sqrt(sum(n * n for n in e["_norms"]))
     assert e["state"] <= tol, e

@@ -225,7 +225,7 @@ def test_tau_solve_is_accurate_against_extended_precision_refinement():
         c[:30] = (rng.standard_normal(30) + 1j * rng.standard_normal(30)) / (1 + np.arange(30)) ** 3
         f = st.ops.A(m) @ c
         f[:4] = 0
-        x = st._solve(st._factor(L), f)
+        x = st._solve_refined(st._factor(L), L, f)
         xr = x.copy()
         Ll = L.astype(np.clongdouble)
         for _ in range(4):
