@@ -106,6 +106,22 @@ int pizza_step(pizza_ctx *ctx, int nsteps);
  * destinations.  Synchronises the context stream. */
 int pizza_explicit_terms(pizza_ctx *ctx, double *e_psi, double *e_theta, double *e_uphi);
 
+/* Diagnostics of the current state (Section 6.2; Eq. cfl).  <f> is the
+ * annulus integral int int f s ds dphi, radial integrals by Clenshaw-Curtis
+ * quadrature on the Gauss-Lobatto points.
+ *   E_K = <u_s^2 + u_phi^2>/2, E_Z = <u_bar^2>/2, enstrophy = <omega^2>,
+ *   Re = sqrt(2 E_K/(pi (s_o^2 - s_i^2))), Ro = Re E,
+ *   Nu = 1 + (d theta_0/ds)(s_o) / (dT_c/ds)(s_o)   (heat flux through the outer
+ *        wall relative to conduction; the paper defines no Nusselt number),
+ *   cfl_s = max |u_s|/ds_k, cfl_phi = max |u_phi|/(s_k dphi) over the physical
+ *        grid (ds_k the local Gauss-Lobatto spacing, dphi = 2 pi/n_phi); the
+ *        Courant condition of Eq. cfl reads dt <= alpha / max(cfl_s, cfl_phi).
+ * Uses the context's work buffers; synchronises the context stream. */
+typedef struct pizza_diag {
+    double E_K, E_Z, enstrophy, Nu, Re, Ro, cfl_s, cfl_phi;
+} pizza_diag;
+int pizza_diagnostics(pizza_ctx *ctx, pizza_diag *out);
+
 /* Per-kernel timing.  pizza_profile_begin starts recording a CUDA event pair on
  * the context stream around every later launch of the kernels selected by mask
  * (bit 0 spectral-to-grid, bit 1 azimuthal products, bit 2 grid-to-spectral,

@@ -20,11 +20,15 @@ STATUS = {0: "PIZZA_OK", -1: "PIZZA_EINVAL", -2: "PIZZA_ENOMEM", -3: "PIZZA_ECUD
 
 # every symbol include/pizza.h declares
 EXPORTS = ("pizza_init", "pizza_set_option", "pizza_set_stream", "pizza_get_sizes", "pizza_set_state",
-           "pizza_get_state", "pizza_step", "pizza_explicit_terms", "pizza_profile_begin",
+           "pizza_get_state", "pizza_step", "pizza_explicit_terms", "pizza_diagnostics", "pizza_profile_begin",
            "pizza_profile_end", "pizza_synchronize",
            "pizza_host_operator", "pizza_explicit_terms_noalloc", "pizza_free", "pizza_last_error")
 
 _lib = None
+
+
+class PizzaDiag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("E_K", "E_Z", "enstrophy", "Nu", "Re", "Ro", "cfl_s", "cfl_phi")]
 
 
 class PizzaError(RuntimeError):
@@ -49,6 +53,7 @@ def load():
     lib.pizza_get_state.argtypes = [vp, dp, dp, dp]
     lib.pizza_step.argtypes = [vp, i]
     lib.pizza_explicit_terms.argtypes = [vp, dp, dp, dp]
+    lib.pizza_diagnostics.argtypes = [vp, ctypes.POINTER(PizzaDiag)]
     lib.pizza_profile_begin.argtypes = [vp, ctypes.c_uint]
     lib.pizza_profile_end.argtypes = [vp, dp, dp]
     lib.pizza_synchronize.argtypes = [vp]
@@ -125,6 +130,12 @@ def pizza_explicit_terms(ctx, e_psi, e_theta, e_uphi):
     return _check(load().pizza_explicit_terms(ctx, _ptr(e_psi), _ptr(e_theta), _ptr(e_uphi)), ctx)
 
 
+def pizza_diagnostics(ctx):
+    d = PizzaDiag()
+    _check(load().pizza_diagnostics(ctx, ctypes.byref(d)), ctx)
+    return {n: getattr(d, n) for n, _ in PizzaDiag._fields_}
+
+
 KERNELS = ("spec_to_grid", "phi_products", "grid_to_spec", "solve")
 
 
@@ -199,6 +210,9 @@ class Solver:
         eu = np.zeros(self.n_c)
         pizza_explicit_terms(self.ctx, ep, et, eu)
         return ep, et, eu
+
+    def diagnostics(self):
+        return pizza_diagnostics(self.ctx)
 
     def close(self):
         if self.ctx is not None:

@@ -87,6 +87,9 @@ struct pizza_ctx {
     };
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> event_pool;
+    // diagnostics: quadrature weights q_k (int f s ds ~ sum q_k f_k), outputs
+    double *diag_q = nullptr, *diag_modes = nullptr, *diag_radii = nullptr;
+    std::vector<double> s_host, ds_host;
 };
 
 namespace {
@@ -538,6 +541,11 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         is[k] = 1.0 / s[k];
     }
     h2[0] = 0.0;  // x_0 = 1 is the outer wall exactly
+    ctx->s_host = s;
+    ctx->ds_host.assign(n_r, 0.0);
+    for (int k = 1; k + 1 < n_r; ++k) ctx->ds_host[k] = 0.5 * (s[k - 1] - s[k + 1]);
+    ctx->ds_host[0] = s[0] - s[1];
+    ctx->ds_host[n_r - 1] = s[n_r - 2] - s[n_r - 1];
     auto& al = ctx->allocs;
     double* ds = dalloc<double>(ctx, n_r, al);
     double* dh = dalloc<double>(ctx, n_r, al);
@@ -760,6 +768,73 @@ int pizza_profile_end(pizza_ctx* ctx, double* total_ms, int* launches) {
         if (total_ms) total_ms[k] = t[k];
         if (launches) launches[k] = n[k];
     }
+    return PIZZA_OK;
+}
+
+int pizza_diagnostics(pizza_ctx* ctx, pizza_diag* out) {
+    if (!ctx || !out) return fail(ctx, PIZZA_EINVAL, "NULL argument");
+    const int n_r = ctx->n_r, M = ctx->M, nc = ctx->nc;
+    if (!ctx->diag_q) {
+        // Clenshaw-Curtis weights on x_k = cos(pi k/K):
+        //   w_k = (c_k/K) [1 - sum_{j=1}^{K/2} b_j cos(2 pi j k/K)/(4 j^2 - 1)],
+        //   c_k = 1 at the ends, 2 inside; b_j = 1 for j = K/2, 2 otherwise;
+        // times ds/dx = a and the s of the area element.
+        const int K = n_r - 1;
+        Geom g = make_geom(ctx->eta);
+        std::vector<double> q(n_r);
+        const long double pi = 3.141592653589793238462643383279502884L;
+        for (int k = 0; k <= K; ++k) {
+            long double acc = 1.0L;
+            for (int j = 1; j <= K / 2; ++j) {
+                const long double b = (2 * j == K) ? 1.0L : 2.0L;
+                acc -= b * cosl(2.0L * pi * j * k / K) / (4.0L * j * j - 1.0L);
+            }
+            const double c = (k == 0 || k == K) ? 1.0 : 2.0;
+            q[k] = (double)(c / K * acc) * g.a * ctx->s_host[k];
+        }
+        ctx->diag_q = dalloc<double>(ctx, n_r, ctx->allocs);
+        ctx->diag_modes = dalloc<double>(ctx, 2 * (size_t)M, ctx->allocs);
+        ctx->diag_radii = dalloc<double>(ctx, 2 * (size_t)n_r, ctx->allocs);
+        if (!ctx->diag_q || !ctx->diag_modes || !ctx->diag_radii)
+            return fail(ctx, PIZZA_ENOMEM, "allocation of diagnostics buffers failed");
+        CK(cudaMemcpy(ctx->diag_q, q.data(), n_r * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    VecSet y = ctx->vec[ctx->ys[0]];
+    CK(launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
+    CK(launch_diagnostics(ctx->P, ctx->G1, ctx->diag_q, ctx->diag_modes, ctx->diag_radii, ctx->stream));
+    std::vector<double> ms(2 * (size_t)M), rm(2 * (size_t)n_r);
+    std::vector<double2> th0(nc);
+    CK(cudaMemcpyAsync(ms.data(), ctx->diag_modes, ms.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(rm.data(), ctx->diag_radii, rm.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(th0.data(), y.th, nc * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const double pi = 3.14159265358979323846;
+    Geom g = make_geom(ctx->eta);
+    double ez = pi * ms[0], ek = ez, z = 2 * pi * ms[1];
+    for (int m = 1; m < M; ++m) {
+        ek += 2 * pi * ms[2 * m];
+        z += 4 * pi * ms[2 * m + 1];
+    }
+    double cs = 0.0, cp = 0.0;
+    const double dphi = 2 * pi / ctx->n_phi;
+    for (int k = 0; k < n_r; ++k) {
+        cs = std::max(cs, rm[2 * k] / ctx->ds_host[k]);
+        cp = std::max(cp, rm[2 * k + 1] / (ctx->s_host[k] * dphi));
+    }
+    // d theta_0/ds at s_o: (1/a) sum_n n^2 c_n, c_n = C w_n theta_hat_0n
+    const double C = std::sqrt(2.0 / (n_r - 1));
+    double dth = 0.0;
+    for (int n = 0; n < nc; ++n) dth += (double)n * n * C * ((n == 0) ? 0.5 : 1.0) * th0[n].x;
+    dth /= g.a;
+    const double dtc = std::log(ctx->eta) != 0.0 ? tc_coefficient(ctx->eta) / g.s_o : 0.0;
+    out->E_K = ek;
+    out->E_Z = ez;
+    out->enstrophy = z;
+    out->Nu = 1.0 + dth / dtc;
+    out->Re = std::sqrt(2.0 * ek / (pi * (g.s_o * g.s_o - g.s_i * g.s_i)));
+    out->Ro = out->Re * ctx->E;
+    out->cfl_s = cs;
+    out->cfl_phi = cp;
     return PIZZA_OK;
 }
 

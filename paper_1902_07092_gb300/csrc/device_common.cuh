@@ -19,14 +19,25 @@ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -
 // multiply by i*t (t real)
 __device__ __forceinline__ double2 cmul_i(double2 a, double t) { return make_double2(-a.y * t, a.x * t); }
 
+// a + w*b and 2a - (a + w*b) = a - w*b with fused multiply-adds
+__device__ __forceinline__ double2 cfma(double2 w, double2 b, double2 a) {
+    return make_double2(fma(w.x, b.x, fma(-w.y, b.y, a.x)), fma(w.x, b.y, fma(w.y, b.x, a.y)));
+}
+__device__ __forceinline__ double2 creflect(double2 a, double2 s) {  // 2a - s
+    return make_double2(fma(2.0, a.x, -s.x), fma(2.0, a.y, -s.y));
+}
+
 // One Stockham pass of radix R over a batch of nb transforms of length L.
 // SIGN = -1: forward  sum_j x_j exp(-2 pi i jk/L);  SIGN = +1: backward (unscaled).
+// In the first pass (Ns = 1) every twiddle factor is 1 and the multiplies are
+// skipped; otherwise the twiddle products are fused into the butterfly adds.
 template <int SIGN, int R>
 __device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, double2* __restrict__ dst, int L,
                                               int Ns, const double2* __restrict__ tw, int nb, int tid,
                                               int nth) {
     const int nbf = L / R;
     const int twmul = L / (Ns * R);
+    const bool first = (Ns == 1);
     for (int t = tid; t < nb * nbf; t += nth) {
         const int bt = t / nbf;
         const int j = t - bt * nbf;
@@ -36,19 +47,31 @@ __device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, d
         double2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = s[j + r * nbf];
+        double2 w[R];
+        w[0] = make_double2(1.0, 0.0);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            double2 w = __ldg(&tw[r * k * twmul]);
-            if (SIGN > 0) w.y = -w.y;
-            v[r] = cmul(v[r], w);
+            w[r] = first ? make_double2(1.0, 0.0) : __ldg(&tw[r * k * twmul]);
+            if (SIGN > 0) w[r].y = -w[r].y;
         }
         if (R == 2) {
-            double2 a = v[0], b = v[1];
-            v[0] = cadd(a, b);
-            v[1] = csub(a, b);
+            double2 y0 = first ? cadd(v[0], v[1]) : cfma(w[1], v[1], v[0]);
+            v[1] = first ? csub(v[0], v[1]) : creflect(v[0], y0);
+            v[0] = y0;
         } else if (R == 4) {
-            double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-            double2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+            double2 t0, t1, t2, t3;
+            if (first) {
+                t0 = cadd(v[0], v[2]);
+                t1 = csub(v[0], v[2]);
+                t2 = cadd(v[1], v[3]);
+                t3 = csub(v[1], v[3]);
+            } else {
+                t0 = cfma(w[2], v[2], v[0]);          // v0 + w2 v2
+                t1 = creflect(v[0], t0);              // v0 - w2 v2
+                const double2 b1 = cmul(w[1], v[1]);
+                t2 = cfma(w[3], v[3], b1);            // w1 v1 + w3 v3
+                t3 = creflect(b1, t2);                // w1 v1 - w3 v3
+            }
             // forward: -i*t3 ; backward: +i*t3
             double2 rt = (SIGN < 0) ? make_double2(t3.y, -t3.x) : make_double2(-t3.y, t3.x);
             v[0] = cadd(t0, t2);
@@ -57,12 +80,21 @@ __device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, d
             v[3] = csub(t1, rt);
         } else if (R == 3) {
             const double h3 = 0.86602540378443864676;  // sqrt(3)/2
-            double2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
-            double2 m1 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
-            double2 m2 = (SIGN < 0) ? make_double2(h3 * t2.y, -h3 * t2.x) : make_double2(-h3 * t2.y, h3 * t2.x);
+            double2 t1, t2;
+            if (first) {
+                t1 = cadd(v[1], v[2]);
+                t2 = csub(v[1], v[2]);
+            } else {
+                const double2 b1 = cmul(w[1], v[1]);
+                t1 = cfma(w[2], v[2], b1);            // w1 v1 + w2 v2
+                t2 = creflect(b1, t1);                // w1 v1 - w2 v2
+            }
+            const double2 m1 = make_double2(fma(-0.5, t1.x, v[0].x), fma(-0.5, t1.y, v[0].y));
+            // forward: -i*h3*t2 ; backward: +i*h3*t2
+            const double2 rt = (SIGN < 0) ? make_double2(t2.y, -t2.x) : make_double2(-t2.y, t2.x);
             v[0] = cadd(v[0], t1);
-            v[1] = cadd(m1, m2);
-            v[2] = csub(m1, m2);
+            v[1] = make_double2(fma(h3, rt.x, m1.x), fma(h3, rt.y, m1.y));
+            v[2] = make_double2(fma(-h3, rt.x, m1.x), fma(-h3, rt.y, m1.y));
         }
         const int idx = (j / Ns) * Ns * R + k;
 #pragma unroll

@@ -364,7 +364,110 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// Diagnostics from G1 (radial-grid Fourier coefficients written by K1):
+// per mode, sums over the Gauss-Lobatto points with quadrature weights q_k
+// (int f s ds ~ sum_k q_k f_k) of |u_s|^2 + |u_phi|^2 and |omega|^2;
+// u_s = (h^2/s) v.  out[m*2 + 0], out[m*2 + 1].
+// ---------------------------------------------------------------------------
+__global__ void k_diag_modes(StepParams P, const double2* __restrict__ G1, const double* __restrict__ q,
+                             double* __restrict__ out) {
+    const int m = blockIdx.x, M = P.M;
+    double e = 0.0, z = 0.0;
+    for (int k = threadIdx.x; k < P.n_r; k += blockDim.x) {
+        const double f = P.h2[k] * P.inv_s[k];
+        const double2 v = G1[g_index(k, 0, m, M)], up = G1[g_index(k, 1, m, M)], w = G1[g_index(k, 2, m, M)];
+        const double us2 = f * f * (v.x * v.x + v.y * v.y);
+        e += q[k] * (us2 + up.x * up.x + up.y * up.y);
+        z += q[k] * (w.x * w.x + w.y * w.y);
+    }
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = e;
+        red[1][threadIdx.x >> 5] = z;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += red[0][i];
+            b += red[1][i];
+        }
+        out[2 * m] = a;
+        out[2 * m + 1] = b;
+    }
+}
+
+// per radius: max |u_s| and max |u_phi| over the azimuthal grid (Eq. fft of
+// g = u_s + i u_phi); out[k*2 + 0], out[k*2 + 1].
+__global__ void __launch_bounds__(512) k_phi_cfl(StepParams P, const double2* __restrict__ G1,
+                                                 double* __restrict__ out) {
+    extern __shared__ double2 sm[];
+    const int k = blockIdx.x;
+    const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
+    double2* X = sm;
+    double2* Y = sm + Pn;
+    const double f = P.h2[k] * P.inv_s[k];
+    const double2* src = G1 + g_index(k, 0, 0, M);
+    for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
+        double2 z = make_double2(0.0, 0.0);
+        if (j == 0) {
+            z = make_double2(f * src[0].x, src[M].x);
+        } else if (j <= n_m) {
+            const double2 a = cscale(src[j], f), b = src[M + j];
+            z = make_double2(a.x - b.y, a.y + b.x);
+        } else if (j >= Pn - n_m) {
+            const int mm = Pn - j;
+            const double2 a = cscale(src[mm], f), b = src[M + mm];
+            z = make_double2(a.x + b.y, -a.y + b.x);
+        }
+        X[j] = z;
+    }
+    double2* R = fft_batched<+1>(X, Y, P.plan_p, 1);
+    double ms = 0.0, mp = 0.0;
+    for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
+        ms = fmax(ms, fabs(R[j].x));
+        mp = fmax(mp, fabs(R[j].y));
+    }
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        ms = fmax(ms, __shfl_xor_sync(0xffffffffu, ms, o));
+        mp = fmax(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = ms;
+        red[1][threadIdx.x >> 5] = mp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a = fmax(a, red[0][i]);
+            b = fmax(b, red[1][i]);
+        }
+        out[2 * k] = a;
+        out[2 * k + 1] = b;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_diagnostics(const StepParams& P, const double2* G1, const double* q, double* mode_sums,
+                               double* radius_max, cudaStream_t st) {
+    k_diag_modes<<<P.M, 128, 0, st>>>(P, G1, q, mode_sums);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const size_t sm = smem_phi_products(P);
+    const int nth = P.n_phi > 256 * MAXPER ? 512 : 256;
+    err = cudaFuncSetAttribute(k_phi_cfl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    k_phi_cfl<<<P.n_r, nth, sm, st>>>(P, G1, radius_max);
+    return cudaGetLastError();
+}
 
 size_t smem_spec_to_grid(const StepParams& P) {
     const int L = 2 * P.K;

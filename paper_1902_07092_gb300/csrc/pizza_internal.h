@@ -82,6 +82,8 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st);
 cudaError_t launch_apply(const StepParams& P, VecSet y, VecSet mass_out, VecSet imp_out, bool want_mass,
                          bool want_imp, cudaStream_t st);
+cudaError_t launch_diagnostics(const StepParams& P, const double2* G1, const double* q, double* mode_sums,
+                               double* radius_max, cudaStream_t st);
 
 // message returned by pizza_last_error(NULL)
 void set_global_error(const char* msg);

@@ -186,3 +186,17 @@ def test_large_workload_sampled():
         # the bound is 5e-11 = 2e5 * 2.2e-16 rounded up.
         assert rel_l2(ps[m], ref_p) <= 5e-11, m
     gpu.close()
+
+
+@pytest.mark.parametrize("n_r,n_phi", [(33, 96), (257, 768)])
+def test_diagnostics_match_oracle(n_r, n_phi):
+    from oracle.diagnostics import diagnostics
+    gpu, ora = make_pair(n_r, n_phi, 1e-3, 2.0, "CNAB2", 1e-4)
+    psi, th, u = random_state(n_r, n_phi, 1.0, 21, psi_amp=1e-2, u_amp=1e-1)
+    th[0] = th[0].real
+    gpu.set_state(th, psi, u)
+    d = gpu.diagnostics()
+    r = diagnostics(ora.g, psi, th, u)
+    for key in ("E_K", "E_Z", "enstrophy", "Nu", "Re", "Ro", "cfl_s", "cfl_phi"):
+        assert abs(d[key] - r[key]) <= 1e-12 * max(abs(r[key]), 1e-300), (key, d[key], r[key])
+    gpu.close()
