@@ -31,13 +31,13 @@ __device__ __forceinline__ double2 creflect(double2 a, double2 s) {  // 2a - s
 // SIGN = -1: forward  sum_j x_j exp(-2 pi i jk/L);  SIGN = +1: backward (unscaled).
 // In the first pass (Ns = 1) every twiddle factor is 1 and the multiplies are
 // skipped; otherwise the twiddle products are fused into the butterfly adds.
-template <int SIGN, int R>
+template <int SIGN, int R, bool FIRST>
 __device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, double2* __restrict__ dst, int L,
                                               int Ns, const double2* __restrict__ tw, int nb, int tid,
                                               int nth) {
     const int nbf = L / R;
     const int twmul = L / (Ns * R);
-    const bool first = (Ns == 1);
+    constexpr bool first = FIRST;
     for (int t = tid; t < nb * nbf; t += nth) {
         const int bt = t / nbf;
         const int j = t - bt * nbf;
@@ -114,12 +114,21 @@ __device__ static double2* fft_batched(double2* buf0, double2* buf1, const FftPl
     __syncthreads();
     for (int p = 0; p < pl.npass; ++p) {
         const int R = pl.radix[p];
-        if (R == 4)
-            stockham_pass<SIGN, 4>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
-        else if (R == 2)
-            stockham_pass<SIGN, 2>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
-        else
-            stockham_pass<SIGN, 3>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+        if (p == 0) {  // Ns == 1: unit twiddles
+            if (R == 4)
+                stockham_pass<SIGN, 4, true>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+            else if (R == 2)
+                stockham_pass<SIGN, 2, true>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+            else
+                stockham_pass<SIGN, 3, true>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+        } else {
+            if (R == 4)
+                stockham_pass<SIGN, 4, false>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+            else if (R == 2)
+                stockham_pass<SIGN, 2, false>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+            else
+                stockham_pass<SIGN, 3, false>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+        }
         __syncthreads();
         double2* t = a;
         a = b;
@@ -139,32 +148,48 @@ __device__ __forceinline__ void even_extend_store(double2* z, int K, int j, doub
 
 // Chebyshev derivative in x of plain coefficients c[0..n-1] -> d[0..n-1]
 // (d[n-1] = 0):  d_j = (2/c_j) sum_{k>j, k+j odd} k c_k  (c_0 = 2, c_j = 1),
-// evaluated as a suffix scan over each index parity.  ``tmp`` is scratch of n
-// entries.  Must be called by the whole CTA.
-__device__ __noinline__ static void cheb_derivative_scan(const double2* c, double2* d, double2* tmp, int n, double scale) {
-    const int tid = threadIdx.x, nth = blockDim.x;
-    // d_j (before the j=0 halving) = sum_{i>=0} 2(j+1+2i) c_{j+1+2i}: suffix sum with stride 2
-    for (int j = tid; j < n; j += nth) {
-        int k = j + 1;
-        d[j] = (k < n) ? cscale(c[k], 2.0 * k) : make_double2(0.0, 0.0);
+// i.e. suffix sums of t_k = 2 k c_k over each index parity.  Work-efficient:
+// warp q (q = 0, 1) owns the indices k = 2i + q; each lane sums a contiguous
+// chunk sequentially, a shuffle scan adds the totals of the chunks above it.
+// ``tmp`` is scratch of n entries.  Must be called by the whole CTA (>= 64 threads).
+__device__ __noinline__ static void cheb_derivative_scan(const double2* c, double2* d, double2* tmp, int n,
+                                                         double scale) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 2) {
+        const int q = warp;
+        const int len = (n - q + 1) / 2;  // number of k = 2i + q below n
+        const int per = (len + 31) / 32;
+        const int i0 = lane * per, i1 = min(i0 + per, len);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int i = i1 - 1; i >= i0; --i) {
+            const int k = 2 * i + q;
+            if (k > 0) {
+                const double f = (double)(2 * k);
+                acc = make_double2(fma(f, c[k].x, acc.x), fma(f, c[k].y, acc.y));
+            }
+            tmp[k] = acc;
+        }
+        // inclusive suffix scan of the chunk totals over the lanes
+        double2 sfx = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double x = __shfl_down_sync(0xffffffffu, sfx.x, o);
+            const double y = __shfl_down_sync(0xffffffffu, sfx.y, o);
+            if (lane + o < 32) {
+                sfx.x += x;
+                sfx.y += y;
+            }
+        }
+        const double2 off = csub(sfx, acc);  // totals of the chunks above this one
+        for (int i = i0; i < i1; ++i) {
+            const int k = 2 * i + q;
+            tmp[k] = cadd(tmp[k], off);
+        }
     }
     __syncthreads();
-    double2* src = d;
-    double2* dst = tmp;
-    for (int off = 2; off < n; off *= 2) {
-        for (int j = tid; j < n; j += nth) {
-            double2 v = src[j];
-            if (j + off < n) v = cadd(v, src[j + off]);
-            dst[j] = v;
-        }
-        __syncthreads();
-        double2* t = src;
-        src = dst;
-        dst = t;
-    }
-    for (int j = tid; j < n; j += nth) {
-        double f = (j == 0) ? 0.5 * scale : scale;
-        d[j] = cscale(src[j], f);  // src may alias d: each j touched by one thread
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double f = (j == 0) ? 0.5 * scale : scale;
+        d[j] = (j + 1 < n) ? cscale(tmp[j + 1], f) : make_double2(0.0, 0.0);
     }
     __syncthreads();
 }
