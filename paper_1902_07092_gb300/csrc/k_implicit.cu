@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_apply(StepParams P, VecSet y, Ve
     for (int k = threadIdx.x; k < nc; k += blockDim.x) apply_row(P, m, k, xp, xt, xu, mass_out, imp_out, want_mass, want_imp);
 }
 
-int modes_per_cta(const StepParams& P) { return P.nc <= 900 ? 2 : 1; }
+int modes_per_cta(const StepParams& P) { return 1; }
 
 size_t smem_solve_mb(const StepParams& P, int MB) { return sizeof(double) * solve_smem_doubles(P.nc, MB); }
 
