@@ -48,7 +48,65 @@ def bordered_solve(Mat, f, p):
     return np.concatenate([psi1, psi2])
 
 
-class IntegrationStepper:
+class ImexScheme:
+    """Scheme logic of Eqs. multistep1 and dirks on tuples of per-field arrays;
+    subclasses provide mass(y), imp(y), explicit(y) and solve(gamma, rhs)."""
+
+    @staticmethod
+    def _axpy(acc, c, v):
+        return tuple(a + c * b for a, b in zip(acc, v))
+
+    def step(self):
+        if self.scheme in schemes.MULTISTEP:
+            self._step_multistep()
+        else:
+            self._step_dirk()
+        self.n_done += 1
+        return self.y
+
+    def _step_multistep(self):
+        a, b0, bI, bE = schemes.multistep_coeffs(self.scheme, self.n_done)
+        dt = self.dt
+        e_n = self.explicit(self.y)
+        ys = [self.y] + self.hist_y
+        es = [e_n] + self.hist_e
+        zero = tuple(np.zeros_like(v) for v in self.mass(self.y))
+        rhs = zero
+        for j, aj in enumerate(a):
+            rhs = self._axpy(rhs, aj, self.mass(ys[j]))
+        for j, bj in enumerate(bI):
+            if bj != 0.0:
+                rhs = self._axpy(rhs, dt * bj, self.imp(ys[j]))
+        for j, bj in enumerate(bE):
+            rhs = self._axpy(rhs, dt * bj, es[j])
+        y_new = self.solve(b0, rhs)
+        keep = 2
+        self.hist_y = ys[:keep]
+        self.hist_e = es[:keep]
+        self.y = y_new
+
+    def _step_dirk(self):
+        aI, aE = schemes.dirk_tableau(self.scheme)
+        nu = aI.shape[0] - 1
+        dt = self.dt
+        ys = [self.y]
+        es, imps = [], {}
+        rhs0 = self.mass(self.y)
+        for i in range(1, nu + 1):
+            es.append(self.explicit(ys[i - 1]))
+            rhs = rhs0
+            for j in range(i):
+                if aE[i, j] != 0.0:
+                    rhs = self._axpy(rhs, dt * aE[i, j], es[j])
+                if aI[i, j] != 0.0:
+                    if j not in imps:
+                        imps[j] = self.imp(ys[j])
+                    rhs = self._axpy(rhs, dt * aI[i, j], imps[j])
+            ys.append(self.solve(aI[i, i], rhs))
+        self.y = ys[nu]
+
+
+class IntegrationStepper(ImexScheme):
     def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt):
         if scheme not in schemes.SCHEME_ID:
             raise ValueError(scheme)
@@ -127,57 +185,3 @@ class IntegrationStepper:
         th = np.stack([self._solve_refined(*lt[m], rt[m]) for m in range(self.g.M)])
         u = self._solve_refined(*lu_, ru)
         return psi, th, u
-
-    @staticmethod
-    def _axpy(acc, c, v):
-        return tuple(a + c * b for a, b in zip(acc, v))
-
-    # -- one step ------------------------------------------------------------
-    def step(self):
-        if self.scheme in schemes.MULTISTEP:
-            self._step_multistep()
-        else:
-            self._step_dirk()
-        self.n_done += 1
-        return self.y
-
-    def _step_multistep(self):
-        a, b0, bI, bE = schemes.multistep_coeffs(self.scheme, self.n_done)
-        dt = self.dt
-        e_n = self.explicit(self.y)
-        ys = [self.y] + self.hist_y
-        es = [e_n] + self.hist_e
-        zero = tuple(np.zeros_like(v) for v in self.y)
-        rhs = zero
-        for j, aj in enumerate(a):
-            rhs = self._axpy(rhs, aj, self.mass(ys[j]))
-        for j, bj in enumerate(bI):
-            if bj != 0.0:
-                rhs = self._axpy(rhs, dt * bj, self.imp(ys[j]))
-        for j, bj in enumerate(bE):
-            rhs = self._axpy(rhs, dt * bj, es[j])
-        y_new = self.solve(b0, rhs)
-        keep = 2
-        self.hist_y = ys[:keep]
-        self.hist_e = es[:keep]
-        self.y = y_new
-
-    def _step_dirk(self):
-        aI, aE = schemes.dirk_tableau(self.scheme)
-        nu = aI.shape[0] - 1
-        dt = self.dt
-        ys = [self.y]
-        es, imps = [], {}
-        rhs0 = self.mass(self.y)
-        for i in range(1, nu + 1):
-            es.append(self.explicit(ys[i - 1]))
-            rhs = rhs0
-            for j in range(i):
-                if aE[i, j] != 0.0:
-                    rhs = self._axpy(rhs, dt * aE[i, j], es[j])
-                if aI[i, j] != 0.0:
-                    if j not in imps:
-                        imps[j] = self.imp(ys[j])
-                    rhs = self._axpy(rhs, dt * aI[i, j], imps[j])
-            ys.append(self.solve(aI[i, i], rhs))
-        self.y = ys[nu]
