@@ -45,7 +45,12 @@ def pencil(E, Pr, Ra, eta, m, n_c):
 
 
 def leading_eigenvalue(E, Pr, Ra, eta, m, n_c, guess=None):
-    L, M = pencil(E, Pr, Ra, eta, m, n_c)
+    return leading_of_pencil(*pencil(E, Pr, Ra, eta, m, n_c), guess)
+
+
+def leading_of_pencil(L, M, guess=None):
+    """Eigenvalue of L x = lambda M x of largest real part among the finite ones
+    (QZ estimate unless ``guess`` is given), refined by shift-and-invert."""
     if guess is None:
         w = sl.eig(L, M, right=False)
         w = w[np.isfinite(w) & (np.abs(w) < 1e8)]
