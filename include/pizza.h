@@ -23,6 +23,17 @@
  * N_c Chebyshev coefficients per mode, N_c = floor(2 (n_r-1)/3) for the
  * integration method (Eq. psi_int and the dealiasing rule below Eq. temp_int).
  *
+ * Chebyshev-collocation formulation (Section 3.1; option "radial" = 0): the
+ * unknowns are the vorticity omega and the streamfunction psi itself
+ * (u_s = (1/s) dpsi/dphi, u_phi = u_bar - dpsi/ds - beta psi, beta = -s/h^2,
+ * Eq. vel_def), theta and u_bar, with N_c = n_r coefficients; the equations are
+ * imposed at the interior Gauss-Lobatto points (Eqs. psiomcoll, uphicoll,
+ * tempcoll) and the boundary conditions at the walls (Eqs. bcs_coll_dirichlet,
+ * bcs_coll_neumann).  The per-mode systems are dense; their inverses restricted
+ * to the interior right-hand-side rows are built on the host (LU with partial
+ * pivoting and one refinement step, O(n_r^3) per mode and implicit weight) and
+ * kept on the device (2 n_r (n_r-2) complex + n_r (n_r-2) real per mode).
+ *
  * Spectral coefficient convention (Eq. cheb): f_m(s_k) = C sum''_{n<N_c}
  * f_hat_{mn} T_n(x_k), C = sqrt(2/(n_r-1)), the double prime halving the n = 0
  * term (and the n = n_r-1 term when present).  Complex arrays are interleaved
@@ -67,9 +78,16 @@ enum pizza_status {
 int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
                double Pr, double radius_ratio, int scheme);
 
-/* Set a numeric option.  Keys: "dt" (time step > 0; invalidates the factored
- * implicit operators, which are rebuilt on the next step).  Returns
- * PIZZA_EINVAL for an unknown key or an invalid value. */
+/* Set a numeric option.  Keys:
+ *   "dt"     time step > 0; invalidates the factored implicit operators, which
+ *            are rebuilt on the next step;
+ *   "radial" 1 = Chebyshev integration with tau rows (Section 3.2, the default),
+ *            0 = Chebyshev collocation (Section 3.1; n_r <= PIZZA_COLL_MAX_NR,
+ *            else PIZZA_EUNSUPPORTED).  Changing it discards the factored
+ *            operators and resets the state to zero and N_c to the new
+ *            formulation's value; any other value returns PIZZA_EUNSUPPORTED.
+ * Returns PIZZA_EINVAL for an unknown key or an invalid value. */
+#define PIZZA_COLL_MAX_NR 513
 int pizza_set_option(pizza_ctx *ctx, const char *key, double value);
 
 /* Use the given cudaStream_t (passed as void*) for all later device work of
@@ -83,13 +101,17 @@ int pizza_get_sizes(const pizza_ctx *ctx, int *n_r, int *n_phi, int *n_m, int *n
  * real [nc_in] (the m = 0 zonal flow).  nc_in <= N_c; missing coefficients are
  * zero; psi_hat of m = 0 is ignored (Psi_0 = 0).  Pointers may be host or
  * device memory (detected); the data are copied and not retained.  Resets the
- * time-scheme history (the next step is a start-up step). */
+ * time-scheme history (the next step is a start-up step).
+ * Collocation: psi_hat holds the coefficients of psi (not Psi); the vorticity
+ * is set to omega = -L_beta psi (Eq. psi) at every grid point, with its limit
+ * -(5/4) d^2psi/ds^2 at s_o. */
 int pizza_set_state(pizza_ctx *ctx, const double *theta_hat, const double *psi_hat,
                     const double *uphi0_hat, int nc_in);
 
 /* Copy the current state out (layouts as in pizza_set_state with nc_in = N_c).
  * Host or device destination pointers; any may be NULL to skip that field.
- * Synchronises the context stream. */
+ * Synchronises the context stream.  (Collocation: the vorticity, whose wall
+ * values are unknowns of their own, is reported by pizza_get_grid.) */
 int pizza_get_state(pizza_ctx *ctx, double *theta_hat, double *psi_hat, double *uphi0_hat);
 
 /* Advance nsteps time steps (Sections 3.2 and 4): per explicit evaluation the
@@ -103,7 +125,10 @@ int pizza_step(pizza_ctx *ctx, int nsteps);
  * bracketed terms of Eqs. psi_int and temp_int after C^I and D^I, and of
  * Eq. uphi_int after D^I): e_psi, e_theta complex [N_m+1][N_c], e_uphi real
  * [N_c]; rows n < 4 (psi) and n < 2 (theta, u) are zero.  Host or device
- * destinations.  Synchronises the context stream. */
+ * destinations.  Synchronises the context stream.
+ * Collocation: the explicit parts of Eqs. psiomcoll, tempcoll and uphicoll at
+ * the grid points instead, [N_m+1][n_r] (the vorticity rows into e_psi), with
+ * the boundary rows k = 0 and n_r-1 zero. */
 int pizza_explicit_terms(pizza_ctx *ctx, double *e_psi, double *e_theta, double *e_uphi);
 
 /* Diagnostics of the current state (Section 6.2; Eq. cfl).  <f> is the
@@ -121,6 +146,13 @@ typedef struct pizza_diag {
     double E_K, E_Z, enstrophy, Nu, Re, Ro, cfl_s, cfl_phi;
 } pizza_diag;
 int pizza_diagnostics(pizza_ctx *ctx, pizza_diag *out);
+
+/* Physical-grid values of the current state (Eq. fft): u_s, u_phi, omega and
+ * theta at (s_k, phi_j = 2 pi j/n_phi), each real [n_r][n_phi] (row-major).
+ * Host or device destinations; any may be NULL.  Uses the context's work
+ * buffers (allocating a 32 n_r n_phi byte staging buffer on the first call);
+ * synchronises the context stream. */
+int pizza_get_grid(pizza_ctx *ctx, double *us, double *uphi, double *omega, double *theta);
 
 /* Per-kernel timing.  pizza_profile_begin starts recording a CUDA event pair on
  * the context stream around every later launch of the kernels selected by mask

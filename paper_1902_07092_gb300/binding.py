@@ -20,8 +20,8 @@ STATUS = {0: "PIZZA_OK", -1: "PIZZA_EINVAL", -2: "PIZZA_ENOMEM", -3: "PIZZA_ECUD
 
 # every symbol include/pizza.h declares
 EXPORTS = ("pizza_init", "pizza_set_option", "pizza_set_stream", "pizza_get_sizes", "pizza_set_state",
-           "pizza_get_state", "pizza_step", "pizza_explicit_terms", "pizza_diagnostics", "pizza_profile_begin",
-           "pizza_profile_end", "pizza_synchronize",
+           "pizza_get_state", "pizza_step", "pizza_explicit_terms", "pizza_diagnostics", "pizza_get_grid",
+           "pizza_profile_begin", "pizza_profile_end", "pizza_synchronize",
            "pizza_host_operator", "pizza_explicit_terms_noalloc", "pizza_free", "pizza_last_error")
 
 _lib = None
@@ -54,6 +54,7 @@ def load():
     lib.pizza_step.argtypes = [vp, i]
     lib.pizza_explicit_terms.argtypes = [vp, dp, dp, dp]
     lib.pizza_diagnostics.argtypes = [vp, ctypes.POINTER(PizzaDiag)]
+    lib.pizza_get_grid.argtypes = [vp, dp, dp, dp, dp]
     lib.pizza_profile_begin.argtypes = [vp, ctypes.c_uint]
     lib.pizza_profile_end.argtypes = [vp, dp, dp]
     lib.pizza_synchronize.argtypes = [vp]
@@ -136,6 +137,10 @@ def pizza_diagnostics(ctx):
     return {n: getattr(d, n) for n, _ in PizzaDiag._fields_}
 
 
+def pizza_get_grid(ctx, us, uphi, omega, theta):
+    return _check(load().pizza_get_grid(ctx, _ptr(us), _ptr(uphi), _ptr(omega), _ptr(theta)), ctx)
+
+
 KERNELS = ("spec_to_grid", "phi_products", "grid_to_spec", "solve")
 
 
@@ -178,10 +183,16 @@ def pizza_last_error(ctx=None):
 
 class Solver:
     """Convenience owner of one context with numpy host arrays in the C layouts
-    (complex128 [N_m+1][N_c] for theta and Psi, float64 [N_c] for u_bar)."""
+    (complex128 [N_m+1][N_c] for theta and Psi, float64 [N_c] for u_bar).
+    ``radial`` selects the formulation: "integration" (Section 3.2, default) or
+    "collocation" (Section 3.1; psi instead of Psi, N_c = n_r)."""
 
-    def __init__(self, n_r, n_phi, E, Ra, Pr, radius_ratio, scheme, dt=None):
+    def __init__(self, n_r, n_phi, E, Ra, Pr, radius_ratio, scheme, dt=None, radial="integration"):
         self.ctx = pizza_init(n_r, n_phi, E, Ra, Pr, radius_ratio, scheme)
+        if radial not in ("integration", "collocation"):
+            raise ValueError(radial)
+        if radial == "collocation":
+            pizza_set_option(self.ctx, "radial", 0)
         self.n_r, self.n_phi, self.n_m, self.n_c = pizza_get_sizes(self.ctx)
         self.M = self.n_m + 1
         if dt is not None:
@@ -213,6 +224,12 @@ class Solver:
 
     def diagnostics(self):
         return pizza_diagnostics(self.ctx)
+
+    def get_grid(self):
+        """(u_s, u_phi, omega, theta) on the physical grid, each [n_r][n_phi]."""
+        out = [np.zeros((self.n_r, self.n_phi)) for _ in range(4)]
+        pizza_get_grid(self.ctx, *out)
+        return tuple(out)
 
     def close(self):
         if self.ctx is not None:

@@ -7,7 +7,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pizza.h"
@@ -74,8 +76,8 @@ struct pizza_ctx {
     // scheme bookkeeping
     int n_done = 0;
     bool aux_valid = false;  // mass/imp of the current state computed
-    // multistep rings (indices into vec)
-    int ys[2]{}, es[4]{}, ms[3]{}, is[3]{};
+    // multistep rings (indices into vec); the collocation path uses four state slots
+    int ys[4]{}, es[4]{}, ms[3]{}, is[3]{};
     // DIRK slots
     int stage_y[4]{}, stage_e[4]{}, stage_imp[4]{}, mass_n = 0;
     std::string err = "no error";
@@ -90,6 +92,11 @@ struct pizza_ctx {
     // diagnostics: quadrature weights q_k (int f s ds ~ sum q_k f_k), outputs
     double *diag_q = nullptr, *diag_modes = nullptr, *diag_radii = nullptr;
     std::vector<double> s_host, ds_host;
+    // Chebyshev-collocation formulation (option "radial" = 0)
+    bool coll = false;
+    std::vector<void*> vec_allocs;     // state and work vectors (re-made when the formulation changes)
+    std::vector<double> coll_d1_row0;  // d/ds at s_o on grid values
+    double* grid_out = nullptr;        // pizza_get_grid staging, 4 x n_r x n_phi
 };
 
 namespace {
@@ -291,11 +298,28 @@ HostOps host_ops_of(pizza_ctx* ctx) {
     return H;
 }
 
+int build_coll_factors(pizza_ctx* ctx, const CollGrid& cg, double gamma, DevFactors& F, std::vector<void*>& al);
+
 int ensure_factors(pizza_ctx* ctx) {
     if (!ctx->factors.empty()) return PIZZA_OK;
     if (!ctx->dt_set) return fail(ctx, PIZZA_ESTATE, "dt is not set (pizza_set_option(ctx, \"dt\", v))");
-    HostOps H = host_ops_of(ctx);
     ctx->gammas = scheme_gammas(ctx->scheme);
+    if (ctx->coll) {
+        CollGrid cg = coll_grid(ctx->n_r, make_geom(ctx->eta));
+        for (double g : ctx->gammas) {
+            DevFactors F{};
+            std::vector<void*> al;
+            int rc = build_coll_factors(ctx, cg, g, F, al);
+            ctx->factor_allocs.push_back(al);
+            if (rc != PIZZA_OK) {
+                free_factors(ctx);
+                return rc;
+            }
+            ctx->factors.push_back(F);
+        }
+        return PIZZA_OK;
+    }
+    HostOps H = host_ops_of(ctx);
     for (double g : ctx->gammas) {
         DevFactors F{};
         std::vector<void*> al;
@@ -317,6 +341,20 @@ const DevFactors* factors_for(pizza_ctx* ctx, double gamma) {
 }
 
 void reset_slots(pizza_ctx* ctx) {
+    if (ctx->coll) {
+        // vec indices: 0..3 state ring (the mass term of a grid state is the state
+        // itself); 4..7 explicit ring; 8..10 imp ring; DIRK stages 11..13; 15 scratch
+        for (int i = 0; i < 4; ++i) ctx->ys[i] = i;
+        for (int i = 0; i < 4; ++i) ctx->es[i] = 4 + i;
+        for (int i = 0; i < 3; ++i) ctx->is[i] = 8 + i;
+        for (int i = 0; i < 4; ++i) ctx->stage_e[i] = 4 + i;
+        ctx->stage_y[1] = 11; ctx->stage_y[2] = 12; ctx->stage_y[3] = 13;
+        ctx->stage_imp[1] = 8; ctx->stage_imp[2] = 9; ctx->stage_imp[3] = 10;
+        ctx->mass_n = 0;
+        ctx->n_done = 0;
+        ctx->aux_valid = false;
+        return;
+    }
     // vec indices: 0,1 state ring; 2..5 explicit ring; 6..8 mass ring; 9..11 imp ring
     ctx->ys[0] = 0; ctx->ys[1] = 1;
     for (int i = 0; i < 4; ++i) ctx->es[i] = 2 + i;
@@ -355,6 +393,12 @@ cudaError_t timed_launch(pizza_ctx* ctx, int k, F&& f) {
 }
 
 int explicit_eval(pizza_ctx* ctx, VecSet y, VecSet e) {
+    if (ctx->coll) {
+        CK(timed_launch(ctx, 0, [&] { return launch_coll_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream); }));
+        CK(timed_launch(ctx, 1, [&] { return launch_phi_products(ctx->P, ctx->G1, ctx->G2, ctx->stream); }));
+        CK(timed_launch(ctx, 2, [&] { return launch_coll_grid_rows(ctx->P, ctx->G1, ctx->G2, e, ctx->stream); }));
+        return PIZZA_OK;
+    }
     CK(timed_launch(ctx, 0, [&] { return launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream); }));
     CK(timed_launch(ctx, 1, [&] { return launch_phi_products(ctx->P, ctx->G1, ctx->G2, ctx->stream); }));
     CK(timed_launch(ctx, 2, [&] { return launch_grid_to_spec(ctx->P, ctx->G2, y, e, ctx->stream); }));
@@ -400,6 +444,11 @@ const double ARS_AE[5][5] = {{0, 0, 0, 0, 0},
 int ensure_aux(pizza_ctx* ctx) {
     if (ctx->aux_valid) return PIZZA_OK;
     VecSet y = ctx->vec[ctx->ys[0]];
+    if (ctx->coll) {
+        if (ctx->scheme == PIZZA_CNAB2) CK(launch_coll_apply(ctx->P, y, ctx->vec[ctx->is[0]], ctx->stream));
+        ctx->aux_valid = true;
+        return PIZZA_OK;
+    }
     if (is_multistep(ctx->scheme)) {
         CK(launch_apply(ctx->P, y, ctx->vec[ctx->ms[0]], ctx->vec[ctx->is[0]], true,
                         ctx->scheme == PIZZA_CNAB2, ctx->stream));
@@ -470,6 +519,165 @@ int step_dirk(pizza_ctx* ctx) {
         }
     }
     std::swap(ctx->ys[0], ctx->ys[1]);
+    return PIZZA_OK;
+}
+
+// Collocation: the mass term of a grid state is the state itself, so the right
+// hand side combines states, implicit terms and explicit rows directly; every
+// output goes to a slot that is not an input of the same launch.
+int step_multistep_coll(pizza_ctx* ctx) {
+    std::vector<double> a, bI, bE;
+    double b0;
+    multistep_coeffs(ctx->scheme, ctx->n_done, a, b0, bI, bE);
+    const double dt = ctx->dt;
+    int e_new = ctx->es[3];
+    for (int i = 3; i > 0; --i) ctx->es[i] = ctx->es[i - 1];
+    ctx->es[0] = e_new;
+    int rc = explicit_eval(ctx, ctx->vec[ctx->ys[0]], ctx->vec[ctx->es[0]]);
+    if (rc) return rc;
+    RhsSpec R{};
+    for (size_t j = 0; j < a.size(); ++j) R.t[R.nterms++] = {ctx->vec[ctx->ys[j]], a[j]};
+    for (size_t j = 0; j < bI.size(); ++j)
+        if (bI[j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->is[j]], dt * bI[j]};
+    for (size_t j = 0; j < bE.size(); ++j) R.t[R.nterms++] = {ctx->vec[ctx->es[j]], dt * bE[j]};
+    const DevFactors* F = factors_for(ctx, b0);
+    if (!F) return fail(ctx, PIZZA_EINVAL, "no factors for implicit weight %g", b0);
+    const int y_new = ctx->ys[3], i_new = ctx->is[2];
+    const bool want_imp = (ctx->scheme == PIZZA_CNAB2);
+    CK(timed_launch(ctx, 3, [&] {
+        return launch_coll_solve(ctx->P, R, *F, ctx->vec[y_new], ctx->vec[y_new], ctx->vec[i_new], false, want_imp,
+                                 ctx->stream);
+    }));
+    for (int i = 3; i > 0; --i) ctx->ys[i] = ctx->ys[i - 1];
+    ctx->ys[0] = y_new;
+    ctx->is[2] = ctx->is[1]; ctx->is[1] = ctx->is[0]; ctx->is[0] = i_new;
+    return PIZZA_OK;
+}
+
+int step_dirk_coll(pizza_ctx* ctx) {
+    const double dt = ctx->dt;
+    const int nu = 4;
+    for (int i = 1; i <= nu; ++i) {
+        VecSet y_prev = (i == 1) ? ctx->vec[ctx->ys[0]] : ctx->vec[ctx->stage_y[i - 1]];
+        int rc = explicit_eval(ctx, y_prev, ctx->vec[ctx->stage_e[i - 1]]);
+        if (rc) return rc;
+        RhsSpec R{};
+        R.t[R.nterms++] = {ctx->vec[ctx->ys[0]], 1.0};
+        for (int j = 0; j < i; ++j) {
+            if (ARS_AE[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_e[j]], dt * ARS_AE[i][j]};
+            if (j >= 1 && ARS_AI[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_imp[j]], dt * ARS_AI[i][j]};
+        }
+        const DevFactors* F = factors_for(ctx, ARS_AI[i][i]);
+        if (!F) return fail(ctx, PIZZA_EINVAL, "no factors for a_ii");
+        const bool last = (i == nu);
+        VecSet out = last ? ctx->vec[ctx->ys[1]] : ctx->vec[ctx->stage_y[i]];
+        VecSet imp = last ? out : ctx->vec[ctx->stage_imp[i]];
+        CK(timed_launch(ctx, 3, [&] {
+            return launch_coll_solve(ctx->P, R, *F, out, out, imp, false, !last, ctx->stream);
+        }));
+    }
+    std::swap(ctx->ys[0], ctx->ys[1]);
+    return PIZZA_OK;
+}
+
+// Grid-valued inverses of the collocation systems for one implicit weight
+// (coll_ops.cpp), one thread range of modes per host thread.
+int build_coll_factors(pizza_ctx* ctx, const CollGrid& cg, double gamma, DevFactors& F, std::vector<void*>& al) {
+    const int M = ctx->M, N = ctx->n_r, ni = N - 2;
+    const double gdt = gamma * ctx->dt;
+    std::vector<double2> hW((size_t)M * 2 * N * ni, make_double2(0.0, 0.0));
+    std::vector<double> hT((size_t)M * N * ni), hU;
+    std::vector<int> bad(M, 0);
+    auto work = [&](int m0, int m1) {
+        std::vector<cplx> G;
+        std::vector<double> Gt;
+        for (int m = m0; m < m1; ++m) {
+            if (m > 0) {
+                if (!coll_inverse_wpsi(cg, ctx->E, m, gdt, G)) {
+                    bad[m] = 1;
+                    continue;
+                }
+                for (size_t i = 0; i < G.size(); ++i)
+                    hW[(size_t)m * 2 * N * ni + i] = make_double2(G[i].real(), G[i].imag());
+            }
+            if (!coll_inverse_dir(cg, 1.0 / ctx->Pr, (double)m * m, gdt, Gt)) {
+                bad[m] = 1;
+                continue;
+            }
+            std::copy(Gt.begin(), Gt.end(), hT.begin() + (size_t)m * N * ni);
+        }
+    };
+    unsigned nthr = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    // interleave the modes so that every thread gets a similar mix
+    for (unsigned t = 0; t < nthr; ++t) {
+        th.emplace_back([&, t] {
+            for (int m = (int)t; m < M; m += (int)nthr) work(m, m + 1);
+        });
+    }
+    for (auto& t : th) t.join();
+    for (int m = 0; m < M; ++m)
+        if (bad[m]) return fail(ctx, PIZZA_EINVAL, "collocation system of mode m=%d is singular", m);
+    if (!coll_inverse_dir(cg, 1.0, 1.0, gdt, hU)) return fail(ctx, PIZZA_EINVAL, "zonal-flow system singular");
+    F.gdt = gdt;
+    auto upload = [&](auto*& dst, const auto& hv) -> int {
+        using T = std::remove_reference_t<decltype(*dst)>;
+        dst = dalloc<T>(ctx, hv.size(), al);
+        if (!dst) return fail(ctx, PIZZA_ENOMEM, "device allocation of the collocation inverses failed");
+        CK(cudaMemcpy(dst, hv.data(), hv.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return PIZZA_OK;
+    };
+    int rc = upload(F.colW, hW);
+    if (!rc) rc = upload(F.colT, hT);
+    if (!rc) rc = upload(F.colU, hU);
+    return rc;
+}
+
+// (Re)allocate the NVEC work vectors with the coefficient stride of the selected
+// formulation (the vorticity field only for collocation), zeroed.
+int alloc_vecs(pizza_ctx* ctx) {
+    for (void* p : ctx->vec_allocs) cudaFree(p);
+    ctx->vec_allocs.clear();
+    const size_t vsz = (size_t)ctx->M * ctx->nc;
+    for (int i = 0; i < NVEC; ++i) {
+        VecSet& v = ctx->vec[i];
+        v = VecSet{};
+        v.psi = dalloc<double2>(ctx, vsz, ctx->vec_allocs);
+        v.th = dalloc<double2>(ctx, vsz, ctx->vec_allocs);
+        v.u = dalloc<double>(ctx, ctx->nc, ctx->vec_allocs);
+        if (ctx->coll) v.w = dalloc<double2>(ctx, vsz, ctx->vec_allocs);
+        if (!v.psi || !v.th || !v.u || (ctx->coll && !v.w))
+            return fail(ctx, PIZZA_ENOMEM, "device allocation of state vectors failed");
+        CK(cudaMemset(v.psi, 0, vsz * 16));
+        CK(cudaMemset(v.th, 0, vsz * 16));
+        CK(cudaMemset(v.u, 0, ctx->nc * 8));
+        if (v.w) CK(cudaMemset(v.w, 0, vsz * 16));
+    }
+    return PIZZA_OK;
+}
+
+// Switch to the collocation formulation: grid tables on the device.
+int enable_collocation(pizza_ctx* ctx) {
+    const int N = ctx->n_r;
+    CollGrid cg = coll_grid(N, make_geom(ctx->eta));
+    auto& al = ctx->allocs;
+    double* beta = dalloc<double>(ctx, N, al);
+    double* dbeta = dalloc<double>(ctx, N, al);
+    double* d1 = dalloc<double>(ctx, (size_t)N * N, al);
+    double* d2 = dalloc<double>(ctx, (size_t)N * N, al);
+    double* tm = dalloc<double>(ctx, (size_t)N * N, al);
+    if (!beta || !dbeta || !d1 || !d2 || !tm) return fail(ctx, PIZZA_ENOMEM, "device allocation failed");
+    CK(cudaMemcpy(beta, cg.beta.data(), N * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dbeta, cg.dbeta.data(), N * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d1, cg.D1.data(), (size_t)N * N * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d2, cg.D2.data(), (size_t)N * N * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(tm, cg.T.data(), (size_t)N * N * 8, cudaMemcpyHostToDevice));
+    ctx->P.beta = beta;
+    ctx->P.dbeta = dbeta;
+    ctx->P.cD1 = d1;
+    ctx->P.cD2 = d2;
+    ctx->P.cTm = tm;
+    ctx->coll_d1_row0.assign(cg.D1.begin(), cg.D1.begin() + N);
     return PIZZA_OK;
 }
 
@@ -628,22 +836,7 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         ctx->err = "device allocation of grid buffers failed";
         return bail(PIZZA_ENOMEM);
     }
-    const size_t vsz = (size_t)ctx->M * ctx->nc;
-    for (int i = 0; i < NVEC; ++i) {
-        ctx->vec[i].psi = dalloc<double2>(ctx, vsz, al);
-        ctx->vec[i].th = dalloc<double2>(ctx, vsz, al);
-        ctx->vec[i].u = dalloc<double>(ctx, ctx->nc, al);
-        if (!ctx->vec[i].psi || !ctx->vec[i].th || !ctx->vec[i].u) {
-            ctx->err = "device allocation of state vectors failed";
-            return bail(PIZZA_ENOMEM);
-        }
-        if (rc == PIZZA_OK && (cudaMemset(ctx->vec[i].psi, 0, vsz * 16) != cudaSuccess ||
-                               cudaMemset(ctx->vec[i].th, 0, vsz * 16) != cudaSuccess ||
-                               cudaMemset(ctx->vec[i].u, 0, ctx->nc * 8) != cudaSuccess)) {
-            ctx->err = "cudaMemset failed";
-            rc = PIZZA_ECUDA;
-        }
-    }
+    if (rc == PIZZA_OK) rc = alloc_vecs(ctx);
     if (rc != PIZZA_OK) return bail(rc);
     reset_slots(ctx);
     *out = ctx;
@@ -659,6 +852,28 @@ int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
         free_factors(ctx);
         ctx->dt = value;
         ctx->dt_set = true;
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "radial") == 0) {
+        if (value != 0.0 && value != 1.0)
+            return fail(ctx, PIZZA_EUNSUPPORTED, "radial must be 0 (collocation) or 1 (integration)");
+        const bool coll = (value == 0.0);
+        if (coll == ctx->coll) return PIZZA_OK;
+        if (coll && ctx->n_r > PIZZA_COLL_MAX_NR)
+            return fail(ctx, PIZZA_EUNSUPPORTED, "collocation is limited to n_r <= %d", PIZZA_COLL_MAX_NR);
+        cudaStreamSynchronize(ctx->stream);
+        free_factors(ctx);
+        ctx->coll = coll;
+        ctx->P.coll = coll ? 1 : 0;
+        ctx->nc = coll ? ctx->n_r : (2 * (ctx->n_r - 1)) / 3;
+        ctx->P.nc = ctx->nc;
+        if (coll && !ctx->P.cD1) {
+            int rc = enable_collocation(ctx);
+            if (rc) return rc;
+        }
+        int rc = alloc_vecs(ctx);
+        if (rc) return rc;
+        reset_slots(ctx);
         return PIZZA_OK;
     }
     return fail(ctx, PIZZA_EINVAL, "unknown option '%s'", key);
@@ -684,7 +899,8 @@ int pizza_set_state(pizza_ctx* ctx, const double* theta_hat, const double* psi_h
     if (!ctx) return PIZZA_EINVAL;
     if (nc_in < 0 || nc_in > ctx->nc) return fail(ctx, PIZZA_EINVAL, "nc_in must be in [0, %d]", ctx->nc);
     reset_slots(ctx);
-    VecSet y = ctx->vec[ctx->ys[0]];
+    // collocation: coefficients go to the scratch slot, then to grid values
+    VecSet y = ctx->coll ? ctx->vec[15] : ctx->vec[ctx->ys[0]];
     const size_t M = ctx->M, nc = ctx->nc;
     CK(cudaMemsetAsync(y.psi, 0, M * nc * 16, ctx->stream));
     CK(cudaMemsetAsync(y.th, 0, M * nc * 16, ctx->stream));
@@ -698,6 +914,7 @@ int pizza_set_state(pizza_ctx* ctx, const double* theta_hat, const double* psi_h
                                  (size_t)nc_in * 16, M - 1, cudaMemcpyDefault, ctx->stream));
         if (uphi0_hat) CK(cudaMemcpyAsync(y.u, uphi0_hat, (size_t)nc_in * 8, cudaMemcpyDefault, ctx->stream));
     }
+    if (ctx->coll) CK(launch_coll_from_hat(ctx->P, y, ctx->vec[ctx->ys[0]], ctx->stream));
     // keep the host buffers valid only for the duration of the call
     CK(cudaStreamSynchronize(ctx->stream));
     return PIZZA_OK;
@@ -706,6 +923,10 @@ int pizza_set_state(pizza_ctx* ctx, const double* theta_hat, const double* psi_h
 int pizza_get_state(pizza_ctx* ctx, double* theta_hat, double* psi_hat, double* uphi0_hat) {
     if (!ctx) return PIZZA_EINVAL;
     VecSet y = ctx->vec[ctx->ys[0]];
+    if (ctx->coll) {
+        CK(launch_coll_to_hat(ctx->P, y, ctx->vec[15], ctx->stream));
+        y = ctx->vec[15];
+    }
     const size_t M = ctx->M, nc = ctx->nc;
     if (theta_hat) CK(cudaMemcpyAsync(theta_hat, y.th, M * nc * 16, cudaMemcpyDefault, ctx->stream));
     if (psi_hat) CK(cudaMemcpyAsync(psi_hat, y.psi, M * nc * 16, cudaMemcpyDefault, ctx->stream));
@@ -722,7 +943,10 @@ int pizza_step(pizza_ctx* ctx, int nsteps) {
     rc = ensure_aux(ctx);
     if (rc) return rc;
     for (int s = 0; s < nsteps; ++s) {
-        rc = is_multistep(ctx->scheme) ? step_multistep(ctx) : step_dirk(ctx);
+        if (ctx->coll)
+            rc = is_multistep(ctx->scheme) ? step_multistep_coll(ctx) : step_dirk_coll(ctx);
+        else
+            rc = is_multistep(ctx->scheme) ? step_multistep(ctx) : step_dirk(ctx);
         if (rc) return rc;
         ctx->n_done++;
     }
@@ -736,7 +960,7 @@ int pizza_explicit_terms(pizza_ctx* ctx, double* e_psi, double* e_theta, double*
     int rc = explicit_eval(ctx, ctx->vec[ctx->ys[0]], e);
     if (rc) return rc;
     const size_t M = ctx->M, nc = ctx->nc;
-    if (e_psi) CK(cudaMemcpyAsync(e_psi, e.psi, M * nc * 16, cudaMemcpyDefault, ctx->stream));
+    if (e_psi) CK(cudaMemcpyAsync(e_psi, ctx->coll ? e.w : e.psi, M * nc * 16, cudaMemcpyDefault, ctx->stream));
     if (e_theta) CK(cudaMemcpyAsync(e_theta, e.th, M * nc * 16, cudaMemcpyDefault, ctx->stream));
     if (e_uphi) CK(cudaMemcpyAsync(e_uphi, e.u, nc * 8, cudaMemcpyDefault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -800,7 +1024,10 @@ int pizza_diagnostics(pizza_ctx* ctx, pizza_diag* out) {
         CK(cudaMemcpy(ctx->diag_q, q.data(), n_r * sizeof(double), cudaMemcpyHostToDevice));
     }
     VecSet y = ctx->vec[ctx->ys[0]];
-    CK(launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
+    if (ctx->coll)
+        CK(launch_coll_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
+    else
+        CK(launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
     CK(launch_diagnostics(ctx->P, ctx->G1, ctx->diag_q, ctx->diag_modes, ctx->diag_radii, ctx->stream));
     std::vector<double> ms(2 * (size_t)M), rm(2 * (size_t)n_r);
     std::vector<double2> th0(nc);
@@ -821,11 +1048,16 @@ int pizza_diagnostics(pizza_ctx* ctx, pizza_diag* out) {
         cs = std::max(cs, rm[2 * k] / ctx->ds_host[k]);
         cp = std::max(cp, rm[2 * k + 1] / (ctx->s_host[k] * dphi));
     }
-    // d theta_0/ds at s_o: (1/a) sum_n n^2 c_n, c_n = C w_n theta_hat_0n
-    const double C = std::sqrt(2.0 / (n_r - 1));
+    // d theta_0/ds at s_o: (1/a) sum_n n^2 c_n, c_n = C w_n theta_hat_0n; on grid
+    // values (collocation) the first row of the differentiation matrix
     double dth = 0.0;
-    for (int n = 0; n < nc; ++n) dth += (double)n * n * C * ((n == 0) ? 0.5 : 1.0) * th0[n].x;
-    dth /= g.a;
+    if (ctx->coll) {
+        for (int j = 0; j < n_r; ++j) dth += ctx->coll_d1_row0[j] * th0[j].x;
+    } else {
+        const double C = std::sqrt(2.0 / (n_r - 1));
+        for (int n = 0; n < nc; ++n) dth += (double)n * n * C * ((n == 0) ? 0.5 : 1.0) * th0[n].x;
+        dth /= g.a;
+    }
     const double dtc = std::log(ctx->eta) != 0.0 ? tc_coefficient(ctx->eta) / g.s_o : 0.0;
     out->E_K = ek;
     out->E_Z = ez;
@@ -835,6 +1067,27 @@ int pizza_diagnostics(pizza_ctx* ctx, pizza_diag* out) {
     out->Ro = out->Re * ctx->E;
     out->cfl_s = cs;
     out->cfl_phi = cp;
+    return PIZZA_OK;
+}
+
+int pizza_get_grid(pizza_ctx* ctx, double* us, double* uphi, double* omega, double* theta) {
+    if (!ctx) return PIZZA_EINVAL;
+    const size_t n = (size_t)ctx->n_r * ctx->n_phi;
+    if (!ctx->grid_out) {
+        ctx->grid_out = dalloc<double>(ctx, 4 * n, ctx->allocs);
+        if (!ctx->grid_out) return fail(ctx, PIZZA_ENOMEM, "allocation of the grid buffer failed");
+    }
+    VecSet y = ctx->vec[ctx->ys[0]];
+    if (ctx->coll)
+        CK(launch_coll_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
+    else
+        CK(launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
+    double* g = ctx->grid_out;
+    CK(launch_phi_fields(ctx->P, ctx->G1, g, g + n, g + 2 * n, g + 3 * n, ctx->stream));
+    double* outs[4] = {us, uphi, omega, theta};
+    for (int f = 0; f < 4; ++f)
+        if (outs[f]) CK(cudaMemcpyAsync(outs[f], g + f * n, n * 8, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return PIZZA_OK;
 }
 
@@ -864,6 +1117,7 @@ void pizza_free(pizza_ctx* ctx) {
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
+    for (void* p : ctx->vec_allocs) cudaFree(p);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }

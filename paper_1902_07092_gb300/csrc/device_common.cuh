@@ -138,6 +138,44 @@ __device__ static double2* fft_batched(double2* buf0, double2* buf1, const FftPl
     return a;
 }
 
+// 2^e with e the difference of the binary exponents of a and b (1 when either
+// is zero), clamped to |e| <= 400.  Two real fields packed into one complex
+// transform as a + i (scale) b are given comparable magnitudes this way: the
+// scaling is exact, and the rounding of the transform then stays relative to
+// each field instead of to the larger one.
+__device__ __forceinline__ double pow2_ratio(double a, double b) {
+    if (!(a > 0.0) || !(b > 0.0)) return 1.0;
+    const int e = max(-400, min(400, ilogb(a) - ilogb(b)));
+    return ldexp(1.0, e);
+}
+
+// CTA-wide max over m < n of |re| + |im| of the nf <= 4 rows src + f*stride,
+// into out[f] (shared).  red: shared scratch of 4*32 doubles.  Whole CTA.
+__device__ __forceinline__ void block_max_abs(const double2* src, int stride, int nf, int n, double* out,
+                                              double* red) {
+    double mx[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+            if (f < nf) {
+                const double2 v = src[(size_t)f * stride + i];
+                mx[f] = fmax(mx[f], fabs(v.x) + fabs(v.y));
+            }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        for (int o = 16; o > 0; o >>= 1) mx[f] = fmax(mx[f], __shfl_xor_sync(0xffffffffu, mx[f], o));
+        if (lane == 0) red[f * 32 + warp] = mx[f];
+    }
+    __syncthreads();
+    if (threadIdx.x < nf) {
+        double r = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[threadIdx.x * 32 + w]);
+        out[threadIdx.x] = r;
+    }
+    __syncthreads();
+}
+
 // Load the even extension of coefficients a_0..a_K (complex) into z (length 2K):
 // z_j = a_j (j <= K), z_{2K-j} = a_j.  The FFT of z then gives
 // Z_n = 2 sum''_{j=0..K} a_j cos(pi n j/K),  n = 0..K (the DCT-I core).

@@ -65,4 +65,23 @@ template <class T>
 bool factor_bordered(const std::vector<T>& mass_lin_band, int n_c, int h,
                      const std::vector<double>& tau, int p, Bordered<T>& out);
 
+// ---------------------------------------------------------------------------
+// Chebyshev collocation (Section 3.1), fields held as Gauss-Lobatto grid values.
+// ---------------------------------------------------------------------------
+struct CollGrid {
+    int N = 0;
+    std::vector<double> s;            // radial grid, s_0 = s_o
+    std::vector<double> beta, dbeta;  // beta = -s/h^2 and d beta/ds; 0 at s_o (a boundary row)
+    std::vector<double> D1, D2;       // d/ds and d^2/ds^2 of the interpolant, row-major N x N
+    std::vector<double> T;            // T[k*N + n] = C w_n T_n(x_k) (Eq. cheb; T T = I, Eq. icheb)
+};
+CollGrid coll_grid(int n_r, const Geom& g);
+
+// Columns 1..N-2 (the interior right-hand-side rows) of the inverse of the
+// vorticity-streamfunction system of mode m >= 1 for implicit weight gdt:
+// G[i*(N-2) + j], i < 2N (omega_0..omega_{N-1}, psi_0..psi_{N-1}).
+bool coll_inverse_wpsi(const CollGrid& c, double E, int m, double gdt, std::vector<cplx>& G);
+// Same for  f - gdt*kappa*(D2 + D1/s - q/s^2) f  with Dirichlet rows: G[i*(N-2) + j], i < N.
+bool coll_inverse_dir(const CollGrid& c, double kappa, double q, double gdt, std::vector<double>& G);
+
 }  // namespace pz

@@ -61,7 +61,14 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
     cheb_derivative_scan(cc0, cc1, bufA, N, P.inv_a);
     if (m > 0) cheb_derivative_scan(cc1, cc2, bufA, N, P.inv_a);
 
-    // field list: 0 Psi, 1 Psi', 2 Psi'', 3 theta, 4 packed u_bar + i u_bar'
+    // field list: 0 Psi, 1 Psi', 2 Psi'', 3 theta, 4 packed u_bar + i lam u_bar'
+    // (lam a power of two balancing the two parts)
+    __shared__ double red[4 * 32], mx[4];
+    double lam = 1.0;
+    if (m == 0) {
+        block_max_abs(cc0, N, 2, N, mx, red);
+        lam = pow2_ratio(mx[0], mx[1]);
+    }
     int fields[4];
     int nf;
     if (m > 0) {
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
                 else if (fid == 2) v = cc2[j];
                 else if (fid == 3)
                     v = (j < nc) ? cscale(y.th[(size_t)m * nc + j], (j == 0) ? 0.5 * C : C) : make_double2(0.0, 0.0);
-                else v = make_double2(cc0[j].x, cc1[j].x);
+                else v = make_double2(cc0[j].x, lam * cc1[j].x);
                 if (j == 0 || j == K) v = cscale(v, 2.0);
                 even_extend_store(z, K, j, v);
             }
@@ -110,7 +117,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
                 } else {
                     out[0] = make_double2(0.0, 0.0);
                     out[M] = make_double2(g.x, 0.0);
-                    out[2 * M] = make_double2(g.y + g.x * is, 0.0);
+                    out[2 * M] = make_double2(g.y / lam + g.x * is, 0.0);
                 }
             }
         }
@@ -125,37 +132,40 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
 //   g1 * Re(g2) = v omega + i u_phi omega,  g1 * Im(g2) = v theta + i u_phi theta.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void load_packed_spectrum(double2* Z, const double2* __restrict__ src, int M, int Pn,
-                                                     int n_m) {
-    // src points at G1/G2 row (k, f): field a = src[0..M), field b = src[M..2M)
+                                                     int n_m, double sa, double sb) {
+    // src points at G1/G2 row (k, f): field a = src[0..M), field b = src[M..2M);
+    // packed as sa a + i sb b
     for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
         double2 z = make_double2(0.0, 0.0);
         if (j == 0) {
-            z = make_double2(src[0].x, src[M].x);
+            z = make_double2(sa * src[0].x, sb * src[M].x);
         } else if (j <= n_m) {
-            const double2 a = src[j], b = src[M + j];
+            const double2 a = cscale(src[j], sa), b = cscale(src[M + j], sb);
             z = make_double2(a.x - b.y, a.y + b.x);  // a + i b
         } else if (j >= Pn - n_m) {
             const int mm = Pn - j;
-            const double2 a = src[mm], b = src[M + mm];
+            const double2 a = cscale(src[mm], sa), b = cscale(src[M + mm], sb);
             z = make_double2(a.x + b.y, -a.y + b.x);  // conj(a) + i conj(b)
         }
         Z[j] = z;
     }
 }
 
+// Split the transform Y of a + i b (a, b real fields) into the spectra of a and
+// b, scaled by sa / Pn and sb / Pn.
 __device__ __forceinline__ void store_split_spectrum(const double2* Y, double2* __restrict__ dst, int M, int Pn,
-                                                     int n_m) {
-    const double inv = 1.0 / (double)Pn;
+                                                     int n_m, double sa, double sb) {
+    const double ia = sa / (double)Pn, ib = sb / (double)Pn;
     for (int m = threadIdx.x; m <= n_m; m += blockDim.x) {
         double2 a, b;
         if (m == 0) {
-            a = make_double2(Y[0].x * inv, 0.0);
-            b = make_double2(Y[0].y * inv, 0.0);
+            a = make_double2(Y[0].x * ia, 0.0);
+            b = make_double2(Y[0].y * ib, 0.0);
         } else {
             const double2 y1 = Y[m], y2 = Y[Pn - m];
             // a = (y1 + conj(y2))/2,  b = (y1 - conj(y2))/(2i)
-            a = make_double2(0.5 * (y1.x + y2.x) * inv, 0.5 * (y1.y - y2.y) * inv);
-            b = make_double2(0.5 * (y1.y + y2.y) * inv, -0.5 * (y1.x - y2.x) * inv);
+            a = make_double2(0.5 * (y1.x + y2.x) * ia, 0.5 * (y1.y - y2.y) * ia);
+            b = make_double2(0.5 * (y1.y + y2.y) * ib, -0.5 * (y1.x - y2.x) * ib);
         }
         dst[m] = a;
         dst[M + m] = b;
@@ -171,8 +181,13 @@ __global__ void __launch_bounds__(512) k_phi_products(StepParams P, const double
     double2* Y = sm + Pn;
     const int tid = threadIdx.x, nth = blockDim.x;
     double2 reg[MAXPER];
+    // exact power-of-two weights that balance the packed pairs:
+    // g1 = v + i l1 u_phi, g2 = omega + i l2 theta
+    __shared__ double red[4 * 32], mx[4];
+    block_max_abs(G1 + g_index(k, 0, 0, M), M, 4, n_m + 1, mx, red);
+    const double l1 = pow2_ratio(mx[0], mx[1]), l2 = pow2_ratio(mx[2], mx[3]);
 
-    load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m);
+    load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, 1.0, l1);
     double2* R = fft_batched<+1>(X, Y, P.plan_p, 1);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
@@ -180,7 +195,7 @@ __global__ void __launch_bounds__(512) k_phi_products(StepParams P, const double
         if (j < Pn) reg[i] = R[j];
     }
     __syncthreads();
-    load_packed_spectrum(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m);
+    load_packed_spectrum(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m, 1.0, l2);
     R = fft_batched<+1>(X, Y, P.plan_p, 1);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
@@ -193,7 +208,8 @@ __global__ void __launch_bounds__(512) k_phi_products(StepParams P, const double
     }
     double2* other = (R == X) ? Y : X;
     double2* S = fft_batched<-1>(R, other, P.plan_p, 1);
-    store_split_spectrum(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m);
+    // g1 Re(g2) = v omega + i l1 u_phi omega
+    store_split_spectrum(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, 1.0, 1.0 / l1);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
@@ -201,7 +217,8 @@ __global__ void __launch_bounds__(512) k_phi_products(StepParams P, const double
         if (j < Pn) X[j] = reg[i];
     }
     S = fft_batched<-1>(X, Y, P.plan_p, 1);
-    store_split_spectrum(S, G2 + g_index(k, 2, 0, M), M, Pn, n_m);
+    // g1 Im(g2) = l2 (v theta + i l1 u_phi theta)
+    store_split_spectrum(S, G2 + g_index(k, 2, 0, M), M, Pn, n_m, 1.0 / l2, 1.0 / (l1 * l2));
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +392,7 @@ __global__ void k_diag_modes(StepParams P, const double2* __restrict__ G1, const
     const int m = blockIdx.x, M = P.M;
     double e = 0.0, z = 0.0;
     for (int k = threadIdx.x; k < P.n_r; k += blockDim.x) {
-        const double f = P.h2[k] * P.inv_s[k];
+        const double f = P.coll ? P.inv_s[k] : P.h2[k] * P.inv_s[k];
         const double2 v = G1[g_index(k, 0, m, M)], up = G1[g_index(k, 1, m, M)], w = G1[g_index(k, 2, m, M)];
         const double us2 = f * f * (v.x * v.x + v.y * v.y);
         e += q[k] * (us2 + up.x * up.x + up.y * up.y);
@@ -403,7 +420,7 @@ __global__ void k_diag_modes(StepParams P, const double2* __restrict__ G1, const
 }
 
 // per radius: max |u_s| and max |u_phi| over the azimuthal grid (Eq. fft of
-// g = u_s + i u_phi); out[k*2 + 0], out[k*2 + 1].
+// g = u_s + i l u_phi, l a balancing power of two); out[k*2 + 0], out[k*2 + 1].
 __global__ void __launch_bounds__(512) k_phi_cfl(StepParams P, const double2* __restrict__ G1,
                                                  double* __restrict__ out) {
     extern __shared__ double2 sm[];
@@ -411,22 +428,12 @@ __global__ void __launch_bounds__(512) k_phi_cfl(StepParams P, const double2* __
     const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
     double2* X = sm;
     double2* Y = sm + Pn;
-    const double f = P.h2[k] * P.inv_s[k];
+    const double f = P.coll ? P.inv_s[k] : P.h2[k] * P.inv_s[k];
     const double2* src = G1 + g_index(k, 0, 0, M);
-    for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
-        double2 z = make_double2(0.0, 0.0);
-        if (j == 0) {
-            z = make_double2(f * src[0].x, src[M].x);
-        } else if (j <= n_m) {
-            const double2 a = cscale(src[j], f), b = src[M + j];
-            z = make_double2(a.x - b.y, a.y + b.x);
-        } else if (j >= Pn - n_m) {
-            const int mm = Pn - j;
-            const double2 a = cscale(src[mm], f), b = src[M + mm];
-            z = make_double2(a.x + b.y, -a.y + b.x);
-        }
-        X[j] = z;
-    }
+    __shared__ double red4[4 * 32], mx[4];
+    block_max_abs(src, M, 2, n_m + 1, mx, red4);
+    const double l = pow2_ratio(f * mx[0], mx[1]);
+    load_packed_spectrum(X, src, M, Pn, n_m, f, l);
     double2* R = fft_batched<+1>(X, Y, P.plan_p, 1);
     double ms = 0.0, mp = 0.0;
     for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
@@ -450,7 +457,39 @@ __global__ void __launch_bounds__(512) k_phi_cfl(StepParams P, const double2* __
             b = fmax(b, red[1][i]);
         }
         out[2 * k] = a;
-        out[2 * k + 1] = b;
+        out[2 * k + 1] = b / l;
+    }
+}
+
+// per radius: the physical-grid values (Eq. fft) of u_s, u_phi, omega and theta,
+// out[k * n_phi + j]; u_s = (h^2/s) v (integration) or v/s (collocation).  The
+// pairs (u_s, u_phi) and (omega, theta) travel in one complex transform each,
+// balanced by powers of two.
+__global__ void __launch_bounds__(512) k_phi_fields(StepParams P, const double2* __restrict__ G1,
+                                                    double* __restrict__ us, double* __restrict__ uphi,
+                                                    double* __restrict__ omega, double* __restrict__ theta) {
+    extern __shared__ double2 sm[];
+    const int k = blockIdx.x;
+    const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
+    double2* X = sm;
+    double2* Y = sm + Pn;
+    const double f = P.coll ? P.inv_s[k] : P.h2[k] * P.inv_s[k];
+    __shared__ double red4[4 * 32], mx[4];
+    block_max_abs(G1 + g_index(k, 0, 0, M), M, 4, n_m + 1, mx, red4);
+    for (int pass = 0; pass < 2; ++pass) {
+        const double2* src = G1 + g_index(k, 2 * pass, 0, M);
+        const double fa = (pass == 0) ? f : 1.0;
+        const double l = pow2_ratio(fa * mx[2 * pass], mx[2 * pass + 1]);
+        load_packed_spectrum(X, src, M, Pn, n_m, fa, l);
+        double2* R = fft_batched<+1>(X, Y, P.plan_p, 1);
+        double* oa = (pass == 0) ? us : omega;
+        double* ob = (pass == 0) ? uphi : theta;
+        const double il = 1.0 / l;
+        for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
+            oa[(size_t)k * Pn + j] = R[j].x;
+            ob[(size_t)k * Pn + j] = R[j].y * il;
+        }
+        __syncthreads();
     }
 }
 
@@ -466,6 +505,15 @@ cudaError_t launch_diagnostics(const StepParams& P, const double2* G1, const dou
     err = cudaFuncSetAttribute(k_phi_cfl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     k_phi_cfl<<<P.n_r, nth, sm, st>>>(P, G1, radius_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_fields(const StepParams& P, const double2* G1, double* us, double* uphi, double* omega,
+                              double* theta, cudaStream_t st) {
+    const size_t sm = smem_phi_products(P);
+    cudaError_t err = cudaFuncSetAttribute(k_phi_fields, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    k_phi_fields<<<P.n_r, 256, sm, st>>>(P, G1, us, uphi, omega, theta);
     return cudaGetLastError();
 }
 

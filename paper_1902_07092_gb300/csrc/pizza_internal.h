@@ -20,11 +20,13 @@ struct FftPlan {
     const double2* tw;  // tw[j] = exp(-2 pi i j / L), j < L
 };
 
-// One set of per-field vectors: Psi and theta complex [M][nc], u real [nc].
+// One set of per-field vectors: Psi and theta complex [M][nc], u real [nc]; the
+// collocation formulation adds the vorticity w [M][n_r] (and stores grid values).
 struct VecSet {
     double2* psi;
     double2* th;
     double* u;
+    double2* w;
 };
 
 // Banded m-independent operators (band storage, half width h, row-major [nc][2h+1]).
@@ -50,6 +52,10 @@ struct DevFactors {
     // zonal flow, real, H = 4: blocks [nb_t][3][16], Y [n_t][2], Sinv [4], band [n_t][9]
     double *uBlk, *uY, *uSinv, *uBand;
     int refine_t;  // also refine the temperature and zonal-flow solves
+    // collocation: interior-row columns of the grid-valued inverses,
+    // colW [M][2 n_r][n_r-2] (omega_k, psi_k), colT [M][n_r][n_r-2], colU [n_r][n_r-2]
+    double2* colW;
+    double *colT, *colU;
 };
 
 // Scalar parameters passed by value to every kernel.
@@ -62,6 +68,11 @@ struct StepParams {
     FftPlan plan_r;       // length 2K (radial DCT-I)
     FftPlan plan_p;       // length n_phi (azimuthal)
     DevOps ops;
+    // collocation formulation (Section 3.1): 1 when selected
+    int coll;
+    const double* beta;   // [n_r] beta = -s/h^2, 0 at s_o
+    const double* dbeta;  // [n_r] d beta/ds, 0 at s_o
+    const double *cD1, *cD2, *cTm;  // [n_r][n_r] d/ds, d^2/ds^2 on grid values; synthesis matrix
 };
 
 struct RhsTerm {
@@ -82,6 +93,16 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st);
 cudaError_t launch_apply(const StepParams& P, VecSet y, VecSet mass_out, VecSet imp_out, bool want_mass,
                          bool want_imp, cudaStream_t st);
+cudaError_t launch_coll_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st);
+cudaError_t launch_coll_grid_rows(const StepParams& P, const double2* G1, const double2* G2, VecSet e,
+                                  cudaStream_t st);
+cudaError_t launch_coll_solve(const StepParams& P, const RhsSpec& R, const DevFactors& F, VecSet y_out,
+                              VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st);
+cudaError_t launch_coll_apply(const StepParams& P, VecSet y, VecSet imp_out, cudaStream_t st);
+cudaError_t launch_coll_from_hat(const StepParams& P, VecSet hat, VecSet y, cudaStream_t st);
+cudaError_t launch_coll_to_hat(const StepParams& P, VecSet y, VecSet out, cudaStream_t st);
+cudaError_t launch_phi_fields(const StepParams& P, const double2* G1, double* us, double* uphi, double* omega,
+                              double* theta, cudaStream_t st);
 cudaError_t launch_diagnostics(const StepParams& P, const double2* G1, const double* q, double* mode_sums,
                                double* radius_max, cudaStream_t st);
 
@@ -96,5 +117,7 @@ size_t smem_spec_to_grid(const StepParams& P);
 size_t smem_phi_products(const StepParams& P);
 size_t smem_grid_to_spec(const StepParams& P);
 size_t smem_solve(const StepParams& P);
+size_t smem_coll_spec_to_grid(const StepParams& P);
+size_t smem_coll_grid_rows(const StepParams& P);
 
 }  // namespace pz
