@@ -3,9 +3,11 @@
 
 Default workload: n_r = 257, n_phi = 768 (N_m = 256), E = 1e-5, Pr = 1,
 Ra = 10 Ra_c, radius ratio 0.35, Chebyshev integration / tau, ARS443, FP64,
-seeded initial temperature perturbation of amplitude 1e-3.
+seeded initial temperature perturbation of amplitude 1e-3.  --workload selects
+another (e.g. coll_n257_p768: the same problem in the collocation formulation;
+coll_n33_p96: n_r = 33 collocation points, CNAB2).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload W]
 
 Timing: W untimed steps, then K steps, each bracketed by CUDA events on the
 library's stream, with a 256 MiB write between steps to flush the 129 MB L2
@@ -45,13 +47,24 @@ def critical_rayleigh(E):
 
 
 # ----------------------------------------------------------- flop counts ----
-def algorithmic_flops(n_r, n_phi, scheme):
+def algorithmic_flops(n_r, n_phi, scheme, radial="integration"):
     """FP64 flops per launch of each kernel (formulas and unit counts in the design
     notes): a complex FFT of length L counts 5 L log2 L, a complex-data DCT-I of
     K+1 points 5 K log2 K (a length-K complex FFT), a banded apply 2 flops per
-    real x complex tap pair, the unpivoted band solve its multiply-adds."""
+    real x complex tap pair, the unpivoted band solve its multiply-adds; the
+    collocation solve 8 flops per complex x complex and 4 per real x complex
+    inverse entry."""
     K = n_r - 1
     M = n_phi // 3 + 1
+    if radial == "collocation":
+        dct = 5.0 * K * math.log2(K)
+        fft = 5.0 * n_phi * math.log2(n_phi)
+        f_s2g = M * (2 * dct + 20.0 * n_r)
+        f_phi = n_r * (4 * fft + 8.0 * n_phi)
+        f_g2s = M * (4 * dct + 40.0 * n_r)
+        nterms = 6
+        f_solve = M * (20.0 * n_r * (n_r - 2) + nterms * 3 * 4.0 * n_r)
+        return dict(zip(KERNELS, (f_s2g, f_phi, f_g2s, f_solve)))
     nc = (2 * (n_r - 1)) // 3
     dct = 5.0 * K * math.log2(K)
     fft = 5.0 * n_phi * math.log2(n_phi)
@@ -121,13 +134,19 @@ class ClockSampler:
 # ------------------------------------------------------------ oracle arm ----
 def oracle_sample(wl, Ra, budget_s, max_steps):
     """Time the oracle (as it stands) on the workload: steps until budget_s."""
+    from oracle.collocation import CollocationStepper
     from oracle.stepper import IntegrationStepper
     n_r, n_phi = wl["n_r"], wl["n_phi"]
+    nc = inputs.n_c_of(wl)
     t0 = time.perf_counter()
-    st = IntegrationStepper(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
-    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"], cfg=wl["cfg"])
-    z, zu = inputs.zero_state(n_r, n_phi)
-    st.set_state(z, th, zu)
+    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"], cfg=wl["cfg"], n_c=nc)
+    z, zu = inputs.zero_state(n_r, n_phi, n_c=nc)
+    if wl.get("radial") == "collocation":
+        st = CollocationStepper(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
+        st.set_state(z, z.copy(), th, zu)
+    else:
+        st = IntegrationStepper(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
+        st.set_state(z, th, zu)
     st.step()                                  # builds the LU factors (set-up, untimed)
     setup = time.perf_counter() - t0
     n, t = 0, 0.0
@@ -168,9 +187,11 @@ def run_reference(args, wl, Ra, rank):
 
 def config_of(args, wl, Ra):
     return {"workload": args.workload, "n_r": wl["n_r"], "n_phi": wl["n_phi"], "N_m": wl["n_phi"] // 3,
-            "N_c": inputs.n_c_integration(wl["n_r"]), "E": wl["E"], "Ra": Ra, "Ra_over_Ra_c": wl["ra_factor"],
+            "N_c": inputs.n_c_of(wl), "E": wl["E"], "Ra": Ra, "Ra_over_Ra_c": wl["ra_factor"],
             "Pr": wl["Pr"], "radius_ratio": wl["eta"], "scheme": wl["scheme"], "dt": wl["dt"],
-            "radial": "chebyshev-integration-tau", "l2": "flushed (256 MiB write) between timed steps",
+            "radial": ("chebyshev-collocation" if wl.get("radial") == "collocation"
+                       else "chebyshev-integration-tau"),
+            "l2": "flushed (256 MiB write) between timed steps",
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
 
@@ -182,15 +203,17 @@ def run_native(args, wl, Ra, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     n_r, n_phi = wl["n_r"], wl["n_phi"]
     gp = n_r * n_phi
-    sol = B.Solver(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
+    sol = B.Solver(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"],
+                   radial=wl.get("radial", "integration"))
     # a dedicated stream: the library launches, the L2 flush and the timing events
     # all go to it (torch's default stream handle is 0, which the library reads
     # as "use your own stream")
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     B.pizza_set_stream(sol.ctx, stream.cuda_stream)
-    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"] + 1000 * rank, cfg=wl["cfg"])
-    z, zu = inputs.zero_state(n_r, n_phi)
+    nc = inputs.n_c_of(wl)
+    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"] + 1000 * rank, cfg=wl["cfg"], n_c=nc)
+    z, zu = inputs.zero_state(n_r, n_phi, n_c=nc)
     sol.set_state(th, z, zu)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -252,7 +275,7 @@ def run_native(args, wl, Ra, rank, world, local_rank):
         sol.close()
         return
     value = world * gp * args.steps / (total_ms / 1e3) / 1e6
-    flops = algorithmic_flops(n_r, n_phi, wl["scheme"])
+    flops = algorithmic_flops(n_r, n_phi, wl["scheme"], wl.get("radial", "integration"))
     share = {k: float(kt[i]) / max(float(kt.sum()), 1e-30) for i, k in enumerate(KERNELS)}
     dom = max(range(4), key=lambda i: kt[i])
     avg_ms = float(kt[dom]) / max(int(kn[dom]), 1)

@@ -592,19 +592,24 @@ int build_coll_factors(pizza_ctx* ctx, const CollGrid& cg, double gamma, DevFact
         std::vector<cplx> G;
         std::vector<double> Gt;
         for (int m = m0; m < m1; ++m) {
+            // stored column-major (one column per interior right-hand-side row)
             if (m > 0) {
                 if (!coll_inverse_wpsi(cg, ctx->E, m, gdt, G)) {
                     bad[m] = 1;
                     continue;
                 }
-                for (size_t i = 0; i < G.size(); ++i)
-                    hW[(size_t)m * 2 * N * ni + i] = make_double2(G[i].real(), G[i].imag());
+                for (int i = 0; i < 2 * N; ++i)
+                    for (int j = 0; j < ni; ++j) {
+                        const cplx g = G[(size_t)i * ni + j];
+                        hW[((size_t)m * ni + j) * 2 * N + i] = make_double2(g.real(), g.imag());
+                    }
             }
             if (!coll_inverse_dir(cg, 1.0 / ctx->Pr, (double)m * m, gdt, Gt)) {
                 bad[m] = 1;
                 continue;
             }
-            std::copy(Gt.begin(), Gt.end(), hT.begin() + (size_t)m * N * ni);
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < ni; ++j) hT[((size_t)m * ni + j) * N + i] = Gt[(size_t)i * ni + j];
         }
     };
     unsigned nthr = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
@@ -618,7 +623,13 @@ int build_coll_factors(pizza_ctx* ctx, const CollGrid& cg, double gamma, DevFact
     for (auto& t : th) t.join();
     for (int m = 0; m < M; ++m)
         if (bad[m]) return fail(ctx, PIZZA_EINVAL, "collocation system of mode m=%d is singular", m);
-    if (!coll_inverse_dir(cg, 1.0, 1.0, gdt, hU)) return fail(ctx, PIZZA_EINVAL, "zonal-flow system singular");
+    {
+        std::vector<double> gu;
+        if (!coll_inverse_dir(cg, 1.0, 1.0, gdt, gu)) return fail(ctx, PIZZA_EINVAL, "zonal-flow system singular");
+        hU.resize(gu.size());
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < ni; ++j) hU[(size_t)j * N + i] = gu[(size_t)i * ni + j];
+    }
     F.gdt = gdt;
     auto upload = [&](auto*& dst, const auto& hv) -> int {
         using T = std::remove_reference_t<decltype(*dst)>;

@@ -106,7 +106,7 @@ __device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, d
 // buf1 is scratch of the same size.  Ends with __syncthreads(); returns the buffer
 // holding the result.
 template <int SIGN>
-__device__ static double2* fft_batched(double2* buf0, double2* buf1, const FftPlan& pl, int nb) {
+__device__ __forceinline__ double2* fft_batched(double2* buf0, double2* buf1, const FftPlan& pl, int nb) {
     double2* a = buf0;
     double2* b = buf1;
     int Ns = 1;

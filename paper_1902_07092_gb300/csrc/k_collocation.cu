@@ -170,17 +170,20 @@ __global__ void __launch_bounds__(NT) k_coll_grid_rows(StepParams P, const doubl
 
 // ---------------------------------------------------------------------------
 // Implicit solve: right-hand side r = sum_t c_t V_t on the interior rows, then
-// the grid values of the solution x = G r with the precomputed inverse columns
-// (2 n_r x (n_r-2) complex for (omega, psi), n_r x (n_r-2) real for theta and
-// u_bar).  With the mass term equal to the field itself, the implicit term of the
-// new state follows from its own equation:  imp = (x - r)/(gamma dt).
-// Grid (M, RB): CTA (m, rb) computes one block of the output rows of mode m,
-// one warp per row.  No output vector may alias an input term.
+// the grid values of the solution x = G r with the precomputed inverse columns,
+// stored column-major so that one thread owns one output row and a warp reads
+// 32 consecutive entries of a column: colW [M][n_r-2][2 n_r] (omega, psi; complex),
+// colT [M][n_r-2][n_r] and colU [n_r-2][n_r] (real).  r sits in shared memory and
+// is broadcast.  With the mass term equal to the field itself, the implicit term
+// of the new state follows from its own equation:  imp = (x - r)/(gamma dt).
+// Grid (M, RB): CTA (m, rb) owns rows rb*blockDim .. of mode m; rows of m >= 1
+// are omega (n_r), psi (n_r), theta (n_r); of m = 0 theta (n_r), u_bar (n_r).
+// No output vector may alias an input term.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_coll_solve(StepParams P, RhsSpec R, DevFactors F, VecSet yo, VecSet mo,
                                                    VecSet io, int want_mass, int want_imp) {
     extern __shared__ double2 sm[];
-    const int m = blockIdx.x, rb = blockIdx.y, RB = gridDim.y;
+    const int m = blockIdx.x;
     const int N = P.n_r, ni = N - 2;
     double2* rw = sm;       // interior vorticity rows (m >= 1) or zonal rows (m = 0, real part)
     double2* rt = rw + ni;  // interior temperature rows
@@ -206,79 +209,69 @@ __global__ void __launch_bounds__(NT) k_coll_solve(StepParams P, RhsSpec R, DevF
         rt[j] = at;
     }
     __syncthreads();
+    const int row = blockIdx.y * nth + tid;
     const int nrows = (m > 0) ? 3 * N : 2 * N;
-    const int per = (nrows + RB - 1) / RB;
-    const int r0 = rb * per, r1 = min(nrows, r0 + per);
-    const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
     const double igdt = 1.0 / F.gdt;
-    if (m == 0 && rb == 0) {
-        for (int k = tid; k < N; k += nth) {
-            yo.w[k] = make_double2(0.0, 0.0);
-            yo.psi[k] = make_double2(0.0, 0.0);
-            if (want_mass) mo.w[k] = make_double2(0.0, 0.0);
-            if (want_imp) io.w[k] = make_double2(0.0, 0.0);
+    if (m == 0 && row < N) {
+        yo.w[row] = make_double2(0.0, 0.0);
+        yo.psi[row] = make_double2(0.0, 0.0);
+        if (want_mass) mo.w[row] = make_double2(0.0, 0.0);
+        if (want_imp) io.w[row] = make_double2(0.0, 0.0);
+    }
+    if (row >= nrows) return;
+    // field: 0 omega, 1 psi, 2 theta, 3 u_bar
+    int fld, k;
+    if (m > 0) {
+        fld = row / N;
+        k = row - fld * N;
+    } else {
+        fld = (row < N) ? 2 : 3;
+        k = (row < N) ? row : row - N;
+    }
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+    if (fld <= 1) {
+        const int ld = 2 * N;
+        const double2* g = F.colW + (size_t)m * ni * ld + row;
+        int j = 0;
+        for (; j + 1 < ni; j += 2) {
+            a0 = cfma(__ldg(&g[(size_t)j * ld]), rw[j], a0);
+            a1 = cfma(__ldg(&g[(size_t)(j + 1) * ld]), rw[j + 1], a1);
+        }
+        if (j < ni) a0 = cfma(__ldg(&g[(size_t)j * ld]), rw[j], a0);
+    } else {
+        const double* g = (fld == 2) ? F.colT + (size_t)m * ni * N + k : F.colU + k;
+        const double2* r = (fld == 2) ? rt : rw;
+        int j = 0;
+        for (; j + 1 < ni; j += 2) {
+            const double b0 = __ldg(&g[(size_t)j * N]), b1 = __ldg(&g[(size_t)(j + 1) * N]);
+            a0.x = fma(b0, r[j].x, a0.x);
+            a0.y = fma(b0, r[j].y, a0.y);
+            a1.x = fma(b1, r[j + 1].x, a1.x);
+            a1.y = fma(b1, r[j + 1].y, a1.y);
+        }
+        if (j < ni) {
+            const double b0 = __ldg(&g[(size_t)j * N]);
+            a0.x = fma(b0, r[j].x, a0.x);
+            a0.y = fma(b0, r[j].y, a0.y);
         }
     }
-    for (int row = r0 + warp; row < r1; row += nw) {
-        // field: 0 omega, 1 psi, 2 theta, 3 u_bar
-        int fld, k;
-        if (m > 0) {
-            fld = row / N;
-            k = row - fld * N;
-        } else {
-            fld = (row < N) ? 2 : 3;
-            k = (row < N) ? row : row - N;
-        }
-        double2 acc0 = make_double2(0.0, 0.0), acc1 = make_double2(0.0, 0.0);
-        if (fld <= 1) {
-            const double2* g = F.colW + ((size_t)m * 2 * N + row) * ni;
-            for (int j = lane; j < ni; j += 64) {
-                acc0 = cfma(__ldg(&g[j]), rw[j], acc0);
-                if (j + 32 < ni) acc1 = cfma(__ldg(&g[j + 32]), rw[j + 32], acc1);
-            }
-        } else {
-            const double* g = (fld == 2) ? F.colT + ((size_t)m * N + k) * ni : F.colU + (size_t)k * ni;
-            const double2* r = (fld == 2) ? rt : rw;
-            for (int j = lane; j < ni; j += 64) {
-                const double a = __ldg(&g[j]);
-                acc0.x = fma(a, r[j].x, acc0.x);
-                acc0.y = fma(a, r[j].y, acc0.y);
-                if (j + 32 < ni) {
-                    const double b = __ldg(&g[j + 32]);
-                    acc1.x = fma(b, r[j + 32].x, acc1.x);
-                    acc1.y = fma(b, r[j + 32].y, acc1.y);
-                }
-            }
-        }
-        double2 acc = cadd(acc0, acc1);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-        }
-        if (lane != 0) continue;
-        const size_t idx = (size_t)m * N + k;
-        const bool interior = (k > 0 && k < N - 1);
-        if (fld == 1) {
-            yo.psi[idx] = interior ? acc : make_double2(0.0, 0.0);
-            continue;
-        }
-        double2 imp = make_double2(0.0, 0.0);
-        if (fld == 0) {
-            yo.w[idx] = acc;
-            if (want_mass) mo.w[idx] = acc;
-            if (interior) imp = cscale(csub(acc, rw[k - 1]), igdt);
-            if (want_imp) io.w[idx] = imp;
-        } else if (fld == 2) {
-            yo.th[idx] = acc;
-            if (want_mass) mo.th[idx] = acc;
-            if (interior) imp = cscale(csub(acc, rt[k - 1]), igdt);
-            if (want_imp) io.th[idx] = imp;
-        } else {
-            yo.u[k] = acc.x;
-            if (want_mass) mo.u[k] = acc.x;
-            if (want_imp) io.u[k] = interior ? (acc.x - rw[k - 1].x) * igdt : 0.0;
-        }
+    const double2 acc = cadd(a0, a1);
+    const size_t idx = (size_t)m * N + k;
+    const bool interior = (k > 0 && k < N - 1);
+    if (fld == 1) {
+        yo.psi[idx] = interior ? acc : make_double2(0.0, 0.0);
+    } else if (fld == 0) {
+        yo.w[idx] = acc;
+        if (want_mass) mo.w[idx] = acc;
+        if (want_imp) io.w[idx] = interior ? cscale(csub(acc, rw[k - 1]), igdt) : make_double2(0.0, 0.0);
+    } else if (fld == 2) {
+        yo.th[idx] = acc;
+        if (want_mass) mo.th[idx] = acc;
+        if (want_imp) io.th[idx] = interior ? cscale(csub(acc, rt[k - 1]), igdt) : make_double2(0.0, 0.0);
+    } else {
+        yo.u[k] = acc.x;
+        if (want_mass) mo.u[k] = acc.x;
+        if (want_imp) io.u[k] = interior ? (acc.x - rw[k - 1].x) * igdt : 0.0;
     }
 }
 
@@ -443,17 +436,10 @@ cudaError_t launch_coll_grid_rows(const StepParams& P, const double2* G1, const 
     return cudaGetLastError();
 }
 
-int coll_row_blocks(const StepParams& P) {
-    const int target = 4 * 152;  // a few CTAs per SM
-    int rb = (target + P.M - 1) / P.M;
-    const int maxrb = (2 * P.n_r) / 8;  // at least one row per warp
-    return std::max(1, std::min(rb, maxrb));
-}
-
 cudaError_t launch_coll_solve(const StepParams& P, const RhsSpec& R, const DevFactors& F, VecSet y_out,
                               VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st) {
     const size_t sm = sizeof(double2) * 2 * (P.n_r - 2);
-    dim3 grid(P.M, coll_row_blocks(P));
+    dim3 grid(P.M, (3 * P.n_r + NT - 1) / NT);
     k_coll_solve<<<grid, NT, sm, st>>>(P, R, F, y_out, mass_out, imp_out, want_mass ? 1 : 0, want_imp ? 1 : 0);
     return cudaGetLastError();
 }

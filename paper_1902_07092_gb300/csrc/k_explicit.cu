@@ -172,7 +172,7 @@ __device__ __forceinline__ void store_split_spectrum(const double2* Y, double2* 
     }
 }
 
-__global__ void __launch_bounds__(512) k_phi_products(StepParams P, const double2* __restrict__ G1,
+__global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const double2* __restrict__ G1,
                                                       double2* __restrict__ G2) {
     extern __shared__ double2 sm[];
     const int k = blockIdx.x;

@@ -52,8 +52,8 @@ struct DevFactors {
     // zonal flow, real, H = 4: blocks [nb_t][3][16], Y [n_t][2], Sinv [4], band [n_t][9]
     double *uBlk, *uY, *uSinv, *uBand;
     int refine_t;  // also refine the temperature and zonal-flow solves
-    // collocation: interior-row columns of the grid-valued inverses,
-    // colW [M][2 n_r][n_r-2] (omega_k, psi_k), colT [M][n_r][n_r-2], colU [n_r][n_r-2]
+    // collocation: interior-row columns of the grid-valued inverses, column-major,
+    // colW [M][n_r-2][2 n_r] (omega_k, psi_k), colT [M][n_r-2][n_r], colU [n_r-2][n_r]
     double2* colW;
     double *colT, *colU;
 };

@@ -74,15 +74,26 @@ def zero_state(n_r, n_phi, n_c=None):
     return np.zeros((M, n_c), np.complex128), np.zeros(n_c)
 
 
-# The five workloads (sizes, physical parameters, schemes); Ra is given as a
-# multiple of the critical Rayleigh number at (E, Pr = 1, eta = 0.35).
+# The workloads (sizes, physical parameters, schemes, radial formulation); Ra is
+# given as a multiple of the critical Rayleigh number at (E, Pr = 1, eta = 0.35).
+# "radial": "collocation" (Section 3.1, N_c = n_r) or "integration" (Section 3.2,
+# N_c = floor(2 (n_r - 1)/3)).
 WORKLOADS = {
-    "tiny_n33_p96": dict(n_r=33, n_phi=96, E=1e-3, Pr=1.0, eta=0.35, ra_factor=2.0, scheme="CNAB2",
-                         dt=1e-4, steps=100, amp=1e-4, seed=1, cfg=1),
+    "coll_n33_p96": dict(n_r=33, n_phi=96, E=1e-3, Pr=1.0, eta=0.35, ra_factor=2.0, scheme="CNAB2",
+                         dt=1e-4, steps=100, amp=1e-4, seed=1, cfg=1, radial="collocation"),
+    "int_n33_p96": dict(n_r=33, n_phi=96, E=1e-3, Pr=1.0, eta=0.35, ra_factor=2.0, scheme="CNAB2",
+                        dt=1e-4, steps=100, amp=1e-4, seed=1, cfg=1, radial="integration"),
     "sparse_n257_p768": dict(n_r=257, n_phi=768, E=1e-5, Pr=1.0, eta=0.35, ra_factor=10.0, scheme="ARS443",
-                             dt=1e-7, steps=1000, amp=1e-3, seed=2, cfg=2),
+                             dt=1e-7, steps=1000, amp=1e-3, seed=2, cfg=2, radial="integration"),
+    "coll_n257_p768": dict(n_r=257, n_phi=768, E=1e-5, Pr=1.0, eta=0.35, ra_factor=10.0, scheme="ARS443",
+                           dt=1e-7, steps=1000, amp=1e-3, seed=2, cfg=2, radial="collocation"),
     "large_n2049_p6144": dict(n_r=2049, n_phi=6144, E=1e-8, Pr=1.0, eta=0.35, ra_factor=20.0, scheme="SBDF3",
-                              dt=1e-10, steps=50, amp=1e-3, seed=3, cfg=3),
+                              dt=1e-10, steps=50, amp=1e-3, seed=3, cfg=3, radial="integration"),
     "adjoint_n257_p768": dict(n_r=257, n_phi=768, E=1e-5, Pr=1.0, eta=0.35, ra_factor=5.0, scheme="CNAB2",
-                              dt=1e-7, steps=400, amp=1e-3, seed=5, cfg=5),
+                              dt=1e-7, steps=400, amp=1e-3, seed=5, cfg=5, radial="integration"),
 }
+
+
+def n_c_of(wl):
+    """Coefficients per mode of a workload's formulation."""
+    return wl["n_r"] if wl.get("radial") == "collocation" else n_c_integration(wl["n_r"])
