@@ -158,6 +158,24 @@ def oracle_sample(wl, Ra, budget_s, max_steps):
     return n, t, setup
 
 
+def max_over_ranks(x, world, device=None):
+    """Largest value of x over the ranks of the default process group (x on a
+    single rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(gridpoints, steps, world, total_ms):
+    """Whole-job throughput in Mgridpoint-steps/s: every rank advances its own
+    replica by ``steps`` steps; the job takes the slowest rank's time."""
+    return world * gridpoints * steps / (total_ms / 1e3) / 1e6
+
+
 def cores_used():
     try:
         from threadpoolctl import threadpool_info
@@ -248,11 +266,7 @@ def run_native(args, wl, Ra, rank, world, local_rank):
         total_ms, _ = timed_pass(False)
     barrier()
     torch.cuda.synchronize()
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     # per-kernel pass
     _, (kt, kn) = timed_pass(True)
     # end to end through host buffers
@@ -274,7 +288,7 @@ def run_native(args, wl, Ra, rank, world, local_rank):
     if rank != 0:
         sol.close()
         return
-    value = world * gp * args.steps / (total_ms / 1e3) / 1e6
+    value = job_value(gp, args.steps, world, total_ms)
     flops = algorithmic_flops(n_r, n_phi, wl["scheme"], wl.get("radial", "integration"))
     share = {k: float(kt[i]) / max(float(kt.sum()), 1e-30) for i, k in enumerate(KERNELS)}
     dom = max(range(4), key=lambda i: kt[i])
