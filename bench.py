@@ -210,10 +210,31 @@ def config_of(args, wl, Ra):
             "radial": ("chebyshev-collocation" if wl.get("radial") == "collocation"
                        else "chebyshev-integration-tau"),
             "l2": "flushed (256 MiB write) between timed steps",
-            "parallelism": "replicas" if args.gpus > 1 else "single"}
+            "parallelism": "replicas" if args.gpus > 1 else "single",
+            "precision": ("fp64" if getattr(args, "precision", "fp64") == "fp64"
+                          else "mixed: FP32 explicit stage, FP64 state/history/couplings/solves")}
 
 
 # ------------------------------------------------------------ native arm ----
+def mixed_error(args, B, wl, Ra, sol, th, z, zu):
+    """Relative L2 distance of the mixed-precision state from an FP64 twin started
+    from the same state, after each of min(steps, 50) steps."""
+    ref = B.Solver(wl["n_r"], wl["n_phi"], wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"],
+                   radial=wl.get("radial", "integration"))
+    sol.set_state(th, z, zu)
+    ref.set_state(th, z, zu)
+    errs = []
+    for _ in range(min(args.steps, 50)):
+        sol.step(1)
+        ref.step(1)
+        a = np.concatenate([np.ravel(x) for x in sol.get_state()])
+        b = np.concatenate([np.ravel(x) for x in ref.get_state()])
+        errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+    ref.close()
+    return {"per_step_max": max(errs), "final": errs[-1], "steps": len(errs),
+            "against": "FP64 GPU path (parity-tested against the oracle) from the same state"}
+
+
 def run_native(args, wl, Ra, rank, world, local_rank):
     import torch
     from paper_1902_07092_gb300 import binding as B
@@ -223,6 +244,8 @@ def run_native(args, wl, Ra, rank, world, local_rank):
     gp = n_r * n_phi
     sol = B.Solver(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"],
                    radial=wl.get("radial", "integration"))
+    if args.precision == "mixed":
+        B.pizza_set_option(sol.ctx, "precision", 1)
     # a dedicated stream: the library launches, the L2 flush and the timing events
     # all go to it (torch's default stream handle is 0, which the library reads
     # as "use your own stream")
@@ -284,6 +307,7 @@ def run_native(args, wl, Ra, rank, world, local_rank):
         B.pizza_get_state(sol.ctx, h_th, h_ps, h_u)
     e2e_s = time.perf_counter() - t0
     nbytes = 2 * M * nc * 16 + nc * 8
+    err = mixed_error(args, B, wl, Ra, sol, th, z, zu) if args.precision == "mixed" else None
 
     if rank != 0:
         sol.close()
@@ -297,7 +321,8 @@ def run_native(args, wl, Ra, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
         "config": config_of(args, wl, Ra),
         "e2e": {"value": gp * k_e2e / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "steps": k_e2e},
@@ -310,6 +335,8 @@ def run_native(args, wl, Ra, rank, world, local_rank):
                         "share": share[k], "gflop_per_launch": flops[k] / 1e9} for i, k in enumerate(KERNELS)},
         "clocks": clk.summary(),
     }
+    if err is not None:
+        line["error_vs_fp64"] = err
     if not args.no_cpu_baseline and world == 1:
         n, t_cpu, _ = oracle_sample(wl, Ra, budget_s=args.cpu_budget, max_steps=1000)
         line["cpu_baseline"] = {"value": gp * n / t_cpu / 1e6, "unit": UNIT, "cores": cores_used(),
@@ -326,6 +353,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="sparse_n257_p768", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -85,7 +85,13 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            0 = Chebyshev collocation (Section 3.1; n_r <= PIZZA_COLL_MAX_NR,
  *            else PIZZA_EUNSUPPORTED).  Changing it discards the factored
  *            operators and resets the state to zero and N_c to the new
- *            formulation's value; any other value returns PIZZA_EUNSUPPORTED.
+ *            formulation's value; any other value returns PIZZA_EUNSUPPORTED;
+ *   "precision" 0 = FP64 throughout (default); 1 = mixed: the explicit stage
+ *            (Chebyshev and Fourier transforms, grid products, flux divergences)
+ *            in FP32 on FP32 grid arrays, while the state, the time-scheme
+ *            history, the linear buoyancy and conduction couplings, the banded
+ *            operators, the boundary rows and the solves stay FP64.  Integration
+ *            formulation only (PIZZA_EUNSUPPORTED with collocation).
  * Returns PIZZA_EINVAL for an unknown key or an invalid value. */
 #define PIZZA_COLL_MAX_NR 513
 int pizza_set_option(pizza_ctx *ctx, const char *key, double value);

@@ -802,6 +802,22 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
     up(dtwp, twp.data(), twp.size() * sizeof(double2));
     P.plan_r.tw = dtwr;
     P.plan_p.tw = dtwp;
+    {
+        // the same twiddles rounded to FP32 for the mixed-precision explicit stage
+        std::vector<float2> fr(twr.size()), fp(twp.size());
+        for (size_t i = 0; i < twr.size(); ++i) fr[i] = make_float2((float)twr[i].x, (float)twr[i].y);
+        for (size_t i = 0; i < twp.size(); ++i) fp[i] = make_float2((float)twp[i].x, (float)twp[i].y);
+        float2* ftr = dalloc<float2>(ctx, fr.size(), al);
+        float2* ftp = dalloc<float2>(ctx, fp.size(), al);
+        if (!ftr || !ftp) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(ftr, fr.data(), fr.size() * sizeof(float2));
+        up(ftp, fp.data(), fp.size() * sizeof(float2));
+        P.plan_r.twf = ftr;
+        P.plan_p.twf = ftp;
+    }
 
     // m-independent banded operators and tau rows
     HostOps H = host_ops_of(ctx);
@@ -865,11 +881,22 @@ int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
         ctx->dt_set = true;
         return PIZZA_OK;
     }
+    if (std::strcmp(key, "precision") == 0) {
+        if (value != 0.0 && value != 1.0)
+            return fail(ctx, PIZZA_EUNSUPPORTED, "precision must be 0 (FP64) or 1 (mixed: FP32 explicit stage)");
+        if (value == 1.0 && ctx->coll)
+            return fail(ctx, PIZZA_EUNSUPPORTED, "mixed precision is implemented for the integration formulation");
+        cudaStreamSynchronize(ctx->stream);
+        ctx->P.fp32 = (value == 1.0) ? 1 : 0;
+        return PIZZA_OK;
+    }
     if (std::strcmp(key, "radial") == 0) {
         if (value != 0.0 && value != 1.0)
             return fail(ctx, PIZZA_EUNSUPPORTED, "radial must be 0 (collocation) or 1 (integration)");
         const bool coll = (value == 0.0);
         if (coll == ctx->coll) return PIZZA_OK;
+        if (coll && ctx->P.fp32)
+            return fail(ctx, PIZZA_EUNSUPPORTED, "mixed precision is implemented for the integration formulation");
         if (coll && ctx->n_r > PIZZA_COLL_MAX_NR)
             return fail(ctx, PIZZA_EUNSUPPORTED, "collocation is limited to n_r <= %d", PIZZA_COLL_MAX_NR);
         cudaStreamSynchronize(ctx->stream);
@@ -1035,11 +1062,13 @@ int pizza_diagnostics(pizza_ctx* ctx, pizza_diag* out) {
         CK(cudaMemcpy(ctx->diag_q, q.data(), n_r * sizeof(double), cudaMemcpyHostToDevice));
     }
     VecSet y = ctx->vec[ctx->ys[0]];
+    StepParams P64 = ctx->P;  // diagnostics read FP64 grid fields in either precision mode
+    P64.fp32 = 0;
     if (ctx->coll)
-        CK(launch_coll_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
+        CK(launch_coll_spec_to_grid(P64, y, ctx->G1, ctx->stream));
     else
-        CK(launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
-    CK(launch_diagnostics(ctx->P, ctx->G1, ctx->diag_q, ctx->diag_modes, ctx->diag_radii, ctx->stream));
+        CK(launch_spec_to_grid(P64, y, ctx->G1, ctx->stream));
+    CK(launch_diagnostics(P64, ctx->G1, ctx->diag_q, ctx->diag_modes, ctx->diag_radii, ctx->stream));
     std::vector<double> ms(2 * (size_t)M), rm(2 * (size_t)n_r);
     std::vector<double2> th0(nc);
     CK(cudaMemcpyAsync(ms.data(), ctx->diag_modes, ms.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1089,12 +1118,14 @@ int pizza_get_grid(pizza_ctx* ctx, double* us, double* uphi, double* omega, doub
         if (!ctx->grid_out) return fail(ctx, PIZZA_ENOMEM, "allocation of the grid buffer failed");
     }
     VecSet y = ctx->vec[ctx->ys[0]];
+    StepParams P64 = ctx->P;
+    P64.fp32 = 0;
     if (ctx->coll)
-        CK(launch_coll_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
+        CK(launch_coll_spec_to_grid(P64, y, ctx->G1, ctx->stream));
     else
-        CK(launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream));
+        CK(launch_spec_to_grid(P64, y, ctx->G1, ctx->stream));
     double* g = ctx->grid_out;
-    CK(launch_phi_fields(ctx->P, ctx->G1, g, g + n, g + 2 * n, g + 3 * n, ctx->stream));
+    CK(launch_phi_fields(P64, ctx->G1, g, g + n, g + 2 * n, g + 3 * n, ctx->stream));
     double* outs[4] = {us, uphi, omega, theta};
     for (int f = 0; f < 4; ++f)
         if (outs[f]) CK(cudaMemcpyAsync(outs[f], g + f * n, n * 8, cudaMemcpyDefault, ctx->stream));

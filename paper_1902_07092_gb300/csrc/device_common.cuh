@@ -9,6 +9,7 @@
 
 namespace pz {
 
+// complex arithmetic on double2 (FP64) and float2 (FP32)
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
@@ -27,39 +28,74 @@ __device__ __forceinline__ double2 creflect(double2 a, double2 s) {  // 2a - s
     return make_double2(fma(2.0, a.x, -s.x), fma(2.0, a.y, -s.y));
 }
 
-// One Stockham pass of radix R over a batch of nb transforms of length L.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul_i(float2 a, float t) { return make_float2(-a.y * t, a.x * t); }
+__device__ __forceinline__ float2 cfma(float2 w, float2 b, float2 a) {
+    return make_float2(fmaf(w.x, b.x, fmaf(-w.y, b.y, a.x)), fmaf(w.x, b.y, fmaf(w.y, b.x, a.y)));
+}
+__device__ __forceinline__ float2 creflect(float2 a, float2 s) {
+    return make_float2(fmaf(2.0f, a.x, -s.x), fmaf(2.0f, a.y, -s.y));
+}
+
+// Real type, constructor and conversions of the two complex types.
+template <class T>
+struct Cx;
+template <>
+struct Cx<double2> {
+    using R = double;
+    __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+    __device__ static double2 from(double2 a) { return a; }
+    __device__ static const double2* tw(const FftPlan& p) { return p.tw; }
+};
+template <>
+struct Cx<float2> {
+    using R = float;
+    __device__ static float2 make(double a, double b) { return make_float2((float)a, (float)b); }
+    __device__ static float2 from(double2 a) { return make_float2((float)a.x, (float)a.y); }
+    __device__ static const float2* tw(const FftPlan& p) { return p.twf; }
+};
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2((double)a.x, (double)a.y); }
+
+// One Stockham pass of radix R over a batch of nb transforms of length L, on
+// complex type T (double2 or float2).
 // SIGN = -1: forward  sum_j x_j exp(-2 pi i jk/L);  SIGN = +1: backward (unscaled).
 // In the first pass (Ns = 1) every twiddle factor is 1 and the multiplies are
 // skipped; otherwise the twiddle products are fused into the butterfly adds.
-template <int SIGN, int R, bool FIRST>
-__device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, double2* __restrict__ dst, int L,
-                                              int Ns, const double2* __restrict__ tw, int nb, int tid,
-                                              int nth) {
+template <int SIGN, int R, bool FIRST, class T>
+__device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __restrict__ dst, int L, int Ns,
+                                              const T* __restrict__ tw, int nb, int tid, int nth) {
+    using RT = typename Cx<T>::R;
     const int nbf = L / R;
     const int twmul = L / (Ns * R);
     constexpr bool first = FIRST;
     for (int t = tid; t < nb * nbf; t += nth) {
         const int bt = t / nbf;
         const int j = t - bt * nbf;
-        const double2* s = src + (size_t)bt * L;
-        double2* d = dst + (size_t)bt * L;
+        const T* s = src + (size_t)bt * L;
+        T* d = dst + (size_t)bt * L;
         const int k = j % Ns;
-        double2 v[R];
+        T v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = s[j + r * nbf];
-        double2 w[R];
-        w[0] = make_double2(1.0, 0.0);
+        T w[R];
+        w[0] = Cx<T>::make(1.0, 0.0);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            w[r] = first ? make_double2(1.0, 0.0) : __ldg(&tw[r * k * twmul]);
+            w[r] = first ? Cx<T>::make(1.0, 0.0) : __ldg(&tw[r * k * twmul]);
             if (SIGN > 0) w[r].y = -w[r].y;
         }
         if (R == 2) {
-            double2 y0 = first ? cadd(v[0], v[1]) : cfma(w[1], v[1], v[0]);
+            T y0 = first ? cadd(v[0], v[1]) : cfma(w[1], v[1], v[0]);
             v[1] = first ? csub(v[0], v[1]) : creflect(v[0], y0);
             v[0] = y0;
         } else if (R == 4) {
-            double2 t0, t1, t2, t3;
+            T t0, t1, t2, t3;
             if (first) {
                 t0 = cadd(v[0], v[2]);
                 t1 = csub(v[0], v[2]);
@@ -68,33 +104,51 @@ __device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, d
             } else {
                 t0 = cfma(w[2], v[2], v[0]);          // v0 + w2 v2
                 t1 = creflect(v[0], t0);              // v0 - w2 v2
-                const double2 b1 = cmul(w[1], v[1]);
+                const T b1 = cmul(w[1], v[1]);
                 t2 = cfma(w[3], v[3], b1);            // w1 v1 + w3 v3
                 t3 = creflect(b1, t2);                // w1 v1 - w3 v3
             }
             // forward: -i*t3 ; backward: +i*t3
-            double2 rt = (SIGN < 0) ? make_double2(t3.y, -t3.x) : make_double2(-t3.y, t3.x);
+            T rt;
+            if (SIGN < 0) {
+                rt.x = t3.y;
+                rt.y = -t3.x;
+            } else {
+                rt.x = -t3.y;
+                rt.y = t3.x;
+            }
             v[0] = cadd(t0, t2);
             v[2] = csub(t0, t2);
             v[1] = cadd(t1, rt);
             v[3] = csub(t1, rt);
         } else if (R == 3) {
-            const double h3 = 0.86602540378443864676;  // sqrt(3)/2
-            double2 t1, t2;
+            const RT h3 = (RT)0.86602540378443864676;  // sqrt(3)/2
+            T t1, t2;
             if (first) {
                 t1 = cadd(v[1], v[2]);
                 t2 = csub(v[1], v[2]);
             } else {
-                const double2 b1 = cmul(w[1], v[1]);
+                const T b1 = cmul(w[1], v[1]);
                 t1 = cfma(w[2], v[2], b1);            // w1 v1 + w2 v2
                 t2 = creflect(b1, t1);                // w1 v1 - w2 v2
             }
-            const double2 m1 = make_double2(fma(-0.5, t1.x, v[0].x), fma(-0.5, t1.y, v[0].y));
+            T m1;
+            m1.x = fma((RT)-0.5, t1.x, v[0].x);
+            m1.y = fma((RT)-0.5, t1.y, v[0].y);
             // forward: -i*h3*t2 ; backward: +i*h3*t2
-            const double2 rt = (SIGN < 0) ? make_double2(t2.y, -t2.x) : make_double2(-t2.y, t2.x);
+            T rt;
+            if (SIGN < 0) {
+                rt.x = t2.y;
+                rt.y = -t2.x;
+            } else {
+                rt.x = -t2.y;
+                rt.y = t2.x;
+            }
             v[0] = cadd(v[0], t1);
-            v[1] = make_double2(fma(h3, rt.x, m1.x), fma(h3, rt.y, m1.y));
-            v[2] = make_double2(fma(-h3, rt.x, m1.x), fma(-h3, rt.y, m1.y));
+            v[1].x = fma(h3, rt.x, m1.x);
+            v[1].y = fma(h3, rt.y, m1.y);
+            v[2].x = fma(-h3, rt.x, m1.x);
+            v[2].y = fma(-h3, rt.y, m1.y);
         }
         const int idx = (j / Ns) * Ns * R + k;
 #pragma unroll
@@ -105,32 +159,33 @@ __device__ __forceinline__ void stockham_pass(const double2* __restrict__ src, d
 // Batched FFT of nb transforms stored contiguously in buf0 (each length pl.L);
 // buf1 is scratch of the same size.  Ends with __syncthreads(); returns the buffer
 // holding the result.
-template <int SIGN>
-__device__ __forceinline__ double2* fft_batched(double2* buf0, double2* buf1, const FftPlan& pl, int nb) {
-    double2* a = buf0;
-    double2* b = buf1;
+template <int SIGN, class T>
+__device__ __forceinline__ T* fft_batched(T* buf0, T* buf1, const FftPlan& pl, int nb) {
+    T* a = buf0;
+    T* b = buf1;
     int Ns = 1;
     const int tid = threadIdx.x, nth = blockDim.x;
+    const T* tw = Cx<T>::tw(pl);
     __syncthreads();
     for (int p = 0; p < pl.npass; ++p) {
         const int R = pl.radix[p];
         if (p == 0) {  // Ns == 1: unit twiddles
             if (R == 4)
-                stockham_pass<SIGN, 4, true>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+                stockham_pass<SIGN, 4, true>(a, b, pl.L, Ns, tw, nb, tid, nth);
             else if (R == 2)
-                stockham_pass<SIGN, 2, true>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+                stockham_pass<SIGN, 2, true>(a, b, pl.L, Ns, tw, nb, tid, nth);
             else
-                stockham_pass<SIGN, 3, true>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+                stockham_pass<SIGN, 3, true>(a, b, pl.L, Ns, tw, nb, tid, nth);
         } else {
             if (R == 4)
-                stockham_pass<SIGN, 4, false>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+                stockham_pass<SIGN, 4, false>(a, b, pl.L, Ns, tw, nb, tid, nth);
             else if (R == 2)
-                stockham_pass<SIGN, 2, false>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+                stockham_pass<SIGN, 2, false>(a, b, pl.L, Ns, tw, nb, tid, nth);
             else
-                stockham_pass<SIGN, 3, false>(a, b, pl.L, Ns, pl.tw, nb, tid, nth);
+                stockham_pass<SIGN, 3, false>(a, b, pl.L, Ns, tw, nb, tid, nth);
         }
         __syncthreads();
-        double2* t = a;
+        T* t = a;
         a = b;
         b = t;
         Ns *= R;
@@ -151,15 +206,15 @@ __device__ __forceinline__ double pow2_ratio(double a, double b) {
 
 // CTA-wide max over m < n of |re| + |im| of the nf <= 4 rows src + f*stride,
 // into out[f] (shared).  red: shared scratch of 4*32 doubles.  Whole CTA.
-__device__ __forceinline__ void block_max_abs(const double2* src, int stride, int nf, int n, double* out,
-                                              double* red) {
+template <class T>
+__device__ __forceinline__ void block_max_abs(const T* src, int stride, int nf, int n, double* out, double* red) {
     double mx[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < n; i += blockDim.x)
 #pragma unroll
         for (int f = 0; f < 4; ++f)
             if (f < nf) {
-                const double2 v = src[(size_t)f * stride + i];
-                mx[f] = fmax(mx[f], fabs(v.x) + fabs(v.y));
+                const T v = src[(size_t)f * stride + i];
+                mx[f] = fmax(mx[f], fabs((double)v.x) + fabs((double)v.y));
             }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -179,7 +234,8 @@ __device__ __forceinline__ void block_max_abs(const double2* src, int stride, in
 // Load the even extension of coefficients a_0..a_K (complex) into z (length 2K):
 // z_j = a_j (j <= K), z_{2K-j} = a_j.  The FFT of z then gives
 // Z_n = 2 sum''_{j=0..K} a_j cos(pi n j/K),  n = 0..K (the DCT-I core).
-__device__ __forceinline__ void even_extend_store(double2* z, int K, int j, double2 aj) {
+template <class T>
+__device__ __forceinline__ void even_extend_store(T* z, int K, int j, T aj) {
     z[j] = aj;
     if (j > 0 && j < K) z[2 * K - j] = aj;
 }
@@ -190,35 +246,37 @@ __device__ __forceinline__ void even_extend_store(double2* z, int K, int j, doub
 // warp q (q = 0, 1) owns the indices k = 2i + q; each lane sums a contiguous
 // chunk sequentially, a shuffle scan adds the totals of the chunks above it.
 // ``tmp`` is scratch of n entries.  Must be called by the whole CTA (>= 64 threads).
-__device__ __noinline__ static void cheb_derivative_scan(const double2* c, double2* d, double2* tmp, int n,
-                                                         double scale) {
+template <class T>
+__device__ __forceinline__ void cheb_derivative_scan(const T* c, T* d, T* tmp, int n, double scale) {
+    using RT = typename Cx<T>::R;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 2) {
         const int q = warp;
         const int len = (n - q + 1) / 2;  // number of k = 2i + q below n
         const int per = (len + 31) / 32;
         const int i0 = lane * per, i1 = min(i0 + per, len);
-        double2 acc = make_double2(0.0, 0.0);
+        T acc = Cx<T>::make(0.0, 0.0);
         for (int i = i1 - 1; i >= i0; --i) {
             const int k = 2 * i + q;
             if (k > 0) {
-                const double f = (double)(2 * k);
-                acc = make_double2(fma(f, c[k].x, acc.x), fma(f, c[k].y, acc.y));
+                const RT f = (RT)(2 * k);
+                acc.x = fma(f, c[k].x, acc.x);
+                acc.y = fma(f, c[k].y, acc.y);
             }
             tmp[k] = acc;
         }
         // inclusive suffix scan of the chunk totals over the lanes
-        double2 sfx = acc;
+        T sfx = acc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const double x = __shfl_down_sync(0xffffffffu, sfx.x, o);
-            const double y = __shfl_down_sync(0xffffffffu, sfx.y, o);
+            const RT x = __shfl_down_sync(0xffffffffu, sfx.x, o);
+            const RT y = __shfl_down_sync(0xffffffffu, sfx.y, o);
             if (lane + o < 32) {
                 sfx.x += x;
                 sfx.y += y;
             }
         }
-        const double2 off = csub(sfx, acc);  // totals of the chunks above this one
+        const T off = csub(sfx, acc);  // totals of the chunks above this one
         for (int i = i0; i < i1; ++i) {
             const int k = 2 * i + q;
             tmp[k] = cadd(tmp[k], off);
@@ -226,8 +284,8 @@ __device__ __noinline__ static void cheb_derivative_scan(const double2* c, doubl
     }
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double f = (j == 0) ? 0.5 * scale : scale;
-        d[j] = (j + 1 < n) ? cscale(tmp[j + 1], f) : make_double2(0.0, 0.0);
+        const RT f = (RT)((j == 0) ? 0.5 * scale : scale);
+        d[j] = (j + 1 < n) ? cscale(tmp[j + 1], f) : Cx<T>::make(0.0, 0.0);
     }
     __syncthreads();
 }

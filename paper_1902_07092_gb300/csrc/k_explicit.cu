@@ -33,27 +33,30 @@ __host__ __device__ inline int radial_batch(int L) { return L <= 1024 ? 2 : 1; }
 // (Section 3.2: u_s = (h^2/s) dPsi/dphi, u_phi = u_bar - h^2 dPsi/ds + 3 s Psi,
 //  omega = (1/s) d(s u_bar)/ds - L_I Psi.)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSet y, double2* __restrict__ G1) {
-    extern __shared__ double2 sm[];
+template <class T>
+__global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSet y, T* __restrict__ G1) {
+    using RT = typename Cx<T>::R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
     const int m = blockIdx.x;
     const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
     const int NB = radial_batch(L);
-    double2* bufA = sm;
-    double2* bufB = bufA + NB * L;
-    double2* cc0 = bufB + NB * L;  // Psi (or u_bar) plain coefficients, length N
-    double2* cc1 = cc0 + N;        // first derivative
-    double2* cc2 = cc1 + N;        // second derivative
+    T* bufA = sm;
+    T* bufB = bufA + NB * L;
+    T* cc0 = bufB + NB * L;  // Psi (or u_bar) plain coefficients, length N
+    T* cc1 = cc0 + N;        // first derivative
+    T* cc2 = cc1 + N;        // second derivative
     const int tid = threadIdx.x, nth = blockDim.x;
     const double C = P.cnorm;
 
     for (int n = tid; n < N; n += nth) {
-        double2 a = make_double2(0.0, 0.0);
+        T a = Cx<T>::make(0.0, 0.0);
         if (n < nc) {
             const double w = (n == 0) ? 0.5 * C : C;
             if (m > 0)
-                a = cscale(y.psi[(size_t)m * nc + n], w);
+                a = Cx<T>::from(cscale(y.psi[(size_t)m * nc + n], w));
             else
-                a = make_double2(y.u[n] * w, 0.0);
+                a = Cx<T>::make(y.u[n] * w, 0.0);
         }
         cc0[n] = a;
     }
@@ -64,10 +67,10 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
     // field list: 0 Psi, 1 Psi', 2 Psi'', 3 theta, 4 packed u_bar + i lam u_bar'
     // (lam a power of two balancing the two parts)
     __shared__ double red[4 * 32], mx[4];
-    double lam = 1.0;
+    RT lam = 1;
     if (m == 0) {
         block_max_abs(cc0, N, 2, N, mx, red);
-        lam = pow2_ratio(mx[0], mx[1]);
+        lam = (RT)pow2_ratio(mx[0], mx[1]);
     }
     int fields[4];
     int nf;
@@ -76,48 +79,52 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
     } else {
         fields[0] = 4; fields[1] = 3; nf = 2;
     }
-    const double dm = (double)m;
+    const RT dm = (RT)m;
     for (int f0 = 0; f0 < nf; f0 += NB) {
         const int nb = min(NB, nf - f0);
         for (int b = 0; b < nb; ++b) {
             const int fid = fields[f0 + b];
-            double2* z = bufA + b * L;
+            T* z = bufA + b * L;
             for (int j = tid; j <= K; j += nth) {
-                double2 v;
+                T v;
                 if (fid == 0) v = cc0[j];
                 else if (fid == 1) v = cc1[j];
                 else if (fid == 2) v = cc2[j];
                 else if (fid == 3)
-                    v = (j < nc) ? cscale(y.th[(size_t)m * nc + j], (j == 0) ? 0.5 * C : C) : make_double2(0.0, 0.0);
-                else v = make_double2(cc0[j].x, lam * cc1[j].x);
-                if (j == 0 || j == K) v = cscale(v, 2.0);
+                    v = (j < nc) ? Cx<T>::from(cscale(y.th[(size_t)m * nc + j], (j == 0) ? 0.5 * C : C))
+                                 : Cx<T>::make(0.0, 0.0);
+                else {
+                    v.x = cc0[j].x;
+                    v.y = lam * cc1[j].x;
+                }
+                if (j == 0 || j == K) v = cscale(v, (RT)2);
                 even_extend_store(z, K, j, v);
             }
         }
-        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
         for (int b = 0; b < nb; ++b) {
             const int fid = fields[f0 + b];
-            const double2* Z = R + b * L;
+            const T* Z = R + b * L;
             for (int k = tid; k < N; k += nth) {
-                const double2 g = cscale(Z[k], 0.5);  // value of the series at x_k
-                const double s = P.s[k], h2 = P.h2[k], is = P.inv_s[k];
-                double2* out = G1 + g_index(k, 0, m, M);
+                const T g = cscale(Z[k], (RT)0.5);  // value of the series at x_k
+                const RT s = (RT)P.s[k], h2 = (RT)P.h2[k], is = (RT)P.inv_s[k];
+                T* out = G1 + g_index(k, 0, m, M);
                 // out[0] = v, out[M] = u_phi, out[2M] = omega, out[3M] = theta
                 if (fid == 0) {
                     out[0] = cmul_i(g, dm);
-                    out[M] = cscale(g, 3.0 * s);
-                    out[2 * M] = cscale(g, 6.0 + dm * dm * h2 * is * is);
+                    out[M] = cscale(g, (RT)3 * s);
+                    out[2 * M] = cscale(g, (RT)6 + dm * dm * h2 * is * is);
                 } else if (fid == 1) {
                     out[M] = csub(out[M], cscale(g, h2));
-                    out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - 5.0 * s));
+                    out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - (RT)5 * s));
                 } else if (fid == 2) {
                     out[2 * M] = csub(out[2 * M], cscale(g, h2));
                 } else if (fid == 3) {
                     out[3 * M] = g;
                 } else {
-                    out[0] = make_double2(0.0, 0.0);
-                    out[M] = make_double2(g.x, 0.0);
-                    out[2 * M] = make_double2(g.y / lam + g.x * is, 0.0);
+                    out[0] = Cx<T>::make(0.0, 0.0);
+                    out[M] = Cx<T>::make(g.x, 0.0);
+                    out[2 * M] = Cx<T>::make(g.y / lam + g.x * is, 0.0);
                 }
             }
         }
@@ -131,21 +138,25 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
 // transform: g1 = v + i u_phi, g2 = omega + i theta; then
 //   g1 * Re(g2) = v omega + i u_phi omega,  g1 * Im(g2) = v theta + i u_phi theta.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void load_packed_spectrum(double2* Z, const double2* __restrict__ src, int M, int Pn,
-                                                     int n_m, double sa, double sb) {
+template <class T>
+__device__ __forceinline__ void load_packed_spectrum(T* Z, const T* __restrict__ src, int M, int Pn, int n_m,
+                                                     typename Cx<T>::R sa, typename Cx<T>::R sb) {
     // src points at G1/G2 row (k, f): field a = src[0..M), field b = src[M..2M);
     // packed as sa a + i sb b
     for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
-        double2 z = make_double2(0.0, 0.0);
+        T z = Cx<T>::make(0.0, 0.0);
         if (j == 0) {
-            z = make_double2(sa * src[0].x, sb * src[M].x);
+            z.x = sa * src[0].x;
+            z.y = sb * src[M].x;
         } else if (j <= n_m) {
-            const double2 a = cscale(src[j], sa), b = cscale(src[M + j], sb);
-            z = make_double2(a.x - b.y, a.y + b.x);  // a + i b
+            const T a = cscale(src[j], sa), b = cscale(src[M + j], sb);
+            z.x = a.x - b.y;  // a + i b
+            z.y = a.y + b.x;
         } else if (j >= Pn - n_m) {
             const int mm = Pn - j;
-            const double2 a = cscale(src[mm], sa), b = cscale(src[M + mm], sb);
-            z = make_double2(a.x + b.y, -a.y + b.x);  // conj(a) + i conj(b)
+            const T a = cscale(src[mm], sa), b = cscale(src[M + mm], sb);
+            z.x = a.x + b.y;  // conj(a) + i conj(b)
+            z.y = -a.y + b.x;
         }
         Z[j] = z;
     }
@@ -153,61 +164,77 @@ __device__ __forceinline__ void load_packed_spectrum(double2* Z, const double2* 
 
 // Split the transform Y of a + i b (a, b real fields) into the spectra of a and
 // b, scaled by sa / Pn and sb / Pn.
-__device__ __forceinline__ void store_split_spectrum(const double2* Y, double2* __restrict__ dst, int M, int Pn,
-                                                     int n_m, double sa, double sb) {
-    const double ia = sa / (double)Pn, ib = sb / (double)Pn;
+template <class T>
+__device__ __forceinline__ void store_split_spectrum(const T* Y, T* __restrict__ dst, int M, int Pn, int n_m,
+                                                     double sa, double sb) {
+    using RT = typename Cx<T>::R;
+    const RT ia = (RT)(sa / (double)Pn), ib = (RT)(sb / (double)Pn);
+    const RT h = (RT)0.5;
     for (int m = threadIdx.x; m <= n_m; m += blockDim.x) {
-        double2 a, b;
+        T a, b;
         if (m == 0) {
-            a = make_double2(Y[0].x * ia, 0.0);
-            b = make_double2(Y[0].y * ib, 0.0);
+            a = Cx<T>::make(Y[0].x * ia, 0.0);
+            b = Cx<T>::make(Y[0].y * ib, 0.0);
         } else {
-            const double2 y1 = Y[m], y2 = Y[Pn - m];
+            const T y1 = Y[m], y2 = Y[Pn - m];
             // a = (y1 + conj(y2))/2,  b = (y1 - conj(y2))/(2i)
-            a = make_double2(0.5 * (y1.x + y2.x) * ia, 0.5 * (y1.y - y2.y) * ia);
-            b = make_double2(0.5 * (y1.y + y2.y) * ib, -0.5 * (y1.x - y2.x) * ib);
+            a.x = h * (y1.x + y2.x) * ia;
+            a.y = h * (y1.y - y2.y) * ia;
+            b.x = h * (y1.y + y2.y) * ib;
+            b.y = -h * (y1.x - y2.x) * ib;
         }
         dst[m] = a;
         dst[M + m] = b;
     }
 }
 
-__global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const double2* __restrict__ G1,
-                                                      double2* __restrict__ G2) {
-    extern __shared__ double2 sm[];
+// balancing weights are limited further in FP32 (exponent range of float)
+template <class T>
+__device__ __forceinline__ double pow2_ratio_t(double a, double b) {
+    const double r = pow2_ratio(a, b);
+    if (sizeof(typename Cx<T>::R) == 8) return r;
+    return fmin(fmax(r, 0x1p-40), 0x1p40);
+}
+
+template <class T>
+__global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* __restrict__ G1,
+                                                         T* __restrict__ G2) {
+    using RT = typename Cx<T>::R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
     const int k = blockIdx.x;
     const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
-    double2* X = sm;
-    double2* Y = sm + Pn;
+    T* X = sm;
+    T* Y = sm + Pn;
     const int tid = threadIdx.x, nth = blockDim.x;
-    double2 reg[MAXPER];
+    T reg[MAXPER];
     // exact power-of-two weights that balance the packed pairs:
     // g1 = v + i l1 u_phi, g2 = omega + i l2 theta
     __shared__ double red[4 * 32], mx[4];
     block_max_abs(G1 + g_index(k, 0, 0, M), M, 4, n_m + 1, mx, red);
-    const double l1 = pow2_ratio(mx[0], mx[1]), l2 = pow2_ratio(mx[2], mx[3]);
+    const double l1 = pow2_ratio_t<T>(mx[0], mx[1]), l2 = pow2_ratio_t<T>(mx[2], mx[3]);
 
-    load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, 1.0, l1);
-    double2* R = fft_batched<+1>(X, Y, P.plan_p, 1);
+    load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, (RT)1, (RT)l1);
+    T* R = fft_batched<+1>(X, Y, P.plan_p, 1);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
         const int j = tid + i * nth;
         if (j < Pn) reg[i] = R[j];
     }
     __syncthreads();
-    load_packed_spectrum(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m, 1.0, l2);
+    load_packed_spectrum(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m, (RT)1, (RT)l2);
     R = fft_batched<+1>(X, Y, P.plan_p, 1);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
         const int j = tid + i * nth;
         if (j < Pn) {
-            const double2 g2 = R[j], g1 = reg[i];
+            const T g2 = R[j], g1 = reg[i];
             R[j] = cscale(g1, g2.x);
             reg[i] = cscale(g1, g2.y);
         }
     }
-    double2* other = (R == X) ? Y : X;
-    double2* S = fft_batched<-1>(R, other, P.plan_p, 1);
+    T* other = (R == X) ? Y : X;
+    T* S = fft_batched<-1>(R, other, P.plan_p, 1);
     // g1 Re(g2) = v omega + i l1 u_phi omega
     store_split_spectrum(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, 1.0, 1.0 / l1);
     __syncthreads();
@@ -233,8 +260,8 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const dou
 // (Eqs. vort, temp, uphi; psi_int, temp_int, uphi_int; u_s = (h^2/s) v and
 //  beta u_s = -v.)  The radial derivative is that of the n_r-point interpolant.
 // ---------------------------------------------------------------------------
-template <int H>
-__device__ __forceinline__ double2 band_row(const double* __restrict__ band, const double2* x, int k, int nc) {
+template <int H, class V>
+__device__ __forceinline__ double2 band_row(const double* __restrict__ band, const V* x, int k, int nc) {
     const double* row = band + (size_t)k * (2 * H + 1);
     double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
@@ -242,43 +269,47 @@ __device__ __forceinline__ double2 band_row(const double* __restrict__ band, con
         const int n = k - H + d;
         if (n >= 0 && n < nc) {
             const double c = __ldg(&row[d]);
-            acc.x = fma(c, x[n].x, acc.x);
-            acc.y = fma(c, x[n].y, acc.y);
+            const double2 v = to_d2(x[n]);
+            acc.x = fma(c, v.x, acc.x);
+            acc.y = fma(c, v.y, acc.y);
         }
     }
     return acc;
 }
 
-__global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const double2* __restrict__ G2, VecSet y,
+template <class T>
+__global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const T* __restrict__ G2, VecSet y,
                                                              VecSet e) {
-    extern __shared__ double2 sm[];
+    using RT = typename Cx<T>::R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
     const int m = blockIdx.x;
     const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
     const int NB = radial_batch(L);
-    double2* bufA = sm;
-    double2* bufB = bufA + NB * L;
-    double2* cc0 = bufB + NB * L;
-    double2* cc1 = cc0 + N;
-    double2* cc2 = cc1 + N;
+    T* bufA = sm;
+    T* bufB = bufA + NB * L;
+    T* cc0 = bufB + NB * L;
+    T* cc1 = cc0 + N;
+    T* cc2 = cc1 + N;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const double dm = (double)m;
+    const RT dm = (RT)m;
 
     // pass A: plain Chebyshev coefficients of F1 = h^2 [v omega]_m, F2 = h^2 [v theta]_m
     for (int b0 = 0; b0 < 2; b0 += NB) {
         const int nb = min(NB, 2 - b0);
         for (int b = 0; b < nb; ++b) {
             const int f = (b0 + b == 0) ? 0 : 2;
-            double2* z = bufA + b * L;
+            T* z = bufA + b * L;
             for (int j = tid; j <= K; j += nth)
-                even_extend_store(z, K, j, cscale(G2[g_index(j, f, m, M)], P.h2[j]));
+                even_extend_store(z, K, j, cscale(G2[g_index(j, f, m, M)], (RT)P.h2[j]));
         }
-        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
         for (int b = 0; b < nb; ++b) {
-            double2* dst = (b0 + b == 0) ? cc0 : cc1;
-            const double2* Z = R + b * L;
+            T* dst = (b0 + b == 0) ? cc0 : cc1;
+            const T* Z = R + b * L;
             for (int n = tid; n <= K; n += nth) {
                 const double w = (n == 0 || n == K) ? 0.5 : 1.0;
-                dst[n] = cscale(Z[n], w / (double)K);
+                dst[n] = cscale(Z[n], (RT)(w / (double)K));
             }
         }
         __syncthreads();
@@ -292,41 +323,39 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
     __syncthreads();
 
     // pass B: derivative values on the grid, then N_omega (or N_u) and N_theta
-    double2* Nbuf = nullptr;
     for (int b0 = 0; b0 < 2; b0 += NB) {
         const int nb = min(NB, 2 - b0);
         for (int b = 0; b < nb; ++b) {
-            const double2* c = (b0 + b == 0) ? cc0 : cc1;
-            double2* z = bufA + b * L;
+            const T* c = (b0 + b == 0) ? cc0 : cc1;
+            T* z = bufA + b * L;
             for (int j = tid; j <= K; j += nth) {
-                double2 v = c[j];
-                if (j == 0 || j == K) v = cscale(v, 2.0);
+                T v = c[j];
+                if (j == 0 || j == K) v = cscale(v, (RT)2);
                 even_extend_store(z, K, j, v);
             }
         }
-        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
-        // nonlinear terms into the even-extension input of pass C, held in the
-        // buffer not holding R (pass C input area must survive: for NB == 1 the two
-        // fields are processed one after the other through cc2 / cc0 staging)
+        T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        // the grid values of N go to cc2 (omega) and cc0 (theta): cc0 was consumed
+        // by the loads above (for NB == 1 the theta pass runs after the omega one)
         for (int b = 0; b < nb; ++b) {
             const int fld = b0 + b;  // 0: omega, 1: theta
-            const double2* Z = R + b * L;
-            double2* dst = (fld == 0) ? cc2 : cc0;  // grid values of N (length N)
+            const T* Z = R + b * L;
+            T* dst = (fld == 0) ? cc2 : cc0;
             for (int k = tid; k <= K; k += nth) {
-                const double2 dF = cscale(Z[k], 0.5);
-                const double is = P.inv_s[k];
-                double2 val;
+                const T dF = cscale(Z[k], (RT)0.5);
+                const RT is = (RT)P.inv_s[k];
+                T val;
                 if (fld == 0) {
                     if (m > 0) {
-                        const double2 uw = G2[g_index(k, 1, m, M)];
+                        const T uw = G2[g_index(k, 1, m, M)];
                         val = cscale(cadd(dF, cmul_i(uw, dm)), is);
                     } else {
-                        const double2 vw = G2[g_index(k, 0, m, M)];
-                        val = cscale(vw, P.h2[k] * is);
+                        const T vw = G2[g_index(k, 0, m, M)];
+                        val = cscale(vw, (RT)P.h2[k] * is);
                     }
                 } else {
-                    const double2 ut = G2[g_index(k, 3, m, M)];
-                    const double2 vt = G2[g_index(k, 2, m, M)];
+                    const T ut = G2[g_index(k, 3, m, M)];
+                    const T vt = G2[g_index(k, 2, m, M)];
                     val = csub(cscale(cadd(dF, cmul_i(ut, dm)), is), vt);
                 }
                 dst[k] = val;
@@ -334,42 +363,43 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
         }
         __syncthreads();
     }
-    (void)Nbuf;
     // pass C: Eq. icheb of N_omega (cc2) and N_theta (cc0), truncated to n < nc
     for (int b0 = 0; b0 < 2; b0 += NB) {
         const int nb = min(NB, 2 - b0);
         for (int b = 0; b < nb; ++b) {
-            const double2* src = (b0 + b == 0) ? cc2 : cc0;
-            double2* z = bufA + b * L;
+            const T* src = (b0 + b == 0) ? cc2 : cc0;
+            T* z = bufA + b * L;
             for (int j = tid; j <= K; j += nth) even_extend_store(z, K, j, src[j]);
         }
-        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
         for (int b = 0; b < nb; ++b) {
-            double2* dst = (b0 + b == 0) ? cc1 : cc2;  // N_omega_hat -> cc1, N_theta_hat -> cc2
-            const double2* Z = R + b * L;
-            // careful: for NB == 1 the theta pass reads cc0 and writes cc2, which
-            // already holds nothing needed any more (N_omega_hat went to cc1).
-            for (int n = tid; n < nc; n += nth) dst[n] = cscale(Z[n], 0.5 * P.cnorm);
+            T* dst = (b0 + b == 0) ? cc1 : cc2;  // N_omega_hat -> cc1, N_theta_hat -> cc2
+            const T* Z = R + b * L;
+            // for NB == 1 the theta pass reads cc0 and writes cc2, which holds
+            // nothing needed any more (N_omega_hat went to cc1)
+            for (int n = tid; n < nc; n += nth) dst[n] = cscale(Z[n], (RT)(0.5 * P.cnorm));
         }
         __syncthreads();
     }
-    // integrated right-hand sides
-    // psi: x = (Ra/Pr)(i m/s_o) theta_hat + N_omega_hat  (into cc0), then C^I
-    const double bfac = P.Ra / P.Pr * dm / P.s_o;
-    for (int n = tid; n < nc; n += nth) {
-        const double2 th = y.th[(size_t)m * nc + n];
-        cc0[n] = cadd(cc1[n], cmul_i(th, bfac));
-        // Psi_hat_m for the conduction term, into bufA
-        bufA[n] = (m > 0) ? y.psi[(size_t)m * nc + n] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
+    // integrated right-hand sides; the linear couplings read the FP64 state
+    //   e_psi = C^I N_omega_hat + (Ra/Pr)(i m/s_o) C^I theta_hat
+    //   e_theta = -D^I N_theta_hat - (alpha/ln eta) i m G^I Psi_hat,  e_u = -D^I N_u_hat
+    const double bfac = P.Ra / P.Pr * (double)m / P.s_o;
+    const double2* th_m = y.th + (size_t)m * nc;
+    const double2* ps_m = y.psi + (size_t)m * nc;
     for (int k = tid; k < nc; k += nth) {
         double2 ep = make_double2(0.0, 0.0), et = make_double2(0.0, 0.0);
-        if (k >= 4 && m > 0) ep = band_row<8>(P.ops.band[OP_C], cc0, k, nc);
+        if (k >= 4 && m > 0)
+            ep = cadd(band_row<8>(P.ops.band[OP_C], cc1, k, nc),
+                      cmul_i(band_row<8>(P.ops.band[OP_C], th_m, k, nc), bfac));
         if (k >= 2) {
             const double2 dn = band_row<4>(P.ops.band[OP_D], cc2, k, nc);
-            const double2 gp = band_row<4>(P.ops.band[OP_G], bufA, k, nc);
-            et = csub(cmul_i(gp, -P.tc * dm), dn);
+            if (m > 0) {
+                const double2 gp = band_row<4>(P.ops.band[OP_G], ps_m, k, nc);
+                et = csub(cmul_i(gp, -P.tc * (double)m), dn);
+            } else {
+                et = cscale(dn, -1.0);
+            }
         }
         e.psi[(size_t)m * nc + k] = ep;
         e.th[(size_t)m * nc + k] = et;
@@ -519,38 +549,55 @@ cudaError_t launch_phi_fields(const StepParams& P, const double2* G1, double* us
 
 size_t smem_spec_to_grid(const StepParams& P) {
     const int L = 2 * P.K;
-    return sizeof(double2) * (2 * radial_batch(L) * L + 3 * P.n_r);
+    const size_t c = P.fp32 ? sizeof(float2) : sizeof(double2);
+    return c * (2 * radial_batch(L) * L + 3 * P.n_r);
 }
-size_t smem_phi_products(const StepParams& P) { return sizeof(double2) * 2 * P.n_phi; }
-size_t smem_grid_to_spec(const StepParams& P) {
-    const int L = 2 * P.K;
-    return sizeof(double2) * (2 * radial_batch(L) * L + 3 * P.n_r);
+size_t smem_phi_products(const StepParams& P) {
+    return (P.fp32 ? sizeof(float2) : sizeof(double2)) * 2 * P.n_phi;
 }
+size_t smem_grid_to_spec(const StepParams& P) { return smem_spec_to_grid(P); }
 
-cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st) {
+// The explicit stage runs on double2 (FP64) or float2 (option "precision" =
+// mixed) grid arrays; G1, G2 hold either type.
+template <class T>
+static cudaError_t spec_to_grid_t(const StepParams& P, VecSet y, void* G1, cudaStream_t st) {
     const size_t sm = smem_spec_to_grid(P);
-    cudaError_t err = cudaFuncSetAttribute(k_spec_to_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t err = cudaFuncSetAttribute(k_spec_to_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    k_spec_to_grid<<<P.M, NTHREADS_R, sm, st>>>(P, y, G1);
+    k_spec_to_grid<T><<<P.M, NTHREADS_R, sm, st>>>(P, y, static_cast<T*>(G1));
     return cudaGetLastError();
 }
 
-cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2* G2, cudaStream_t st) {
+template <class T>
+static cudaError_t phi_products_t(const StepParams& P, const void* G1, void* G2, cudaStream_t st) {
     const size_t sm = smem_phi_products(P);
     const int nth = P.n_phi > 256 * MAXPER ? 512 : 256;
     if (P.n_phi > nth * MAXPER) return cudaErrorInvalidValue;
-    cudaError_t err = cudaFuncSetAttribute(k_phi_products, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t err = cudaFuncSetAttribute(k_phi_products<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    k_phi_products<<<P.n_r, nth, sm, st>>>(P, G1, G2);
+    k_phi_products<T><<<P.n_r, nth, sm, st>>>(P, static_cast<const T*>(G1), static_cast<T*>(G2));
     return cudaGetLastError();
 }
 
-cudaError_t launch_grid_to_spec(const StepParams& P, const double2* G2, VecSet y, VecSet e, cudaStream_t st) {
+template <class T>
+static cudaError_t grid_to_spec_t(const StepParams& P, const void* G2, VecSet y, VecSet e, cudaStream_t st) {
     const size_t sm = smem_grid_to_spec(P);
-    cudaError_t err = cudaFuncSetAttribute(k_grid_to_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t err = cudaFuncSetAttribute(k_grid_to_spec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    k_grid_to_spec<<<P.M, NTHREADS_R, sm, st>>>(P, G2, y, e);
+    k_grid_to_spec<T><<<P.M, NTHREADS_R, sm, st>>>(P, static_cast<const T*>(G2), y, e);
     return cudaGetLastError();
+}
+
+cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st) {
+    return P.fp32 ? spec_to_grid_t<float2>(P, y, G1, st) : spec_to_grid_t<double2>(P, y, G1, st);
+}
+
+cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2* G2, cudaStream_t st) {
+    return P.fp32 ? phi_products_t<float2>(P, G1, G2, st) : phi_products_t<double2>(P, G1, G2, st);
+}
+
+cudaError_t launch_grid_to_spec(const StepParams& P, const double2* G2, VecSet y, VecSet e, cudaStream_t st) {
+    return P.fp32 ? grid_to_spec_t<float2>(P, G2, y, e, st) : grid_to_spec_t<double2>(P, G2, y, e, st);
 }
 
 }  // namespace pz

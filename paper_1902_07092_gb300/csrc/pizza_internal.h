@@ -18,6 +18,7 @@ struct FftPlan {
     int npass;
     int radix[MAX_PASSES];
     const double2* tw;  // tw[j] = exp(-2 pi i j / L), j < L
+    const float2* twf;  // the same, rounded to FP32 (mixed-precision explicit stage)
 };
 
 // One set of per-field vectors: Psi and theta complex [M][nc], u real [nc]; the
@@ -68,6 +69,8 @@ struct StepParams {
     FftPlan plan_r;       // length 2K (radial DCT-I)
     FftPlan plan_p;       // length n_phi (azimuthal)
     DevOps ops;
+    // explicit stage in FP32 (option "precision" = mixed): 1 when selected
+    int fp32;
     // collocation formulation (Section 3.1): 1 when selected
     int coll;
     const double* beta;   // [n_r] beta = -s/h^2, 0 at s_o
