@@ -223,16 +223,21 @@ def mixed_error(args, B, wl, Ra, sol, th, z, zu):
                    radial=wl.get("radial", "integration"))
     sol.set_state(th, z, zu)
     ref.set_state(th, z, zu)
-    errs = []
-    for _ in range(min(args.steps, 50)):
+    errs, bad = [], []
+    for k in range(min(args.steps, 50)):
         sol.step(1)
         ref.step(1)
         a = np.concatenate([np.ravel(x) for x in sol.get_state()])
         b = np.concatenate([np.ravel(x) for x in ref.get_state()])
+        if not (np.all(np.isfinite(a)) and np.all(np.isfinite(b))):
+            bad.append([k + 1, bool(np.all(np.isfinite(a))), bool(np.all(np.isfinite(b)))])
         errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
     ref.close()
-    return {"per_step_max": max(errs), "final": errs[-1], "steps": len(errs),
-            "against": "FP64 GPU path (parity-tested against the oracle) from the same state"}
+    out = {"per_step_max": float(np.max(errs)), "final": errs[-1], "steps": len(errs),
+           "against": "FP64 GPU path (parity-tested against the oracle) from the same state"}
+    if bad:
+        out["nonfinite"] = bad[:5]  # [step, mixed finite, FP64 finite]
+    return out
 
 
 def run_native(args, wl, Ra, rank, world, local_rank):

@@ -204,7 +204,7 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
                     continue;
                 }
                 std::vector<cplx> blk;
-                if (!block_lu(bp, nc, 8, 4, blk)) {
+                if (!block_lu_twisted(bp, nc, 8, 4, blk)) {
                     bad[m] = 1;
                     continue;
                 }
@@ -230,7 +230,7 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
             }
             std::copy(bt.begin() + 2 * 9, bt.end(), htB.begin() + (size_t)m * nt * 9);
             std::vector<double> tb;
-            if (!block_lu(bt, nc, 4, 2, tb)) {
+            if (!block_lu_twisted(bt, nc, 4, 2, tb)) {
                 bad[m] = 1;
                 continue;
             }
@@ -269,7 +269,7 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         CK(cudaMemcpy(dst, (hv).data(), (hv).size() * sizeof(T), cudaMemcpyHostToDevice));       \
     } while (0)
     std::vector<double> ub;
-    if (!block_lu(bu, nc, 4, 2, ub)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
+    if (!block_lu_twisted(bu, nc, 4, 2, ub)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
     UPLOAD(F.pBlk, double2, hpK);
     UPLOAD(F.pY, double2, hpY);
     UPLOAD(F.pSinv, double2, hpS);

@@ -461,6 +461,100 @@ bool block_lu(const std::vector<T>& band, int n_c, int h, int p, std::vector<T>&
     return true;
 }
 
+template <class T>
+bool block_lu_twisted(const std::vector<T>& band, int n_c, int h, int p, std::vector<T>& out) {
+    const int W = 2 * h + 1;
+    const int n = n_c - p;
+    const int nb = (n + h - 1) / h;
+    const int c = nb / 2;
+    auto Dat = [&](int i, int j) -> T {
+        if (i >= n || j >= n) return (i == j) ? T(1) : T(0);
+        const int d = j - i + h;
+        if (d < 0 || d >= W) return T(0);
+        return band[(size_t)(i + p) * W + d];
+    };
+    const size_t hh = (size_t)h * h;
+    out.assign((size_t)nb * 3 * hh, T(0));
+    auto blockD = [&](int bi, int bj, std::vector<T>& M) {
+        for (int i = 0; i < h; ++i)
+            for (int j = 0; j < h; ++j) M[(size_t)i * h + j] = Dat(bi * h + i, bj * h + j);
+    };
+    auto matmul = [&](const std::vector<T>& A, const std::vector<T>& B, std::vector<T>& C) {
+        for (int i = 0; i < h; ++i)
+            for (int j = 0; j < h; ++j) {
+                T acc = T(0);
+                for (int t = 0; t < h; ++t) acc += A[(size_t)i * h + t] * B[(size_t)t * h + j];
+                C[(size_t)i * h + j] = acc;
+            }
+    };
+    std::vector<T> U(hh), Ui(hh), Uprev(hh), L(hh), X(hh), Dc(hh), Dn(hh);
+    auto put = [&](int k, int slot, const std::vector<T>& M) {
+        std::copy(M.begin(), M.end(), out.begin() + (size_t)k * 3 * hh + slot * hh);
+    };
+    // top: U_k = D_kk - L_k D_{k-1,k},  L_k = D_{k,k-1} U_{k-1}^{-1},  H_k = U_k^{-1} D_{k,k+1}
+    for (int k = 0; k < c; ++k) {
+        blockD(k, k, U);
+        if (k > 0) {
+            blockD(k, k - 1, Dc);
+            matmul(Dc, Uprev, L);
+            blockD(k - 1, k, Dn);
+            matmul(L, Dn, X);
+            for (size_t i = 0; i < hh; ++i) U[i] -= X[i];
+            put(k, 0, L);
+        }
+        if (!invert_small(U, h, Ui)) return false;
+        put(k, 1, Ui);
+        blockD(k, k + 1, Dn);
+        matmul(Ui, Dn, X);
+        put(k, 2, X);
+        Uprev = Ui;
+    }
+    std::vector<T> Lc(hh, T(0)), Utop = Uprev;
+    // bottom: V_k = D_kk - M_k D_{k+1,k},  M_k = D_{k,k+1} V_{k+1}^{-1},  G_k = V_k^{-1} D_{k,k-1}
+    std::vector<T> Vprev(hh);
+    for (int k = nb - 1; k > c; --k) {
+        blockD(k, k, U);
+        if (k < nb - 1) {
+            blockD(k, k + 1, Dn);
+            matmul(Dn, Vprev, L);
+            blockD(k + 1, k, Dc);
+            matmul(L, Dc, X);
+            for (size_t i = 0; i < hh; ++i) U[i] -= X[i];
+            put(k, 0, L);
+        }
+        if (!invert_small(U, h, Ui)) return false;
+        put(k, 1, Ui);
+        blockD(k, k - 1, Dc);
+        matmul(Ui, Dc, X);
+        put(k, 2, X);
+        Vprev = Ui;
+    }
+    // middle: S = D_cc - L_c D_{c-1,c} - M_c D_{c+1,c}
+    blockD(c, c, U);
+    if (c > 0) {
+        blockD(c, c - 1, Dc);
+        matmul(Dc, Utop, Lc);
+        blockD(c - 1, c, Dn);
+        matmul(Lc, Dn, X);
+        for (size_t i = 0; i < hh; ++i) U[i] -= X[i];
+        put(c, 0, Lc);
+    }
+    if (c < nb - 1) {
+        std::vector<T> Mc(hh);
+        blockD(c, c + 1, Dn);
+        matmul(Dn, Vprev, Mc);
+        blockD(c + 1, c, Dc);
+        matmul(Mc, Dc, X);
+        for (size_t i = 0; i < hh; ++i) U[i] -= X[i];
+        put(c, 2, Mc);
+    }
+    if (!invert_small(U, h, Ui)) return false;
+    put(c, 1, Ui);
+    return true;
+}
+
+template bool block_lu_twisted<double>(const std::vector<double>&, int, int, int, std::vector<double>&);
+template bool block_lu_twisted<cplx>(const std::vector<cplx>&, int, int, int, std::vector<cplx>&);
 template bool block_lu<double>(const std::vector<double>&, int, int, int, std::vector<double>&);
 template bool block_lu<cplx>(const std::vector<cplx>&, int, int, int, std::vector<cplx>&);
 

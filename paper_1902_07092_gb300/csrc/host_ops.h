@@ -59,6 +59,22 @@ struct Bordered {
 template <class T>
 bool block_lu(const std::vector<T>& band, int n_c, int h, int p, std::vector<T>& out);
 
+// Two-sided ("twisted") block factorisation of the same block-tridiagonal D,
+// meeting at the middle block c = nb/2: the top blocks k < c are factored from
+// the top as in block_lu, the bottom blocks k > c from the bottom, and the
+// middle block takes both Schur complements.  Stored per block k as three
+// row-major h x h matrices:
+//   k < c:  [0] L_k = D_{k,k-1} U_{k-1}^{-1}, [1] U_k^{-1}, [2] U_k^{-1} D_{k,k+1}
+//   k > c:  [0] M_k = D_{k,k+1} V_{k+1}^{-1}, [1] V_k^{-1}, [2] V_k^{-1} D_{k,k-1}
+//   k = c:  [0] L_c, [1] S^{-1}, [2] M_c,  S = D_cc - L_c D_{c-1,c} - M_c D_{c+1,c}
+// with U_k = D_kk - L_k D_{k-1,k} and V_k = D_kk - M_k D_{k+1,k}.  Then D x = b by
+//   z_k = b_k - L_k z_{k-1} (k < c),  w_k = b_k - M_k w_{k+1} (k > c),
+//   x_c = S^{-1}(b_c - L_c z_{c-1} - M_c w_{c+1}),
+//   x_k = U_k^{-1} z_k - [2]_k x_{k+1} (k < c),  x_k = V_k^{-1} w_k - [2]_k x_{k-1} (k > c):
+// two chains of about nb/2 blocks each instead of one of nb.
+template <class T>
+bool block_lu_twisted(const std::vector<T>& band, int n_c, int h, int p, std::vector<T>& out);
+
 // Assemble and factor the tau system  [tau rows; Mass - gdt*Lin]  for one m.
 // mass_band / lin_band: band storage with half bandwidth h (complex).
 template <class T>

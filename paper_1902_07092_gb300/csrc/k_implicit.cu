@@ -11,16 +11,17 @@
 // grows, so its solution is refined once: the residual of the assembled system
 // is formed in FP64 and solved again with the same factors.
 //
-// The banded block is solved through its block-tridiagonal LU (blocks of 8 rows
-// for the streamfunction, 4 for temperature and zonal flow; host_ops.h): the
-// sequential part is one lane-parallel H x H mat-vec per block forward and one
-// fused pair of them per block backward.  On GB300 a
-// dependent FP64 FMA costs ~64 cycles, so this cuts the sequential chain of a
-// row-by-row substitution (two to four dependent FMAs per row) several-fold.
-// One warp per system: lane (r, c) = (lane/4, lane%4) owns row r of a block and
-// columns c, c+4.  A CTA handles MB consecutive modes; the right-hand side,
-// Schur updates, residual and the banded mass/implicit applies for later stages
-// use the whole CTA.
+// The banded block is solved through its two-sided block-tridiagonal
+// factorisation (blocks of 8 rows for the streamfunction, 4 for temperature and
+// zonal flow; host_ops.h, block_lu_twisted): a pair of warps walks the top and
+// the bottom half towards the middle block and back, each step one lane-parallel
+// H x H mat-vec forward and a fused pair of them backward.  On GB300 a dependent
+// FP64 FMA costs ~64 cycles, so the sequential chain, not the flop count, sets
+// the time of a solve; two half-length chains halve it.  Lane (r, c) =
+// (lane/4, lane%4) owns row r of a block and columns c, c+4.  A CTA handles one
+// mode: warps 0-1 the streamfunction, 2-3 the temperature, 4-5 the zonal flow
+// (m = 0); the right-hand side, Schur updates, residual and the banded mass
+// applies for later stages use the whole CTA.
 #include "device_common.cuh"
 
 namespace pz {
@@ -81,25 +82,35 @@ __device__ __forceinline__ double fms_x(double a, double b, double acc) { return
 
 constexpr int PFB = 2;  // blocks of coefficients prefetched ahead in the chains
 
-// Solve D x = b with the block-tridiagonal LU (blocks of H rows; per block
-// [0] L_{k,k-1}, [1] Uinv_k, [2] H_k) by one warp.  Lane (r, c) = (lane/4,
-// lane%4) owns row r of a block and columns c + 4q, q < H/4; the four lanes of a
-// row reduce by shuffles.
-//   forward:  z_k = b_k - L_{k,k-1} z_{k-1}          (Z: nb*H entries)
-//   backward: x_k = Uinv_k z_k - H_k x_{k+1}         (x: n entries)
-// Rows of b at or beyond n read as zero.
+// Barrier of the two warps (64 threads) of a solver pair.
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// Solve D x = b with the two-sided block factorisation (host_ops.h,
+// block_lu_twisted) by a pair of warps: half 0 walks the top blocks down, half 1
+// the bottom blocks up, both compute the middle block, then each substitutes
+// back through its half.  Lane (r, c) = (lane/4, lane%4) owns row r of a block
+// and columns c + 4q.  Z holds the forward values (nb*H entries), x the solution
+// (n entries); rows of b at or beyond n read as zero.  Both warps of the pair
+// must call it (bar: named barrier id); act = false skips all memory accesses.
+// On return the whole of x is visible to both warps.
 template <int H, class TF, class TX>
-__device__ void warp_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __restrict__ blk, bool act) {
+__device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __restrict__ blk, bool act, int half,
+                                 int bar) {
     constexpr int CPL = H / 4;
     constexpr int HH = H * H;
     const int lane = threadIdx.x & 31;
     const int r = lane >> 2, c = lane & 3;
     const bool ra = act && r < H;
     const int nb = (n + H - 1) / H;
+    const int cm = nb / 2;
+    const int dir = half ? -1 : 1;
+    const int len = half ? (nb - 1 - cm) : cm;  // blocks of this half
+    const int k_fw = half ? nb - 1 : 0;         // first block of the forward walk
+    const int k_bw = half ? cm + 1 : cm - 1;    // first block of the backward walk
     auto coef = [&](int k, int which, int q) -> TF {
         return (ra && k >= 0 && k < nb) ? blk[(size_t)k * 3 * HH + which * HH + r * H + c + 4 * q] : zero<TF>();
     };
-    // forward chain
+    // forward: Z_k = b_k - [0]_k Z_prev
     {
         TX prev[CPL];
         TF cur[PFB][CPL], nxt[PFB][CPL];
@@ -108,16 +119,17 @@ __device__ void warp_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
 #pragma unroll
         for (int i = 0; i < PFB; ++i)
 #pragma unroll
-            for (int q = 0; q < CPL; ++q) cur[i][q] = coef(i, 0, q);
-        for (int k0 = 0; k0 < nb; k0 += PFB) {
+            for (int q = 0; q < CPL; ++q) cur[i][q] = (i < len) ? coef(k_fw + dir * i, 0, q) : zero<TF>();
+        for (int i0 = 0; i0 < len; i0 += PFB) {
 #pragma unroll
             for (int i = 0; i < PFB; ++i)
 #pragma unroll
-                for (int q = 0; q < CPL; ++q) nxt[i][q] = coef(k0 + PFB + i, 0, q);
+                for (int q = 0; q < CPL; ++q)
+                    nxt[i][q] = (i0 + PFB + i < len) ? coef(k_fw + dir * (i0 + PFB + i), 0, q) : zero<TF>();
 #pragma unroll
             for (int i = 0; i < PFB; ++i) {
-                const int k = k0 + i;
-                if (k < nb) {
+                if (i0 + i < len) {
+                    const int k = k_fw + dir * (i0 + i);
                     const int row = k * H + r;
                     const TX bv = (ra && row < n) ? b[row] : zero<TX>();
                     TX p = zero<TX>();
@@ -136,40 +148,64 @@ __device__ void warp_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
                 for (int q = 0; q < CPL; ++q) cur[i][q] = nxt[i][q];
         }
     }
-    __syncwarp();
-    // backward chain
+    pair_sync(bar);
+    // middle block, by both warps: x_c = S^{-1}(b_c - L_c z_{c-1} - M_c w_{c+1})
+    TX prev[CPL];
     {
-        TX prev[CPL];
-        TF cu[PFB][CPL], ch[PFB][CPL], nu[PFB][CPL], nh[PFB][CPL];
+        TX t = zero<TX>();
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) prev[q] = zero<TX>();
+        for (int q = 0; q < CPL; ++q) {
+            const int col = c + 4 * q;
+            if (ra && cm > 0) t = fma_x(coef(cm, 0, q), Z[(cm - 1) * H + col], t);
+            if (ra && cm < nb - 1) t = fma_x(coef(cm, 2, q), Z[(cm + 1) * H + col], t);
+        }
+        t = reduce4(t);
+        const int row = cm * H + r;
+        const TX bv = (ra && row < n) ? b[row] : zero<TX>();
+        const TX rv = sub_x(bv, t);
+        TX rr[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) rr[q] = shfl_idx(rv, 4 * (c + 4 * q));
+        TX xv = zero<TX>();
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) xv = fma_x(coef(cm, 1, q), rr[q], xv);
+        xv = reduce4(xv);
+        if (half == 0 && ra && c == 0 && row < n) x[row] = xv;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(xv, 4 * (c + 4 * q));
+    }
+    // backward: x_k = [1]_k Z_k - [2]_k x_prev, walking away from the middle
+    {
+        TF cu[PFB][CPL], ch[PFB][CPL], nu[PFB][CPL], nh[PFB][CPL];
+        const int bdir = half ? 1 : -1;
 #pragma unroll
         for (int i = 0; i < PFB; ++i)
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
-                cu[i][q] = coef(nb - 1 - i, 1, q);
-                ch[i][q] = coef(nb - 1 - i, 2, q);
+                cu[i][q] = (i < len) ? coef(k_bw + bdir * i, 1, q) : zero<TF>();
+                ch[i][q] = (i < len) ? coef(k_bw + bdir * i, 2, q) : zero<TF>();
             }
-        for (int i0 = 0; i0 < nb; i0 += PFB) {
+        for (int i0 = 0; i0 < len; i0 += PFB) {
 #pragma unroll
             for (int i = 0; i < PFB; ++i)
 #pragma unroll
                 for (int q = 0; q < CPL; ++q) {
-                    nu[i][q] = coef(nb - 1 - (i0 + PFB + i), 1, q);
-                    nh[i][q] = coef(nb - 1 - (i0 + PFB + i), 2, q);
+                    const bool in = i0 + PFB + i < len;
+                    nu[i][q] = in ? coef(k_bw + bdir * (i0 + PFB + i), 1, q) : zero<TF>();
+                    nh[i][q] = in ? coef(k_bw + bdir * (i0 + PFB + i), 2, q) : zero<TF>();
                 }
 #pragma unroll
             for (int i = 0; i < PFB; ++i) {
-                const int k = nb - 1 - (i0 + i);
-                if (k >= 0) {
-                    TX p = zero<TX>();
+                if (i0 + i < len) {
+                    const int k = k_bw + bdir * (i0 + i);
+                    TX pz = zero<TX>(), ph = zero<TX>();
 #pragma unroll
                     for (int q = 0; q < CPL; ++q) {
                         const TX zq = ra ? Z[k * H + c + 4 * q] : zero<TX>();
-                        p = fma_x(cu[i][q], zq, p);
-                        p = fms_x(ch[i][q], prev[q], p);
+                        pz = fma_x(cu[i][q], zq, pz);
+                        ph = fma_x(ch[i][q], prev[q], ph);
                     }
-                    p = reduce4(p);
+                    TX p = reduce4(sub_x(pz, ph));
                     const int row = k * H + r;
                     if (ra && c == 0 && row < n) x[row] = p;
 #pragma unroll
@@ -185,7 +221,9 @@ __device__ void warp_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
                 }
         }
     }
-    __syncwarp();
+    // both halves of x written before either warp goes on (a Schur step of the
+    // caller reads all of it)
+    pair_sync(bar);
 }
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
@@ -318,6 +356,60 @@ __device__ void apply_row(const StepParams& P, int m, int k, const double2* xp, 
     }
 }
 
+// Epilogue of a solve for row k of mode m: the mass term of the new state
+// (A^I_m Psi, D^I theta, D^I u) and, from the solved equation
+// (Mass - gamma dt Lin) y = f on the rows below the tau rows, its implicit term
+// Lin y = (Mass y - f)/(gamma dt), which saves the banded B^I, C^I, F^I, E^I
+// applies.  f is the right-hand side of the solve (recomputed here from the
+// same terms in the same order).
+__device__ void epilogue_row(const StepParams& P, const RhsSpec& R, double gdt, int m, int k, const double2* xp,
+                             const double2* xt, const double* xu, VecSet mass_out, VecSet imp_out, bool want_mass,
+                             bool want_imp) {
+    const int nc = P.nc;
+    const double mu = (double)m * m;
+    double2 mp = make_double2(0.0, 0.0), mt = make_double2(0.0, 0.0);
+    double muu = 0.0;
+    if (m > 0 && k >= 4) {
+        const double2 a0 = band_row_c<8>(P.ops.band[OP_A0], xp, k, nc);
+        const double2 a2 = band_row_c<8>(P.ops.band[OP_A2], xp, k, nc);
+        mp = make_double2(fma(mu, a2.x, a0.x), fma(mu, a2.y, a0.y));
+    }
+    if (k >= 2) {
+        mt = band_row_c<4>(P.ops.band[OP_D], xt, k, nc);
+        if (m == 0) {
+            const double* rd = P.ops.band[OP_D] + (size_t)k * 9;
+            for (int d = 0; d < 9; ++d) {
+                const int n = k - 4 + d;
+                if (n >= 0 && n < nc) muu = fma(__ldg(&rd[d]), xu[n], muu);
+            }
+        }
+    }
+    const size_t idx = (size_t)m * nc + k;
+    if (want_imp) {  // before any store: an output may be one of the terms of f
+        double2 fp = make_double2(0.0, 0.0), ft = make_double2(0.0, 0.0);
+        double fu = 0.0;
+        for (int t = 0; t < R.nterms; ++t) {
+            const double c = R.t[t].c;
+            const double2 vp = R.t[t].v.psi[idx];
+            const double2 vt = R.t[t].v.th[idx];
+            fp.x = fma(c, vp.x, fp.x);
+            fp.y = fma(c, vp.y, fp.y);
+            ft.x = fma(c, vt.x, ft.x);
+            ft.y = fma(c, vt.y, ft.y);
+            if (m == 0) fu = fma(c, R.t[t].v.u[k], fu);
+        }
+        const double ig = 1.0 / gdt;
+        imp_out.psi[idx] = (m > 0 && k >= 4) ? cscale(csub(mp, fp), ig) : make_double2(0.0, 0.0);
+        imp_out.th[idx] = (k >= 2) ? cscale(csub(mt, ft), ig) : make_double2(0.0, 0.0);
+        if (m == 0) imp_out.u[k] = (k >= 2) ? (muu - fu) * ig : 0.0;
+    }
+    if (want_mass) {
+        mass_out.psi[idx] = mp;
+        mass_out.th[idx] = mt;
+        if (m == 0) mass_out.u[k] = muu;
+    }
+}
+
 // shared-memory layout of one CTA, per mode mi < MB:
 //   streamfunction: pf rhs (then the refinement residual), pw forward-chain
 //                   values, px solution, pd correction
@@ -413,14 +505,14 @@ __device__ void refine_temperature(const StepParams& P, const DevFactors& F, Sol
     }
     __syncthreads();
     double2* dt_[2] = {s.pd[0], s.pd[MB > 1 ? 1 : 0]};
-    double* du = reinterpret_cast<double*>(s.pw[0]);  // after the streamfunction solves
-    if (warp >= MB && warp < 2 * MB) {
-        const int mi = warp - MB, m = m0 + mi;
-        const bool act = m < M;
-        warp_block_solve<4>(s.tf[mi] + 2, s.tw[mi], dt_[mi] + 2, nt, F.tBlk + (size_t)(act ? m : 0) * nbt * 48, act);
-        if (act) warp_schur<2>(dt_[mi], s.tf[mi], nc, P.ops.tau_dir_B, F.tSinv + (size_t)m * 4);
-        if (has_u && mi == 0) {
-            warp_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.tw[0]), du + 2, nt, F.uBlk, true);
+    // after the streamfunction solves: zonal-flow correction in pw, its chain scratch in pf
+    double* du = reinterpret_cast<double*>(s.pw[0]);
+    if (warp == 2 || warp == 3) {
+        pair_block_solve<4>(s.tf[0] + 2, s.tw[0], dt_[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true, warp - 2, 2);
+        if (warp == 2) warp_schur<2>(dt_[0], s.tf[0], nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
+    } else if ((warp == 4 || warp == 5) && has_u) {
+        pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pf[0]), du + 2, nt, F.uBlk, true, warp - 4, 3);
+        if (warp == 4) {
             double t0 = 0.0, t1 = 0.0;
             for (int j = lane; j < nt; j += 32) {
                 t0 = fma(__ldg(&P.ops.tau_dir_B[j]), du[2 + j], t0);
@@ -494,31 +586,26 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     }
     __syncthreads();
 
-    // 2. banded solves: warp w < MB streamfunction of mode w, warps MB..2MB-1
-    //    temperature (the warp of mode m = 0 then also the zonal flow)
-    if (warp < MB) {
-        const int m = m0 + warp;
-        const bool act = m < M && m > 0;
-        warp_block_solve<8>(s.pf[warp] + 4, s.pw[warp], s.px[warp] + 4, np,
-                            F.pBlk + (size_t)(act ? m : 0) * nbp * 192, act);
-    } else if (warp < 2 * MB) {
-        const int mi = warp - MB, m = m0 + mi;
-        const bool act = m < M;
-        warp_block_solve<4>(s.tf[mi] + 2, s.tw[mi], s.tx[mi] + 2, nt,
-                            F.tBlk + (size_t)(act ? m : 0) * nbt * 48, act);
-        if (has_u && mi == 0)
-            warp_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.tw[0]), s.ux + 2, nt, F.uBlk, true);
+    // 2. banded solves by warp pairs meeting at their middle blocks: warps 0-1
+    //    streamfunction, 2-3 temperature, 4-5 zonal flow (m = 0 only; its chain
+    //    scratch is the streamfunction correction array, unused until step 5)
+    if (warp < 2) {
+        const bool act = m0 > 0;
+        pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, np, F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act,
+                            warp, 1);
+    } else if (warp < 4) {
+        pair_block_solve<4>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true, warp - 2, 2);
+    } else if (warp < 6 && has_u) {
+        pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4, 3);
     }
     __syncthreads();
 
-    // 3. Schur steps (same warp assignment)
-    if (warp < MB) {
-        const int m = m0 + warp;
-        if (m < M && m > 0) warp_schur<4>(s.px[warp], nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
-    } else if (warp < 2 * MB) {
-        const int mi = warp - MB, m = m0 + mi;
-        if (m < M) warp_schur<2>(s.tx[mi], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m * 4);
-    } else if (warp == 2 * MB && has_u) {
+    // 3. Schur steps: warp 0 streamfunction, 2 temperature, 4 zonal flow
+    if (warp == 0) {
+        if (m0 > 0) warp_schur<4>(s.px[0], nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
+    } else if (warp == 2) {
+        warp_schur<2>(s.tx[0], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
+    } else if (warp == 4 && has_u) {
         double t0 = 0.0, t1 = 0.0;
         for (int j = lane; j < nt; j += 32) {
             t0 = fma(__ldg(&P.ops.tau_dir_B[j]), s.ux[2 + j], t0);
@@ -590,12 +677,11 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         }
     }
     __syncthreads();
-    if (warp < MB) {
-        const int m = m0 + warp;
-        const bool act = m < M && m > 0;
-        warp_block_solve<8>(s.pf[warp] + 4, s.pw[warp], s.pd[warp] + 4, np,
-                            F.pBlk + (size_t)(act ? m : 0) * nbp * 192, act);
-        if (act) warp_schur<4>(s.pd[warp], s.pf[warp], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
+    if (warp < 2) {
+        const bool act = m0 > 0;
+        pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.pd[0] + 4, np, F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act,
+                            warp, 1);
+        if (act && warp == 0) warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
     }
     __syncthreads();
     {
@@ -622,7 +708,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         y_out.th[(size_t)m * nc + n] = s.tx[mi][n];
         if (m == 0) y_out.u[n] = s.ux[n];
         if (want_mass || want_imp)
-            apply_row(P, m, n, s.px[mi], s.tx[mi], s.ux, mass_out, imp_out, want_mass, want_imp);
+            epilogue_row(P, R, F.gdt, m, n, s.px[mi], s.tx[mi], s.ux, mass_out, imp_out, want_mass, want_imp);
     }
 }
 
@@ -643,31 +729,19 @@ __global__ void __launch_bounds__(NTHREADS_S) k_apply(StepParams P, VecSet y, Ve
     for (int k = threadIdx.x; k < nc; k += blockDim.x) apply_row(P, m, k, xp, xt, xu, mass_out, imp_out, want_mass, want_imp);
 }
 
-int modes_per_cta(const StepParams& P) { return 1; }
-
 size_t smem_solve_mb(const StepParams& P, int MB) { return sizeof(double) * solve_smem_doubles(P.nc, MB); }
 
 }  // namespace
 
-size_t smem_solve(const StepParams& P) { return smem_solve_mb(P, modes_per_cta(P)); }
+size_t smem_solve(const StepParams& P) { return smem_solve_mb(P, 1); }
 
 cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFactors& F, VecSet y_out,
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st) {
-    const int MB = modes_per_cta(P);
-    const size_t sm = smem_solve_mb(P, MB);
-    const int grid = (P.M + MB - 1) / MB;
-    cudaError_t err;
-    if (MB == 2) {
-        err = cudaFuncSetAttribute(k_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (err != cudaSuccess) return err;
-        k_solve<2><<<grid, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
-                                                  want_imp ? 1 : 0);
-    } else {
-        err = cudaFuncSetAttribute(k_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (err != cudaSuccess) return err;
-        k_solve<1><<<grid, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
-                                                  want_imp ? 1 : 0);
-    }
+    const size_t sm = smem_solve_mb(P, 1);
+    cudaError_t err = cudaFuncSetAttribute(k_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    k_solve<1><<<P.M, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+                                            want_imp ? 1 : 0);
     return cudaGetLastError();
 }
 

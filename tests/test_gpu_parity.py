@@ -200,3 +200,32 @@ def test_diagnostics_match_oracle(n_r, n_phi):
     for key in ("E_K", "E_Z", "enstrophy", "Nu", "Re", "Ro", "cfl_s", "cfl_phi"):
         assert abs(d[key] - r[key]) <= 1e-12 * max(abs(r[key]), 1e-300), (key, d[key], r[key])
     gpu.close()
+
+
+@pytest.mark.parametrize("radial", ["integration", "collocation"])
+def test_overlapping_contexts_match_a_context_run_alone(radial):
+    """Two contexts stepping on their own streams with no synchronisation between
+    them (their kernels share SMs) must give bitwise the results of a context
+    stepped alone: every kernel's result depends only on its own inputs."""
+    from paper_1902_07092_gb300.binding import Solver
+    n_r, n_phi, E = (257, 768, 1e-5) if radial == "integration" else (65, 192, 1e-4)
+    Ra = 10.0 * critical_rayleigh(1e-5) if radial == "integration" else 2e6
+    nc = n_r if radial == "collocation" else None
+    th = inputs.theta_init(n_r, n_phi, 1e-3, 2, cfg=2, n_c=nc)
+    z, zu = inputs.zero_state(n_r, n_phi, n_c=nc)
+    alone = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "ARS443", 1e-7, radial=radial)
+    alone.set_state(th, z, zu)
+    alone.step(6)
+    ref = alone.get_state()
+    alone.close()
+    a = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "ARS443", 1e-7, radial=radial)
+    b = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "ARS443", 1e-7, radial=radial)
+    a.set_state(th, z, zu)
+    b.set_state(th, z, zu)
+    for _ in range(6):
+        a.step(1)
+        b.step(1)
+    for s in (a, b):
+        for x, y in zip(s.get_state(), ref):
+            assert np.array_equal(x, y)
+        s.close()
