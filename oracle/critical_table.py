@@ -16,9 +16,9 @@ from .onset import marginal_rayleigh
 CASES = [  # E, radial resolution n_c, initial Ra guess, m scan range
     (1e-3, 48, 5e4, range(1, 10)),
     (1e-5, 96, 5e6, range(6, 26)),
-    (1e-6, 128, 5e7, range(10, 50)),
+    (1e-6, 160, 1.7e8, range(32, 46)),
     (1e-4, 64, 5e5, range(2, 16)),
-    (1e-8, 320, 5e10, range(40, 200)),
+    (1e-8, 320, 6.0e10, range(96, 154, 6)),
 ]
 
 
