@@ -182,6 +182,23 @@ int pizza_synchronize(pizza_ctx *ctx);
  * integrations are zero) into out.  Needs no CUDA device. */
 int pizza_host_operator(int which, int n_r, int n_c, double radius_ratio, double *out);
 
+/* Host-side collocation set-up (Section 3.1), exposed for verification without a
+ * GPU.  Grid values x_k = cos(pi k/(n_r-1)), s_k = ((s_o - s_i)/2) x_k + (s_o + s_i)/2.
+ *   which 0: interior-row columns of the inverse of the vorticity-streamfunction
+ *            system of mode m (Eq. psiomcoll with the boundary rows of
+ *            Eqs. bcs_coll_dirichlet, bcs_coll_neumann; unknowns the grid values
+ *            omega_k, psi_k) for implicit weight gdt: complex, row-major
+ *            [2 n_r][n_r - 2] (interleaved re, im);
+ *   which 1: the same for theta - gdt (1/Pr)(D2 + D1/s - m^2/s^2) theta with
+ *            Dirichlet rows (Eq. tempcoll): real [n_r][n_r - 2];
+ *   which 2: the zonal flow u - gdt (D2 + D1/s - 1/s^2) u (Eq. uphicoll):
+ *            real [n_r][n_r - 2] (m, Pr unused);
+ *   which 3, 4: the differentiation matrices d/ds, d^2/ds^2 on grid values,
+ *            real [n_r][n_r].
+ * Needs no CUDA device.  PIZZA_EINVAL for invalid arguments or a singular system. */
+int pizza_host_collocation(int which, int n_r, double radius_ratio, double E, double Pr, int m,
+                           double gdt, double *out);
+
 /* Explicit stage without device allocation.  This entry point has no
  * counterpart in the paper; it exists for callers that cannot allocate device
  * memory themselves or through the library -- for example code running inside a

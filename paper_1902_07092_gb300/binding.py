@@ -22,7 +22,8 @@ STATUS = {0: "PIZZA_OK", -1: "PIZZA_EINVAL", -2: "PIZZA_ENOMEM", -3: "PIZZA_ECUD
 EXPORTS = ("pizza_init", "pizza_set_option", "pizza_set_stream", "pizza_get_sizes", "pizza_set_state",
            "pizza_get_state", "pizza_step", "pizza_explicit_terms", "pizza_diagnostics", "pizza_get_grid",
            "pizza_profile_begin", "pizza_profile_end", "pizza_synchronize",
-           "pizza_host_operator", "pizza_explicit_terms_noalloc", "pizza_free", "pizza_last_error")
+           "pizza_host_operator", "pizza_host_collocation", "pizza_explicit_terms_noalloc", "pizza_free",
+           "pizza_last_error")
 
 _lib = None
 
@@ -59,6 +60,7 @@ def load():
     lib.pizza_profile_end.argtypes = [vp, dp, dp]
     lib.pizza_synchronize.argtypes = [vp]
     lib.pizza_host_operator.argtypes = [i, i, i, d, dp]
+    lib.pizza_host_collocation.argtypes = [i, i, d, d, d, i, d, dp]
     lib.pizza_explicit_terms_noalloc.argtypes = [i, i, d, d, d, dp, dp, dp, dp, dp, dp, vp]
     lib.pizza_free.argtypes = [vp]
     lib.pizza_free.restype = None
@@ -162,6 +164,13 @@ def pizza_synchronize(ctx):
 def pizza_host_operator(which, n_r, n_c, radius_ratio):
     out = np.zeros((n_c, n_c))
     _check(load().pizza_host_operator(which, n_r, n_c, radius_ratio, _ptr(out)))
+    return out
+
+
+def pizza_host_collocation(which, n_r, radius_ratio, E=1.0, Pr=1.0, m=1, gdt=0.0):
+    shape = {0: (2 * n_r, n_r - 2), 1: (n_r, n_r - 2), 2: (n_r, n_r - 2), 3: (n_r, n_r), 4: (n_r, n_r)}[which]
+    out = np.zeros(shape, np.complex128 if which == 0 else np.float64)
+    _check(load().pizza_host_collocation(which, n_r, radius_ratio, E, Pr, m, gdt, _ptr(out)))
     return out
 
 

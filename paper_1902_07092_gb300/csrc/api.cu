@@ -1149,6 +1149,29 @@ int pizza_host_operator(int which, int n_r, int n_c, double radius_ratio, double
     return PIZZA_OK;
 }
 
+int pizza_host_collocation(int which, int n_r, double radius_ratio, double E, double Pr, int m, double gdt,
+                           double* out) {
+    if (which < 0 || which > 4 || n_r < 5 || n_r > PIZZA_COLL_MAX_NR || !out || !(radius_ratio > 0 && radius_ratio < 1) ||
+        m < 0 || (which == 0 && m < 1) || !(E > 0) || !(Pr > 0))
+        return fail(nullptr, PIZZA_EINVAL, "invalid arguments to pizza_host_collocation");
+    CollGrid cg = coll_grid(n_r, make_geom(radius_ratio));
+    if (which == 0) {
+        std::vector<cplx> G;
+        if (!coll_inverse_wpsi(cg, E, m, gdt, G)) return fail(nullptr, PIZZA_EINVAL, "singular system");
+        std::memcpy(out, G.data(), G.size() * sizeof(cplx));
+    } else if (which <= 2) {
+        std::vector<double> G;
+        const bool ok = (which == 1) ? coll_inverse_dir(cg, 1.0 / Pr, (double)m * m, gdt, G)
+                                     : coll_inverse_dir(cg, 1.0, 1.0, gdt, G);
+        if (!ok) return fail(nullptr, PIZZA_EINVAL, "singular system");
+        std::memcpy(out, G.data(), G.size() * sizeof(double));
+    } else {
+        const auto& D = (which == 3) ? cg.D1 : cg.D2;
+        std::memcpy(out, D.data(), D.size() * sizeof(double));
+    }
+    return PIZZA_OK;
+}
+
 void pizza_free(pizza_ctx* ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
