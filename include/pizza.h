@@ -160,6 +160,45 @@ int pizza_diagnostics(pizza_ctx *ctx, pizza_diag *out);
  * synchronises the context stream. */
 int pizza_get_grid(pizza_ctx *ctx, double *us, double *uphi, double *omega, double *theta);
 
+/* Discrete adjoint of CNAB2 runs (integration formulation, FP64, n_phi <= 3072;
+ * PIZZA_EUNSUPPORTED otherwise), for gradients of J = sum_{n=1..K} j_n(y_n) of
+ * the states y_n = (Psi_hat, theta_hat, u_hat) after n steps.  The forward step
+ * (Eq. multistep1 with the start-up rule) is
+ *   y_{n+1} = S^{-1} P r_n,  r_0 = A y_0 + dt E(y_0),
+ *   r_n = A y_n + dt (3/2 E(y_n) - 1/2 E(y_{n-1})),
+ * A = Mass + (dt/2) Lin, S the tau system of weight dt/2 (Section 3.2) and P the
+ * projection zeroing its tau rows, E the explicit terms.  With the inner product
+ * <a, b> = Re sum conj(a) b over the stored arrays, the reverse sweep is
+ *   rho_n = P S^{-H} lambda_{n+1},
+ *   lambda_n = g_n + A^H rho_n + J_E(y_n)* w_n,  w_n = dt (c_n rho_n - 1/2 rho_{n+1}),
+ * c_0 = 1, c_n = 3/2, rho_K = 0, g_n = dj_n/dy_n; dJ/dRa = sum_n < w_n, dE/dRa(y_n) >.
+ *
+ * pizza_tape_begin: start recording, right after pizza_set_state (n = 0); the
+ * following pizza_step calls store a checkpoint (y_n, E(y_{n-1})) every
+ * checkpoint_every steps.  The dense adjoint solves are built on the host the
+ * first time (O(N_c^3) per mode).
+ * pizza_adjoint_step: reverse one recorded step.  The k-th call (k = 1..K) takes
+ * g_{K-k+1} (theta and Psi complex [N_m+1][N_c], u real [N_c]; host or device; NULL
+ * = zero) and leaves lambda_{K-k} without its own g; the states needed are
+ * recomputed segment by segment from the checkpoints (which overwrites the
+ * forward state of the context).  *dJ_dRa (may be NULL) receives the running total
+ * of the Ra derivative.  PIZZA_ESTATE when no recorded step is left.
+ * pizza_get_adjoint: copy lambda (after K calls: dJ/dy_0) out.
+ * pizza_explicit_adjoint: J_E(y)* applied to (e_psi_bar, e_theta_bar, e_u_bar) at
+ * the current state, without the tape (verification). */
+int pizza_tape_begin(pizza_ctx *ctx, int checkpoint_every);
+int pizza_adjoint_step(pizza_ctx *ctx, const double *g_theta, const double *g_psi, const double *g_u,
+                       double *dJ_dRa);
+int pizza_get_adjoint(pizza_ctx *ctx, double *theta_bar, double *psi_bar, double *uphi0_bar);
+int pizza_explicit_adjoint(pizza_ctx *ctx, const double *e_psi_bar, const double *e_theta_bar,
+                           const double *e_u_bar, double *psi_bar, double *theta_bar, double *uphi0_bar);
+
+/* Weights w[n] (N_c reals) of the Nusselt number of the integration state:
+ * Nu - 1 = (d theta_0/ds)(s_o)/(dT_c/ds)(s_o) = sum_n w_n Re theta_hat_0n (the
+ * definition used by pizza_diagnostics; the paper defines no Nusselt number).
+ * PIZZA_EUNSUPPORTED for the collocation formulation. */
+int pizza_nusselt_weights(const pizza_ctx *ctx, double *w);
+
 /* Per-kernel timing.  pizza_profile_begin starts recording a CUDA event pair on
  * the context stream around every later launch of the kernels selected by mask
  * (bit 0 spectral-to-grid, bit 1 azimuthal products, bit 2 grid-to-spectral,

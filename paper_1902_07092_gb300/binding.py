@@ -23,7 +23,8 @@ EXPORTS = ("pizza_init", "pizza_set_option", "pizza_set_stream", "pizza_get_size
            "pizza_get_state", "pizza_step", "pizza_explicit_terms", "pizza_diagnostics", "pizza_get_grid",
            "pizza_profile_begin", "pizza_profile_end", "pizza_synchronize",
            "pizza_host_operator", "pizza_host_collocation", "pizza_explicit_terms_noalloc", "pizza_free",
-           "pizza_last_error")
+           "pizza_last_error", "pizza_tape_begin", "pizza_adjoint_step", "pizza_get_adjoint",
+           "pizza_explicit_adjoint", "pizza_nusselt_weights")
 
 _lib = None
 
@@ -61,6 +62,11 @@ def load():
     lib.pizza_synchronize.argtypes = [vp]
     lib.pizza_host_operator.argtypes = [i, i, i, d, dp]
     lib.pizza_host_collocation.argtypes = [i, i, d, d, d, i, d, dp]
+    lib.pizza_tape_begin.argtypes = [vp, i]
+    lib.pizza_adjoint_step.argtypes = [vp, dp, dp, dp, ctypes.POINTER(d)]
+    lib.pizza_get_adjoint.argtypes = [vp, dp, dp, dp]
+    lib.pizza_explicit_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp]
+    lib.pizza_nusselt_weights.argtypes = [vp, dp]
     lib.pizza_explicit_terms_noalloc.argtypes = [i, i, d, d, d, dp, dp, dp, dp, dp, dp, vp]
     lib.pizza_free.argtypes = [vp]
     lib.pizza_free.restype = None
@@ -167,6 +173,32 @@ def pizza_host_operator(which, n_r, n_c, radius_ratio):
     return out
 
 
+def pizza_tape_begin(ctx, checkpoint_every=20):
+    return _check(load().pizza_tape_begin(ctx, checkpoint_every), ctx)
+
+
+def pizza_adjoint_step(ctx, g_theta=None, g_psi=None, g_u=None):
+    """Reverse one recorded step; returns the running dJ/dRa."""
+    r = ctypes.c_double(0.0)
+    _check(load().pizza_adjoint_step(ctx, _ptr(g_theta), _ptr(g_psi), _ptr(g_u), ctypes.byref(r)), ctx)
+    return r.value
+
+
+def pizza_get_adjoint(ctx, theta_bar, psi_bar, uphi0_bar):
+    return _check(load().pizza_get_adjoint(ctx, _ptr(theta_bar), _ptr(psi_bar), _ptr(uphi0_bar)), ctx)
+
+
+def pizza_explicit_adjoint(ctx, e_psi_bar, e_theta_bar, e_u_bar, psi_bar, theta_bar, uphi0_bar):
+    return _check(load().pizza_explicit_adjoint(ctx, _ptr(e_psi_bar), _ptr(e_theta_bar), _ptr(e_u_bar),
+                                                _ptr(psi_bar), _ptr(theta_bar), _ptr(uphi0_bar)), ctx)
+
+
+def pizza_nusselt_weights(ctx, n_c):
+    w = np.zeros(n_c)
+    _check(load().pizza_nusselt_weights(ctx, _ptr(w)), ctx)
+    return w
+
+
 def pizza_host_collocation(which, n_r, radius_ratio, E=1.0, Pr=1.0, m=1, gdt=0.0):
     shape = {0: (2 * n_r, n_r - 2), 1: (n_r, n_r - 2), 2: (n_r, n_r - 2), 3: (n_r, n_r), 4: (n_r, n_r)}[which]
     out = np.zeros(shape, np.complex128 if which == 0 else np.float64)
@@ -233,6 +265,32 @@ class Solver:
 
     def diagnostics(self):
         return pizza_diagnostics(self.ctx)
+
+    def tape_begin(self, checkpoint_every=20):
+        pizza_tape_begin(self.ctx, checkpoint_every)
+
+    def adjoint_step(self, g_theta=None, g_psi=None, g_u=None):
+        c = lambda a, dt: None if a is None else np.ascontiguousarray(a, dtype=dt)
+        return pizza_adjoint_step(self.ctx, c(g_theta, np.complex128), c(g_psi, np.complex128), c(g_u, np.float64))
+
+    def get_adjoint(self):
+        th = np.zeros((self.M, self.n_c), np.complex128)
+        ps = np.zeros((self.M, self.n_c), np.complex128)
+        up = np.zeros(self.n_c)
+        pizza_get_adjoint(self.ctx, th, ps, up)
+        return ps, th, up
+
+    def explicit_adjoint(self, e_psi_bar, e_theta_bar, e_u_bar):
+        c = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+        ps = np.zeros((self.M, self.n_c), np.complex128)
+        th = np.zeros((self.M, self.n_c), np.complex128)
+        up = np.zeros(self.n_c)
+        pizza_explicit_adjoint(self.ctx, c(e_psi_bar, np.complex128), c(e_theta_bar, np.complex128),
+                               c(e_u_bar, np.float64), ps, th, up)
+        return ps, th, up
+
+    def nusselt_weights(self):
+        return pizza_nusselt_weights(self.ctx, self.n_c)
 
     def get_grid(self):
         """(u_s, u_phi, omega, theta) on the physical grid, each [n_r][n_phi]."""

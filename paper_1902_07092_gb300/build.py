@@ -13,7 +13,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpizza.so")
 
-SOURCES = ["host_ops.cpp", "coll_ops.cpp", "k_explicit.cu", "k_implicit.cu", "k_collocation.cu", "api.cu",
+SOURCES = ["host_ops.cpp", "coll_ops.cpp", "k_explicit.cu", "k_implicit.cu", "k_collocation.cu", "k_adjoint.cu",
+           "api.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),

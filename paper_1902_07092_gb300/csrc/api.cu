@@ -97,6 +97,25 @@ struct pizza_ctx {
     std::vector<void*> vec_allocs;     // state and work vectors (re-made when the formulation changes)
     std::vector<double> coll_d1_row0;  // d/ds at s_o on grid values
     double* grid_out = nullptr;        // pizza_get_grid staging, 4 x n_r x n_phi
+    // discrete adjoint (pizza_tape_begin / pizza_adjoint_step)
+    struct Adjoint {
+        bool taping = false;       // forward steps are being recorded
+        bool ready = false;        // buffers and dense inverses built
+        int every = 20;            // checkpoint interval
+        int K = 0;                 // recorded steps
+        int pos = 0;               // adjoint position: lam holds dJ/dy_pos (without g_pos)
+        int seg = -1;              // segment cached in seg_y
+        double dRa = 0.0;
+        std::vector<VecSet> ck_y, ck_e;  // checkpoints: y_{s*every}, E(y_{s*every - 1})
+        std::vector<VecSet> seg_y;       // y_{seg*every + i}, i < every
+        VecSet lam{}, rho[2]{}, w{}, g{};
+        int rcur = 0;
+        double2 *Gb1 = nullptr, *Gb2 = nullptr;
+        double* ra = nullptr;
+        AdjFactors A{};
+        std::vector<void*> allocs;     // buffers and inverses
+        std::vector<void*> ck_allocs;  // checkpoints of the current tape
+    } adj;
 };
 
 namespace {
@@ -692,6 +711,216 @@ int enable_collocation(pizza_ctx* ctx) {
     return PIZZA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Discrete adjoint: buffers, dense inverses of the transposed tau systems,
+// checkpoints and the recomputation of a segment of forward states.
+// ---------------------------------------------------------------------------
+VecSet adj_vec(pizza_ctx* ctx, bool& ok, bool checkpoint = false) {
+    VecSet v{};
+    const size_t vsz = (size_t)ctx->M * ctx->nc;
+    auto& list = checkpoint ? ctx->adj.ck_allocs : ctx->adj.allocs;
+    v.psi = dalloc<double2>(ctx, vsz, list);
+    v.th = dalloc<double2>(ctx, vsz, list);
+    v.u = dalloc<double>(ctx, ctx->nc, list);
+    if (!v.psi || !v.th || !v.u) {
+        ok = false;
+        return v;
+    }
+    ok = cudaMemset(v.psi, 0, vsz * 16) == cudaSuccess && cudaMemset(v.th, 0, vsz * 16) == cudaSuccess &&
+         cudaMemset(v.u, 0, ctx->nc * 8) == cudaSuccess;
+    return v;
+}
+
+int copy_vec(pizza_ctx* ctx, VecSet dst, VecSet src) {
+    const size_t vsz = (size_t)ctx->M * ctx->nc;
+    CK(cudaMemcpyAsync(dst.psi, src.psi, vsz * 16, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dst.th, src.th, vsz * 16, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dst.u, src.u, ctx->nc * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    return PIZZA_OK;
+}
+
+int zero_vec(pizza_ctx* ctx, VecSet v) {
+    const size_t vsz = (size_t)ctx->M * ctx->nc;
+    CK(cudaMemsetAsync(v.psi, 0, vsz * 16, ctx->stream));
+    CK(cudaMemsetAsync(v.th, 0, vsz * 16, ctx->stream));
+    CK(cudaMemsetAsync(v.u, 0, ctx->nc * 8, ctx->stream));
+    return PIZZA_OK;
+}
+
+// Dense P S^{-H} for gamma dt = dt/2 (the CNAB2 weight): S is the tau system of
+// each field (tau rows on top), inverted by refined LU on the host; stored
+// column-major without the tau rows of the output (host_ops.h, dense_inverse).
+int build_adjoint_factors(pizza_ctx* ctx) {
+    const int M = ctx->M, nc = ctx->nc, np = nc - 4, nt = nc - 2;
+    const double gdt = 0.5 * ctx->dt;
+    HostOps H = host_ops_of(ctx);
+    const auto tauP = tau_rows_psi(ctx->n_r, nc);
+    const auto tauD = tau_rows_dir(ctx->n_r, nc);
+    auto get = [&](int id, int k, int n) -> double {
+        const int h = op_h(id);
+        const int d = n - k + h;
+        if (d < 0 || d > 2 * h) return 0.0;
+        return H.band[id][(size_t)k * (2 * h + 1) + d];
+    };
+    std::vector<double2> hW((size_t)M * nc * np, make_double2(0.0, 0.0));
+    std::vector<double> hT((size_t)M * nc * nt), hU((size_t)nc * nt);
+    std::vector<int> bad(M, 0);
+    auto work = [&](int m) {
+        const double mu = (double)m * m, dm = (double)m;
+        if (m > 0) {
+            std::vector<cplx> S((size_t)nc * nc), inv;
+            for (int k = 0; k < nc; ++k)
+                for (int n = 0; n < nc; ++n) {
+                    cplx v;
+                    if (k < 4) {
+                        v = cplx(tauP[(size_t)k * nc + n], 0.0);
+                    } else {
+                        const double a = get(OP_A0, k, n) + mu * get(OP_A2, k, n);
+                        const double b = get(OP_B0, k, n) + mu * (get(OP_B2, k, n) + mu * get(OP_B4, k, n));
+                        v = cplx(a - gdt * b, -gdt * 2.0 * dm / ctx->E * get(OP_C, k, n));
+                    }
+                    S[(size_t)k * nc + n] = v;
+                }
+            if (!dense_inverse(nc, S, inv)) {
+                bad[m] = 1;
+                return;
+            }
+            // W = (S^{-1})^H rows >= 4, column-major: W[j][i-4] = conj(inv[j][i])
+            for (int j = 0; j < nc; ++j)
+                for (int i = 4; i < nc; ++i) {
+                    const cplx c = std::conj(inv[(size_t)j * nc + i]);
+                    hW[((size_t)m * nc + j) * np + (i - 4)] = make_double2(c.real(), c.imag());
+                }
+        }
+        std::vector<double> S((size_t)nc * nc), inv;
+        for (int k = 0; k < nc; ++k)
+            for (int n = 0; n < nc; ++n)
+                S[(size_t)k * nc + n] = (k < 2) ? tauD[(size_t)k * nc + n]
+                                                : get(OP_D, k, n) - gdt * (get(OP_F0, k, n) + mu * get(OP_F2, k, n)) / ctx->Pr;
+        if (!dense_inverse(nc, S, inv)) {
+            bad[m] = 1;
+            return;
+        }
+        for (int j = 0; j < nc; ++j)
+            for (int i = 2; i < nc; ++i) hT[((size_t)m * nc + j) * nt + (i - 2)] = inv[(size_t)j * nc + i];
+    };
+    unsigned nthr = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nthr; ++t)
+        th.emplace_back([&, t] {
+            for (int m = (int)t; m < M; m += (int)nthr) work(m);
+        });
+    for (auto& t : th) t.join();
+    for (int m = 0; m < M; ++m)
+        if (bad[m]) return fail(ctx, PIZZA_EINVAL, "transposed tau system of mode m=%d is singular", m);
+    {
+        std::vector<double> S((size_t)nc * nc), inv;
+        for (int k = 0; k < nc; ++k)
+            for (int n = 0; n < nc; ++n)
+                S[(size_t)k * nc + n] = (k < 2) ? tauD[(size_t)k * nc + n] : get(OP_D, k, n) - gdt * get(OP_EZ, k, n);
+        if (!dense_inverse(nc, S, inv)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
+        for (int j = 0; j < nc; ++j)
+            for (int i = 2; i < nc; ++i) hU[(size_t)j * nt + (i - 2)] = inv[(size_t)j * nc + i];
+    }
+    auto& al = ctx->adj.allocs;
+    double2* wp = dalloc<double2>(ctx, hW.size(), al);
+    double* wt = dalloc<double>(ctx, hT.size(), al);
+    double* wu = dalloc<double>(ctx, hU.size(), al);
+    if (!wp || !wt || !wu) return fail(ctx, PIZZA_ENOMEM, "allocation of the adjoint solves failed");
+    CK(cudaMemcpy(wp, hW.data(), hW.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(wt, hT.data(), hT.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(wu, hU.data(), hU.size() * 8, cudaMemcpyHostToDevice));
+    ctx->adj.A = AdjFactors{wp, wt, wu};
+    return PIZZA_OK;
+}
+
+int ensure_adjoint(pizza_ctx* ctx) {
+    auto& a = ctx->adj;
+    if (a.ready) return PIZZA_OK;
+    if (ctx->coll || ctx->P.fp32 || ctx->scheme != PIZZA_CNAB2)
+        return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is implemented for CNAB2, integration, FP64");
+    if (ctx->n_phi > 3072) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is limited to n_phi <= 3072");
+    if (!ctx->dt_set) return fail(ctx, PIZZA_ESTATE, "dt is not set");
+    int rc = build_adjoint_factors(ctx);
+    if (rc) return rc;
+    bool ok = true;
+    a.lam = adj_vec(ctx, ok);
+    a.rho[0] = adj_vec(ctx, ok);
+    a.rho[1] = adj_vec(ctx, ok);
+    a.w = adj_vec(ctx, ok);
+    a.g = adj_vec(ctx, ok);
+    const size_t gsz = (size_t)ctx->n_r * 4 * ctx->M;
+    a.Gb1 = dalloc<double2>(ctx, gsz, a.allocs);
+    a.Gb2 = dalloc<double2>(ctx, gsz, a.allocs);
+    a.ra = dalloc<double>(ctx, ctx->M, a.allocs);
+    if (!ok || !a.Gb1 || !a.Gb2 || !a.ra) return fail(ctx, PIZZA_ENOMEM, "allocation of adjoint buffers failed");
+    a.ready = true;
+    return PIZZA_OK;
+}
+
+// after forward step number K (counted from the start of the tape): checkpoint
+// y_K and E(y_{K-1}) every a.every steps
+int tape_record(pizza_ctx* ctx) {
+    auto& a = ctx->adj;
+    a.K++;
+    a.pos = a.K;
+    if (a.K % a.every != 0) return PIZZA_OK;
+    bool ok = true;
+    VecSet y = adj_vec(ctx, ok, true), e = adj_vec(ctx, ok, true);
+    if (!ok) return fail(ctx, PIZZA_ENOMEM, "allocation of a checkpoint failed");
+    int rc = copy_vec(ctx, y, ctx->vec[ctx->ys[0]]);
+    if (!rc) rc = copy_vec(ctx, e, ctx->vec[ctx->es[0]]);
+    a.ck_y.push_back(y);
+    a.ck_e.push_back(e);
+    return rc;
+}
+
+// forward states y_{s*every + i} (i < every, up to K - 1) from checkpoint s
+int load_segment(pizza_ctx* ctx, int s) {
+    auto& a = ctx->adj;
+    if (a.seg == s) return PIZZA_OK;
+    bool ok = true;
+    while ((int)a.seg_y.size() < a.every) {
+        a.seg_y.push_back(adj_vec(ctx, ok));
+        if (!ok) return fail(ctx, PIZZA_ENOMEM, "allocation of the segment states failed");
+    }
+    const int n0 = s * a.every;
+    const int n1 = std::min(n0 + a.every, a.K);  // states n0 .. n1-1
+    const bool taping = a.taping;
+    a.taping = false;
+    reset_slots(ctx);
+    int rc = copy_vec(ctx, ctx->vec[ctx->ys[0]], a.ck_y[s]);
+    if (!rc && n0 > 0) rc = copy_vec(ctx, ctx->vec[ctx->es[0]], a.ck_e[s]);
+    if (rc) return rc;
+    ctx->n_done = n0;
+    ctx->aux_valid = false;
+    rc = ensure_aux(ctx);
+    if (rc) return rc;
+    rc = copy_vec(ctx, a.seg_y[0], ctx->vec[ctx->ys[0]]);
+    for (int n = n0 + 1; !rc && n < n1; ++n) {
+        rc = step_multistep(ctx);
+        if (rc) break;
+        ctx->n_done++;
+        rc = copy_vec(ctx, a.seg_y[n - n0], ctx->vec[ctx->ys[0]]);
+    }
+    a.taping = taping;
+    if (rc) return rc;
+    a.seg = s;
+    return PIZZA_OK;
+}
+
+// copy a caller's gradient (host or device, NULL = zero) into a.g
+int load_gradient(pizza_ctx* ctx, const double* g_theta, const double* g_psi, const double* g_u) {
+    auto& a = ctx->adj;
+    int rc = zero_vec(ctx, a.g);
+    if (rc) return rc;
+    const size_t vsz = (size_t)ctx->M * ctx->nc;
+    if (g_theta) CK(cudaMemcpyAsync(a.g.th, g_theta, vsz * 16, cudaMemcpyDefault, ctx->stream));
+    if (g_psi) CK(cudaMemcpyAsync(a.g.psi, g_psi, vsz * 16, cudaMemcpyDefault, ctx->stream));
+    if (g_u) CK(cudaMemcpyAsync(a.g.u, g_u, ctx->nc * 8, cudaMemcpyDefault, ctx->stream));
+    return PIZZA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -750,6 +979,7 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
     P.inv_a = 1.0 / g.a;
     P.tc = tc_coefficient(radius_ratio);
     P.cnorm = std::sqrt(2.0 / (n_r - 1));
+    P.inv_nphi = 1.0 / n_phi;
 
     std::vector<double> s(n_r), h2(n_r), is(n_r);
     const long double pi = 3.141592653589793238462643383279502884L;
@@ -786,6 +1016,27 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
     P.s = ds;
     P.h2 = dh;
     P.inv_s = di;
+    {
+        std::vector<float> sf(n_r), hf(n_r), isf(n_r);
+        for (int k = 0; k < n_r; ++k) {
+            sf[k] = (float)s[k];
+            hf[k] = (float)h2[k];
+            isf[k] = (float)is[k];
+        }
+        float* fs = dalloc<float>(ctx, n_r, al);
+        float* fh = dalloc<float>(ctx, n_r, al);
+        float* fi = dalloc<float>(ctx, n_r, al);
+        if (!fs || !fh || !fi) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(fs, sf.data(), n_r * 4);
+        up(fh, hf.data(), n_r * 4);
+        up(fi, isf.data(), n_r * 4);
+        P.s_f = fs;
+        P.h2_f = fh;
+        P.inv_s_f = fi;
+    }
 
     if (!make_fft_plan(2 * ctx->K, P.plan_r) || !make_fft_plan(n_phi, P.plan_p)) {
         ctx->err = "unsupported transform length";
@@ -829,6 +1080,22 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         }
         up(d, H.band[id].data(), H.band[id].size() * 8);
         P.ops.band[id] = d;
+        // the transposed operator in the same band storage: row n holds X[k][n],
+        // k = n-h..n+h (used by the adjoint)
+        const int h = op_h(id), W = 2 * h + 1, nc = ctx->nc;
+        std::vector<double> bt((size_t)nc * W, 0.0);
+        for (int n = 0; n < nc; ++n)
+            for (int d2 = 0; d2 < W; ++d2) {
+                const int k = n - h + d2;
+                if (k >= 0 && k < nc) bt[(size_t)n * W + d2] = H.band[id][(size_t)k * W + (n - k + h)];
+            }
+        double* dt_ = dalloc<double>(ctx, bt.size(), al);
+        if (!dt_) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(dt_, bt.data(), bt.size() * 8);
+        P.ops.bandT[id] = dt_;
     }
     {
         const int nc = ctx->nc;
@@ -987,6 +1254,10 @@ int pizza_step(pizza_ctx* ctx, int nsteps) {
             rc = is_multistep(ctx->scheme) ? step_multistep(ctx) : step_dirk(ctx);
         if (rc) return rc;
         ctx->n_done++;
+        if (ctx->adj.taping) {
+            rc = tape_record(ctx);
+            if (rc) return rc;
+        }
     }
     return PIZZA_OK;
 }
@@ -1133,6 +1404,129 @@ int pizza_get_grid(pizza_ctx* ctx, double* us, double* uphi, double* omega, doub
     return PIZZA_OK;
 }
 
+int pizza_tape_begin(pizza_ctx* ctx, int checkpoint_every) {
+    if (!ctx) return PIZZA_EINVAL;
+    if (checkpoint_every < 1) return fail(ctx, PIZZA_EINVAL, "checkpoint_every must be >= 1");
+    if (ctx->n_done != 0) return fail(ctx, PIZZA_ESTATE, "the tape starts right after pizza_set_state");
+    int rc = ensure_factors(ctx);
+    if (rc) return rc;
+    rc = ensure_adjoint(ctx);
+    if (rc) return rc;
+    auto& a = ctx->adj;
+    cudaStreamSynchronize(ctx->stream);
+    for (void* p : a.ck_allocs) cudaFree(p);
+    a.ck_allocs.clear();
+    a.ck_y.clear();
+    a.ck_e.clear();
+    a.every = checkpoint_every;
+    a.K = 0;
+    a.pos = 0;
+    a.seg = -1;
+    a.dRa = 0.0;
+    a.rcur = 0;
+    bool ok = true;
+    VecSet y = adj_vec(ctx, ok, true), e = adj_vec(ctx, ok, true);
+    if (!ok) return fail(ctx, PIZZA_ENOMEM, "allocation of a checkpoint failed");
+    rc = copy_vec(ctx, y, ctx->vec[ctx->ys[0]]);
+    if (rc) return rc;
+    a.ck_y.push_back(y);
+    a.ck_e.push_back(e);
+    rc = zero_vec(ctx, a.lam);
+    if (!rc) rc = zero_vec(ctx, a.rho[0]);
+    if (!rc) rc = zero_vec(ctx, a.rho[1]);
+    if (rc) return rc;
+    a.taping = true;
+    return PIZZA_OK;
+}
+
+int pizza_adjoint_step(pizza_ctx* ctx, const double* g_theta, const double* g_psi, const double* g_u,
+                       double* dJ_dRa) {
+    if (!ctx) return PIZZA_EINVAL;
+    auto& a = ctx->adj;
+    if (!a.ready || a.pos <= 0) return fail(ctx, PIZZA_ESTATE, "no recorded forward step left to reverse");
+    a.taping = false;
+    const int cur = a.pos, n = cur - 1;
+    // lam <- lam + g_cur: the full adjoint of y_cur
+    int rc = load_gradient(ctx, g_theta, g_psi, g_u);
+    if (rc) return rc;
+    CK(launch_vec_add(ctx->P, a.lam, a.g, ctx->stream));
+    VecSet rho = a.rho[a.rcur], rho_next = a.rho[1 - a.rcur];
+    if (cur == a.K) rc = zero_vec(ctx, rho_next);  // no step beyond y_K
+    if (rc) return rc;
+    // rho_n = P S^{-H} lam
+    CK(launch_adj_solve(ctx->P, a.A, a.lam, rho, ctx->stream));
+    // lam = (Mass + dt/2 Lin)^H rho_n,  w = dt (c rho_n - 1/2 rho_{n+1})
+    const double c = (n == 0) ? 1.0 : 1.5;
+    const double c2 = (cur < a.K) ? -0.5 : 0.0;
+    VecSet none{};
+    CK(launch_adj_apply(ctx->P, none, rho, rho_next, a.lam, a.w, ctx->dt, c, c2, ctx->stream));
+    // lam += J_E(y_n)* w
+    rc = load_segment(ctx, n / a.every);
+    if (rc) return rc;
+    VecSet y = a.seg_y[n % a.every];
+    StepParams P64 = ctx->P;
+    P64.fp32 = 0;
+    CK(launch_spec_to_grid(P64, y, ctx->G1, ctx->stream));
+    CK(launch_adj_explicit(P64, a.w, y, a.lam, ctx->G1, a.Gb2, a.Gb1, a.ra, ctx->stream));
+    std::vector<double> ra(ctx->M);
+    CK(cudaMemcpyAsync(ra.data(), a.ra, ctx->M * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int m = 0; m < ctx->M; ++m) a.dRa += ra[m];
+    a.rcur = 1 - a.rcur;
+    a.pos = n;
+    if (dJ_dRa) *dJ_dRa = a.dRa;
+    return PIZZA_OK;
+}
+
+int pizza_get_adjoint(pizza_ctx* ctx, double* theta_bar, double* psi_bar, double* uphi0_bar) {
+    if (!ctx) return PIZZA_EINVAL;
+    auto& a = ctx->adj;
+    if (!a.ready) return fail(ctx, PIZZA_ESTATE, "no adjoint has been computed");
+    const size_t vsz = (size_t)ctx->M * ctx->nc;
+    if (theta_bar) CK(cudaMemcpyAsync(theta_bar, a.lam.th, vsz * 16, cudaMemcpyDefault, ctx->stream));
+    if (psi_bar) CK(cudaMemcpyAsync(psi_bar, a.lam.psi, vsz * 16, cudaMemcpyDefault, ctx->stream));
+    if (uphi0_bar) CK(cudaMemcpyAsync(uphi0_bar, a.lam.u, ctx->nc * 8, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIZZA_OK;
+}
+
+int pizza_explicit_adjoint(pizza_ctx* ctx, const double* e_psi_bar, const double* e_theta_bar, const double* e_u_bar,
+                           double* psi_bar, double* theta_bar, double* uphi0_bar) {
+    if (!ctx) return PIZZA_EINVAL;
+    int rc = ensure_factors(ctx);
+    if (rc) return rc;
+    rc = ensure_adjoint(ctx);
+    if (rc) return rc;
+    auto& a = ctx->adj;
+    rc = load_gradient(ctx, e_theta_bar, e_psi_bar, e_u_bar);
+    if (!rc) rc = copy_vec(ctx, a.w, a.g);
+    if (!rc) rc = zero_vec(ctx, a.g);
+    if (rc) return rc;
+    VecSet y = ctx->vec[ctx->ys[0]];
+    StepParams P64 = ctx->P;
+    P64.fp32 = 0;
+    CK(launch_spec_to_grid(P64, y, ctx->G1, ctx->stream));
+    CK(launch_adj_explicit(P64, a.w, y, a.g, ctx->G1, a.Gb2, a.Gb1, a.ra, ctx->stream));
+    const size_t vsz = (size_t)ctx->M * ctx->nc;
+    if (theta_bar) CK(cudaMemcpyAsync(theta_bar, a.g.th, vsz * 16, cudaMemcpyDefault, ctx->stream));
+    if (psi_bar) CK(cudaMemcpyAsync(psi_bar, a.g.psi, vsz * 16, cudaMemcpyDefault, ctx->stream));
+    if (uphi0_bar) CK(cudaMemcpyAsync(uphi0_bar, a.g.u, ctx->nc * 8, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIZZA_OK;
+}
+
+int pizza_nusselt_weights(const pizza_ctx* ctx, double* w) {
+    if (!ctx || !w) return PIZZA_EINVAL;
+    if (ctx->coll) return PIZZA_EUNSUPPORTED;
+    // Nu - 1 = (d theta_0/ds)(s_o)/(dT_c/ds)(s_o) = sum_n w_n Re theta_hat_0n with
+    // w_n = C c_n n^2 / (a dT_c/ds(s_o)), c_0 = 1/2 (T_n'(1) = n^2, d/ds = (1/a) d/dx)
+    Geom g = make_geom(ctx->eta);
+    const double dtc = tc_coefficient(ctx->eta) / g.s_o;
+    const double C = std::sqrt(2.0 / (ctx->n_r - 1));
+    for (int n = 0; n < ctx->nc; ++n) w[n] = C * ((n == 0) ? 0.5 : 1.0) * (double)n * n / (g.a * dtc);
+    return PIZZA_OK;
+}
+
 int pizza_synchronize(pizza_ctx* ctx) {
     if (!ctx) return PIZZA_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1183,6 +1577,8 @@ void pizza_free(pizza_ctx* ctx) {
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     for (void* p : ctx->vec_allocs) cudaFree(p);
+    for (void* p : ctx->adj.allocs) cudaFree(p);
+    for (void* p : ctx->adj.ck_allocs) cudaFree(p);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }

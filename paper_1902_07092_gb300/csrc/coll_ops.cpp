@@ -275,6 +275,36 @@ bool inverse_columns(const Dense& A0, const std::vector<int>& rows, std::vector<
 
 }  // namespace
 
+bool dense_inverse(int n, const std::vector<cplx>& A, std::vector<cplx>& inv) {
+    Dense D;
+    D.n = n;
+    D.cx = true;
+    D.re.resize((size_t)n * n);
+    D.im.resize((size_t)n * n);
+    for (size_t i = 0; i < D.re.size(); ++i) {
+        D.re[i] = A[i].real();
+        D.im[i] = A[i].imag();
+    }
+    std::vector<int> rows(n);
+    for (int i = 0; i < n; ++i) rows[i] = i;
+    std::vector<double> xr, xi;
+    if (!inverse_columns(D, rows, xr, xi)) return false;
+    inv.resize((size_t)n * n);
+    for (size_t i = 0; i < inv.size(); ++i) inv[i] = cplx(xr[i], xi[i]);
+    return true;
+}
+
+bool dense_inverse(int n, const std::vector<double>& A, std::vector<double>& inv) {
+    Dense D;
+    D.n = n;
+    D.cx = false;
+    D.re = A;
+    std::vector<int> rows(n);
+    for (int i = 0; i < n; ++i) rows[i] = i;
+    std::vector<double> xi;
+    return inverse_columns(D, rows, inv, xi);
+}
+
 bool coll_inverse_wpsi(const CollGrid& c, double E, int m, double gdt, std::vector<cplx>& G) {
     const int N = c.N, n = 2 * N;
     Dense A;

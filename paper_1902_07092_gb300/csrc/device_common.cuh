@@ -42,6 +42,10 @@ __device__ __forceinline__ float2 creflect(float2 a, float2 s) {
     return make_float2(fmaf(2.0f, a.x, -s.x), fmaf(2.0f, a.y, -s.y));
 }
 
+// fused multiply-add in the precision of its arguments (never promoted to FP64)
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
 // Real type, constructor and conversions of the two complex types.
 template <class T>
 struct Cx;
@@ -58,6 +62,21 @@ struct Cx<float2> {
     __device__ static float2 make(double a, double b) { return make_float2((float)a, (float)b); }
     __device__ static float2 from(double2 a) { return make_float2((float)a.x, (float)a.y); }
     __device__ static const float2* tw(const FftPlan& p) { return p.twf; }
+};
+// radial tables in the precision of the complex type
+template <class T>
+struct Tab;
+template <>
+struct Tab<double2> {
+    __device__ static double s(const StepParams& P, int k) { return P.s[k]; }
+    __device__ static double h2(const StepParams& P, int k) { return P.h2[k]; }
+    __device__ static double is(const StepParams& P, int k) { return P.inv_s[k]; }
+};
+template <>
+struct Tab<float2> {
+    __device__ static float s(const StepParams& P, int k) { return P.s_f[k]; }
+    __device__ static float h2(const StepParams& P, int k) { return P.h2_f[k]; }
+    __device__ static float is(const StepParams& P, int k) { return P.inv_s_f[k]; }
 };
 __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
 __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2((double)a.x, (double)a.y); }
@@ -133,8 +152,8 @@ __device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __re
                 t2 = creflect(b1, t1);                // w1 v1 - w2 v2
             }
             T m1;
-            m1.x = fma((RT)-0.5, t1.x, v[0].x);
-            m1.y = fma((RT)-0.5, t1.y, v[0].y);
+            m1.x = fmat((RT)-0.5, t1.x, v[0].x);
+            m1.y = fmat((RT)-0.5, t1.y, v[0].y);
             // forward: -i*h3*t2 ; backward: +i*h3*t2
             T rt;
             if (SIGN < 0) {
@@ -145,10 +164,10 @@ __device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __re
                 rt.y = t2.x;
             }
             v[0] = cadd(v[0], t1);
-            v[1].x = fma(h3, rt.x, m1.x);
-            v[1].y = fma(h3, rt.y, m1.y);
-            v[2].x = fma(-h3, rt.x, m1.x);
-            v[2].y = fma(-h3, rt.y, m1.y);
+            v[1].x = fmat(h3, rt.x, m1.x);
+            v[1].y = fmat(h3, rt.y, m1.y);
+            v[2].x = fmat(-h3, rt.x, m1.x);
+            v[2].y = fmat(-h3, rt.y, m1.y);
         }
         const int idx = (j / Ns) * Ns * R + k;
 #pragma unroll
@@ -203,24 +222,32 @@ __device__ __forceinline__ double pow2_ratio(double a, double b) {
     const int e = max(-400, min(400, ilogb(a) - ilogb(b)));
     return ldexp(1.0, e);
 }
+// the exponent e of pow2_ratio, clamped to |e| <= lim
+__device__ __forceinline__ int pow2_exponent(double a, double b, int lim) {
+    if (!(a > 0.0) || !(b > 0.0)) return 0;
+    return max(-lim, min(lim, ilogb(a) - ilogb(b)));
+}
+__device__ __forceinline__ float pow2f(int e) { return ldexpf(1.0f, e); }
+__device__ __forceinline__ double pow2d(int e) { return ldexp(1.0, e); }
 
 // CTA-wide max over m < n of |re| + |im| of the nf <= 4 rows src + f*stride,
 // into out[f] (shared).  red: shared scratch of 4*32 doubles.  Whole CTA.
 template <class T>
 __device__ __forceinline__ void block_max_abs(const T* src, int stride, int nf, int n, double* out, double* red) {
-    double mx[4] = {0.0, 0.0, 0.0, 0.0};
+    using RT = typename Cx<T>::R;
+    RT mx[4] = {0, 0, 0, 0};
     for (int i = threadIdx.x; i < n; i += blockDim.x)
 #pragma unroll
         for (int f = 0; f < 4; ++f)
             if (f < nf) {
                 const T v = src[(size_t)f * stride + i];
-                mx[f] = fmax(mx[f], fabs((double)v.x) + fabs((double)v.y));
+                mx[f] = max(mx[f], abs(v.x) + abs(v.y));
             }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        for (int o = 16; o > 0; o >>= 1) mx[f] = fmax(mx[f], __shfl_xor_sync(0xffffffffu, mx[f], o));
-        if (lane == 0) red[f * 32 + warp] = mx[f];
+        for (int o = 16; o > 0; o >>= 1) mx[f] = max(mx[f], __shfl_xor_sync(0xffffffffu, mx[f], o));
+        if (lane == 0) red[f * 32 + warp] = (double)mx[f];
     }
     __syncthreads();
     if (threadIdx.x < nf) {
@@ -260,8 +287,8 @@ __device__ __forceinline__ void cheb_derivative_scan(const T* c, T* d, T* tmp, i
             const int k = 2 * i + q;
             if (k > 0) {
                 const RT f = (RT)(2 * k);
-                acc.x = fma(f, c[k].x, acc.x);
-                acc.y = fma(f, c[k].y, acc.y);
+                acc.x = fmat(f, c[k].x, acc.x);
+                acc.y = fmat(f, c[k].y, acc.y);
             }
             tmp[k] = acc;
         }
@@ -283,9 +310,61 @@ __device__ __forceinline__ void cheb_derivative_scan(const T* c, T* d, T* tmp, i
         }
     }
     __syncthreads();
+    const RT fs = (RT)scale, f0 = (RT)(0.5 * scale);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const RT f = (RT)((j == 0) ? 0.5 * scale : scale);
+        const RT f = (j == 0) ? f0 : fs;
         d[j] = (j + 1 < n) ? cscale(tmp[j + 1], f) : Cx<T>::make(0.0, 0.0);
+    }
+    __syncthreads();
+}
+
+// Transpose of cheb_derivative_scan: with d = D c, d_j = (2/c_j) sum_{k>j, k+j odd}
+// k c_k (times scale), returns out = D^T e:
+//   out_k = 2 k scale sum_{j<k, j+k odd} e_j / c_j   (c_0 = 2, c_j = 1),
+// i.e. prefix sums of e_j/c_j over each index parity.  Warp q (q = 0, 1) owns the
+// indices j = 2i + q; each lane sums a contiguous chunk, a shuffle scan adds the
+// totals of the chunks below it.  ``tmp`` is scratch of n entries.  Whole CTA
+// (>= 64 threads).
+template <class T>
+__device__ __forceinline__ void cheb_derivative_adjoint_scan(const T* e, T* out, T* tmp, int n, double scale) {
+    using RT = typename Cx<T>::R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 2) {
+        const int q = warp;
+        const int len = (n - q + 1) / 2;
+        const int per = (len + 31) / 32;
+        const int i0 = lane * per, i1 = min(i0 + per, len);
+        T acc = Cx<T>::make(0.0, 0.0);
+        for (int i = i0; i < i1; ++i) {
+            const int j = 2 * i + q;
+            const RT f = (j == 0) ? (RT)0.5 : (RT)1;
+            acc.x = fmat(f, e[j].x, acc.x);
+            acc.y = fmat(f, e[j].y, acc.y);
+            tmp[j] = acc;  // inclusive prefix within the chunk
+        }
+        // exclusive scan of the chunk totals over the lanes
+        T pfx = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const RT x = __shfl_up_sync(0xffffffffu, pfx.x, o);
+            const RT y = __shfl_up_sync(0xffffffffu, pfx.y, o);
+            if (lane >= o) {
+                pfx.x += x;
+                pfx.y += y;
+            }
+        }
+        const T off = csub(pfx, acc);
+        for (int i = i0; i < i1; ++i) {
+            const int j = 2 * i + q;
+            tmp[j] = cadd(tmp[j], off);
+        }
+    }
+    __syncthreads();
+    // out_k needs the inclusive prefix of the other parity up to k - 1
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        T v = Cx<T>::make(0.0, 0.0);
+        if (k > 0) v = cscale(tmp[k - 1], (RT)(2.0 * k * scale));
+        out[k] = v;
     }
     __syncthreads();
 }

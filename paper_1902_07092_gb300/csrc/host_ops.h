@@ -100,4 +100,9 @@ bool coll_inverse_wpsi(const CollGrid& c, double E, int m, double gdt, std::vect
 // Same for  f - gdt*kappa*(D2 + D1/s - q/s^2) f  with Dirichlet rows: G[i*(N-2) + j], i < N.
 bool coll_inverse_dir(const CollGrid& c, double kappa, double q, double gdt, std::vector<double>& G);
 
+// Inverse of a dense n x n matrix (row-major) by LU with row equilibration,
+// partial pivoting and one refinement step (coll_ops.cpp).
+bool dense_inverse(int n, const std::vector<cplx>& A, std::vector<cplx>& inv);
+bool dense_inverse(int n, const std::vector<double>& A, std::vector<double>& inv);
+
 }  // namespace pz

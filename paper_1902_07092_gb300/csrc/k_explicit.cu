@@ -47,16 +47,17 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
     T* cc1 = cc0 + N;        // first derivative
     T* cc2 = cc1 + N;        // second derivative
     const int tid = threadIdx.x, nth = blockDim.x;
-    const double C = P.cnorm;
+    // C w_n of Eq. cheb in the working precision (the state is converted first)
+    const RT Cw = (RT)P.cnorm, Cw0 = (RT)(0.5 * P.cnorm);
 
     for (int n = tid; n < N; n += nth) {
         T a = Cx<T>::make(0.0, 0.0);
         if (n < nc) {
-            const double w = (n == 0) ? 0.5 * C : C;
+            const RT w = (n == 0) ? Cw0 : Cw;
             if (m > 0)
-                a = Cx<T>::from(cscale(y.psi[(size_t)m * nc + n], w));
+                a = cscale(Cx<T>::from(y.psi[(size_t)m * nc + n]), w);
             else
-                a = Cx<T>::make(y.u[n] * w, 0.0);
+                a = Cx<T>::make((RT)y.u[n] * w, 0.0);
         }
         cc0[n] = a;
     }
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
                 else if (fid == 1) v = cc1[j];
                 else if (fid == 2) v = cc2[j];
                 else if (fid == 3)
-                    v = (j < nc) ? Cx<T>::from(cscale(y.th[(size_t)m * nc + j], (j == 0) ? 0.5 * C : C))
+                    v = (j < nc) ? cscale(Cx<T>::from(y.th[(size_t)m * nc + j]), (j == 0) ? Cw0 : Cw)
                                  : Cx<T>::make(0.0, 0.0);
                 else {
                     v.x = cc0[j].x;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
             const T* Z = R + b * L;
             for (int k = tid; k < N; k += nth) {
                 const T g = cscale(Z[k], (RT)0.5);  // value of the series at x_k
-                const RT s = (RT)P.s[k], h2 = (RT)P.h2[k], is = (RT)P.inv_s[k];
+                const RT s = Tab<T>::s(P, k), h2 = Tab<T>::h2(P, k), is = Tab<T>::is(P, k);
                 T* out = G1 + g_index(k, 0, m, M);
                 // out[0] = v, out[M] = u_phi, out[2M] = omega, out[3M] = theta
                 if (fid == 0) {
@@ -163,12 +164,11 @@ __device__ __forceinline__ void load_packed_spectrum(T* Z, const T* __restrict__
 }
 
 // Split the transform Y of a + i b (a, b real fields) into the spectra of a and
-// b, scaled by sa / Pn and sb / Pn.
+// b, scaled by ia and ib (1/Pn times the inverse packing weights).
 template <class T>
 __device__ __forceinline__ void store_split_spectrum(const T* Y, T* __restrict__ dst, int M, int Pn, int n_m,
-                                                     double sa, double sb) {
+                                                     typename Cx<T>::R ia, typename Cx<T>::R ib) {
     using RT = typename Cx<T>::R;
-    const RT ia = (RT)(sa / (double)Pn), ib = (RT)(sb / (double)Pn);
     const RT h = (RT)0.5;
     for (int m = threadIdx.x; m <= n_m; m += blockDim.x) {
         T a, b;
@@ -188,13 +188,20 @@ __device__ __forceinline__ void store_split_spectrum(const T* Y, T* __restrict__
     }
 }
 
-// balancing weights are limited further in FP32 (exponent range of float)
+// exact powers of two in the working precision; balancing exponents are
+// limited further in FP32 (exponent range of float)
 template <class T>
-__device__ __forceinline__ double pow2_ratio_t(double a, double b) {
-    const double r = pow2_ratio(a, b);
-    if (sizeof(typename Cx<T>::R) == 8) return r;
-    return fmin(fmax(r, 0x1p-40), 0x1p40);
-}
+struct P2;
+template <>
+struct P2<double2> {
+    static constexpr int lim = 400;
+    __device__ static double v(int e) { return pow2d(e); }
+};
+template <>
+struct P2<float2> {
+    static constexpr int lim = 40;
+    __device__ static float v(int e) { return pow2f(e); }
+};
 
 template <class T>
 __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* __restrict__ G1,
@@ -212,9 +219,11 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* 
     // g1 = v + i l1 u_phi, g2 = omega + i l2 theta
     __shared__ double red[4 * 32], mx[4];
     block_max_abs(G1 + g_index(k, 0, 0, M), M, 4, n_m + 1, mx, red);
-    const double l1 = pow2_ratio_t<T>(mx[0], mx[1]), l2 = pow2_ratio_t<T>(mx[2], mx[3]);
+    const int e1 = pow2_exponent(mx[0], mx[1], P2<T>::lim), e2 = pow2_exponent(mx[2], mx[3], P2<T>::lim);
+    const RT l1 = P2<T>::v(e1), l2 = P2<T>::v(e2);
+    const RT iP = (RT)P.inv_nphi;  // 1/n_phi, a power of two divided by 3
 
-    load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, (RT)1, (RT)l1);
+    load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, (RT)1, l1);
     T* R = fft_batched<+1>(X, Y, P.plan_p, 1);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* 
         if (j < Pn) reg[i] = R[j];
     }
     __syncthreads();
-    load_packed_spectrum(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m, (RT)1, (RT)l2);
+    load_packed_spectrum(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m, (RT)1, l2);
     R = fft_batched<+1>(X, Y, P.plan_p, 1);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* 
     T* other = (R == X) ? Y : X;
     T* S = fft_batched<-1>(R, other, P.plan_p, 1);
     // g1 Re(g2) = v omega + i l1 u_phi omega
-    store_split_spectrum(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, 1.0, 1.0 / l1);
+    store_split_spectrum(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, iP, iP * P2<T>::v(-e1));
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
@@ -245,7 +254,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* 
     }
     S = fft_batched<-1>(X, Y, P.plan_p, 1);
     // g1 Im(g2) = l2 (v theta + i l1 u_phi theta)
-    store_split_spectrum(S, G2 + g_index(k, 2, 0, M), M, Pn, n_m, 1.0 / l2, 1.0 / (l1 * l2));
+    store_split_spectrum(S, G2 + g_index(k, 2, 0, M), M, Pn, n_m, iP * P2<T>::v(-e2), iP * P2<T>::v(-e1 - e2));
 }
 
 // ---------------------------------------------------------------------------
@@ -301,16 +310,14 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
             const int f = (b0 + b == 0) ? 0 : 2;
             T* z = bufA + b * L;
             for (int j = tid; j <= K; j += nth)
-                even_extend_store(z, K, j, cscale(G2[g_index(j, f, m, M)], (RT)P.h2[j]));
+                even_extend_store(z, K, j, cscale(G2[g_index(j, f, m, M)], Tab<T>::h2(P, j)));
         }
         T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        const RT iK = (RT)(1.0 / (double)K), hK = (RT)(0.5 / (double)K);
         for (int b = 0; b < nb; ++b) {
             T* dst = (b0 + b == 0) ? cc0 : cc1;
             const T* Z = R + b * L;
-            for (int n = tid; n <= K; n += nth) {
-                const double w = (n == 0 || n == K) ? 0.5 : 1.0;
-                dst[n] = cscale(Z[n], (RT)(w / (double)K));
-            }
+            for (int n = tid; n <= K; n += nth) dst[n] = cscale(Z[n], (n == 0 || n == K) ? hK : iK);
         }
         __syncthreads();
     }
@@ -343,7 +350,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
             T* dst = (fld == 0) ? cc2 : cc0;
             for (int k = tid; k <= K; k += nth) {
                 const T dF = cscale(Z[k], (RT)0.5);
-                const RT is = (RT)P.inv_s[k];
+                const RT is = Tab<T>::is(P, k);
                 T val;
                 if (fld == 0) {
                     if (m > 0) {
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
                         val = cscale(cadd(dF, cmul_i(uw, dm)), is);
                     } else {
                         const T vw = G2[g_index(k, 0, m, M)];
-                        val = cscale(vw, (RT)P.h2[k] * is);
+                        val = cscale(vw, Tab<T>::h2(P, k) * is);
                     }
                 } else {
                     const T ut = G2[g_index(k, 3, m, M)];
@@ -377,7 +384,8 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
             const T* Z = R + b * L;
             // for NB == 1 the theta pass reads cc0 and writes cc2, which holds
             // nothing needed any more (N_omega_hat went to cc1)
-            for (int n = tid; n < nc; n += nth) dst[n] = cscale(Z[n], (RT)(0.5 * P.cnorm));
+            const RT hc = (RT)(0.5 * P.cnorm);
+            for (int n = tid; n < nc; n += nth) dst[n] = cscale(Z[n], hc);
         }
         __syncthreads();
     }

@@ -156,6 +156,7 @@ extern "C" int pizza_explicit_terms_noalloc(int n_r, int n_phi, double Ra, doubl
     P.inv_a = 1.0 / g.a;
     P.tc = tc_coefficient(radius_ratio);
     P.cnorm = std::sqrt(2.0 / (n_r - 1));
+    P.inv_nphi = 1.0 / n_phi;
     P.s = sl->tables;
     P.h2 = sl->tables + NA_MAX_NR;
     P.inv_s = sl->tables + 2 * NA_MAX_NR;

@@ -33,6 +33,7 @@ struct VecSet {
 // Banded m-independent operators (band storage, half width h, row-major [nc][2h+1]).
 struct DevOps {
     const double* band[OP_COUNT];
+    const double* bandT[OP_COUNT];  // transposed operators in the same band storage (adjoint)
     const double* tau_psi_B;  // 4 x (nc-4): tau rows restricted to columns 4..
     const double* tau_dir_B;  // 2 x (nc-2)
     const double* tau_psi;    // 4 x nc: the full streamfunction tau rows
@@ -60,12 +61,22 @@ struct DevFactors {
 };
 
 // Scalar parameters passed by value to every kernel.
+// Dense adjoint solves P S^{-H} for the implicit weight of CNAB2, column-major:
+// Wp [M][nc][nc-4] complex (streamfunction, rows below its 4 tau rows),
+// Wt [M][nc][nc-2], Wu [nc][nc-2] real (temperature, zonal flow).
+struct AdjFactors {
+    const double2* Wp;
+    const double* Wt;
+    const double* Wu;
+};
+
 struct StepParams {
     int n_r, n_phi, n_m, M, nc, K;   // K = n_r - 1
-    double E, Ra, Pr, s_o, inv_a, tc, cnorm;
+    double E, Ra, Pr, s_o, inv_a, tc, cnorm, inv_nphi;
     const double* s;      // [n_r] radial grid
     const double* h2;     // [n_r]
     const double* inv_s;  // [n_r]
+    const float *s_f, *h2_f, *inv_s_f;  // the same in FP32 (mixed-precision explicit stage)
     FftPlan plan_r;       // length 2K (radial DCT-I)
     FftPlan plan_p;       // length n_phi (azimuthal)
     DevOps ops;
@@ -106,6 +117,12 @@ cudaError_t launch_coll_from_hat(const StepParams& P, VecSet hat, VecSet y, cuda
 cudaError_t launch_coll_to_hat(const StepParams& P, VecSet y, VecSet out, cudaStream_t st);
 cudaError_t launch_phi_fields(const StepParams& P, const double2* G1, double* us, double* uphi, double* omega,
                               double* theta, cudaStream_t st);
+cudaError_t launch_adj_explicit(const StepParams& P, VecSet w, VecSet y, VecSet lam, const double2* G1, double2* Gb2,
+                                double2* Gb1, double* ra, cudaStream_t st);
+cudaError_t launch_adj_solve(const StepParams& P, const AdjFactors& A, VecSet lam, VecSet rho, cudaStream_t st);
+cudaError_t launch_adj_apply(const StepParams& P, VecSet g, VecSet rho, VecSet rho_next, VecSet lam, VecSet w,
+                             double dt, double c, double c2, cudaStream_t st);
+cudaError_t launch_vec_add(const StepParams& P, VecSet a, VecSet b, cudaStream_t st);
 cudaError_t launch_diagnostics(const StepParams& P, const double2* G1, const double* q, double* mode_sums,
                                double* radius_max, cudaStream_t st);
 
