@@ -42,8 +42,17 @@ KERNELS = ("spec_to_grid", "phi_products", "grid_to_spec", "solve")
 
 
 def critical_rayleigh(E):
+    """Ra_c from the oracle's table; between tabulated E, log-log interpolation."""
     t = json.load(open(os.path.join(ROOT, "tests", "golden", "critical_rayleigh.json")))
-    return t["%g" % E]["Ra_c"]
+    key = "%g" % E
+    if key in t:
+        return t[key]["Ra_c"]
+    pts = sorted((float(k), v["Ra_c"]) for k, v in t.items())
+    for (e0, r0), (e1, r1) in zip(pts, pts[1:]):
+        if e0 <= E <= e1:
+            f = (math.log(E) - math.log(e0)) / (math.log(e1) - math.log(e0))
+            return math.exp(math.log(r0) + f * (math.log(r1) - math.log(r0)))
+    raise KeyError("no critical Rayleigh number for E = %g" % E)
 
 
 # ----------------------------------------------------------- flop counts ----
@@ -240,6 +249,110 @@ def mixed_error(args, B, wl, Ra, sol, th, z, zu):
     return out
 
 
+def adjoint_cost(args, B, wl, Ra, sol, th, z, zu):
+    """Discrete adjoint of a CNAB2 run of args.steps steps (J = time-averaged
+    Nusselt number): wall time of the taped forward run and of the checkpointed
+    reverse sweep (which recomputes the forward states segment by segment)."""
+    import torch
+    K = args.steps
+    every = int(wl.get("checkpoint_every", 20))
+    w = sol.nusselt_weights()
+    g = np.zeros((sol.M, sol.n_c), np.complex128)
+    g[0] = w / K
+    sol.set_state(th, z, zu)
+    sol.tape_begin(every)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sol.step(K)
+    B.pizza_synchronize(sol.ctx)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(K):
+        dRa = sol.adjoint_step(g_theta=g)
+    B.pizza_synchronize(sol.ctx)
+    t_rev = time.perf_counter() - t0
+    return {"steps": K, "checkpoint_every": every, "forward_ms_per_step": 1e3 * t_fwd / K,
+            "reverse_ms_per_step": 1e3 * t_rev / K, "reverse_over_forward": t_rev / t_fwd,
+            "dJ_dRa": dRa, "objective": "J = (1/K) sum_n (Nu_n - 1)",
+            "timing": "wall clock, synchronised, inputs resident; reverse includes the segment recomputation"}
+
+
+def run_batch(args, wl, rank, world, local_rank):
+    """64 independent CNAB2 runs of uneven sizes advanced args.steps steps by one
+    CUDA graph (pizza_batch_step), each context autotuned first; timed against
+    the same contexts stepped one after another."""
+    import torch
+    from paper_1902_07092_gb300 import binding as B
+    torch.cuda.set_device(local_rank)
+    runs = inputs.batch_runs(wl["batch"])
+    sols, states = [], []
+    t0 = time.perf_counter()
+    for r in runs:
+        Ra = r["ra_factor"] * critical_rayleigh(r["E"])
+        s = B.Solver(r["n_r"], r["n_phi"], r["E"], Ra, r["Pr"], r["eta"], r["scheme"], r["dt"])
+        th = inputs.theta_init(r["n_r"], r["n_phi"], r["amp"], r["seed"] + 1000 * rank, cfg=r["cfg"])
+        z, zu = inputs.zero_state(r["n_r"], r["n_phi"])
+        s.set_state(th, z, zu)
+        s.step(1)                      # factor set-up outside the timing
+        sols.append(s)
+        states.append((th, z, zu))
+    setup_s = time.perf_counter() - t0
+    tuned = [s.autotune() for s in sols]
+    K = args.steps if args.steps_given else wl["steps"]
+    gp_steps = sum(r["n_r"] * r["n_phi"] for r in runs) * K
+    # plain: one context after another
+    for s, st in zip(sols, states):
+        s.set_state(*st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in sols:
+        s.step(K)
+        B.pizza_synchronize(s.ctx)
+    plain_s = time.perf_counter() - t0
+    # one graph for all runs: capture + first launch, then the timed relaunch
+    batch = B.Batch(sols)
+    for s, st in zip(sols, states):
+        s.set_state(*st)
+    t0 = time.perf_counter()
+    batch.step(K)
+    torch.cuda.synchronize()
+    capture_s = time.perf_counter() - t0
+    for s, st in zip(sols, states):
+        s.set_state(*st)
+    torch.cuda.synchronize()
+    stream = torch.cuda.ExternalStream(batch.stream)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        a.record(stream)
+        batch.step(K)
+        b.record(stream)
+        torch.cuda.synchronize()
+    graph_ms = a.elapsed_time(b)
+    graph_ms = max_over_ranks(graph_ms, world, torch.device("cuda", local_rank))
+    finite = all(np.all(np.isfinite(x)) for s in sols for x in s.get_state())
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * gp_steps / (graph_ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": 1, "ms_per_step": graph_ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "batch64", "runs": len(runs), "scheme": "CNAB2", "radial": "chebyshev-integration-tau",
+                           "sizes": "n_r in {65,129,257,513} x n_phi in {192,384,768,1536}, seeds 1000..1063",
+                           "l2": "working set of all runs larger than L2 (no flush)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "batch": {"graph_ms": graph_ms, "plain_ms": 1e3 * plain_s, "speedup_vs_plain": 1e3 * plain_s / graph_ms,
+                          "capture_and_first_launch_ms": 1e3 * capture_s, "setup_s": setup_s,
+                          "autotuned": sorted(set(map(tuple, tuned))), "finite": bool(finite),
+                          "timing": "CUDA events on the batch stream around one graph launch of all runs"},
+                "e2e": {"value": gp_steps / plain_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0, "note": "plain: contexts stepped one after another"},
+                "gpu_launches": launches_per_step("CNAB2") * K * len(runs),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for s in sols:
+        s.close()
+
+
 def run_native(args, wl, Ra, rank, world, local_rank):
     import torch
     from paper_1902_07092_gb300 import binding as B
@@ -313,6 +426,7 @@ def run_native(args, wl, Ra, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     nbytes = 2 * M * nc * 16 + nc * 8
     err = mixed_error(args, B, wl, Ra, sol, th, z, zu) if args.precision == "mixed" else None
+    adj = adjoint_cost(args, B, wl, Ra, sol, th, z, zu) if wl.get("adjoint") else None
 
     if rank != 0:
         sol.close()
@@ -342,6 +456,8 @@ def run_native(args, wl, Ra, rank, world, local_rank):
     }
     if err is not None:
         line["error_vs_fp64"] = err
+    if adj is not None:
+        line["adjoint"] = adj
     if not args.no_cpu_baseline and world == 1:
         n, t_cpu, _ = oracle_sample(wl, Ra, budget_s=args.cpu_budget, max_steps=1000)
         line["cpu_baseline"] = {"value": gp * n / t_cpu / 1e6, "unit": UNIT, "cores": cores_used(),
@@ -354,7 +470,7 @@ def run_native(args, wl, Ra, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="sparse_n257_p768", choices=sorted(inputs.WORKLOADS))
@@ -362,10 +478,27 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    args.steps_given = args.steps is not None
+    if args.steps is None:
+        args.steps = 100
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     wl = inputs.WORKLOADS[args.workload]
+    if wl.get("batch"):
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the oracle has no batched mode; "
+                                  "its per-run rate is the cpu_baseline of the single-run workloads"}))
+            return
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        run_batch(args, wl, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     Ra = wl["ra_factor"] * critical_rayleigh(wl["E"])
     if args.impl == "reference":
         run_reference(args, wl, Ra, rank)

@@ -199,6 +199,30 @@ int pizza_explicit_adjoint(pizza_ctx *ctx, const double *e_psi_bar, const double
  * PIZZA_EUNSUPPORTED for the collocation formulation. */
 int pizza_nusselt_weights(const pizza_ctx *ctx, double *w);
 
+/* Autotuner: times the explicit stage of the context (on its current state)
+ * for each launch shape the device allows -- radial transforms batched one or two
+ * per shared-memory pass, 128/256/512 threads in the azimuthal kernel -- and
+ * keeps the fastest for later steps.  The shapes change the schedule, not the
+ * arithmetic: results are bitwise the same.  *nb_r and *phi_threads (may be NULL)
+ * receive the choice.  Integration formulation only. */
+int pizza_autotune(pizza_ctx *ctx, int *nb_r, int *phi_threads);
+
+/* Batches of independent contexts (any sizes, parameters and schemes) advanced
+ * by one CUDA graph: pizza_batch_step captures the nsteps steps of every context,
+ * each on its own stream forked from the batch's stream, instantiates the graph
+ * once and launches it; a later call with the same nsteps relaunches it when every
+ * context is back in the slot state the graph started from (e.g. after
+ * pizza_set_state, or a whole number of ring periods later), else recaptures.
+ * Factors are built before the capture.  The call returns without waiting; work
+ * later queued on a context's stream is ordered after the graph.  The contexts must
+ * outlive the batch and must not record an adjoint tape.  Errors go to
+ * pizza_last_error(NULL). */
+typedef struct pizza_batch pizza_batch;
+int pizza_batch_create(pizza_batch **out, pizza_ctx *const *ctxs, int n);
+int pizza_batch_step(pizza_batch *b, int nsteps);
+void *pizza_batch_stream(pizza_batch *b);  /* the cudaStream_t the graph is launched on */
+void pizza_batch_free(pizza_batch *b);
+
 /* Per-kernel timing.  pizza_profile_begin starts recording a CUDA event pair on
  * the context stream around every later launch of the kernels selected by mask
  * (bit 0 spectral-to-grid, bit 1 azimuthal products, bit 2 grid-to-spectral,

@@ -24,7 +24,8 @@ EXPORTS = ("pizza_init", "pizza_set_option", "pizza_set_stream", "pizza_get_size
            "pizza_profile_begin", "pizza_profile_end", "pizza_synchronize",
            "pizza_host_operator", "pizza_host_collocation", "pizza_explicit_terms_noalloc", "pizza_free",
            "pizza_last_error", "pizza_tape_begin", "pizza_adjoint_step", "pizza_get_adjoint",
-           "pizza_explicit_adjoint", "pizza_nusselt_weights")
+           "pizza_explicit_adjoint", "pizza_nusselt_weights", "pizza_autotune", "pizza_batch_create",
+           "pizza_batch_step", "pizza_batch_stream", "pizza_batch_free")
 
 _lib = None
 
@@ -67,13 +68,20 @@ def load():
     lib.pizza_get_adjoint.argtypes = [vp, dp, dp, dp]
     lib.pizza_explicit_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp]
     lib.pizza_nusselt_weights.argtypes = [vp, dp]
+    lib.pizza_autotune.argtypes = [vp, ip, ip]
+    lib.pizza_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), i]
+    lib.pizza_batch_step.argtypes = [vp, i]
+    lib.pizza_batch_stream.argtypes = [vp]
+    lib.pizza_batch_stream.restype = vp
+    lib.pizza_batch_free.argtypes = [vp]
+    lib.pizza_batch_free.restype = None
     lib.pizza_explicit_terms_noalloc.argtypes = [i, i, d, d, d, dp, dp, dp, dp, dp, dp, vp]
     lib.pizza_free.argtypes = [vp]
     lib.pizza_free.restype = None
     lib.pizza_last_error.argtypes = [vp]
     lib.pizza_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("pizza_free", "pizza_last_error"):
+        if name not in ("pizza_free", "pizza_last_error", "pizza_batch_free", "pizza_batch_stream"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -199,6 +207,41 @@ def pizza_nusselt_weights(ctx, n_c):
     return w
 
 
+def pizza_autotune(ctx):
+    nb, th = ctypes.c_int(), ctypes.c_int()
+    _check(load().pizza_autotune(ctx, ctypes.byref(nb), ctypes.byref(th)), ctx)
+    return nb.value, th.value
+
+
+class Batch:
+    """Several contexts advanced together by one CUDA graph (pizza_batch_*)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        _check(load().pizza_batch_create(ctypes.byref(h), arr, len(self.solvers)))
+        self.h = h
+
+    def step(self, nsteps):
+        _check(load().pizza_batch_step(self.h, nsteps))
+
+    @property
+    def stream(self):
+        return load().pizza_batch_stream(self.h)
+
+    def close(self):
+        if self.h is not None:
+            load().pizza_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def pizza_host_collocation(which, n_r, radius_ratio, E=1.0, Pr=1.0, m=1, gdt=0.0):
     shape = {0: (2 * n_r, n_r - 2), 1: (n_r, n_r - 2), 2: (n_r, n_r - 2), 3: (n_r, n_r), 4: (n_r, n_r)}[which]
     out = np.zeros(shape, np.complex128 if which == 0 else np.float64)
@@ -288,6 +331,9 @@ class Solver:
         pizza_explicit_adjoint(self.ctx, c(e_psi_bar, np.complex128), c(e_theta_bar, np.complex128),
                                c(e_u_bar, np.float64), ps, th, up)
         return ps, th, up
+
+    def autotune(self):
+        return pizza_autotune(self.ctx)
 
     def nusselt_weights(self):
         return pizza_nusselt_weights(self.ctx, self.n_c)

@@ -1527,6 +1527,241 @@ int pizza_nusselt_weights(const pizza_ctx* ctx, double* w) {
     return PIZZA_OK;
 }
 
+int pizza_autotune(pizza_ctx* ctx, int* nb_r, int* phi_thr) {
+    if (!ctx) return PIZZA_EINVAL;
+    if (ctx->coll) return fail(ctx, PIZZA_EUNSUPPORTED, "the autotuner covers the integration formulation");
+    int dev = 0, smax = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int keep_nb = ctx->P.nb_r, keep_th = ctx->P.phi_threads;
+    std::vector<std::pair<int, int>> cand;
+    for (int nb = 1; nb <= 2; ++nb)
+        for (int th : {128, 256, 512}) {
+            if (ctx->n_phi > th * 12) continue;  // the azimuthal kernel holds 12 points per thread
+            ctx->P.nb_r = nb;
+            ctx->P.phi_threads = th;
+            if (smem_spec_to_grid(ctx->P) > (size_t)smax || smem_grid_to_spec(ctx->P) > (size_t)smax) continue;
+            cand.push_back({nb, th});
+        }
+    cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
+    VecSet y = ctx->vec[ctx->ys[0]], e = ctx->vec[15];
+    float best = 1e30f;
+    std::pair<int, int> pick{keep_nb, keep_th};
+    for (auto c : cand) {
+        ctx->P.nb_r = c.first;
+        ctx->P.phi_threads = c.second;
+        int rc = explicit_eval(ctx, y, e);  // warm-up
+        if (rc) return rc;
+        CK(cudaEventRecord(a, ctx->stream));
+        for (int r = 0; r < 5; ++r) {
+            rc = explicit_eval(ctx, y, e);
+            if (rc) return rc;
+        }
+        CK(cudaEventRecord(b, ctx->stream));
+        CK(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    ctx->event_pool.push_back(a);
+    ctx->event_pool.push_back(b);
+    ctx->P.nb_r = pick.first;
+    ctx->P.phi_threads = pick.second;
+    if (nb_r) *nb_r = pick.first;
+    if (phi_thr) *phi_thr = pick.second;
+    return PIZZA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many contexts advanced by one CUDA graph.  The step sequences of all
+// contexts are captured on their own streams, forked from and joined to the
+// batch's stream, so independent runs execute concurrently on the GPU.  A graph
+// is kept with the slot state (rings, step count) of every context at its start
+// and end, and relaunched when the contexts are back in its start state.
+// ---------------------------------------------------------------------------
+namespace {
+struct Snap {
+    int ys[4], es[4], ms[3], is[3], n_done;
+    bool aux_valid;
+    bool same_start(const pizza_ctx* c) const {
+        if (std::memcmp(ys, c->ys, sizeof ys) || std::memcmp(es, c->es, sizeof es) || std::memcmp(ms, c->ms, sizeof ms) ||
+            std::memcmp(is, c->is, sizeof is) || aux_valid != c->aux_valid)
+            return false;
+        // the coefficients depend on the step count only during the start-up steps
+        return n_done == c->n_done || (n_done >= 3 && c->n_done >= 3);
+    }
+};
+Snap snap_of(const pizza_ctx* c) {
+    Snap s;
+    std::memcpy(s.ys, c->ys, sizeof s.ys);
+    std::memcpy(s.es, c->es, sizeof s.es);
+    std::memcpy(s.ms, c->ms, sizeof s.ms);
+    std::memcpy(s.is, c->is, sizeof s.is);
+    s.n_done = c->n_done;
+    s.aux_valid = c->aux_valid;
+    return s;
+}
+void restore_snap(pizza_ctx* c, const Snap& s, int n_done) {
+    std::memcpy(c->ys, s.ys, sizeof s.ys);
+    std::memcpy(c->es, s.es, sizeof s.es);
+    std::memcpy(c->ms, s.ms, sizeof s.ms);
+    std::memcpy(c->is, s.is, sizeof s.is);
+    c->aux_valid = s.aux_valid;
+    c->n_done = n_done;
+}
+}  // namespace
+
+struct pizza_batch {
+    std::vector<pizza_ctx*> ctxs;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraphExec_t exec = nullptr;
+    int graph_steps = 0;
+    std::vector<Snap> start, end;
+};
+
+namespace {
+int batch_fail(int code, const char* msg) {
+    set_global_error(msg);
+    return code;
+}
+int step_one(pizza_ctx* ctx) {
+    int rc;
+    if (ctx->coll)
+        rc = is_multistep(ctx->scheme) ? step_multistep_coll(ctx) : step_dirk_coll(ctx);
+    else
+        rc = is_multistep(ctx->scheme) ? step_multistep(ctx) : step_dirk(ctx);
+    if (!rc) ctx->n_done++;
+    return rc;
+}
+}  // namespace
+
+extern "C" {
+
+int pizza_batch_create(pizza_batch** out, pizza_ctx* const* ctxs, int n) {
+    if (!out || !ctxs || n < 1) return batch_fail(PIZZA_EINVAL, "pizza_batch_create: invalid arguments");
+    *out = nullptr;
+    pizza_batch* b = new pizza_batch();
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) {
+            delete b;
+            return batch_fail(PIZZA_EINVAL, "pizza_batch_create: NULL context");
+        }
+        if (ctxs[i]->adj.taping) {
+            delete b;
+            return batch_fail(PIZZA_ESTATE, "pizza_batch_create: a context is recording a tape");
+        }
+        b->ctxs.push_back(ctxs[i]);
+    }
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        pizza_batch_free(b);
+        return batch_fail(PIZZA_ECUDA, "pizza_batch_create: stream or event creation failed");
+    }
+    b->joins.resize(n);
+    for (int i = 0; i < n; ++i)
+        if (cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) != cudaSuccess) {
+            pizza_batch_free(b);
+            return batch_fail(PIZZA_ECUDA, "pizza_batch_create: event creation failed");
+        }
+    *out = b;
+    return PIZZA_OK;
+}
+
+int pizza_batch_step(pizza_batch* b, int nsteps) {
+    if (!b || nsteps < 0) return batch_fail(PIZZA_EINVAL, "pizza_batch_step: invalid arguments");
+    if (nsteps == 0) return PIZZA_OK;
+    const int n = (int)b->ctxs.size();
+    // set-up outside the graph: factors, first mass/implicit terms; then order the
+    // batch stream after everything already queued on the contexts' streams
+    for (int i = 0; i < n; ++i) {
+        pizza_ctx* c = b->ctxs[i];
+        int rc = ensure_factors(c);
+        if (!rc) rc = ensure_aux(c);
+        if (rc) return batch_fail(rc, c->err.c_str());
+        if (cudaEventRecord(b->joins[i], c->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(b->stream, b->joins[i], 0) != cudaSuccess)
+            return batch_fail(PIZZA_ECUDA, "pizza_batch_step: event ordering failed");
+    }
+    bool reuse = b->exec && b->graph_steps == nsteps;
+    for (int i = 0; reuse && i < n; ++i) reuse = b->start[i].same_start(b->ctxs[i]);
+    if (!reuse) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        b->start.assign(n, Snap{});
+        b->end.assign(n, Snap{});
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return batch_fail(PIZZA_ECUDA, "pizza_batch_step: stream capture failed to start");
+        int rc = PIZZA_OK;
+        if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) rc = PIZZA_ECUDA;
+        for (int i = 0; !rc && i < n; ++i) {
+            pizza_ctx* c = b->ctxs[i];
+            if (cudaStreamWaitEvent(c->stream, b->fork, 0) != cudaSuccess) {
+                rc = PIZZA_ECUDA;
+                break;
+            }
+            b->start[i] = snap_of(c);
+            for (int s = 0; !rc && s < nsteps; ++s) rc = step_one(c);
+            b->end[i] = snap_of(c);
+            if (!rc && (cudaEventRecord(b->joins[i], c->stream) != cudaSuccess ||
+                        cudaStreamWaitEvent(b->stream, b->joins[i], 0) != cudaSuccess))
+                rc = PIZZA_ECUDA;
+        }
+        const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+        if (rc || ec != cudaSuccess || !graph) {
+            // the captured sequence did not run: put the contexts back
+            for (int i = 0; i < n; ++i)
+                if (b->start.size() > (size_t)i) restore_snap(b->ctxs[i], b->start[i], b->start[i].n_done);
+            if (graph) cudaGraphDestroy(graph);
+            return batch_fail(rc ? rc : PIZZA_ECUDA, "pizza_batch_step: capture of the step sequence failed");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            for (int i = 0; i < n; ++i) restore_snap(b->ctxs[i], b->start[i], b->start[i].n_done);
+            b->exec = nullptr;
+            return batch_fail(PIZZA_ECUDA, "pizza_batch_step: graph instantiation failed");
+        }
+        b->graph_steps = nsteps;
+        // the capture advanced the host bookkeeping; undo it, the launch below redoes it
+        for (int i = 0; i < n; ++i) restore_snap(b->ctxs[i], b->start[i], b->start[i].n_done);
+    }
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess)
+        return batch_fail(PIZZA_ECUDA, "pizza_batch_step: graph launch failed");
+    for (int i = 0; i < n; ++i) {
+        pizza_ctx* c = b->ctxs[i];
+        restore_snap(c, b->end[i], c->n_done + nsteps);
+    }
+    // later work on any context's stream waits for the graph
+    if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return batch_fail(PIZZA_ECUDA, "event record failed");
+    for (int i = 0; i < n; ++i)
+        if (cudaStreamWaitEvent(b->ctxs[i]->stream, b->done, 0) != cudaSuccess)
+            return batch_fail(PIZZA_ECUDA, "pizza_batch_step: event ordering failed");
+    return PIZZA_OK;
+}
+
+void* pizza_batch_stream(pizza_batch* b) { return b ? b->stream : nullptr; }
+
+void pizza_batch_free(pizza_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto e : b->joins)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
 int pizza_synchronize(pizza_ctx* ctx) {
     if (!ctx) return PIZZA_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));

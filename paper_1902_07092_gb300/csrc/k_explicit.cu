@@ -22,8 +22,16 @@ constexpr int MAXPER = 12;       // azimuthal points per thread held in register
 
 __device__ __forceinline__ int g_index(int k, int f, int m, int M) { return (k * 4 + f) * M + m; }
 
-// number of radial transforms batched together in shared memory
-__host__ __device__ inline int radial_batch(int L) { return L <= 1024 ? 2 : 1; }
+// number of radial transforms batched together in shared memory (the
+// autotuner's choice, else two up to 1024 points)
+__host__ __device__ inline int radial_batch(const StepParams& P) {
+    return P.nb_r > 0 ? P.nb_r : (2 * P.K <= 1024 ? 2 : 1);
+}
+// threads of the per-radius azimuthal kernels
+inline int phi_threads(const StepParams& P) {
+    if (P.phi_threads > 0) return P.phi_threads;
+    return P.n_phi > 256 * MAXPER ? 512 : 256;
+}
 
 // ---------------------------------------------------------------------------
 // K1: per m, Chebyshev coefficients -> values on the Gauss-Lobatto grid.
@@ -40,7 +48,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
     T* sm = reinterpret_cast<T*>(smraw);
     const int m = blockIdx.x;
     const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
-    const int NB = radial_batch(L);
+    const int NB = radial_batch(P);
     T* bufA = sm;
     T* bufB = bufA + NB * L;
     T* cc0 = bufB + NB * L;  // Psi (or u_bar) plain coefficients, length N
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
     T* sm = reinterpret_cast<T*>(smraw);
     const int m = blockIdx.x;
     const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
-    const int NB = radial_batch(L);
+    const int NB = radial_batch(P);
     T* bufA = sm;
     T* bufB = bufA + NB * L;
     T* cc0 = bufB + NB * L;
@@ -558,7 +566,7 @@ cudaError_t launch_phi_fields(const StepParams& P, const double2* G1, double* us
 size_t smem_spec_to_grid(const StepParams& P) {
     const int L = 2 * P.K;
     const size_t c = P.fp32 ? sizeof(float2) : sizeof(double2);
-    return c * (2 * radial_batch(L) * L + 3 * P.n_r);
+    return c * (2 * radial_batch(P) * L + 3 * P.n_r);
 }
 size_t smem_phi_products(const StepParams& P) {
     return (P.fp32 ? sizeof(float2) : sizeof(double2)) * 2 * P.n_phi;
@@ -579,8 +587,8 @@ static cudaError_t spec_to_grid_t(const StepParams& P, VecSet y, void* G1, cudaS
 template <class T>
 static cudaError_t phi_products_t(const StepParams& P, const void* G1, void* G2, cudaStream_t st) {
     const size_t sm = smem_phi_products(P);
-    const int nth = P.n_phi > 256 * MAXPER ? 512 : 256;
-    if (P.n_phi > nth * MAXPER) return cudaErrorInvalidValue;
+    const int nth = phi_threads(P);
+    if (P.n_phi > nth * MAXPER || nth > 512) return cudaErrorInvalidValue;
     cudaError_t err = cudaFuncSetAttribute(k_phi_products<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     k_phi_products<T><<<P.n_r, nth, sm, st>>>(P, static_cast<const T*>(G1), static_cast<T*>(G2));

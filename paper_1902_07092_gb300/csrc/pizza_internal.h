@@ -82,6 +82,9 @@ struct StepParams {
     DevOps ops;
     // explicit stage in FP32 (option "precision" = mixed): 1 when selected
     int fp32;
+    // launch shapes chosen by pizza_autotune (0: the default rule): radial
+    // transforms batched per shared-memory pass, threads of the azimuthal kernel
+    int nb_r, phi_threads;
     // collocation formulation (Section 3.1): 1 when selected
     int coll;
     const double* beta;   // [n_r] beta = -s/h^2, 0 at s_o

@@ -89,9 +89,29 @@ WORKLOADS = {
                            dt=1e-7, steps=1000, amp=1e-3, seed=2, cfg=2, radial="collocation"),
     "large_n2049_p6144": dict(n_r=2049, n_phi=6144, E=1e-8, Pr=1.0, eta=0.35, ra_factor=20.0, scheme="SBDF3",
                               dt=1e-10, steps=50, amp=1e-3, seed=3, cfg=3, radial="integration"),
+    "batch64": dict(n_r=0, n_phi=0, E=0.0, Pr=1.0, eta=0.35, ra_factor=0.0, scheme="CNAB2", dt=0.0, steps=200,
+                    amp=1e-3, seed=1000, cfg=4, radial="integration", batch=64),
     "adjoint_n257_p768": dict(n_r=257, n_phi=768, E=1e-5, Pr=1.0, eta=0.35, ra_factor=5.0, scheme="CNAB2",
-                              dt=1e-7, steps=400, amp=1e-3, seed=5, cfg=5, radial="integration"),
+                              dt=1e-7, steps=400, amp=1e-3, seed=5, cfg=5, radial="integration",
+                              adjoint=True, checkpoint_every=20),
 }
+
+
+def batch_runs(n=64):
+    """The batched workload: run r (seed 1000 + r) draws n_r and n_phi independently
+    from {65, 129, 257, 513} x {192, 384, 768, 1536}, E log-uniform in [1e-6, 1e-4]
+    and Ra/Ra_c uniform in [1.5, 20]; CNAB2 with dt = 0.01 E, integration/tau,
+    perturbation amplitude 1e-3."""
+    sizes_r = (65, 129, 257, 513)
+    sizes_p = (192, 384, 768, 1536)
+    runs = []
+    for r in range(n):
+        u = (uniform(1000 + r, 7, np.arange(4)) + 1.0) * 0.5      # U[0, 1)
+        E = 10.0 ** (-6.0 + 2.0 * u[2])
+        runs.append(dict(n_r=sizes_r[min(3, int(4 * u[0]))], n_phi=sizes_p[min(3, int(4 * u[1]))], E=float(E),
+                         ra_factor=float(1.5 + 18.5 * u[3]), Pr=1.0, eta=0.35, scheme="CNAB2", dt=float(0.01 * E),
+                         amp=1e-3, seed=1000 + r, cfg=4))
+    return runs
 
 
 def n_c_of(wl):

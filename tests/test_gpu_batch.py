@@ -1,0 +1,77 @@
+"""Batches in one CUDA graph and the autotuner: both change the schedule, not
+the arithmetic, so the states must equal those of contexts stepped one by one,
+bit for bit."""
+import numpy as np
+import pytest
+
+from paper_1902_07092_gb300 import inputs
+from tests.parity_util import critical_rayleigh
+
+pytestmark = pytest.mark.gpu
+
+RUNS = [  # n_r, n_phi, E, Ra/Ra_c, scheme, dt, radial
+    (33, 96, 1e-3, 2.0, "CNAB2", 1e-4, "integration"),
+    (65, 192, 1e-4, 5.0, "SBDF3", 1e-6, "integration"),
+    (33, 96, 1e-3, 3.0, "ARS443", 1e-4, "integration"),
+    (33, 96, 1e-3, 2.0, "CNAB2", 1e-4, "collocation"),
+    (129, 384, 1e-5, 10.0, "SBDF2", 1e-7, "integration"),
+]
+
+
+def _make(k, run):
+    from paper_1902_07092_gb300.binding import Solver
+    n_r, n_phi, E, rf, scheme, dt, radial = run
+    s = Solver(n_r, n_phi, E, rf * critical_rayleigh(E), 1.0, 0.35, scheme, dt, radial=radial)
+    nc = n_r if radial == "collocation" else None
+    th = inputs.theta_init(n_r, n_phi, 1e-2, 100 + k, cfg=4, n_c=nc)
+    z, zu = inputs.zero_state(n_r, n_phi, n_c=nc)
+    s.set_state(th, z, zu)
+    return s, (th, z, zu)
+
+
+def test_batch_graph_equals_contexts_stepped_alone():
+    from paper_1902_07092_gb300.binding import Batch
+    alone, batched, states = [], [], []
+    for k, run in enumerate(RUNS):
+        a, st = _make(k, run)
+        a.step(7)
+        alone.append(a.get_state())
+        a.close()
+        b, st = _make(k, run)
+        batched.append(b)
+        states.append(st)
+    batch = Batch(batched)
+    batch.step(7)                        # capture, instantiate, launch
+    for b, ref in zip(batched, alone):
+        for x, y in zip(b.get_state(), ref):
+            assert np.array_equal(x, y)
+    for b, st in zip(batched, states):   # back to the graph's start state: relaunch
+        b.set_state(*st)
+    batch.step(7)
+    for b, ref in zip(batched, alone):
+        for x, y in zip(b.get_state(), ref):
+            assert np.array_equal(x, y)
+    batch.step(5)                        # another length: a new capture from the current state
+    for b in batched:
+        assert all(np.all(np.isfinite(x)) for x in b.get_state())
+    batch.close()
+    for b in batched:
+        b.close()
+
+
+def test_autotuned_launch_shapes_do_not_change_results():
+    ref = []
+    for k, run in enumerate(RUNS[:3] + RUNS[4:]):
+        a, _ = _make(k, run)
+        a.step(4)
+        ref.append(a.get_state())
+        a.close()
+    for k, run in enumerate(RUNS[:3] + RUNS[4:]):
+        a, st = _make(k, run)
+        nb, th = a.autotune()
+        assert nb in (1, 2) and th in (128, 256, 512)
+        a.set_state(*st)
+        a.step(4)
+        for x, y in zip(a.get_state(), ref[k]):
+            assert np.array_equal(x, y)
+        a.close()
