@@ -89,6 +89,14 @@ def algorithmic_flops(n_r, n_phi, scheme, radial="integration"):
     return dict(zip(KERNELS, (f_s2g, f_phi, f_g2s, f_solve)))
 
 
+# DRAM bytes (read + write) per launch of the roofline kernel from one ncu capture
+# of this workload (summaries under profiles/); null for kernels not captured.
+NCU_TRAFFIC = {
+    ("sparse_n257_p768", "solve"): (44.32e6 + 0.17e6, "profiles/imex_step_kernels_n257_p768.md"),
+    ("coll_n257_p768", "solve"): (726.5e6 + 6.8e6, "profiles/collocation_step_kernels_n257_p768.md"),
+}
+
+
 def launches_per_step(scheme):
     return {"CNAB2": 4, "SBDF2": 4, "SBDF3": 4, "ARS443": 16}[scheme]
 
@@ -447,7 +455,9 @@ def run_native(args, wl, Ra, rank, world, local_rank):
                 "d2h_bytes_per_step": nbytes, "steps": k_e2e},
         "gpu_launches": launches_per_step(wl["scheme"]) * args.steps,
         "roofline": {"bound": "alu", "kernel": KERNELS[dom], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": NCU_TRAFFIC.get((args.workload, KERNELS[dom]), (None, None))[0],
+                     "traffic_source": NCU_TRAFFIC.get((args.workload, KERNELS[dom]), (None, None))[1],
                      "peak_source": "nominal FP64 rate of the profiling recipe (not in MEASURED_PEAKS)",
                      "timing": "CUDA events around each launch, second pass of the same K steps"},
         "kernels": {k: {"launches": int(kn[i]), "avg_us": 1e3 * float(kt[i]) / max(int(kn[i]), 1),

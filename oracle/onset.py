@@ -23,8 +23,10 @@ from scipy.optimize import brentq
 from .operators import IntegrationOperators
 
 
-def pencil(E, Pr, Ra, eta, m, n_c):
-    n_r = int(1.5 * n_c) + 2
+def pencil(E, Pr, Ra, eta, m, n_c, n_r=None):
+    """(L, M) in the f_hat coordinates of a radial grid of n_r points (the
+    eigenvalues do not depend on n_r, the column scaling of the vectors does)."""
+    n_r = int(1.5 * n_c) + 2 if n_r is None else n_r
     op = IntegrationOperators(n_r, n_c, eta, E, Pr, Ra)
     n = n_c
     L = np.zeros((2 * n, 2 * n), complex)
@@ -61,6 +63,19 @@ def leading_of_pencil(L, M, guess=None):
     lam = guess + 1.0 / mu
     lam = lam[np.abs(lam) < 1e8]
     return lam[np.argmin(np.abs(lam - guess))]
+
+
+def leading_mode(E, Pr, Ra, eta, m, n_c, n_r=None, guess=None):
+    """Leading eigenvalue and its eigenvector (Psi_hat, theta_hat), unit 2-norm,
+    by inverse iteration at the refined eigenvalue."""
+    L, M = pencil(E, Pr, Ra, eta, m, n_c, n_r)
+    lam = leading_of_pencil(L, M, guess)
+    lu = sl.lu_factor(L - lam * M)
+    x = np.ones(2 * n_c, complex)
+    for _ in range(3):
+        x = sl.lu_solve(lu, M @ x)
+        x /= np.linalg.norm(x)
+    return lam, x[:n_c], x[n_c:]
 
 
 def critical_rayleigh_m(E, Pr, eta, m, n_c, ra_lo, ra_hi, rtol=1e-9):
