@@ -6,7 +6,9 @@ Test infrastructure only (see the package docstring).
 Unknowns per mode (N_c = N_r, paper coefficients with both ends halved):
 omega_hat and psi_hat (m >= 1), theta_hat, and u_hat (m = 0).  With T, T', T''
 the Chebyshev polynomials and their s-derivatives at the Gauss-Lobatto points,
-and Ekman pumping off (Upsilon = 0):
+and Ekman pumping off (Upsilon = 0; with ``pumping`` the exact terms of
+``pumping.collocation_blocks`` join A^C, B^C and the zonal-flow operator, all
+implicit):
   A^C = T'' + T'/s - (m^2/s^2) T
   B^C = -(2/E)(i m beta/s) T
   C^C = T'' + (beta + 1/s) T' + (dbeta/ds + beta/s - m^2/s^2) T
@@ -37,13 +39,15 @@ from . import fourier as fo
 from .geometry import Annulus, gauss_lobatto
 from .operators import bc_rows_plain
 from .onset import leading_of_pencil
+from .pumping import collocation_blocks, upsilon
 from .stepper import ImexScheme
 from . import schemes
 
 
 class CollocationOperators:
-    def __init__(self, n_r, eta, E, Pr, Ra):
+    def __init__(self, n_r, eta, E, Pr, Ra, pumping=False):
         self.n_r = self.n_c = n_r
+        self.pumping = bool(pumping)
         self.ann = ann = Annulus(eta)
         self.E, self.Pr, self.Ra = float(E), float(Pr), float(Ra)
         N = n_r
@@ -69,6 +73,14 @@ class CollocationOperators:
     def A(self, m):
         return self.Q - (m * m / self.s ** 2)[:, None] * self.T
 
+    def pump(self, m):
+        """(F_omega, F_psi) of the exact Ekman pumping for mode m (zeros when off)."""
+        if not self.pumping or m == 0:
+            z = np.zeros_like(self.T)
+            return z, z
+        Fw, Fpsi, _ = collocation_blocks(self, m)
+        return Fw, Fpsi
+
     def Bdiag(self, m):
         """B^C = diag(bdiag) T."""
         return -(2.0 / self.E) * 1j * m * self.beta / self.s
@@ -82,13 +94,17 @@ class CollocationOperators:
         return (self.Q - (m * m / self.s ** 2)[:, None] * self.T) / self.Pr
 
     def Lu(self):
-        return self.Q - (1.0 / self.s ** 2)[:, None] * self.T
+        L = self.Q - (1.0 / self.s ** 2)[:, None] * self.T
+        if self.pumping:
+            L = L + collocation_blocks(self, 1)[2]
+        return L
 
     def lhs_wpsi(self, m, gdt):
         N = self.n_r
         L = np.zeros((2 * N, 2 * N), complex)
-        L[:N, :N] = self.T - gdt * self.A(m)
-        L[:N, N:] = gdt * self.Bdiag(m)[:, None] * self.T
+        Fw, Fpsi = self.pump(m)
+        L[:N, :N] = self.T - gdt * (self.A(m) + Fw)
+        L[:N, N:] = gdt * (self.Bdiag(m)[:, None] * self.T - Fpsi)
         L[N:, :N] = self.T
         L[N:, N:] = self.C(m)
         for row in (0, N - 1, N, 2 * N - 1):
@@ -110,10 +126,10 @@ class CollocationStepper(ImexScheme):
     """State tuple (omega_hat, psi_hat, theta_hat, u_hat); mass/imp/explicit return
     grid-row tuples (omega rows, constraint rows, theta rows, u rows)."""
 
-    def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt):
+    def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt, pumping=False):
         if scheme not in schemes.SCHEME_ID:
             raise ValueError(scheme)
-        self.ops = CollocationOperators(n_r, eta, E, Pr, Ra)
+        self.ops = CollocationOperators(n_r, eta, E, Pr, Ra, pumping)
         self.n_c = n_r
         if n_phi % 3:
             raise ValueError("N_phi must be a multiple of 3")
@@ -157,7 +173,8 @@ class CollocationStepper(ImexScheme):
     def imp(self, y):
         w, psi, th, u = y
         o = self.ops
-        iw = np.stack([o.A(m) @ w[m] - o.Bdiag(m) * (o.T @ psi[m]) for m in range(self.M)])
+        iw = np.stack([o.A(m) @ w[m] - o.Bdiag(m) * (o.T @ psi[m]) + o.pump(m)[0] @ w[m] + o.pump(m)[1] @ psi[m]
+                       for m in range(self.M)])
         iw[0] = 0.0
         it = np.stack([o.Lt(m) @ th[m] for m in range(self.M)])
         return iw, np.zeros_like(psi), it, o.Lu() @ u
@@ -191,6 +208,10 @@ class CollocationStepper(ImexScheme):
         bt[0] = 0.0
         Nt = (deriv(vt) + 1j * m * ut) / s + bt
         Nu = vw[:, 0] / o.s
+        if o.pumping:   # self-interaction of the zonal wind (Eq. uphicoll), explicit
+            ups = upsilon(o.ann, o.E, o.s)
+            ups[0] = 0.0
+            Nu = Nu + 0.5 * o.E * ups * ub * W[:, 0]
         ew = -(o.Ra / o.Pr) * (1j * m / o.ann.s_o) * TH - Nw
         et = -(1j * m / s) * o.tc[:, None] * P - Nt
         eu = -Nu
@@ -257,17 +278,18 @@ class CollocationStepper(ImexScheme):
         return us, uphi, W, o.T @ th.T
 
 
-def collocation_pencil(E, Pr, Ra, eta, m, n_r):
+def collocation_pencil(E, Pr, Ra, eta, m, n_r, pumping=False):
     """Linearised Eqs. psiomcoll and tempcoll for normal modes exp(i m phi +
     lambda t): unknowns (omega_hat, psi_hat, theta_hat); boundary rows carry no
-    mass."""
-    o = CollocationOperators(n_r, eta, E, Pr, Ra)
+    mass.  ``pumping``: the exact Ekman pumping of Eq. pumping_full."""
+    o = CollocationOperators(n_r, eta, E, Pr, Ra, pumping)
+    Fw, Fpsi = o.pump(m)
     N = n_r
     L = np.zeros((3 * N, 3 * N), complex)
     M = np.zeros((3 * N, 3 * N), complex)
     M[:N, :N] = o.T
-    L[:N, :N] = o.A(m)
-    L[:N, N:2 * N] = -o.Bdiag(m)[:, None] * o.T
+    L[:N, :N] = o.A(m) + Fw
+    L[:N, N:2 * N] = -o.Bdiag(m)[:, None] * o.T + Fpsi
     L[:N, 2 * N:] = -(Ra / Pr) * (1j * m / o.ann.s_o) * o.T
     L[N:2 * N, :N] = o.T
     L[N:2 * N, N:2 * N] = o.C(m)
@@ -283,5 +305,5 @@ def collocation_pencil(E, Pr, Ra, eta, m, n_r):
     return L, M
 
 
-def leading_eigenvalue_collocation(E, Pr, Ra, eta, m, n_r, guess=None):
-    return leading_of_pencil(*collocation_pencil(E, Pr, Ra, eta, m, n_r), guess)
+def leading_eigenvalue_collocation(E, Pr, Ra, eta, m, n_r, guess=None, pumping=False):
+    return leading_of_pencil(*collocation_pencil(E, Pr, Ra, eta, m, n_r, pumping), guess)

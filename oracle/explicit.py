@@ -25,13 +25,16 @@ From the state (Psi_hat, theta_hat, u_hat; paper coefficients, N_c per mode):
       Psi:   C^I [ (Ra/Pr)(i m/s_o) theta_hat + N_omega_hat ]           (Eq. psi_int)
       theta: -D^I N_theta_hat - (alpha/ln eta) i m G^I Psi_hat          (Eq. temp_int)
       u_bar: -D^I N_u_hat                                                (Eq. uphi_int)
-Ekman pumping is off.
+Ekman pumping (``g.pump_eps`` not None): the approximate F_eps of Eq. approx_pump
+on the radial grid (``pumping.integration_grid``) joins step 3 as
+N_omega - F_eps, and Upsilon_eps u_bar joins N_u.
 """
 import numpy as np
 
 from . import chebyshev as ch
 from . import fourier as fo
 from .geometry import gauss_lobatto
+from .pumping import integration_grid
 
 
 class Grid:
@@ -49,6 +52,7 @@ class Grid:
         self.m = np.arange(self.M)
         self.T = ch.tmat(self.n_r, self.n_r)
         self.Dn = ch.diff_matrix(self.n_r) / ann.a      # d/ds on plain coefficients
+        self.pump_eps = None                             # Ekman pumping off
 
 
 def radial_fields(g, psi_hat, theta_hat, u_hat):
@@ -118,6 +122,10 @@ def explicit_terms(g, psi_hat, theta_hat, u_hat, return_parts=False):
     v, uphi, omega, theta = radial_fields(g, psi_hat, theta_hat, u_hat)
     vw, uw, vt, ut = products(g, v, uphi, omega, theta)
     Nw_g, Nt_g, Nu_g = nonlinear_grid(g, vw, uw, vt, ut)
+    if g.pump_eps is not None:
+        F = integration_grid(g, psi_hat, u_hat, g.pump_eps)
+        Nw_g = Nw_g - F
+        Nu_g = Nu_g + F[:, 0].real
     nc = g.n_c
     Nw = ch.analysis(Nw_g, g.n_r)[:nc].T
     Nt = ch.analysis(Nt_g, g.n_r)[:nc].T

@@ -23,9 +23,12 @@ from scipy.optimize import brentq
 from .operators import IntegrationOperators
 
 
-def pencil(E, Pr, Ra, eta, m, n_c, n_r=None):
+def pencil(E, Pr, Ra, eta, m, n_c, n_r=None, pumping_eps=None):
     """(L, M) in the f_hat coordinates of a radial grid of n_r points (the
-    eigenvalues do not depend on n_r, the column scaling of the vectors does)."""
+    eigenvalues do not depend on n_r, the column scaling of the vectors does).
+    pumping_eps: the approximate Ekman pumping F_eps of Eq. approx_pump, the
+    linear map of the explicit stage (grid values, Eq. icheb, truncation), which
+    enters the streamfunction rows as -C^I F_eps (Eq. psiint)."""
     n_r = int(1.5 * n_c) + 2 if n_r is None else n_r
     op = IntegrationOperators(n_r, n_c, eta, E, Pr, Ra)
     n = n_c
@@ -33,6 +36,11 @@ def pencil(E, Pr, Ra, eta, m, n_c, n_r=None):
     M = np.zeros((2 * n, 2 * n), complex)
     M[:n, :n] = op.A(m)
     L[:n, :n] = op.B(m)
+    if pumping_eps is not None:
+        from .explicit import Grid
+        from .pumping import integration_matrix
+        g = Grid(op, 3 * (m + 1))
+        L[:n, :n] -= op.C @ integration_matrix(g, m, pumping_eps)
     L[:n, n:] = (Ra / Pr) * (1j * m / op.ann.s_o) * op.C
     M[n:, n:] = op.D
     L[n:, n:] = op.F(m) / Pr
@@ -46,8 +54,8 @@ def pencil(E, Pr, Ra, eta, m, n_c, n_r=None):
     return L, M
 
 
-def leading_eigenvalue(E, Pr, Ra, eta, m, n_c, guess=None):
-    return leading_of_pencil(*pencil(E, Pr, Ra, eta, m, n_c), guess)
+def leading_eigenvalue(E, Pr, Ra, eta, m, n_c, guess=None, n_r=None, pumping_eps=None):
+    return leading_of_pencil(*pencil(E, Pr, Ra, eta, m, n_c, n_r, pumping_eps), guess)
 
 
 def leading_of_pencil(L, M, guess=None):
@@ -65,10 +73,10 @@ def leading_of_pencil(L, M, guess=None):
     return lam[np.argmin(np.abs(lam - guess))]
 
 
-def leading_mode(E, Pr, Ra, eta, m, n_c, n_r=None, guess=None):
+def leading_mode(E, Pr, Ra, eta, m, n_c, n_r=None, guess=None, pumping_eps=None):
     """Leading eigenvalue and its eigenvector (Psi_hat, theta_hat), unit 2-norm,
     by inverse iteration at the refined eigenvalue."""
-    L, M = pencil(E, Pr, Ra, eta, m, n_c, n_r)
+    L, M = pencil(E, Pr, Ra, eta, m, n_c, n_r, pumping_eps)
     lam = leading_of_pencil(L, M, guess)
     lu = sl.lu_factor(L - lam * M)
     x = np.ones(2 * n_c, complex)

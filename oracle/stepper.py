@@ -107,12 +107,13 @@ class ImexScheme:
 
 
 class IntegrationStepper(ImexScheme):
-    def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt):
+    def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt, pumping_eps=None):
         if scheme not in schemes.SCHEME_ID:
             raise ValueError(scheme)
         self.n_c = n_c_integration(n_r)
         self.ops = IntegrationOperators(n_r, self.n_c, eta, E, Pr, Ra)
         self.g = Grid(self.ops, n_phi)
+        self.g.pump_eps = pumping_eps       # Ekman pumping, explicit (Eq. approx_pump)
         self.scheme, self.dt = scheme, float(dt)
         self._lu = {}
         self.n_done = 0
