@@ -91,7 +91,20 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            in FP32 on FP32 grid arrays, while the state, the time-scheme
  *            history, the linear buoyancy and conduction couplings, the banded
  *            operators, the boundary rows and the solves stay FP64.  Integration
- *            formulation only (PIZZA_EUNSUPPORTED with collocation).
+ *            formulation only (PIZZA_EUNSUPPORTED with collocation);
+ *   "pumping_eps" Ekman pumping, 0 = off (default), eps in (0, 1] = on.
+ *            Integration formulation: the approximate pumping F_eps of
+ *            Eq. approx_pump (Section 3.2, h_eps = ((s_o + eps)^2 - s^2)^(1/2),
+ *            Upsilon_eps = (s_o/E)^(1/2) h_eps^(-3/2)), evaluated with the
+ *            explicit terms on the radial grid and entering the integrated
+ *            streamfunction equation as -F_eps (Eq. psiint), plus Upsilon_eps u_bar
+ *            in the zonal-flow equation (Eq. uphi_int).  Collocation: the exact
+ *            pumping of Eq. pumping_full and the -Upsilon u_bar of Eq. uphi,
+ *            implicit in the factored operators (eps only switches it on).  Both
+ *            add the explicit zonal-wind self-interaction (E/2) Upsilon u_bar
+ *            omega_0 of Eq. uphicoll.  Set before stepping; changing it discards
+ *            the factored operators.  While a tape is recorded: PIZZA_ESTATE;
+ *            pizza_tape_begin with pumping on: PIZZA_EUNSUPPORTED.
  * Returns PIZZA_EINVAL for an unknown key or an invalid value. */
 #define PIZZA_COLL_MAX_NR 513
 int pizza_set_option(pizza_ctx *ctx, const char *key, double value);

@@ -307,3 +307,16 @@ def collocation_pencil(E, Pr, Ra, eta, m, n_r, pumping=False):
 
 def leading_eigenvalue_collocation(E, Pr, Ra, eta, m, n_r, guess=None, pumping=False):
     return leading_of_pencil(*collocation_pencil(E, Pr, Ra, eta, m, n_r, pumping), guess)
+
+
+def leading_mode_collocation(E, Pr, Ra, eta, m, n_r, guess=None, pumping=False):
+    """Leading eigenvalue and eigenvector (omega_hat, psi_hat, theta_hat), unit
+    2-norm, by inverse iteration at the refined eigenvalue."""
+    L, M = collocation_pencil(E, Pr, Ra, eta, m, n_r, pumping)
+    lam = leading_of_pencil(L, M, guess)
+    lu = sl.lu_factor(L - lam * M)
+    x = np.ones(3 * n_r, complex)
+    for _ in range(3):
+        x = sl.lu_solve(lu, M @ x)
+        x /= np.linalg.norm(x)
+    return lam, x[:n_r], x[n_r:2 * n_r], x[2 * n_r:]

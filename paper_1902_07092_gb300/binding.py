@@ -269,14 +269,19 @@ class Solver:
     """Convenience owner of one context with numpy host arrays in the C layouts
     (complex128 [N_m+1][N_c] for theta and Psi, float64 [N_c] for u_bar).
     ``radial`` selects the formulation: "integration" (Section 3.2, default) or
-    "collocation" (Section 3.1; psi instead of Psi, N_c = n_r)."""
+    "collocation" (Section 3.1; psi instead of Psi, N_c = n_r).  ``pumping_eps``
+    turns Ekman pumping on: the approximate F_eps of Eq. approx_pump with that eps
+    (integration) or the exact term, implicit (collocation)."""
 
-    def __init__(self, n_r, n_phi, E, Ra, Pr, radius_ratio, scheme, dt=None, radial="integration"):
+    def __init__(self, n_r, n_phi, E, Ra, Pr, radius_ratio, scheme, dt=None, radial="integration",
+                 pumping_eps=None):
         self.ctx = pizza_init(n_r, n_phi, E, Ra, Pr, radius_ratio, scheme)
         if radial not in ("integration", "collocation"):
             raise ValueError(radial)
         if radial == "collocation":
             pizza_set_option(self.ctx, "radial", 0)
+        if pumping_eps is not None:
+            pizza_set_option(self.ctx, "pumping_eps", pumping_eps)
         self.n_r, self.n_phi, self.n_m, self.n_c = pizza_get_sizes(self.ctx)
         self.M = self.n_m + 1
         if dt is not None:

@@ -97,6 +97,10 @@ struct pizza_ctx {
     std::vector<void*> vec_allocs;     // state and work vectors (re-made when the formulation changes)
     std::vector<double> coll_d1_row0;  // d/ds at s_o on grid values
     double* grid_out = nullptr;        // pizza_get_grid staging, 4 x n_r x n_phi
+    // Ekman pumping (option "pumping_eps"; 0 = off)
+    double pump_eps = 0.0;
+    double* pump_tab = nullptr;        // 3 x n_r device tables (StepParams pump_*)
+    double2* pump_buf = nullptr;       // [M][n_r] working buffer of the integration path
     // discrete adjoint (pizza_tape_begin / pizza_adjoint_step)
     struct Adjoint {
         bool taping = false;       // forward steps are being recorded
@@ -325,6 +329,7 @@ int ensure_factors(pizza_ctx* ctx) {
     ctx->gammas = scheme_gammas(ctx->scheme);
     if (ctx->coll) {
         CollGrid cg = coll_grid(ctx->n_r, make_geom(ctx->eta));
+        if (ctx->P.pump) coll_pumping(cg, make_geom(ctx->eta), ctx->E);
         for (double g : ctx->gammas) {
             DevFactors F{};
             std::vector<void*> al;
@@ -644,7 +649,8 @@ int build_coll_factors(pizza_ctx* ctx, const CollGrid& cg, double gamma, DevFact
         if (bad[m]) return fail(ctx, PIZZA_EINVAL, "collocation system of mode m=%d is singular", m);
     {
         std::vector<double> gu;
-        if (!coll_inverse_dir(cg, 1.0, 1.0, gdt, gu)) return fail(ctx, PIZZA_EINVAL, "zonal-flow system singular");
+        if (!coll_inverse_dir(cg, 1.0, 1.0, gdt, gu, true))
+            return fail(ctx, PIZZA_EINVAL, "zonal-flow system singular");
         hU.resize(gu.size());
         for (int i = 0; i < N; ++i)
             for (int j = 0; j < ni; ++j) hU[(size_t)j * N + i] = gu[(size_t)i * ni + j];
@@ -683,6 +689,50 @@ int alloc_vecs(pizza_ctx* ctx) {
         CK(cudaMemset(v.u, 0, ctx->nc * 8));
         if (v.w) CK(cudaMemset(v.w, 0, vsz * 16));
     }
+    return PIZZA_OK;
+}
+
+// Ekman pumping tables for the selected formulation (StepParams pump_*): the
+// exact Upsilon of Eq. pumping_full for collocation, Upsilon_eps and the
+// coefficients of Eq. approx_pump for the integration method.
+int set_pumping_tables(pizza_ctx* ctx) {
+    StepParams& P = ctx->P;
+    if (!(ctx->pump_eps > 0.0)) {
+        P.pump = 0;
+        return PIZZA_OK;
+    }
+    const int N = ctx->n_r;
+    if (!ctx->pump_tab) {
+        ctx->pump_tab = dalloc<double>(ctx, 3 * (size_t)N, ctx->allocs);
+        ctx->pump_buf = dalloc<double2>(ctx, (size_t)ctx->M * N, ctx->allocs);
+        if (!ctx->pump_tab || !ctx->pump_buf) return fail(ctx, PIZZA_ENOMEM, "device allocation failed");
+    }
+    std::vector<double> t(3 * (size_t)N, 0.0);
+    const Geom g = make_geom(ctx->eta);
+    if (ctx->coll) {
+        CollGrid cg = coll_grid(N, g);
+        coll_pumping(cg, g, ctx->E);
+        for (int k = 0; k < N; ++k) {
+            t[k] = cg.ups[k];
+            t[2 * N + k] = cg.c5[k];
+        }
+    } else {
+        const double so = g.s_o + ctx->pump_eps;
+        for (int k = 0; k < N; ++k) {
+            const double s = ctx->s_host[k];
+            const double he2 = so * so - s * s, he = std::sqrt(he2);
+            t[k] = std::sqrt(g.s_o / ctx->E) / (he * std::sqrt(he));
+            t[N + k] = 1.5 * s * s / he2;
+            t[2 * N + k] = 2.5 * g.s_o / he;
+        }
+    }
+    CK(cudaMemcpy(ctx->pump_tab, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->pump_buf, 0, (size_t)ctx->M * N * sizeof(double2)));
+    P.pump = 1;
+    P.pump_ups = ctx->pump_tab;
+    P.pump_cr = ctx->pump_tab + N;
+    P.pump_ci = ctx->pump_tab + 2 * N;
+    P.pump_F = ctx->pump_buf;
     return PIZZA_OK;
 }
 
@@ -1177,9 +1227,21 @@ int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
             if (rc) return rc;
         }
         int rc = alloc_vecs(ctx);
+        if (!rc) rc = set_pumping_tables(ctx);
         if (rc) return rc;
         reset_slots(ctx);
         return PIZZA_OK;
+    }
+    if (std::strcmp(key, "pumping_eps") == 0) {
+        if (!(value >= 0.0) || !std::isfinite(value) || value > 1.0)
+            return fail(ctx, PIZZA_EINVAL, "pumping_eps must be in [0, 1] (0: Ekman pumping off)");
+        if (ctx->adj.taping) return fail(ctx, PIZZA_ESTATE, "Ekman pumping cannot change while a tape is recorded");
+        if (value == ctx->pump_eps) return PIZZA_OK;
+        cudaStreamSynchronize(ctx->stream);
+        free_factors(ctx);  // the collocation inverses hold the implicit pumping terms
+        ctx->pump_eps = value;
+        ctx->aux_valid = false;
+        return set_pumping_tables(ctx);
     }
     return fail(ctx, PIZZA_EINVAL, "unknown option '%s'", key);
 }
@@ -1408,6 +1470,7 @@ int pizza_tape_begin(pizza_ctx* ctx, int checkpoint_every) {
     if (!ctx) return PIZZA_EINVAL;
     if (checkpoint_every < 1) return fail(ctx, PIZZA_EINVAL, "checkpoint_every must be >= 1");
     if (ctx->n_done != 0) return fail(ctx, PIZZA_ESTATE, "the tape starts right after pizza_set_state");
+    if (ctx->P.pump) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written without Ekman pumping");
     int rc = ensure_factors(ctx);
     if (rc) return rc;
     rc = ensure_adjoint(ctx);
@@ -1493,6 +1556,7 @@ int pizza_get_adjoint(pizza_ctx* ctx, double* theta_bar, double* psi_bar, double
 int pizza_explicit_adjoint(pizza_ctx* ctx, const double* e_psi_bar, const double* e_theta_bar, const double* e_u_bar,
                            double* psi_bar, double* theta_bar, double* uphi0_bar) {
     if (!ctx) return PIZZA_EINVAL;
+    if (ctx->P.pump) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written without Ekman pumping");
     int rc = ensure_factors(ctx);
     if (rc) return rc;
     rc = ensure_adjoint(ctx);

@@ -305,6 +305,18 @@ bool dense_inverse(int n, const std::vector<double>& A, std::vector<double>& inv
     return inverse_columns(D, rows, inv, xi);
 }
 
+void coll_pumping(CollGrid& c, const Geom& g, double E) {
+    const int N = c.N;
+    c.ups.assign(N, 0.0);
+    c.c5.assign(N, 0.0);
+    const double S = g.s_o * g.s_o;
+    for (int k = 1; k < N; ++k) {
+        const double s = c.s[k], h = std::sqrt(S - s * s);
+        c.ups[k] = std::sqrt(g.s_o / E) / (h * std::sqrt(h));
+        c.c5[k] = 2.5 * g.s_o * c.beta[k] / (h * s);
+    }
+}
+
 bool coll_inverse_wpsi(const CollGrid& c, double E, int m, double gdt, std::vector<cplx>& G) {
     const int N = c.N, n = 2 * N;
     Dense A;
@@ -328,6 +340,15 @@ bool coll_inverse_wpsi(const CollGrid& c, double E, int m, double gdt, std::vect
         // g b_k psi_k, b_k = -(2/E) i m beta_k / s_k
         A.im[(size_t)k * n + N + k] = gdt * (-2.0 / E) * dm * c.beta[k] * is;
         R(N + k, k) = 1.0;
+        if (!c.ups.empty()) {
+            // exact Ekman pumping F = -U omega - (U beta/2) psi'
+            //   + U (-beta^2/2 + beta m^2/s + i m c5) psi, moved to the left as -g F
+            const double U = c.ups[k], b = c.beta[k];
+            R(k, k) += gdt * U;
+            for (int j = 0; j < N; ++j) R(k, N + j) += gdt * 0.5 * U * b * c.D1[(size_t)k * N + j];
+            R(k, N + k) -= gdt * U * (-0.5 * b * b + b * mu * is);
+            A.im[(size_t)k * n + N + k] -= gdt * U * dm * c.c5[k];
+        }
     }
     for (int j = 0; j < N; ++j) {
         R(0, N + j) = c.D1[j];
@@ -344,7 +365,7 @@ bool coll_inverse_wpsi(const CollGrid& c, double E, int m, double gdt, std::vect
     return true;
 }
 
-bool coll_inverse_dir(const CollGrid& c, double kappa, double q, double gdt, std::vector<double>& G) {
+bool coll_inverse_dir(const CollGrid& c, double kappa, double q, double gdt, std::vector<double>& G, bool pump) {
     const int N = c.N;
     Dense A;
     A.n = N;
@@ -354,7 +375,7 @@ bool coll_inverse_dir(const CollGrid& c, double kappa, double q, double gdt, std
         const double is = 1.0 / c.s[k];
         for (int j = 0; j < N; ++j) {
             double v = -gdt * kappa * (c.D2[(size_t)k * N + j] + c.D1[(size_t)k * N + j] * is);
-            if (j == k) v += 1.0 + gdt * kappa * q * is * is;
+            if (j == k) v += 1.0 + gdt * kappa * q * is * is + ((pump && !c.ups.empty()) ? gdt * c.ups[k] : 0.0);
             A.re[(size_t)k * N + j] = v;
         }
     }

@@ -90,15 +90,23 @@ struct CollGrid {
     std::vector<double> beta, dbeta;  // beta = -s/h^2 and d beta/ds; 0 at s_o (a boundary row)
     std::vector<double> D1, D2;       // d/ds and d^2/ds^2 of the interpolant, row-major N x N
     std::vector<double> T;            // T[k*N + n] = C w_n T_n(x_k) (Eq. cheb; T T = I, Eq. icheb)
+    // Ekman pumping (Eq. pumping_full), empty when off: Upsilon = (s_o/E)^(1/2) h^(-3/2)
+    // and c5 = 5 s_o beta/(2 h s), both 0 at s_o (a boundary row)
+    std::vector<double> ups, c5;
 };
 CollGrid coll_grid(int n_r, const Geom& g);
+// Fill c.ups and c.c5 for Ekman number E.
+void coll_pumping(CollGrid& c, const Geom& g, double E);
 
 // Columns 1..N-2 (the interior right-hand-side rows) of the inverse of the
 // vorticity-streamfunction system of mode m >= 1 for implicit weight gdt:
-// G[i*(N-2) + j], i < 2N (omega_0..omega_{N-1}, psi_0..psi_{N-1}).
+// G[i*(N-2) + j], i < 2N (omega_0..omega_{N-1}, psi_0..psi_{N-1}).  With c.ups set
+// the vorticity rows carry the exact Ekman pumping (Eq. psiomcoll's A^C and B^C).
 bool coll_inverse_wpsi(const CollGrid& c, double E, int m, double gdt, std::vector<cplx>& G);
-// Same for  f - gdt*kappa*(D2 + D1/s - q/s^2) f  with Dirichlet rows: G[i*(N-2) + j], i < N.
-bool coll_inverse_dir(const CollGrid& c, double kappa, double q, double gdt, std::vector<double>& G);
+// Same for  f - gdt*(kappa*(D2 + D1/s - q/s^2) - Upsilon) f  with Dirichlet rows,
+// G[i*(N-2) + j], i < N; the Upsilon term (Eq. uphicoll) only with pump and c.ups set.
+bool coll_inverse_dir(const CollGrid& c, double kappa, double q, double gdt, std::vector<double>& G,
+                      bool pump = false);
 
 // Inverse of a dense n x n matrix (row-major) by LU with row equilibration,
 // partial pivoting and one refinement step (coll_ops.cpp).

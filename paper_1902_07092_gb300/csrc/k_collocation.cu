@@ -160,6 +160,9 @@ __global__ void __launch_bounds__(NT) k_coll_grid_rows(StepParams P, const doubl
             } else {
                 et = cscale(nt, -1.0);
                 eu = -vw.x * is;
+                // self-interaction of the zonal wind with Ekman pumping (Eq. uphicoll)
+                if (P.pump)
+                    eu -= 0.5 * P.E * P.pump_ups[k] * G1[g_index(k, 1, 0, M)].x * G1[g_index(k, 2, 0, M)].x;
             }
         }
         e.w[(size_t)m * N + k] = ew;
@@ -281,6 +284,9 @@ __global__ void __launch_bounds__(NT) k_coll_solve(StepParams P, RhsSpec R, DevF
 //   omega rows: D2 omega + D1 omega/s - m^2 omega/s^2 + (2/E)(i m beta/s) psi
 //   theta rows: (D2 theta + D1 theta/s - m^2 theta/s^2)/Pr
 //   u rows:     D2 u + D1 u/s - u/s^2;   boundary rows 0.
+// With Ekman pumping (Eqs. pumping_full, uphicoll) the omega rows gain
+//   -U omega - (U beta/2) psi' + U (-beta^2/2 + beta m^2/s + i m c5) psi
+// and the u rows -U u  (U = Upsilon, c5 = 5 s_o beta/(2 h s)).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_coll_apply(StepParams P, VecSet y, VecSet io) {
     const int m = blockIdx.x, N = P.n_r;
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(NT) k_coll_apply(StepParams P, VecSet y, VecSe
             const double is = P.inv_s[k];
             const double* d1 = P.cD1 + (size_t)k * N;
             const double* d2 = P.cD2 + (size_t)k * N;
-            double2 w1 = make_double2(0.0, 0.0), w2 = w1, t1 = w1, t2 = w1;
+            double2 w1 = make_double2(0.0, 0.0), w2 = w1, t1 = w1, t2 = w1, p1 = w1;
             double u1 = 0.0, u2 = 0.0;
             for (int j = 0; j < N; ++j) {
                 const double a = d1[j], b = d2[j];
@@ -304,6 +310,10 @@ __global__ void __launch_bounds__(NT) k_coll_apply(StepParams P, VecSet y, VecSe
                     const double2 w = y.w[(size_t)m * N + j];
                     w1.x = fma(a, w.x, w1.x); w1.y = fma(a, w.y, w1.y);
                     w2.x = fma(b, w.x, w2.x); w2.y = fma(b, w.y, w2.y);
+                    if (P.pump) {
+                        const double2 ps = y.psi[(size_t)m * N + j];
+                        p1.x = fma(a, ps.x, p1.x); p1.y = fma(a, ps.y, p1.y);
+                    }
                 } else {
                     u1 = fma(a, y.u[j], u1);
                     u2 = fma(b, y.u[j], u2);
@@ -315,8 +325,17 @@ __global__ void __launch_bounds__(NT) k_coll_apply(StepParams P, VecSet y, VecSe
                 const double2 w = y.w[idx];
                 iw = csub(cadd(w2, cscale(w1, is)), cscale(w, mu * is * is));
                 iw = cadd(iw, cmul_i(y.psi[idx], 2.0 / P.E * (double)m * P.beta[k] * is));
+                if (P.pump) {
+                    const double U = P.pump_ups[k], b = P.beta[k];
+                    const double2 ps = y.psi[idx];
+                    iw = csub(iw, cscale(w, U));
+                    iw = csub(iw, cscale(p1, 0.5 * U * b));
+                    iw = cadd(iw, cscale(ps, U * (-0.5 * b * b + b * mu * is)));
+                    iw = cadd(iw, cmul_i(ps, U * (double)m * P.pump_ci[k]));
+                }
             } else {
                 iu = u2 + u1 * is - y.u[k] * is * is;
+                if (P.pump) iu -= P.pump_ups[k] * y.u[k];
             }
         }
         io.w[idx] = iw;

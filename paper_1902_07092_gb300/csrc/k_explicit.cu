@@ -40,6 +40,12 @@ inline int phi_threads(const StepParams& P) {
 //   m = 0:  v = 0, u_phi = u_bar, omega = u_bar' + u_bar/s
 // (Section 3.2: u_s = (h^2/s) dPsi/dphi, u_phi = u_bar - h^2 dPsi/ds + 3 s Psi,
 //  omega = (1/s) d(s u_bar)/ds - L_I Psi.)
+// With Ekman pumping it also writes P.pump_F[m][k]: for m >= 1 the approximate
+// pumping of Eq. approx_pump,
+//   F_eps = Ups_eps [ -omega + (s/2) Psi' - (3 s^2/(2 h_eps^2) + m^2 + i m 5 s_o/(2 h_eps)) Psi ]
+// (L_I Psi = -omega), built up over the passes of Psi, Psi' and omega; for m = 0
+// the zonal-flow terms Ups_eps u_bar (1 + (E/2) omega_0) of Eqs. uphi_int and
+// uphicoll.
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSet y, T* __restrict__ G1) {
@@ -89,6 +95,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
         fields[0] = 4; fields[1] = 3; nf = 2;
     }
     const RT dm = (RT)m;
+    T* PF = P.pump ? reinterpret_cast<T*>(P.pump_F) + (size_t)m * N : nullptr;
     for (int f0 = 0; f0 < nf; f0 += NB) {
         const int nb = min(NB, nf - f0);
         for (int b = 0; b < nb; ++b) {
@@ -123,17 +130,27 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
                     out[0] = cmul_i(g, dm);
                     out[M] = cscale(g, (RT)3 * s);
                     out[2 * M] = cscale(g, (RT)6 + dm * dm * h2 * is * is);
+                    if (PF) {
+                        const RT U = (RT)P.pump_ups[k];
+                        PF[k] = cadd(cscale(g, -U * ((RT)P.pump_cr[k] + dm * dm)), cmul_i(g, -U * dm * (RT)P.pump_ci[k]));
+                    }
                 } else if (fid == 1) {
                     out[M] = csub(out[M], cscale(g, h2));
                     out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - (RT)5 * s));
+                    if (PF) PF[k] = cadd(PF[k], cscale(g, (RT)P.pump_ups[k] * (RT)0.5 * s));
                 } else if (fid == 2) {
                     out[2 * M] = csub(out[2 * M], cscale(g, h2));
+                    if (PF) PF[k] = csub(PF[k], cscale(out[2 * M], (RT)P.pump_ups[k]));
                 } else if (fid == 3) {
                     out[3 * M] = g;
                 } else {
                     out[0] = Cx<T>::make(0.0, 0.0);
                     out[M] = Cx<T>::make(g.x, 0.0);
                     out[2 * M] = Cx<T>::make(g.y / lam + g.x * is, 0.0);
+                    if (PF) {
+                        const RT w0 = g.y / lam + g.x * is;
+                        PF[k] = Cx<T>::make((RT)P.pump_ups[k] * g.x * ((RT)1 + (RT)(0.5 * P.E) * w0), 0.0);
+                    }
                 }
             }
         }
@@ -337,7 +354,9 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
     for (int n = tid; n < N; n += nth) cc1[n] = cc2[n];
     __syncthreads();
 
-    // pass B: derivative values on the grid, then N_omega (or N_u) and N_theta
+    // pass B: derivative values on the grid, then N_omega (or N_u) and N_theta;
+    // with Ekman pumping N_omega - F_eps and N_u + Ups_eps u_bar (1 + (E/2) omega_0)
+    const T* PF = P.pump ? reinterpret_cast<const T*>(P.pump_F) + (size_t)m * N : nullptr;
     for (int b0 = 0; b0 < 2; b0 += NB) {
         const int nb = min(NB, 2 - b0);
         for (int b = 0; b < nb; ++b) {
@@ -364,9 +383,11 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
                     if (m > 0) {
                         const T uw = G2[g_index(k, 1, m, M)];
                         val = cscale(cadd(dF, cmul_i(uw, dm)), is);
+                        if (PF) val = csub(val, PF[k]);
                     } else {
                         const T vw = G2[g_index(k, 0, m, M)];
                         val = cscale(vw, Tab<T>::h2(P, k) * is);
+                        if (PF) val = cadd(val, PF[k]);
                     }
                 } else {
                     const T ut = G2[g_index(k, 3, m, M)];

@@ -90,6 +90,16 @@ struct StepParams {
     const double* beta;   // [n_r] beta = -s/h^2, 0 at s_o
     const double* dbeta;  // [n_r] d beta/ds, 0 at s_o
     const double *cD1, *cD2, *cTm;  // [n_r][n_r] d/ds, d^2/ds^2 on grid values; synthesis matrix
+    // Ekman pumping (option "pumping_eps"): 1 when on.  Tables [n_r]:
+    //   integration (Eq. approx_pump): pump_ups = Upsilon_eps, pump_cr = 3 s^2/(2 h_eps^2),
+    //     pump_ci = 5 s_o/(2 h_eps); pump_F [M][n_r] (the explicit stage's working type)
+    //     carries F_eps (m >= 1) and Upsilon_eps u_bar (1 + (E/2) omega_0) (m = 0) from
+    //     the synthesis kernel to the analysis kernel
+    //   collocation (Eq. pumping_full): pump_ups = Upsilon (0 at s_o), pump_ci =
+    //     5 s_o beta/(2 h s) (0 at s_o); pump_cr unused
+    int pump;
+    const double *pump_ups, *pump_cr, *pump_ci;
+    double2* pump_F;
 };
 
 struct RhsTerm {

@@ -2,12 +2,13 @@
 the onset solver's leading m = 12 eigenmode (E = 3e-6, Ra = 1e7, Pr = 0.025,
 radius ratio 0.35) at (N_r, N_c, N_m) = (257, 170, 128) grows and drifts at the
 eigenvalue of the same discretisation (614.99910 - 9536.95338i), within the time
-error of each scheme at dt = 1e-7, and the third-order schemes reproduce the
-eigensolver's growth rate and drift frequency of Table 3
+error of each scheme at dt = 1e-7.  The DIRK scheme (ARS443) hits it to 1e-8 and
+reproduces the eigensolver's growth rate and drift frequency of Table 3
 (tests/golden/growth_rates_table3.json) to the six digits the paper underlines
-for its own integration runs (6.14999e2, -9.53695e3).  CNAB2's time error at
-this dt (Table 3: 6.150091e2 for its collocation run) allows only the first
-check."""
+for its own DIRK runs (BPR353: 6.14999e2, -9.53695e3).  The multistep schemes
+carry a time error of a few 1e-3 in tau at this dt, as Table 3 shows for the
+paper's own multistep runs (SBDF3 6.150048e2, CNAB2 6.150091e2 against
+6.149994e2), so they are held to 1e-6 of |lambda| only."""
 import json
 import os
 
@@ -20,7 +21,7 @@ from tests.parity_util import GOLDEN
 pytestmark = pytest.mark.gpu
 
 N_R, N_PHI, M_MODE, DT = 257, 384, 12, 1e-7
-SCHEME_TOL = {"SBDF3": 1e-7, "ARS443": 1e-7, "CNAB2": 2e-6}   # relative error of lambda
+SCHEME_TOL = {"SBDF3": 1e-6, "ARS443": 1e-8, "CNAB2": 1e-6}   # relative error of lambda
 
 
 @pytest.fixture(scope="module")
@@ -54,7 +55,7 @@ def test_growth_rate_and_drift_of_the_m12_mode(mode, scheme):
         scheme, est.real, est.imag, lam.real, lam.imag, t3["eigensolver"]["tau"], t3["eigensolver"]["omega_d"]))
     assert np.linalg.norm(th2 - z2 * T[M_MODE]) < 1e-6 * np.linalg.norm(th2)
     assert abs(est - lam) < SCHEME_TOL[scheme] * abs(lam)
-    if scheme != "CNAB2":
+    if scheme == "ARS443":
         lsb = t3["eigensolver"]
         assert abs(est.real - lsb["tau"]) < 1e-3
         assert abs(est.imag - lsb["omega_d"]) < 5e-3
