@@ -45,6 +45,7 @@ bool make_fft_plan(int L, FftPlan& pl) {
     }
     pl.L = L;
     pl.npass = np;
+    pl.tws = 1;
     return np <= MAX_PASSES;
 }
 
@@ -1119,6 +1120,14 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         P.plan_r.twf = ftr;
         P.plan_p.twf = ftp;
     }
+    // half-length radial plan: its twiddles exp(-2 pi i j/K) are plan_r's at stride 2
+    if (!make_fft_plan(ctx->K, P.plan_h)) {
+        ctx->err = "unsupported transform length";
+        return bail(PIZZA_EINVAL);
+    }
+    P.plan_h.tw = P.plan_r.tw;
+    P.plan_h.twf = P.plan_r.twf;
+    P.plan_h.tws = 2;
 
     // m-independent banded operators and tau rows
     HostOps H = host_ops_of(ctx);

@@ -88,10 +88,10 @@ __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2((double
 // skipped; otherwise the twiddle products are fused into the butterfly adds.
 template <int SIGN, int R, bool FIRST, class T>
 __device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __restrict__ dst, int L, int Ns,
-                                              const T* __restrict__ tw, int nb, int tid, int nth) {
+                                              const T* __restrict__ tw, int tws, int nb, int tid, int nth) {
     using RT = typename Cx<T>::R;
     const int nbf = L / R;
-    const int twmul = L / (Ns * R);
+    const int twmul = L / (Ns * R) * tws;
     constexpr bool first = FIRST;
     for (int t = tid; t < nb * nbf; t += nth) {
         const int bt = t / nbf;
@@ -190,18 +190,18 @@ __device__ __forceinline__ T* fft_batched(T* buf0, T* buf1, const FftPlan& pl, i
         const int R = pl.radix[p];
         if (p == 0) {  // Ns == 1: unit twiddles
             if (R == 4)
-                stockham_pass<SIGN, 4, true>(a, b, pl.L, Ns, tw, nb, tid, nth);
+                stockham_pass<SIGN, 4, true>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
             else if (R == 2)
-                stockham_pass<SIGN, 2, true>(a, b, pl.L, Ns, tw, nb, tid, nth);
+                stockham_pass<SIGN, 2, true>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
             else
-                stockham_pass<SIGN, 3, true>(a, b, pl.L, Ns, tw, nb, tid, nth);
+                stockham_pass<SIGN, 3, true>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
         } else {
             if (R == 4)
-                stockham_pass<SIGN, 4, false>(a, b, pl.L, Ns, tw, nb, tid, nth);
+                stockham_pass<SIGN, 4, false>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
             else if (R == 2)
-                stockham_pass<SIGN, 2, false>(a, b, pl.L, Ns, tw, nb, tid, nth);
+                stockham_pass<SIGN, 2, false>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
             else
-                stockham_pass<SIGN, 3, false>(a, b, pl.L, Ns, tw, nb, tid, nth);
+                stockham_pass<SIGN, 3, false>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
         }
         __syncthreads();
         T* t = a;
@@ -210,6 +210,110 @@ __device__ __forceinline__ T* fft_batched(T* buf0, T* buf1, const FftPlan& pl, i
         Ns *= R;
     }
     return a;
+}
+
+// DCT-I of nb complex vectors by one complex FFT of length K each (half the
+// length of the even-extension transform).  Input x_b[j], j = 0..K (K a power of
+// two), at buf0[b * 2K + j]; output at the same places:
+//   C_k = x_0 + (-1)^k x_K + 2 sum_{j=1}^{K-1} x_j cos(pi j k / K),  k = 0..K,
+// i.e. the transform of the even extension of x.  With
+//   y_j = (x_j + x_{K-j})/2 - sin(pi j/K) (x_j - x_{K-j}),  j = 0..K-1,
+//   F_k = sum_j y_j exp(+2 pi i j k/K),
+// the even outputs are C_{2k} = F_k + F_{K-k} (F_K = F_0) and the odd ones follow
+// from C_1 = sum_j (x_j - x_{K-j}) cos(pi j/K) by C_{2k+1} = C_{2k-1} - i (F_k - F_{K-k})
+// (the cosine-sum recurrence of the real-data case, applied to the real and
+// imaginary parts at once), a prefix sum taken by one warp per vector.
+// plan_h: length K; plan_r: length 2K, whose twiddles give cos and sin(pi j/K).
+// buf1: scratch of 2 nb K entries.  nb <= 4.  Starts and ends with __syncthreads().
+template <class T>
+__device__ T* dct1_batched(T* buf0, T* buf1, const FftPlan& plan_h, const FftPlan& plan_r, int nb) {
+    using RT = typename Cx<T>::R;
+    const int K = plan_h.L, L = 2 * K, H = K / 2;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
+    const T* tw = Cx<T>::tw(plan_r);  // tw[j] = (cos(pi j/K), -sin(pi j/K))
+    __shared__ T c1s[4];
+    __syncthreads();
+    for (int t = tid; t < nb * K; t += nth) {
+        const int b = t / K, j = t - b * K;
+        const T* x = buf0 + (size_t)b * L;
+        const T xa = x[j], xb = x[K - j];
+        const RT s = -tw[j].y;
+        const T sum = cadd(xa, xb), dif = csub(xa, xb);
+        T y;
+        y.x = fmat(-s, dif.x, (RT)0.5 * sum.x);
+        y.y = fmat(-s, dif.y, (RT)0.5 * sum.y);
+        buf1[(size_t)b * K + j] = y;
+    }
+    if (warp < nb) {
+        const T* x = buf0 + (size_t)warp * L;
+        T acc = Cx<T>::make(0.0, 0.0);
+        for (int j = lane; j < K; j += 32) {
+            const T dif = csub(x[j], x[K - j]);
+            const RT c = tw[j].x;
+            acc.x = fmat(c, dif.x, acc.x);
+            acc.y = fmat(c, dif.y, acc.y);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) c1s[warp] = acc;
+    }
+    T* F = fft_batched<+1>(buf1, buf1 + (size_t)nb * K, plan_h, nb);
+    // even outputs
+    for (int t = tid; t < nb * (H + 1); t += nth) {
+        const int b = t / (H + 1), k = t - b * (H + 1);
+        const T* f = F + (size_t)b * K;
+        buf0[(size_t)b * L + 2 * k] = cadd(f[k], f[k == 0 ? 0 : K - k]);
+    }
+    // odd outputs: prefix sum of d_k = -i (F_k - F_{K-k}), d_0 = 0, one warp per vector
+    if (warp < nb) {
+        const T* f = F + (size_t)warp * K;
+        T* out = buf0 + (size_t)warp * L;
+        const int chunk = (H + 31) / 32;
+        const int lo = min(lane * chunk, H), hi = min(lo + chunk, H);
+        T tot = Cx<T>::make(0.0, 0.0);
+        for (int k = lo; k < hi; ++k) {
+            if (k == 0) continue;
+            const T df = csub(f[k], f[K - k]);
+            tot.x += df.y;
+            tot.y -= df.x;
+        }
+        // exclusive scan of the chunk totals across the warp
+        T inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const RT ux = __shfl_up_sync(0xffffffffu, inc.x, o);
+            const RT uy = __shfl_up_sync(0xffffffffu, inc.y, o);
+            if (lane >= o) {
+                inc.x += ux;
+                inc.y += uy;
+            }
+        }
+        T run = c1s[warp];
+        run.x += inc.x - tot.x;
+        run.y += inc.y - tot.y;
+        for (int k = lo; k < hi; ++k) {
+            if (k > 0) {
+                const T df = csub(f[k], f[K - k]);
+                run.x += df.y;
+                run.y -= df.x;
+            }
+            out[2 * k + 1] = run;
+        }
+    }
+    __syncthreads();
+    return buf0;
+}
+
+// The radial DCT-I of nb even-extended vectors in buf0 (stride 2K): by the
+// half-length transform when the plan is set, else by the FFT of the even
+// extension.  Result at the returned pointer, vector b at [b * 2K + k], k <= K.
+template <class T>
+__device__ __forceinline__ T* radial_dct1(T* buf0, T* buf1, const StepParams& P, int nb) {
+    if (P.plan_h.L == P.K && P.K >= 8) return dct1_batched(buf0, buf1, P.plan_h, P.plan_r, nb);
+    return fft_batched<-1>(buf0, buf1, P.plan_r, nb);
 }
 
 // 2^e with e the difference of the binary exponents of a and b (1 when either

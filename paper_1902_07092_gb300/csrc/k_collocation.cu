@@ -65,12 +65,12 @@ __global__ void __launch_bounds__(NT) k_coll_spec_to_grid(StepParams P, VecSet y
         const double2 v = (m > 0) ? f[j] : make_double2(y.u[j], 0.0);
         even_extend_store(bufA, K, j, v);
     }
-    double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, 1);
+    double2* R = radial_dct1(bufA, bufB, P, 1);
     plain_from_fft(R, cc0, K);
     __syncthreads();
     cheb_derivative_scan(cc0, cc1, bufA, N, P.inv_a);
     load_plain_for_synthesis(bufA, cc1, K);
-    R = fft_batched<-1>(bufA, bufB, P.plan_r, 1);
+    R = radial_dct1(bufA, bufB, P, 1);
     const double dm = (double)m;
     for (int k = tid; k < N; k += nth) {
         const double2 d = cscale(R[k], 0.5);
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(NT) k_coll_grid_rows(StepParams P, const doubl
             const int f = (b0 + b == 0) ? 0 : 2;
             for (int j = tid; j <= K; j += nth) even_extend_store(bufA + b * L, K, j, G2[g_index(j, f, m, M)]);
         }
-        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        double2* R = radial_dct1(bufA, bufB, P, nb);
         for (int b = 0; b < nb; ++b) plain_from_fft(R + b * L, (b0 + b == 0) ? cc0 : cc1, K);
         __syncthreads();
     }
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(NT) k_coll_grid_rows(StepParams P, const doubl
     for (int b0 = 0; b0 < 2; b0 += NB) {
         const int nb = min(NB, 2 - b0);
         for (int b = 0; b < nb; ++b) load_plain_for_synthesis(bufA + b * L, (b0 + b == 0) ? cc0 : cc1, K);
-        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        double2* R = radial_dct1(bufA, bufB, P, nb);
         for (int b = 0; b < nb; ++b) {
             double2* dst = (b0 + b == 0) ? cc2 : cc0;
             for (int k = tid; k < N; k += nth) dst[k] = cscale(R[b * L + k], 0.5);

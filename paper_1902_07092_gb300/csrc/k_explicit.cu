@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
                 even_extend_store(z, K, j, v);
             }
         }
-        T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        T* R = radial_dct1(bufA, bufB, P, nb);
         for (int b = 0; b < nb; ++b) {
             const int fid = fields[f0 + b];
             const T* Z = R + b * L;
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
             for (int j = tid; j <= K; j += nth)
                 even_extend_store(z, K, j, cscale(G2[g_index(j, f, m, M)], Tab<T>::h2(P, j)));
         }
-        T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        T* R = radial_dct1(bufA, bufB, P, nb);
         const RT iK = (RT)(1.0 / (double)K), hK = (RT)(0.5 / (double)K);
         for (int b = 0; b < nb; ++b) {
             T* dst = (b0 + b == 0) ? cc0 : cc1;
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
                 even_extend_store(z, K, j, v);
             }
         }
-        T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        T* R = radial_dct1(bufA, bufB, P, nb);
         // the grid values of N go to cc2 (omega) and cc0 (theta): cc0 was consumed
         // by the loads above (for NB == 1 the theta pass runs after the omega one)
         for (int b = 0; b < nb; ++b) {
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
             T* z = bufA + b * L;
             for (int j = tid; j <= K; j += nth) even_extend_store(z, K, j, src[j]);
         }
-        T* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        T* R = radial_dct1(bufA, bufB, P, nb);
         for (int b = 0; b < nb; ++b) {
             T* dst = (b0 + b == 0) ? cc1 : cc2;  // N_omega_hat -> cc1, N_theta_hat -> cc2
             const T* Z = R + b * L;

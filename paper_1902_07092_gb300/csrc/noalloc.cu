@@ -163,6 +163,9 @@ extern "C" int pizza_explicit_terms_noalloc(int n_r, int n_phi, double Ra, doubl
     if (!make_fft_plan(2 * P.K, P.plan_r) || !make_fft_plan(n_phi, P.plan_p))
         return na_fail(PIZZA_EINVAL, "unsupported transform length");
     P.plan_r.tw = reinterpret_cast<const double2*>(sl->tables + NA_TAB_GRID);
+    if (!make_fft_plan(P.K, P.plan_h)) return na_fail(PIZZA_EINVAL, "unsupported transform length");
+    P.plan_h.tw = P.plan_r.tw;  // exp(-2 pi i j/K) = plan_r's twiddles at stride 2
+    P.plan_h.tws = 2;
     P.plan_p.tw = reinterpret_cast<const double2*>(sl->tables + NA_TAB_GRID + NA_TAB_TWR);
     size_t off = NA_TAB_GRID + NA_TAB_TW;
     for (int id = 0; id < OP_COUNT; ++id) {

@@ -16,6 +16,7 @@ constexpr int MAX_RHS_TERMS = 10;
 struct FftPlan {
     int L;
     int npass;
+    int tws;  // stride of the twiddle table: tw[tws * j] = exp(-2 pi i j / L)
     int radix[MAX_PASSES];
     const double2* tw;  // tw[j] = exp(-2 pi i j / L), j < L
     const float2* twf;  // the same, rounded to FP32 (mixed-precision explicit stage)
@@ -77,7 +78,8 @@ struct StepParams {
     const double* h2;     // [n_r]
     const double* inv_s;  // [n_r]
     const float *s_f, *h2_f, *inv_s_f;  // the same in FP32 (mixed-precision explicit stage)
-    FftPlan plan_r;       // length 2K (radial DCT-I)
+    FftPlan plan_r;       // length 2K (radial DCT-I as an FFT of the even extension)
+    FftPlan plan_h;       // length K, plan_r's twiddles at stride 2 (radial DCT-I, dct1_batched)
     FftPlan plan_p;       // length n_phi (azimuthal)
     DevOps ops;
     // explicit stage in FP32 (option "precision" = mixed): 1 when selected
