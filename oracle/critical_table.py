@@ -20,7 +20,7 @@ CASES = [  # E, radial resolution n_c, initial Ra guess, m scan range, drift-fre
     (1e-4, 64, 5e5, range(2, 16), None),
     # at E = 1e-8 the QZ estimate without a guess lands on spurious branches of the
     # tau pencil; the scan follows the thermal Rossby wave from omega_d ~ -1e5
-    (1e-8, 320, 6.2e10, range(132, 157, 6), -1.0e5j),
+    (1e-8, 320, 6.0e10, range(132, 157, 6), -1.0e5j),
 ]
 
 
@@ -31,7 +31,9 @@ def critical(E, n_c, ra0, ms, guess=None, log=lambda *a: print(*a, flush=True)):
     for m in ms:
         ra, lam = marginal_rayleigh(E, 1.0, 0.35, m, n_c, ra_guess, guess=guess)
         log("E=%g m=%d Ra=%.8e omega=%.6e" % (E, m, ra, lam.imag))
-        ra_guess = ra
+        # with a branch guess every mode starts from the same Ra below onset (a
+        # start above the marginal Ra lets the continuation lose the branch)
+        ra_guess = ra if guess is None else ra0
         if best is None or ra < best[0]:
             best = (ra, m, lam.imag)
         if prev is not None and ra > prev and m > best[1] + 2:

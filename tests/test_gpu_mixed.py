@@ -82,7 +82,7 @@ def test_mixed_large_workload_50_steps():
     after every step."""
     from paper_1902_07092_gb300.binding import Solver
     n_r, n_phi, E, dt = 2049, 6144, 1e-8, 1e-10
-    Ra = 2.0e11     # order of 20 Ra_c at E = 1e-8
+    Ra = 2.0e11     # 3.2 Ra_c at E = 1e-8 (Ra_c = 6.16e10)
     ref = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "SBDF3", dt)
     mix = mixed_solver(n_r, n_phi, E, Ra, "SBDF3", dt)
     th = inputs.theta_init(n_r, n_phi, 1e-3, 3, cfg=3)

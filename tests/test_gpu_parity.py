@@ -154,7 +154,7 @@ def test_large_workload_sampled():
     from paper_1902_07092_gb300.binding import Solver
     from oracle.explicit import Grid
     from oracle.operators import IntegrationOperators
-    Ra = 2.0e11     # order of 20 Ra_c at E = 1e-8; the value does not affect parity
+    Ra = 2.0e11     # 3.2 Ra_c at E = 1e-8; the value does not affect parity
     gpu = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "SBDF3", dt)
     nc = gpu.n_c
     th = inputs.theta_init(n_r, n_phi, 1e-3, 3, cfg=3)
