@@ -104,7 +104,13 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            add the explicit zonal-wind self-interaction (E/2) Upsilon u_bar
  *            omega_0 of Eq. uphicoll.  Set before stepping; changing it discards
  *            the factored operators.  While a tape is recorded: PIZZA_ESTATE;
- *            pizza_tape_begin with pumping on: PIZZA_EUNSUPPORTED.
+ *            pizza_tape_begin with pumping on: PIZZA_EUNSUPPORTED;
+ *   "radial_batch" radial transforms batched per shared-memory pass in the
+ *            per-mode explicit kernels: 1, 2 or 4, 0 = the default rule (up to
+ *            n_r = 513: 4 in FP64, 2 in mixed precision; else 1); "phi_threads" threads of the per-radius azimuthal
+ *            kernel: 128, 256 or 512 (at most 12 points per thread), 0 = default.
+ *            Launch shapes only (pizza_autotune picks them by timing): results
+ *            are bitwise the same.
  * Returns PIZZA_EINVAL for an unknown key or an invalid value. */
 #define PIZZA_COLL_MAX_NR 513
 int pizza_set_option(pizza_ctx *ctx, const char *key, double value);
@@ -213,8 +219,8 @@ int pizza_explicit_adjoint(pizza_ctx *ctx, const double *e_psi_bar, const double
 int pizza_nusselt_weights(const pizza_ctx *ctx, double *w);
 
 /* Autotuner: times the explicit stage of the context (on its current state)
- * for each launch shape the device allows -- radial transforms batched one or two
- * per shared-memory pass, 128/256/512 threads in the azimuthal kernel -- and
+ * for each launch shape the device allows -- radial transforms batched one, two
+ * or four per shared-memory pass, 128/256/512 threads in the azimuthal kernel -- and
  * keeps the fastest for later steps.  The shapes change the schedule, not the
  * arithmetic: results are bitwise the same.  *nb_r and *phi_threads (may be NULL)
  * receive the choice.  Integration formulation only. */

@@ -1241,6 +1241,22 @@ int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
         reset_slots(ctx);
         return PIZZA_OK;
     }
+    if (std::strcmp(key, "radial_batch") == 0) {
+        if (value != 0.0 && value != 1.0 && value != 2.0 && value != 4.0)
+            return fail(ctx, PIZZA_EINVAL, "radial_batch must be 0 (default rule), 1, 2 or 4");
+        cudaStreamSynchronize(ctx->stream);
+        ctx->P.nb_r = (int)value;
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "phi_threads") == 0) {
+        if (value != 0.0 && value != 128.0 && value != 256.0 && value != 512.0)
+            return fail(ctx, PIZZA_EINVAL, "phi_threads must be 0 (default rule), 128, 256 or 512");
+        if (value > 0.0 && ctx->n_phi > 12 * (int)value)
+            return fail(ctx, PIZZA_EINVAL, "phi_threads too small: at most 12 azimuthal points per thread");
+        cudaStreamSynchronize(ctx->stream);
+        ctx->P.phi_threads = (int)value;
+        return PIZZA_OK;
+    }
     if (std::strcmp(key, "pumping_eps") == 0) {
         if (!(value >= 0.0) || !std::isfinite(value) || value > 1.0)
             return fail(ctx, PIZZA_EINVAL, "pumping_eps must be in [0, 1] (0: Ekman pumping off)");
@@ -1608,7 +1624,7 @@ int pizza_autotune(pizza_ctx* ctx, int* nb_r, int* phi_thr) {
     CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int keep_nb = ctx->P.nb_r, keep_th = ctx->P.phi_threads;
     std::vector<std::pair<int, int>> cand;
-    for (int nb = 1; nb <= 2; ++nb)
+    for (int nb : {1, 2, 4})
         for (int th : {128, 256, 512}) {
             if (ctx->n_phi > th * 12) continue;  // the azimuthal kernel holds 12 points per thread
             ctx->P.nb_r = nb;

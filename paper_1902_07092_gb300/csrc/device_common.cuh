@@ -308,11 +308,13 @@ __device__ T* dct1_batched(T* buf0, T* buf1, const FftPlan& plan_h, const FftPla
 }
 
 // The radial DCT-I of nb even-extended vectors in buf0 (stride 2K): by the
-// half-length transform when the plan is set, else by the FFT of the even
-// extension.  Result at the returned pointer, vector b at [b * 2K + k], k <= K.
+// half-length transform when the plan is set and K >= 128, else by the FFT of
+// the even extension (at small K the extra reduction and scan phases cost more
+// latency than the shorter transform saves).  Result at the returned pointer,
+// vector b at [b * 2K + k], k <= K.
 template <class T>
 __device__ __forceinline__ T* radial_dct1(T* buf0, T* buf1, const StepParams& P, int nb) {
-    if (P.plan_h.L == P.K && P.K >= 8) return dct1_batched(buf0, buf1, P.plan_h, P.plan_r, nb);
+    if (P.plan_h.L == P.K && P.K >= 128) return dct1_batched(buf0, buf1, P.plan_h, P.plan_r, nb);
     return fft_batched<-1>(buf0, buf1, P.plan_r, nb);
 }
 

@@ -23,9 +23,12 @@ constexpr int MAXPER = 12;       // azimuthal points per thread held in register
 __device__ __forceinline__ int g_index(int k, int f, int m, int M) { return (k * 4 + f) * M + m; }
 
 // number of radial transforms batched together in shared memory (the
-// autotuner's choice, else two up to 1024 points)
+// autotuner's choice, else up to n_r = 513 four in FP64 -- all four synthesised
+// fields of a mode in one pass -- and two in FP32, measured fastest at n_r = 257)
 __host__ __device__ inline int radial_batch(const StepParams& P) {
-    return P.nb_r > 0 ? P.nb_r : (2 * P.K <= 1024 ? 2 : 1);
+    if (P.nb_r > 0) return P.nb_r;
+    if (2 * P.K > 1024) return 1;
+    return P.fp32 ? 2 : 4;
 }
 // threads of the per-radius azimuthal kernels
 inline int phi_threads(const StepParams& P) {

@@ -69,9 +69,33 @@ def test_autotuned_launch_shapes_do_not_change_results():
     for k, run in enumerate(RUNS[:3] + RUNS[4:]):
         a, st = _make(k, run)
         nb, th = a.autotune()
-        assert nb in (1, 2) and th in (128, 256, 512)
+        assert nb in (1, 2, 4) and th in (128, 256, 512)
         a.set_state(*st)
         a.step(4)
         for x, y in zip(a.get_state(), ref[k]):
             assert np.array_equal(x, y)
         a.close()
+
+
+def test_explicit_launch_shapes_give_the_same_states():
+    """Options radial_batch (1, 2, 4) and phi_threads (256, 512): the same steps,
+    bitwise, in FP64 and in mixed precision."""
+    from paper_1902_07092_gb300.binding import pizza_set_option
+    run = RUNS[4]
+    for prec in (0, 1):
+        ref = None
+        for nb in (1, 2, 4):
+            for th in (256, 512):
+                a, st = _make(0, run)
+                pizza_set_option(a.ctx, "precision", prec)
+                pizza_set_option(a.ctx, "radial_batch", nb)
+                pizza_set_option(a.ctx, "phi_threads", th)
+                a.set_state(*st)
+                a.step(3)
+                got = a.get_state()
+                if ref is None:
+                    ref = got
+                else:
+                    for x, y in zip(got, ref):
+                        assert np.array_equal(x, y), (prec, nb, th)
+                a.close()
