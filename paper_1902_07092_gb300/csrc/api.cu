@@ -306,7 +306,20 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         std::vector<double> ubd(bu.begin() + 2 * 9, bu.end());
         UPLOAD(F.uBand, double, ubd);
     }
+    // Large N_c: the temperature systems lose digits in the unpivoted block
+    // factorisation and need a refinement step.  Two FP64-residual corrections of
+    // FP32 solves reach the accuracy of the FP64 solve there (1e-13 at N_c = 1365,
+    // measured on the tau systems), with the chains on the FP32 pipe; the
+    // zonal-flow system (one mode) keeps its FP64 refinement.
     F.refine_t = (nc > 600) ? 1 : 0;
+    F.ir_t = (nc > 600) ? 2 : 0;
+    if (F.ir_t) {
+        const std::vector<float> tK32(htK.begin(), htK.end()), tY32(htY.begin(), htY.end()),
+            tS32(htS.begin(), htS.end());
+        UPLOAD(F.tBlk32, float, tK32);
+        UPLOAD(F.tY32, float, tY32);
+        UPLOAD(F.tSinv32, float, tS32);
+    }
     UPLOAD(F.uBlk, double, ub);
     UPLOAD(F.uY, double, fu.Y);
     UPLOAD(F.uSinv, double, fu.Sinv);
@@ -1176,6 +1189,14 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         up(dd, bd.data(), bd.size() * 8);
         up(dfull, tp.data(), tp.size() * 8);
         up(dfull2, td.data(), td.size() * 8);
+        std::vector<float> bd32(bd.begin(), bd.end());
+        float* dd32 = dalloc<float>(ctx, bd32.size(), al);
+        if (!dd32) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(dd32, bd32.data(), bd32.size() * 4);
+        P.ops.tau_dir_B32 = dd32;
         P.ops.tau_dir = dfull2;
         P.ops.tau_psi_B = dp;
         P.ops.tau_dir_B = dd;

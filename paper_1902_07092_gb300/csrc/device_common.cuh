@@ -224,6 +224,7 @@ __device__ __forceinline__ T* fft_batched(T* buf0, T* buf1, const FftPlan& pl, i
 // (the cosine-sum recurrence of the real-data case, applied to the real and
 // imaginary parts at once), a prefix sum taken by one warp per vector.
 // plan_h: length K; plan_r: length 2K, whose twiddles give cos and sin(pi j/K).
+// The sum for C_1 and the prefix sum are accumulated in FP64.
 // buf1: scratch of 2 nb K entries.  nb <= 4.  Starts and ends with __syncthreads().
 template <class T>
 __device__ T* dct1_batched(T* buf0, T* buf1, const FftPlan& plan_h, const FftPlan& plan_r, int nb) {
@@ -231,7 +232,7 @@ __device__ T* dct1_batched(T* buf0, T* buf1, const FftPlan& plan_h, const FftPla
     const int K = plan_h.L, L = 2 * K, H = K / 2;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
     const T* tw = Cx<T>::tw(plan_r);  // tw[j] = (cos(pi j/K), -sin(pi j/K))
-    __shared__ T c1s[4];
+    __shared__ double2 c1s[4];
     __syncthreads();
     for (int t = tid; t < nb * K; t += nth) {
         const int b = t / K, j = t - b * K;
@@ -246,12 +247,12 @@ __device__ T* dct1_batched(T* buf0, T* buf1, const FftPlan& plan_h, const FftPla
     }
     if (warp < nb) {
         const T* x = buf0 + (size_t)warp * L;
-        T acc = Cx<T>::make(0.0, 0.0);
+        double2 acc = make_double2(0.0, 0.0);
         for (int j = lane; j < K; j += 32) {
             const T dif = csub(x[j], x[K - j]);
-            const RT c = tw[j].x;
-            acc.x = fmat(c, dif.x, acc.x);
-            acc.y = fmat(c, dif.y, acc.y);
+            const double c = (double)tw[j].x;
+            acc.x = fma(c, (double)dif.x, acc.x);
+            acc.y = fma(c, (double)dif.y, acc.y);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -273,48 +274,52 @@ __device__ T* dct1_batched(T* buf0, T* buf1, const FftPlan& plan_h, const FftPla
         T* out = buf0 + (size_t)warp * L;
         const int chunk = (H + 31) / 32;
         const int lo = min(lane * chunk, H), hi = min(lo + chunk, H);
-        T tot = Cx<T>::make(0.0, 0.0);
+        double2 tot = make_double2(0.0, 0.0);
         for (int k = lo; k < hi; ++k) {
             if (k == 0) continue;
             const T df = csub(f[k], f[K - k]);
-            tot.x += df.y;
-            tot.y -= df.x;
+            tot.x += (double)df.y;
+            tot.y -= (double)df.x;
         }
         // exclusive scan of the chunk totals across the warp
-        T inc = tot;
+        double2 inc = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const RT ux = __shfl_up_sync(0xffffffffu, inc.x, o);
-            const RT uy = __shfl_up_sync(0xffffffffu, inc.y, o);
+            const double ux = __shfl_up_sync(0xffffffffu, inc.x, o);
+            const double uy = __shfl_up_sync(0xffffffffu, inc.y, o);
             if (lane >= o) {
                 inc.x += ux;
                 inc.y += uy;
             }
         }
-        T run = c1s[warp];
+        double2 run = c1s[warp];
         run.x += inc.x - tot.x;
         run.y += inc.y - tot.y;
         for (int k = lo; k < hi; ++k) {
             if (k > 0) {
                 const T df = csub(f[k], f[K - k]);
-                run.x += df.y;
-                run.y -= df.x;
+                run.x += (double)df.y;
+                run.y -= (double)df.x;
             }
-            out[2 * k + 1] = run;
+            out[2 * k + 1] = Cx<T>::from(run);
         }
     }
     __syncthreads();
     return buf0;
 }
 
-// The radial DCT-I of nb even-extended vectors in buf0 (stride 2K): by the
-// half-length transform when the plan is set and K >= 128, else by the FFT of
-// the even extension (at small K the extra reduction and scan phases cost more
-// latency than the shorter transform saves).  Result at the returned pointer,
-// vector b at [b * 2K + k], k <= K.
+// The radial DCT-I of nb even-extended vectors in buf0 (stride 2K): in FP64 by
+// the half-length transform when the plan is set and K >= 128, else by the FFT
+// of the even extension.  At small K the extra reduction and scan phases cost
+// more latency than the shorter transform saves; in FP32 the odd outputs'
+// differences F_k - F_{K-k} cancel to a few ulps of F each and their sum loses
+// more than the FP32 transform's own rounding (measured: 50x the state error of
+// the mixed path after 50 steps at n_r = 2049), so FP32 keeps the long transform.
+// Result at the returned pointer, vector b at [b * 2K + k], k <= K.
 template <class T>
 __device__ __forceinline__ T* radial_dct1(T* buf0, T* buf1, const StepParams& P, int nb) {
-    if (P.plan_h.L == P.K && P.K >= 128) return dct1_batched(buf0, buf1, P.plan_h, P.plan_r, nb);
+    constexpr bool fp64 = sizeof(typename Cx<T>::R) == sizeof(double);
+    if (fp64 && P.plan_h.L == P.K && P.K >= 128) return dct1_batched(buf0, buf1, P.plan_h, P.plan_r, nb);
     return fft_batched<-1>(buf0, buf1, P.plan_r, nb);
 }
 

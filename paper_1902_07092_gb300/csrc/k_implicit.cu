@@ -80,6 +80,26 @@ __device__ __forceinline__ double2 fms_x(double a, double2 b, double2 acc) {
 }
 __device__ __forceinline__ double fms_x(double a, double b, double acc) { return fma(-a, b, acc); }
 
+// FP32 counterparts for the refined FP32 temperature solves
+template <>
+__device__ __forceinline__ float2 zero<float2>() { return make_float2(0.f, 0.f); }
+template <>
+__device__ __forceinline__ float zero<float>() { return 0.f; }
+template <>
+__device__ __forceinline__ float2 shfl_idx<float2>(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float reduce4(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+__device__ __forceinline__ float2 reduce4(float2 v) { return make_float2(reduce4(v.x), reduce4(v.y)); }
+__device__ __forceinline__ float2 fma_x(float a, float2 b, float2 acc) {
+    return make_float2(fmaf(a, b.x, acc.x), fmaf(a, b.y, acc.y));
+}
+__device__ __forceinline__ float2 sub_x(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
 constexpr int PFB = 2;  // blocks of coefficients prefetched ahead in the chains
 
 // Barrier of the two warps (64 threads) of a solver pair.
@@ -280,6 +300,53 @@ __device__ void schur_update(double2* sol, int nc, const TF* __restrict__ Y, int
     }
 }
 
+// FP32 Schur step of the temperature system by one warp: sol[2..] = D^{-1} r on
+// entry, sol[0..2) = S^{-1}(g - B sol[2..]) on exit, g = the residual's tau rows;
+// B: 2 x (nc-2) tau rows in FP32, Sinv real 2 x 2.
+__device__ void warp_schur32_dir(float2* sol, const float2* g, int nc, const float* __restrict__ B,
+                                 const float* __restrict__ Sinv) {
+    const int lane = threadIdx.x & 31;
+    const int n = nc - 2;
+    float2 t[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int j = lane; j < n; j += 32) {
+        const float2 xv = sol[2 + j];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float b = __ldg(&B[(size_t)r * n + j]);
+            t[r].x = fmaf(b, xv.x, t[r].x);
+            t[r].y = fmaf(b, xv.y, t[r].y);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            t[r].x += __shfl_xor_sync(0xffffffffu, t[r].x, o);
+            t[r].y += __shfl_xor_sync(0xffffffffu, t[r].y, o);
+        }
+        t[r] = make_float2(g[r].x - t[r].x, g[r].y - t[r].y);
+    }
+    __syncwarp();
+    if (lane < 2) {
+        const float a = Sinv[lane * 2], b = Sinv[lane * 2 + 1];
+        sol[lane] = make_float2(fmaf(a, t[0].x, b * t[1].x), fmaf(a, t[0].y, b * t[1].y));
+    }
+    __syncwarp();
+}
+
+// FP32 y2 -= Y y1 for the temperature system, threads [t0, t0 + nt)
+__device__ void schur_update32_dir(float2* sol, int nc, const float* __restrict__ Y, int t0, int nt) {
+    const int n = nc - 2;
+    const float2 y0 = sol[0], y1 = sol[1];
+    for (int j = threadIdx.x - t0; j < n; j += nt) {
+        const float a = Y[(size_t)j * 2], b = Y[(size_t)j * 2 + 1];
+        float2 acc = sol[2 + j];
+        acc.x -= fmaf(a, y0.x, b * y1.x);
+        acc.y -= fmaf(a, y0.y, b * y1.y);
+        sol[2 + j] = acc;
+    }
+}
+
 template <int H>
 __device__ __forceinline__ double2 band_row_c(const double* __restrict__ band, const double2* x, int k, int nc) {
     const double* row = band + (size_t)k * (2 * H + 1);
@@ -419,13 +486,14 @@ __device__ void epilogue_row(const StepParams& P, const RhsSpec& R, double gdt, 
 struct SolveSmem {
     double2 *pf[2], *pw[2], *px[2], *pd[2], *tf[2], *tw[2], *tx[2];
     double *uf, *ux;
+    float2 *tr, *tq, *td;  // refined FP32 temperature solves: residual, chain scratch, correction (MB = 1)
 };
 
 __host__ __device__ inline int round8(int n) { return (n + 7) / 8 * 8; }
 
 __host__ __device__ inline size_t solve_smem_doubles(int nc, int MB) {
     const int b = round8(nc);
-    return (size_t)MB * 2 * 7 * b + 2 * (size_t)b;
+    return (size_t)MB * 2 * 7 * b + 2 * (size_t)b + 3 * (size_t)b;  // last: 3 b float2
 }
 
 template <int MB>
@@ -444,7 +512,11 @@ __device__ SolveSmem carve(double2* base, int nc) {
     }
     double* d = reinterpret_cast<double*>(p);
     s.uf = d; d += b;
-    s.ux = d;
+    s.ux = d; d += b;
+    float2* f = reinterpret_cast<float2*>(d);
+    s.tr = f; f += b;
+    s.tq = f; f += b;
+    s.td = f;
     return s;
 }
 
@@ -453,10 +525,11 @@ __device__ SolveSmem carve(double2* base, int nc) {
 // same factors, x += correction.  The residual replaces the right-hand side and
 // the correction goes to the streamfunction's correction array (no longer needed).
 template <int MB>
-__device__ void refine_temperature(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u) {
+__device__ void refine_temperature(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u,
+                                   bool theta) {
     const int nc = P.nc, M = P.M, nt = nc - 2, nbt = (nt + 3) / 4;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
-    for (int idx = tid; idx < MB * nc; idx += nth) {
+    for (int idx = tid; theta && idx < MB * nc; idx += nth) {
         const int mi = idx / nc, k = idx - mi * nc, m = m0 + mi;
         if (m >= M || k < 2) continue;
         const double* row = F.tBand + ((size_t)m * nt + (k - 2)) * 9;
@@ -482,7 +555,7 @@ __device__ void refine_temperature(const StepParams& P, const DevFactors& F, Sol
     if (warp < MB + (has_u ? 1 : 0)) {  // tau rows
         const bool is_u = (warp == MB);
         const int m = m0 + warp;
-        if (is_u || m < M) {
+        if (is_u || (theta && m < M)) {
             double2 t0 = make_double2(0.0, 0.0), t1 = make_double2(0.0, 0.0);
             for (int j = lane; j < nc; j += 32) {
                 const double2 xv = is_u ? make_double2(s.ux[j], 0.0) : s.tx[warp][j];
@@ -508,8 +581,11 @@ __device__ void refine_temperature(const StepParams& P, const DevFactors& F, Sol
     // after the streamfunction solves: zonal-flow correction in pw, its chain scratch in pf
     double* du = reinterpret_cast<double*>(s.pw[0]);
     if (warp == 2 || warp == 3) {
-        pair_block_solve<4>(s.tf[0] + 2, s.tw[0], dt_[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true, warp - 2, 2);
-        if (warp == 2) warp_schur<2>(dt_[0], s.tf[0], nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
+        if (theta) {
+            pair_block_solve<4>(s.tf[0] + 2, s.tw[0], dt_[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true, warp - 2,
+                                2);
+            if (warp == 2) warp_schur<2>(dt_[0], s.tf[0], nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
+        }
     } else if ((warp == 4 || warp == 5) && has_u) {
         pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pf[0]), du + 2, nt, F.uBlk, true, warp - 4, 3);
         if (warp == 4) {
@@ -534,7 +610,7 @@ __device__ void refine_temperature(const StepParams& P, const DevFactors& F, Sol
         const int per = nth / MB;
         const int sys = tid / per, t0 = sys * per;
         const int m = m0 + sys;
-        if (sys < MB && m < M) schur_update<2>(dt_[sys], nc, F.tY + (size_t)m * nt * 2, t0, per);
+        if (theta && sys < MB && m < M) schur_update<2>(dt_[sys], nc, F.tY + (size_t)m * nt * 2, t0, per);
         if (has_u) {
             __syncthreads();
             const double u0 = du[0], u1 = du[1];
@@ -545,7 +621,7 @@ __device__ void refine_temperature(const StepParams& P, const DevFactors& F, Sol
     for (int idx = tid; idx < MB * nc; idx += nth) {
         const int mi = idx / nc, n = idx - mi * nc, m = m0 + mi;
         if (m >= M) continue;
-        s.tx[mi][n] = cadd(s.tx[mi][n], dt_[mi][n]);
+        if (theta) s.tx[mi][n] = cadd(s.tx[mi][n], dt_[mi][n]);
         if (m == 0) s.ux[n] += du[n];
     }
     __syncthreads();
@@ -582,6 +658,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         }
         s.pf[mi][n] = (n < 4 || m == 0) ? make_double2(0.0, 0.0) : ap;
         s.tf[mi][n] = (n < 2) ? make_double2(0.0, 0.0) : at;
+        if (F.ir_t) s.tr[n] = to_f2(s.tf[mi][n]);  // MB == 1 with ir_t
         if (m == 0) s.uf[n] = (n < 2) ? 0.0 : au;
     }
     __syncthreads();
@@ -594,7 +671,11 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, np, F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act,
                             warp, 1);
     } else if (warp < 4) {
-        pair_block_solve<4>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true, warp - 2, 2);
+        if (F.ir_t)
+            pair_block_solve<4>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 48, true, warp - 2, 2);
+        else
+            pair_block_solve<4>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true, warp - 2,
+                                2);
     } else if (warp < 6 && has_u) {
         pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4, 3);
     }
@@ -604,7 +685,10 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     if (warp == 0) {
         if (m0 > 0) warp_schur<4>(s.px[0], nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
     } else if (warp == 2) {
-        warp_schur<2>(s.tx[0], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
+        if (F.ir_t)
+            warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
+        else
+            warp_schur<2>(s.tx[0], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
     } else if (warp == 4 && has_u) {
         double t0 = 0.0, t1 = 0.0;
         for (int j = lane; j < nt; j += 32) {
@@ -629,7 +713,12 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
             if (m < M && m > 0) schur_update<4>(s.px[sys], nc, F.pY + (size_t)m * np * 4, t0, per);
         } else if (sys < 2 * MB) {
             const int mi = sys - MB, m = m0 + mi;
-            if (m < M) schur_update<2>(s.tx[mi], nc, F.tY + (size_t)m * nt * 2, t0, per);
+            if (m < M) {
+                if (F.ir_t)
+                    schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, t0, per);
+                else
+                    schur_update<2>(s.tx[mi], nc, F.tY + (size_t)m * nt * 2, t0, per);
+            }
         }
         if (has_u) {
             __syncthreads();
@@ -638,6 +727,10 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         }
     }
     __syncthreads();
+    if (F.ir_t) {  // the FP32 temperature solve becomes the FP64 iterate
+        for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
+        __syncthreads();
+    }
 
     // 5. one refinement step of the streamfunction solve: r = f - L x (a second
     //    step gains nothing: FP64 residuals limit the accuracy to ~cond * eps)
@@ -698,7 +791,48 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     }
     __syncthreads();
     }
-    if (F.refine_t) refine_temperature<MB>(P, F, s, m0, has_u);
+    if (F.ir_t) {
+        // temperature: x += S32^{-1}(f - L x), ir_t times, residuals in FP64 (MB == 1)
+        for (int it = 0; it < F.ir_t; ++it) {
+            for (int k = 2 + tid; k < nc; k += nth) {
+                const double* row = F.tBand + ((size_t)m0 * nt + (k - 2)) * 9;
+                double2 acc = s.tf[0][k];
+#pragma unroll
+                for (int d = 0; d < 9; ++d) {
+                    const int n = k - 4 + d;
+                    if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), s.tx[0][n]);
+                }
+                s.tr[k] = to_f2(acc);
+            }
+            if (warp == 0) {  // tau rows: r = 0 - tau x
+                double2 t0 = make_double2(0.0, 0.0), t1 = t0;
+                for (int j = lane; j < nc; j += 32) {
+                    const double2 xv = s.tx[0][j];
+                    const double b0 = __ldg(&P.ops.tau_dir[j]), b1 = __ldg(&P.ops.tau_dir[nc + j]);
+                    t0.x = fma(b0, xv.x, t0.x);
+                    t0.y = fma(b0, xv.y, t0.y);
+                    t1.x = fma(b1, xv.x, t1.x);
+                    t1.y = fma(b1, xv.y, t1.y);
+                }
+                t0 = warp_sum(t0);
+                t1 = warp_sum(t1);
+                if (lane < 2) s.tr[lane] = to_f2(lane ? make_double2(-t1.x, -t1.y) : make_double2(-t0.x, -t0.y));
+            }
+            __syncthreads();
+            if (warp == 2 || warp == 3)
+                pair_block_solve<4>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 48, true, warp - 2, 2);
+            __syncthreads();
+            if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
+            __syncthreads();
+            schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
+            __syncthreads();
+            for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
+            __syncthreads();
+        }
+        if (has_u) refine_temperature<MB>(P, F, s, m0, true, false);  // zonal flow only, FP64
+    } else if (F.refine_t) {
+        refine_temperature<MB>(P, F, s, m0, has_u, true);
+    }
 
     // 6. store, then mass / implicit operators for later stages
     for (int idx = tid; idx < MB * nc; idx += nth) {

@@ -39,6 +39,7 @@ struct DevOps {
     const double* tau_dir_B;  // 2 x (nc-2)
     const double* tau_psi;    // 4 x nc: the full streamfunction tau rows
     const double* tau_dir;    // 2 x nc: the full Dirichlet tau rows
+    const float* tau_dir_B32;  // tau_dir_B rounded to FP32 (refined FP32 temperature solves)
 };
 
 // Factored bordered systems (Appendix A) for one implicit weight gamma*dt.  The
@@ -55,6 +56,11 @@ struct DevFactors {
     // zonal flow, real, H = 4: blocks [nb_t][3][16], Y [n_t][2], Sinv [4], band [n_t][9]
     double *uBlk, *uY, *uSinv, *uBand;
     int refine_t;  // also refine the temperature and zonal-flow solves
+    // temperature by mixed-precision iterative refinement (large N_c): ir_t > 0
+    // solves with the block factors, Y and S^{-1} rounded to FP32 and corrects
+    // ir_t times from FP64 residuals of the assembled system
+    int ir_t;
+    float *tBlk32, *tY32, *tSinv32;
     // collocation: interior-row columns of the grid-valued inverses, column-major,
     // colW [M][n_r-2][2 n_r] (omega_k, psi_k), colT [M][n_r-2][n_r], colU [n_r-2][n_r]
     double2* colW;
