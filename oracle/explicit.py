@@ -28,6 +28,8 @@ From the state (Psi_hat, theta_hat, u_hat; paper coefficients, N_c per mode):
 Ekman pumping (``g.pump_eps`` not None): the approximate F_eps of Eq. approx_pump
 on the radial grid (``pumping.integration_grid``) joins step 3 as
 N_omega - F_eps, and Upsilon_eps u_bar joins N_u.
+Implicit buoyancy (``g.buoy_implicit``, Section 4): the buoyancy term leaves e_psi
+and joins the implicit operator (``stepper.IntegrationStepper``).
 """
 import numpy as np
 
@@ -53,6 +55,7 @@ class Grid:
         self.T = ch.tmat(self.n_r, self.n_r)
         self.Dn = ch.diff_matrix(self.n_r) / ann.a      # d/ds on plain coefficients
         self.pump_eps = None                             # Ekman pumping off
+        self.buoy_implicit = False                       # buoyancy in the explicit terms
 
 
 def radial_fields(g, psi_hat, theta_hat, u_hat):
@@ -132,6 +135,8 @@ def explicit_terms(g, psi_hat, theta_hat, u_hat, return_parts=False):
     Nu = ch.analysis(Nu_g, g.n_r)[:nc].real
     m = g.m[:, None]
     buoy = (ops.Ra / ops.Pr) * (1j * m / ops.ann.s_o) * theta_hat
+    if g.buoy_implicit:
+        buoy = np.zeros_like(buoy)
     e_psi = (ops.C @ (buoy + Nw).T).T
     e_psi[0] = 0.0
     e_theta = -(ops.D @ Nt.T).T - ops.tc_coef * 1j * m * (ops.G @ psi_hat.T).T

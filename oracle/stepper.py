@@ -107,13 +107,17 @@ class ImexScheme:
 
 
 class IntegrationStepper(ImexScheme):
-    def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt, pumping_eps=None):
+    def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt, pumping_eps=None, buoy_implicit=False):
         if scheme not in schemes.SCHEME_ID:
             raise ValueError(scheme)
         self.n_c = n_c_integration(n_r)
         self.ops = IntegrationOperators(n_r, self.n_c, eta, E, Pr, Ra)
         self.g = Grid(self.ops, n_phi)
         self.g.pump_eps = pumping_eps       # Ekman pumping, explicit (Eq. approx_pump)
+        # implicit buoyancy (Section 4): (Ra/Pr)(i m/s_o) C^I theta joins the implicit
+        # operator of the streamfunction equation; the temperature is advanced first
+        self.buoy_implicit = bool(buoy_implicit)
+        self.g.buoy_implicit = self.buoy_implicit
         self.scheme, self.dt = scheme, float(dt)
         self._lu = {}
         self.n_done = 0
@@ -140,12 +144,19 @@ class IntegrationStepper(ImexScheme):
         psi, th, u = y
         ops = self.ops
         ip = np.stack([ops.B(m) @ psi[m] for m in range(self.g.M)])
+        if self.buoy_implicit:
+            ip = ip + np.stack([self._buoyancy(m, th[m]) for m in range(self.g.M)])
         ip[0] = 0.0
         it = np.stack([ops.F(m) @ th[m] for m in range(self.g.M)]) / ops.Pr
         return ip, it, ops.Ez @ u
 
     def explicit(self, y):
         return explicit_terms(self.g, *y)
+
+    def _buoyancy(self, m, theta_m):
+        """(Ra/Pr)(i m/s_o) C^I theta_m, the buoyancy term of Eq. psi_int."""
+        ops = self.ops
+        return (ops.Ra / ops.Pr) * (1j * m / ops.ann.s_o) * (ops.C @ theta_m)
 
     @staticmethod
     def _factor(L):
@@ -180,9 +191,16 @@ class IntegrationStepper(ImexScheme):
         rp[:, :4] = 0.0
         rt[:, :2] = 0.0
         ru[:2] = 0.0
+        th = np.stack([self._solve_refined(*lt[m], rt[m]) for m in range(self.g.M)])
+        if self.buoy_implicit:
+            # (Mass - g Lin) y = r with Lin_psi = B Psi + buoyancy(theta): the
+            # temperature is solved first, its buoyancy moves to the right-hand side
+            gdt = gamma * self.dt
+            for m in range(1, self.g.M):
+                rp[m] = rp[m] + gdt * self._buoyancy(m, th[m])
+            rp[:, :4] = 0.0
         psi = np.zeros_like(rp)
         for m in range(1, self.g.M):
             psi[m] = self._solve_refined(*lp[m], rp[m])
-        th = np.stack([self._solve_refined(*lt[m], rt[m]) for m in range(self.g.M)])
         u = self._solve_refined(*lu_, ru)
         return psi, th, u

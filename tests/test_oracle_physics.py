@@ -261,3 +261,57 @@ def test_tau_solve_is_accurate_against_extended_precision_refinement():
             r = (f.astype(np.clongdouble) - Ll @ xr.astype(np.clongdouble)).astype(complex)
             xr = xr + st._solve(st._factor(L), r)
         assert np.linalg.norm(x - xr) <= 1e-13 * np.linalg.norm(xr)
+
+
+# --------------------------------------------------- implicit buoyancy ----
+def test_implicit_buoyancy_solve_equals_the_coupled_dense_solve():
+    """Section 4: with the buoyancy term implicit, the stage system of mode m is
+    [A - g B, -g (Ra/Pr)(i m/s_o) C^I; 0, D - g F/Pr] (tau rows on top of each
+    block) and the temperature is advanced first.  The stepper's block-ordered
+    solve equals a dense solve of the coupled 2 N_c system."""
+    n_r, n_phi, gamma, dt = 33, 24, 0.5, 3e-4
+    st = IntegrationStepper(n_r, n_phi, 1e-3, 2e5, 0.7, 0.35, "CNAB2", dt, buoy_implicit=True)
+    ops, nc, M = st.ops, st.n_c, st.g.M
+    rng = np.random.default_rng(4)
+    rp = (rng.standard_normal((M, nc)) + 1j * rng.standard_normal((M, nc))) / (1 + np.arange(nc)) ** 2
+    rt = (rng.standard_normal((M, nc)) + 1j * rng.standard_normal((M, nc))) / (1 + np.arange(nc)) ** 2
+    ru = rng.standard_normal(nc) / (1 + np.arange(nc)) ** 2
+    psi, th, u = st.solve(gamma, (rp, rt, ru))
+    gdt = gamma * dt
+    for m in (1, 3, M - 1):
+        L = np.zeros((2 * nc, 2 * nc), complex)
+        L[:nc, :nc] = ops.lhs_psi(m, gdt)
+        cpl = -gdt * (ops.Ra / ops.Pr) * (1j * m / ops.ann.s_o) * ops.C
+        cpl[:4] = 0.0
+        L[:nc, nc:] = cpl
+        L[nc:, nc:] = ops.lhs_theta(m, gdt)
+        b = np.concatenate([rp[m], rt[m]])
+        b[:4] = 0.0
+        b[nc:nc + 2] = 0.0
+        x = np.linalg.solve(L, b)
+        ref = np.concatenate([psi[m], th[m]])
+        assert np.linalg.norm(ref - x) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_implicit_buoyancy_run_keeps_second_order_at_the_eigenvalue():
+    """The eigenmode run of test_dns_from_eigenmode_grows_at_the_eigenvalue with
+    the buoyancy implicit: CNAB2 still converges to the eigenvalue at second order."""
+    n_r, n_phi, m = 65, 48, 12
+    nc = (2 * (n_r - 1)) // 3
+    lam, p, th = leading_mode(3e-6, 0.025, 1e7, 0.35, m, nc, n_r=n_r, guess=615.0 - 9537.0j)
+    errs = []
+    for dt, K1, K2 in ((4e-7, 10, 110), (2e-7, 20, 220)):
+        st = IntegrationStepper(n_r, n_phi, 3e-6, 1e7, 0.025, 0.35, "CNAB2", dt, buoy_implicit=True)
+        P = np.zeros((n_phi // 3 + 1, nc), complex)
+        T = np.zeros_like(P)
+        a = 1e-8 / np.max(np.abs(th))
+        P[m], T[m] = a * p, a * th
+        st.set_state(P, T, np.zeros(nc))
+        for k in range(K2):
+            st.step()
+            if k + 1 == K1:
+                z1 = np.vdot(T[m], st.y[1][m]) / np.vdot(T[m], T[m])
+        z2 = np.vdot(T[m], st.y[1][m]) / np.vdot(T[m], T[m])
+        errs.append(abs(np.log(z2 / z1) / ((K2 - K1) * dt) - lam) / abs(lam))
+    assert errs[1] < 1e-5
+    assert 3.0 < errs[0] / errs[1] < 5.0
