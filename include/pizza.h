@@ -105,6 +105,12 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            omega_0 of Eq. uphicoll.  Set before stepping; changing it discards
  *            the factored operators.  While a tape is recorded: PIZZA_ESTATE;
  *            pizza_tape_begin with pumping on: PIZZA_EUNSUPPORTED;
+ *   "buoy_implicit" 0 = buoyancy explicit (default), 1 = the buoyancy term
+ *            (Ra/Pr)(i m/s_o) C^I theta of Eq. psi_int in the implicit operator
+ *            (Section 4): each stage solves the temperature first and carries its
+ *            buoyancy into the streamfunction system.  Integration formulation
+ *            only (PIZZA_EUNSUPPORTED with collocation); the adjoint refuses it.
+ *            Set before stepping;
  *   "radial_batch" radial transforms batched per shared-memory pass in the
  *            per-mode explicit kernels: 1, 2 or 4, 0 = the default rule (up to
  *            n_r = 513: 4 in FP64, 2 in mixed precision; else 1); "phi_threads" threads of the per-radius azimuthal

@@ -274,7 +274,7 @@ class Solver:
     (integration) or the exact term, implicit (collocation)."""
 
     def __init__(self, n_r, n_phi, E, Ra, Pr, radius_ratio, scheme, dt=None, radial="integration",
-                 pumping_eps=None):
+                 pumping_eps=None, buoy_implicit=False):
         self.ctx = pizza_init(n_r, n_phi, E, Ra, Pr, radius_ratio, scheme)
         if radial not in ("integration", "collocation"):
             raise ValueError(radial)
@@ -282,6 +282,8 @@ class Solver:
             pizza_set_option(self.ctx, "radial", 0)
         if pumping_eps is not None:
             pizza_set_option(self.ctx, "pumping_eps", pumping_eps)
+        if buoy_implicit:
+            pizza_set_option(self.ctx, "buoy_implicit", 1)
         self.n_r, self.n_phi, self.n_m, self.n_c = pizza_get_sizes(self.ctx)
         self.M = self.n_m + 1
         if dt is not None:

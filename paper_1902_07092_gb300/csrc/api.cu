@@ -1244,6 +1244,8 @@ int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
         if (coll == ctx->coll) return PIZZA_OK;
         if (coll && ctx->P.fp32)
             return fail(ctx, PIZZA_EUNSUPPORTED, "mixed precision is implemented for the integration formulation");
+        if (coll && ctx->P.buoy_imp)
+            return fail(ctx, PIZZA_EUNSUPPORTED, "implicit buoyancy is implemented for the integration formulation");
         if (coll && ctx->n_r > PIZZA_COLL_MAX_NR)
             return fail(ctx, PIZZA_EUNSUPPORTED, "collocation is limited to n_r <= %d", PIZZA_COLL_MAX_NR);
         cudaStreamSynchronize(ctx->stream);
@@ -1260,6 +1262,16 @@ int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
         if (!rc) rc = set_pumping_tables(ctx);
         if (rc) return rc;
         reset_slots(ctx);
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "buoy_implicit") == 0) {
+        if (value != 0.0 && value != 1.0) return fail(ctx, PIZZA_EINVAL, "buoy_implicit must be 0 or 1");
+        if (value == 1.0 && ctx->coll)
+            return fail(ctx, PIZZA_EUNSUPPORTED, "implicit buoyancy is implemented for the integration formulation");
+        if (ctx->adj.taping) return fail(ctx, PIZZA_ESTATE, "the buoyancy split cannot change while a tape is recorded");
+        cudaStreamSynchronize(ctx->stream);
+        ctx->P.buoy_imp = (value == 1.0) ? 1 : 0;
+        ctx->aux_valid = false;
         return PIZZA_OK;
     }
     if (std::strcmp(key, "radial_batch") == 0) {
@@ -1517,6 +1529,7 @@ int pizza_tape_begin(pizza_ctx* ctx, int checkpoint_every) {
     if (checkpoint_every < 1) return fail(ctx, PIZZA_EINVAL, "checkpoint_every must be >= 1");
     if (ctx->n_done != 0) return fail(ctx, PIZZA_ESTATE, "the tape starts right after pizza_set_state");
     if (ctx->P.pump) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written without Ekman pumping");
+    if (ctx->P.buoy_imp) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written for explicit buoyancy");
     int rc = ensure_factors(ctx);
     if (rc) return rc;
     rc = ensure_adjoint(ctx);
@@ -1603,6 +1616,7 @@ int pizza_explicit_adjoint(pizza_ctx* ctx, const double* e_psi_bar, const double
                            double* psi_bar, double* theta_bar, double* uphi0_bar) {
     if (!ctx) return PIZZA_EINVAL;
     if (ctx->P.pump) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written without Ekman pumping");
+    if (ctx->P.buoy_imp) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written for explicit buoyancy");
     int rc = ensure_factors(ctx);
     if (rc) return rc;
     rc = ensure_adjoint(ctx);

@@ -429,9 +429,10 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
     const double2* ps_m = y.psi + (size_t)m * nc;
     for (int k = tid; k < nc; k += nth) {
         double2 ep = make_double2(0.0, 0.0), et = make_double2(0.0, 0.0);
-        if (k >= 4 && m > 0)
-            ep = cadd(band_row<8>(P.ops.band[OP_C], cc1, k, nc),
-                      cmul_i(band_row<8>(P.ops.band[OP_C], th_m, k, nc), bfac));
+        if (k >= 4 && m > 0) {
+            ep = band_row<8>(P.ops.band[OP_C], cc1, k, nc);
+            if (!P.buoy_imp) ep = cadd(ep, cmul_i(band_row<8>(P.ops.band[OP_C], th_m, k, nc), bfac));
+        }
         if (k >= 2) {
             const double2 dn = band_row<4>(P.ops.band[OP_D], cc2, k, nc);
             if (m > 0) {

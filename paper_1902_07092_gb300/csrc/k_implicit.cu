@@ -385,6 +385,8 @@ __device__ void apply_row(const StepParams& P, int m, int k, const double2* xp, 
             const double ce = 2.0 * dm / P.E;
             ip.x = b0.x + mu * (b2.x + mu * b4.x) - ce * c.y;
             ip.y = b0.y + mu * (b2.y + mu * b4.y) + ce * c.x;
+            if (P.buoy_imp)  // (Ra/Pr)(i m/s_o) C^I theta
+                ip = cadd(ip, cmul_i(band_row_c<8>(P.ops.band[OP_C], xt, k, nc), P.Ra / P.Pr * dm / P.s_o));
         }
     }
     if (k >= 2) {
@@ -627,6 +629,59 @@ __device__ void refine_temperature(const StepParams& P, const DevFactors& F, Sol
     __syncthreads();
 }
 
+// Temperature refinement for large N_c after its first solve: ir_t corrections
+// of FP32 solves from FP64 residuals (zonal flow: one FP64 refinement step), or
+// the FP64 refinement step of both.  Leaves the streamfunction arrays alone
+// except, in the CTA of m = 0 (no streamfunction), as zonal-flow scratch.
+template <int MB>
+__device__ void temperature_corrections(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u) {
+    const int nc = P.nc, nt = nc - 2, nbt = (nt + 3) / 4;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
+    if (F.ir_t) {
+        // x += S32^{-1}(f - L x), ir_t times, residuals in FP64 (MB == 1)
+        for (int it = 0; it < F.ir_t; ++it) {
+            for (int k = 2 + tid; k < nc; k += nth) {
+                const double* row = F.tBand + ((size_t)m0 * nt + (k - 2)) * 9;
+                double2 acc = s.tf[0][k];
+#pragma unroll
+                for (int d = 0; d < 9; ++d) {
+                    const int n = k - 4 + d;
+                    if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), s.tx[0][n]);
+                }
+                s.tr[k] = to_f2(acc);
+            }
+            if (warp == 0) {  // tau rows: r = 0 - tau x
+                double2 t0 = make_double2(0.0, 0.0), t1 = t0;
+                for (int j = lane; j < nc; j += 32) {
+                    const double2 xv = s.tx[0][j];
+                    const double b0 = __ldg(&P.ops.tau_dir[j]), b1 = __ldg(&P.ops.tau_dir[nc + j]);
+                    t0.x = fma(b0, xv.x, t0.x);
+                    t0.y = fma(b0, xv.y, t0.y);
+                    t1.x = fma(b1, xv.x, t1.x);
+                    t1.y = fma(b1, xv.y, t1.y);
+                }
+                t0 = warp_sum(t0);
+                t1 = warp_sum(t1);
+                if (lane < 2) s.tr[lane] = to_f2(lane ? make_double2(-t1.x, -t1.y) : make_double2(-t0.x, -t0.y));
+            }
+            __syncthreads();
+            if (warp == 2 || warp == 3)
+                pair_block_solve<4>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 48, true, warp - 2, 2);
+            __syncthreads();
+            if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
+            __syncthreads();
+            schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
+            __syncthreads();
+            for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
+            __syncthreads();
+        }
+        if (has_u) refine_temperature<MB>(P, F, s, m0, true, false);  // zonal flow only, FP64
+    } else if (F.refine_t) {
+        refine_temperature<MB>(P, F, s, m0, has_u, true);
+    }
+
+}
+
 template <int MB>
 __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, DevFactors F, VecSet y_out,
                                                       VecSet mass_out, VecSet imp_out, int want_mass,
@@ -663,73 +718,101 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     }
     __syncthreads();
 
-    // 2. banded solves by warp pairs meeting at their middle blocks: warps 0-1
-    //    streamfunction, 2-3 temperature, 4-5 zonal flow (m = 0 only; its chain
-    //    scratch is the streamfunction correction array, unused until step 5)
-    if (warp < 2) {
-        const bool act = m0 > 0;
-        pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, np, F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act,
-                            warp, 1);
-    } else if (warp < 4) {
-        if (F.ir_t)
-            pair_block_solve<4>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 48, true, warp - 2, 2);
-        else
-            pair_block_solve<4>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true, warp - 2,
-                                2);
-    } else if (warp < 6 && has_u) {
-        pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4, 3);
-    }
-    __syncthreads();
-
-    // 3. Schur steps: warp 0 streamfunction, 2 temperature, 4 zonal flow
-    if (warp == 0) {
-        if (m0 > 0) warp_schur<4>(s.px[0], nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
-    } else if (warp == 2) {
-        if (F.ir_t)
-            warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
-        else
-            warp_schur<2>(s.tx[0], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
-    } else if (warp == 4 && has_u) {
-        double t0 = 0.0, t1 = 0.0;
-        for (int j = lane; j < nt; j += 32) {
-            t0 = fma(__ldg(&P.ops.tau_dir_B[j]), s.ux[2 + j], t0);
-            t1 = fma(__ldg(&P.ops.tau_dir_B[nt + j]), s.ux[2 + j], t1);
+    // 2.-4. banded solves, Schur steps and Y updates.  With explicit buoyancy the
+    //    streamfunction and temperature systems are independent and run together;
+    //    with implicit buoyancy (Section 4) the temperature (and zonal flow) goes
+    //    first, then g (Ra/Pr)(i m/s_o) C^I theta_new joins the streamfunction rows.
+    const int npass = P.buoy_imp ? 2 : 1;
+    for (int pass = 0; pass < npass; ++pass) {
+        const bool do_p = !P.buoy_imp || pass == 1;
+        const bool do_t = !P.buoy_imp || pass == 0;
+        if (P.buoy_imp && pass == 1) {
+            if (m0 > 0) {
+                const double cb = F.gdt * P.Ra / P.Pr * (double)m0 / P.s_o;
+                for (int k = 4 + tid; k < nc; k += nth)
+                    s.pf[0][k] = cadd(s.pf[0][k], cmul_i(band_row_c<8>(P.ops.band[OP_C], s.tx[0], k, nc), cb));
+            }
+            __syncthreads();
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-            t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-        }
-        if (lane < 2) s.ux[lane] = -(F.uSinv[lane * 2] * t0 + F.uSinv[lane * 2 + 1] * t1);
-        __syncwarp();
-    }
-    __syncthreads();
-    // 4. y2 -= Y y1 (threads split evenly over the systems of the CTA)
-    {
-        const int per = nth / (2 * MB);
-        const int sys = tid / per, t0 = sys * per;
-        if (sys < MB) {
-            const int m = m0 + sys;
-            if (m < M && m > 0) schur_update<4>(s.px[sys], nc, F.pY + (size_t)m * np * 4, t0, per);
-        } else if (sys < 2 * MB) {
-            const int mi = sys - MB, m = m0 + mi;
-            if (m < M) {
+        // 2. banded solves by warp pairs meeting at their middle blocks: warps 0-1
+        //    streamfunction, 2-3 temperature, 4-5 zonal flow (m = 0 only; its chain
+        //    scratch is the streamfunction correction array, unused until step 5)
+        if (warp < 2) {
+            if (do_p) {
+                const bool act = m0 > 0;
+                pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, np,
+                                    F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
+            }
+        } else if (warp < 4) {
+            if (do_t) {
                 if (F.ir_t)
-                    schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, t0, per);
+                    pair_block_solve<4>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 48, true, warp - 2,
+                                        2);
                 else
-                    schur_update<2>(s.tx[mi], nc, F.tY + (size_t)m * nt * 2, t0, per);
+                    pair_block_solve<4>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true,
+                                        warp - 2, 2);
+            }
+        } else if (warp < 6 && has_u) {
+            if (do_t)
+                pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4,
+                                    3);
+        }
+        __syncthreads();
+
+        // 3. Schur steps: warp 0 streamfunction, 2 temperature, 4 zonal flow
+        if (warp == 0) {
+            if (do_p && m0 > 0) warp_schur<4>(s.px[0], nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
+        } else if (warp == 2) {
+            if (do_t) {
+                if (F.ir_t)
+                    warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
+                else
+                    warp_schur<2>(s.tx[0], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
+            }
+        } else if (warp == 4 && has_u && do_t) {
+            double t0 = 0.0, t1 = 0.0;
+            for (int j = lane; j < nt; j += 32) {
+                t0 = fma(__ldg(&P.ops.tau_dir_B[j]), s.ux[2 + j], t0);
+                t1 = fma(__ldg(&P.ops.tau_dir_B[nt + j]), s.ux[2 + j], t1);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+                t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+            }
+            if (lane < 2) s.ux[lane] = -(F.uSinv[lane * 2] * t0 + F.uSinv[lane * 2 + 1] * t1);
+            __syncwarp();
+        }
+        __syncthreads();
+        // 4. y2 -= Y y1 (threads split evenly over the systems of the CTA)
+        {
+            const int per = nth / (2 * MB);
+            const int sys = tid / per, t0 = sys * per;
+            if (sys < MB) {
+                const int m = m0 + sys;
+                if (do_p && m < M && m > 0) schur_update<4>(s.px[sys], nc, F.pY + (size_t)m * np * 4, t0, per);
+            } else if (sys < 2 * MB) {
+                const int mi = sys - MB, m = m0 + mi;
+                if (do_t && m < M) {
+                    if (F.ir_t)
+                        schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, t0, per);
+                    else
+                        schur_update<2>(s.tx[mi], nc, F.tY + (size_t)m * nt * 2, t0, per);
+                }
+            }
+            if (has_u && do_t) {
+                __syncthreads();
+                const double u0 = s.ux[0], u1 = s.ux[1];
+                for (int j = tid; j < nt; j += nth)
+                    s.ux[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
             }
         }
-        if (has_u) {
-            __syncthreads();
-            const double u0 = s.ux[0], u1 = s.ux[1];
-            for (int j = tid; j < nt; j += nth) s.ux[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
-        }
-    }
-    __syncthreads();
-    if (F.ir_t) {  // the FP32 temperature solve becomes the FP64 iterate
-        for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
         __syncthreads();
+        if (F.ir_t && do_t) {  // the FP32 temperature solve becomes the FP64 iterate
+            for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
+            __syncthreads();
+        }
+        if (P.buoy_imp && pass == 0) temperature_corrections<MB>(P, F, s, m0, has_u);
     }
 
     // 5. one refinement step of the streamfunction solve: r = f - L x (a second
@@ -791,48 +874,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     }
     __syncthreads();
     }
-    if (F.ir_t) {
-        // temperature: x += S32^{-1}(f - L x), ir_t times, residuals in FP64 (MB == 1)
-        for (int it = 0; it < F.ir_t; ++it) {
-            for (int k = 2 + tid; k < nc; k += nth) {
-                const double* row = F.tBand + ((size_t)m0 * nt + (k - 2)) * 9;
-                double2 acc = s.tf[0][k];
-#pragma unroll
-                for (int d = 0; d < 9; ++d) {
-                    const int n = k - 4 + d;
-                    if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), s.tx[0][n]);
-                }
-                s.tr[k] = to_f2(acc);
-            }
-            if (warp == 0) {  // tau rows: r = 0 - tau x
-                double2 t0 = make_double2(0.0, 0.0), t1 = t0;
-                for (int j = lane; j < nc; j += 32) {
-                    const double2 xv = s.tx[0][j];
-                    const double b0 = __ldg(&P.ops.tau_dir[j]), b1 = __ldg(&P.ops.tau_dir[nc + j]);
-                    t0.x = fma(b0, xv.x, t0.x);
-                    t0.y = fma(b0, xv.y, t0.y);
-                    t1.x = fma(b1, xv.x, t1.x);
-                    t1.y = fma(b1, xv.y, t1.y);
-                }
-                t0 = warp_sum(t0);
-                t1 = warp_sum(t1);
-                if (lane < 2) s.tr[lane] = to_f2(lane ? make_double2(-t1.x, -t1.y) : make_double2(-t0.x, -t0.y));
-            }
-            __syncthreads();
-            if (warp == 2 || warp == 3)
-                pair_block_solve<4>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 48, true, warp - 2, 2);
-            __syncthreads();
-            if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
-            __syncthreads();
-            schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
-            __syncthreads();
-            for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
-            __syncthreads();
-        }
-        if (has_u) refine_temperature<MB>(P, F, s, m0, true, false);  // zonal flow only, FP64
-    } else if (F.refine_t) {
-        refine_temperature<MB>(P, F, s, m0, has_u, true);
-    }
+    if (!P.buoy_imp) temperature_corrections<MB>(P, F, s, m0, has_u);
 
     // 6. store, then mass / implicit operators for later stages
     for (int idx = tid; idx < MB * nc; idx += nth) {

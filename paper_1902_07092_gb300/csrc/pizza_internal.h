@@ -107,6 +107,9 @@ struct StepParams {
     //     5 s_o beta/(2 h s) (0 at s_o); pump_cr unused
     int pump;
     const double *pump_ups, *pump_cr, *pump_ci;
+    // implicit buoyancy (option "buoy_implicit", Section 4): 1 when the buoyancy
+    // term is part of the implicit operator of the streamfunction equation
+    int buoy_imp;
     double2* pump_F;
 };
 
