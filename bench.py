@@ -92,7 +92,8 @@ def algorithmic_flops(n_r, n_phi, scheme, radial="integration"):
 # DRAM bytes (read + write) per launch of the roofline kernel from one ncu capture
 # of this workload (summaries under profiles/); null for kernels not captured.
 NCU_TRAFFIC = {
-    ("sparse_n257_p768", "solve"): (44.32e6 + 0.17e6, "profiles/imex_step_kernels_n257_p768.md"),
+    ("sparse_n257_p768", "solve"): (44.34e6 + 0.27e6, "profiles/imex_step_kernels_n257_p768.md"),
+    ("large_n2049_p6144", "solve"): (4145.9e6 + 228.4e6, "profiles/solve_kernel_n2049_p6144.md"),
     ("coll_n257_p768", "solve"): (726.5e6 + 6.8e6, "profiles/collocation_step_kernels_n257_p768.md"),
 }
 
