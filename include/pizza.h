@@ -61,7 +61,8 @@ enum pizza_status {
     PIZZA_EINVAL = -1,      /* invalid argument or size                          */
     PIZZA_ENOMEM = -2,      /* device or host allocation failed                  */
     PIZZA_ECUDA = -3,       /* a CUDA runtime call failed (message has details)  */
-    PIZZA_ENONFINITE = -4,  /* a NaN/Inf was found in the state                  */
+    PIZZA_ENONFINITE = -4,  /* a NaN/Inf in the state (pizza_diagnostics; with
+                               option "check_finite" pizza_synchronize)       */
     PIZZA_ECFL = -5,        /* reserved: Courant criterion exceeded              */
     PIZZA_ETIMEOUT = -6,    /* reserved: a bounded device wait gave up           */
     PIZZA_ESTATE = -7,      /* call out of order (e.g. step before dt is set)    */
@@ -111,6 +112,10 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            buoyancy into the streamfunction system.  Integration formulation
  *            only (PIZZA_EUNSUPPORTED with collocation); the adjoint refuses it.
  *            Set before stepping;
+ *   "check_finite" 1 = after every step a small kernel scans the state for NaN
+ *            or infinite values and sets a device flag; pizza_synchronize then
+ *            returns PIZZA_ENONFINITE (cleared by pizza_set_state).  0 (default) =
+ *            no scan; pizza_diagnostics reports a non-finite state either way;
  *   "radial_batch" radial transforms batched per shared-memory pass in the
  *            per-mode explicit kernels: 1, 2 or 4, 0 = the default rule (up to
  *            n_r = 513: 4 in FP64, 2 in mixed precision; else 1); "phi_threads" threads of the per-radius azimuthal

@@ -100,6 +100,9 @@ struct pizza_ctx {
     double* grid_out = nullptr;        // pizza_get_grid staging, 4 x n_r x n_phi
     // Ekman pumping (option "pumping_eps"; 0 = off)
     double pump_eps = 0.0;
+    // option "check_finite": scan the state for NaN/Inf after every step
+    int check_finite = 0;
+    int* finite_flag = nullptr;  // device flag set by the scan, read by pizza_synchronize
     double* pump_tab = nullptr;        // 3 x n_r device tables (StepParams pump_*)
     double2* pump_buf = nullptr;       // [M][n_r] working buffer of the integration path
     // discrete adjoint (pizza_tape_begin / pizza_adjoint_step)
@@ -1264,6 +1267,17 @@ int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
         reset_slots(ctx);
         return PIZZA_OK;
     }
+    if (std::strcmp(key, "check_finite") == 0) {
+        if (value != 0.0 && value != 1.0) return fail(ctx, PIZZA_EINVAL, "check_finite must be 0 or 1");
+        cudaStreamSynchronize(ctx->stream);
+        if (value == 1.0 && !ctx->finite_flag) {
+            ctx->finite_flag = dalloc<int>(ctx, 1, ctx->allocs);
+            if (!ctx->finite_flag) return fail(ctx, PIZZA_ENOMEM, "device allocation failed");
+            CK(cudaMemset(ctx->finite_flag, 0, sizeof(int)));
+        }
+        ctx->check_finite = (value == 1.0) ? 1 : 0;
+        return PIZZA_OK;
+    }
     if (std::strcmp(key, "buoy_implicit") == 0) {
         if (value != 0.0 && value != 1.0) return fail(ctx, PIZZA_EINVAL, "buoy_implicit must be 0 or 1");
         if (value == 1.0 && ctx->coll)
@@ -1324,6 +1338,7 @@ int pizza_set_state(pizza_ctx* ctx, const double* theta_hat, const double* psi_h
     if (!ctx) return PIZZA_EINVAL;
     if (nc_in < 0 || nc_in > ctx->nc) return fail(ctx, PIZZA_EINVAL, "nc_in must be in [0, %d]", ctx->nc);
     reset_slots(ctx);
+    if (ctx->finite_flag) CK(cudaMemsetAsync(ctx->finite_flag, 0, sizeof(int), ctx->stream));
     // collocation: coefficients go to the scratch slot, then to grid values
     VecSet y = ctx->coll ? ctx->vec[15] : ctx->vec[ctx->ys[0]];
     const size_t M = ctx->M, nc = ctx->nc;
@@ -1374,6 +1389,7 @@ int pizza_step(pizza_ctx* ctx, int nsteps) {
             rc = is_multistep(ctx->scheme) ? step_multistep(ctx) : step_dirk(ctx);
         if (rc) return rc;
         ctx->n_done++;
+        if (ctx->check_finite) CK(launch_check_finite(ctx->P, ctx->vec[ctx->ys[0]], ctx->finite_flag, ctx->stream));
         if (ctx->adj.taping) {
             rc = tape_record(ctx);
             if (rc) return rc;
@@ -1498,6 +1514,9 @@ int pizza_diagnostics(pizza_ctx* ctx, pizza_diag* out) {
     out->Ro = out->Re * ctx->E;
     out->cfl_s = cs;
     out->cfl_phi = cp;
+    bool finite = std::isfinite(ek) && std::isfinite(z) && std::isfinite(dth);
+    for (double v : rm) finite = finite && std::isfinite(v);
+    if (!finite) return fail(ctx, PIZZA_ENONFINITE, "the state holds NaN or infinite values");
     return PIZZA_OK;
 }
 
@@ -1762,6 +1781,9 @@ int step_one(pizza_ctx* ctx) {
     else
         rc = is_multistep(ctx->scheme) ? step_multistep(ctx) : step_dirk(ctx);
     if (!rc) ctx->n_done++;
+    if (!rc && ctx->check_finite &&
+        launch_check_finite(ctx->P, ctx->vec[ctx->ys[0]], ctx->finite_flag, ctx->stream) != cudaSuccess)
+        rc = PIZZA_ECUDA;
     return rc;
 }
 }  // namespace
@@ -1890,6 +1912,11 @@ int pizza_synchronize(pizza_ctx* ctx) {
     if (!ctx) return PIZZA_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaGetLastError());
+    if (ctx->finite_flag) {
+        int f = 0;
+        CK(cudaMemcpy(&f, ctx->finite_flag, sizeof(int), cudaMemcpyDeviceToHost));
+        if (f) return fail(ctx, PIZZA_ENONFINITE, "a NaN or infinite value appeared in the state");
+    }
     return PIZZA_OK;
 }
 

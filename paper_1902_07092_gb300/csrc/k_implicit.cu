@@ -905,6 +905,22 @@ __global__ void __launch_bounds__(NTHREADS_S) k_apply(StepParams P, VecSet y, Ve
     for (int k = threadIdx.x; k < nc; k += blockDim.x) apply_row(P, m, k, xp, xt, xu, mass_out, imp_out, want_mass, want_imp);
 }
 
+// Sets *flag when any entry of the state (Psi, theta, u_bar and, for
+// collocation, omega) is NaN or infinite.
+__global__ void k_check_finite(VecSet y, size_t n2, int nu, int* __restrict__ flag) {
+    bool bad = false;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 a = y.psi[i], b = y.th[i];
+        bad |= !(isfinite(a.x) && isfinite(a.y) && isfinite(b.x) && isfinite(b.y));
+        if (y.w) {
+            const double2 c = y.w[i];
+            bad |= !(isfinite(c.x) && isfinite(c.y));
+        }
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) bad |= !isfinite(y.u[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 size_t smem_solve_mb(const StepParams& P, int MB) { return sizeof(double) * solve_smem_doubles(P.nc, MB); }
 
 }  // namespace
@@ -918,6 +934,11 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
     if (err != cudaSuccess) return err;
     k_solve<1><<<P.M, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
                                             want_imp ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const StepParams& P, VecSet y, int* flag, cudaStream_t st) {
+    k_check_finite<<<152, 256, 0, st>>>(y, (size_t)P.M * P.nc, P.nc, flag);
     return cudaGetLastError();
 }
 

@@ -131,6 +131,7 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st);
 cudaError_t launch_apply(const StepParams& P, VecSet y, VecSet mass_out, VecSet imp_out, bool want_mass,
                          bool want_imp, cudaStream_t st);
+cudaError_t launch_check_finite(const StepParams& P, VecSet y, int* flag, cudaStream_t st);
 cudaError_t launch_coll_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st);
 cudaError_t launch_coll_grid_rows(const StepParams& P, const double2* G1, const double2* G2, VecSet e,
                                   cudaStream_t st);
