@@ -314,7 +314,6 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
     // FP32 solves reach the accuracy of the FP64 solve there (1e-13 at N_c = 1365,
     // measured on the tau systems), with the chains on the FP32 pipe; the
     // zonal-flow system (one mode) keeps its FP64 refinement.
-    F.refine_t = (nc > 600) ? 1 : 0;
     F.ir_t = (nc > 600) ? 2 : 0;
     if (F.ir_t) {
         const std::vector<float> tK32(htK.begin(), htK.end()), tY32(htY.begin(), htY.end()),

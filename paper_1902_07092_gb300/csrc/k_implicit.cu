@@ -522,73 +522,39 @@ __device__ SolveSmem carve(double2* base, int nc) {
     return s;
 }
 
-// One refinement step of the temperature (and zonal-flow) solves, used for large
-// N_c: r = f - L x over the assembled rows and the tau rows, solved with the
-// same factors, x += correction.  The residual replaces the right-hand side and
-// the correction goes to the streamfunction's correction array (no longer needed).
-template <int MB>
-__device__ void refine_temperature(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u,
-                                   bool theta) {
-    const int nc = P.nc, M = P.M, nt = nc - 2, nbt = (nt + 3) / 4;
+// One FP64 refinement step of the zonal-flow solve (the CTA of m = 0, large N_c):
+// r = f - L u over the assembled rows and the tau rows, solved with the same
+// factors, u += correction.  The residual replaces the right-hand side; the
+// correction and its chain scratch use streamfunction arrays, which mode 0 leaves
+// unused.
+__device__ void refine_zonal_flow(const StepParams& P, const DevFactors& F, SolveSmem& s) {
+    const int nc = P.nc, nt = nc - 2;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
-    for (int idx = tid; theta && idx < MB * nc; idx += nth) {
-        const int mi = idx / nc, k = idx - mi * nc, m = m0 + mi;
-        if (m >= M || k < 2) continue;
-        const double* row = F.tBand + ((size_t)m * nt + (k - 2)) * 9;
-        const double2* x = s.tx[mi];
-        double2 acc = s.tf[mi][k];
-#pragma unroll
+    for (int k = 2 + tid; k < nc; k += nth) {
+        const double* row = F.uBand + (size_t)(k - 2) * 9;
+        double acc = s.uf[k];
         for (int d = 0; d < 9; ++d) {
             const int n = k - 4 + d;
-            if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), x[n]);
+            if (n >= 0 && n < nc) acc = fma(-__ldg(&row[d]), s.ux[n], acc);
         }
-        s.tf[mi][k] = acc;
+        s.uf[k] = acc;
     }
-    if (has_u)
-        for (int k = 2 + tid; k < nc; k += nth) {
-            const double* row = F.uBand + (size_t)(k - 2) * 9;
-            double acc = s.uf[k];
-            for (int d = 0; d < 9; ++d) {
-                const int n = k - 4 + d;
-                if (n >= 0 && n < nc) acc = fma(-__ldg(&row[d]), s.ux[n], acc);
-            }
-            s.uf[k] = acc;
+    if (warp == 0) {  // tau rows: r = 0 - tau u
+        double t0 = 0.0, t1 = 0.0;
+        for (int j = lane; j < nc; j += 32) {
+            t0 = fma(__ldg(&P.ops.tau_dir[j]), s.ux[j], t0);
+            t1 = fma(__ldg(&P.ops.tau_dir[nc + j]), s.ux[j], t1);
         }
-    if (warp < MB + (has_u ? 1 : 0)) {  // tau rows
-        const bool is_u = (warp == MB);
-        const int m = m0 + warp;
-        if (is_u || (theta && m < M)) {
-            double2 t0 = make_double2(0.0, 0.0), t1 = make_double2(0.0, 0.0);
-            for (int j = lane; j < nc; j += 32) {
-                const double2 xv = is_u ? make_double2(s.ux[j], 0.0) : s.tx[warp][j];
-                const double b0 = __ldg(&P.ops.tau_dir[j]), b1 = __ldg(&P.ops.tau_dir[nc + j]);
-                t0.x = fma(b0, xv.x, t0.x);
-                t0.y = fma(b0, xv.y, t0.y);
-                t1.x = fma(b1, xv.x, t1.x);
-                t1.y = fma(b1, xv.y, t1.y);
-            }
-            t0 = warp_sum(t0);
-            t1 = warp_sum(t1);
-            if (lane < 2) {
-                const double2 t = lane ? t1 : t0;
-                if (is_u)
-                    s.uf[lane] = -t.x;
-                else
-                    s.tf[warp][lane] = make_double2(-t.x, -t.y);
-            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+            t1 += __shfl_xor_sync(0xffffffffu, t1, o);
         }
+        if (lane < 2) s.uf[lane] = -(lane ? t1 : t0);
     }
     __syncthreads();
-    double2* dt_[2] = {s.pd[0], s.pd[MB > 1 ? 1 : 0]};
-    // after the streamfunction solves: zonal-flow correction in pw, its chain scratch in pf
     double* du = reinterpret_cast<double*>(s.pw[0]);
-    if (warp == 2 || warp == 3) {
-        if (theta) {
-            pair_block_solve<4>(s.tf[0] + 2, s.tw[0], dt_[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true, warp - 2,
-                                2);
-            if (warp == 2) warp_schur<2>(dt_[0], s.tf[0], nc, P.ops.tau_dir_B, F.tSinv + (size_t)m0 * 4);
-        }
-    } else if ((warp == 4 || warp == 5) && has_u) {
+    if (warp == 4 || warp == 5) {
         pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pf[0]), du + 2, nt, F.uBlk, true, warp - 4, 3);
         if (warp == 4) {
             double t0 = 0.0, t1 = 0.0;
@@ -609,30 +575,14 @@ __device__ void refine_temperature(const StepParams& P, const DevFactors& F, Sol
     }
     __syncthreads();
     {
-        const int per = nth / MB;
-        const int sys = tid / per, t0 = sys * per;
-        const int m = m0 + sys;
-        if (theta && sys < MB && m < M) schur_update<2>(dt_[sys], nc, F.tY + (size_t)m * nt * 2, t0, per);
-        if (has_u) {
-            __syncthreads();
-            const double u0 = du[0], u1 = du[1];
-            for (int j = tid; j < nt; j += nth) du[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
-        }
+        const double u0 = du[0], u1 = du[1];
+        for (int j = tid; j < nt; j += nth) du[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
     }
     __syncthreads();
-    for (int idx = tid; idx < MB * nc; idx += nth) {
-        const int mi = idx / nc, n = idx - mi * nc, m = m0 + mi;
-        if (m >= M) continue;
-        if (theta) s.tx[mi][n] = cadd(s.tx[mi][n], dt_[mi][n]);
-        if (m == 0) s.ux[n] += du[n];
-    }
+    for (int n = tid; n < nc; n += nth) s.ux[n] += du[n];
     __syncthreads();
 }
 
-// Temperature refinement for large N_c after its first solve: ir_t corrections
-// of FP32 solves from FP64 residuals (zonal flow: one FP64 refinement step), or
-// the FP64 refinement step of both.  Leaves the streamfunction arrays alone
-// except, in the CTA of m = 0 (no streamfunction), as zonal-flow scratch.
 template <int MB>
 __device__ void temperature_corrections(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u) {
     const int nc = P.nc, nt = nc - 2, nbt = (nt + 3) / 4;
@@ -675,9 +625,7 @@ __device__ void temperature_corrections(const StepParams& P, const DevFactors& F
             for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
             __syncthreads();
         }
-        if (has_u) refine_temperature<MB>(P, F, s, m0, true, false);  // zonal flow only, FP64
-    } else if (F.refine_t) {
-        refine_temperature<MB>(P, F, s, m0, has_u, true);
+        if (has_u) refine_zonal_flow(P, F, s);  // FP64
     }
 
 }

@@ -55,7 +55,6 @@ struct DevFactors {
     double *tBlk, *tY, *tSinv, *tBand;
     // zonal flow, real, H = 4: blocks [nb_t][3][16], Y [n_t][2], Sinv [4], band [n_t][9]
     double *uBlk, *uY, *uSinv, *uBand;
-    int refine_t;  // also refine the temperature and zonal-flow solves
     // temperature by mixed-precision iterative refinement (large N_c): ir_t > 0
     // solves with the block factors, Y and S^{-1} rounded to FP32 and corrects
     // ir_t times from FP64 residuals of the assembled system
