@@ -242,7 +242,8 @@ int pizza_autotune(pizza_ctx *ctx, int *nb_r, int *phi_threads);
  * each on its own stream forked from the batch's stream, instantiates the graph
  * once and launches it; a later call with the same nsteps relaunches it when every
  * context is back in the slot state the graph started from (e.g. after
- * pizza_set_state, or a whole number of ring periods later), else recaptures.
+ * pizza_set_state, or a whole number of ring periods later) and no option of any
+ * context has been set since the capture, else recaptures.
  * Factors are built before the capture.  The call returns without waiting; work
  * later queued on a context's stream is ordered after the graph.  The contexts must
  * outlive the batch and must not record an adjoint tape.  Errors go to

@@ -100,6 +100,9 @@ struct pizza_ctx {
     double* grid_out = nullptr;        // pizza_get_grid staging, 4 x n_r x n_phi
     // Ekman pumping (option "pumping_eps"; 0 = off)
     double pump_eps = 0.0;
+    // bumped by every accepted option change: a batch graph captured under other
+    // options (or other factor buffers) is not relaunched
+    unsigned epoch = 0;
     // option "check_finite": scan the state for NaN/Inf after every step
     int check_finite = 0;
     int* finite_flag = nullptr;  // device flag set by the scan, read by pizza_synchronize
@@ -1219,8 +1222,23 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
     return PIZZA_OK;
 }
 
+}  // extern "C"
+namespace {
+int set_option_impl(pizza_ctx* ctx, const char* key, double value);
+}  // namespace
+extern "C" {
+
 int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
     if (!ctx || !key) return fail(ctx, PIZZA_EINVAL, "NULL argument");
+    const int rc = set_option_impl(ctx, key, value);
+    if (rc == PIZZA_OK) ctx->epoch++;
+    return rc;
+}
+
+}  // extern "C"
+
+namespace {
+int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
     if (std::strcmp(key, "dt") == 0) {
         if (!(value > 0.0) || !std::isfinite(value)) return fail(ctx, PIZZA_EINVAL, "dt must be > 0");
         if (ctx->dt_set && value == ctx->dt) return PIZZA_OK;
@@ -1316,6 +1334,9 @@ int pizza_set_option(pizza_ctx* ctx, const char* key, double value) {
     }
     return fail(ctx, PIZZA_EINVAL, "unknown option '%s'", key);
 }
+}  // namespace
+
+extern "C" {
 
 int pizza_set_stream(pizza_ctx* ctx, void* stream) {
     if (!ctx) return PIZZA_EINVAL;
@@ -1730,9 +1751,10 @@ namespace {
 struct Snap {
     int ys[4], es[4], ms[3], is[3], n_done;
     bool aux_valid;
+    unsigned epoch;
     bool same_start(const pizza_ctx* c) const {
         if (std::memcmp(ys, c->ys, sizeof ys) || std::memcmp(es, c->es, sizeof es) || std::memcmp(ms, c->ms, sizeof ms) ||
-            std::memcmp(is, c->is, sizeof is) || aux_valid != c->aux_valid)
+            std::memcmp(is, c->is, sizeof is) || aux_valid != c->aux_valid || epoch != c->epoch)
             return false;
         // the coefficients depend on the step count only during the start-up steps
         return n_done == c->n_done || (n_done >= 3 && c->n_done >= 3);
@@ -1746,6 +1768,7 @@ Snap snap_of(const pizza_ctx* c) {
     std::memcpy(s.is, c->is, sizeof s.is);
     s.n_done = c->n_done;
     s.aux_valid = c->aux_valid;
+    s.epoch = c->epoch;
     return s;
 }
 void restore_snap(pizza_ctx* c, const Snap& s, int n_done) {

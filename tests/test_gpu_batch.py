@@ -99,3 +99,30 @@ def test_explicit_launch_shapes_give_the_same_states():
                     for x, y in zip(got, ref):
                         assert np.array_equal(x, y), (prec, nb, th)
                 a.close()
+
+
+def test_option_change_forces_a_new_graph():
+    """Two launches from the same start state with an option changed in between
+    (precision: no buffer is freed, but the explicit kernels differ): the second
+    launch is captured anew and matches a context stepped alone in the new mode.
+    The same check guards option changes that rebuild the factors (dt)."""
+    from paper_1902_07092_gb300.binding import Batch, pizza_set_option
+    run = RUNS[0]
+    a, st = _make(0, run)
+    b = Batch([a])
+    b.step(3)
+    fp64 = a.get_state()
+    pizza_set_option(a.ctx, "precision", 1)
+    a.set_state(*st)
+    b.step(3)
+    got = a.get_state()
+    b.close()
+    ref, st2 = _make(0, run)
+    pizza_set_option(ref.ctx, "precision", 1)
+    ref.set_state(*st2)
+    ref.step(3)
+    for x, y in zip(got, ref.get_state()):
+        assert np.array_equal(x, y)
+    assert not all(np.array_equal(x, y) for x, y in zip(got, fp64))
+    a.close()
+    ref.close()
