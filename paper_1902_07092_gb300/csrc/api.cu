@@ -1733,6 +1733,7 @@ int pizza_autotune(pizza_ctx* ctx, int* nb_r, int* phi_thr) {
     ctx->event_pool.push_back(b);
     ctx->P.nb_r = pick.first;
     ctx->P.phi_threads = pick.second;
+    ctx->epoch++;  // launch shapes changed: batch graphs are captured anew
     if (nb_r) *nb_r = pick.first;
     if (phi_thr) *phi_thr = pick.second;
     return PIZZA_OK;
