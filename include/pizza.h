@@ -106,12 +106,12 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            omega_0 of Eq. uphicoll.  Set before stepping; changing it discards
  *            the factored operators.  While a tape is recorded: PIZZA_ESTATE;
  *            pizza_tape_begin with pumping on: PIZZA_EUNSUPPORTED;
- *   "buoy_implicit" 0 = buoyancy explicit (default), 1 = the buoyancy term
- *            (Ra/Pr)(i m/s_o) C^I theta of Eq. psi_int in the implicit operator
- *            (Section 4): each stage solves the temperature first and carries its
- *            buoyancy into the streamfunction system.  Integration formulation
- *            only (PIZZA_EUNSUPPORTED with collocation); the adjoint refuses it.
- *            Set before stepping;
+ *   "buoy_implicit" 0 = buoyancy explicit (default), 1 = the buoyancy term in
+ *            the implicit operator (Section 4): (Ra/Pr)(i m/s_o) C^I theta of
+ *            Eq. psi_int, or -(Ra/Pr)(i m/s_o) theta on the vorticity rows of
+ *            Eq. psiomcoll; each stage solves the temperature first and carries
+ *            its buoyancy into the streamfunction (vorticity) system.  The adjoint
+ *            refuses it.  Set before stepping;
  *   "check_finite" 1 = after every step a small kernel scans the state for NaN
  *            or infinite values and sets a device flag; pizza_synchronize then
  *            returns PIZZA_ENONFINITE (cleared by pizza_set_state).  0 (default) =

@@ -126,10 +126,13 @@ class CollocationStepper(ImexScheme):
     """State tuple (omega_hat, psi_hat, theta_hat, u_hat); mass/imp/explicit return
     grid-row tuples (omega rows, constraint rows, theta rows, u rows)."""
 
-    def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt, pumping=False):
+    def __init__(self, n_r, n_phi, E, Ra, Pr, eta, scheme, dt, pumping=False, buoy_implicit=False):
         if scheme not in schemes.SCHEME_ID:
             raise ValueError(scheme)
         self.ops = CollocationOperators(n_r, eta, E, Pr, Ra, pumping)
+        # implicit buoyancy (Section 4): -(Ra/Pr)(i m/s_o) theta joins the implicit
+        # operator of the vorticity rows; the temperature is solved first
+        self.buoy_implicit = bool(buoy_implicit)
         self.n_c = n_r
         if n_phi % 3:
             raise ValueError("N_phi must be a multiple of 3")
@@ -175,6 +178,8 @@ class CollocationStepper(ImexScheme):
         o = self.ops
         iw = np.stack([o.A(m) @ w[m] - o.Bdiag(m) * (o.T @ psi[m]) + o.pump(m)[0] @ w[m] + o.pump(m)[1] @ psi[m]
                        for m in range(self.M)])
+        if self.buoy_implicit:
+            iw = iw + np.stack([self._buoyancy(m, th[m]) for m in range(self.M)])
         iw[0] = 0.0
         it = np.stack([o.Lt(m) @ th[m] for m in range(self.M)])
         return iw, np.zeros_like(psi), it, o.Lu() @ u
@@ -213,6 +218,8 @@ class CollocationStepper(ImexScheme):
             ups[0] = 0.0
             Nu = Nu + 0.5 * o.E * ups * ub * W[:, 0]
         ew = -(o.Ra / o.Pr) * (1j * m / o.ann.s_o) * TH - Nw
+        if self.buoy_implicit:
+            ew = -Nw
         et = -(1j * m / s) * o.tc[:, None] * P - Nt
         eu = -Nu
         ew[:, 0] = 0.0
@@ -222,6 +229,11 @@ class CollocationStepper(ImexScheme):
         eu = eu.real.copy()
         eu[0] = eu[-1] = 0.0
         return ew.T, np.zeros_like(psi), et.T, eu
+
+    def _buoyancy(self, m, theta_m):
+        """-(Ra/Pr)(i m/s_o) theta on the grid rows (vorticity equation, Eq. psiomcoll)."""
+        o = self.ops
+        return -(o.Ra / o.Pr) * (1j * m / o.ann.s_o) * (o.T @ theta_m)
 
     # -- solve --------------------------------------------------------------
     @staticmethod
@@ -249,6 +261,12 @@ class CollocationStepper(ImexScheme):
         lw, lt, lu_ = self.lu(gamma)
         rw, _, rt, ru = (np.array(r) for r in rhs)
         N = self.n_c
+        rt[:, 0] = rt[:, -1] = 0.0
+        th = np.stack([self._solve(lt[m], rt[m]) for m in range(self.M)])
+        if self.buoy_implicit:
+            gdt = gamma * self.dt
+            for m in range(1, self.M):
+                rw[m] = rw[m] + gdt * self._buoyancy(m, th[m])
         w = np.zeros_like(rw)
         psi = np.zeros_like(rw)
         for m in range(1, self.M):
@@ -256,8 +274,6 @@ class CollocationStepper(ImexScheme):
             b[1:N - 1] = rw[m, 1:N - 1]
             x = self._solve(lw[m], b)
             w[m], psi[m] = x[:N], x[N:]
-        rt[:, 0] = rt[:, -1] = 0.0
-        th = np.stack([self._solve(lt[m], rt[m]) for m in range(self.M)])
         ru[0] = ru[-1] = 0.0
         u = self._solve(lu_, ru)
         return w, psi, th, u

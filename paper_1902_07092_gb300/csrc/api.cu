@@ -1264,8 +1264,6 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
         if (coll == ctx->coll) return PIZZA_OK;
         if (coll && ctx->P.fp32)
             return fail(ctx, PIZZA_EUNSUPPORTED, "mixed precision is implemented for the integration formulation");
-        if (coll && ctx->P.buoy_imp)
-            return fail(ctx, PIZZA_EUNSUPPORTED, "implicit buoyancy is implemented for the integration formulation");
         if (coll && ctx->n_r > PIZZA_COLL_MAX_NR)
             return fail(ctx, PIZZA_EUNSUPPORTED, "collocation is limited to n_r <= %d", PIZZA_COLL_MAX_NR);
         cudaStreamSynchronize(ctx->stream);
@@ -1297,8 +1295,6 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
     }
     if (std::strcmp(key, "buoy_implicit") == 0) {
         if (value != 0.0 && value != 1.0) return fail(ctx, PIZZA_EINVAL, "buoy_implicit must be 0 or 1");
-        if (value == 1.0 && ctx->coll)
-            return fail(ctx, PIZZA_EUNSUPPORTED, "implicit buoyancy is implemented for the integration formulation");
         if (ctx->adj.taping) return fail(ctx, PIZZA_ESTATE, "the buoyancy split cannot change while a tape is recorded");
         cudaStreamSynchronize(ctx->stream);
         ctx->P.buoy_imp = (value == 1.0) ? 1 : 0;

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_coll_grid_rows(StepParams P, const doubl
             if (m > 0) {
                 const double2 nw = cscale(cadd(cc2[k], cmul_i(uw, dm)), is);
                 const double2 th = G1[g_index(k, 3, m, M)], v = G1[g_index(k, 0, m, M)];
-                ew = csub(cmul_i(th, -bfac), nw);
+                ew = P.buoy_imp ? cscale(nw, -1.0) : csub(cmul_i(th, -bfac), nw);
                 et = csub(cscale(v, -P.tc * is * is), nt);
             } else {
                 et = cscale(nt, -1.0);
@@ -183,13 +183,19 @@ __global__ void __launch_bounds__(NT) k_coll_grid_rows(StepParams P, const doubl
 // are omega (n_r), psi (n_r), theta (n_r); of m = 0 theta (n_r), u_bar (n_r).
 // No output vector may alias an input term.
 // ---------------------------------------------------------------------------
+// With implicit buoyancy the solve runs in two launches: phase 1 the temperature
+// and zonal-flow rows, phase 2 the vorticity and streamfunction rows, whose
+// right-hand side gains g (-(Ra/Pr)(i m/s_o)) theta_new at the interior points
+// (the implicit term of the new state still uses the original right-hand side).
+// phase 0: all rows at once (explicit buoyancy).
 __global__ void __launch_bounds__(NT) k_coll_solve(StepParams P, RhsSpec R, DevFactors F, VecSet yo, VecSet mo,
-                                                   VecSet io, int want_mass, int want_imp) {
+                                                   VecSet io, int want_mass, int want_imp, int phase) {
     extern __shared__ double2 sm[];
     const int m = blockIdx.x;
     const int N = P.n_r, ni = N - 2;
     double2* rw = sm;       // interior vorticity rows (m >= 1) or zonal rows (m = 0, real part)
     double2* rt = rw + ni;  // interior temperature rows
+    double2* rg = rt + ni;  // phase 2: vorticity rows with the new temperature's buoyancy
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int j = tid; j < ni; j += nth) {
         const size_t idx = (size_t)m * N + j + 1;
@@ -210,12 +216,14 @@ __global__ void __launch_bounds__(NT) k_coll_solve(StepParams P, RhsSpec R, DevF
         }
         rw[j] = aw;
         rt[j] = at;
+        if (phase == 2 && m > 0)
+            rg[j] = cadd(aw, cmul_i(yo.th[idx], -F.gdt * P.Ra / P.Pr * (double)m / P.s_o));
     }
     __syncthreads();
     const int row = blockIdx.y * nth + tid;
     const int nrows = (m > 0) ? 3 * N : 2 * N;
     const double igdt = 1.0 / F.gdt;
-    if (m == 0 && row < N) {
+    if (m == 0 && row < N && phase != 2) {
         yo.w[row] = make_double2(0.0, 0.0);
         yo.psi[row] = make_double2(0.0, 0.0);
         if (want_mass) mo.w[row] = make_double2(0.0, 0.0);
@@ -231,16 +239,18 @@ __global__ void __launch_bounds__(NT) k_coll_solve(StepParams P, RhsSpec R, DevF
         fld = (row < N) ? 2 : 3;
         k = (row < N) ? row : row - N;
     }
+    if ((phase == 1 && fld <= 1) || (phase == 2 && fld >= 2)) return;
+    const double2* rwg = (phase == 2) ? rg : rw;  // the right-hand side the inverse acts on
     double2 a0 = make_double2(0.0, 0.0), a1 = a0;
     if (fld <= 1) {
         const int ld = 2 * N;
         const double2* g = F.colW + (size_t)m * ni * ld + row;
         int j = 0;
         for (; j + 1 < ni; j += 2) {
-            a0 = cfma(__ldg(&g[(size_t)j * ld]), rw[j], a0);
-            a1 = cfma(__ldg(&g[(size_t)(j + 1) * ld]), rw[j + 1], a1);
+            a0 = cfma(__ldg(&g[(size_t)j * ld]), rwg[j], a0);
+            a1 = cfma(__ldg(&g[(size_t)(j + 1) * ld]), rwg[j + 1], a1);
         }
-        if (j < ni) a0 = cfma(__ldg(&g[(size_t)j * ld]), rw[j], a0);
+        if (j < ni) a0 = cfma(__ldg(&g[(size_t)j * ld]), rwg[j], a0);
     } else {
         const double* g = (fld == 2) ? F.colT + (size_t)m * ni * N + k : F.colU + k;
         const double2* r = (fld == 2) ? rt : rw;
@@ -325,6 +335,8 @@ __global__ void __launch_bounds__(NT) k_coll_apply(StepParams P, VecSet y, VecSe
                 const double2 w = y.w[idx];
                 iw = csub(cadd(w2, cscale(w1, is)), cscale(w, mu * is * is));
                 iw = cadd(iw, cmul_i(y.psi[idx], 2.0 / P.E * (double)m * P.beta[k] * is));
+                if (P.buoy_imp)  // -(Ra/Pr)(i m/s_o) theta
+                    iw = cadd(iw, cmul_i(y.th[idx], -P.Ra / P.Pr * (double)m / P.s_o));
                 if (P.pump) {
                     const double U = P.pump_ups[k], b = P.beta[k];
                     const double2 ps = y.psi[idx];
@@ -457,10 +469,15 @@ cudaError_t launch_coll_grid_rows(const StepParams& P, const double2* G1, const 
 
 cudaError_t launch_coll_solve(const StepParams& P, const RhsSpec& R, const DevFactors& F, VecSet y_out,
                               VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st) {
-    const size_t sm = sizeof(double2) * 2 * (P.n_r - 2);
+    const size_t sm = sizeof(double2) * 3 * (P.n_r - 2);
     dim3 grid(P.M, (3 * P.n_r + NT - 1) / NT);
-    k_coll_solve<<<grid, NT, sm, st>>>(P, R, F, y_out, mass_out, imp_out, want_mass ? 1 : 0, want_imp ? 1 : 0);
-    return cudaGetLastError();
+    for (int phase = P.buoy_imp ? 1 : 0; phase <= (P.buoy_imp ? 2 : 0); ++phase) {
+        k_coll_solve<<<grid, NT, sm, st>>>(P, R, F, y_out, mass_out, imp_out, want_mass ? 1 : 0, want_imp ? 1 : 0,
+                                           phase);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_coll_apply(const StepParams& P, VecSet y, VecSet imp_out, cudaStream_t st) {

@@ -1,8 +1,9 @@
 """Implicit buoyancy on the GPU (option "buoy_implicit", Section 4): the
 temperature of each stage is solved first and its buoyancy joins the
-streamfunction system.  Parity with the oracle's IntegrationStepper(...,
-buoy_implicit=True), itself pinned against a dense solve of the coupled system
-and by the order of an eigenmode run (tests/test_oracle_physics.py).
+streamfunction (collocation: vorticity) system.  Parity with the oracle's
+steppers with buoy_implicit=True, themselves pinned against dense solves of the
+coupled systems and, for the integration formulation, by the order of an
+eigenmode run (tests/test_oracle_physics.py, tests/test_oracle_collocation.py).
 
 Tolerances as for explicit buoyancy (tests/test_gpu_parity.py): 1e-12 at n_r = 33,
 2e-12 at 257.  At n_r = 1025 (N_c = 682, the temperature solved by FP32 solves
@@ -106,18 +107,48 @@ def test_implicit_buoyancy_eigenmode_run_grows_at_the_eigenvalue():
 
 def test_implicit_buoyancy_option_limits():
     from paper_1902_07092_gb300.binding import PizzaError, Solver, pizza_set_option
-    s = Solver(33, 96, 1e-3, 1e5, 1.0, 0.35, "CNAB2", 1e-4, radial="collocation")
-    with pytest.raises(PizzaError) as ei:
-        pizza_set_option(s.ctx, "buoy_implicit", 1)
-    assert ei.value.code == -8
-    s.close()
     s = Solver(33, 96, 1e-3, 1e5, 1.0, 0.35, "CNAB2", 1e-4, buoy_implicit=True)
     with pytest.raises(PizzaError):
         pizza_set_option(s.ctx, "buoy_implicit", 2)
     with pytest.raises(PizzaError) as ei:
         s.tape_begin(5)
     assert ei.value.code == -8
-    with pytest.raises(PizzaError) as ei:
-        pizza_set_option(s.ctx, "radial", 0)
-    assert ei.value.code == -8
     s.close()
+
+
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443"])
+@pytest.mark.parametrize("amp", [1e-4, 1.0])
+def test_implicit_buoyancy_collocation_steps_match_oracle(scheme, amp):
+    """Collocation (Section 3.1) with the buoyancy implicit: the solve runs the
+    temperature rows first, then the vorticity-streamfunction rows."""
+    from oracle.collocation import CollocationStepper
+    from paper_1902_07092_gb300.binding import Solver
+    from tests.test_gpu_collocation import EPS, coll_state, compare_state, set_both
+    n_r, n_phi = 33, 96
+    Ra = 2.0 * critical_rayleigh(1e-3)
+    gpu = Solver(n_r, n_phi, 1e-3, Ra, 1.0, 0.35, scheme, 1e-4, radial="collocation", buoy_implicit=True)
+    ora = CollocationStepper(n_r, n_phi, 1e-3, Ra, 1.0, 0.35, scheme, 1e-4, buoy_implicit=True)
+    psi, th, u = coll_state(n_r, n_phi, amp, 1, psi_amp=amp, u_amp=amp)
+    set_both(gpu, ora, psi, th, u)
+    for _ in range(4):
+        gpu.step(1)
+        ora.step()
+        compare_state(gpu, ora, 1e-12, tol_w=max(1e-12, n_r ** 4 * EPS / 4))
+    gpu.close()
+
+
+def test_implicit_buoyancy_collocation_steps_match_oracle_n129():
+    from oracle.collocation import CollocationStepper
+    from paper_1902_07092_gb300.binding import Solver
+    from tests.test_gpu_collocation import EPS, coll_state, compare_state, set_both
+    n_r, n_phi = 129, 384
+    Ra = 10.0 * critical_rayleigh(1e-5)
+    gpu = Solver(n_r, n_phi, 1e-5, Ra, 1.0, 0.35, "ARS443", 1e-7, radial="collocation", buoy_implicit=True)
+    ora = CollocationStepper(n_r, n_phi, 1e-5, Ra, 1.0, 0.35, "ARS443", 1e-7, buoy_implicit=True)
+    psi, th, u = coll_state(n_r, n_phi, 1e-3, 2, psi_amp=1e-5, u_amp=1e-5)
+    set_both(gpu, ora, psi, th, u)
+    for _ in range(2):
+        gpu.step(1)
+        ora.step()
+        compare_state(gpu, ora, 2e-12, tol_w=max(2e-12, n_r ** 4 * EPS / 4))
+    gpu.close()

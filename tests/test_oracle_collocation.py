@@ -148,3 +148,33 @@ def test_collocation_and_integration_formulations_agree():
         assert d65[f] < 1e-4, (f, d65)
         assert d65[f] < d33[f] / 10, (f, d33, d65)
     assert d65["omega"] < d33["omega"] / 5
+
+
+def test_collocation_implicit_buoyancy_solve_equals_the_coupled_dense_solve():
+    """Section 4 in the collocation formulation: the stage system couples the
+    vorticity rows to the new temperature through -g(-(Ra/Pr)(i m/s_o)) T theta;
+    the block-ordered solve (temperature first) equals a dense solve of the
+    coupled 3N system."""
+    from oracle.collocation import CollocationStepper
+    N, n_phi, gamma, dt = 17, 24, 0.5, 2e-4
+    st = CollocationStepper(N, n_phi, 1e-3, 2e5, 0.7, 0.35, "CNAB2", dt, buoy_implicit=True)
+    o, M = st.ops, st.M
+    rng = np.random.default_rng(8)
+    rw = rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N))
+    rt = rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N))
+    ru = rng.standard_normal(N)
+    w, psi, th, u = st.solve(gamma, (rw, np.zeros_like(rw), rt, ru))
+    gdt = gamma * dt
+    for m in (1, 4, M - 1):
+        L = np.zeros((3 * N, 3 * N), complex)
+        L[:2 * N, :2 * N] = o.lhs_wpsi(m, gdt)
+        cpl = -gdt * (-(o.Ra / o.Pr) * (1j * m / o.ann.s_o)) * o.T
+        cpl[0] = cpl[N - 1] = 0.0
+        L[:N, 2 * N:] = cpl
+        L[2 * N:, 2 * N:] = o.lhs_dir(o.Lt(m), gdt)
+        b = np.zeros(3 * N, complex)
+        b[1:N - 1] = rw[m, 1:N - 1]
+        b[2 * N + 1:3 * N - 1] = rt[m, 1:N - 1]
+        x = np.linalg.solve(L, b)
+        ref = np.concatenate([w[m], psi[m], th[m]])
+        assert np.linalg.norm(ref - x) <= 1e-9 * np.linalg.norm(x)
