@@ -92,9 +92,9 @@ def algorithmic_flops(n_r, n_phi, scheme, radial="integration"):
 # DRAM bytes (read + write) per launch of the roofline kernel from one ncu capture
 # of this workload (summaries under profiles/); null for kernels not captured.
 NCU_TRAFFIC = {
-    ("sparse_n257_p768", "solve"): (44.34e6 + 0.27e6, "profiles/imex_step_kernels_n257_p768.md"),
+    ("sparse_n257_p768", "solve"): (44.34e6 + 0.23e6, "profiles/imex_step_kernels_n257_p768.md"),
     ("large_n2049_p6144", "solve"): (4145.9e6 + 228.4e6, "profiles/solve_kernel_n2049_p6144.md"),
-    ("coll_n257_p768", "solve"): (726.5e6 + 6.8e6, "profiles/collocation_step_kernels_n257_p768.md"),
+    ("coll_n257_p768", "solve"): (735.4e6 + 6.9e6, "profiles/collocation_step_kernels_n257_p768.md"),
 }
 
 
@@ -195,11 +195,19 @@ def job_value(gridpoints, steps, world, total_ms):
 
 
 def cores_used():
+    """Threads the oracle's numpy/scipy can use: the BLAS/OpenMP pools (when
+    threadpoolctl is there), else the CPU count, capped by the thread-count
+    variables of the environment."""
     try:
         from threadpoolctl import threadpool_info
-        return max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
+        n = max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
     except Exception:
-        return os.cpu_count() or 1
+        n = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var, "")
+        if v.isdigit() and int(v) > 0:
+            n = min(n, int(v))
+    return n
 
 
 def run_reference(args, wl, Ra, rank):
