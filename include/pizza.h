@@ -112,6 +112,10 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            Eq. psiomcoll; each stage solves the temperature first and carries
  *            its buoyancy into the streamfunction (vorticity) system.  The adjoint
  *            refuses it.  Set before stepping;
+ *   "azimuthal_dd" 1 (default) = the azimuthal transforms and grid products of
+ *            the FP64 explicit stage in double-float arithmetic (pairs of floats,
+ *            ~48-bit significands, on the FP32 pipe), their m = 0 modes in FP64;
+ *            0 = in FP64.  Both meet the FP64 parity bars of the explicit terms;
  *   "check_finite" 1 = after every step a small kernel scans the state for NaN
  *            or infinite values and sets a device flag; pizza_synchronize then
  *            returns PIZZA_ENONFINITE (cleared by pizza_set_state).  0 (default) =

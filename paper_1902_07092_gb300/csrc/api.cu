@@ -1138,6 +1138,25 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         P.plan_r.twf = ftr;
         P.plan_p.twf = ftp;
     }
+    {
+        // the azimuthal twiddles as double-float pairs for the double-float products
+        std::vector<float4> dd(n_phi);
+        const long double pi = 3.141592653589793238462643383279502884L;
+        for (int j = 0; j < n_phi; ++j) {
+            const long double a = 2.0L * pi * (long double)j / (long double)n_phi;
+            const long double c = cosl(a), sn = -sinl(a);
+            const float ch = (float)c, sh = (float)sn;
+            dd[j] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(sn - (long double)sh));
+        }
+        float4* dtw = dalloc<float4>(ctx, dd.size(), al);
+        if (!dtw) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(dtw, dd.data(), dd.size() * sizeof(float4));
+        P.plan_p.twdd = dtw;
+        P.phi_dd = 1;
+    }
     // half-length radial plan: its twiddles exp(-2 pi i j/K) are plan_r's at stride 2
     if (!make_fft_plan(ctx->K, P.plan_h)) {
         ctx->err = "unsupported transform length";
@@ -1280,6 +1299,12 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
         if (!rc) rc = set_pumping_tables(ctx);
         if (rc) return rc;
         reset_slots(ctx);
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "azimuthal_dd") == 0) {
+        if (value != 0.0 && value != 1.0) return fail(ctx, PIZZA_EINVAL, "azimuthal_dd must be 0 or 1");
+        cudaStreamSynchronize(ctx->stream);
+        ctx->P.phi_dd = (value == 1.0) ? 1 : 0;
         return PIZZA_OK;
     }
     if (std::strcmp(key, "check_finite") == 0) {

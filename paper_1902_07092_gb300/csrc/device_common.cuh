@@ -5,6 +5,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "ddfloat.cuh"
 #include "pizza_internal.h"
 
 namespace pz {
@@ -63,6 +64,32 @@ struct Cx<float2> {
     __device__ static float2 from(double2 a) { return make_float2((float)a.x, (float)a.y); }
     __device__ static const float2* tw(const FftPlan& p) { return p.twf; }
 };
+template <>
+struct Cx<ddc> {
+    using R = ddf;
+    __device__ static ddc make(double a, double b) { return ddc{dd_from(a), dd_from(b)}; }
+    __device__ static ddc from(double2 a) { return dd_from(a); }
+    __device__ static const ddc* tw(const FftPlan& p) { return reinterpret_cast<const ddc*>(p.twdd); }
+};
+// a real constant in the real type of a complex type
+template <class RT>
+__device__ __forceinline__ RT rconst(double c) {
+    return (RT)c;
+}
+template <>
+__device__ __forceinline__ ddf rconst<ddf>(double c) {
+    return dd_from(c);
+}
+// twiddle load through the read-only cache
+template <class T>
+__device__ __forceinline__ T ldg_tw(const T* p) {
+    return __ldg(p);
+}
+template <>
+__device__ __forceinline__ ddc ldg_tw<ddc>(const ddc* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return ddc{ddf{v.x, v.y}, ddf{v.z, v.w}};
+}
 // radial tables in the precision of the complex type
 template <class T>
 struct Tab;
@@ -106,7 +133,7 @@ __device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __re
         w[0] = Cx<T>::make(1.0, 0.0);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            w[r] = first ? Cx<T>::make(1.0, 0.0) : __ldg(&tw[r * k * twmul]);
+            w[r] = first ? Cx<T>::make(1.0, 0.0) : ldg_tw(&tw[r * k * twmul]);
             if (SIGN > 0) w[r].y = -w[r].y;
         }
         if (R == 2) {
@@ -141,7 +168,7 @@ __device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __re
             v[1] = cadd(t1, rt);
             v[3] = csub(t1, rt);
         } else if (R == 3) {
-            const RT h3 = (RT)0.86602540378443864676;  // sqrt(3)/2
+            const RT h3 = rconst<RT>(0.86602540378443864676);  // sqrt(3)/2
             T t1, t2;
             if (first) {
                 t1 = cadd(v[1], v[2]);
@@ -152,8 +179,8 @@ __device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __re
                 t2 = creflect(b1, t1);                // w1 v1 - w2 v2
             }
             T m1;
-            m1.x = fmat((RT)-0.5, t1.x, v[0].x);
-            m1.y = fmat((RT)-0.5, t1.y, v[0].y);
+            m1.x = fmat(rconst<RT>(-0.5), t1.x, v[0].x);
+            m1.y = fmat(rconst<RT>(-0.5), t1.y, v[0].y);
             // forward: -i*h3*t2 ; backward: +i*h3*t2
             T rt;
             if (SIGN < 0) {

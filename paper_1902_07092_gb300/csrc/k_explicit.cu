@@ -286,6 +286,136 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* 
 }
 
 // ---------------------------------------------------------------------------
+// K2 of the FP64 stage in double-float arithmetic (ddfloat.cuh): the FP64
+// spectra are split into float pairs on load, the transforms and products run
+// on the FP32 pipe with ~48-bit significands, and the product spectra are
+// rounded back to FP64 on store.  The same steps as k_phi_products; the packed
+// pairs are balanced within float range (|exponent difference| <= 40).
+// The m = 0 modes of the products are taken in FP64 from the input spectra
+// instead: with band-limited fields (2 n_m < n_phi, no aliasing) the mean of
+// a b is a_0 b_0 + 2 sum_{m >= 1} Re(a_m conj(b_m)).  These means (the zonal
+// forcing [v omega]_0 above all) cancel to ~1e-4 of their terms, which would
+// magnify the double-float rounding beyond FP64 accuracy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_packed_spectrum_dd(ddc* Z, const double2* __restrict__ src, int M, int Pn,
+                                                        int n_m, float sb) {
+    // each spectral value converted once, written to m and to its mirror Pn - m
+    for (int m = threadIdx.x; m <= n_m; m += blockDim.x) {
+        if (m == 0) {
+            Z[0] = ddc{dd_from(src[0].x), dd_scale2(dd_from(src[M].x), sb)};
+            continue;
+        }
+        const ddc a = dd_from(src[m]);
+        ddc b = dd_from(src[M + m]);
+        b.x = dd_scale2(b.x, sb);
+        b.y = dd_scale2(b.y, sb);
+        Z[m] = ddc{a.x - b.y, a.y + b.x};        // a + i b
+        Z[Pn - m] = ddc{a.x + b.y, b.x - a.y};   // conj(a) + i conj(b)
+    }
+    for (int j = n_m + 1 + threadIdx.x; j < Pn - n_m; j += blockDim.x) Z[j] = ddc{ddf{0.f, 0.f}, ddf{0.f, 0.f}};
+}
+
+__device__ __forceinline__ void store_split_spectrum_dd(const ddc* Y, double2* __restrict__ dst, int M, int Pn,
+                                                        int n_m, ddf ia, ddf ib) {
+    for (int m = threadIdx.x; m <= n_m; m += blockDim.x) {
+        ddc a, b;
+        if (m == 0) {
+            a = ddc{Y[0].x * ia, ddf{0.f, 0.f}};
+            b = ddc{Y[0].y * ib, ddf{0.f, 0.f}};
+        } else {
+            const ddc y1 = Y[m], y2 = Y[Pn - m];
+            // a = (y1 + conj(y2))/2,  b = (y1 - conj(y2))/(2i)
+            a.x = dd_scale2(y1.x + y2.x, 0.5f) * ia;
+            a.y = dd_scale2(y1.y - y2.y, 0.5f) * ia;
+            b.x = dd_scale2(y1.y + y2.y, 0.5f) * ib;
+            b.y = -(dd_scale2(y1.x - y2.x, 0.5f) * ib);
+        }
+        dst[m] = dd_to(a);
+        dst[M + m] = dd_to(b);
+    }
+}
+
+__global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const double2* __restrict__ G1,
+                                                            double2* __restrict__ G2) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ddc* sm = reinterpret_cast<ddc*>(smraw);
+    const int k = blockIdx.x;
+    const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
+    ddc* X = sm;
+    ddc* Y = sm + Pn;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    ddc reg[MAXPER];
+    __shared__ double red[4 * 32], mx[4];
+    block_max_abs(G1 + g_index(k, 0, 0, M), M, 4, n_m + 1, mx, red);
+    const int e1 = pow2_exponent(mx[0], mx[1], 40), e2 = pow2_exponent(mx[2], mx[3], 40);
+    const ddf iP = dd_from(P.inv_nphi);  // 1/n_phi
+    // FP64 means of the four products, pairs (v, omega), (u_phi, omega), (v, theta),
+    // (u_phi, theta), reduced per warp here and summed at the end
+    __shared__ double msum[4][16];
+    {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        const double2* f = G1 + g_index(k, 0, 0, M);  // f[q * M + m]: v, u_phi, omega, theta
+        for (int m = tid; m <= n_m; m += nth) {
+            // m = 0: the real parts only (the transforms read no more of mode 0)
+            const double w = (m == 0) ? 1.0 : 2.0, wi = (m == 0) ? 0.0 : 2.0;
+            const double2 v = f[m], up = f[M + m], om = f[2 * M + m], th = f[3 * M + m];
+            acc[0] = fma(w, v.x * om.x, fma(wi, v.y * om.y, acc[0]));
+            acc[1] = fma(w, up.x * om.x, fma(wi, up.y * om.y, acc[1]));
+            acc[2] = fma(w, v.x * th.x, fma(wi, v.y * th.y, acc[2]));
+            acc[3] = fma(w, up.x * th.x, fma(wi, up.y * th.y, acc[3]));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        }
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) msum[q][tid >> 5] = acc[q];
+    }
+
+    load_packed_spectrum_dd(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, pow2f(e1));
+    ddc* R = fft_batched<+1>(X, Y, P.plan_p, 1);
+#pragma unroll
+    for (int i = 0; i < MAXPER; ++i) {
+        const int j = tid + i * nth;
+        if (j < Pn) reg[i] = R[j];
+    }
+    __syncthreads();
+    load_packed_spectrum_dd(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m, pow2f(e2));
+    R = fft_batched<+1>(X, Y, P.plan_p, 1);
+#pragma unroll
+    for (int i = 0; i < MAXPER; ++i) {
+        const int j = tid + i * nth;
+        if (j < Pn) {
+            const ddc g2 = R[j], g1 = reg[i];
+            R[j] = cscale(g1, g2.x);
+            reg[i] = cscale(g1, g2.y);
+        }
+    }
+    ddc* other = (R == X) ? Y : X;
+    ddc* S = fft_batched<-1>(R, other, P.plan_p, 1);
+    // g1 Re(g2) = v omega + i l1 u_phi omega
+    store_split_spectrum_dd(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, iP, dd_scale2(iP, pow2f(-e1)));
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < MAXPER; ++i) {
+        const int j = tid + i * nth;
+        if (j < Pn) X[j] = reg[i];
+    }
+    S = fft_batched<-1>(X, Y, P.plan_p, 1);
+    // g1 Im(g2) = l2 (v theta + i l1 u_phi theta)
+    store_split_spectrum_dd(S, G2 + g_index(k, 2, 0, M), M, Pn, n_m, dd_scale2(iP, pow2f(-e2)),
+                            dd_scale2(dd_scale2(iP, pow2f(-e1)), pow2f(-e2)));
+    __syncthreads();  // the stores above are done (thread 0 wrote the m = 0 entries replaced here)
+    if (tid < 4) {
+        double t = 0.0;
+        for (int w = 0; w < (nth >> 5); ++w) t += msum[tid][w];
+        G2[g_index(k, tid, 0, M)] = make_double2(t, 0.0);  // G2 fields follow the pair order
+    }
+}
+
+// ---------------------------------------------------------------------------
 // K3: per m, radial divergences of the fluxes, Eq. icheb, truncation to n < N_c
 // (dealiasing), and the integrated right-hand sides
 //   N_omega = (1/s) d/ds(h^2 [v omega]_m) + (i m/s) [u_phi omega]_m
@@ -634,7 +764,17 @@ cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cuda
 }
 
 cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2* G2, cudaStream_t st) {
-    return P.fp32 ? phi_products_t<float2>(P, G1, G2, st) : phi_products_t<double2>(P, G1, G2, st);
+    if (P.fp32) return phi_products_t<float2>(P, G1, G2, st);
+    if (P.phi_dd && P.plan_p.twdd) {
+        const size_t sm = smem_phi_products(P);
+        const int nth = phi_threads(P);
+        if (P.n_phi > nth * MAXPER || nth > 512) return cudaErrorInvalidValue;
+        cudaError_t err = cudaFuncSetAttribute(k_phi_products_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_phi_products_dd<<<P.n_r, nth, sm, st>>>(P, G1, G2);
+        return cudaGetLastError();
+    }
+    return phi_products_t<double2>(P, G1, G2, st);
 }
 
 cudaError_t launch_grid_to_spec(const StepParams& P, const double2* G2, VecSet y, VecSet e, cudaStream_t st) {

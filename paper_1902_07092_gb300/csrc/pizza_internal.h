@@ -20,6 +20,7 @@ struct FftPlan {
     int radix[MAX_PASSES];
     const double2* tw;  // tw[j] = exp(-2 pi i j / L), j < L
     const float2* twf;  // the same, rounded to FP32 (mixed-precision explicit stage)
+    const float4* twdd; // the same as double-float pairs (hi, lo) of (re, im), or null
 };
 
 // One set of per-field vectors: Psi and theta complex [M][nc], u real [nc]; the
@@ -109,6 +110,9 @@ struct StepParams {
     // implicit buoyancy (option "buoy_implicit", Section 4): 1 when the buoyancy
     // term is part of the implicit operator of the streamfunction equation
     int buoy_imp;
+    // azimuthal products of the FP64 explicit stage in double-float arithmetic on
+    // the FP32 pipe (option "azimuthal_dd"): 1 when selected (plan_p.twdd set)
+    int phi_dd;
     double2* pump_F;
 };
 

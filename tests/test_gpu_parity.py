@@ -229,3 +229,23 @@ def test_overlapping_contexts_match_a_context_run_alone(radial):
         for x, y in zip(s.get_state(), ref):
             assert np.array_equal(x, y)
         s.close()
+
+
+@pytest.mark.parametrize("n_r,n_phi", [(65, 192), (257, 768)])
+def test_azimuthal_products_in_ddfloat_and_fp64_match_oracle(n_r, n_phi):
+    """Option azimuthal_dd: the azimuthal transforms and products of the FP64
+    stage in double-float arithmetic (default) or in FP64; both within the
+    explicit-term tolerance of the oracle, on states with O(1) fields."""
+    from paper_1902_07092_gb300.binding import pizza_set_option
+    psi, th, u = random_state(n_r, n_phi, 1.0, 5, psi_amp=1.0, u_amp=1.0)
+    tol = max(1e-12, 4 * n_r * n_r * 2.0 ** -53)
+    for dd in (1, 0):
+        gpu, ora = make_pair(n_r, n_phi, 1e-3, 2.0, "CNAB2", 1e-4)
+        pizza_set_option(gpu.ctx, "azimuthal_dd", dd)
+        gpu.set_state(th, psi, u)
+        ep, et, eu = gpu.explicit_terms()
+        rp, rt, ru = explicit_terms(ora.g, psi, th, u)
+        errs = (rel_l2(ep, rp), rel_l2(et, rt), rel_l2(eu, ru))
+        print("azimuthal_dd=%d n_r=%d: psi %.2e theta %.2e u %.2e (tol %.1e)" % ((dd, n_r) + errs + (tol,)))
+        assert max(errs) <= tol
+        gpu.close()
