@@ -276,6 +276,7 @@ def adjoint_cost(args, B, wl, Ra, sol, th, z, zu):
     w = sol.nusselt_weights()
     g = np.zeros((sol.M, sol.n_c), np.complex128)
     g[0] = w / K
+    g = torch.from_numpy(g).cuda()  # the objective's gradient, resident like the state
     sol.set_state(th, z, zu)
     sol.tape_begin(every)
     torch.cuda.synchronize()
@@ -284,14 +285,15 @@ def adjoint_cost(args, B, wl, Ra, sol, th, z, zu):
     B.pizza_synchronize(sol.ctx)
     t_fwd = time.perf_counter() - t0
     t0 = time.perf_counter()
-    for _ in range(K):
-        dRa = sol.adjoint_step(g_theta=g)
+    for i in range(K):
+        dRa = sol.adjoint_step(g_theta=g, want_dRa=(i == K - 1))
     B.pizza_synchronize(sol.ctx)
     t_rev = time.perf_counter() - t0
     return {"steps": K, "checkpoint_every": every, "forward_ms_per_step": 1e3 * t_fwd / K,
             "reverse_ms_per_step": 1e3 * t_rev / K, "reverse_over_forward": t_rev / t_fwd,
             "dJ_dRa": dRa, "objective": "J = (1/K) sum_n (Nu_n - 1)",
-            "timing": "wall clock, synchronised, inputs resident; reverse includes the segment recomputation"}
+            "timing": "wall clock, synchronised, inputs and the objective's gradient resident; dJ/dRa read after "
+                      "the last step; reverse includes the segment recomputation"}
 
 
 def run_batch(args, wl, rank, world, local_rank):

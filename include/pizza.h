@@ -115,7 +115,8 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *   "azimuthal_dd" 1 (default) = the azimuthal transforms and grid products of
  *            the FP64 explicit stage in double-float arithmetic (pairs of floats,
  *            ~48-bit significands, on the FP32 pipe), their m = 0 modes in FP64;
- *            0 = in FP64.  Both meet the FP64 parity bars of the explicit terms;
+ *            0 = in FP64.  Both meet the FP64 parity bars of the explicit terms.
+ *            The adjoint's azimuthal stage is FP64 either way;
  *   "check_finite" 1 = after every step a small kernel scans the state for NaN
  *            or infinite values and sets a device flag; pizza_synchronize then
  *            returns PIZZA_ENONFINITE (cleared by pizza_set_state).  0 (default) =
@@ -194,8 +195,8 @@ int pizza_diagnostics(pizza_ctx *ctx, pizza_diag *out);
  * synchronises the context stream. */
 int pizza_get_grid(pizza_ctx *ctx, double *us, double *uphi, double *omega, double *theta);
 
-/* Discrete adjoint of CNAB2 runs (integration formulation, FP64, n_phi <= 3072;
- * PIZZA_EUNSUPPORTED otherwise), for gradients of J = sum_{n=1..K} j_n(y_n) of
+/* Discrete adjoint of CNAB2 runs (integration formulation, FP64, n_phi <= 3072,
+ * n_r <= 1025; PIZZA_EUNSUPPORTED otherwise), for gradients of J = sum_{n=1..K} j_n(y_n) of
  * the states y_n = (Psi_hat, theta_hat, u_hat) after n steps.  The forward step
  * (Eq. multistep1 with the start-up rule) is
  *   y_{n+1} = S^{-1} P r_n,  r_0 = A y_0 + dt E(y_0),
@@ -216,7 +217,9 @@ int pizza_get_grid(pizza_ctx *ctx, double *us, double *uphi, double *omega, doub
  * = zero) and leaves lambda_{K-k} without its own g; the states needed are
  * recomputed segment by segment from the checkpoints (which overwrites the
  * forward state of the context).  *dJ_dRa (may be NULL) receives the running total
- * of the Ra derivative.  PIZZA_ESTATE when no recorded step is left.
+ * of the Ra derivative (accumulated on the device); with dJ_dRa NULL the call only
+ * enqueues work on the context's stream, otherwise it waits for it.  PIZZA_ESTATE
+ * when no recorded step is left.
  * pizza_get_adjoint: copy lambda (after K calls: dJ/dy_0) out.
  * pizza_explicit_adjoint: J_E(y)* applied to (e_psi_bar, e_theta_bar, e_u_bar) at
  * the current state, without the tape (verification). */

@@ -185,8 +185,12 @@ def pizza_tape_begin(ctx, checkpoint_every=20):
     return _check(load().pizza_tape_begin(ctx, checkpoint_every), ctx)
 
 
-def pizza_adjoint_step(ctx, g_theta=None, g_psi=None, g_u=None):
-    """Reverse one recorded step; returns the running dJ/dRa."""
+def pizza_adjoint_step(ctx, g_theta=None, g_psi=None, g_u=None, want_dRa=True):
+    """Reverse one recorded step; returns the running dJ/dRa (None, without
+    waiting for the GPU, when want_dRa is false)."""
+    if not want_dRa:
+        _check(load().pizza_adjoint_step(ctx, _ptr(g_theta), _ptr(g_psi), _ptr(g_u), None), ctx)
+        return None
     r = ctypes.c_double(0.0)
     _check(load().pizza_adjoint_step(ctx, _ptr(g_theta), _ptr(g_psi), _ptr(g_u), ctypes.byref(r)), ctx)
     return r.value
@@ -319,9 +323,18 @@ class Solver:
     def tape_begin(self, checkpoint_every=20):
         pizza_tape_begin(self.ctx, checkpoint_every)
 
-    def adjoint_step(self, g_theta=None, g_psi=None, g_u=None):
-        c = lambda a, dt: None if a is None else np.ascontiguousarray(a, dtype=dt)
-        return pizza_adjoint_step(self.ctx, c(g_theta, np.complex128), c(g_psi, np.complex128), c(g_u, np.float64))
+    def adjoint_step(self, g_theta=None, g_psi=None, g_u=None, want_dRa=True):
+        """g_*: numpy arrays or contiguous tensors (host or device) of the step's
+        objective gradient; returns the running dJ/dRa, or None when want_dRa is
+        false (the step is then only enqueued)."""
+        def c(a, dt):
+            if a is None or isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+                return None if a is None else np.ascontiguousarray(a, dtype=dt)
+            if str(a.dtype) != "torch." + np.dtype(dt).name:
+                raise TypeError("expected a %s tensor" % np.dtype(dt).name)
+            return a
+        return pizza_adjoint_step(self.ctx, c(g_theta, np.complex128), c(g_psi, np.complex128), c(g_u, np.float64),
+                                  want_dRa)
 
     def get_adjoint(self):
         th = np.zeros((self.M, self.n_c), np.complex128)

@@ -116,7 +116,7 @@ struct pizza_ctx {
         int K = 0;                 // recorded steps
         int pos = 0;               // adjoint position: lam holds dJ/dy_pos (without g_pos)
         int seg = -1;              // segment cached in seg_y
-        double dRa = 0.0;
+        double* dRa_dev = nullptr;  // running dJ/dRa on the device (ra[M])
         std::vector<VecSet> ck_y, ck_e;  // checkpoints: y_{s*every}, E(y_{s*every - 1})
         std::vector<VecSet> seg_y;       // y_{seg*every + i}, i < every
         VecSet lam{}, rho[2]{}, w{}, g{};
@@ -909,6 +909,14 @@ int ensure_adjoint(pizza_ctx* ctx) {
     if (ctx->coll || ctx->P.fp32 || ctx->scheme != PIZZA_CNAB2)
         return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is implemented for CNAB2, integration, FP64");
     if (ctx->n_phi > 3072) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is limited to n_phi <= 3072");
+    {
+        int dev = 0, smax = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (smem_adj_grid_to_spec(ctx->P) > (size_t)smax || smem_adj_spec_to_grid(ctx->P) > (size_t)smax)
+            return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint's radial kernels do not fit the device at n_r = %d",
+                        ctx->n_r);
+    }
     if (!ctx->dt_set) return fail(ctx, PIZZA_ESTATE, "dt is not set");
     int rc = build_adjoint_factors(ctx);
     if (rc) return rc;
@@ -921,8 +929,9 @@ int ensure_adjoint(pizza_ctx* ctx) {
     const size_t gsz = (size_t)ctx->n_r * 4 * ctx->M;
     a.Gb1 = dalloc<double2>(ctx, gsz, a.allocs);
     a.Gb2 = dalloc<double2>(ctx, gsz, a.allocs);
-    a.ra = dalloc<double>(ctx, ctx->M, a.allocs);
+    a.ra = dalloc<double>(ctx, ctx->M + 1, a.allocs);
     if (!ok || !a.Gb1 || !a.Gb2 || !a.ra) return fail(ctx, PIZZA_ENOMEM, "allocation of adjoint buffers failed");
+    a.dRa_dev = a.ra + ctx->M;
     a.ready = true;
     return PIZZA_OK;
 }
@@ -1604,7 +1613,7 @@ int pizza_tape_begin(pizza_ctx* ctx, int checkpoint_every) {
     a.K = 0;
     a.pos = 0;
     a.seg = -1;
-    a.dRa = 0.0;
+    CK(cudaMemsetAsync(a.dRa_dev, 0, sizeof(double), ctx->stream));
     a.rcur = 0;
     bool ok = true;
     VecSet y = adj_vec(ctx, ok, true), e = adj_vec(ctx, ok, true);
@@ -1650,13 +1659,13 @@ int pizza_adjoint_step(pizza_ctx* ctx, const double* g_theta, const double* g_ps
     P64.fp32 = 0;
     CK(launch_spec_to_grid(P64, y, ctx->G1, ctx->stream));
     CK(launch_adj_explicit(P64, a.w, y, a.lam, ctx->G1, a.Gb2, a.Gb1, a.ra, ctx->stream));
-    std::vector<double> ra(ctx->M);
-    CK(cudaMemcpyAsync(ra.data(), a.ra, ctx->M * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    for (int m = 0; m < ctx->M; ++m) a.dRa += ra[m];
+    CK(launch_ra_accumulate(a.ra, ctx->M, a.dRa_dev, ctx->stream));
     a.rcur = 1 - a.rcur;
     a.pos = n;
-    if (dJ_dRa) *dJ_dRa = a.dRa;
+    if (dJ_dRa) {  // the only host synchronisation of the reverse step
+        CK(cudaMemcpyAsync(dJ_dRa, a.dRa_dev, sizeof(double), cudaMemcpyDefault, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     return PIZZA_OK;
 }
 

@@ -31,7 +31,10 @@ constexpr int MAXPER_A = 12;  // azimuthal points per thread (n_phi <= 3072)
 
 __device__ __forceinline__ int g_index(int k, int f, int m, int M) { return (k * 4 + f) * M + m; }
 
+// radial transforms per shared-memory pass: the analysis adjoint has pairs, the
+// synthesis adjoint four fields (one pass up to n_r = 513)
 __host__ __device__ inline int adj_batch(int L) { return L <= 1024 ? 2 : 1; }
+__host__ __device__ inline int adj_batch4(int L) { return L <= 1024 ? 4 : 1; }
 
 // (X^T x)_n for a band operator stored transposed (row n of X^T, half width H)
 template <int H>
@@ -63,19 +66,19 @@ __device__ __forceinline__ double bandT_row_r(const double* __restrict__ bandT, 
 }
 
 // sum_k cos(pi n k/K) a_k for n = 0..K of nb vectors a (length K+1 each, in src
-// with stride K+1), through the FFT of the even extension with the end values
-// doubled: Z_n = 2 sum''_k z_k cos(...) = 2 sum_k a_k cos(...).  Results are Z/2
-// into dst (stride K+1).  bufA, bufB: nb*2K scratch.
-__device__ void cos_sums(const double2* src, double2* dst, int nb, double2* bufA, double2* bufB, const FftPlan& pl,
-                         int K) {
-    const int L = 2 * K;
+// with stride K+1): the DCT-I of the even extension with the end values doubled,
+// Z_n = 2 sum''_k z_k cos(...) = 2 sum_k a_k cos(...) (the half-length transform
+// where the forward stage uses it).  Results are Z/2 into dst (stride K+1).
+// bufA, bufB: nb*2K scratch, nb <= 4.
+__device__ void cos_sums(const double2* src, double2* dst, int nb, double2* bufA, double2* bufB, const StepParams& P) {
+    const int K = P.K, L = 2 * K;
     for (int b = 0; b < nb; ++b)
         for (int j = threadIdx.x; j <= K; j += blockDim.x) {
             double2 v = src[b * (K + 1) + j];
             if (j == 0 || j == K) v = cscale(v, 2.0);
             even_extend_store(bufA + b * L, K, j, v);
         }
-    double2* R = fft_batched<-1>(bufA, bufB, pl, nb);
+    double2* R = radial_dct1(bufA, bufB, P, nb);
     for (int b = 0; b < nb; ++b)
         for (int n = threadIdx.x; n <= K; n += blockDim.x) dst[b * (K + 1) + n] = cscale(R[b * L + n], 0.5);
     __syncthreads();
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(NTA) k_adj_grid_to_spec(StepParams P, VecSet w
     // grid adjoints: f_bar_k = C w'_k sum_n cos(pi n k/K) f_hat_bar_n  -> c0, c1
     for (int b0 = 0; b0 < 2; b0 += NB) {
         const int nb = min(NB, 2 - b0);
-        cos_sums(c0 + b0 * N, c0 + b0 * N, nb, bufA, bufB, P.plan_r, K);
+        cos_sums(c0 + b0 * N, c0 + b0 * N, nb, bufA, bufB, P);
     }
     for (int k = tid; k < N; k += nth) {
         const double f = P.cnorm * ((k == 0 || k == K) ? 0.5 : 1.0);
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(NTA) k_adj_grid_to_spec(StepParams P, VecSet w
     // Dg^T a = Ana^T Dc^T Syn^T a for a in (c2, c3) (m = 0: only the theta field)
     for (int b0 = 0; b0 < 2; b0 += NB) {
         const int nb = min(NB, 2 - b0);
-        cos_sums(c2 + b0 * N, c2 + b0 * N, nb, bufA, bufB, P.plan_r, K);  // Syn^T
+        cos_sums(c2 + b0 * N, c2 + b0 * N, nb, bufA, bufB, P);  // Syn^T
     }
     for (int f = 0; f < 2; ++f) {
         double2* v = f ? c3 : c2;
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(NTA) k_adj_grid_to_spec(StepParams P, VecSet w
         const int nb = min(NB, 2 - b0);
         for (int b = 0; b < nb; ++b)
             for (int j = tid; j <= K; j += nth) even_extend_store(bufA + b * L, K, j, c2[(b0 + b) * N + j]);
-        double2* R = fft_batched<-1>(bufA, bufB, P.plan_r, nb);
+        double2* R = radial_dct1(bufA, bufB, P, nb);
         for (int b = 0; b < nb; ++b)
             for (int k = tid; k <= K; k += nth) {
                 const double wk = (k == 0 || k == K) ? 0.5 : 1.0;
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(NTA) k_adj_spec_to_grid(StepParams P, const do
     extern __shared__ double2 sm[];
     const int m = blockIdx.x;
     const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
-    const int NB = adj_batch(L);
+    const int NB = adj_batch4(L);
     double2* bufA = sm;
     double2* bufB = bufA + NB * L;
     double2* a = bufB + NB * L;  // [4][N]: a0, a1, a2, t
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(NTA) k_adj_spec_to_grid(StepParams P, const do
     __syncthreads();
     for (int b0 = 0; b0 < 4; b0 += NB) {
         const int nb = min(NB, 4 - b0);
-        cos_sums(a + b0 * N, a + b0 * N, nb, bufA, bufB, P.plan_r, K);  // Syn^T of each
+        cos_sums(a + b0 * N, a + b0 * N, nb, bufA, bufB, P);  // Syn^T of each
     }
     // Horner: a1 += Dc^T a2 (m > 0); a0 += Dc^T a1
     if (m > 0) {
@@ -378,55 +381,81 @@ __global__ void __launch_bounds__(NTA) k_adj_spec_to_grid(StepParams P, const do
 
 // ---------------------------------------------------------------------------
 // rho = P S^{-H} lam with the dense inverses (column-major: Wp [M][nc][nc-4]
-// complex, Wt [M][nc][nc-2], Wu [nc][nc-2] real): thread per output row, the
-// input vector in shared memory; rows below the tau rows are written 0.
-// Grid (M, ceil(3 nc / NTA)): rows [0, nc-4) psi, [nc-4, 2nc-6) theta, then u.
+// complex, Wt [M][nc][nc-2], Wu [nc][nc-2] real); rows below the tau rows are
+// written 0.  The kernel streams the inverses once (HBM-bound): a CTA takes ASR
+// consecutive output rows of one kind (Psi, theta or u) of one mode m, its ASS
+// warps split the columns j into slices, each warp load reading one column's ASR
+// consecutive rows (coalesced), so that every thread has only ~nc/ASS dependent
+// iterations; the slices' partial sums are added in a fixed order.
+// Grid (M, tp + 2 tt): row tiles [0, tp) Psi, [tp, tp + tt) theta, then u (m = 0).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTA) k_adj_solve(StepParams P, AdjFactors A, VecSet lam, VecSet rho) {
-    extern __shared__ double2 sm[];
+constexpr int ASR = 32, ASS = 8;
+
+__global__ void __launch_bounds__(ASR * ASS) k_adj_solve(StepParams P, AdjFactors A, VecSet lam, VecSet rho) {
+    extern __shared__ double2 sm[];  // the input vector, nc entries
+    __shared__ double2 part[ASS][ASR];
     const int m = blockIdx.x, nc = P.nc, np = nc - 4, nt = nc - 2;
-    double2* lp = sm;
-    double2* lt = lp + nc;
-    double* lu = reinterpret_cast<double*>(lt + nc);
-    const int tid = threadIdx.x;
+    const int tp = (np + ASR - 1) / ASR, tt = (nt + ASR - 1) / ASR;
+    const int tile = blockIdx.y;
+    const int kind = (tile < tp) ? 0 : (tile < tp + tt) ? 1 : 2;
+    if (kind == 2 && m != 0) return;
+    const int r0 = (tile - (kind == 0 ? 0 : (kind == 1 ? tp : tp + tt))) * ASR;
+    const int tid = threadIdx.x, lane = tid & 31, sl = tid >> 5;
     for (int j = tid; j < nc; j += blockDim.x) {
-        lp[j] = lam.psi[(size_t)m * nc + j];
-        lt[j] = lam.th[(size_t)m * nc + j];
-        if (m == 0) lu[j] = lam.u[j];
+        const size_t idx = (size_t)m * nc + j;
+        sm[j] = (kind == 0) ? lam.psi[idx] : (kind == 1) ? lam.th[idx] : make_double2(lam.u[j], 0.0);
     }
     __syncthreads();
-    const int row = blockIdx.y * blockDim.x + tid;
-    if (row < np) {
-        double2 acc = make_double2(0.0, 0.0), acc1 = acc;
-        if (m > 0) {
-            const double2* g = A.Wp + (size_t)m * nc * np + row;
-            int j = 0;
-            for (; j + 1 < nc; j += 2) {
-                acc = cfma(__ldg(&g[(size_t)j * np]), lp[j], acc);
-                acc1 = cfma(__ldg(&g[(size_t)(j + 1) * np]), lp[j + 1], acc1);
+    const int row = r0 + lane, nrows = (kind == 0) ? np : nt;
+    const int j0 = sl * nc / ASS, j1 = (sl + 1) * nc / ASS;
+    double2 acc = make_double2(0.0, 0.0), acc1 = acc;
+    if (row < nrows) {
+        if (kind == 0) {
+            if (m > 0) {
+                const double2* g = A.Wp + (size_t)m * nc * np + row;
+                int j = j0;
+#pragma unroll 4
+                for (; j + 1 < j1; j += 2) {
+                    acc = cfma(__ldg(&g[(size_t)j * np]), sm[j], acc);
+                    acc1 = cfma(__ldg(&g[(size_t)(j + 1) * np]), sm[j + 1], acc1);
+                }
+                if (j < j1) acc = cfma(__ldg(&g[(size_t)j * np]), sm[j], acc);
             }
-            if (j < nc) acc = cfma(__ldg(&g[(size_t)j * np]), lp[j], acc);
+        } else {
+            const double* g = (kind == 1) ? A.Wt + (size_t)m * nc * nt + row : A.Wu + row;
+            int j = j0;
+#pragma unroll 4
+            for (; j + 1 < j1; j += 2) {
+                const double c = __ldg(&g[(size_t)j * nt]), c1 = __ldg(&g[(size_t)(j + 1) * nt]);
+                acc.x = fma(c, sm[j].x, acc.x);
+                acc.y = fma(c, sm[j].y, acc.y);
+                acc1.x = fma(c1, sm[j + 1].x, acc1.x);
+                acc1.y = fma(c1, sm[j + 1].y, acc1.y);
+            }
+            if (j < j1) {
+                const double c = __ldg(&g[(size_t)j * nt]);
+                acc.x = fma(c, sm[j].x, acc.x);
+                acc.y = fma(c, sm[j].y, acc.y);
+            }
         }
-        rho.psi[(size_t)m * nc + 4 + row] = cadd(acc, acc1);
-        if (row < 4) rho.psi[(size_t)m * nc + row] = make_double2(0.0, 0.0);
-    } else if (row < np + nt) {
-        const int r = row - np;
-        const double* g = A.Wt + (size_t)m * nc * nt + r;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int j = 0; j < nc; ++j) {
-            const double c = __ldg(&g[(size_t)j * nt]);
-            acc.x = fma(c, lt[j].x, acc.x);
-            acc.y = fma(c, lt[j].y, acc.y);
+    }
+    part[sl][lane] = cadd(acc, acc1);
+    __syncthreads();
+    if (sl == 0 && row < nrows) {
+        double2 t = part[0][lane];
+#pragma unroll
+        for (int q = 1; q < ASS; ++q) t = cadd(t, part[q][lane]);
+        const size_t base = (size_t)m * nc;
+        if (kind == 0) {
+            rho.psi[base + 4 + row] = t;
+            if (row < 4) rho.psi[base + row] = make_double2(0.0, 0.0);
+        } else if (kind == 1) {
+            rho.th[base + 2 + row] = t;
+            if (row < 2) rho.th[base + row] = make_double2(0.0, 0.0);
+        } else {
+            rho.u[2 + row] = t.x;
+            if (row < 2) rho.u[row] = 0.0;
         }
-        rho.th[(size_t)m * nc + 2 + r] = acc;
-        if (r < 2) rho.th[(size_t)m * nc + r] = make_double2(0.0, 0.0);
-    } else if (m == 0 && row < np + 2 * nt) {
-        const int r = row - np - nt;
-        const double* g = A.Wu + r;
-        double acc = 0.0;
-        for (int j = 0; j < nc; ++j) acc = fma(__ldg(&g[(size_t)j * nt]), lu[j], acc);
-        rho.u[2 + r] = acc;
-        if (r < 2) rho.u[r] = 0.0;
     }
 }
 
@@ -498,7 +527,20 @@ __global__ void k_vec_add(int M, int nc, VecSet a, VecSet b) {
     }
 }
 
+__global__ void k_ra_accumulate(const double* __restrict__ ra, int M, double* __restrict__ acc) {
+    double t = 0.0;
+    for (int m = threadIdx.x; m < M; m += 32) t += ra[m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *acc += t;
+}
+
 }  // namespace
+
+cudaError_t launch_ra_accumulate(const double* ra, int M, double* acc, cudaStream_t st) {
+    k_ra_accumulate<<<1, 32, 0, st>>>(ra, M, acc);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_vec_add(const StepParams& P, VecSet a, VecSet b, cudaStream_t st) {
     k_vec_add<<<P.M, NTA, 0, st>>>(P.M, P.nc, a, b);
@@ -511,7 +553,7 @@ size_t smem_adj_grid_to_spec(const StepParams& P) {
 }
 size_t smem_adj_spec_to_grid(const StepParams& P) {
     const int L = 2 * P.K;
-    return sizeof(double2) * (2 * adj_batch(L) * L + 5 * P.n_r);
+    return sizeof(double2) * (2 * adj_batch4(L) * L + 5 * P.n_r);
 }
 
 cudaError_t launch_adj_explicit(const StepParams& P, VecSet w, VecSet y, VecSet lam, const double2* G1, double2* Gb2,
@@ -537,9 +579,10 @@ cudaError_t launch_adj_explicit(const StepParams& P, VecSet w, VecSet y, VecSet 
 }
 
 cudaError_t launch_adj_solve(const StepParams& P, const AdjFactors& A, VecSet lam, VecSet rho, cudaStream_t st) {
-    const size_t sm = sizeof(double2) * 2 * P.nc + sizeof(double) * P.nc;
-    dim3 grid(P.M, (3 * P.nc + NTA - 1) / NTA);
-    k_adj_solve<<<grid, NTA, sm, st>>>(P, A, lam, rho);
+    const size_t sm = sizeof(double2) * P.nc;
+    const int tp = (P.nc - 4 + ASR - 1) / ASR, tt = (P.nc - 2 + ASR - 1) / ASR;
+    dim3 grid(P.M, tp + 2 * tt);
+    k_adj_solve<<<grid, ASR * ASS, sm, st>>>(P, A, lam, rho);
     return cudaGetLastError();
 }
 

@@ -151,6 +151,8 @@ cudaError_t launch_adj_solve(const StepParams& P, const AdjFactors& A, VecSet la
 cudaError_t launch_adj_apply(const StepParams& P, VecSet g, VecSet rho, VecSet rho_next, VecSet lam, VecSet w,
                              double dt, double c, double c2, cudaStream_t st);
 cudaError_t launch_vec_add(const StepParams& P, VecSet a, VecSet b, cudaStream_t st);
+// *acc += sum_m ra[m] (m < M, a fixed summation order), one warp
+cudaError_t launch_ra_accumulate(const double* ra, int M, double* acc, cudaStream_t st);
 cudaError_t launch_diagnostics(const StepParams& P, const double2* G1, const double* q, double* mode_sums,
                                double* radius_max, cudaStream_t st);
 
@@ -162,6 +164,8 @@ bool make_fft_plan(int L, FftPlan& pl);
 std::vector<double2> fft_twiddles(int L);
 
 size_t smem_spec_to_grid(const StepParams& P);
+size_t smem_adj_grid_to_spec(const StepParams& P);
+size_t smem_adj_spec_to_grid(const StepParams& P);
 size_t smem_phi_products(const StepParams& P);
 size_t smem_grid_to_spec(const StepParams& P);
 size_t smem_solve(const StepParams& P);

@@ -120,13 +120,17 @@ def test_adjoint_gradient_matches_finite_differences_n257():
     assert abs(fdR - float(r.grad)) <= 1e-4 * abs(float(r.grad))
 
 
-def test_adjoint_run_matches_oracle_n257():
+@pytest.mark.parametrize("dd", [1, 0])
+def test_adjoint_run_matches_oracle_n257(dd):
     """Three CNAB2 steps on the adjoint workload's grid (257, 768), E = 1e-5,
-    Ra = 5 Ra_c, dt = 1e-7, from a state with all fields nonzero."""
-    from paper_1902_07092_gb300.binding import Solver
+    Ra = 5 Ra_c, dt = 1e-7, from a state with all fields nonzero; the segments
+    recomputed with either form of the forward azimuthal stage (option
+    azimuthal_dd)."""
+    from paper_1902_07092_gb300.binding import Solver, pizza_set_option
     n_r, n_phi, E, dt, K = 257, 768, 1e-5, 1e-7, 3
     Ra = 5.0 * critical_rayleigh(E)
     gpu = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "CNAB2", dt)
+    pizza_set_option(gpu.ctx, "azimuthal_dd", dd)
     ora = IntegrationStepper(n_r, n_phi, E, Ra, 1.0, 0.35, "CNAB2", dt)
     rng = np.random.default_rng(8)
     y0 = _rand(rng, gpu.M, gpu.n_c, 1e-3)
@@ -142,7 +146,7 @@ def test_adjoint_run_matches_oracle_n257():
         dRa = gpu.adjoint_step(g_theta=g)
     ps, th, u = gpu.get_adjoint()
     errs = (rel_l2(ps, lam_ref[0]), rel_l2(th, lam_ref[1]), rel_l2(u, lam_ref[2]))
-    print("adjoint run n257: psi %.2e theta %.2e u %.2e dRa %.6e vs %.6e" % (errs + (dRa, dRa_ref)))
+    print("adjoint run n257 dd=%d: psi %.2e theta %.2e u %.2e dRa %.6e vs %.6e" % ((dd,) + errs + (dRa, dRa_ref)))
     assert errs[0] <= 8 * float(n_r) ** 4 * EPS   # the Psi_bar bound of the explicit adjoint
     assert max(errs[1:]) <= 1e-8
     assert abs(dRa - dRa_ref) <= 1e-8 * abs(dRa_ref)
