@@ -82,8 +82,14 @@ def algorithmic_flops(n_r, n_phi, scheme, radial="integration"):
     band = lambda h: 4.0 * (2 * h + 1) * nc            # real band x complex vector
     f_g2s = M * (6 * dct + 30.0 * n_r + band(8) + 2 * band(4))
     np_, nt = nc - 4, nc - 2
-    solve_psi = np_ * (8 * 8 + 8 * 8 + 6) + 4 * 4 * np_ + 4 * 8 * np_   # LU sweeps + Schur
-    solve_th = nt * (4 * 4 + 4 * 4 + 2) + 2 * 4 * nt + 2 * 4 * nt
+    if radial == "galerkin":
+        # pivoted band sweeps: 8 + 20 complex multiply-adds per Psi row (8 flops),
+        # 4 + 10 real x complex per temperature row (4 flops); the basis expansion
+        solve_psi = np_ * (8 + 20 + 1) * 8.0 + 4.0 * 5 * nc
+        solve_th = nt * (4 + 10 + 1) * 4.0 + 4.0 * 2 * nc
+    else:
+        solve_psi = np_ * (8 * 8 + 8 * 8 + 6) + 4 * 4 * np_ + 4 * 8 * np_   # LU sweeps + Schur
+        solve_th = nt * (4 * 4 + 4 * 4 + 2) + 2 * 4 * nt + 2 * 4 * nt
     epi = band(8) * 2 + band(6) * 3 + band(8) + band(4) + 2 * band(2)
     f_solve = M * (solve_psi + solve_th + 6 * 8.0 * nc + epi)
     return dict(zip(KERNELS, (f_s2g, f_phi, f_g2s, f_solve)))
@@ -95,6 +101,7 @@ NCU_TRAFFIC = {
     ("sparse_n257_p768", "solve"): (44.34e6 + 0.23e6, "profiles/imex_step_kernels_n257_p768.md"),
     ("large_n2049_p6144", "solve"): (4145.9e6 + 228.4e6, "profiles/solve_kernel_n2049_p6144.md"),
     ("coll_n257_p768", "solve"): (735.4e6 + 6.9e6, "profiles/collocation_step_kernels_n257_p768.md"),
+    ("galerkin_n257_p768", "solve"): (34.58e6 + 0.003e6, "profiles/galerkin_step_kernels_n257_p768.md"),
 }
 
 
@@ -153,6 +160,7 @@ class ClockSampler:
 def oracle_sample(wl, Ra, budget_s, max_steps):
     """Time the oracle (as it stands) on the workload: steps until budget_s."""
     from oracle.collocation import CollocationStepper
+    from oracle.galerkin import GalerkinStepper
     from oracle.stepper import IntegrationStepper
     n_r, n_phi = wl["n_r"], wl["n_phi"]
     nc = inputs.n_c_of(wl)
@@ -163,7 +171,8 @@ def oracle_sample(wl, Ra, budget_s, max_steps):
         st = CollocationStepper(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
         st.set_state(z, z.copy(), th, zu)
     else:
-        st = IntegrationStepper(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
+        cls = GalerkinStepper if wl.get("radial") == "galerkin" else IntegrationStepper
+        st = cls(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
         st.set_state(z, th, zu)
     st.step()                                  # builds the LU factors (set-up, untimed)
     setup = time.perf_counter() - t0
@@ -233,8 +242,8 @@ def config_of(args, wl, Ra):
     return {"workload": args.workload, "n_r": wl["n_r"], "n_phi": wl["n_phi"], "N_m": wl["n_phi"] // 3,
             "N_c": inputs.n_c_of(wl), "E": wl["E"], "Ra": Ra, "Ra_over_Ra_c": wl["ra_factor"],
             "Pr": wl["Pr"], "radius_ratio": wl["eta"], "scheme": wl["scheme"], "dt": wl["dt"],
-            "radial": ("chebyshev-collocation" if wl.get("radial") == "collocation"
-                       else "chebyshev-integration-tau"),
+            "radial": {"collocation": "chebyshev-collocation", "galerkin": "chebyshev-integration-galerkin"}.get(
+                wl.get("radial"), "chebyshev-integration-tau"),
             "l2": "flushed (256 MiB write) between timed steps",
             "parallelism": "replicas" if args.gpus > 1 else "single",
             "precision": ("fp64" if getattr(args, "precision", "fp64") == "fp64"

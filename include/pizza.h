@@ -83,10 +83,16 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *   "dt"     time step > 0; invalidates the factored implicit operators, which
  *            are rebuilt on the next step;
  *   "radial" 1 = Chebyshev integration with tau rows (Section 3.2, the default),
+ *            2 = Chebyshev integration solved in Galerkin bases (Appendix B: the
+ *            streamfunction in phi_n = sum_i gamma_i^n T_{n+i}, temperature and
+ *            zonal flow in T_{n+2} - T_n; the square integrated systems, 8 and 12
+ *            diagonals below and above for Psi, 4 and 6 otherwise, by banded LU
+ *            with partial pivoting; the same discrete solution as 1),
  *            0 = Chebyshev collocation (Section 3.1; n_r <= PIZZA_COLL_MAX_NR,
- *            else PIZZA_EUNSUPPORTED).  Changing it discards the factored
- *            operators and resets the state to zero and N_c to the new
- *            formulation's value; any other value returns PIZZA_EUNSUPPORTED;
+ *            else PIZZA_EUNSUPPORTED).  Changing between 1 and 2 discards the
+ *            factored operators and keeps the state; changing to or from 0 also
+ *            resets the state to zero and N_c to the new formulation's value; any
+ *            other value returns PIZZA_EUNSUPPORTED;
  *   "precision" 0 = FP64 throughout (default); 1 = mixed: the explicit stage
  *            (Chebyshev and Fourier transforms, grid products, flux divergences)
  *            in FP32 on FP32 grid arrays, while the state, the time-scheme

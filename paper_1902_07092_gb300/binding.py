@@ -272,18 +272,19 @@ def pizza_last_error(ctx=None):
 class Solver:
     """Convenience owner of one context with numpy host arrays in the C layouts
     (complex128 [N_m+1][N_c] for theta and Psi, float64 [N_c] for u_bar).
-    ``radial`` selects the formulation: "integration" (Section 3.2, default) or
-    "collocation" (Section 3.1; psi instead of Psi, N_c = n_r).  ``pumping_eps``
+    ``radial`` selects the formulation: "integration" (Section 3.2, default; tau
+    rows), "galerkin" (the same unknowns solved in the Galerkin bases of Appendix
+    B) or "collocation" (Section 3.1; psi instead of Psi, N_c = n_r).  ``pumping_eps``
     turns Ekman pumping on: the approximate F_eps of Eq. approx_pump with that eps
     (integration) or the exact term, implicit (collocation)."""
 
     def __init__(self, n_r, n_phi, E, Ra, Pr, radius_ratio, scheme, dt=None, radial="integration",
                  pumping_eps=None, buoy_implicit=False):
         self.ctx = pizza_init(n_r, n_phi, E, Ra, Pr, radius_ratio, scheme)
-        if radial not in ("integration", "collocation"):
+        if radial not in ("integration", "collocation", "galerkin"):
             raise ValueError(radial)
-        if radial == "collocation":
-            pizza_set_option(self.ctx, "radial", 0)
+        if radial != "integration":
+            pizza_set_option(self.ctx, "radial", 0 if radial == "collocation" else 2)
         if pumping_eps is not None:
             pizza_set_option(self.ctx, "pumping_eps", pumping_eps)
         if buoy_implicit:

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <algorithm>
 #include <thread>
@@ -95,6 +96,8 @@ struct pizza_ctx {
     std::vector<double> s_host, ds_host;
     // Chebyshev-collocation formulation (option "radial" = 0)
     bool coll = false;
+    // Galerkin bases for the integration formulation's solves (option "radial" = 2)
+    bool gal = false;
     std::vector<void*> vec_allocs;     // state and work vectors (re-made when the formulation changes)
     std::vector<double> coll_d1_row0;  // d/ds at s_o on grid values
     double* grid_out = nullptr;        // pizza_get_grid staging, 4 x n_r x n_phi
@@ -332,6 +335,129 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
     return PIZZA_OK;
 }
 
+// Factorisation (host) of the Galerkin-basis systems (Appendix B) for one
+// implicit weight: the integrated rows of the tau operators (the same entries as
+// build_factors) times the stencils and 1/(C w_n), in band rows, then banded LU
+// with partial pivoting.
+int build_galerkin_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
+                           std::vector<void*>& al) {
+    const int M = ctx->M, nc = ctx->nc, np = nc - 4, nt = nc - 2;
+    const double gdt = gamma * ctx->dt;
+    if (np < 1) return fail(ctx, PIZZA_EINVAL, "too few coefficients for the Galerkin bases");
+    const double cn = std::sqrt(2.0 / (ctx->n_r - 1));
+    auto ihs = [&](int j) { return (j == 0 ? 2.0 : 1.0) / cn; };  // 1/(C w_j)
+    std::vector<double> gam((size_t)np * 5);
+    for (int n = 0; n < np; ++n) galerkin_gamma(n, &gam[(size_t)n * 5]);
+    auto get = [&](int id, int k, int n) -> double {
+        const int h = op_h(id);
+        const int d = n - k + h;
+        if (n < 0 || n >= nc || d < 0 || d > 2 * h) return 0.0;
+        return H.band[id][(size_t)k * (2 * h + 1) + d];
+    };
+    std::vector<double2> hpL((size_t)M * np * 8), hpU((size_t)M * np * 21);
+    std::vector<double> hpR((size_t)M * np), htL((size_t)M * nt * 4), htU((size_t)M * nt * 12), htR((size_t)M * nt);
+    std::vector<unsigned char> hpP((size_t)M * np), htP((size_t)M * nt);
+    std::vector<int> bad(M, 0);
+    // Dirichlet system of rows k = i + 2 of an operator L(k, j): band rows of
+    // G(i, n) = L(i+2, n+2)/(C w_{n+2}) - L(i+2, n)/(C w_n), 4 below, 6 above
+    auto dir_band = [&](const std::function<double(int, int)>& L) {
+        std::vector<double> b((size_t)nt * 11, 0.0);
+        for (int i = 0; i < nt; ++i)
+            for (int d = 0; d < 11; ++d) {
+                const int n = i - 4 + d;
+                if (n >= 0 && n < nt) b[(size_t)i * 11 + d] = L(i + 2, n + 2) * ihs(n + 2) - L(i + 2, n) * ihs(n);
+            }
+        return b;
+    };
+    auto work = [&](int m0, int m1) {
+        std::vector<cplx> bp((size_t)np * 21), Lm, Uc;
+        std::vector<double> rs, Lt, Ut;
+        std::vector<unsigned char> pv;
+        for (int m = m0; m < m1; ++m) {
+            const double mu = (double)m * m, dm = (double)m;
+            if (m > 0) {
+                // G(i, n) = sum_q L(i+4, n+q) gamma_q^n / (C w_{n+q}), 8 below, 12 above
+                auto L = [&](int k, int j) -> cplx {
+                    const double a = get(OP_A0, k, j) + mu * get(OP_A2, k, j);
+                    const double b = get(OP_B0, k, j) + mu * (get(OP_B2, k, j) + mu * get(OP_B4, k, j));
+                    return cplx(a - gdt * b, -gdt * 2.0 * dm / ctx->E * get(OP_C, k, j));
+                };
+                for (int i = 0; i < np; ++i)
+                    for (int d = 0; d < 21; ++d) {
+                        const int n = i - 8 + d;
+                        cplx v(0.0, 0.0);
+                        if (n >= 0 && n < np)
+                            for (int q = 0; q < 5; ++q) v += L(i + 4, n + q) * (gam[(size_t)n * 5 + q] * ihs(n + q));
+                        bp[(size_t)i * 21 + d] = v;
+                    }
+                if (!band_lu_pivot(np, 8, 12, bp, Lm, Uc, pv, rs)) {
+                    bad[m] = 1;
+                    continue;
+                }
+                for (size_t i = 0; i < Lm.size(); ++i)
+                    hpL[(size_t)m * np * 8 + i] = make_double2(Lm[i].real(), Lm[i].imag());
+                for (size_t i = 0; i < Uc.size(); ++i)
+                    hpU[(size_t)m * np * 21 + i] = make_double2(Uc[i].real(), Uc[i].imag());
+                std::copy(pv.begin(), pv.end(), hpP.begin() + (size_t)m * np);
+                std::copy(rs.begin(), rs.end(), hpR.begin() + (size_t)m * np);
+            }
+            const auto bt = dir_band([&](int k, int j) {
+                return get(OP_D, k, j) - gdt * (get(OP_F0, k, j) + mu * get(OP_F2, k, j)) / ctx->Pr;
+            });
+            if (!band_lu_pivot(nt, 4, 6, bt, Lt, Ut, pv, rs)) {
+                bad[m] = 1;
+                continue;
+            }
+            std::copy(Lt.begin(), Lt.end(), htL.begin() + (size_t)m * nt * 4);
+            for (int i = 0; i < nt; ++i)  // rows padded to 12 (whole 16-byte pieces)
+                std::copy(Ut.begin() + (size_t)i * 11, Ut.begin() + (size_t)(i + 1) * 11,
+                          htU.begin() + ((size_t)m * nt + i) * 12);
+            std::copy(pv.begin(), pv.end(), htP.begin() + (size_t)m * nt);
+            std::copy(rs.begin(), rs.end(), htR.begin() + (size_t)m * nt);
+        }
+    };
+    unsigned nthr = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    const int chunk = (M + (int)nthr - 1) / (int)nthr;
+    for (unsigned t = 0; t < nthr; ++t) {
+        int a = (int)t * chunk, b = std::min(M, a + chunk);
+        if (a < b) th.emplace_back(work, a, b);
+    }
+    for (auto& t : th) t.join();
+    for (int m = 0; m < M; ++m)
+        if (bad[m]) return fail(ctx, PIZZA_EINVAL, "Galerkin system of mode m=%d is singular", m);
+    std::vector<double> uL, uU, uR;
+    std::vector<unsigned char> uP;
+    const auto bu = dir_band([&](int k, int j) { return get(OP_D, k, j) - gdt * get(OP_EZ, k, j); });
+    if (!band_lu_pivot(nt, 4, 6, bu, uL, uU, uP, uR)) return fail(ctx, PIZZA_EINVAL, "zonal-flow Galerkin system singular");
+
+    F.gdt = gdt;
+    F.gal = 1;
+#define UPLOAD(dst, T, hv)                                                                        \
+    do {                                                                                          \
+        dst = dalloc<T>(ctx, (hv).size(), al);                                                    \
+        if (!dst) return fail(ctx, PIZZA_ENOMEM, "device allocation of factors failed");          \
+        CK(cudaMemcpy(dst, (hv).data(), (hv).size() * sizeof(T), cudaMemcpyHostToDevice));       \
+    } while (0)
+    UPLOAD(F.gpL, double2, hpL);
+    UPLOAD(F.gpU, double2, hpU);
+    UPLOAD(F.gpR, double, hpR);
+    UPLOAD(F.gpPiv, unsigned char, hpP);
+    UPLOAD(F.gtL, double, htL);
+    UPLOAD(F.gtU, double, htU);
+    UPLOAD(F.gtR, double, htR);
+    UPLOAD(F.gtPiv, unsigned char, htP);
+    UPLOAD(F.guL, double, uL);
+    std::vector<double> uU12((size_t)nt * 12, 0.0);
+    for (int i = 0; i < nt; ++i) std::copy(uU.begin() + (size_t)i * 11, uU.begin() + (size_t)(i + 1) * 11, uU12.begin() + (size_t)i * 12);
+    UPLOAD(F.guU, double, uU12);
+    UPLOAD(F.guR, double, uR);
+    UPLOAD(F.guPiv, unsigned char, uP);
+    UPLOAD(F.gam, double, gam);
+#undef UPLOAD
+    return PIZZA_OK;
+}
+
 HostOps host_ops_of(pizza_ctx* ctx) {
     HostOps H;
     Geom g = make_geom(ctx->eta);
@@ -366,7 +492,7 @@ int ensure_factors(pizza_ctx* ctx) {
     for (double g : ctx->gammas) {
         DevFactors F{};
         std::vector<void*> al;
-        int rc = build_factors(ctx, H, g, F, al);
+        int rc = ctx->gal ? build_galerkin_factors(ctx, H, g, F, al) : build_factors(ctx, H, g, F, al);
         ctx->factor_allocs.push_back(al);
         if (rc != PIZZA_OK) {
             free_factors(ctx);
@@ -1286,10 +1412,17 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
         return PIZZA_OK;
     }
     if (std::strcmp(key, "radial") == 0) {
-        if (value != 0.0 && value != 1.0)
-            return fail(ctx, PIZZA_EUNSUPPORTED, "radial must be 0 (collocation) or 1 (integration)");
-        const bool coll = (value == 0.0);
-        if (coll == ctx->coll) return PIZZA_OK;
+        if (value != 0.0 && value != 1.0 && value != 2.0)
+            return fail(ctx, PIZZA_EUNSUPPORTED,
+                        "radial must be 0 (collocation), 1 (integration, tau) or 2 (integration, Galerkin)");
+        const bool coll = (value == 0.0), gal = (value == 2.0);
+        if (coll == ctx->coll && gal == ctx->gal) return PIZZA_OK;
+        if (coll == ctx->coll) {  // tau <-> Galerkin: same unknowns, new factors
+            cudaStreamSynchronize(ctx->stream);
+            free_factors(ctx);
+            ctx->gal = gal;
+            return PIZZA_OK;
+        }
         if (coll && ctx->P.fp32)
             return fail(ctx, PIZZA_EUNSUPPORTED, "mixed precision is implemented for the integration formulation");
         if (coll && ctx->n_r > PIZZA_COLL_MAX_NR)
@@ -1297,6 +1430,7 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
         cudaStreamSynchronize(ctx->stream);
         free_factors(ctx);
         ctx->coll = coll;
+        ctx->gal = gal;
         ctx->P.coll = coll ? 1 : 0;
         ctx->nc = coll ? ctx->n_r : (2 * (ctx->n_r - 1)) / 3;
         ctx->P.nc = ctx->nc;

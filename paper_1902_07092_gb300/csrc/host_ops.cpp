@@ -553,6 +553,70 @@ bool block_lu_twisted(const std::vector<T>& band, int n_c, int h, int p, std::ve
     return true;
 }
 
+void galerkin_gamma(int n, double g[5]) {
+    const double x = (double)n;
+    const double den = 2 * x * x * x * x + 20 * x * x * x + 78 * x * x + 140 * x + 95;
+    const double q = x * x + 4 * x + 5;
+    g[0] = 1.0;
+    g[1] = 8 * (x + 1) * q / den;
+    g[2] = -2 * (x + 2) * (2 * x * x * x * x + 16 * x * x * x + 58 * x * x + 104 * x + 75) / ((x + 3) * den);
+    g[3] = -8 * (x + 1) * q / den;
+    g[4] = (x + 1) * (2 * x * x * x * x + 12 * x * x * x + 30 * x * x + 36 * x + 15) / ((x + 3) * den);
+}
+
+template <class T>
+bool band_lu_pivot(int n, int kl, int ku, const std::vector<T>& band, std::vector<T>& Lm, std::vector<T>& Ucol,
+                   std::vector<unsigned char>& piv, std::vector<double>& rs) {
+    // working rows of width 2 kl + ku + 1: row i holds columns i - kl .. i + kl + ku
+    // (the last kl for the fill-in of the interchanges), W[i][c - i + kl]
+    const int wb = kl + ku + 1, ww = 2 * kl + ku + 1, kk = kl + ku;
+    std::vector<T> W((size_t)n * ww, T(0));
+    rs.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double mx = 0.0;
+        for (int d = 0; d < wb; ++d) mx = std::max(mx, std::abs(band[(size_t)i * wb + d]));
+        if (!(mx > 0.0)) return false;
+        rs[i] = 1.0 / mx;
+        for (int d = 0; d < wb; ++d) W[(size_t)i * ww + d] = band[(size_t)i * wb + d] * rs[i];
+    }
+    auto at = [&](int i, int c) -> T& { return W[(size_t)i * ww + (c - i + kl)]; };
+    Lm.assign((size_t)n * kl, T(0));
+    piv.assign(n, 0);
+    for (int j = 0; j < n; ++j) {
+        const int last = std::min(n - 1, j + kl), cend = std::min(n - 1, j + kk);
+        int p = j;
+        double best = std::abs(at(j, j));
+        for (int i = j + 1; i <= last; ++i)
+            if (std::abs(at(i, j)) > best) {
+                best = std::abs(at(i, j));
+                p = i;
+            }
+        if (!(best > 0.0)) return false;
+        piv[j] = (unsigned char)(p - j);
+        if (p != j)
+            for (int c = j; c <= cend; ++c) std::swap(at(j, c), at(p, c));
+        const T d = at(j, j);
+        for (int i = j + 1; i <= last; ++i) {
+            const T l = at(i, j) / d;
+            Lm[(size_t)j * kl + (i - j - 1)] = l;
+            at(i, j) = T(0);
+            for (int c = j + 1; c <= cend; ++c) at(i, c) -= l * at(j, c);
+        }
+    }
+    Ucol.assign((size_t)n * (kk + 1), T(0));
+    for (int i = 0; i < n; ++i) {
+        const T rd = T(1) / at(i, i);
+        Ucol[(size_t)i * (kk + 1)] = rd;
+        for (int t = 1; t <= kk && i - t >= 0; ++t) Ucol[(size_t)i * (kk + 1) + t] = at(i - t, i) * rd;
+    }
+    return true;
+}
+
+template bool band_lu_pivot<double>(int, int, int, const std::vector<double>&, std::vector<double>&,
+                                    std::vector<double>&, std::vector<unsigned char>&, std::vector<double>&);
+template bool band_lu_pivot<cplx>(int, int, int, const std::vector<cplx>&, std::vector<cplx>&, std::vector<cplx>&,
+                                  std::vector<unsigned char>&, std::vector<double>&);
+
 template bool block_lu_twisted<double>(const std::vector<double>&, int, int, int, std::vector<double>&);
 template bool block_lu_twisted<cplx>(const std::vector<cplx>&, int, int, int, std::vector<cplx>&);
 template bool block_lu<double>(const std::vector<double>&, int, int, int, std::vector<double>&);

@@ -82,6 +82,27 @@ bool factor_bordered(const std::vector<T>& mass_lin_band, int n_c, int h,
                      const std::vector<double>& tau, int p, Bordered<T>& out);
 
 // ---------------------------------------------------------------------------
+// Galerkin bases (Appendix B).  gamma_0..gamma_4 of the streamfunction basis
+// function phi_n = sum_i gamma_i T_{n+i} (gamma_0 = 1), which meets the four
+// boundary conditions of the tau rows; the Dirichlet basis is T_{n+2} - T_n.
+void galerkin_gamma(int n, double g[5]);
+
+// Banded LU with partial pivoting of an n x n matrix with kl diagonals below and
+// ku above, given by rows: band[i*(kl+ku+1) + (c - i + kl)] = G(i, c) for
+// i - kl <= c <= i + ku.  The row interchanges stay interleaved with the
+// elimination (as in LAPACK's band factorisation): at column j the row j + piv[j]
+// (piv[j] in 0..kl) is swapped with row j, then rows j+1..j+kl are eliminated with
+// the multipliers Lm[j*kl + t] (row j+1+t); U gains up to kl + ku diagonals above.
+// Output per column i of U: Ucol[i*(kl+ku+1)] = 1/U(i,i) and
+// Ucol[i*(kl+ku+1) + t] = U(i-t, i)/U(i,i) (t = 1..kl+ku, zero above row 0), i.e.
+// the unit upper factor U D^{-1} with x = D^{-1} z', z' = (U D^{-1})^{-1} z.
+// Every row is first scaled to unit maximum (rs[i] = 1/max_c |G(i, c)|; the
+// right-hand side takes the same scaling).  Returns false on a zero pivot.
+template <class T>
+bool band_lu_pivot(int n, int kl, int ku, const std::vector<T>& band, std::vector<T>& Lm, std::vector<T>& Ucol,
+                   std::vector<unsigned char>& piv, std::vector<double>& rs);
+
+// ---------------------------------------------------------------------------
 // Chebyshev collocation (Section 3.1), fields held as Gauss-Lobatto grid values.
 // ---------------------------------------------------------------------------
 struct CollGrid {

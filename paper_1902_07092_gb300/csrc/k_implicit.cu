@@ -836,6 +836,236 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     }
 }
 
+// ---------------------------------------------------------------------------
+// Galerkin-basis solve (Appendix B; option "radial" = 2).  Per mode the square
+// systems P_4 (A - g dt B) S_Psi x = P_4 r and P_2 (D - g dt F/Pr) S_D x = P_2 r
+// (and the zonal-flow one) are solved with their banded LU factors with partial
+// pivoting (host_ops.h, band_lu_pivot), then expanded to Chebyshev coefficients:
+// f_hat_k = (1/(C w_k)) sum_i S(k, n) x_n.  The same discrete problem as the tau
+// solve, without border rows, Schur steps or refinement.
+//
+// A system is solved by one warp in two sweeps of n dependent steps each.  The
+// rows the next steps touch sit in a register window across the lanes:
+//   forward (L, interchanges interleaved): lanes 0..KL hold b[j..j+KL]; step j
+//     swaps row j with row j + piv[j], lanes 1..KL subtract l_t b_j, the window
+//     shifts down one lane and lane KL takes b[j+KL+1];
+//   backward (U, column by column, with U's columns divided by their diagonal
+//     entries): lanes 0..KK hold y[i..i-KK]; step i takes y_i final, lanes
+//     1..KK subtract (U(i-t, i)/U_ii) y_i, the window shifts; x_i = y_i / U_ii
+//     is formed afterwards by the whole CTA (off the chain).
+// A step's chain is two shuffles and one or two dependent FMAs; the factors are
+// staged through shared memory in chunks of GCH rows by asynchronous copies, the
+// next chunk in flight while the current one is used.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double shfl_down_x(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double2 shfl_down_x(double2 v) {
+    return make_double2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+
+// Asynchronous 16-byte global -> shared copies (cp.async): a lane's copies
+// complete at cp.async.wait_group; __syncwarp then publishes them to the warp.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+constexpr int GCH = 32;  // rows of factors staged per chunk
+
+// Copy rows [r0, r1) of a row-major factor array (W entries of TF per row, W *
+// sizeof(TF) a multiple of 16 bytes, the array 16-byte aligned) to dst, by one warp.
+template <int W, class TF>
+__device__ __forceinline__ void stage_rows(TF* dst, const TF* src, int r0, int r1) {
+    constexpr int PER = W * (int)sizeof(TF) / 16;
+    static_assert(PER * 16 == W * (int)sizeof(TF), "factor rows must be whole 16-byte pieces");
+    const char* s = reinterpret_cast<const char*>(src + (size_t)r0 * W);
+    char* d = reinterpret_cast<char*>(dst);
+    for (int q = threadIdx.x & 31; q < (r1 - r0) * PER; q += 32) cp_async16(d + 16 * q, s + 16 * q);
+}
+
+// b: right-hand side (n entries, row-scaled), overwritten by the forward result;
+// x: y = U_ii x_i (n entries; the caller multiplies by Uc[i][0] = 1/U_ii).
+// Lm [n][KL], Uc [n][UW] (UW >= KK+1, padded to whole 16-byte rows):
+// band_lu_pivot's factors; pv: the pivot offsets in shared memory.
+// stg: shared staging of 2 GCH rows of Uc (which also holds 2 GCH rows of Lm):
+// chunk k+1 of the factors is copied while chunk k is used.
+template <int KL, int KK, int UW, class TF, class TX>
+__device__ void warp_band_solve(TX* b, TX* x, int n, const TF* __restrict__ Lm, const TF* __restrict__ Uc,
+                                const unsigned char* pv, TF* stg) {
+    static_assert(KK < 32 && KL <= KK && UW >= KK + 1, "window wider than a warp");
+    const int lane = threadIdx.x & 31;
+    const bool lrow = lane >= 1 && lane <= KL, urow = lane >= 1 && lane <= KK;
+    // forward: L z = P b
+    TX w = (lane <= KL && lane < n) ? b[lane] : zero<TX>();
+    stage_rows<KL>(stg, Lm, 0, min(n, GCH));
+    cp_async_commit();
+    for (int c0 = 0, k = 0; c0 < n; c0 += GCH, k ^= 1) {
+        const int c1 = min(n, c0 + GCH);
+        if (c1 < n) stage_rows<KL>(stg + (k ^ 1) * GCH * KL, Lm, c1, min(n, c1 + GCH));
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        const TF* sl = stg + k * GCH * KL;
+        for (int j = c0; j < c1; ++j) {
+            const int p = pv[j];
+            const TF l = lrow ? sl[(j - c0) * KL + lane - 1] : zero<TF>();
+            const TX in = (lane == KL && j + KL + 1 < n) ? b[j + KL + 1] : zero<TX>();
+            const TX bj = shfl_idx(w, p);
+            const TX w0 = shfl_idx(w, 0);
+            if (lane == p) w = w0;
+            if (lrow) w = fms_x(l, bj, w);
+            if (lane == 0) b[j] = bj;
+            w = shfl_down_x(w);
+            if (lane == KL) w = in;
+        }
+        __syncwarp();
+    }
+    // backward: U x = z, chunks of rows taken from the bottom
+    TX v = (lane <= KK && n - 1 - lane >= 0) ? b[n - 1 - lane] : zero<TX>();
+    stage_rows<UW>(stg, Uc, max(0, n - GCH), n);
+    cp_async_commit();
+    for (int c1 = n, k = 0; c1 > 0; c1 -= GCH, k ^= 1) {
+        const int c0 = max(0, c1 - GCH);
+        if (c0 > 0) stage_rows<UW>(stg + (k ^ 1) * GCH * UW, Uc, max(0, c0 - GCH), c0);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        const TF* su = stg + k * GCH * UW;
+        for (int i = c1 - 1; i >= c0; --i) {
+            const TF u = urow ? su[(i - c0) * UW + lane] : zero<TF>();
+            const TX in2 = (lane == KK && i - KK - 1 >= 0) ? b[i - KK - 1] : zero<TX>();
+            const TX yi = shfl_idx(v, 0);
+            if (lane == 0) x[i] = yi;
+            if (urow) v = fms_x(u, yi, v);
+            v = shfl_down_x(v);
+            if (lane == KK) v = in2;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS_S) k_solve_galerkin(StepParams P, RhsSpec R, DevFactors F, VecSet y_out,
+                                                               VecSet mass_out, VecSet imp_out, int want_mass,
+                                                               int want_imp) {
+    extern __shared__ double2 sm[];
+    const int nc = P.nc, m = blockIdx.x;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5;
+    const int np = nc - 4, nt = nc - 2;
+    SolveSmem s = carve<1>(sm, nc);
+    const bool has_u = (m == 0);
+    double2 *pf = s.pf[0], *tf = s.tf[0], *px = s.px[0], *tx = s.tx[0], *xp = s.pw[0], *xt = s.tw[0];
+    double* xu = reinterpret_cast<double*>(s.pd[0]);
+    // after the FP64 solve arrays (over the FP32 refinement arrays of the tau
+    // path, unused here): factor staging (2 GCH rows per system) and pivots
+    double2* stp = sm + 8 * round8(nc);
+    double* stt = reinterpret_cast<double*>(stp + 2 * GCH * 21);
+    double* stu = stt + 2 * GCH * 12;
+    unsigned char* pvp = reinterpret_cast<unsigned char*>(stu + 2 * GCH * 12);
+    unsigned char* pvt = pvp + round8(nc);
+    unsigned char* pvu = pvt + round8(nc);
+    for (int n = tid; n < nt; n += nth) {
+        if (n < np && m > 0) pvp[n] = F.gpPiv[(size_t)m * np + n];
+        pvt[n] = F.gtPiv[(size_t)m * nt + n];
+        if (has_u) pvu[n] = F.guPiv[n];
+    }
+
+    // right-hand side sum_t c_t V_t; the rows of the integrated equations
+    // (k >= 4 for Psi, k >= 2 otherwise) times the row scales of the factors
+    for (int n = tid; n < nc; n += nth) {
+        double2 ap = make_double2(0.0, 0.0), at = make_double2(0.0, 0.0);
+        double au = 0.0;
+        for (int t = 0; t < R.nterms; ++t) {
+            const double c = R.t[t].c;
+            const double2 vp = R.t[t].v.psi[(size_t)m * nc + n];
+            const double2 vt = R.t[t].v.th[(size_t)m * nc + n];
+            ap.x = fma(c, vp.x, ap.x);
+            ap.y = fma(c, vp.y, ap.y);
+            at.x = fma(c, vt.x, at.x);
+            at.y = fma(c, vt.y, at.y);
+            if (has_u) au = fma(c, R.t[t].v.u[n], au);
+        }
+        pf[n] = (n < 4 || m == 0) ? make_double2(0.0, 0.0) : ap;
+        tf[n] = (n < 2) ? make_double2(0.0, 0.0) : cscale(at, F.gtR[(size_t)m * nt + n - 2]);
+        if (has_u) s.uf[n] = (n < 2) ? 0.0 : au * F.guR[n - 2];
+    }
+    __syncthreads();
+    const double ic = 1.0 / P.cnorm;  // 1/(C w_k), w_0 = 1/2
+    // implicit buoyancy (Section 4): temperature first, then the streamfunction
+    // rows with g dt (Ra/Pr)(i m/s_o) C^I theta_new; otherwise all in one pass
+    const int npass = P.buoy_imp ? 2 : 1;
+    for (int pass = 0; pass < npass; ++pass) {
+        const bool do_p = !P.buoy_imp || pass == 1, do_t = !P.buoy_imp || pass == 0;
+        if (do_p && m > 0) {
+            if (P.buoy_imp) {
+                const double cb = F.gdt * P.Ra / P.Pr * (double)m / P.s_o;
+                for (int k = 4 + tid; k < nc; k += nth)
+                    pf[k] = cadd(pf[k], cmul_i(band_row_c<8>(P.ops.band[OP_C], tx, k, nc), cb));
+                __syncthreads();
+            }
+            for (int k = 4 + tid; k < nc; k += nth) pf[k] = cscale(pf[k], F.gpR[(size_t)m * np + k - 4]);
+            __syncthreads();
+        }
+        if (warp == 0) {
+            if (do_p && m > 0)
+                warp_band_solve<8, 20, 21>(pf + 4, xp, np, F.gpL + (size_t)m * np * 8,
+                                           F.gpU + (size_t)m * np * 21, pvp, stp);
+        } else if (warp == 1) {
+            if (do_t)
+                warp_band_solve<4, 10, 12>(tf + 2, xt, nt, F.gtL + (size_t)m * nt * 4,
+                                           F.gtU + (size_t)m * nt * 12, pvt, stt);
+        } else if (warp == 2) {
+            if (do_t && has_u) warp_band_solve<4, 10, 12>(s.uf + 2, xu, nt, F.guL, F.guU, pvu, stu);
+        }
+        __syncthreads();
+        // x_n = y_n / U_nn
+        for (int n = tid; n < nt; n += nth) {
+            if (do_p && m > 0 && n < np) xp[n] = mul(F.gpU[((size_t)m * np + n) * 21], xp[n]);
+            if (do_t) {
+                xt[n] = mul(F.gtU[((size_t)m * nt + n) * 12], xt[n]);
+                if (has_u) xu[n] *= F.guU[(size_t)n * 12];
+            }
+        }
+        __syncthreads();
+        // expansion to f_hat: Psi_k = sum_i gamma_i^{k-i} x_{k-i}, f_k = x_{k-2} - x_k
+        for (int k = tid; k < nc; k += nth) {
+            const double h = (k == 0) ? 2.0 * ic : ic;
+            if (do_p) {
+                double2 a = make_double2(0.0, 0.0);
+                if (m > 0) {
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        const int n = k - i;
+                        if (n >= 0 && n < np) {
+                            const double g = __ldg(&F.gam[n * 5 + i]);
+                            a.x = fma(g, xp[n].x, a.x);
+                            a.y = fma(g, xp[n].y, a.y);
+                        }
+                    }
+                }
+                px[k] = cscale(a, h);
+            }
+            if (do_t) {
+                double2 a = (k < nt) ? make_double2(-xt[k].x, -xt[k].y) : make_double2(0.0, 0.0);
+                if (k >= 2) a = cadd(a, xt[k - 2]);
+                tx[k] = cscale(a, h);
+                if (has_u) s.ux[k] = h * (((k >= 2) ? xu[k - 2] : 0.0) - ((k < nt) ? xu[k] : 0.0));
+            }
+        }
+        __syncthreads();
+    }
+
+    // store, then mass / implicit operators for later stages
+    for (int n = tid; n < nc; n += nth) {
+        y_out.psi[(size_t)m * nc + n] = px[n];
+        y_out.th[(size_t)m * nc + n] = tx[n];
+        if (has_u) y_out.u[n] = s.ux[n];
+        if (want_mass || want_imp)
+            epilogue_row(P, R, F.gdt, m, n, px, tx, s.ux, mass_out, imp_out, want_mass, want_imp);
+    }
+}
+
 __global__ void __launch_bounds__(NTHREADS_S) k_apply(StepParams P, VecSet y, VecSet mass_out, VecSet imp_out,
                                                       int want_mass, int want_imp) {
     extern __shared__ double2 sm[];
@@ -878,6 +1108,17 @@ size_t smem_solve(const StepParams& P) { return smem_solve_mb(P, 1); }
 cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFactors& F, VecSet y_out,
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st) {
     const size_t sm = smem_solve_mb(P, 1);
+    if (F.gal) {
+        // the FP64 solve arrays (16 round8(nc) doubles), the staging of the factors
+        // (double2 x 2 GCH x 21, double x 2 GCH x 12 twice) and 3 pivot rows
+        const size_t smg = sizeof(double) * 16 * round8(P.nc) + sizeof(double2) * 2 * GCH * 21 +
+                           sizeof(double) * 2 * 2 * GCH * 12 + 3 * round8(P.nc);
+        cudaError_t err = cudaFuncSetAttribute(k_solve_galerkin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg);
+        if (err != cudaSuccess) return err;
+        k_solve_galerkin<<<P.M, NTHREADS_S, smg, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+                                                      want_imp ? 1 : 0);
+        return cudaGetLastError();
+    }
     cudaError_t err = cudaFuncSetAttribute(k_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     k_solve<1><<<P.M, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,

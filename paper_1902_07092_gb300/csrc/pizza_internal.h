@@ -61,6 +61,16 @@ struct DevFactors {
     // ir_t times from FP64 residuals of the assembled system
     int ir_t;
     float *tBlk32, *tY32, *tSinv32;
+    // Galerkin bases (option "radial" = 2, Appendix B): banded LU with partial
+    // pivoting of the square integrated systems (host_ops.h, band_lu_pivot).
+    // Streamfunction, complex, 8 diagonals below / 12 above: gpL [M][n_p][8],
+    // gpU [M][n_p][21], gpPiv [M][n_p], row scales gpR [M][n_p]; temperature, real,
+    // 4 / 6: gtL [M][n_t][4], gtU [M][n_t][12] (11 used), gtPiv, gtR; zonal flow
+    // guL [n_t][4], guU [n_t][12], guPiv, guR; gam [n_p][5] the coefficients gamma
+    int gal;
+    double2 *gpL, *gpU;
+    double *gpR, *gtL, *gtU, *gtR, *guL, *guU, *guR, *gam;
+    unsigned char *gpPiv, *gtPiv, *guPiv;
     // collocation: interior-row columns of the grid-valued inverses, column-major,
     // colW [M][n_r-2][2 n_r] (omega_k, psi_k), colT [M][n_r-2][n_r], colU [n_r-2][n_r]
     double2* colW;

@@ -76,8 +76,9 @@ def zero_state(n_r, n_phi, n_c=None):
 
 # The workloads (sizes, physical parameters, schemes, radial formulation); Ra is
 # given as a multiple of the critical Rayleigh number at (E, Pr = 1, eta = 0.35).
-# "radial": "collocation" (Section 3.1, N_c = n_r) or "integration" (Section 3.2,
-# N_c = floor(2 (n_r - 1)/3)).
+# "radial": "collocation" (Section 3.1, N_c = n_r), "integration" (Section 3.2,
+# N_c = floor(2 (n_r - 1)/3), tau rows) or "galerkin" (the same with the Galerkin
+# bases of Appendix B).
 WORKLOADS = {
     "coll_n33_p96": dict(n_r=33, n_phi=96, E=1e-3, Pr=1.0, eta=0.35, ra_factor=2.0, scheme="CNAB2",
                          dt=1e-4, steps=100, amp=1e-4, seed=1, cfg=1, radial="collocation"),
@@ -85,6 +86,8 @@ WORKLOADS = {
                         dt=1e-4, steps=100, amp=1e-4, seed=1, cfg=1, radial="integration"),
     "sparse_n257_p768": dict(n_r=257, n_phi=768, E=1e-5, Pr=1.0, eta=0.35, ra_factor=10.0, scheme="ARS443",
                              dt=1e-7, steps=1000, amp=1e-3, seed=2, cfg=2, radial="integration"),
+    "galerkin_n257_p768": dict(n_r=257, n_phi=768, E=1e-5, Pr=1.0, eta=0.35, ra_factor=10.0, scheme="ARS443",
+                               dt=1e-7, steps=1000, amp=1e-3, seed=2, cfg=2, radial="galerkin"),
     "coll_n257_p768": dict(n_r=257, n_phi=768, E=1e-5, Pr=1.0, eta=0.35, ra_factor=10.0, scheme="ARS443",
                            dt=1e-7, steps=1000, amp=1e-3, seed=2, cfg=2, radial="collocation"),
     "large_n2049_p6144": dict(n_r=2049, n_phi=6144, E=1e-8, Pr=1.0, eta=0.35, ra_factor=20.0, scheme="SBDF3",
