@@ -160,8 +160,9 @@ def test_collocation_option_limits():
     from paper_1902_07092_gb300.binding import PizzaError, Solver, pizza_set_option
     s = Solver(33, 96, 1e-3, 1e5, 1.0, 0.35, "CNAB2", 1e-4)
     with pytest.raises(PizzaError) as ei:
-        pizza_set_option(s.ctx, "radial", 2)
+        pizza_set_option(s.ctx, "radial", 3)
     assert ei.value.code == -8
+    pizza_set_option(s.ctx, "radial", 2)   # Galerkin bases (Appendix B)
     pizza_set_option(s.ctx, "radial", 0)
     assert s.ctx is not None
     s.close()
