@@ -162,3 +162,86 @@ def test_galerkin_large_workload_sampled():
         assert ep <= max(1e-12, 4 * cp * eps), m
         assert et <= max(1e-12, 4 * ct * eps), m
     gpu.close()
+
+
+def test_galerkin_with_pumping_mixed_precision_batch_and_adjoint():
+    """The Galerkin solve combined with the other options: Ekman pumping (explicit
+    in the integration formulation) against the Galerkin oracle with pumping;
+    mixed precision against that oracle within the mixed-precision bar; one batch
+    graph over a Galerkin and a tau context equal to each stepped alone, bit for
+    bit; and a taped CNAB2 run reversed by the adjoint (the adjoint of the tau
+    step, the same discrete map) against the oracle's adjoint."""
+    from oracle.adjoint import adjoint_cnab2
+    from oracle.stepper import IntegrationStepper
+    from paper_1902_07092_gb300.binding import Batch, Solver, pizza_set_option
+    n_r, n_phi, E = 33, 96, 1e-3
+    Ra = 3.0 * critical_rayleigh(E)
+    th = inputs.theta_init(n_r, n_phi, 1e-2, 21, cfg=1, m_min=0)
+    z, zu = inputs.zero_state(n_r, n_phi)
+    # pumping
+    gpu = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "SBDF3", 1e-4, radial="galerkin", pumping_eps=1e-2)
+    ora = GalerkinStepper(n_r, n_phi, E, Ra, 1.0, 0.35, "SBDF3", 1e-4, pumping_eps=1e-2)
+    gpu.set_state(th, z, zu)
+    ora.set_state(z, th, zu)
+    for _ in range(3):
+        gpu.step(1)
+        ora.step()
+    assert_state_close(gpu.get_state(), ora.y, 1e-12)
+    gpu.close()
+    # mixed precision
+    gpu = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "ARS443", 1e-4, radial="galerkin")
+    pizza_set_option(gpu.ctx, "precision", 1)
+    ora = GalerkinStepper(n_r, n_phi, E, Ra, 1.0, 0.35, "ARS443", 1e-4)
+    gpu.set_state(th, z, zu)
+    ora.set_state(z, th, zu)
+    for _ in range(5):
+        gpu.step(1)
+        ora.step()
+    assert_state_close(gpu.get_state(), ora.y, 1e-6)
+    gpu.close()
+    # one batch graph
+    runs = [("galerkin", "CNAB2"), ("integration", "ARS443")]
+    alone = []
+    for radial, scheme in runs:
+        a = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, scheme, 1e-4, radial=radial)
+        a.set_state(th, z, zu)
+        a.step(4)
+        alone.append(a.get_state())
+        a.close()
+    sols = [Solver(n_r, n_phi, E, Ra, 1.0, 0.35, s, 1e-4, radial=r) for r, s in runs]
+    for s in sols:
+        s.set_state(th, z, zu)
+    batch = Batch(sols)
+    batch.step(4)
+    for s, ref in zip(sols, alone):
+        for x, y in zip(s.get_state(), ref):
+            assert np.array_equal(x, y)
+    batch.close()
+    for s in sols:
+        s.close()
+    # adjoint of a Galerkin-stepped run, (17, 24), nine steps, checkpoints every 4
+    n_r, n_phi, E, Ra, dt, K = 17, 24, 1e-3, 2e5, 2e-4, 9
+    gpu = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "CNAB2", dt, radial="galerkin")
+    ora = IntegrationStepper(n_r, n_phi, E, Ra, 1.0, 0.35, "CNAB2", dt)
+    rng = np.random.default_rng(5)
+    c = lambda: 0.5 * (rng.standard_normal((gpu.M, gpu.n_c)) + 1j * rng.standard_normal((gpu.M, gpu.n_c))) \
+        / (1 + np.arange(gpu.n_c)) ** 2
+    psi0, th0 = c(), c()
+    psi0[0] = 0.0
+    th0[0] = th0[0].real
+    u0 = 0.5 * rng.standard_normal(gpu.n_c) / (1 + np.arange(gpu.n_c)) ** 2
+    J_ref, lam_ref, dRa_ref = adjoint_cnab2(ora, (psi0, th0, u0), K)
+    gpu.set_state(th0, psi0, u0)
+    gpu.tape_begin(4)
+    gpu.step(K)
+    w = gpu.nusselt_weights()
+    g = np.zeros((gpu.M, gpu.n_c), complex)
+    g[0] = w / K
+    for i in range(K):
+        dRa = gpu.adjoint_step(g_theta=g, want_dRa=(i == K - 1))
+    ps, tt, uu = gpu.get_adjoint()
+    errs = (rel_l2(ps, lam_ref[0]), rel_l2(tt, lam_ref[1]), rel_l2(uu, lam_ref[2]))
+    print("galerkin adjoint run: psi %.2e theta %.2e u %.2e dRa %.3e vs %.3e" % (errs + (dRa, dRa_ref)))
+    assert max(errs) <= 1e-9
+    assert abs(dRa - dRa_ref) <= 1e-9 * abs(dRa_ref)
+    gpu.close()
