@@ -122,6 +122,10 @@ struct pizza_ctx {
         double* dRa_dev = nullptr;  // running dJ/dRa on the device (ra[M])
         std::vector<VecSet> ck_y, ck_e;  // checkpoints: y_{s*every}, E(y_{s*every - 1})
         std::vector<VecSet> seg_y;       // y_{seg*every + i}, i < every
+        // grid fields (k_spec_to_grid output) of seg_y[i], written by the segment
+        // recomputation's explicit stage for i < seg_g1n (all but the last state)
+        std::vector<double2*> seg_G1;
+        int seg_g1n = 0;
         VecSet lam{}, rho[2]{}, w{}, g{};
         int rcur = 0;
         double2 *Gb1 = nullptr, *Gb2 = nullptr;
@@ -1088,6 +1092,11 @@ int load_segment(pizza_ctx* ctx, int s) {
         a.seg_y.push_back(adj_vec(ctx, ok));
         if (!ok) return fail(ctx, PIZZA_ENOMEM, "allocation of the segment states failed");
     }
+    while ((int)a.seg_G1.size() < a.every - 1) {
+        a.seg_G1.push_back(dalloc<double2>(ctx, (size_t)ctx->n_r * 4 * ctx->M, a.allocs));
+        if (!a.seg_G1.back()) return fail(ctx, PIZZA_ENOMEM, "allocation of the segment grid fields failed");
+    }
+    a.seg_g1n = 0;
     const int n0 = s * a.every;
     const int n1 = std::min(n0 + a.every, a.K);  // states n0 .. n1-1
     const bool taping = a.taping;
@@ -1101,14 +1110,19 @@ int load_segment(pizza_ctx* ctx, int s) {
     rc = ensure_aux(ctx);
     if (rc) return rc;
     rc = copy_vec(ctx, a.seg_y[0], ctx->vec[ctx->ys[0]]);
+    double2* const g1 = ctx->G1;
     for (int n = n0 + 1; !rc && n < n1; ++n) {
+        // the step's explicit stage synthesises y_{n-1}: into its slot
+        ctx->G1 = a.seg_G1[n - 1 - n0];
         rc = step_multistep(ctx);
+        ctx->G1 = g1;
         if (rc) break;
         ctx->n_done++;
         rc = copy_vec(ctx, a.seg_y[n - n0], ctx->vec[ctx->ys[0]]);
     }
     a.taping = taping;
     if (rc) return rc;
+    a.seg_g1n = n1 - n0 - 1;
     a.seg = s;
     return PIZZA_OK;
 }
@@ -1747,6 +1761,7 @@ int pizza_tape_begin(pizza_ctx* ctx, int checkpoint_every) {
     a.K = 0;
     a.pos = 0;
     a.seg = -1;
+    a.seg_g1n = 0;
     CK(cudaMemsetAsync(a.dRa_dev, 0, sizeof(double), ctx->stream));
     a.rcur = 0;
     bool ok = true;
@@ -1788,11 +1803,16 @@ int pizza_adjoint_step(pizza_ctx* ctx, const double* g_theta, const double* g_ps
     // lam += J_E(y_n)* w
     rc = load_segment(ctx, n / a.every);
     if (rc) return rc;
-    VecSet y = a.seg_y[n % a.every];
+    const int i = n % a.every;
+    VecSet y = a.seg_y[i];
     StepParams P64 = ctx->P;
     P64.fp32 = 0;
-    CK(launch_spec_to_grid(P64, y, ctx->G1, ctx->stream));
-    CK(launch_adj_explicit(P64, a.w, y, a.lam, ctx->G1, a.Gb2, a.Gb1, a.ra, ctx->stream));
+    const double2* g1 = ctx->G1;
+    if (i < a.seg_g1n)
+        g1 = a.seg_G1[i];  // recorded by the recomputation
+    else
+        CK(launch_spec_to_grid(P64, y, ctx->G1, ctx->stream));
+    CK(launch_adj_explicit(P64, a.w, y, a.lam, g1, a.Gb2, a.Gb1, a.ra, ctx->stream));
     CK(launch_ra_accumulate(a.ra, ctx->M, a.dRa_dev, ctx->stream));
     a.rcur = 1 - a.rcur;
     a.pos = n;
