@@ -202,10 +202,10 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
     const double gdt = gamma * ctx->dt;
     const auto tauP = tau_rows_psi(ctx->n_r, nc);
     const auto tauD = tau_rows_dir(ctx->n_r, nc);
-    const int nbp = (np + 7) / 8, nbt = (nt + 3) / 4;
+    const int nbp = (np + 7) / 8, nbt = (nt + 7) / 8;
     std::vector<double2> hpK((size_t)M * nbp * 3 * 64), hpY((size_t)M * np * 4), hpS((size_t)M * 16),
         hpB((size_t)M * np * 17);
-    std::vector<double> htK((size_t)M * nbt * 3 * 16), htY((size_t)M * nt * 2), htS((size_t)M * 4),
+    std::vector<double> htK((size_t)M * nbt * 3 * 64), htY((size_t)M * nt * 2), htS((size_t)M * 4),
         htB((size_t)M * nt * 9);
     std::vector<int> bad(M, 0);
     auto get = [&](int id, int k, int n) -> double {
@@ -266,12 +266,16 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
                 continue;
             }
             std::copy(bt.begin() + 2 * 9, bt.end(), htB.begin() + (size_t)m * nt * 9);
-            std::vector<double> tb;
-            if (!block_lu_twisted(bt, nc, 4, 2, tb)) {
+            // block chains of 8 rows (the band of half width 4 padded): half the
+            // chain steps of 4-row blocks, and every lane of the warp busy
+            std::vector<double> tb, bt8((size_t)nc * 17, 0.0);
+            for (int k = 0; k < nc; ++k)
+                for (int d = 0; d < 9; ++d) bt8[(size_t)k * 17 + d + 4] = bt[(size_t)k * 9 + d];
+            if (!block_lu_twisted(bt8, nc, 8, 2, tb)) {
                 bad[m] = 1;
                 continue;
             }
-            std::copy(tb.begin(), tb.end(), htK.begin() + (size_t)m * nbt * 48);
+            std::copy(tb.begin(), tb.end(), htK.begin() + (size_t)m * nbt * 192);
             std::copy(g.Y.begin(), g.Y.end(), htY.begin() + (size_t)m * nt * 2);
             std::copy(g.Sinv.begin(), g.Sinv.end(), htS.begin() + (size_t)m * 4);
         }
@@ -305,8 +309,10 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         if (!dst) return fail(ctx, PIZZA_ENOMEM, "device allocation of factors failed");          \
         CK(cudaMemcpy(dst, (hv).data(), (hv).size() * sizeof(T), cudaMemcpyHostToDevice));       \
     } while (0)
-    std::vector<double> ub;
-    if (!block_lu_twisted(bu, nc, 4, 2, ub)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
+    std::vector<double> ub, bu8((size_t)nc * 17, 0.0);
+    for (int k = 0; k < nc; ++k)
+        for (int d = 0; d < 9; ++d) bu8[(size_t)k * 17 + d + 4] = bu[(size_t)k * 9 + d];
+    if (!block_lu_twisted(bu8, nc, 8, 2, ub)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
     UPLOAD(F.pBlk, double2, hpK);
     UPLOAD(F.pY, double2, hpY);
     UPLOAD(F.pSinv, double2, hpS);

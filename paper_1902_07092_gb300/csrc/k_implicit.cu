@@ -12,8 +12,9 @@
 // is formed in FP64 and solved again with the same factors.
 //
 // The banded block is solved through its two-sided block-tridiagonal
-// factorisation (blocks of 8 rows for the streamfunction, 4 for temperature and
-// zonal flow; host_ops.h, block_lu_twisted): a pair of warps walks the top and
+// factorisation (blocks of 8 rows; the temperature and zonal-flow bands, half
+// width 4, are padded to that: twice the block size halves their chains and keeps
+// all 32 lanes busy; host_ops.h, block_lu_twisted): a pair of warps walks the top and
 // the bottom half towards the middle block and back, each step one lane-parallel
 // H x H mat-vec forward and a fused pair of them backward.  On GB300 a dependent
 // FP64 FMA costs ~64 cycles, so the sequential chain, not the flop count, sets
@@ -555,7 +556,7 @@ __device__ void refine_zonal_flow(const StepParams& P, const DevFactors& F, Solv
     __syncthreads();
     double* du = reinterpret_cast<double*>(s.pw[0]);
     if (warp == 4 || warp == 5) {
-        pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pf[0]), du + 2, nt, F.uBlk, true, warp - 4, 3);
+        pair_block_solve<8>(s.uf + 2, reinterpret_cast<double*>(s.pf[0]), du + 2, nt, F.uBlk, true, warp - 4, 3);
         if (warp == 4) {
             double t0 = 0.0, t1 = 0.0;
             for (int j = lane; j < nt; j += 32) {
@@ -585,7 +586,7 @@ __device__ void refine_zonal_flow(const StepParams& P, const DevFactors& F, Solv
 
 template <int MB>
 __device__ void temperature_corrections(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u) {
-    const int nc = P.nc, nt = nc - 2, nbt = (nt + 3) / 4;
+    const int nc = P.nc, nt = nc - 2, nbt = (nt + 7) / 8;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
     if (F.ir_t) {
         // x += S32^{-1}(f - L x), ir_t times, residuals in FP64 (MB == 1)
@@ -616,7 +617,7 @@ __device__ void temperature_corrections(const StepParams& P, const DevFactors& F
             }
             __syncthreads();
             if (warp == 2 || warp == 3)
-                pair_block_solve<4>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 48, true, warp - 2, 2);
+                pair_block_solve<8>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2, 2);
             __syncthreads();
             if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
             __syncthreads();
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     const int m0 = blockIdx.x * MB;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
     const int np = nc - 4, nt = nc - 2;
-    const int nbp = (np + 7) / 8, nbt = (nt + 3) / 4;
+    const int nbp = (np + 7) / 8, nbt = (nt + 7) / 8;
     SolveSmem s = carve<MB>(sm, nc);
     const bool has_u = (m0 == 0);
 
@@ -694,15 +695,15 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         } else if (warp < 4) {
             if (do_t) {
                 if (F.ir_t)
-                    pair_block_solve<4>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 48, true, warp - 2,
+                    pair_block_solve<8>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2,
                                         2);
                 else
-                    pair_block_solve<4>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 48, true,
+                    pair_block_solve<8>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 192, true,
                                         warp - 2, 2);
             }
         } else if (warp < 6 && has_u) {
             if (do_t)
-                pair_block_solve<4>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4,
+                pair_block_solve<8>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4,
                                     3);
         }
         __syncthreads();

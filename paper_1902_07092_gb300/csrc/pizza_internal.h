@@ -51,10 +51,11 @@ struct DevFactors {
     // streamfunction, complex, H = 8: blocks [M][nb_p][3][64], Y [M][n_p][4],
     // Sinv [M][16], assembled rows 4..nc-1 of A^I_m - gamma dt B^I_m [M][n_p][17]
     double2 *pBlk, *pY, *pSinv, *pBand;
-    // temperature, real, H = 4: blocks [M][nb_t][3][16], Y [M][n_t][2], Sinv [M][4],
+    // temperature, real, blocks of H = 8 rows (band half width 4, padded): blocks
+    // [M][nb_t][3][64], nb_t = ceil(n_t/8), Y [M][n_t][2], Sinv [M][4],
     // assembled rows 2..nc-1 of D^I - gamma dt F^I_m/Pr [M][n_t][9]
     double *tBlk, *tY, *tSinv, *tBand;
-    // zonal flow, real, H = 4: blocks [nb_t][3][16], Y [n_t][2], Sinv [4], band [n_t][9]
+    // zonal flow, real, H = 8: blocks [nb_t][3][64], Y [n_t][2], Sinv [4], band [n_t][9]
     double *uBlk, *uY, *uSinv, *uBand;
     // temperature by mixed-precision iterative refinement (large N_c): ir_t > 0
     // solves with the block factors, Y and S^{-1} rounded to FP32 and corrects
