@@ -456,6 +456,57 @@ __device__ __forceinline__ void cheb_derivative_scan(const T* c, T* d, T* tmp, i
     __syncthreads();
 }
 
+// Two independent derivatives at once, in place: c0 <- D c0 (warps 0-1, scratch
+// t0) and c1 <- D c1 (warps 2-3, scratch t1), the same arithmetic as
+// cheb_derivative_scan (whose second phase reads only the scratch, so the result
+// may overwrite the input).  Whole CTA (>= 128 threads).
+template <class T>
+__device__ __forceinline__ void cheb_derivative_scan2(T* c0, T* t0, T* c1, T* t1, int n, double scale) {
+    using RT = typename Cx<T>::R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+        const int q = warp & 1;
+        const T* c = (warp < 2) ? c0 : c1;
+        T* tmp = (warp < 2) ? t0 : t1;
+        const int len = (n - q + 1) / 2;
+        const int per = (len + 31) / 32;
+        const int i0 = lane * per, i1 = min(i0 + per, len);
+        T acc = Cx<T>::make(0.0, 0.0);
+        for (int i = i1 - 1; i >= i0; --i) {
+            const int k = 2 * i + q;
+            if (k > 0) {
+                const RT f = (RT)(2 * k);
+                acc.x = fmat(f, c[k].x, acc.x);
+                acc.y = fmat(f, c[k].y, acc.y);
+            }
+            tmp[k] = acc;
+        }
+        T sfx = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const RT x = __shfl_down_sync(0xffffffffu, sfx.x, o);
+            const RT y = __shfl_down_sync(0xffffffffu, sfx.y, o);
+            if (lane + o < 32) {
+                sfx.x += x;
+                sfx.y += y;
+            }
+        }
+        const T off = csub(sfx, acc);
+        for (int i = i0; i < i1; ++i) {
+            const int k = 2 * i + q;
+            tmp[k] = cadd(tmp[k], off);
+        }
+    }
+    __syncthreads();
+    const RT fs = (RT)scale, f0 = (RT)(0.5 * scale);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const RT f = (j == 0) ? f0 : fs;
+        c0[j] = (j + 1 < n) ? cscale(t0[j + 1], f) : Cx<T>::make(0.0, 0.0);
+        c1[j] = (j + 1 < n) ? cscale(t1[j + 1], f) : Cx<T>::make(0.0, 0.0);
+    }
+    __syncthreads();
+}
+
 // Transpose of cheb_derivative_scan: with d = D c, d_j = (2/c_j) sum_{k>j, k+j odd}
 // k c_k (times scale), returns out = D^T e:
 //   out_k = 2 k scale sum_{j<k, j+k odd} e_j / c_j   (c_0 = 2, c_j = 1),
@@ -503,6 +554,59 @@ __device__ __forceinline__ void cheb_derivative_adjoint_scan(const T* e, T* out,
         T v = Cx<T>::make(0.0, 0.0);
         if (k > 0) v = cscale(tmp[k - 1], (RT)(2.0 * k * scale));
         out[k] = v;
+    }
+    __syncthreads();
+}
+
+// Two independent transposed derivatives at once, in place: e0 <- post D^T e0
+// (warps 0-1, scratch t0) and e1 <- post D^T e1 (warps 2-3, scratch t1), the same
+// arithmetic as cheb_derivative_adjoint_scan followed by a multiplication by post.
+// Whole CTA (>= 128 threads).
+template <class T>
+__device__ __forceinline__ void cheb_derivative_adjoint_scan2(T* e0, T* t0, T* e1, T* t1, int n, double scale,
+                                                              double post) {
+    using RT = typename Cx<T>::R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+        const int q = warp & 1;
+        const T* e = (warp < 2) ? e0 : e1;
+        T* tmp = (warp < 2) ? t0 : t1;
+        const int len = (n - q + 1) / 2;
+        const int per = (len + 31) / 32;
+        const int i0 = lane * per, i1 = min(i0 + per, len);
+        T acc = Cx<T>::make(0.0, 0.0);
+        for (int i = i0; i < i1; ++i) {
+            const int j = 2 * i + q;
+            const RT f = (j == 0) ? (RT)0.5 : (RT)1;
+            acc.x = fmat(f, e[j].x, acc.x);
+            acc.y = fmat(f, e[j].y, acc.y);
+            tmp[j] = acc;
+        }
+        T pfx = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const RT x = __shfl_up_sync(0xffffffffu, pfx.x, o);
+            const RT y = __shfl_up_sync(0xffffffffu, pfx.y, o);
+            if (lane >= o) {
+                pfx.x += x;
+                pfx.y += y;
+            }
+        }
+        const T off = csub(pfx, acc);
+        for (int i = i0; i < i1; ++i) {
+            const int j = 2 * i + q;
+            tmp[j] = cadd(tmp[j], off);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        T v0 = Cx<T>::make(0.0, 0.0), v1 = v0;
+        if (k > 0) {
+            v0 = cscale(t0[k - 1], (RT)(2.0 * k * scale));
+            v1 = cscale(t1[k - 1], (RT)(2.0 * k * scale));
+        }
+        e0[k] = cscale(v0, (RT)post);
+        e1[k] = cscale(v1, (RT)post);
     }
     __syncthreads();
 }

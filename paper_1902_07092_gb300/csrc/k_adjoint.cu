@@ -162,12 +162,8 @@ __global__ void __launch_bounds__(NTA) k_adj_grid_to_spec(StepParams P, VecSet w
         const int nb = min(NB, 2 - b0);
         cos_sums(c2 + b0 * N, c2 + b0 * N, nb, bufA, bufB, P);  // Syn^T
     }
-    for (int f = 0; f < 2; ++f) {
-        double2* v = f ? c3 : c2;
-        cheb_derivative_adjoint_scan(v, c4, bufA, N, P.inv_a);  // Dc^T
-        for (int n = tid; n < N; n += nth) v[n] = cscale(c4[n], 2.0 / (double)K);  // Ana^T weights 2 w_n/K
-        __syncthreads();
-    }
+    // Dc^T of both, then the Ana^T weights 2 w_n/K (the scans side by side, in place)
+    cheb_derivative_adjoint_scan2(c2, bufA, c3, bufB, N, P.inv_a, 2.0 / (double)K);
     // Ana^T: sum''_n ... with the ends halved: the even extension already counts
     // the end values once, so load without doubling
     for (int b0 = 0; b0 < 2; b0 += NB) {

@@ -479,13 +479,8 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
         }
         __syncthreads();
     }
-    // d/ds of both (in place through cc2 as output, then copy back)
-    cheb_derivative_scan(cc0, cc2, bufA, N, P.inv_a);
-    for (int n = tid; n < N; n += nth) cc0[n] = cc2[n];
-    __syncthreads();
-    cheb_derivative_scan(cc1, cc2, bufA, N, P.inv_a);
-    for (int n = tid; n < N; n += nth) cc1[n] = cc2[n];
-    __syncthreads();
+    // d/ds of both, in place, the two scans side by side (bufA, bufB: scratch)
+    cheb_derivative_scan2(cc0, bufA, cc1, bufB, N, P.inv_a);
 
     // pass B: derivative values on the grid, then N_omega (or N_u) and N_theta;
     // with Ekman pumping N_omega - F_eps and N_u + Ups_eps u_bar (1 + (E/2) omega_0)
