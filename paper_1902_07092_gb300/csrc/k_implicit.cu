@@ -434,7 +434,8 @@ __device__ void apply_row(const StepParams& P, int m, int k, const double2* xp, 
 // same terms in the same order).
 __device__ void epilogue_row(const StepParams& P, const RhsSpec& R, double gdt, int m, int k, const double2* xp,
                              const double2* xt, const double* xu, VecSet mass_out, VecSet imp_out, bool want_mass,
-                             bool want_imp) {
+                             bool want_imp, const double2* fps = nullptr, const double2* fts = nullptr,
+                             const double* fus = nullptr) {
     const int nc = P.nc;
     const double mu = (double)m * m;
     double2 mp = make_double2(0.0, 0.0), mt = make_double2(0.0, 0.0);
@@ -458,7 +459,12 @@ __device__ void epilogue_row(const StepParams& P, const RhsSpec& R, double gdt, 
     if (want_imp) {  // before any store: an output may be one of the terms of f
         double2 fp = make_double2(0.0, 0.0), ft = make_double2(0.0, 0.0);
         double fu = 0.0;
-        for (int t = 0; t < R.nterms; ++t) {
+        if (fps) {  // kept by the caller (the same sums)
+            fp = fps[k];
+            ft = fts[k];
+            if (m == 0) fu = fus[k];
+        }
+        for (int t = 0; t < (fps ? 0 : R.nterms); ++t) {
             const double c = R.t[t].c;
             const double2 vp = R.t[t].v.psi[idx];
             const double2 vt = R.t[t].v.th[idx];
@@ -490,6 +496,11 @@ struct SolveSmem {
     double2 *pf[2], *pw[2], *px[2], *pd[2], *tf[2], *tw[2], *tx[2];
     double *uf, *ux;
     float2 *tr, *tq, *td;  // refined FP32 temperature solves: residual, chain scratch, correction (MB = 1)
+    // the streamfunction and zonal-flow right-hand sides as assembled (pf and uf
+    // become residuals), for the epilogue; past the end of solve_smem_doubles,
+    // present when the launch adds keep_f_doubles (MB = 1)
+    double2* fp;
+    double* fu;
 };
 
 __host__ __device__ inline int round8(int n) { return (n + 7) / 8 * 8; }
@@ -498,6 +509,8 @@ __host__ __device__ inline size_t solve_smem_doubles(int nc, int MB) {
     const int b = round8(nc);
     return (size_t)MB * 2 * 7 * b + 2 * (size_t)b + 3 * (size_t)b;  // last: 3 b float2
 }
+
+__host__ __device__ inline size_t keep_f_doubles(int nc) { return 3 * (size_t)round8(nc); }
 
 template <int MB>
 __device__ SolveSmem carve(double2* base, int nc) {
@@ -519,7 +532,9 @@ __device__ SolveSmem carve(double2* base, int nc) {
     float2* f = reinterpret_cast<float2*>(d);
     s.tr = f; f += b;
     s.tq = f; f += b;
-    s.td = f;
+    s.td = f; f += b;
+    s.fp = reinterpret_cast<double2*>(f);
+    s.fu = reinterpret_cast<double*>(s.fp + b);
     return s;
 }
 
@@ -634,7 +649,7 @@ __device__ void temperature_corrections(const StepParams& P, const DevFactors& F
 template <int MB>
 __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, DevFactors F, VecSet y_out,
                                                       VecSet mass_out, VecSet imp_out, int want_mass,
-                                                      int want_imp) {
+                                                      int want_imp, int keep_f) {
     extern __shared__ double2 sm[];
     const int nc = P.nc, M = P.M;
     const int m0 = blockIdx.x * MB;
@@ -650,6 +665,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         if (m >= M) continue;
         double2 ap = make_double2(0.0, 0.0), at = make_double2(0.0, 0.0);
         double au = 0.0;
+#pragma unroll 4
         for (int t = 0; t < R.nterms; ++t) {
             const double c = R.t[t].c;
             const double2 vp = R.t[t].v.psi[(size_t)m * nc + n];
@@ -664,6 +680,10 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         s.tf[mi][n] = (n < 2) ? make_double2(0.0, 0.0) : at;
         if (F.ir_t) s.tr[n] = to_f2(s.tf[mi][n]);  // MB == 1 with ir_t
         if (m == 0) s.uf[n] = (n < 2) ? 0.0 : au;
+        if (MB == 1 && keep_f) {  // for the epilogue: pf and uf become residuals
+            s.fp[n] = s.pf[mi][n];
+            if (m == 0) s.fu[n] = s.uf[n];
+        }
     }
     __syncthreads();
 
@@ -833,7 +853,8 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         y_out.th[(size_t)m * nc + n] = s.tx[mi][n];
         if (m == 0) y_out.u[n] = s.ux[n];
         if (want_mass || want_imp)
-            epilogue_row(P, R, F.gdt, m, n, s.px[mi], s.tx[mi], s.ux, mass_out, imp_out, want_mass, want_imp);
+            epilogue_row(P, R, F.gdt, m, n, s.px[mi], s.tx[mi], s.ux, mass_out, imp_out, want_mass, want_imp,
+                         (MB == 1 && keep_f) ? s.fp : nullptr, s.tf[mi], s.fu);
     }
 }
 
@@ -977,6 +998,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve_galerkin(StepParams P, Rhs
     for (int n = tid; n < nc; n += nth) {
         double2 ap = make_double2(0.0, 0.0), at = make_double2(0.0, 0.0);
         double au = 0.0;
+#pragma unroll 4
         for (int t = 0; t < R.nterms; ++t) {
             const double c = R.t[t].c;
             const double2 vp = R.t[t].v.psi[(size_t)m * nc + n];
@@ -1120,10 +1142,18 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
                                                       want_imp ? 1 : 0);
         return cudaGetLastError();
     }
-    cudaError_t err = cudaFuncSetAttribute(k_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // the epilogue reads the assembled right-hand sides from shared memory where
+    // they fit (up to N_c ~ 1300), else sums the terms again
+    int dev = 0, smax = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (err != cudaSuccess) return err;
-    k_solve<1><<<P.M, NTHREADS_S, sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
-                                            want_imp ? 1 : 0);
+    const size_t smk = sm + sizeof(double) * keep_f_doubles(P.nc);
+    const int keep = smk <= (size_t)smax ? 1 : 0;
+    err = cudaFuncSetAttribute(k_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(keep ? smk : sm));
+    if (err != cudaSuccess) return err;
+    k_solve<1><<<P.M, NTHREADS_S, keep ? smk : sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+                                                         want_imp ? 1 : 0, keep);
     return cudaGetLastError();
 }
 
