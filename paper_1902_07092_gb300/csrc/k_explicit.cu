@@ -233,7 +233,7 @@ struct P2<float2> {
 
 template <class T>
 __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* __restrict__ G1,
-                                                         T* __restrict__ G2) {
+                                                         T* __restrict__ G2, int pair) {
     using RT = typename Cx<T>::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
@@ -251,6 +251,24 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* 
     const RT l1 = P2<T>::v(e1), l2 = P2<T>::v(e2);
     const RT iP = (RT)P.inv_nphi;  // 1/n_phi, a power of two divided by 3
 
+    if (pair) {
+        // both packed pairs in one batched transform each way (X, Y hold 2 Pn)
+        Y = X + 2 * Pn;
+        load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, (RT)1, l1);
+        load_packed_spectrum(X + Pn, G1 + g_index(k, 2, 0, M), M, Pn, n_m, (RT)1, l2);
+        T* R = fft_batched<+1>(X, Y, P.plan_p, 2);
+        T* O = (R == X) ? Y : X;
+        for (int j = tid; j < Pn; j += nth) {
+            const T g1 = R[j], g2 = R[Pn + j];
+            O[j] = cscale(g1, g2.x);
+            O[Pn + j] = cscale(g1, g2.y);
+        }
+        T* S = fft_batched<-1>(O, R, P.plan_p, 2);
+        store_split_spectrum(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, iP, iP * P2<T>::v(-e1));
+        store_split_spectrum(S + Pn, G2 + g_index(k, 2, 0, M), M, Pn, n_m, iP * P2<T>::v(-e2),
+                             iP * P2<T>::v(-e1 - e2));
+        return;
+    }
     load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, (RT)1, l1);
     T* R = fft_batched<+1>(X, Y, P.plan_p, 1);
 #pragma unroll
@@ -336,7 +354,7 @@ __device__ __forceinline__ void store_split_spectrum_dd(const ddc* Y, double2* _
 }
 
 __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const double2* __restrict__ G1,
-                                                            double2* __restrict__ G2) {
+                                                            double2* __restrict__ G2, int pair) {
     extern __shared__ __align__(16) unsigned char smraw[];
     ddc* sm = reinterpret_cast<ddc*>(smraw);
     const int k = blockIdx.x;
@@ -374,6 +392,31 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
             for (int q = 0; q < 4; ++q) msum[q][tid >> 5] = acc[q];
     }
 
+    if (pair) {
+        // both packed pairs in one batched transform each way (X, Y hold 2 Pn):
+        // half the barrier-separated passes, the same arithmetic per transform
+        Y = X + 2 * Pn;
+        load_packed_spectrum_dd(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, pow2f(e1));
+        load_packed_spectrum_dd(X + Pn, G1 + g_index(k, 2, 0, M), M, Pn, n_m, pow2f(e2));
+        ddc* R = fft_batched<+1>(X, Y, P.plan_p, 2);
+        ddc* O = (R == X) ? Y : X;
+        for (int j = tid; j < Pn; j += nth) {
+            const ddc g1 = R[j], g2 = R[Pn + j];
+            O[j] = cscale(g1, g2.x);
+            O[Pn + j] = cscale(g1, g2.y);
+        }
+        ddc* S = fft_batched<-1>(O, R, P.plan_p, 2);
+        store_split_spectrum_dd(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, iP, dd_scale2(iP, pow2f(-e1)));
+        store_split_spectrum_dd(S + Pn, G2 + g_index(k, 2, 0, M), M, Pn, n_m, dd_scale2(iP, pow2f(-e2)),
+                                dd_scale2(dd_scale2(iP, pow2f(-e1)), pow2f(-e2)));
+        __syncthreads();  // the stores above are done (thread 0 wrote the m = 0 entries replaced here)
+        if (tid < 4) {
+            double t = 0.0;
+            for (int w = 0; w < (nth >> 5); ++w) t += msum[tid][w];
+            G2[g_index(k, tid, 0, M)] = make_double2(t, 0.0);
+        }
+        return;
+    }
     load_packed_spectrum_dd(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, pow2f(e1));
     ddc* R = fft_batched<+1>(X, Y, P.plan_p, 1);
 #pragma unroll
@@ -734,14 +777,26 @@ static cudaError_t spec_to_grid_t(const StepParams& P, VecSet y, void* G1, cudaS
     return cudaGetLastError();
 }
 
+// 1 when the azimuthal kernels can hold both packed pairs at once (twice
+// smem_phi_products: n_phi <= 3072 in FP64), else 0
+static int phi_pair(const StepParams& P, cudaError_t& err) {
+    int dev = 0, smax = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return (err == cudaSuccess && 2 * smem_phi_products(P) <= (size_t)smax) ? 1 : 0;
+}
+
 template <class T>
 static cudaError_t phi_products_t(const StepParams& P, const void* G1, void* G2, cudaStream_t st) {
-    const size_t sm = smem_phi_products(P);
     const int nth = phi_threads(P);
     if (P.n_phi > nth * MAXPER || nth > 512) return cudaErrorInvalidValue;
-    cudaError_t err = cudaFuncSetAttribute(k_phi_products<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t err;
+    const int pair = phi_pair(P, err);
     if (err != cudaSuccess) return err;
-    k_phi_products<T><<<P.n_r, nth, sm, st>>>(P, static_cast<const T*>(G1), static_cast<T*>(G2));
+    const size_t sm = (pair ? 2 : 1) * smem_phi_products(P);
+    err = cudaFuncSetAttribute(k_phi_products<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    k_phi_products<T><<<P.n_r, nth, sm, st>>>(P, static_cast<const T*>(G1), static_cast<T*>(G2), pair);
     return cudaGetLastError();
 }
 
@@ -761,12 +816,16 @@ cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cuda
 cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2* G2, cudaStream_t st) {
     if (P.fp32) return phi_products_t<float2>(P, G1, G2, st);
     if (P.phi_dd && P.plan_p.twdd) {
-        const size_t sm = smem_phi_products(P);
         const int nth = phi_threads(P);
         if (P.n_phi > nth * MAXPER || nth > 512) return cudaErrorInvalidValue;
-        cudaError_t err = cudaFuncSetAttribute(k_phi_products_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        // the batched pair of transforms needs twice the buffers (n_phi <= 3072)
+        cudaError_t err;
+        const int pair = phi_pair(P, err);
         if (err != cudaSuccess) return err;
-        k_phi_products_dd<<<P.n_r, nth, sm, st>>>(P, G1, G2);
+        const size_t sm = (pair ? 2 : 1) * smem_phi_products(P);
+        err = cudaFuncSetAttribute(k_phi_products_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_phi_products_dd<<<P.n_r, nth, sm, st>>>(P, G1, G2, pair);
         return cudaGetLastError();
     }
     return phi_products_t<double2>(P, G1, G2, st);
