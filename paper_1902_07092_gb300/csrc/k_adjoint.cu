@@ -243,7 +243,8 @@ __device__ __forceinline__ void store_split_adjoint(const double2* Y, double2* _
 }
 
 __global__ void __launch_bounds__(NTA, 1) k_adj_phi(StepParams P, const double2* __restrict__ G1,
-                                                    const double2* __restrict__ Gb2, double2* __restrict__ Gb1) {
+                                                    const double2* __restrict__ Gb2, double2* __restrict__ Gb1,
+                                                    int pair) {
     extern __shared__ double2 sm[];
     const int k = blockIdx.x;
     const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
@@ -252,6 +253,37 @@ __global__ void __launch_bounds__(NTA, 1) k_adj_phi(StepParams P, const double2*
     double2* F1 = Y + Pn;  // v + i u_phi on the grid
     double2* F2 = F1 + Pn; // omega + i theta
     const int tid = threadIdx.x, nth = blockDim.x;
+    if (pair) {
+        // the three pairs of independent transforms batched (X, Y hold 2 Pn each):
+        // half the barrier-separated passes, the same arithmetic per transform
+        Y = X + 2 * Pn;
+        F1 = Y + 2 * Pn;
+        F2 = F1 + Pn;
+        load_hermitian_pair(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, 1.0, 1.0);
+        load_hermitian_pair(X + Pn, G1 + g_index(k, 2, 0, M), M, Pn, n_m, 1.0, 1.0);
+        double2* R = fft_batched<+1>(X, Y, P.plan_p, 2);
+        for (int j = tid; j < Pn; j += nth) {
+            F1[j] = R[j];
+            F2[j] = R[Pn + j];
+        }
+        __syncthreads();
+        const double ip = 1.0 / (double)Pn;
+        load_hermitian_pair(X, Gb2 + g_index(k, 0, 0, M), M, Pn, n_m, ip, 0.5 * ip);
+        load_hermitian_pair(X + Pn, Gb2 + g_index(k, 2, 0, M), M, Pn, n_m, ip, 0.5 * ip);
+        R = fft_batched<+1>(X, Y, P.plan_p, 2);
+        double2* O = (R == X) ? Y : X;
+        for (int j = tid; j < Pn; j += nth) {
+            const double2 p = R[j], q = R[Pn + j], f1 = F1[j], f2 = F2[j];
+            double2 a1 = make_double2(f2.x * p.x, f2.x * p.y);
+            a1 = make_double2(fma(f2.y, q.x, a1.x), fma(f2.y, q.y, a1.y));
+            O[j] = a1;
+            O[Pn + j] = make_double2(fma(f1.x, p.x, f1.y * p.y), fma(f1.x, q.x, f1.y * q.y));
+        }
+        R = fft_batched<-1>(O, R, P.plan_p, 2);
+        store_split_adjoint(R, Gb1 + g_index(k, 0, 0, M), M, Pn, n_m);
+        store_split_adjoint(R + Pn, Gb1 + g_index(k, 2, 0, M), M, Pn, n_m);
+        return;
+    }
     double2 acc1[MAXPER_A], acc2[MAXPER_A];
     // forward fields
     load_hermitian_pair(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, 1.0, 1.0);
@@ -561,10 +593,16 @@ cudaError_t launch_adj_explicit(const StepParams& P, VecSet w, VecSet y, VecSet 
     k_adj_grid_to_spec<<<P.M, NTA, sm, st>>>(P, w, y, lam, Gb2, ra);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    sm = sizeof(double2) * 4 * P.n_phi;
+    // the batched pairs need 6 n_phi entries (n_phi <= 2048), else 4 n_phi
+    int dev = 0, smax = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (err != cudaSuccess) return err;
+    const int pair = sizeof(double2) * 6 * P.n_phi <= (size_t)smax ? 1 : 0;
+    sm = sizeof(double2) * (pair ? 6 : 4) * P.n_phi;
     err = cudaFuncSetAttribute(k_adj_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    k_adj_phi<<<P.n_r, NTA, sm, st>>>(P, G1, Gb2, Gb1);
+    k_adj_phi<<<P.n_r, NTA, sm, st>>>(P, G1, Gb2, Gb1, pair);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     sm = smem_adj_spec_to_grid(P);
