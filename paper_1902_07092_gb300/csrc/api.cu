@@ -29,25 +29,40 @@ constexpr int NVEC = 16;
 namespace pz {
 void set_global_error(const char* msg) { g_init_error = msg; }
 
-bool make_fft_plan(int L, FftPlan& pl) {
+// Factor L = 3^a 2^b into Stockham passes: radix 3 first, then (with use8)
+// radix 8 while a factor of 8 remains (16 stays 4 x 4), then 4s and 2s.
+static int fft_factors(int L, bool use8, int* radix) {
     int n = L, np = 0;
     if (n % 3 == 0) {
-        pl.radix[np++] = 3;
+        radix[np++] = 3;
         n /= 3;
     }
-    if (n <= 0 || (n & (n - 1)) != 0) return false;
-    while (n % 4 == 0) {
-        pl.radix[np++] = 4;
+    if (n <= 0 || (n & (n - 1)) != 0) return -1;
+    while (use8 && n % 8 == 0 && n != 16 && np < MAX_PASSES) {
+        radix[np++] = 8;
+        n /= 8;
+    }
+    while (n % 4 == 0 && np < MAX_PASSES) {
+        radix[np++] = 4;
         n /= 4;
     }
-    while (n % 2 == 0) {
-        pl.radix[np++] = 2;
+    while (n % 2 == 0 && np < MAX_PASSES) {
+        radix[np++] = 2;
         n /= 2;
     }
+    return n == 1 ? np : -1;
+}
+
+bool make_fft_plan(int L, FftPlan& pl) {
+    // FP64 / double-float transforms keep radix 4 (radix 8 measured slower there:
+    // its butterflies hold more registers); FP32 transforms take radix 8
+    const int np = fft_factors(L, false, pl.radix), np8 = fft_factors(L, true, pl.radix8);
+    if (np < 0 || np8 < 0) return false;
     pl.L = L;
     pl.npass = np;
+    pl.npass8 = np8;
     pl.tws = 1;
-    return np <= MAX_PASSES;
+    return true;
 }
 
 std::vector<double2> fft_twiddles(int L) {

@@ -108,6 +108,24 @@ struct Tab<float2> {
 __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
 __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2((double)a.x, (double)a.y); }
 
+// 4-point DFT y_k = sum_n a_n e^(SIGN 2 pi i nk/4) (SIGN = -1 forward, +1 backward)
+template <int SIGN, class T>
+__device__ __forceinline__ void dft4(T a0, T a1, T a2, T a3, T* y) {
+    const T t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = csub(a1, a3);
+    T rt;  // forward: -i t3, backward: +i t3
+    if (SIGN < 0) {
+        rt.x = t3.y;
+        rt.y = -t3.x;
+    } else {
+        rt.x = -t3.y;
+        rt.y = t3.x;
+    }
+    y[0] = cadd(t0, t2);
+    y[2] = csub(t0, t2);
+    y[1] = cadd(t1, rt);
+    y[3] = csub(t1, rt);
+}
+
 // One Stockham pass of radix R over a batch of nb transforms of length L, on
 // complex type T (double2 or float2).
 // SIGN = -1: forward  sum_j x_j exp(-2 pi i jk/L);  SIGN = +1: backward (unscaled).
@@ -194,7 +212,41 @@ __device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __re
             v[1].x = fmat(h3, rt.x, m1.x);
             v[1].y = fmat(h3, rt.y, m1.y);
             v[2].x = fmat(-h3, rt.x, m1.x);
-            v[2].y = fmat(-h3, rt.y, m1.y);
+            v[2].y = fmat(-h3, rt.y, m1.y);        } else if (R == 8) {
+            // 8-point DFT of x_r = w_r v_r: 4-point DFTs of the even and of the odd
+            // samples, the odd ones times e^(-/+ 2 pi i k/8), then one radix-2 level
+            T x[8];
+            x[0] = v[0];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) x[r] = first ? v[r] : cmul(w[r], v[r]);
+            T e[4], o[4];
+            dft4<SIGN>(x[0], x[2], x[4], x[6], e);
+            dft4<SIGN>(x[1], x[3], x[5], x[7], o);
+            const RT c = rconst<RT>(0.70710678118654752440);  // 1/sqrt(2)
+            T o1, o2, o3;
+            if (SIGN < 0) {  // (1 - i)/sqrt2, -i, (-1 - i)/sqrt2
+                o1.x = (o[1].x + o[1].y) * c;
+                o1.y = (o[1].y - o[1].x) * c;
+                o2.x = o[2].y;
+                o2.y = -o[2].x;
+                o3.x = (o[3].y - o[3].x) * c;
+                o3.y = -((o[3].x + o[3].y) * c);
+            } else {         // (1 + i)/sqrt2, +i, (-1 + i)/sqrt2
+                o1.x = (o[1].x - o[1].y) * c;
+                o1.y = (o[1].x + o[1].y) * c;
+                o2.x = -o[2].y;
+                o2.y = o[2].x;
+                o3.x = -((o[3].x + o[3].y) * c);
+                o3.y = (o[3].x - o[3].y) * c;
+            }
+            v[0] = cadd(e[0], o[0]);
+            v[4] = csub(e[0], o[0]);
+            v[1] = cadd(e[1], o1);
+            v[5] = csub(e[1], o1);
+            v[2] = cadd(e[2], o2);
+            v[6] = csub(e[2], o2);
+            v[3] = cadd(e[3], o3);
+            v[7] = csub(e[3], o3);
         }
         const int idx = (j / Ns) * Ns * R + k;
 #pragma unroll
@@ -212,18 +264,24 @@ __device__ __forceinline__ T* fft_batched(T* buf0, T* buf1, const FftPlan& pl, i
     int Ns = 1;
     const int tid = threadIdx.x, nth = blockDim.x;
     const T* tw = Cx<T>::tw(pl);
+    constexpr bool f32 = sizeof(typename Cx<T>::R) == sizeof(float);  // FP32: the radix-8 factorisation
+    const int npass = f32 ? pl.npass8 : pl.npass;
     __syncthreads();
-    for (int p = 0; p < pl.npass; ++p) {
-        const int R = pl.radix[p];
+    for (int p = 0; p < npass; ++p) {
+        const int R = f32 ? pl.radix8[p] : pl.radix[p];
         if (p == 0) {  // Ns == 1: unit twiddles
-            if (R == 4)
+            if (R == 8)
+                stockham_pass<SIGN, 8, true>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
+            else if (R == 4)
                 stockham_pass<SIGN, 4, true>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
             else if (R == 2)
                 stockham_pass<SIGN, 2, true>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
             else
                 stockham_pass<SIGN, 3, true>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
         } else {
-            if (R == 4)
+            if (R == 8)
+                stockham_pass<SIGN, 8, false>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
+            else if (R == 4)
                 stockham_pass<SIGN, 4, false>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);
             else if (R == 2)
                 stockham_pass<SIGN, 2, false>(a, b, pl.L, Ns, tw, pl.tws, nb, tid, nth);

@@ -17,7 +17,9 @@ struct FftPlan {
     int L;
     int npass;
     int tws;  // stride of the twiddle table: tw[tws * j] = exp(-2 pi i j / L)
-    int radix[MAX_PASSES];
+    int radix[MAX_PASSES];   // FP64 and double-float transforms: radix 3, then 4s and 2s
+    int npass8;
+    int radix8[MAX_PASSES];  // FP32 transforms: radix 3, then 8s, 4s and 2s (fewer passes)
     const double2* tw;  // tw[j] = exp(-2 pi i j / L), j < L
     const float2* twf;  // the same, rounded to FP32 (mixed-precision explicit stage)
     const float4* twdd; // the same as double-float pairs (hi, lo) of (re, im), or null
