@@ -50,10 +50,12 @@ def test_galerkin_steps_match_oracle_tiny(scheme, amp):
     gpu.close()
 
 
-@pytest.mark.parametrize("n_r,n_phi", [(17, 48), (65, 192), (129, 384)])
+@pytest.mark.parametrize("n_r,n_phi", [(9, 24), (17, 48), (65, 192), (129, 384)])
 def test_galerkin_sizes_and_implicit_buoyancy(n_r, n_phi):
-    """Ragged and small systems (n_r = 17: 6 streamfunction unknowns, fewer than
-    the 8 subdiagonals) and the temperature-first ordering of implicit buoyancy."""
+    """Ragged and small systems (n_r = 9, the smallest grid: one streamfunction
+    unknown and three for temperature; n_r = 17: 6 streamfunction unknowns, fewer
+    than the 8 subdiagonals) and the temperature-first ordering of implicit
+    buoyancy."""
     for buoy in (False, True):
         gpu, ora = make_pair(n_r, n_phi, 1e-3, 3.0, "CNAB2", 1e-4, buoy=buoy)
         th = inputs.theta_init(n_r, n_phi, 1e-2, 11, cfg=1, m_min=0)
