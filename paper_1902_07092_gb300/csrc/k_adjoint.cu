@@ -109,7 +109,6 @@ __global__ void __launch_bounds__(NTA) k_adj_grid_to_spec(StepParams P, VecSet w
     double2* c1 = c0 + N;
     double2* c2 = c1 + N;         // [2][N] work
     double2* c3 = c2 + N;
-    double2* c4 = c3 + N;         // scan scratch
     const int tid = threadIdx.x, nth = blockDim.x;
     const double dm = (double)m;
     const double2* wp = w.psi + (size_t)m * nc;
@@ -577,7 +576,7 @@ cudaError_t launch_vec_add(const StepParams& P, VecSet a, VecSet b, cudaStream_t
 
 size_t smem_adj_grid_to_spec(const StepParams& P) {
     const int L = 2 * P.K;
-    return sizeof(double2) * (2 * adj_batch(L) * L + 5 * P.n_r);
+    return sizeof(double2) * (2 * adj_batch(L) * L + 4 * P.n_r);
 }
 size_t smem_adj_spec_to_grid(const StepParams& P) {
     const int L = 2 * P.K;

@@ -1126,7 +1126,6 @@ size_t smem_solve_mb(const StepParams& P, int MB) { return sizeof(double) * solv
 
 }  // namespace
 
-size_t smem_solve(const StepParams& P) { return smem_solve_mb(P, 1); }
 
 cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFactors& F, VecSet y_out,
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st) {

@@ -181,7 +181,6 @@ size_t smem_adj_grid_to_spec(const StepParams& P);
 size_t smem_adj_spec_to_grid(const StepParams& P);
 size_t smem_phi_products(const StepParams& P);
 size_t smem_grid_to_spec(const StepParams& P);
-size_t smem_solve(const StepParams& P);
 size_t smem_coll_spec_to_grid(const StepParams& P);
 size_t smem_coll_grid_rows(const StepParams& P);
 
