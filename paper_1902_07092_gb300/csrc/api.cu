@@ -229,6 +229,75 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         if (d < 0 || d > 2 * h) return 0.0;
         return H.band[id][(size_t)k * (2 * h + 1) + d];
     };
+    // the streamfunction block split in two halves, rows [0, nA) and [nA, np) of D
+    // (rows and columns 4.. of the band), when its chains are long: from 40 blocks
+    // of 8 rows (n_r >= 481).  The join (interface solve, spike corrections, two
+    // barriers per solve) cost more than the halved chains saved at n_r = 257 (21
+    // blocks: solve 89.7 -> 99.6 us); at n_r = 2049 (171 blocks) 7.87 -> 6.56 ms.
+    const bool psplit = nbp >= 40;
+    const int nA = 8 * (nbp / 2), nB = np - nA;
+    std::vector<double2> hpSpk(psplit ? (size_t)M * np * 8 : 0), hpRj(psplit ? (size_t)M * 256 : 0);
+    auto split_factors = [&](const std::vector<cplx>& bp, int m, std::vector<cplx>& blk) -> bool {
+        std::vector<cplx> ba, bb;
+        if (!block_lu_twisted(bp, 4 + nA, 8, 4, ba) || !block_lu_twisted(bp, nc, 8, 4 + nA, bb)) return false;
+        blk = ba;
+        blk.insert(blk.end(), bb.begin(), bb.end());
+        // each half alone in band rows (its coupling to the other half cut), then
+        // the spikes V = D_A^{-1} E (E: A's rows x B's first 8 columns) and
+        // W = D_B^{-1} F (F: B's rows x A's last 8 columns) by pivoted band LU
+        auto half = [&](int r0, int n, std::vector<cplx>& band) {
+            band.assign((size_t)n * 17, cplx(0.0, 0.0));
+            for (int i = 0; i < n; ++i)
+                for (int d = 0; d < 17; ++d) {
+                    const int j = i - 8 + d;
+                    if (j >= 0 && j < n) band[(size_t)i * 17 + d] = bp[(size_t)(r0 + i) * 17 + d];
+                }
+        };
+        auto D = [&](int i, int j) -> cplx {  // D(i, j), i, j < np
+            const int d = j - i + 8;
+            return (d < 0 || d > 16) ? cplx(0.0, 0.0) : bp[(size_t)(i + 4) * 17 + d];
+        };
+        std::vector<cplx> bandA, bandB, La, Ua, Lb, Ub, col;
+        std::vector<unsigned char> pa, pb;
+        std::vector<double> ra, rb;
+        half(4, nA, bandA);
+        half(4 + nA, nB, bandB);
+        if (!band_lu_pivot(nA, 8, 8, bandA, La, Ua, pa, ra) || !band_lu_pivot(nB, 8, 8, bandB, Lb, Ub, pb, rb))
+            return false;
+        std::vector<cplx> V((size_t)nA * 8), Wm((size_t)nB * 8);
+        for (int c = 0; c < 8; ++c) {
+            col.assign(nA, cplx(0.0, 0.0));
+            for (int i = 0; i < nA; ++i) col[i] = D(i, nA + c);
+            band_lu_pivot_solve(nA, 8, 8, La, Ua, pa, ra, col.data());
+            for (int i = 0; i < nA; ++i) V[(size_t)i * 8 + c] = col[i];
+            col.assign(nB, cplx(0.0, 0.0));
+            for (int i = 0; i < nB; ++i) col[i] = D(nA + i, nA - 8 + c);
+            band_lu_pivot_solve(nB, 8, 8, Lb, Ub, pb, rb, col.data());
+            for (int i = 0; i < nB; ++i) Wm[(size_t)i * 8 + c] = col[i];
+        }
+        std::vector<cplx> J(256, cplx(0.0, 0.0)), Jinv;
+        for (int r = 0; r < 8; ++r) {
+            J[(size_t)r * 16 + r] = 1.0;
+            J[(size_t)(8 + r) * 16 + 8 + r] = 1.0;
+            for (int c = 0; c < 8; ++c) {
+                J[(size_t)r * 16 + 8 + c] = V[(size_t)(nA - 8 + r) * 8 + c];
+                J[(size_t)(8 + r) * 16 + c] = Wm[(size_t)r * 8 + c];
+            }
+        }
+        if (!dense_inverse(16, J, Jinv)) return false;
+        for (int i = 0; i < nA; ++i)
+            for (int c = 0; c < 8; ++c) {
+                const cplx v = V[(size_t)i * 8 + c];
+                hpSpk[((size_t)m * np + i) * 8 + c] = make_double2(v.real(), v.imag());
+            }
+        for (int i = 0; i < nB; ++i)
+            for (int c = 0; c < 8; ++c) {
+                const cplx v = Wm[(size_t)i * 8 + c];
+                hpSpk[((size_t)m * np + nA + i) * 8 + c] = make_double2(v.real(), v.imag());
+            }
+        for (int i = 0; i < 256; ++i) hpRj[(size_t)m * 256 + i] = make_double2(Jinv[i].real(), Jinv[i].imag());
+        return true;
+    };
     auto work = [&](int m0, int m1) {
         std::vector<cplx> bp((size_t)nc * 17);
         std::vector<double> bt((size_t)nc * 9);
@@ -256,7 +325,12 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
                     continue;
                 }
                 std::vector<cplx> blk;
-                if (!block_lu_twisted(bp, nc, 8, 4, blk)) {
+                if (!psplit) {
+                    if (!block_lu_twisted(bp, nc, 8, 4, blk)) {
+                        bad[m] = 1;
+                        continue;
+                    }
+                } else if (!split_factors(bp, m, blk)) {
                     bad[m] = 1;
                     continue;
                 }
@@ -329,6 +403,11 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         for (int d = 0; d < 9; ++d) bu8[(size_t)k * 17 + d + 4] = bu[(size_t)k * 9 + d];
     if (!block_lu_twisted(bu8, nc, 8, 2, ub)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
     UPLOAD(F.pBlk, double2, hpK);
+    F.psplit = psplit ? 1 : 0;
+    if (psplit) {
+        UPLOAD(F.pSpk, double2, hpSpk);
+        UPLOAD(F.pRj, double2, hpRj);
+    }
     UPLOAD(F.pY, double2, hpY);
     UPLOAD(F.pSinv, double2, hpS);
     UPLOAD(F.pBand, double2, hpB);

@@ -612,6 +612,26 @@ bool band_lu_pivot(int n, int kl, int ku, const std::vector<T>& band, std::vecto
     return true;
 }
 
+template <class T>
+void band_lu_pivot_solve(int n, int kl, int ku, const std::vector<T>& Lm, const std::vector<T>& Ucol,
+                         const std::vector<unsigned char>& piv, const std::vector<double>& rs, T* b) {
+    const int kk = kl + ku;
+    for (int i = 0; i < n; ++i) b[i] *= rs[i];
+    for (int j = 0; j < n; ++j) {  // L z = P b, the interchanges interleaved
+        const int p = j + piv[j];
+        if (p != j) std::swap(b[j], b[p]);
+        for (int t = 0; t < kl && j + 1 + t < n; ++t) b[j + 1 + t] -= Lm[(size_t)j * kl + t] * b[j];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // U x = z with U's columns divided by U_ii
+        const T yi = b[i];
+        for (int t = 1; t <= kk && i - t >= 0; ++t) b[i - t] -= Ucol[(size_t)i * (kk + 1) + t] * yi;
+        b[i] = yi * Ucol[(size_t)i * (kk + 1)];
+    }
+}
+
+template void band_lu_pivot_solve<cplx>(int, int, int, const std::vector<cplx>&, const std::vector<cplx>&,
+                                        const std::vector<unsigned char>&, const std::vector<double>&, cplx*);
+
 template bool band_lu_pivot<double>(int, int, int, const std::vector<double>&, std::vector<double>&,
                                     std::vector<double>&, std::vector<unsigned char>&, std::vector<double>&);
 template bool band_lu_pivot<cplx>(int, int, int, const std::vector<cplx>&, std::vector<cplx>&, std::vector<cplx>&,

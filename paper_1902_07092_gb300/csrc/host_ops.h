@@ -102,6 +102,11 @@ template <class T>
 bool band_lu_pivot(int n, int kl, int ku, const std::vector<T>& band, std::vector<T>& Lm, std::vector<T>& Ucol,
                    std::vector<unsigned char>& piv, std::vector<double>& rs);
 
+// Solve with band_lu_pivot's factors, in place: b (n entries) <- G^{-1} b.
+template <class T>
+void band_lu_pivot_solve(int n, int kl, int ku, const std::vector<T>& Lm, const std::vector<T>& Ucol,
+                         const std::vector<unsigned char>& piv, const std::vector<double>& rs, T* b);
+
 // ---------------------------------------------------------------------------
 // Chebyshev collocation (Section 3.1), fields held as Gauss-Lobatto grid values.
 // ---------------------------------------------------------------------------

@@ -247,6 +247,37 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
     pair_sync(bar);
 }
 
+// Join of the streamfunction block solved in two halves (rows [0, nA) by warps
+// 0-1, [nA, n) by warps 6-7; DevFactors psplit): x holds each half's own solution
+// g.  The interface unknowns, A's last block and B's first, are
+// [x_A,last; x_B,first] = Rj [g_A,last; g_B,first], Rj the inverse of
+// [[I, V_last], [W_first, I]]; then x_A = g_A - V x_B,first and
+// x_B = g_B - W x_A,last with the spikes V = D_A^{-1} E, W = D_B^{-1} F (spk rows
+// < nA: V, the rest: W).  Whole CTA, after a __syncthreads that published x;
+// ends with one.  act = false: no memory accesses.
+__device__ void split_join(double2* x, int n, int nA, const double2* __restrict__ spk, const double2* __restrict__ rj,
+                           bool act) {
+    __shared__ double2 xi[16];
+    const int tid = threadIdx.x;
+    if (act && tid < 16) {
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) acc = cfma(__ldg(&rj[tid * 16 + c]), x[c < 8 ? nA - 8 + c : nA + c - 8], acc);
+        xi[tid] = acc;
+    }
+    __syncthreads();
+    if (act)
+        for (int i = tid; i < n; i += blockDim.x) {
+            const double2* row = spk + (size_t)i * 8;
+            const double2* v = (i < nA) ? xi + 8 : xi;
+            double2 t = x[i];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) t = fms(t, __ldg(&row[c]), v[c]);
+            x[i] = t;
+        }
+    __syncthreads();
+}
+
 __device__ __forceinline__ double2 warp_sum(double2 v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -656,6 +687,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
     const int np = nc - 4, nt = nc - 2;
     const int nbp = (np + 7) / 8, nbt = (nt + 7) / 8;
+    const int nA = 8 * (nbp / 2);  // first half of a split streamfunction block (F.psplit)
     SolveSmem s = carve<MB>(sm, nc);
     const bool has_u = (m0 == 0);
 
@@ -709,8 +741,14 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         if (warp < 2) {
             if (do_p) {
                 const bool act = m0 > 0;
-                pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, np,
+                pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, F.psplit ? nA : np,
                                     F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
+            }
+        } else if (warp >= 6) {
+            if (do_p && F.psplit) {  // the second half of the streamfunction block
+                const bool act = m0 > 0;
+                pair_block_solve<8>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.px[0] + 4 + nA, np - nA,
+                                    F.pBlk + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
             }
         } else if (warp < 4) {
             if (do_t) {
@@ -727,6 +765,9 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
                                     3);
         }
         __syncthreads();
+        if (do_p && F.psplit)
+            split_join(s.px[0] + 4, np, nA, F.pSpk + (size_t)(m0 > 0 ? m0 : 0) * np * 8,
+                       F.pRj + (size_t)(m0 > 0 ? m0 : 0) * 256, m0 > 0);
 
         // 3. Schur steps: warp 0 streamfunction, 2 temperature, 4 zonal flow
         if (warp == 0) {
@@ -824,11 +865,22 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     __syncthreads();
     if (warp < 2) {
         const bool act = m0 > 0;
-        pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.pd[0] + 4, np, F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act,
-                            warp, 1);
-        if (act && warp == 0) warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
+        pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.pd[0] + 4, F.psplit ? nA : np,
+                            F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
+        if (!F.psplit && act && warp == 0)
+            warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
+    } else if (warp >= 6 && F.psplit) {
+        const bool act = m0 > 0;
+        pair_block_solve<8>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.pd[0] + 4 + nA, np - nA,
+                            F.pBlk + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
     }
     __syncthreads();
+    if (F.psplit) {
+        split_join(s.pd[0] + 4, np, nA, F.pSpk + (size_t)(m0 > 0 ? m0 : 0) * np * 8,
+                   F.pRj + (size_t)(m0 > 0 ? m0 : 0) * 256, m0 > 0);
+        if (m0 > 0 && warp == 0) warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
+        __syncthreads();
+    }
     {
         const int per = nth / MB;
         const int sys = tid / per, t0 = sys * per;
@@ -1147,8 +1199,11 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
     cudaError_t err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (err != cudaSuccess) return err;
+    cudaFuncAttributes fa;
+    err = cudaFuncGetAttributes(&fa, k_solve<1>);
+    if (err != cudaSuccess) return err;
     const size_t smk = sm + sizeof(double) * keep_f_doubles(P.nc);
-    const int keep = smk <= (size_t)smax ? 1 : 0;
+    const int keep = smk + fa.sharedSizeBytes <= (size_t)smax ? 1 : 0;
     err = cudaFuncSetAttribute(k_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(keep ? smk : sm));
     if (err != cudaSuccess) return err;
     k_solve<1><<<P.M, NTHREADS_S, keep ? smk : sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,

@@ -53,6 +53,14 @@ struct DevFactors {
     // streamfunction, complex, H = 8: blocks [M][nb_p][3][64], Y [M][n_p][4],
     // Sinv [M][16], assembled rows 4..nc-1 of A^I_m - gamma dt B^I_m [M][n_p][17]
     double2 *pBlk, *pY, *pSinv, *pBand;
+    // streamfunction block split in two halves (psplit = 1 when n_p has >= 40
+    // blocks; rows [0, n_A), n_A = 8 floor(nb_p/2), and [n_A, n_p)): pBlk then
+    // holds each half's two-sided factors, A's blocks first; spikes pSpk
+    // [M][n_p][8] (rows < n_A: V = D_A^{-1} E, the coupling of A's last block rows
+    // to B's first block columns; rows >= n_A: W = D_B^{-1} F); pRj [M][16][16]
+    // the inverse of the interface system [[I, V_last], [W_first, I]]
+    int psplit;
+    double2 *pSpk, *pRj;
     // temperature, real, blocks of H = 8 rows (band half width 4, padded): blocks
     // [M][nb_t][3][64], nb_t = ceil(n_t/8), Y [M][n_t][2], Sinv [M][4],
     // assembled rows 2..nc-1 of D^I - gamma dt F^I_m/Pr [M][n_t][9]

@@ -249,3 +249,25 @@ def test_azimuthal_products_in_ddfloat_and_fp64_match_oracle(n_r, n_phi):
         print("azimuthal_dd=%d n_r=%d: psi %.2e theta %.2e u %.2e (tol %.1e)" % ((dd, n_r) + errs + (tol,)))
         assert max(errs) <= tol
         gpu.close()
+
+
+@pytest.mark.parametrize("scheme", ["CNAB2", "ARS443"])
+def test_steps_match_oracle_split_streamfunction_solve(scheme):
+    """n_r = 513 (N_c = 341, 43 blocks of 8 rows): the streamfunction block is
+    solved in two halves joined through spikes (from 40 blocks); explicit
+    buoyancy, all fields nonzero, two steps.  5e-12, the bound of the n_r = 1025
+    tests: the block's conditioning grows with N_c."""
+    n_r, n_phi = 513, 24
+    gpu, ora = make_pair(n_r, n_phi, 1e-5, 5.0, scheme, 1e-7)
+    th = inputs.theta_init(n_r, n_phi, 1e-3, 31, cfg=1)
+    psi = inputs.theta_init(n_r, n_phi, 1e-5, 32, cfg=8)
+    psi[0] = 0.0
+    u = inputs.theta_init(n_r, n_phi, 1e-3, 33, cfg=9, m_min=0)[0].real.copy()
+    gpu.set_state(th, psi, u)
+    ora.set_state(psi, th, u)
+    for k in range(2):
+        gpu.step(1)
+        ora.step()
+        e = assert_state_close(gpu.get_state(), ora.y, 5e-12)
+        print("split solve n_r=513 %s step %d: state %.2e" % (scheme, k + 1, e["state"]))
+    gpu.close()
