@@ -98,8 +98,8 @@ def algorithmic_flops(n_r, n_phi, scheme, radial="integration"):
 # DRAM bytes (read + write) per launch of the roofline kernel from one ncu capture
 # of this workload (summaries under profiles/); null for kernels not captured.
 NCU_TRAFFIC = {
-    ("sparse_n257_p768", "solve"): (48.49e6 + 0.32e6, "profiles/imex_step_kernels_n257_p768.md"),
-    ("large_n2049_p6144", "solve"): (4420.4e6 + 237.5e6, "profiles/solve_kernel_n2049_p6144.md"),
+    ("sparse_n257_p768", "solve"): (48.52e6 + 0.17e6, "profiles/imex_step_kernels_n257_p768.md"),
+    ("large_n2049_p6144", "solve"): (5161.6e6 + 238.1e6, "profiles/solve_kernel_n2049_p6144.md"),
     ("coll_n257_p768", "solve"): (735.4e6 + 6.9e6, "profiles/collocation_step_kernels_n257_p768.md"),
     ("galerkin_n257_p768", "solve"): (34.58e6 + 0.003e6, "profiles/galerkin_step_kernels_n257_p768.md"),
 }
