@@ -101,7 +101,15 @@ __device__ __forceinline__ float2 fma_x(float a, float2 b, float2 acc) {
 __device__ __forceinline__ float2 sub_x(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
-constexpr int PFB = 2;  // blocks of coefficients prefetched ahead in the chains
+// Blocks of coefficients prefetched ahead in the chains.  With a few CTAs per SM
+// (N_c up to ~600) two blocks cover the L2 latency at little register cost; the
+// large systems run one CTA per SM (shared memory) with their factors streamed
+// from HBM, where the chains wait on that latency unless loads go further ahead:
+// there the streamfunction chains (FP64 complex coefficients) prefetch 4 blocks
+// and the FP32 temperature chains 8.
+constexpr int PFB = 2;
+constexpr int PFB_DEEP_P = 4;
+constexpr int PFB_DEEP_T = 8;
 
 // Barrier of the two warps (64 threads) of a solver pair.
 __device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
@@ -114,7 +122,7 @@ __device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 6
 // (n entries); rows of b at or beyond n read as zero.  Both warps of the pair
 // must call it (bar: named barrier id); act = false skips all memory accesses.
 // On return the whole of x is visible to both warps.
-template <int H, class TF, class TX>
+template <int H, int PF, class TF, class TX>
 __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __restrict__ blk, bool act, int half,
                                  int bar) {
     constexpr int CPL = H / 4;
@@ -134,21 +142,21 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
     // forward: Z_k = b_k - [0]_k Z_prev
     {
         TX prev[CPL];
-        TF cur[PFB][CPL], nxt[PFB][CPL];
+        TF cur[PF][CPL], nxt[PF][CPL];
 #pragma unroll
         for (int q = 0; q < CPL; ++q) prev[q] = zero<TX>();
 #pragma unroll
-        for (int i = 0; i < PFB; ++i)
+        for (int i = 0; i < PF; ++i)
 #pragma unroll
             for (int q = 0; q < CPL; ++q) cur[i][q] = (i < len) ? coef(k_fw + dir * i, 0, q) : zero<TF>();
-        for (int i0 = 0; i0 < len; i0 += PFB) {
+        for (int i0 = 0; i0 < len; i0 += PF) {
 #pragma unroll
-            for (int i = 0; i < PFB; ++i)
+            for (int i = 0; i < PF; ++i)
 #pragma unroll
                 for (int q = 0; q < CPL; ++q)
-                    nxt[i][q] = (i0 + PFB + i < len) ? coef(k_fw + dir * (i0 + PFB + i), 0, q) : zero<TF>();
+                    nxt[i][q] = (i0 + PF + i < len) ? coef(k_fw + dir * (i0 + PF + i), 0, q) : zero<TF>();
 #pragma unroll
-            for (int i = 0; i < PFB; ++i) {
+            for (int i = 0; i < PF; ++i) {
                 if (i0 + i < len) {
                     const int k = k_fw + dir * (i0 + i);
                     const int row = k * H + r;
@@ -164,7 +172,7 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
                 }
             }
 #pragma unroll
-            for (int i = 0; i < PFB; ++i)
+            for (int i = 0; i < PF; ++i)
 #pragma unroll
                 for (int q = 0; q < CPL; ++q) cur[i][q] = nxt[i][q];
         }
@@ -197,26 +205,26 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
     }
     // backward: x_k = [1]_k Z_k - [2]_k x_prev, walking away from the middle
     {
-        TF cu[PFB][CPL], ch[PFB][CPL], nu[PFB][CPL], nh[PFB][CPL];
+        TF cu[PF][CPL], ch[PF][CPL], nu[PF][CPL], nh[PF][CPL];
         const int bdir = half ? 1 : -1;
 #pragma unroll
-        for (int i = 0; i < PFB; ++i)
+        for (int i = 0; i < PF; ++i)
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
                 cu[i][q] = (i < len) ? coef(k_bw + bdir * i, 1, q) : zero<TF>();
                 ch[i][q] = (i < len) ? coef(k_bw + bdir * i, 2, q) : zero<TF>();
             }
-        for (int i0 = 0; i0 < len; i0 += PFB) {
+        for (int i0 = 0; i0 < len; i0 += PF) {
 #pragma unroll
-            for (int i = 0; i < PFB; ++i)
+            for (int i = 0; i < PF; ++i)
 #pragma unroll
                 for (int q = 0; q < CPL; ++q) {
-                    const bool in = i0 + PFB + i < len;
-                    nu[i][q] = in ? coef(k_bw + bdir * (i0 + PFB + i), 1, q) : zero<TF>();
-                    nh[i][q] = in ? coef(k_bw + bdir * (i0 + PFB + i), 2, q) : zero<TF>();
+                    const bool in = i0 + PF + i < len;
+                    nu[i][q] = in ? coef(k_bw + bdir * (i0 + PF + i), 1, q) : zero<TF>();
+                    nh[i][q] = in ? coef(k_bw + bdir * (i0 + PF + i), 2, q) : zero<TF>();
                 }
 #pragma unroll
-            for (int i = 0; i < PFB; ++i) {
+            for (int i = 0; i < PF; ++i) {
                 if (i0 + i < len) {
                     const int k = k_bw + bdir * (i0 + i);
                     TX pz = zero<TX>(), ph = zero<TX>();
@@ -234,7 +242,7 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
                 }
             }
 #pragma unroll
-            for (int i = 0; i < PFB; ++i)
+            for (int i = 0; i < PF; ++i)
 #pragma unroll
                 for (int q = 0; q < CPL; ++q) {
                     cu[i][q] = nu[i][q];
@@ -602,7 +610,7 @@ __device__ void refine_zonal_flow(const StepParams& P, const DevFactors& F, Solv
     __syncthreads();
     double* du = reinterpret_cast<double*>(s.pw[0]);
     if (warp == 4 || warp == 5) {
-        pair_block_solve<8>(s.uf + 2, reinterpret_cast<double*>(s.pf[0]), du + 2, nt, F.uBlk, true, warp - 4, 3);
+        pair_block_solve<8, PFB>(s.uf + 2, reinterpret_cast<double*>(s.pf[0]), du + 2, nt, F.uBlk, true, warp - 4, 3);
         if (warp == 4) {
             double t0 = 0.0, t1 = 0.0;
             for (int j = lane; j < nt; j += 32) {
@@ -630,40 +638,53 @@ __device__ void refine_zonal_flow(const StepParams& P, const DevFactors& F, Solv
     __syncthreads();
 }
 
-template <int MB>
-__device__ void temperature_corrections(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u) {
-    const int nc = P.nc, nt = nc - 2, nbt = (nt + 7) / 8;
+// FP64 residual r = f - L x of the temperature system of mode m0 (MB == 1),
+// rounded to FP32 into s.tr: the assembled rows by the whole CTA, the two tau
+// rows (r = 0 - tau x) by warp tw.  The caller synchronises.
+__device__ void temperature_residual(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, int tw) {
+    const int nc = P.nc, nt = nc - 2;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
-    if (F.ir_t) {
-        // x += S32^{-1}(f - L x), ir_t times, residuals in FP64 (MB == 1)
-        for (int it = 0; it < F.ir_t; ++it) {
-            for (int k = 2 + tid; k < nc; k += nth) {
-                const double* row = F.tBand + ((size_t)m0 * nt + (k - 2)) * 9;
-                double2 acc = s.tf[0][k];
+    for (int k = 2 + tid; k < nc; k += nth) {
+        const double* row = F.tBand + ((size_t)m0 * nt + (k - 2)) * 9;
+        double2 acc = s.tf[0][k];
 #pragma unroll
-                for (int d = 0; d < 9; ++d) {
-                    const int n = k - 4 + d;
-                    if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), s.tx[0][n]);
-                }
-                s.tr[k] = to_f2(acc);
-            }
-            if (warp == 0) {  // tau rows: r = 0 - tau x
-                double2 t0 = make_double2(0.0, 0.0), t1 = t0;
-                for (int j = lane; j < nc; j += 32) {
-                    const double2 xv = s.tx[0][j];
-                    const double b0 = __ldg(&P.ops.tau_dir[j]), b1 = __ldg(&P.ops.tau_dir[nc + j]);
-                    t0.x = fma(b0, xv.x, t0.x);
-                    t0.y = fma(b0, xv.y, t0.y);
-                    t1.x = fma(b1, xv.x, t1.x);
-                    t1.y = fma(b1, xv.y, t1.y);
-                }
-                t0 = warp_sum(t0);
-                t1 = warp_sum(t1);
-                if (lane < 2) s.tr[lane] = to_f2(lane ? make_double2(-t1.x, -t1.y) : make_double2(-t0.x, -t0.y));
-            }
+        for (int d = 0; d < 9; ++d) {
+            const int n = k - 4 + d;
+            if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), s.tx[0][n]);
+        }
+        s.tr[k] = to_f2(acc);
+    }
+    if (warp == tw) {
+        double2 t0 = make_double2(0.0, 0.0), t1 = t0;
+        for (int j = lane; j < nc; j += 32) {
+            const double2 xv = s.tx[0][j];
+            const double b0 = __ldg(&P.ops.tau_dir[j]), b1 = __ldg(&P.ops.tau_dir[nc + j]);
+            t0.x = fma(b0, xv.x, t0.x);
+            t0.y = fma(b0, xv.y, t0.y);
+            t1.x = fma(b1, xv.x, t1.x);
+            t1.y = fma(b1, xv.y, t1.y);
+        }
+        t0 = warp_sum(t0);
+        t1 = warp_sum(t1);
+        if (lane < 2) s.tr[lane] = to_f2(lane ? make_double2(-t1.x, -t1.y) : make_double2(-t0.x, -t0.y));
+    }
+}
+
+// The FP32-refined temperature solve (F.ir_t > 0, MB == 1): x += S32^{-1}(f - L x)
+// for the passes it0 .. ir_t - 1 (pass 0 may have run beside the streamfunction
+// refinement), then the FP64 refinement of the zonal flow (mode 0).
+template <int MB, bool DEEP>
+__device__ void temperature_corrections(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0, bool has_u,
+                                        int it0) {
+    const int nc = P.nc, nt = nc - 2, nbt = (nt + 7) / 8;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5;
+    constexpr int PT = DEEP ? PFB_DEEP_T : PFB;
+    if (F.ir_t) {
+        for (int it = it0; it < F.ir_t; ++it) {
+            temperature_residual(P, F, s, m0, 0);
             __syncthreads();
             if (warp == 2 || warp == 3)
-                pair_block_solve<8>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2, 2);
+                pair_block_solve<8, PT>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2, 2);
             __syncthreads();
             if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
             __syncthreads();
@@ -674,10 +695,9 @@ __device__ void temperature_corrections(const StepParams& P, const DevFactors& F
         }
         if (has_u) refine_zonal_flow(P, F, s);  // FP64
     }
-
 }
 
-template <int MB>
+template <int MB, bool DEEP>
 __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, DevFactors F, VecSet y_out,
                                                       VecSet mass_out, VecSet imp_out, int want_mass,
                                                       int want_imp, int keep_f) {
@@ -690,6 +710,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     const int nA = 8 * (nbp / 2);  // first half of a split streamfunction block (F.psplit)
     SolveSmem s = carve<MB>(sm, nc);
     const bool has_u = (m0 == 0);
+    constexpr int PP = DEEP ? PFB_DEEP_P : PFB, PT = DEEP ? PFB_DEEP_T : PFB;
 
     // 1. right-hand side sum_t c_t V_t (tau rows zero)
     for (int idx = tid; idx < MB * nc; idx += nth) {
@@ -741,27 +762,27 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         if (warp < 2) {
             if (do_p) {
                 const bool act = m0 > 0;
-                pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, F.psplit ? nA : np,
+                pair_block_solve<8, PP>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, F.psplit ? nA : np,
                                     F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
             }
         } else if (warp >= 6) {
             if (do_p && F.psplit) {  // the second half of the streamfunction block
                 const bool act = m0 > 0;
-                pair_block_solve<8>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.px[0] + 4 + nA, np - nA,
+                pair_block_solve<8, PP>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.px[0] + 4 + nA, np - nA,
                                     F.pBlk + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
             }
         } else if (warp < 4) {
             if (do_t) {
                 if (F.ir_t)
-                    pair_block_solve<8>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2,
+                    pair_block_solve<8, PT>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2,
                                         2);
                 else
-                    pair_block_solve<8>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 192, true,
+                    pair_block_solve<8, PP>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m0 * nbt * 192, true,
                                         warp - 2, 2);
             }
         } else if (warp < 6 && has_u) {
             if (do_t)
-                pair_block_solve<8>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4,
+                pair_block_solve<8, PFB>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4,
                                     3);
         }
         __syncthreads();
@@ -822,11 +843,15 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
             for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
             __syncthreads();
         }
-        if (P.buoy_imp && pass == 0) temperature_corrections<MB>(P, F, s, m0, has_u);
+        if (P.buoy_imp && pass == 0) temperature_corrections<MB, DEEP>(P, F, s, m0, has_u, 0);
     }
 
     // 5. one refinement step of the streamfunction solve: r = f - L x (a second
-    //    step gains nothing: FP64 residuals limit the accuracy to ~cond * eps)
+    //    step gains nothing: FP64 residuals limit the accuracy to ~cond * eps).
+    //    With the FP32-refined temperature solve and explicit buoyancy the first
+    //    temperature correction runs beside it: its chain (FP32, warps 2-3) beside
+    //    the streamfunction chains (FP64), on disjoint arrays.
+    const bool fuse_t = F.ir_t && !P.buoy_imp;
     for (int it = 0; it < 1; ++it) {
     for (int idx = tid; idx < MB * nc; idx += nth) {
         const int mi = idx / nc, k = idx - mi * nc, m = m0 + mi;
@@ -862,17 +887,21 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
             if (lane < 4) s.pf[warp][lane] = csub(s.pf[warp][lane], t[lane]);
         }
     }
+    if (fuse_t) temperature_residual(P, F, s, m0, 1);
     __syncthreads();
     if (warp < 2) {
         const bool act = m0 > 0;
-        pair_block_solve<8>(s.pf[0] + 4, s.pw[0], s.pd[0] + 4, F.psplit ? nA : np,
+        pair_block_solve<8, PP>(s.pf[0] + 4, s.pw[0], s.pd[0] + 4, F.psplit ? nA : np,
                             F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
         if (!F.psplit && act && warp == 0)
             warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
     } else if (warp >= 6 && F.psplit) {
         const bool act = m0 > 0;
-        pair_block_solve<8>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.pd[0] + 4 + nA, np - nA,
+        pair_block_solve<8, PP>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.pd[0] + 4 + nA, np - nA,
                             F.pBlk + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
+    } else if (fuse_t && warp < 4) {
+        pair_block_solve<8, PT>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2, 2);
+        if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
     }
     __syncthreads();
     if (F.psplit) {
@@ -886,16 +915,18 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         const int sys = tid / per, t0 = sys * per;
         const int m = m0 + sys;
         if (sys < MB && m < M && m > 0) schur_update<4>(s.pd[sys], nc, F.pY + (size_t)m * np * 4, t0, per);
+        if (fuse_t) schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
     }
     __syncthreads();
     for (int idx = tid; idx < MB * nc; idx += nth) {
         const int mi = idx / nc, n = idx - mi * nc, m = m0 + mi;
         if (m >= M) continue;
         s.px[mi][n] = (m == 0) ? make_double2(0.0, 0.0) : cadd(s.px[mi][n], s.pd[mi][n]);
+        if (fuse_t) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
     }
     __syncthreads();
     }
-    if (!P.buoy_imp) temperature_corrections<MB>(P, F, s, m0, has_u);
+    if (!P.buoy_imp) temperature_corrections<MB, DEEP>(P, F, s, m0, has_u, fuse_t ? 1 : 0);
 
     // 6. store, then mass / implicit operators for later stages
     for (int idx = tid; idx < MB * nc; idx += nth) {
@@ -1193,6 +1224,9 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
                                                       want_imp ? 1 : 0);
         return cudaGetLastError();
     }
+    // the systems with FP32-refined temperature solves (N_c > 600) take the deep
+    // chain prefetch (one or two CTAs per SM by shared memory)
+    auto kern = F.ir_t ? k_solve<1, true> : k_solve<1, false>;
     // the epilogue reads the assembled right-hand sides from shared memory where
     // they fit (up to N_c ~ 1300), else sums the terms again
     int dev = 0, smax = 0;
@@ -1200,14 +1234,14 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (err != cudaSuccess) return err;
     cudaFuncAttributes fa;
-    err = cudaFuncGetAttributes(&fa, k_solve<1>);
+    err = cudaFuncGetAttributes(&fa, kern);
     if (err != cudaSuccess) return err;
     const size_t smk = sm + sizeof(double) * keep_f_doubles(P.nc);
     const int keep = smk + fa.sharedSizeBytes <= (size_t)smax ? 1 : 0;
-    err = cudaFuncSetAttribute(k_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(keep ? smk : sm));
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(keep ? smk : sm));
     if (err != cudaSuccess) return err;
-    k_solve<1><<<P.M, NTHREADS_S, keep ? smk : sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
-                                                         want_imp ? 1 : 0, keep);
+    kern<<<P.M, NTHREADS_S, keep ? smk : sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+                                                   want_imp ? 1 : 0, keep);
     return cudaGetLastError();
 }
 
