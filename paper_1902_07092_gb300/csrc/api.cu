@@ -212,6 +212,59 @@ struct HostOps {
     std::vector<double> band[OP_COUNT];  // band storage with each operator's own half width
 };
 
+// A banded block D (rows and columns [off, off + n) of a band of half width hw,
+// rows of 2 hw + 1 entries) split into halves [0, nA) and [nA, n), coupled
+// through 8 columns each way: the spikes V = D_A^{-1} E (E: A's rows x B's first
+// 8 columns) and W = D_B^{-1} F (F: B's rows x A's last 8 columns), by pivoted
+// band LU of each half with its coupling cut, and the inverse of the 16 x 16
+// interface system [[I, V_last], [W_first, I]].  V is nA x 8, W (n - nA) x 8.
+template <class T>
+bool split_spikes(const std::vector<T>& band, int hw, int off, int n, int nA, std::vector<T>& V, std::vector<T>& W,
+                  std::vector<T>& Jinv) {
+    const int w = 2 * hw + 1, nB = n - nA;
+    auto half = [&](int r0, int nh, std::vector<T>& hb) {
+        hb.assign((size_t)nh * w, T(0.0));
+        for (int i = 0; i < nh; ++i)
+            for (int d = 0; d < w; ++d) {
+                const int j = i - hw + d;
+                if (j >= 0 && j < nh) hb[(size_t)i * w + d] = band[(size_t)(off + r0 + i) * w + d];
+            }
+    };
+    auto D = [&](int i, int j) -> T {  // D(i, j), i, j < n
+        const int d = j - i + hw;
+        return (d < 0 || d >= w) ? T(0.0) : band[(size_t)(off + i) * w + d];
+    };
+    std::vector<T> bandA, bandB, La, Ua, Lb, Ub, col;
+    std::vector<unsigned char> pa, pb;
+    std::vector<double> ra, rb;
+    half(0, nA, bandA);
+    half(nA, nB, bandB);
+    if (!band_lu_pivot(nA, hw, hw, bandA, La, Ua, pa, ra) || !band_lu_pivot(nB, hw, hw, bandB, Lb, Ub, pb, rb))
+        return false;
+    V.assign((size_t)nA * 8, T(0.0));
+    W.assign((size_t)nB * 8, T(0.0));
+    for (int c = 0; c < 8; ++c) {
+        col.assign(nA, T(0.0));
+        for (int i = 0; i < nA; ++i) col[i] = D(i, nA + c);
+        band_lu_pivot_solve(nA, hw, hw, La, Ua, pa, ra, col.data());
+        for (int i = 0; i < nA; ++i) V[(size_t)i * 8 + c] = col[i];
+        col.assign(nB, T(0.0));
+        for (int i = 0; i < nB; ++i) col[i] = D(nA + i, nA - 8 + c);
+        band_lu_pivot_solve(nB, hw, hw, Lb, Ub, pb, rb, col.data());
+        for (int i = 0; i < nB; ++i) W[(size_t)i * 8 + c] = col[i];
+    }
+    std::vector<T> J(256, T(0.0));
+    for (int r = 0; r < 8; ++r) {
+        J[(size_t)r * 16 + r] = T(1.0);
+        J[(size_t)(8 + r) * 16 + 8 + r] = T(1.0);
+        for (int c = 0; c < 8; ++c) {
+            J[(size_t)r * 16 + 8 + c] = V[(size_t)(nA - 8 + r) * 8 + c];
+            J[(size_t)(8 + r) * 16 + c] = W[(size_t)r * 8 + c];
+        }
+    }
+    return dense_inverse(16, J, Jinv);
+}
+
 int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F, std::vector<void*>& al) {
     const int M = ctx->M, nc = ctx->nc, np = nc - 4, nt = nc - 2;
     const double gdt = gamma * ctx->dt;
@@ -242,49 +295,8 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         if (!block_lu_twisted(bp, 4 + nA, 8, 4, ba) || !block_lu_twisted(bp, nc, 8, 4 + nA, bb)) return false;
         blk = ba;
         blk.insert(blk.end(), bb.begin(), bb.end());
-        // each half alone in band rows (its coupling to the other half cut), then
-        // the spikes V = D_A^{-1} E (E: A's rows x B's first 8 columns) and
-        // W = D_B^{-1} F (F: B's rows x A's last 8 columns) by pivoted band LU
-        auto half = [&](int r0, int n, std::vector<cplx>& band) {
-            band.assign((size_t)n * 17, cplx(0.0, 0.0));
-            for (int i = 0; i < n; ++i)
-                for (int d = 0; d < 17; ++d) {
-                    const int j = i - 8 + d;
-                    if (j >= 0 && j < n) band[(size_t)i * 17 + d] = bp[(size_t)(r0 + i) * 17 + d];
-                }
-        };
-        auto D = [&](int i, int j) -> cplx {  // D(i, j), i, j < np
-            const int d = j - i + 8;
-            return (d < 0 || d > 16) ? cplx(0.0, 0.0) : bp[(size_t)(i + 4) * 17 + d];
-        };
-        std::vector<cplx> bandA, bandB, La, Ua, Lb, Ub, col;
-        std::vector<unsigned char> pa, pb;
-        std::vector<double> ra, rb;
-        half(4, nA, bandA);
-        half(4 + nA, nB, bandB);
-        if (!band_lu_pivot(nA, 8, 8, bandA, La, Ua, pa, ra) || !band_lu_pivot(nB, 8, 8, bandB, Lb, Ub, pb, rb))
-            return false;
-        std::vector<cplx> V((size_t)nA * 8), Wm((size_t)nB * 8);
-        for (int c = 0; c < 8; ++c) {
-            col.assign(nA, cplx(0.0, 0.0));
-            for (int i = 0; i < nA; ++i) col[i] = D(i, nA + c);
-            band_lu_pivot_solve(nA, 8, 8, La, Ua, pa, ra, col.data());
-            for (int i = 0; i < nA; ++i) V[(size_t)i * 8 + c] = col[i];
-            col.assign(nB, cplx(0.0, 0.0));
-            for (int i = 0; i < nB; ++i) col[i] = D(nA + i, nA - 8 + c);
-            band_lu_pivot_solve(nB, 8, 8, Lb, Ub, pb, rb, col.data());
-            for (int i = 0; i < nB; ++i) Wm[(size_t)i * 8 + c] = col[i];
-        }
-        std::vector<cplx> J(256, cplx(0.0, 0.0)), Jinv;
-        for (int r = 0; r < 8; ++r) {
-            J[(size_t)r * 16 + r] = 1.0;
-            J[(size_t)(8 + r) * 16 + 8 + r] = 1.0;
-            for (int c = 0; c < 8; ++c) {
-                J[(size_t)r * 16 + 8 + c] = V[(size_t)(nA - 8 + r) * 8 + c];
-                J[(size_t)(8 + r) * 16 + c] = Wm[(size_t)r * 8 + c];
-            }
-        }
-        if (!dense_inverse(16, J, Jinv)) return false;
+        std::vector<cplx> V, Wm, Jinv;
+        if (!split_spikes(bp, 8, 4, np, nA, V, Wm, Jinv)) return false;
         for (int i = 0; i < nA; ++i)
             for (int c = 0; c < 8; ++c) {
                 const cplx v = V[(size_t)i * 8 + c];
@@ -298,6 +310,12 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         for (int i = 0; i < 256; ++i) hpRj[(size_t)m * 256 + i] = make_double2(Jinv[i].real(), Jinv[i].imag());
         return true;
     };
+    // Large N_c: the temperature systems lose digits in the unpivoted block
+    // factorisation and need a refinement step.  Two FP64-residual corrections of
+    // FP32 solves reach the accuracy of the FP64 solve there (1e-13 at N_c = 1365,
+    // measured on the tau systems), with the chains on the FP32 pipe; the
+    // zonal-flow system (one mode) keeps its FP64 refinement.
+    const int ir_t = (nc > 600) ? 2 : 0;
     auto work = [&](int m0, int m1) {
         std::vector<cplx> bp((size_t)nc * 17);
         std::vector<double> bt((size_t)nc * 9);
@@ -411,7 +429,7 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
     UPLOAD(F.pY, double2, hpY);
     UPLOAD(F.pSinv, double2, hpS);
     UPLOAD(F.pBand, double2, hpB);
-    UPLOAD(F.tBlk, double, htK);
+    if (!ir_t) UPLOAD(F.tBlk, double, htK);  // with ir_t only the FP32 copy is read
     UPLOAD(F.tY, double, htY);
     UPLOAD(F.tSinv, double, htS);
     UPLOAD(F.tBand, double, htB);
@@ -419,12 +437,7 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         std::vector<double> ubd(bu.begin() + 2 * 9, bu.end());
         UPLOAD(F.uBand, double, ubd);
     }
-    // Large N_c: the temperature systems lose digits in the unpivoted block
-    // factorisation and need a refinement step.  Two FP64-residual corrections of
-    // FP32 solves reach the accuracy of the FP64 solve there (1e-13 at N_c = 1365,
-    // measured on the tau systems), with the chains on the FP32 pipe; the
-    // zonal-flow system (one mode) keeps its FP64 refinement.
-    F.ir_t = (nc > 600) ? 2 : 0;
+    F.ir_t = ir_t;
     if (F.ir_t) {
         const std::vector<float> tK32(htK.begin(), htK.end()), tY32(htY.begin(), htY.end()),
             tS32(htS.begin(), htS.end());
