@@ -271,3 +271,28 @@ def test_steps_match_oracle_split_streamfunction_solve(scheme):
         e = assert_state_close(gpu.get_state(), ora.y, 5e-12)
         print("split solve n_r=513 %s step %d: state %.2e" % (scheme, k + 1, e["state"]))
     gpu.close()
+
+
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF3"])
+def test_steps_match_oracle_fp32_refined_temperature_solve(scheme):
+    """n_r = 1025 (N_c = 682): the temperature systems are solved by FP32 block
+    chains with two FP64-residual corrections, the first beside the
+    streamfunction refinement (explicit buoyancy); the streamfunction block is
+    split in two halves; mode 0 refines its zonal flow in FP64.  All fields
+    nonzero, two steps, against the FP64 oracle.  5e-12, the bound of the
+    n_r = 1025 implicit-buoyancy test."""
+    n_r, n_phi = 1025, 24
+    gpu, ora = make_pair(n_r, n_phi, 1e-6, 5.0, scheme, 1e-9)
+    th = inputs.theta_init(n_r, n_phi, 1e-3, 41, cfg=1, m_min=0)
+    psi = inputs.theta_init(n_r, n_phi, 1e-5, 42, cfg=8)
+    psi[0] = 0.0
+    u = inputs.theta_init(n_r, n_phi, 1e-3, 43, cfg=9, m_min=0)[0].real.copy()
+    gpu.set_state(th, psi, u)
+    ora.set_state(psi, th, u)
+    for k in range(2):
+        gpu.step(1)
+        ora.step()
+        e = assert_state_close(gpu.get_state(), ora.y, 5e-12)
+        print("FP32-refined temperature n_r=1025 %s step %d: %s" % (
+            scheme, k + 1, {a: "%.2e" % b for a, b in e.items() if a != "_norms"}))
+    gpu.close()
