@@ -66,7 +66,7 @@ enum pizza_status {
     PIZZA_ECFL = -5,        /* reserved: Courant criterion exceeded              */
     PIZZA_ETIMEOUT = -6,    /* reserved: a bounded device wait gave up           */
     PIZZA_ESTATE = -7,      /* call out of order (e.g. step before dt is set)    */
-    PIZZA_EUNSUPPORTED = -8 /* valid request this build does not implement       */
+    PIZZA_EUNSUPPORTED = -8 /* valid request the library does not implement      */
 };
 
 /* Create a context.  Validation: n_r >= 9 with n_r - 1 a power of two (the
