@@ -325,11 +325,15 @@ int pizza_host_collocation(int which, int n_r, double radius_ratio, double E, do
  * library until the process exits), so the sizes are limited to
  * n_r <= PIZZA_NOALLOC_MAX_NR and n_phi <= PIZZA_NOALLOC_MAX_NPHI; larger sizes
  * return PIZZA_EINVAL with a message.  The first call on a device, and any
- * call whose (n_r, n_phi, Ra, Pr, radius_ratio) differ from the previous one on
- * that device, does a synchronous set-up (address look-up of the static arrays,
- * table upload); make that first call before any stream capture.  All calls on
- * a device share the static arrays: calls whose work overlaps on the GPU (other
- * streams, other host threads without ordering) race and give wrong results.
+ * call whose (n_r, n_phi, radius_ratio) differ from the previous one on that
+ * device, does a synchronous set-up: the address look-up of the static arrays
+ * (first call only) and the table upload, which first waits for the whole
+ * device (cudaDeviceSynchronize) so that no call queued earlier still reads the
+ * old tables, then copies on `stream` and waits for it.  Make that first call
+ * before any stream capture.  Ra and Pr change nothing in the tables.  Calls
+ * ordered on one stream are therefore correct whatever their sizes; calls whose
+ * work overlaps on the GPU (other streams or host threads without ordering)
+ * share the static arrays, race and give wrong results.
  * Errors are reported through pizza_last_error(NULL). */
 #define PIZZA_NOALLOC_MAX_NR 257
 #define PIZZA_NOALLOC_MAX_NPHI 768

@@ -52,7 +52,7 @@ struct DeviceSlot {
     double* tables = nullptr;
     bool have_params = false;  // tables hold the parameters below
     int n_r = 0, n_phi = 0;
-    double Ra = 0, Pr = 0, eta = 0;
+    double eta = 0;  // Ra and Pr enter the kernels by value, not through the tables
 };
 
 DeviceSlot g_slots[NA_MAX_DEVICES];
@@ -64,8 +64,11 @@ int na_fail(int code, const char* msg) {
 }
 
 // Set-up on the current device: resolve the device addresses of the static
-// arrays (once per device) and (re)write the tables when the parameters change.
-int na_setup(int dev, int n_r, int n_phi, double Ra, double Pr, double eta, DeviceSlot*& out) {
+// arrays (once per device) and (re)write the tables when (n_r, n_phi, eta)
+// change.  A rewrite first waits for the whole device, so that no call queued
+// earlier (on this stream or another) still reads the old tables, then copies
+// on the caller's stream and waits for that copy.
+int na_setup(int dev, int n_r, int n_phi, double eta, cudaStream_t st, DeviceSlot*& out) {
     if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(PIZZA_EINVAL, "device index beyond the supported range");
     DeviceSlot& sl = g_slots[dev];
     if (!sl.ready) {
@@ -78,7 +81,8 @@ int na_setup(int dev, int n_r, int n_phi, double Ra, double Pr, double eta, Devi
         sl.tables = static_cast<double*>(p);
         sl.ready = true;
     }
-    if (!(sl.have_params && sl.n_r == n_r && sl.n_phi == n_phi && sl.Ra == Ra && sl.Pr == Pr && sl.eta == eta)) {
+    if (!(sl.have_params && sl.n_r == n_r && sl.n_phi == n_phi && sl.eta == eta)) {
+        sl.have_params = false;  // stays false unless the whole upload succeeds
         const int nc = (2 * (n_r - 1)) / 3;
         std::vector<double> host(NA_TABLES, 0.0);
         Geom g = make_geom(eta);
@@ -96,18 +100,23 @@ int na_setup(int dev, int n_r, int n_phi, double Ra, double Pr, double eta, Devi
         std::memcpy(&host[NA_TAB_GRID + NA_TAB_TWR], twp.data(), twp.size() * sizeof(double2));
         size_t off = NA_TAB_GRID + NA_TAB_TW;
         for (int id = 0; id < OP_COUNT; ++id) {
+            if (2 * op_h(id) + 1 != NA_WIDTH[id])
+                return na_fail(PIZZA_EINVAL, "operator band width differs from the static table layout");
             auto b = to_band(build_operator(id, n_r, nc, g), nc, op_h(id));
+            if (b.size() != (size_t)nc * NA_WIDTH[id])
+                return na_fail(PIZZA_EINVAL, "operator band size differs from the static table layout");
             std::memcpy(&host[off], b.data(), b.size() * sizeof(double));
             off += (size_t)NA_MAX_NC * NA_WIDTH[id];
         }
-        cudaError_t e = cudaMemcpy(sl.tables, host.data(), NA_TABLES * sizeof(double), cudaMemcpyHostToDevice);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return na_fail(PIZZA_ECUDA, cudaGetErrorString(e));
+        e = cudaMemcpyAsync(sl.tables, host.data(), NA_TABLES * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return na_fail(PIZZA_ECUDA, "copy of the tables into static device memory failed");
-        sl.have_params = true;
         sl.n_r = n_r;
         sl.n_phi = n_phi;
-        sl.Ra = Ra;
-        sl.Pr = Pr;
         sl.eta = eta;
+        sl.have_params = true;
     }
     out = &sl;
     return PIZZA_OK;
@@ -136,9 +145,10 @@ extern "C" int pizza_explicit_terms_noalloc(int n_r, int n_phi, double Ra, doubl
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return na_fail(PIZZA_ECUDA, "no CUDA device available");
 
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> guard(g_lock);
     DeviceSlot* sl = nullptr;
-    int rc = na_setup(dev, n_r, n_phi, Ra, Pr, radius_ratio, sl);
+    int rc = na_setup(dev, n_r, n_phi, radius_ratio, st, sl);
     if (rc != PIZZA_OK) return rc;
 
     Geom g = make_geom(radius_ratio);
@@ -181,7 +191,6 @@ extern "C" int pizza_explicit_terms_noalloc(int n_r, int n_phi, double Ra, doubl
     VecSet y{const_cast<double2*>(reinterpret_cast<const double2*>(psi_hat)),
              const_cast<double2*>(reinterpret_cast<const double2*>(theta_hat)), const_cast<double*>(uphi0_hat)};
     VecSet e{reinterpret_cast<double2*>(e_psi), reinterpret_cast<double2*>(e_theta), e_uphi};
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t err = launch_spec_to_grid(P, y, G1, st);
     if (err == cudaSuccess) err = launch_phi_products(P, G1, G2, st);
     if (err == cudaSuccess) err = launch_grid_to_spec(P, G2, y, e, st);

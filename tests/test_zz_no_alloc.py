@@ -53,6 +53,39 @@ def test_noalloc_matches_context_path_on_two_calls(n_r, n_phi):
     ref_solver.close()
 
 
+def test_noalloc_calls_ordered_on_one_stream_with_different_sizes():
+    """Two calls queued back to back on one non-blocking stream, with no host
+    synchronisation between them, whose sizes and radius ratios differ: the
+    second call rewrites the shared tables, which must not disturb the first."""
+    import torch
+    from paper_1902_07092_gb300 import binding as B
+    dev = torch.device("cuda", 0)
+    cases = [(257, 768, 0.35, 1e-5, 11), (65, 192, 0.5, 1e-3, 29)]
+    refs, outs, keep = [], [], []
+    for n_r, n_phi, eta, E, seed in cases:
+        Ra = 3.0 * critical_rayleigh(E)
+        psi, th, u = _state(n_r, n_phi, seed)
+        ref = B.Solver(n_r, n_phi, E, Ra, 1.0, eta, "CNAB2", 1e-4)
+        ref.set_state(th, psi, u)
+        refs.append(ref.explicit_terms())
+        ref.close()
+        keep.append((n_r, n_phi, eta, Ra, [torch.from_numpy(x).to(dev) for x in (psi, th, u)]))
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        for n_r, n_phi, eta, Ra, (d_psi, d_th, d_u) in keep:
+            e = [torch.full_like(x, float("nan")) for x in (d_psi, d_th, d_u)]
+            B.pizza_explicit_terms_noalloc(n_r, n_phi, Ra, 1.0, eta, d_psi, d_th, d_u, *e, side.cuda_stream)
+            outs.append(e)
+    side.synchronize()
+    for (n_r, *_), e, r in zip(cases, outs, refs):
+        tol = max(1e-12, 4 * n_r * n_r * 2.0 ** -53)
+        for g, want in zip(e, r):
+            got = g.cpu().numpy()
+            assert np.all(np.isfinite(got))
+            assert rel_l2(got, want) <= tol
+
+
 def test_noalloc_rejects_sizes_beyond_its_static_scratch():
     import torch
     from paper_1902_07092_gb300 import binding as B
