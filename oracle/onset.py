@@ -86,18 +86,21 @@ def leading_mode(E, Pr, Ra, eta, m, n_c, n_r=None, guess=None, pumping_eps=None)
     return lam, x[:n_c], x[n_c:]
 
 
-def critical_rayleigh_m(E, Pr, eta, m, n_c, ra_lo, ra_hi, rtol=1e-9):
-    """Ra at which the leading growth rate of mode m crosses zero."""
-    f = lambda ra: leading_eigenvalue(E, Pr, ra, eta, m, n_c).real
-    ra = brentq(f, ra_lo, ra_hi, rtol=rtol)
-    return ra, leading_eigenvalue(E, Pr, ra, eta, m, n_c)
+def critical_rayleigh_m(E, Pr, eta, m, n_c, ra_lo, ra_hi, rtol=1e-9, eigenvalue=None):
+    """Ra at which the leading growth rate of mode m crosses zero, bracketed by
+    [ra_lo, ra_hi].  ``eigenvalue(m, ra)``, when given, returns the leading
+    eigenvalue of another discretisation of Eq. lin (default: the
+    integration/tau pencil of this module)."""
+    lead = eigenvalue or (lambda mm, ra: leading_eigenvalue(E, Pr, ra, eta, mm, n_c))
+    ra = brentq(lambda r: lead(m, r).real, ra_lo, ra_hi, rtol=rtol)
+    return ra, lead(m, ra)
 
 
-def critical_rayleigh(E, Pr, eta, m_values, n_c, ra_lo, ra_hi):
+def critical_rayleigh(E, Pr, eta, m_values, n_c, ra_lo, ra_hi, eigenvalue=None):
     """Minimum over m of the marginal Ra: returns (Ra_c, m_c, omega_d)."""
     best = None
     for m in m_values:
-        ra, lam = critical_rayleigh_m(E, Pr, eta, m, n_c, ra_lo, ra_hi)
+        ra, lam = critical_rayleigh_m(E, Pr, eta, m, n_c, ra_lo, ra_hi, eigenvalue=eigenvalue)
         if best is None or ra < best[0]:
             best = (ra, m, lam.imag)
     return best
@@ -117,15 +120,26 @@ def leading_eigenvalue_arnoldi(E, Pr, Ra, eta, m, n_c, guess, k=6):
     return lam[np.argmax(lam.real)]
 
 
-def marginal_rayleigh(E, Pr, eta, m, n_c, ra0, guess=None, rtol=1e-10):
+def marginal_rayleigh(E, Pr, eta, m, n_c, ra0, guess=None, rtol=1e-10, eigenvalue=None):
     """Ra at which the leading growth rate of mode m vanishes, by bracketing from
-    ra0 with factor-2 steps and then Brent's method; returns (Ra, lambda)."""
+    ra0 with factor-2 steps and then Brent's method; returns (Ra, lambda).
+
+    ``eigenvalue(ra, g)``, when given, replaces the integration/tau pencil of this
+    module: it returns the eigenvalue of the discretised Eq. lin nearest the
+    branch guess g (g = i omega_d of the previous evaluation, or ``guess`` first;
+    None: the leading one).  This lets the same root finder run on the
+    collocation pencil, with or without Ekman pumping."""
     state = {"g": guess}
     memo = {}
 
     def tau(ra):
         if ra in memo:
             return memo[ra]
+        if eigenvalue is not None:
+            lam = eigenvalue(ra, state["g"])
+            state["g"] = 1j * lam.imag
+            memo[ra] = lam.real
+            return lam.real
         lam = None
         if state["g"] is not None:
             lam = leading_eigenvalue_arnoldi(E, Pr, ra, eta, m, n_c, state["g"])
@@ -153,5 +167,7 @@ def marginal_rayleigh(E, Pr, eta, m, n_c, ra0, guess=None, rtol=1e-10):
                 break
             hi = lo
     ra = brentq(tau, lo, hi, rtol=rtol)
+    if eigenvalue is not None:
+        return ra, eigenvalue(ra, state["g"])
     lam = leading_eigenvalue(E, Pr, ra, eta, m, n_c, guess=state["g"])
     return ra, lam
