@@ -18,16 +18,23 @@ Diagonally implicit (Eq. dirks), stiffly accurate, stage 0 = y_n:
   ARS443 (Ascher, Ruuth & Spiteri 1997, Section 2.8), rows i = 0..4:
     aI: [0], [0,1/2], [0,1/6,1/2], [0,-1/2,1/2,1/2], [0,3/2,-3/2,1/2,1/2]
     aE: [0], [1/2], [11/18,1/18], [5/6,-5/6,1/2], [1/4,7/4,3/4,-7/4]
+  BPR353 (Boscarino, Pareschi & Russo 2013, Section 8.3; Table 1: third order,
+  five implicit and three explicit terms per step), rows i = 0..4:
+    aI: [0], [1/2,1/2], [5/18,-1/9,1/2], [1/2,0,0,1/2], [1/4,0,3/4,-1/2,1/2]
+    aE: [0], [1], [4/9,2/9], [1/4,0,3/4], [1/4,0,3/4,0]
+  Its first implicit column is not zero: the stages use the implicit term of
+  y_n itself.  The tableau is recalled from the cited paper (not printed in this
+  one) and pinned by the order conditions and by Table 1's term counts.
 """
 from fractions import Fraction as Fr
 
 import numpy as np
 
 MULTISTEP = ("CNAB2", "SBDF2", "SBDF3")
-DIRK = ("ARS443",)
+DIRK = ("ARS443", "BPR353")
 
 # enum values of the C interface
-SCHEME_ID = {"CNAB2": 0, "SBDF2": 1, "SBDF3": 2, "ARS443": 3}
+SCHEME_ID = {"CNAB2": 0, "SBDF2": 1, "SBDF3": 2, "ARS443": 3, "BPR353": 4}
 
 
 def multistep_coeffs(name, n_done):
@@ -52,7 +59,7 @@ def implicit_weights(name):
         return [1.0, 2 / 3]
     if name == "SBDF3":
         return [1.0, 2 / 3, 6 / 11]
-    if name == "ARS443":
+    if name in DIRK:
         return [0.5]
     raise ValueError(name)
 
@@ -72,9 +79,25 @@ def ars443_exact():
     return aI, aE
 
 
+def bpr353_exact():
+    h = Fr(1, 2)
+    aI = [[0] * 5 for _ in range(5)]
+    aE = [[0] * 5 for _ in range(5)]
+    aI[1][0], aI[1][1] = h, h
+    aI[2][0], aI[2][1], aI[2][2] = Fr(5, 18), Fr(-1, 9), h
+    aI[3][0], aI[3][3] = h, h
+    aI[4][0], aI[4][2], aI[4][3], aI[4][4] = Fr(1, 4), Fr(3, 4), -h, h
+    aE[1][0] = Fr(1)
+    aE[2][0], aE[2][1] = Fr(4, 9), Fr(2, 9)
+    aE[3][0], aE[3][2] = Fr(1, 4), Fr(3, 4)
+    aE[4][0], aE[4][2] = Fr(1, 4), Fr(3, 4)
+    return aI, aE
+
+
 def dirk_tableau(name):
-    if name != "ARS443":
+    exact = {"ARS443": ars443_exact, "BPR353": bpr353_exact}
+    if name not in exact:
         raise ValueError(name)
-    aI, aE = ars443_exact()
+    aI, aE = exact[name]()
     return (np.array([[float(v) for v in r] for r in aI]),
             np.array([[float(v) for v in r] for r in aE]))

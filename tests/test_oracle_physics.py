@@ -54,8 +54,9 @@ def test_dns_from_eigenmode_grows_at_the_eigenvalue():
 
 
 # -------------------------------------------------------------- schemes ----
-def test_ars443_tableau_is_third_order_and_stiffly_accurate():
-    aI, aE = schemes.ars443_exact()
+@pytest.mark.parametrize("exact", [schemes.ars443_exact, schemes.bpr353_exact])
+def test_dirk_tableau_is_third_order_and_stiffly_accurate(exact):
+    aI, aE = exact()
     nu = 4
     c = [sum(r) for r in aI]
     assert c == [sum(r) for r in aE]                       # same abscissae
@@ -70,6 +71,15 @@ def test_ars443_tableau_is_third_order_and_stiffly_accurate():
     # coupling conditions of the additive pair
     assert sum(bI[i] * aE[i][j] * c[j] for i in range(5) for j in range(5)) == Fr(1, 6)
     assert sum(bE[i] * aI[i][j] * c[j] for i in range(5) for j in range(5)) == Fr(1, 6)
+
+
+def test_bpr353_term_counts_match_table1():
+    """Table 1: BPR353 computes five implicit and three explicit terms per step
+    (columns of the tableaux with a nonzero entry), ARS443 four implicit ones."""
+    cols = lambda A: sum(1 for j in range(5) if any(A[i][j] != 0 for i in range(5)))
+    aI, aE = schemes.bpr353_exact()
+    assert (cols(aI), cols(aE)) == (5, 3)
+    assert cols(schemes.ars443_exact()[0]) == 4
 
 
 def _scalar_run(name, lam_i, lam_e, dt, T, exact_start=False):
@@ -107,7 +117,7 @@ def _scalar_run(name, lam_i, lam_e, dt, T, exact_start=False):
 
 
 @pytest.mark.parametrize("name,order,exact_start", [
-    ("CNAB2", 2, False), ("SBDF2", 2, True), ("SBDF3", 3, True), ("ARS443", 3, False),
+    ("CNAB2", 2, False), ("SBDF2", 2, True), ("SBDF3", 3, True), ("ARS443", 3, False), ("BPR353", 3, False),
     # with the lower-order start-up steps the global error of SBDF2/SBDF3 is that
     # of the first SBDF1 step, O(dt^2) (the paper notes the start-up penalty)
     ("SBDF2", 2, False), ("SBDF3", 2, False)])
@@ -132,7 +142,7 @@ def _bessel_mode(ann, m):
     return k, prof
 
 
-@pytest.mark.parametrize("scheme,order", [("CNAB2", 2), ("ARS443", 3)])
+@pytest.mark.parametrize("scheme,order", [("CNAB2", 2), ("ARS443", 3), ("BPR353", 3)])
 def test_temperature_operator_decays_annulus_eigenmode(scheme, order):
     """With Psi = u_bar = 0 the temperature obeys d theta/dt = Delta theta/Pr; the
     Dirichlet annulus mode J_m(ks)Y_m(ks_i) - J_m(ks_i)Y_m(ks) decays as
