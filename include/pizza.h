@@ -53,8 +53,12 @@ typedef struct pizza_ctx pizza_ctx;
 /* Time schemes (Section 4, Table 1; Eqs. multistep1 and dirks).  The multistep
  * schemes start with lower-order steps: CNAB2 uses bE = (1) on its first step,
  * SBDF3 one SBDF1 and one SBDF2 step, SBDF2 one SBDF1 step.  ARS443 is the
- * third-order stiffly accurate SDIRK of Ascher, Ruuth & Spiteri (1997). */
-enum pizza_scheme { PIZZA_CNAB2 = 0, PIZZA_SBDF2 = 1, PIZZA_SBDF3 = 2, PIZZA_ARS443 = 3 };
+ * third-order stiffly accurate SDIRK of Ascher, Ruuth & Spiteri (1997);
+ * BPR353 the third-order stiffly accurate SDIRK of Boscarino, Pareschi & Russo
+ * (2013), Table 1's preferred third-order scheme: five implicit and three
+ * explicit terms per step (one explicit evaluation fewer than ARS443), its
+ * stages using the implicit term of y_n. */
+enum pizza_scheme { PIZZA_CNAB2 = 0, PIZZA_SBDF2 = 1, PIZZA_SBDF3 = 2, PIZZA_ARS443 = 3, PIZZA_BPR353 = 4 };
 
 enum pizza_status {
     PIZZA_OK = 0,
@@ -63,7 +67,7 @@ enum pizza_status {
     PIZZA_ECUDA = -3,       /* a CUDA runtime call failed (message has details)  */
     PIZZA_ENONFINITE = -4,  /* a NaN/Inf in the state (pizza_diagnostics; with
                                option "check_finite" pizza_synchronize)       */
-    PIZZA_ECFL = -5,        /* reserved: Courant criterion exceeded              */
+    PIZZA_ECFL = -5,        /* Courant criterion of Eq. cfl exceeded (cfl_alpha) */
     PIZZA_ETIMEOUT = -6,    /* reserved: a bounded device wait gave up           */
     PIZZA_ESTATE = -7,      /* call out of order (e.g. step before dt is set)    */
     PIZZA_EUNSUPPORTED = -8 /* valid request the library does not implement      */
@@ -127,6 +131,15 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            or infinite values and sets a device flag; pizza_synchronize then
  *            returns PIZZA_ENONFINITE (cleared by pizza_set_state).  0 (default) =
  *            no scan; pizza_diagnostics reports a non-finite state either way;
+ *   "cfl_alpha" alpha > 0 = the Courant guard of Eq. cfl (Section 4; Table 1
+ *            lists each scheme's largest stable alpha): the azimuthal kernel of
+ *            every explicit evaluation folds max |u_s|/ds_k and
+ *            max |u_phi|/(s_k dphi) over its radii into two running maxima (ds_k
+ *            the local Gauss-Lobatto spacing, dphi = 2 pi/n_phi; the rates of
+ *            pizza_diagnostics), and pizza_synchronize returns PIZZA_ECFL when
+ *            dt > alpha / max(rate) for a state evaluated since the previous
+ *            pizza_synchronize, then clears the maxima.  0 (default) = off;
+ *            negative: PIZZA_EINVAL;
  *   "radial_batch" radial transforms batched per shared-memory pass in the
  *            per-mode explicit kernels: 1, 2 or 4, 0 = the default rule (up to
  *            n_r = 513: 4 in FP64, 2 in mixed precision; else 1); "phi_threads" threads of the per-radius azimuthal
@@ -242,6 +255,17 @@ int pizza_explicit_adjoint(pizza_ctx *ctx, const double *e_psi_bar, const double
  * PIZZA_EUNSUPPORTED for the collocation formulation. */
 int pizza_nusselt_weights(const pizza_ctx *ctx, double *w);
 
+/* Running sum of Nu - 1 on the device: after pizza_nusselt_begin every completed
+ * step adds sum_n w_n Re theta_hat_0n of its new state to a device accumulator
+ * (a one-warp kernel on the context's stream, fixed summation order); then
+ * pizza_nusselt_end synchronises the stream and writes the sum and the number
+ * of steps it covers (steps may be NULL).  The time average of the objective of
+ * the adjoint, J = (1/K) sum_{n=1..K} (Nu_n - 1), without a state copy per step.
+ * PIZZA_EUNSUPPORTED for collocation and slab contexts; pizza_nusselt_end
+ * without begin: PIZZA_ESTATE. */
+int pizza_nusselt_begin(pizza_ctx *ctx);
+int pizza_nusselt_end(pizza_ctx *ctx, double *sum, int *steps);
+
 /* Autotuner: times the explicit stage of the context (on its current state)
  * for each launch shape the device allows -- radial transforms batched one, two
  * or four per shared-memory pass, 128/256/512 threads in the azimuthal kernel -- and
@@ -278,7 +302,9 @@ int pizza_profile_begin(pizza_ctx *ctx, unsigned mask);
 int pizza_profile_end(pizza_ctx *ctx, double *total_ms, int *launches);
 
 /* Block until all queued work of the context is done; returns the first
- * deferred CUDA error, if any. */
+ * deferred CUDA error, if any, then PIZZA_ENONFINITE (option "check_finite")
+ * or PIZZA_ECFL (option "cfl_alpha") when the steps since the last call
+ * tripped those checks. */
 int pizza_synchronize(pizza_ctx *ctx);
 
 /* Host-side operator construction, exposed for verification without a GPU.
@@ -341,6 +367,46 @@ int pizza_explicit_terms_noalloc(int n_r, int n_phi, double Ra, double Pr, doubl
                                  const double *psi_hat, const double *theta_hat,
                                  const double *uphi0_hat, double *e_psi, double *e_theta,
                                  double *e_uphi, void *stream);
+
+/* m-slab decomposition of one step over ranks (Section 5: the 1-D decomposition
+ * of the paper, radius-local for the azimuthal transforms, m-local for the
+ * radial work, joined by two all-to-all transposes per explicit evaluation).
+ *
+ * After this call the context advances only the modes m_lo <= m < m_hi of its
+ * state (every per-mode kernel: synthesis a1, analysis a3, right-hand side and
+ * solve; the zonal flow on the rank whose slab holds m = 0) and runs the
+ * azimuthal products a2 only for the radii k_lo <= k < k_hi.  The grid arrays
+ * live in the caller's buffers grid1 and grid2 (DEVICE memory, 16-byte aligned,
+ * at least n_r * 4 * (N_m + 1) * 16 bytes each, radius-major [k][field][m]); the
+ * library calls
+ *     exchange(user, 1, grid1, elem_bytes, stream)   after a1,
+ *     exchange(user, 2, grid2, elem_bytes, stream)   after a2,
+ * from the thread that called pizza_step, with work already queued on `stream`
+ * (the context's cudaStream_t).  Call 1 must leave in grid1, for this rank's
+ * radii, the synthesis values of every mode (the other ranks' columns
+ * [k][f][m] with m in their slabs); call 2 must leave in grid2, for this rank's
+ * modes, the product values of every radius.  elem_bytes is 16 (complex FP64)
+ * or 8 (complex FP32, option "precision" = 1).  A nonzero return fails the
+ * step with PIZZA_ECUDA.  The state arrays keep their full size; get_state
+ * returns meaningful values only for the slab's modes.
+ *
+ * The full ranges (0, N_m+1, 0, n_r) with exchange = NULL return the context
+ * to the whole step.  Integration formulation only (tau rows or Galerkin
+ * bases); diagnostics, the physical grid, the adjoint, the autotuner and
+ * batches return PIZZA_EUNSUPPORTED on a slab context.  PIZZA_EINVAL for bad
+ * ranges, missing buffers or callback. */
+typedef int (*pizza_exchange_fn)(void *user, int which, void *grid, int elem_bytes, void *stream);
+int pizza_set_slab(pizza_ctx *ctx, int m_lo, int m_hi, int k_lo, int k_hi, void *grid1, void *grid2,
+                   pizza_exchange_fn exchange, void *user);
+
+/* Measured FP64 fused multiply-add rate of the current device, in TFLOP/s
+ * (2 flops per FMA): one launch of `iters` rounds of 8 independent FMA chains in
+ * each of 8 x 256 threads per SM, timed with CUDA events after a short warm-up
+ * launch.  A measurement helper with no counterpart in the paper: the FP64
+ * kernels of the step are bound by FP64 issue on this GPU, and this is their
+ * roofline denominator.  *ms (may be NULL) receives the timed launch's duration.
+ * Allocates a small output array; PIZZA_EINVAL for iters < 1 or NULL tflops. */
+int pizza_fp64_fma_rate(int iters, double *tflops, double *ms);
 
 void pizza_free(pizza_ctx *ctx);
 

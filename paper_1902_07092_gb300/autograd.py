@@ -1,6 +1,7 @@
 """torch.autograd.Function for the time-averaged Nusselt number of a CNAB2 run,
 J = (1/K) sum_{n=1..K} (Nu_n - 1), as a function of the initial temperature
-coefficients and of Ra; the backward pass is the library's discrete adjoint
+coefficients and of Ra, J summed on the device by the library (one read at the
+end); the backward pass is the library's discrete adjoint
 (pizza_tape_begin / pizza_adjoint_step), with checkpoints every
 ``checkpoint_every`` steps.  Argument marshalling only: the forward steps and the
 adjoint run in the CUDA library.
@@ -30,12 +31,13 @@ class NusseltAverage(torch.autograd.Function):
         s.tape_begin(int(cfg.get("checkpoint_every", 20)))
         w = s.nusselt_weights()
         K = int(cfg["steps"])
-        J = 0.0
-        for _ in range(K):
-            s.step(1)
-            J += float(np.dot(w, s.get_state()[1][0].real)) / K
+        s.nusselt_begin()          # Nu_n - 1 summed on the device after every step
+        s.step(K)
+        total, n = s.nusselt_end()
+        if n != K:
+            raise RuntimeError("the Nusselt sum covers %d of %d steps" % (n, K))
         ctx.solver, ctx.K, ctx.w = s, K, w
-        return torch.tensor(J, dtype=torch.float64)
+        return torch.tensor(total / K, dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, grad_J):

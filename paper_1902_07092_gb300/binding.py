@@ -12,8 +12,8 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libpizza.so")
 
-PIZZA_CNAB2, PIZZA_SBDF2, PIZZA_SBDF3, PIZZA_ARS443 = 0, 1, 2, 3
-SCHEMES = {"CNAB2": 0, "SBDF2": 1, "SBDF3": 2, "ARS443": 3}
+PIZZA_CNAB2, PIZZA_SBDF2, PIZZA_SBDF3, PIZZA_ARS443, PIZZA_BPR353 = 0, 1, 2, 3, 4
+SCHEMES = {"CNAB2": 0, "SBDF2": 1, "SBDF3": 2, "ARS443": 3, "BPR353": 4}
 
 STATUS = {0: "PIZZA_OK", -1: "PIZZA_EINVAL", -2: "PIZZA_ENOMEM", -3: "PIZZA_ECUDA", -4: "PIZZA_ENONFINITE",
           -5: "PIZZA_ECFL", -6: "PIZZA_ETIMEOUT", -7: "PIZZA_ESTATE", -8: "PIZZA_EUNSUPPORTED"}
@@ -25,7 +25,8 @@ EXPORTS = ("pizza_init", "pizza_set_option", "pizza_set_stream", "pizza_get_size
            "pizza_host_operator", "pizza_host_collocation", "pizza_explicit_terms_noalloc", "pizza_free",
            "pizza_last_error", "pizza_tape_begin", "pizza_adjoint_step", "pizza_get_adjoint",
            "pizza_explicit_adjoint", "pizza_nusselt_weights", "pizza_autotune", "pizza_batch_create",
-           "pizza_batch_step", "pizza_batch_stream", "pizza_batch_free")
+           "pizza_batch_step", "pizza_batch_stream", "pizza_batch_free", "pizza_fp64_fma_rate",
+           "pizza_set_slab", "pizza_nusselt_begin", "pizza_nusselt_end")
 
 _lib = None
 
@@ -76,6 +77,10 @@ def load():
     lib.pizza_batch_free.argtypes = [vp]
     lib.pizza_batch_free.restype = None
     lib.pizza_explicit_terms_noalloc.argtypes = [i, i, d, d, d, dp, dp, dp, dp, dp, dp, vp]
+    lib.pizza_fp64_fma_rate.argtypes = [i, ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.pizza_set_slab.argtypes = [vp, i, i, i, i, vp, vp, vp, vp]
+    lib.pizza_nusselt_begin.argtypes = [vp]
+    lib.pizza_nusselt_end.argtypes = [vp, ctypes.POINTER(d), ip]
     lib.pizza_free.argtypes = [vp]
     lib.pizza_free.restype = None
     lib.pizza_last_error.argtypes = [vp]
@@ -261,6 +266,20 @@ def pizza_explicit_terms_noalloc(n_r, n_phi, Ra, Pr, radius_ratio, psi_hat, thet
                                                       _ptr(e_theta), _ptr(e_uphi), stream))
 
 
+def pizza_set_slab(ctx, m_lo, m_hi, k_lo, k_hi, grid1, grid2, exchange, user=None):
+    """exchange: a ctypes callback of slabs.EXCHANGE_FN (or None with the full
+    ranges, which returns the context to the whole step)."""
+    fn = ctypes.cast(exchange, ctypes.c_void_p) if exchange is not None else None
+    return _check(load().pizza_set_slab(ctx, m_lo, m_hi, k_lo, k_hi, _ptr(grid1), _ptr(grid2), fn, user), ctx)
+
+
+def pizza_fp64_fma_rate(iters=20000):
+    """Measured FP64 FMA rate of the current device: (TFLOP/s, ms of the launch)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().pizza_fp64_fma_rate(iters, ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
+
+
 def pizza_free(ctx):
     load().pizza_free(ctx)
 
@@ -320,6 +339,15 @@ class Solver:
 
     def diagnostics(self):
         return pizza_diagnostics(self.ctx)
+
+    def nusselt_begin(self):
+        _check(load().pizza_nusselt_begin(self.ctx), self.ctx)
+
+    def nusselt_end(self):
+        """(sum of Nu_n - 1 over the steps since nusselt_begin, number of steps)"""
+        v, n = ctypes.c_double(), ctypes.c_int()
+        _check(load().pizza_nusselt_end(self.ctx, ctypes.byref(v), ctypes.byref(n)), self.ctx)
+        return v.value, n.value
 
     def tape_begin(self, checkpoint_every=20):
         pizza_tape_begin(self.ctx, checkpoint_every)

@@ -15,7 +15,7 @@ LIB = os.path.join(PKG, "libpizza.so")
 
 SOURCES = ["host_ops.cpp", "coll_ops.cpp", "k_explicit.cu", "k_implicit.cu", "k_collocation.cu", "k_adjoint.cu",
            "api.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "--expt-relaxed-constexpr"]

@@ -4,6 +4,7 @@
 // Section 4 of Gastine, pizza, GJI 2019.
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -124,6 +125,14 @@ struct pizza_ctx {
     // option "check_finite": scan the state for NaN/Inf after every step
     int check_finite = 0;
     int* finite_flag = nullptr;  // device flag set by the scan, read by pizza_synchronize
+    // running sum of Nu - 1 over completed steps (pizza_nusselt_begin/end)
+    bool nu_on = false;
+    int nu_steps = 0;
+    double* nu_buf = nullptr;  // [0] the sum, [1 ..] the weights w_n
+    // option "cfl_alpha" (Eq. cfl): > 0 checks dt <= alpha / max(cfl_s, cfl_phi)
+    // of every state whose explicit terms were evaluated since the last check
+    double cfl_alpha = 0.0;
+    double* cfl_buf = nullptr;   // [2] running maxima, then [n_r] local spacing
     double* pump_tab = nullptr;        // 3 x n_r device tables (StepParams pump_*)
     double2* pump_buf = nullptr;       // [M][n_r] working buffer of the integration path
     // discrete adjoint (pizza_tape_begin / pizza_adjoint_step)
@@ -149,6 +158,16 @@ struct pizza_ctx {
         std::vector<void*> allocs;     // buffers and inverses
         std::vector<void*> ck_allocs;  // checkpoints of the current tape
     } adj;
+    // m-slab decomposition (pizza_set_slab): this context advances modes
+    // [P.m_lo, P.m_lo + P.m_n) and transforms radii [P.k_lo, P.k_lo + P.k_n) in
+    // the caller's grid buffers, the exchange callback moving the grid between
+    // the two layouts after a1 and after a2
+    struct Slab {
+        bool on = false;
+        void *g1 = nullptr, *g2 = nullptr;
+        pizza_exchange_fn fn = nullptr;
+        void* user = nullptr;
+    } slab;
 };
 
 namespace {
@@ -201,6 +220,7 @@ std::vector<double> scheme_gammas(int scheme) {
         case PIZZA_SBDF2: return {1.0, 2.0 / 3.0};
         case PIZZA_SBDF3: return {1.0, 2.0 / 3.0, 6.0 / 11.0};
         case PIZZA_ARS443: return {0.5};
+        case PIZZA_BPR353: return {0.5};
     }
     return {};
 }
@@ -635,7 +655,7 @@ void reset_slots(pizza_ctx* ctx) {
         for (int i = 0; i < 3; ++i) ctx->is[i] = 8 + i;
         for (int i = 0; i < 4; ++i) ctx->stage_e[i] = 4 + i;
         ctx->stage_y[1] = 11; ctx->stage_y[2] = 12; ctx->stage_y[3] = 13;
-        ctx->stage_imp[1] = 8; ctx->stage_imp[2] = 9; ctx->stage_imp[3] = 10;
+        ctx->stage_imp[0] = 14; ctx->stage_imp[1] = 8; ctx->stage_imp[2] = 9; ctx->stage_imp[3] = 10;
         ctx->mass_n = 0;
         ctx->n_done = 0;
         ctx->aux_valid = false;
@@ -646,10 +666,11 @@ void reset_slots(pizza_ctx* ctx) {
     for (int i = 0; i < 4; ++i) ctx->es[i] = 2 + i;
     for (int i = 0; i < 3; ++i) ctx->ms[i] = 6 + i;
     for (int i = 0; i < 3; ++i) ctx->is[i] = 9 + i;
-    // DIRK: stage states 12..14 (y_1..y_3), explicit 2..5 (e_0..e_3), imp 9..11 (I_1..I_3), mass 6
+    // DIRK: stage states 12..14 (y_1..y_3), explicit 2..5 (e_0..e_3), imp 7 (I_0 = Imp y_n,
+    // BPR353 only) and 9..11 (I_1..I_3), mass 6
     ctx->stage_y[1] = 12; ctx->stage_y[2] = 13; ctx->stage_y[3] = 14;
     for (int i = 0; i < 4; ++i) ctx->stage_e[i] = 2 + i;
-    ctx->stage_imp[1] = 9; ctx->stage_imp[2] = 10; ctx->stage_imp[3] = 11;
+    ctx->stage_imp[0] = 7; ctx->stage_imp[1] = 9; ctx->stage_imp[2] = 10; ctx->stage_imp[3] = 11;
     ctx->mass_n = 6;
     ctx->n_done = 0;
     ctx->aux_valid = false;
@@ -685,13 +706,28 @@ int explicit_eval(pizza_ctx* ctx, VecSet y, VecSet e) {
         CK(timed_launch(ctx, 2, [&] { return launch_coll_grid_rows(ctx->P, ctx->G1, ctx->G2, e, ctx->stream); }));
         return PIZZA_OK;
     }
+    if (ctx->slab.on) {
+        // a1 on this rank's modes, transpose to radius slabs, a2 on this rank's
+        // radii, transpose back, a3 on this rank's modes (Section 5)
+        double2* g1 = static_cast<double2*>(ctx->slab.g1);
+        double2* g2 = static_cast<double2*>(ctx->slab.g2);
+        const int eb = ctx->P.fp32 ? 8 : 16;
+        CK(timed_launch(ctx, 0, [&] { return launch_spec_to_grid(ctx->P, y, g1, ctx->stream); }));
+        if (int rc = ctx->slab.fn(ctx->slab.user, 1, g1, eb, ctx->stream))
+            return fail(ctx, PIZZA_ECUDA, "slab exchange after the synthesis failed (%d)", rc);
+        CK(timed_launch(ctx, 1, [&] { return launch_phi_products(ctx->P, g1, g2, ctx->stream); }));
+        if (int rc = ctx->slab.fn(ctx->slab.user, 2, g2, eb, ctx->stream))
+            return fail(ctx, PIZZA_ECUDA, "slab exchange after the azimuthal products failed (%d)", rc);
+        CK(timed_launch(ctx, 2, [&] { return launch_grid_to_spec(ctx->P, g2, y, e, ctx->stream); }));
+        return PIZZA_OK;
+    }
     CK(timed_launch(ctx, 0, [&] { return launch_spec_to_grid(ctx->P, y, ctx->G1, ctx->stream); }));
     CK(timed_launch(ctx, 1, [&] { return launch_phi_products(ctx->P, ctx->G1, ctx->G2, ctx->stream); }));
     CK(timed_launch(ctx, 2, [&] { return launch_grid_to_spec(ctx->P, ctx->G2, y, e, ctx->stream); }));
     return PIZZA_OK;
 }
 
-bool is_multistep(int scheme) { return scheme != PIZZA_ARS443; }
+bool is_multistep(int scheme) { return scheme <= PIZZA_SBDF3; }
 
 // (a, b0, bI, bE) of Eq. multistep1 with the start-up rule
 void multistep_coeffs(int scheme, int n_done, std::vector<double>& a, double& b0, std::vector<double>& bI,
@@ -715,23 +751,58 @@ void multistep_coeffs(int scheme, int n_done, std::vector<double>& a, double& b0
     }
 }
 
-// ARS443 tableau (Ascher, Ruuth & Spiteri 1997, Section 2.8), stage 0 = y_n
-const double ARS_AI[5][5] = {{0, 0, 0, 0, 0},
-                             {0, 0.5, 0, 0, 0},
-                             {0, 1.0 / 6.0, 0.5, 0, 0},
-                             {0, -0.5, 0.5, 0.5, 0},
-                             {0, 1.5, -1.5, 0.5, 0.5}};
-const double ARS_AE[5][5] = {{0, 0, 0, 0, 0},
-                             {0.5, 0, 0, 0, 0},
-                             {11.0 / 18.0, 1.0 / 18.0, 0, 0, 0},
-                             {5.0 / 6.0, -5.0 / 6.0, 0.5, 0, 0},
-                             {0.25, 1.75, 0.75, -1.75, 0}};
+// Stiffly accurate SDIRK tableaux of Eq. dirks, stage 0 = y_n, y_{n+1} = stage 4.
+struct Tableau {
+    double aI[5][5], aE[5][5];
+};
+// ARS443 (Ascher, Ruuth & Spiteri 1997, Section 2.8)
+const Tableau ARS443 = {{{0, 0, 0, 0, 0},
+                         {0, 0.5, 0, 0, 0},
+                         {0, 1.0 / 6.0, 0.5, 0, 0},
+                         {0, -0.5, 0.5, 0.5, 0},
+                         {0, 1.5, -1.5, 0.5, 0.5}},
+                        {{0, 0, 0, 0, 0},
+                         {0.5, 0, 0, 0, 0},
+                         {11.0 / 18.0, 1.0 / 18.0, 0, 0, 0},
+                         {5.0 / 6.0, -5.0 / 6.0, 0.5, 0, 0},
+                         {0.25, 1.75, 0.75, -1.75, 0}}};
+// BPR353 (Boscarino, Pareschi & Russo 2013, Section 8.3): its first implicit
+// column is not zero (the stages use Imp y_n), and its last explicit column is,
+// so E(y_3) is never needed: three explicit evaluations per step (Table 1)
+const Tableau BPR353 = {{{0, 0, 0, 0, 0},
+                         {0.5, 0.5, 0, 0, 0},
+                         {5.0 / 18.0, -1.0 / 9.0, 0.5, 0, 0},
+                         {0.5, 0, 0, 0.5, 0},
+                         {0.25, 0, 0.75, -0.5, 0.5}},
+                        {{0, 0, 0, 0, 0},
+                         {1.0, 0, 0, 0, 0},
+                         {4.0 / 9.0, 2.0 / 9.0, 0, 0, 0},
+                         {0.25, 0, 0.75, 0, 0},
+                         {0.25, 0, 0.75, 0, 0}}};
+
+const Tableau& tableau_of(int scheme) { return scheme == PIZZA_BPR353 ? BPR353 : ARS443; }
+
+bool column_used(const double (&a)[5][5], int j) {
+    for (int i = j + 1; i < 5; ++i)
+        if (a[i][j] != 0.0) return true;
+    return false;
+}
+
+// The stage j in 1..3 whose implicit term the last stage does not read: the last
+// solve writes Imp y_{n+1} there, and the slot then becomes I_0 of the next step.
+int spare_imp_stage(const Tableau& T) {
+    for (int j = 1; j < 4; ++j)
+        if (T.aI[4][j] == 0.0) return j;
+    return -1;
+}
 
 int ensure_aux(pizza_ctx* ctx) {
     if (ctx->aux_valid) return PIZZA_OK;
     VecSet y = ctx->vec[ctx->ys[0]];
+    const bool imp0 = !is_multistep(ctx->scheme) && column_used(tableau_of(ctx->scheme).aI, 0);
     if (ctx->coll) {
         if (ctx->scheme == PIZZA_CNAB2) CK(launch_coll_apply(ctx->P, y, ctx->vec[ctx->is[0]], ctx->stream));
+        if (imp0) CK(launch_coll_apply(ctx->P, y, ctx->vec[ctx->stage_imp[0]], ctx->stream));
         ctx->aux_valid = true;
         return PIZZA_OK;
     }
@@ -739,7 +810,8 @@ int ensure_aux(pizza_ctx* ctx) {
         CK(launch_apply(ctx->P, y, ctx->vec[ctx->ms[0]], ctx->vec[ctx->is[0]], true,
                         ctx->scheme == PIZZA_CNAB2, ctx->stream));
     } else {
-        CK(launch_apply(ctx->P, y, ctx->vec[ctx->mass_n], ctx->vec[ctx->mass_n], true, false, ctx->stream));
+        CK(launch_apply(ctx->P, y, ctx->vec[ctx->mass_n], imp0 ? ctx->vec[ctx->stage_imp[0]] : ctx->vec[ctx->mass_n],
+                        true, imp0, ctx->stream));
     }
     ctx->aux_valid = true;
     return PIZZA_OK;
@@ -776,20 +848,32 @@ int step_multistep(pizza_ctx* ctx) {
     return PIZZA_OK;
 }
 
-int step_dirk(pizza_ctx* ctx) {
+// Right-hand side of stage i (Eq. dirks): mass term of y_n plus dt times the
+// explicit and implicit terms of the earlier stages that the tableau weights.
+RhsSpec dirk_rhs(pizza_ctx* ctx, const Tableau& T, int i, VecSet mass) {
     const double dt = ctx->dt;
+    RhsSpec R{};
+    R.t[R.nterms++] = {mass, 1.0};
+    for (int j = 0; j < i; ++j) {
+        if (T.aE[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_e[j]], dt * T.aE[i][j]};
+        if (T.aI[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_imp[j]], dt * T.aI[i][j]};
+    }
+    return R;
+}
+
+int step_dirk(pizza_ctx* ctx) {
+    const Tableau& T = tableau_of(ctx->scheme);
     const int nu = 4;
+    const bool imp0 = column_used(T.aI, 0);
+    const int spare = imp0 ? spare_imp_stage(T) : -1;
     for (int i = 1; i <= nu; ++i) {
         VecSet y_prev = (i == 1) ? ctx->vec[ctx->ys[0]] : ctx->vec[ctx->stage_y[i - 1]];
-        int rc = explicit_eval(ctx, y_prev, ctx->vec[ctx->stage_e[i - 1]]);
-        if (rc) return rc;
-        RhsSpec R{};
-        R.t[R.nterms++] = {ctx->vec[ctx->mass_n], 1.0};
-        for (int j = 0; j < i; ++j) {
-            if (ARS_AE[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_e[j]], dt * ARS_AE[i][j]};
-            if (j >= 1 && ARS_AI[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_imp[j]], dt * ARS_AI[i][j]};
+        if (column_used(T.aE, i - 1)) {
+            int rc = explicit_eval(ctx, y_prev, ctx->vec[ctx->stage_e[i - 1]]);
+            if (rc) return rc;
         }
-        const DevFactors* F = factors_for(ctx, ARS_AI[i][i]);
+        RhsSpec R = dirk_rhs(ctx, T, i, ctx->vec[ctx->mass_n]);
+        const DevFactors* F = factors_for(ctx, T.aI[i][i]);
         if (!F) return fail(ctx, PIZZA_EINVAL, "no factors for a_ii");
         if (i < nu) {
             CK(timed_launch(ctx, 3, [&] {
@@ -797,13 +881,16 @@ int step_dirk(pizza_ctx* ctx) {
                                     ctx->vec[ctx->stage_imp[i]], false, true, ctx->stream);
             }));
         } else {
-            // y_{n+1} = y_nu (stiffly accurate); its mass term replaces Mass(y_n)
+            // y_{n+1} = y_nu (stiffly accurate); its mass term replaces Mass(y_n), and
+            // where the stages use Imp y_n, Imp y_{n+1} goes to the spare stage slot
+            VecSet imp_out = imp0 ? ctx->vec[ctx->stage_imp[spare]] : ctx->vec[ctx->mass_n];
             CK(timed_launch(ctx, 3, [&] {
-                return launch_solve(ctx->P, R, *F, ctx->vec[ctx->ys[1]], ctx->vec[ctx->mass_n],
-                                    ctx->vec[ctx->mass_n], true, false, ctx->stream);
+                return launch_solve(ctx->P, R, *F, ctx->vec[ctx->ys[1]], ctx->vec[ctx->mass_n], imp_out, true, imp0,
+                                    ctx->stream);
             }));
         }
     }
+    if (imp0) std::swap(ctx->stage_imp[0], ctx->stage_imp[spare]);
     std::swap(ctx->ys[0], ctx->ys[1]);
     return PIZZA_OK;
 }
@@ -841,27 +928,29 @@ int step_multistep_coll(pizza_ctx* ctx) {
 }
 
 int step_dirk_coll(pizza_ctx* ctx) {
-    const double dt = ctx->dt;
+    const Tableau& T = tableau_of(ctx->scheme);
     const int nu = 4;
+    const bool imp0 = column_used(T.aI, 0);
+    const int spare = imp0 ? spare_imp_stage(T) : -1;
     for (int i = 1; i <= nu; ++i) {
         VecSet y_prev = (i == 1) ? ctx->vec[ctx->ys[0]] : ctx->vec[ctx->stage_y[i - 1]];
-        int rc = explicit_eval(ctx, y_prev, ctx->vec[ctx->stage_e[i - 1]]);
-        if (rc) return rc;
-        RhsSpec R{};
-        R.t[R.nterms++] = {ctx->vec[ctx->ys[0]], 1.0};
-        for (int j = 0; j < i; ++j) {
-            if (ARS_AE[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_e[j]], dt * ARS_AE[i][j]};
-            if (j >= 1 && ARS_AI[i][j] != 0.0) R.t[R.nterms++] = {ctx->vec[ctx->stage_imp[j]], dt * ARS_AI[i][j]};
+        if (column_used(T.aE, i - 1)) {
+            int rc = explicit_eval(ctx, y_prev, ctx->vec[ctx->stage_e[i - 1]]);
+            if (rc) return rc;
         }
-        const DevFactors* F = factors_for(ctx, ARS_AI[i][i]);
+        RhsSpec R = dirk_rhs(ctx, T, i, ctx->vec[ctx->ys[0]]);
+        const DevFactors* F = factors_for(ctx, T.aI[i][i]);
         if (!F) return fail(ctx, PIZZA_EINVAL, "no factors for a_ii");
         const bool last = (i == nu);
         VecSet out = last ? ctx->vec[ctx->ys[1]] : ctx->vec[ctx->stage_y[i]];
-        VecSet imp = last ? out : ctx->vec[ctx->stage_imp[i]];
+        // the spare slot is not an input of the last stage
+        VecSet imp = last ? (imp0 ? ctx->vec[ctx->stage_imp[spare]] : out) : ctx->vec[ctx->stage_imp[i]];
+        const bool want_imp = !last || imp0;
         CK(timed_launch(ctx, 3, [&] {
-            return launch_coll_solve(ctx->P, R, *F, out, out, imp, false, !last, ctx->stream);
+            return launch_coll_solve(ctx->P, R, *F, out, out, imp, false, want_imp, ctx->stream);
         }));
     }
+    if (imp0) std::swap(ctx->stage_imp[0], ctx->stage_imp[spare]);
     std::swap(ctx->ys[0], ctx->ys[1]);
     return PIZZA_OK;
 }
@@ -1266,7 +1355,7 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         return fail(nullptr, PIZZA_EINVAL, "n_phi must be 3*2^j with 12 <= n_phi <= 6144 (got %d)", n_phi);
     if (!(radius_ratio > 0.0 && radius_ratio < 1.0)) return fail(nullptr, PIZZA_EINVAL, "radius_ratio not in (0,1)");
     if (!(E > 0.0) || !(Pr > 0.0) || !std::isfinite(Ra)) return fail(nullptr, PIZZA_EINVAL, "E, Pr must be > 0");
-    if (scheme < PIZZA_CNAB2 || scheme > PIZZA_ARS443) return fail(nullptr, PIZZA_EINVAL, "unknown scheme %d", scheme);
+    if (scheme < PIZZA_CNAB2 || scheme > PIZZA_BPR353) return fail(nullptr, PIZZA_EINVAL, "unknown scheme %d", scheme);
 
     pizza_ctx* ctx = new pizza_ctx();
     ctx->n_r = n_r;
@@ -1544,6 +1633,7 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
                         "radial must be 0 (collocation), 1 (integration, tau) or 2 (integration, Galerkin)");
         const bool coll = (value == 0.0), gal = (value == 2.0);
         if (coll == ctx->coll && gal == ctx->gal) return PIZZA_OK;
+        if (coll && ctx->slab.on) return fail(ctx, PIZZA_EUNSUPPORTED, "slab contexts use the integration formulation");
         if (coll == ctx->coll) {  // tau <-> Galerkin: same unknowns, new factors
             cudaStreamSynchronize(ctx->stream);
             free_factors(ctx);
@@ -1575,6 +1665,24 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
         if (value != 0.0 && value != 1.0) return fail(ctx, PIZZA_EINVAL, "azimuthal_dd must be 0 or 1");
         cudaStreamSynchronize(ctx->stream);
         ctx->P.phi_dd = (value == 1.0) ? 1 : 0;
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "cfl_alpha") == 0) {
+        if (!(value >= 0.0) || !std::isfinite(value)) return fail(ctx, PIZZA_EINVAL, "cfl_alpha must be >= 0");
+        cudaStreamSynchronize(ctx->stream);
+        if (value > 0.0 && !ctx->cfl_buf) {
+            ctx->cfl_buf = dalloc<double>(ctx, 2 + ctx->n_r, ctx->allocs);
+            if (!ctx->cfl_buf) return fail(ctx, PIZZA_ENOMEM, "device allocation failed");
+            // local spacing of the Gauss-Lobatto grid (half the distance between
+            // the two neighbours, one-sided at the walls), as the diagnostics use it
+            CK(cudaMemcpy(ctx->cfl_buf + 2, ctx->ds_host.data(), ctx->n_r * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        ctx->cfl_alpha = value;
+        ctx->P.cfl_max = (value > 0.0) ? ctx->cfl_buf : nullptr;
+        ctx->P.cfl_ds = ctx->cfl_buf ? ctx->cfl_buf + 2 : nullptr;
+        ctx->P.cfl_dphi = 2.0 * 3.141592653589793238462643383279502884 / ctx->n_phi;
+        if (ctx->cfl_buf) CK(cudaMemset(ctx->cfl_buf, 0, 2 * sizeof(double)));
+        ++ctx->epoch;
         return PIZZA_OK;
     }
     if (std::strcmp(key, "check_finite") == 0) {
@@ -1628,6 +1736,39 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
 }  // namespace
 
 extern "C" {
+
+int pizza_set_slab(pizza_ctx* ctx, int m_lo, int m_hi, int k_lo, int k_hi, void* grid1, void* grid2,
+                   pizza_exchange_fn exchange, void* user) {
+    if (!ctx) return PIZZA_EINVAL;
+    const bool full = (m_lo == 0 && m_hi == ctx->M && k_lo == 0 && k_hi == ctx->n_r);
+    if (full && !exchange) {  // back to the whole step on this context
+        cudaStreamSynchronize(ctx->stream);
+        ctx->slab = pizza_ctx::Slab{};
+        ctx->P.m_lo = ctx->P.m_n = ctx->P.k_lo = ctx->P.k_n = 0;
+        ++ctx->epoch;
+        return PIZZA_OK;
+    }
+    if (!(0 <= m_lo && m_lo < m_hi && m_hi <= ctx->M && 0 <= k_lo && k_lo < k_hi && k_hi <= ctx->n_r))
+        return fail(ctx, PIZZA_EINVAL, "slab ranges must satisfy 0 <= m_lo < m_hi <= N_m+1, 0 <= k_lo < k_hi <= n_r");
+    if (!grid1 || !grid2 || !exchange)
+        return fail(ctx, PIZZA_EINVAL, "a slab needs two grid buffers and an exchange callback");
+    if ((reinterpret_cast<uintptr_t>(grid1) | reinterpret_cast<uintptr_t>(grid2)) & 15)
+        return fail(ctx, PIZZA_EINVAL, "grid buffers must be 16-byte aligned");
+    if (ctx->coll) return fail(ctx, PIZZA_EUNSUPPORTED, "slab contexts use the integration formulation");
+    if (ctx->adj.taping) return fail(ctx, PIZZA_ESTATE, "a tape is being recorded");
+    cudaStreamSynchronize(ctx->stream);
+    ctx->slab.on = true;
+    ctx->slab.g1 = grid1;
+    ctx->slab.g2 = grid2;
+    ctx->slab.fn = exchange;
+    ctx->slab.user = user;
+    ctx->P.m_lo = m_lo;
+    ctx->P.m_n = m_hi - m_lo;
+    ctx->P.k_lo = k_lo;
+    ctx->P.k_n = k_hi - k_lo;
+    ++ctx->epoch;
+    return PIZZA_OK;
+}
 
 int pizza_set_stream(pizza_ctx* ctx, void* stream) {
     if (!ctx) return PIZZA_EINVAL;
@@ -1701,6 +1842,10 @@ int pizza_step(pizza_ctx* ctx, int nsteps) {
         if (rc) return rc;
         ctx->n_done++;
         if (ctx->check_finite) CK(launch_check_finite(ctx->P, ctx->vec[ctx->ys[0]], ctx->finite_flag, ctx->stream));
+        if (ctx->nu_on) {
+            CK(launch_nusselt_accumulate(ctx->P, ctx->vec[ctx->ys[0]], ctx->nu_buf + 1, ctx->nu_buf, ctx->stream));
+            ctx->nu_steps++;
+        }
         if (ctx->adj.taping) {
             rc = tape_record(ctx);
             if (rc) return rc;
@@ -1753,6 +1898,7 @@ int pizza_profile_end(pizza_ctx* ctx, double* total_ms, int* launches) {
 
 int pizza_diagnostics(pizza_ctx* ctx, pizza_diag* out) {
     if (!ctx || !out) return fail(ctx, PIZZA_EINVAL, "NULL argument");
+    if (ctx->slab.on) return fail(ctx, PIZZA_EUNSUPPORTED, "diagnostics need every mode: not on a slab context");
     const int n_r = ctx->n_r, M = ctx->M, nc = ctx->nc;
     if (!ctx->diag_q) {
         // Clenshaw-Curtis weights on x_k = cos(pi k/K):
@@ -1833,6 +1979,7 @@ int pizza_diagnostics(pizza_ctx* ctx, pizza_diag* out) {
 
 int pizza_get_grid(pizza_ctx* ctx, double* us, double* uphi, double* omega, double* theta) {
     if (!ctx) return PIZZA_EINVAL;
+    if (ctx->slab.on) return fail(ctx, PIZZA_EUNSUPPORTED, "the physical grid needs every mode: not on a slab context");
     const size_t n = (size_t)ctx->n_r * ctx->n_phi;
     if (!ctx->grid_out) {
         ctx->grid_out = dalloc<double>(ctx, 4 * n, ctx->allocs);
@@ -1858,6 +2005,7 @@ int pizza_tape_begin(pizza_ctx* ctx, int checkpoint_every) {
     if (!ctx) return PIZZA_EINVAL;
     if (checkpoint_every < 1) return fail(ctx, PIZZA_EINVAL, "checkpoint_every must be >= 1");
     if (ctx->n_done != 0) return fail(ctx, PIZZA_ESTATE, "the tape starts right after pizza_set_state");
+    if (ctx->slab.on) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is not written for slab contexts");
     if (ctx->P.pump) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written without Ekman pumping");
     if (ctx->P.buoy_imp) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written for explicit buoyancy");
     int rc = ensure_factors(ctx);
@@ -1951,6 +2099,7 @@ int pizza_get_adjoint(pizza_ctx* ctx, double* theta_bar, double* psi_bar, double
 int pizza_explicit_adjoint(pizza_ctx* ctx, const double* e_psi_bar, const double* e_theta_bar, const double* e_u_bar,
                            double* psi_bar, double* theta_bar, double* uphi0_bar) {
     if (!ctx) return PIZZA_EINVAL;
+    if (ctx->slab.on) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is not written for slab contexts");
     if (ctx->P.pump) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written without Ekman pumping");
     if (ctx->P.buoy_imp) return fail(ctx, PIZZA_EUNSUPPORTED, "the adjoint is written for explicit buoyancy");
     int rc = ensure_factors(ctx);
@@ -1975,6 +2124,33 @@ int pizza_explicit_adjoint(pizza_ctx* ctx, const double* e_psi_bar, const double
     return PIZZA_OK;
 }
 
+int pizza_nusselt_begin(pizza_ctx* ctx) {
+    if (!ctx) return PIZZA_EINVAL;
+    if (ctx->coll) return fail(ctx, PIZZA_EUNSUPPORTED, "the Nusselt weights are those of the integration state");
+    if (ctx->slab.on) return fail(ctx, PIZZA_EUNSUPPORTED, "the sum needs the rank holding m = 0: not on a slab");
+    if (!ctx->nu_buf) {
+        ctx->nu_buf = dalloc<double>(ctx, 1 + ctx->nc, ctx->allocs);
+        if (!ctx->nu_buf) return fail(ctx, PIZZA_ENOMEM, "device allocation failed");
+        std::vector<double> w(1 + ctx->nc, 0.0);
+        pizza_nusselt_weights(ctx, w.data() + 1);
+        CK(cudaMemcpy(ctx->nu_buf, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemsetAsync(ctx->nu_buf, 0, sizeof(double), ctx->stream));
+    ctx->nu_on = true;
+    ctx->nu_steps = 0;
+    return PIZZA_OK;
+}
+
+int pizza_nusselt_end(pizza_ctx* ctx, double* sum, int* steps) {
+    if (!ctx || !sum) return fail(ctx, PIZZA_EINVAL, "NULL argument");
+    if (!ctx->nu_on) return fail(ctx, PIZZA_ESTATE, "pizza_nusselt_begin was not called");
+    CK(cudaMemcpyAsync(sum, ctx->nu_buf, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (steps) *steps = ctx->nu_steps;
+    ctx->nu_on = false;
+    return PIZZA_OK;
+}
+
 int pizza_nusselt_weights(const pizza_ctx* ctx, double* w) {
     if (!ctx || !w) return PIZZA_EINVAL;
     if (ctx->coll) return PIZZA_EUNSUPPORTED;
@@ -1990,6 +2166,7 @@ int pizza_nusselt_weights(const pizza_ctx* ctx, double* w) {
 int pizza_autotune(pizza_ctx* ctx, int* nb_r, int* phi_thr) {
     if (!ctx) return PIZZA_EINVAL;
     if (ctx->coll) return fail(ctx, PIZZA_EUNSUPPORTED, "the autotuner covers the integration formulation");
+    if (ctx->slab.on) return fail(ctx, PIZZA_EUNSUPPORTED, "the autotuner times whole contexts, not slabs");
     int dev = 0, smax = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -2123,6 +2300,10 @@ int pizza_batch_create(pizza_batch** out, pizza_ctx* const* ctxs, int n) {
             delete b;
             return batch_fail(PIZZA_ESTATE, "pizza_batch_create: a context is recording a tape");
         }
+        if (ctxs[i]->slab.on) {
+            delete b;
+            return batch_fail(PIZZA_EUNSUPPORTED, "pizza_batch_create: slab contexts exchange through callbacks");
+        }
         b->ctxs.push_back(ctxs[i]);
     }
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -2236,6 +2417,17 @@ int pizza_synchronize(pizza_ctx* ctx) {
         int f = 0;
         CK(cudaMemcpy(&f, ctx->finite_flag, sizeof(int), cudaMemcpyDeviceToHost));
         if (f) return fail(ctx, PIZZA_ENONFINITE, "a NaN or infinite value appeared in the state");
+    }
+    if (ctx->cfl_alpha > 0.0) {
+        double r[2] = {0.0, 0.0};
+        CK(cudaMemcpy(r, ctx->cfl_buf, sizeof r, cudaMemcpyDeviceToHost));
+        CK(cudaMemset(ctx->cfl_buf, 0, sizeof r));
+        const double rate = std::max(r[0], r[1]);
+        if (rate > 0.0 && ctx->dt * rate > ctx->cfl_alpha)
+            return fail(ctx, PIZZA_ECFL,
+                        "Courant criterion (Eq. cfl) exceeded: dt = %.6g > alpha / max(|u_s|/ds, |u_phi|/(s dphi)) = "
+                        "%.6g (alpha %.3g, rates %.17g, %.17g)",
+                        ctx->dt, ctx->cfl_alpha / rate, ctx->cfl_alpha, r[0], r[1]);
     }
     return PIZZA_OK;
 }

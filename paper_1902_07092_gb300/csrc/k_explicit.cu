@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
     using RT = typename Cx<T>::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
-    const int m = blockIdx.x;
+    const int m = P.m_lo + blockIdx.x;
     const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
     const int NB = radial_batch(P);
     T* bufA = sm;
@@ -231,13 +231,61 @@ struct P2<float2> {
     __device__ static float v(int e) { return pow2f(e); }
 };
 
+// Courant rates of Eq. cfl at radius k from the synthesised packed pair
+// g1 = v + i l1 u_phi on the n_phi points (v = d Psi/d phi, u_s = (h^2/s) v in
+// the integration formulation, v/s in collocation): max |u_s|/ds_k and
+// max |u_phi|/(s_k dphi), folded into P.cfl_max[0..1] as atomic maxima of their
+// bit patterns (non-negative doubles order like their bits).  Called by every
+// thread of the block; uses red[0 .. 2 * warps).
+__device__ __forceinline__ double re_abs(float2 z) { return fabs((double)z.x); }
+__device__ __forceinline__ double im_abs(float2 z) { return fabs((double)z.y); }
+__device__ __forceinline__ double re_abs(double2 z) { return fabs(z.x); }
+__device__ __forceinline__ double im_abs(double2 z) { return fabs(z.y); }
+__device__ __forceinline__ double re_abs(ddc z) { return fabs(dd_to(z.x)); }
+__device__ __forceinline__ double im_abs(ddc z) { return fabs(dd_to(z.y)); }
+
+template <class T>
+__device__ void cfl_rates(const StepParams& P, const T* R, int Pn, double l1, int k, double* red) {
+    double a = 0.0, b = 0.0;
+    for (int j = threadIdx.x; j < Pn; j += blockDim.x) {
+        a = fmax(a, re_abs(R[j]));
+        b = fmax(b, im_abs(R[j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red[2 * w] = a;
+        red[2 * w + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < nw; ++i) {
+            a = fmax(a, red[2 * i]);
+            b = fmax(b, red[2 * i + 1]);
+        }
+        const double s = P.s[k];
+        const double fs = P.coll ? 1.0 / s : P.h2[k] / s;
+        const double rs = fs * a / P.cfl_ds[k];
+        const double rp = b / l1 / (s * P.cfl_dphi);
+        atomicMax(reinterpret_cast<unsigned long long*>(P.cfl_max), (unsigned long long)__double_as_longlong(rs));
+        atomicMax(reinterpret_cast<unsigned long long*>(P.cfl_max + 1),
+                  (unsigned long long)__double_as_longlong(rp));
+    }
+    __syncthreads();
+}
+
 template <class T>
 __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* __restrict__ G1,
                                                          T* __restrict__ G2, int pair) {
     using RT = typename Cx<T>::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
-    const int k = blockIdx.x;
+    const int k = P.k_lo + blockIdx.x;
     const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
     T* X = sm;
     T* Y = sm + Pn;
@@ -257,6 +305,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* 
         load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, (RT)1, l1);
         load_packed_spectrum(X + Pn, G1 + g_index(k, 2, 0, M), M, Pn, n_m, (RT)1, l2);
         T* R = fft_batched<+1>(X, Y, P.plan_p, 2);
+        if (P.cfl_max) cfl_rates(P, R, Pn, (double)l1, k, red);
         T* O = (R == X) ? Y : X;
         for (int j = tid; j < Pn; j += nth) {
             const T g1 = R[j], g2 = R[Pn + j];
@@ -271,6 +320,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products(StepParams P, const T* 
     }
     load_packed_spectrum(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, (RT)1, l1);
     T* R = fft_batched<+1>(X, Y, P.plan_p, 1);
+    if (P.cfl_max) cfl_rates(P, R, Pn, (double)l1, k, red);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
         const int j = tid + i * nth;
@@ -357,7 +407,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
                                                             double2* __restrict__ G2, int pair) {
     extern __shared__ __align__(16) unsigned char smraw[];
     ddc* sm = reinterpret_cast<ddc*>(smraw);
-    const int k = blockIdx.x;
+    const int k = P.k_lo + blockIdx.x;
     const int Pn = P.n_phi, M = P.M, n_m = P.n_m;
     ddc* X = sm;
     ddc* Y = sm + Pn;
@@ -399,6 +449,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
         load_packed_spectrum_dd(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, pow2f(e1));
         load_packed_spectrum_dd(X + Pn, G1 + g_index(k, 2, 0, M), M, Pn, n_m, pow2f(e2));
         ddc* R = fft_batched<+1>(X, Y, P.plan_p, 2);
+        if (P.cfl_max) cfl_rates(P, R, Pn, (double)pow2f(e1), k, red);
         ddc* O = (R == X) ? Y : X;
         for (int j = tid; j < Pn; j += nth) {
             const ddc g1 = R[j], g2 = R[Pn + j];
@@ -419,6 +470,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
     }
     load_packed_spectrum_dd(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, pow2f(e1));
     ddc* R = fft_batched<+1>(X, Y, P.plan_p, 1);
+    if (P.cfl_max) cfl_rates(P, R, Pn, (double)pow2f(e1), k, red);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
         const int j = tid + i * nth;
@@ -493,7 +545,7 @@ __global__ void __launch_bounds__(NTHREADS_R) k_grid_to_spec(StepParams P, const
     using RT = typename Cx<T>::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
-    const int m = blockIdx.x;
+    const int m = P.m_lo + blockIdx.x;
     const int K = P.K, L = 2 * K, N = P.n_r, nc = P.nc, M = P.M;
     const int NB = radial_batch(P);
     T* bufA = sm;
@@ -773,7 +825,7 @@ static cudaError_t spec_to_grid_t(const StepParams& P, VecSet y, void* G1, cudaS
     const size_t sm = smem_spec_to_grid(P);
     cudaError_t err = cudaFuncSetAttribute(k_spec_to_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    k_spec_to_grid<T><<<P.M, NTHREADS_R, sm, st>>>(P, y, static_cast<T*>(G1));
+    k_spec_to_grid<T><<<slab_modes(P), NTHREADS_R, sm, st>>>(P, y, static_cast<T*>(G1));
     return cudaGetLastError();
 }
 
@@ -796,7 +848,7 @@ static cudaError_t phi_products_t(const StepParams& P, const void* G1, void* G2,
     const size_t sm = (pair ? 2 : 1) * smem_phi_products(P);
     err = cudaFuncSetAttribute(k_phi_products<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    k_phi_products<T><<<P.n_r, nth, sm, st>>>(P, static_cast<const T*>(G1), static_cast<T*>(G2), pair);
+    k_phi_products<T><<<slab_radii(P), nth, sm, st>>>(P, static_cast<const T*>(G1), static_cast<T*>(G2), pair);
     return cudaGetLastError();
 }
 
@@ -805,7 +857,7 @@ static cudaError_t grid_to_spec_t(const StepParams& P, const void* G2, VecSet y,
     const size_t sm = smem_grid_to_spec(P);
     cudaError_t err = cudaFuncSetAttribute(k_grid_to_spec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    k_grid_to_spec<T><<<P.M, NTHREADS_R, sm, st>>>(P, static_cast<const T*>(G2), y, e);
+    k_grid_to_spec<T><<<slab_modes(P), NTHREADS_R, sm, st>>>(P, static_cast<const T*>(G2), y, e);
     return cudaGetLastError();
 }
 
@@ -825,7 +877,7 @@ cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2*
         const size_t sm = (pair ? 2 : 1) * smem_phi_products(P);
         err = cudaFuncSetAttribute(k_phi_products_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (err != cudaSuccess) return err;
-        k_phi_products_dd<<<P.n_r, nth, sm, st>>>(P, G1, G2, pair);
+        k_phi_products_dd<<<slab_radii(P), nth, sm, st>>>(P, G1, G2, pair);
         return cudaGetLastError();
     }
     return phi_products_t<double2>(P, G1, G2, st);

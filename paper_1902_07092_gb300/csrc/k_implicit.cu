@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
                                                       int want_imp, int keep_f) {
     extern __shared__ double2 sm[];
     const int nc = P.nc, M = P.M;
-    const int m0 = blockIdx.x * MB;
+    const int m0 = P.m_lo + blockIdx.x * MB;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
     const int np = nc - 4, nt = nc - 2;
     const int nbp = (np + 7) / 8, nbt = (nt + 7) / 8;
@@ -1055,7 +1055,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve_galerkin(StepParams P, Rhs
                                                                VecSet mass_out, VecSet imp_out, int want_mass,
                                                                int want_imp) {
     extern __shared__ double2 sm[];
-    const int nc = P.nc, m = blockIdx.x;
+    const int nc = P.nc, m = P.m_lo + blockIdx.x;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5;
     const int np = nc - 4, nt = nc - 2;
     SolveSmem s = carve<1>(sm, nc);
@@ -1175,7 +1175,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve_galerkin(StepParams P, Rhs
 __global__ void __launch_bounds__(NTHREADS_S) k_apply(StepParams P, VecSet y, VecSet mass_out, VecSet imp_out,
                                                       int want_mass, int want_imp) {
     extern __shared__ double2 sm[];
-    const int m = blockIdx.x;
+    const int m = P.m_lo + blockIdx.x;
     const int nc = P.nc;
     double2* xp = sm;
     double2* xt = xp + nc;
@@ -1220,7 +1220,7 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
                            sizeof(double) * 2 * 2 * GCH * 12 + 3 * round8(P.nc);
         cudaError_t err = cudaFuncSetAttribute(k_solve_galerkin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg);
         if (err != cudaSuccess) return err;
-        k_solve_galerkin<<<P.M, NTHREADS_S, smg, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+        k_solve_galerkin<<<slab_modes(P), NTHREADS_S, smg, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
                                                       want_imp ? 1 : 0);
         return cudaGetLastError();
     }
@@ -1240,8 +1240,25 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
     const int keep = smk + fa.sharedSizeBytes <= (size_t)smax ? 1 : 0;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(keep ? smk : sm));
     if (err != cudaSuccess) return err;
-    kern<<<P.M, NTHREADS_S, keep ? smk : sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+    kern<<<slab_modes(P), NTHREADS_S, keep ? smk : sm, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
                                                    want_imp ? 1 : 0, keep);
+    return cudaGetLastError();
+}
+
+// acc[0] += sum_n w_n Re theta_hat_0n = Nu - 1 of the state (one warp, a fixed
+// summation order: the lane sums, then a butterfly of shuffles)
+__global__ void k_nusselt_accumulate(const double2* __restrict__ th0, const double* __restrict__ w, int nc,
+                                     double* acc) {
+    double t = 0.0;
+    for (int n = threadIdx.x; n < nc; n += 32) t = fma(w[n], th0[n].x, t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) acc[0] += t;
+}
+
+cudaError_t launch_nusselt_accumulate(const StepParams& P, VecSet y, const double* w, double* acc,
+                                      cudaStream_t st) {
+    k_nusselt_accumulate<<<1, 32, 0, st>>>(y.th, w, P.nc, acc);
     return cudaGetLastError();
 }
 
@@ -1255,7 +1272,7 @@ cudaError_t launch_apply(const StepParams& P, VecSet y, VecSet mass_out, VecSet 
     const size_t sm = sizeof(double2) * 2 * P.nc + sizeof(double) * P.nc;
     cudaError_t err = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    k_apply<<<P.M, NTHREADS_S, sm, st>>>(P, y, mass_out, imp_out, want_mass ? 1 : 0, want_imp ? 1 : 0);
+    k_apply<<<slab_modes(P), NTHREADS_S, sm, st>>>(P, y, mass_out, imp_out, want_mass ? 1 : 0, want_imp ? 1 : 0);
     return cudaGetLastError();
 }
 

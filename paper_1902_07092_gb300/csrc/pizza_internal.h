@@ -135,7 +135,20 @@ struct StepParams {
     // the FP32 pipe (option "azimuthal_dd"): 1 when selected (plan_p.twdd set)
     int phi_dd;
     double2* pump_F;
+    // m-slab decomposition (pizza_set_slab): the per-mode kernels (a1, a3, solve)
+    // take modes [m_lo, m_lo + m_n), the per-radius kernel (a2) radii
+    // [k_lo, k_lo + k_n); a count of 0 means every mode / radius
+    int m_lo, m_n, k_lo, k_n;
+    // Courant guard (option "cfl_alpha", Eq. cfl): when cfl_max is set the
+    // azimuthal kernel folds max |u_s|/ds_k and max |u_phi|/(s_k dphi) of the
+    // synthesised state into cfl_max[0], cfl_max[1] (atomic maxima)
+    double* cfl_max;
+    const double* cfl_ds;  // [n_r] local Gauss-Lobatto spacing
+    double cfl_dphi;       // 2 pi / n_phi
 };
+
+__host__ __device__ inline int slab_modes(const StepParams& P) { return P.m_n > 0 ? P.m_n : P.M; }
+__host__ __device__ inline int slab_radii(const StepParams& P) { return P.k_n > 0 ? P.k_n : P.n_r; }
 
 struct RhsTerm {
     VecSet v;
@@ -156,6 +169,8 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
 cudaError_t launch_apply(const StepParams& P, VecSet y, VecSet mass_out, VecSet imp_out, bool want_mass,
                          bool want_imp, cudaStream_t st);
 cudaError_t launch_check_finite(const StepParams& P, VecSet y, int* flag, cudaStream_t st);
+cudaError_t launch_nusselt_accumulate(const StepParams& P, VecSet y, const double* w, double* acc,
+                                      cudaStream_t st);
 cudaError_t launch_coll_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st);
 cudaError_t launch_coll_grid_rows(const StepParams& P, const double2* G1, const double2* G2, VecSet e,
                                   cudaStream_t st);

@@ -40,21 +40,42 @@ def state_errors(gpu, ref):
     return out
 
 
-# The zonal flow is forced only by the azimuthal mean of u_s omega, a sum of
-# products of size |v||omega| that cancels to ~1e-4 of its terms; rounding of the
-# products (1e-16 of their size) is therefore ~1e-12 of u_bar itself.  Its own
-# relative error is held to U_FACTOR times the state tolerance.
+# The zonal flow is forced only by the azimuthal mean of u_s omega,
+# [v omega]_0 = sum_{m >= 1} 2 Re(v_m conj(omega_m)), a sum of terms of size
+# |v_m||omega_m| that cancels to a small fraction of them.  Any relative error
+# delta of the state (v, omega) is therefore a relative error ~ c_u delta of the
+# forcing, c_u = |sum 2 |v_m||omega_m|| / |sum 2 Re(v_m conj(omega_m))| (norms
+# over the radial grid), and of u_bar, which integrates it.  Measured in the
+# oracle: c_u ~ 1e2 .. 6e2 at n_r = 33, ~4e3 on the n_r = 257 workload.  u_bar's
+# own relative error is held to max(U_FACTOR, c_u) times the state tolerance,
+# c_u evaluated on the reference state.
 U_FACTOR = 20.0
 
 
-def assert_state_close(gpu, ref, tol, floor=1e-3):
-    """Whole-state relative L2 <= tol; per field <= tol (u_bar: U_FACTOR * tol) for
-    fields carrying more than ``floor`` of the state norm (a smaller field's error
-    is bounded, relative to the state, by the whole-state check)."""
+def zonal_cancellation(oracle):
+    """c_u of the oracle's current state (integration and Galerkin steppers)."""
+    from oracle.explicit import radial_fields
+    v, _, omega, _ = radial_fields(oracle.g, *oracle.y)
+    terms = 2.0 * np.sum(np.abs(v[:, 1:]) * np.abs(omega[:, 1:]), axis=1)
+    mean = 2.0 * np.sum((v[:, 1:] * np.conj(omega[:, 1:])).real, axis=1)
+    nm = np.linalg.norm(mean)
+    return float(np.linalg.norm(terms) / nm) if nm > 0 else 1.0
+
+
+def assert_state_close(gpu, ref, tol, floor=1e-9, oracle=None):
+    """Whole-state relative L2 <= tol; per field <= tol (u_bar: max(U_FACTOR, c_u)
+    * tol, c_u from ``oracle`` when given) for fields carrying more than
+    ``floor`` of the state norm (a smaller field's error is bounded, relative to
+    the state, by the whole-state check)."""
     e = state_errors(gpu, ref)
     total = np.sqrt(sum(n * n for n in e["_norms"]))
     assert e["state"] <= tol, e
     for name, n in zip(("psi", "theta", "u"), e["_norms"]):
         if n > floor * total:
-            assert e[name] <= (U_FACTOR * tol if name == "u" else tol), (name, e)
+            if name != "u":
+                assert e[name] <= tol, (name, e)
+            elif e["u"] > U_FACTOR * tol:
+                assert oracle is not None, ("u", e)
+                c_u = zonal_cancellation(oracle)
+                assert e["u"] <= max(U_FACTOR, c_u) * tol, ("u", c_u, e)
     return e

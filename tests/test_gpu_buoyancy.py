@@ -38,7 +38,7 @@ def nonzero_state(n_r, n_phi, amp, seed):
     return psi, th, u
 
 
-@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443"])
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443", "BPR353"])
 @pytest.mark.parametrize("amp", [1e-4, 1.0])
 def test_implicit_buoyancy_steps_match_oracle_tiny(scheme, amp):
     n_r, n_phi = 33, 96
@@ -49,7 +49,7 @@ def test_implicit_buoyancy_steps_match_oracle_tiny(scheme, amp):
     for _ in range(4):
         gpu.step(1)
         ora.step()
-        assert_state_close(gpu.get_state(), ora.y, 1e-12)
+        assert_state_close(gpu.get_state(), ora.y, 1e-12, oracle=ora)
     gpu.close()
 
 
@@ -62,7 +62,7 @@ def test_implicit_buoyancy_steps_match_oracle_n257():
     for _ in range(2):
         gpu.step(1)
         ora.step()
-        assert_state_close(gpu.get_state(), ora.y, 2e-12)
+        assert_state_close(gpu.get_state(), ora.y, 2e-12, oracle=ora)
     gpu.close()
 
 
@@ -75,7 +75,7 @@ def test_implicit_buoyancy_steps_match_oracle_n1025():
     for k in range(2):
         gpu.step(1)
         ora.step()
-        e = assert_state_close(gpu.get_state(), ora.y, 5e-12)
+        e = assert_state_close(gpu.get_state(), ora.y, 5e-12, oracle=ora)
         print("implicit buoyancy n_r=1025 step %d: %s" % (k + 1, {a: "%.2e" % b for a, b in e.items() if a != "_norms"}))
     gpu.close()
 
@@ -116,7 +116,7 @@ def test_implicit_buoyancy_option_limits():
     s.close()
 
 
-@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443"])
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443", "BPR353"])
 @pytest.mark.parametrize("amp", [1e-4, 1.0])
 def test_implicit_buoyancy_collocation_steps_match_oracle(scheme, amp):
     """Collocation (Section 3.1) with the buoyancy implicit: the solve runs the

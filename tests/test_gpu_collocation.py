@@ -105,7 +105,7 @@ def test_collocation_set_state_grid_fields(n_r, n_phi):
     gpu.close()
 
 
-@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443"])
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443", "BPR353"])
 @pytest.mark.parametrize("amp", [1e-4, 1.0])
 def test_collocation_steps_match_oracle_tiny(scheme, amp):
     """n_r = 33 collocation points, n_phi = 96, E = 1e-3, Pr = 1, Ra = 2 Ra_c,

@@ -34,7 +34,7 @@ def make_pair(n_r, n_phi, E, ra_factor, scheme, dt, buoy=False):
     return gpu, ora
 
 
-@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF3", "ARS443"])
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF3", "ARS443", "BPR353"])
 @pytest.mark.parametrize("amp", [1e-4, 1.0])
 def test_galerkin_steps_match_oracle_tiny(scheme, amp):
     n_r, n_phi = 33, 96
@@ -46,7 +46,7 @@ def test_galerkin_steps_match_oracle_tiny(scheme, amp):
     for _ in range(5):
         gpu.step(1)
         ora.step()
-        assert_state_close(gpu.get_state(), ora.y, 1e-12)
+        assert_state_close(gpu.get_state(), ora.y, 1e-12, oracle=ora)
     gpu.close()
 
 
@@ -66,7 +66,7 @@ def test_galerkin_sizes_and_implicit_buoyancy(n_r, n_phi):
         for _ in range(3):
             gpu.step(1)
             ora.step()
-        e = assert_state_close(gpu.get_state(), ora.y, 1e-12)
+        e = assert_state_close(gpu.get_state(), ora.y, 1e-12, oracle=ora)
         print("galerkin n_r=%d buoy=%d: state %.2e" % (n_r, buoy, e["state"]))
         gpu.close()
 
@@ -87,8 +87,8 @@ def test_galerkin_sparse_workload_matches_oracle_and_tau():
         gpu.step(1)
         tau.step(1)
         ora.step()
-        e = assert_state_close(gpu.get_state(), ora.y, 2e-11)
-        et = assert_state_close(gpu.get_state(), tau.get_state(), 2e-11)
+        e = assert_state_close(gpu.get_state(), ora.y, 2e-11, oracle=ora)
+        et = assert_state_close(gpu.get_state(), tau.get_state(), 2e-11, oracle=ora)
         print("galerkin n257: vs oracle %.2e, vs GPU tau %.2e" % (e["state"], et["state"]))
     gpu.close()
     tau.close()
@@ -188,7 +188,7 @@ def test_galerkin_with_pumping_mixed_precision_batch_and_adjoint():
     for _ in range(3):
         gpu.step(1)
         ora.step()
-    assert_state_close(gpu.get_state(), ora.y, 1e-12)
+    assert_state_close(gpu.get_state(), ora.y, 1e-12, oracle=ora)
     gpu.close()
     # mixed precision
     gpu = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "ARS443", 1e-4, radial="galerkin")
@@ -199,7 +199,7 @@ def test_galerkin_with_pumping_mixed_precision_batch_and_adjoint():
     for _ in range(5):
         gpu.step(1)
         ora.step()
-    assert_state_close(gpu.get_state(), ora.y, 1e-6)
+    assert_state_close(gpu.get_state(), ora.y, 1e-6, oracle=ora)
     gpu.close()
     # one batch graph
     runs = [("galerkin", "CNAB2"), ("integration", "ARS443")]

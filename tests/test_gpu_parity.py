@@ -50,7 +50,7 @@ def test_explicit_terms_match_oracle(n_r, n_phi):
     gpu.close()
 
 
-@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443"])
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF2", "SBDF3", "ARS443", "BPR353"])
 @pytest.mark.parametrize("amp", [1e-4, 1.0])
 def test_steps_match_oracle_tiny(scheme, amp):
     """configs: n_r = 33, n_phi = 96, E = 1e-3, Pr = 1, Ra = 2 Ra_c, dt = 1e-4;
@@ -64,7 +64,7 @@ def test_steps_match_oracle_tiny(scheme, amp):
     for k in range(5):
         gpu.step(1)
         ora.step()
-        assert_state_close(gpu.get_state(), ora.y, 1e-12)
+        assert_state_close(gpu.get_state(), ora.y, 1e-12, oracle=ora)
     gpu.close()
 
 
@@ -80,7 +80,7 @@ def test_steps_match_oracle_sparse_workload():
     for k in range(2):
         gpu.step(1)
         ora.step()
-        assert_state_close(gpu.get_state(), ora.y, 2e-12)
+        assert_state_close(gpu.get_state(), ora.y, 2e-12, oracle=ora)
     gpu.close()
 
 
@@ -120,7 +120,7 @@ def test_edge_cases():
     for _ in range(3):
         gpu.step(1)
         ora.step()
-    assert_state_close(gpu.get_state(), ora.y, 1e-12)
+    assert_state_close(gpu.get_state(), ora.y, 1e-12, oracle=ora)
     # ragged input: fewer coefficients than N_c are zero-padded
     th = inputs.theta_init(n_r, n_phi, 1e-3, 8, cfg=1)
     thr = np.ascontiguousarray(th[:, :7])
@@ -268,7 +268,7 @@ def test_steps_match_oracle_split_streamfunction_solve(scheme):
     for k in range(2):
         gpu.step(1)
         ora.step()
-        e = assert_state_close(gpu.get_state(), ora.y, 5e-12)
+        e = assert_state_close(gpu.get_state(), ora.y, 5e-12, oracle=ora)
         print("split solve n_r=513 %s step %d: state %.2e" % (scheme, k + 1, e["state"]))
     gpu.close()
 
@@ -292,7 +292,7 @@ def test_steps_match_oracle_fp32_refined_temperature_solve(scheme):
     for k in range(2):
         gpu.step(1)
         ora.step()
-        e = assert_state_close(gpu.get_state(), ora.y, 5e-12)
+        e = assert_state_close(gpu.get_state(), ora.y, 5e-12, oracle=ora)
         print("FP32-refined temperature n_r=1025 %s step %d: %s" % (
             scheme, k + 1, {a: "%.2e" % b for a, b in e.items() if a != "_norms"}))
     gpu.close()

@@ -53,7 +53,7 @@ def test_pumping_explicit_terms_match_oracle(n_r, n_phi):
     gpu.close()
 
 
-@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF3", "ARS443"])
+@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF3", "ARS443", "BPR353"])
 @pytest.mark.parametrize("amp", [1e-4, 1.0])
 def test_pumping_steps_match_oracle_integration(scheme, amp):
     n_r, n_phi = 33, 96
@@ -67,7 +67,7 @@ def test_pumping_steps_match_oracle_integration(scheme, amp):
     for _ in range(4):
         gpu.step(1)
         ora.step()
-        assert_state_close(gpu.get_state(), ora.y, 1e-12)
+        assert_state_close(gpu.get_state(), ora.y, 1e-12, oracle=ora)
     gpu.close()
 
 
@@ -82,7 +82,7 @@ def test_pumping_steps_match_oracle_n257():
     for _ in range(2):
         gpu.step(1)
         ora.step()
-        assert_state_close(gpu.get_state(), ora.y, 2e-12)
+        assert_state_close(gpu.get_state(), ora.y, 2e-12, oracle=ora)
     gpu.close()
 
 

@@ -21,7 +21,7 @@ from tests.parity_util import GOLDEN
 pytestmark = pytest.mark.gpu
 
 N_R, N_PHI, M_MODE, DT = 257, 384, 12, 1e-7
-SCHEME_TOL = {"SBDF3": 1e-6, "ARS443": 1e-8, "CNAB2": 1e-6}   # relative error of lambda
+SCHEME_TOL = {"SBDF3": 1e-6, "ARS443": 1e-8, "BPR353": 1e-8, "CNAB2": 1e-6}   # relative error of lambda
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +33,7 @@ def mode():
     return t3, nc, lam, p, th
 
 
-@pytest.mark.parametrize("scheme", ["SBDF3", "CNAB2", "ARS443"])
+@pytest.mark.parametrize("scheme", ["SBDF3", "CNAB2", "ARS443", "BPR353"])
 def test_growth_rate_and_drift_of_the_m12_mode(mode, scheme):
     from paper_1902_07092_gb300.binding import Solver
     t3, nc, lam, p, th = mode
@@ -55,7 +55,7 @@ def test_growth_rate_and_drift_of_the_m12_mode(mode, scheme):
         scheme, est.real, est.imag, lam.real, lam.imag, t3["eigensolver"]["tau"], t3["eigensolver"]["omega_d"]))
     assert np.linalg.norm(th2 - z2 * T[M_MODE]) < 1e-6 * np.linalg.norm(th2)
     assert abs(est - lam) < SCHEME_TOL[scheme] * abs(lam)
-    if scheme == "ARS443":
+    if scheme in ("ARS443", "BPR353"):
         lsb = t3["eigensolver"]
         assert abs(est.real - lsb["tau"]) < 1e-3
         assert abs(est.imag - lsb["omega_d"]) < 5e-3
