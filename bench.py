@@ -1,11 +1,15 @@
 #!/usr/bin/env python
 """Throughput of the IMEX time step (Mgridpoint-steps/s = n_r * n_phi * steps / s).
 
-Default workload: n_r = 257, n_phi = 768 (N_m = 256), E = 1e-5, Pr = 1,
-Ra = 10 Ra_c, radius ratio 0.35, Chebyshev integration / tau, ARS443, FP64,
-seeded initial temperature perturbation of amplitude 1e-3.  --workload selects
-another (e.g. coll_n257_p768: the same problem in the collocation formulation;
-coll_n33_p96: n_r = 33 collocation points, CNAB2).
+Default workload (large_n2049_p6144): n_r = 2049, n_phi = 6144 (N_m = 2048,
+N_c = 1365), E = 1e-8, Pr = 1, Ra = 20 Ra_c, radius ratio 0.35, Chebyshev
+integration / tau, SBDF3, dt = 1e-10, FP64, seeded initial temperature
+perturbation of amplitude 1e-3 -- the largest single-GPU configuration.  The
+same line carries the mixed-precision form of the same workload (FP32 explicit
+stage, FP64 solves and history) with its distance from the FP64 path.
+--workload selects another (sparse_n257_p768: n_r = 257, ARS443;
+coll_n257_p768: the same problem in the collocation formulation; batch64: 64
+uneven runs in one CUDA graph; ...).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload W]
 
@@ -14,9 +18,8 @@ library's stream, with a 256 MiB write between steps to flush the 129 MB L2
 (outside the events).  A second pass of K steps records events around every
 kernel launch for the per-kernel (roofline) numbers.  The end-to-end figure
 times set_state (pinned host buffers) + step + get_state per step.
-Multi-GPU (torchrun): independent replicas, one per rank (the step does not
-shard without an all-to-all exchange); value = all ranks' grid-point-steps /
-max time over ranks.
+Multi-GPU (torchrun): independent replicas, one per rank; value = all ranks'
+grid-point-steps / max time over ranks.
 """
 import argparse
 import json
@@ -37,7 +40,10 @@ from paper_1902_07092_gb300 import inputs  # noqa: E402
 
 METRIC = "Mgridpoint-steps/s (n_r*n_phi*steps/s), FP64 vs mixed/batched at <=1e-6 rel err"
 UNIT = "Mgridpoint-steps/s"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (152 SMs x 4 flop/clk x ~2.07 GHz)
+# GB300 FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk (ncu's
+# sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304/cycle)
+# x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 KERNELS = ("spec_to_grid", "phi_products", "grid_to_spec", "solve")
 
 
@@ -106,7 +112,7 @@ NCU_TRAFFIC = {
 
 
 def launches_per_step(scheme):
-    return {"CNAB2": 4, "SBDF2": 4, "SBDF3": 4, "ARS443": 16}[scheme]
+    return {"CNAB2": 4, "SBDF2": 4, "SBDF3": 4, "ARS443": 16, "BPR353": 13}[scheme]
 
 
 # --------------------------------------------------------------- clocks -----
@@ -157,11 +163,22 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ oracle arm ----
+def oracle_kind(wl):
+    if wl.get("radial") == "collocation":
+        return "oracle.collocation: dense grid-valued inverses"
+    if wl.get("radial") == "galerkin":
+        return "oracle.galerkin: LAPACK banded LU of the Galerkin systems"
+    return "oracle.banded: band-stored operators, Appendix A bordered solves with a banded LU"
+
+
 def oracle_sample(wl, Ra, budget_s, max_steps):
-    """Time the oracle (as it stands) on the workload: steps until budget_s."""
+    """Time the oracle (as it stands) on the workload: steps until budget_s.
+    Returns (steps, seconds, set-up seconds, average busy cores), the last from
+    the process's CPU time over the wall time of the timed steps."""
+    from oracle.banded import BandedIntegrationStepper
     from oracle.collocation import CollocationStepper
     from oracle.galerkin import GalerkinStepper
-    from oracle.stepper import IntegrationStepper
+    from oracle import schemes
     n_r, n_phi = wl["n_r"], wl["n_phi"]
     nc = inputs.n_c_of(wl)
     t0 = time.perf_counter()
@@ -171,18 +188,24 @@ def oracle_sample(wl, Ra, budget_s, max_steps):
         st = CollocationStepper(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
         st.set_state(z, z.copy(), th, zu)
     else:
-        cls = GalerkinStepper if wl.get("radial") == "galerkin" else IntegrationStepper
+        cls = GalerkinStepper if wl.get("radial") == "galerkin" else BandedIntegrationStepper
         st = cls(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
         st.set_state(z, th, zu)
-    st.step()                                  # builds the LU factors (set-up, untimed)
+    if hasattr(st, "lu"):
+        for g in schemes.implicit_weights(wl["scheme"]):   # every factorisation (set-up, untimed)
+            st.lu(g)
+    st.step()                                  # first step (start-up; untimed)
     setup = time.perf_counter() - t0
     n, t = 0, 0.0
+    r0 = os.times()
     while n < max_steps and (t < budget_s or n == 0):
         a = time.perf_counter()
         st.step()
         t += time.perf_counter() - a
         n += 1
-    return n, t, setup
+    r1 = os.times()
+    busy = ((r1.user - r0.user) + (r1.system - r0.system)) / max(t, 1e-9)
+    return n, t, setup, round(busy, 1)
 
 
 def max_over_ranks(x, world, device=None):
@@ -223,16 +246,18 @@ def run_reference(args, wl, Ra, rank):
     if rank != 0:
         return
     per_step_budget = 150.0 / max(args.steps + args.warmup, 1)
-    n, t, setup = oracle_sample(wl, Ra, budget_s=min(150.0, per_step_budget * args.steps), max_steps=args.steps)
+    n, t, setup, busy = oracle_sample(wl, Ra, budget_s=min(150.0, per_step_budget * args.steps),
+                                      max_steps=args.steps)
     gp = wl["n_r"] * wl["n_phi"]
     val = gp * n / t / 1e6
-    sample = "%d of %d requested steps of the full %s workload (oracle set-up %.1f s untimed)" % (
-        n, args.steps, args.workload, setup)
+    sample = ("%d of %d requested steps of the full %s workload (oracle set-up, factorisation and first step "
+              "%.1f s untimed; %s; %d BLAS threads available)" % (n, args.steps, args.workload, setup,
+                                                                 oracle_kind(wl), cores_used()))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": n, "warmup": 1, "ms_per_step": 1e3 * t / n, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args, wl, Ra),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": busy, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -246,7 +271,11 @@ def config_of(args, wl, Ra):
                 wl.get("radial"), "chebyshev-integration-tau"),
             "l2": "flushed (256 MiB write) between timed steps",
             "parallelism": "replicas" if args.gpus > 1 else "single",
-            "precision": ("fp64" if getattr(args, "precision", "fp64") == "fp64"
+            "precision": ("fp64 throughout (the oracle)" if getattr(args, "impl", "native") == "reference" else
+                          "fp64: radial transforms, state, history, linear couplings and solves in FP64; the "
+                          "azimuthal FFTs and products in double-float (pairs of FP32 words, ~48-bit significands) "
+                          "with the m = 0 means of the products in FP64"
+                          if getattr(args, "precision", "fp64") == "fp64"
                           else "mixed: FP32 explicit stage, FP64 state/history/couplings/solves")}
 
 
@@ -381,34 +410,33 @@ def run_batch(args, wl, rank, world, local_rank):
         s.close()
 
 
-def run_native(args, wl, Ra, rank, world, local_rank):
+def algorithmic_bytes(n_r, n_phi, scheme, radial="integration"):
+    """HBM bytes per launch of each kernel that a fused pipeline must move (the
+    grid stays on chip inside a kernel; formulas in the design notes):
+    a1 reads 2 spectral fields and writes 4 radius-major grid fields, 16 B each;
+    a2 reads 4 and writes 4 grid fields; a3 reads 4 grid fields, the 2 spectral
+    state fields for its linear couplings and writes 2 spectral fields; the solve
+    reads its right-hand-side terms and factors and writes the new state and its
+    mass (and implicit) terms: 32 B per (m, n) per vector pair (Psi, theta), the
+    paper's bordered factor storage 16 x 33 B (Psi) + 8 x 17 B (theta) per (m, n).
+    Multistep counts are the steady-state ones; DIRK counts average the stages."""
+    M = n_phi // 3 + 1
+    if radial == "collocation":
+        nc = n_r
+        f_solve = M * (16 * 2 * n_r * (n_r - 2) + 8 * n_r * (n_r - 2) + 32 * 6 * n_r)
+        return dict(zip(KERNELS, (16.0 * M * (2 * nc + 4 * n_r), 16.0 * 8 * M * n_r, 16.0 * M * (4 * n_r + 2 * nc),
+                                  float(f_solve))))
+    nc = (2 * (n_r - 1)) // 3
+    terms_out = {"CNAB2": (4, 3), "SBDF2": (4, 2), "SBDF3": (6, 2), "ARS443": (4.5, 1.5), "BPR353": (5.0, 1.5)}[scheme]
+    per_mn = 32.0 * (terms_out[0] + terms_out[1]) + 16 * 33 + 8 * 17
+    return dict(zip(KERNELS, (16.0 * M * (2 * nc + 4 * n_r), 16.0 * 8 * M * n_r, 16.0 * M * (4 * n_r + 4 * nc),
+                              per_mn * M * nc)))
+
+
+def measure_context(args, B, sol, stream, flush, world, dev, barrier, local_rank):
+    """W warm-up steps, K timed steps (events around each step, L2 flushed between
+    steps), then K steps with events around every launch."""
     import torch
-    from paper_1902_07092_gb300 import binding as B
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    n_r, n_phi = wl["n_r"], wl["n_phi"]
-    gp = n_r * n_phi
-    sol = B.Solver(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"],
-                   radial=wl.get("radial", "integration"))
-    if args.precision == "mixed":
-        B.pizza_set_option(sol.ctx, "precision", 1)
-    # a dedicated stream: the library launches, the L2 flush and the timing events
-    # all go to it (torch's default stream handle is 0, which the library reads
-    # as "use your own stream")
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-    B.pizza_set_stream(sol.ctx, stream.cuda_stream)
-    nc = inputs.n_c_of(wl)
-    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"] + 1000 * rank, cfg=wl["cfg"], n_c=nc)
-    z, zu = inputs.zero_state(n_r, n_phi, n_c=nc)
-    sol.set_state(th, z, zu)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     for _ in range(args.warmup):
         sol.step(1)
     torch.cuda.synchronize()
@@ -436,9 +464,13 @@ def run_native(args, wl, Ra, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     total_ms = max_over_ranks(total_ms, world, dev)
-    # per-kernel pass
     _, (kt, kn) = timed_pass(True)
-    # end to end through host buffers
+    return total_ms, kt, kn, clk.summary()
+
+
+def e2e_rate(args, B, sol, gp):
+    """set_state from pinned host buffers + one step + get_state into them, per step."""
+    import torch
     M, nc = sol.M, sol.n_c
     h_th = torch.empty((M, nc), dtype=torch.complex128, pin_memory=True).numpy()
     h_ps = torch.empty((M, nc), dtype=torch.complex128, pin_memory=True).numpy()
@@ -453,6 +485,87 @@ def run_native(args, wl, Ra, rank, world, local_rank):
         B.pizza_get_state(sol.ctx, h_th, h_ps, h_u)
     e2e_s = time.perf_counter() - t0
     nbytes = 2 * M * nc * 16 + nc * 8
+    return {"value": gp * k_e2e / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": k_e2e}
+
+
+def kernel_table(kt, kn, flops, nbytes, hbm_peak):
+    share = {k: float(kt[i]) / max(float(kt.sum()), 1e-30) for i, k in enumerate(KERNELS)}
+    out = {}
+    for i, k in enumerate(KERNELS):
+        us = 1e3 * float(kt[i]) / max(int(kn[i]), 1)
+        out[k] = {"launches": int(kn[i]), "avg_us": us, "share": share[k], "gflop_per_launch": flops[k] / 1e9,
+                  "fp64_tflops": flops[k] / (us * 1e-6) / 1e12 if us > 0 else None,
+                  "mb_per_launch": nbytes[k] / 1e6,
+                  "hbm_frac": nbytes[k] / (us * 1e-6) / 1e9 / hbm_peak if us > 0 else None}
+    return out
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_native(args, wl, Ra, rank, world, local_rank):
+    import torch
+    from paper_1902_07092_gb300 import binding as B
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n_r, n_phi = wl["n_r"], wl["n_phi"]
+    gp = n_r * n_phi
+    radial = wl.get("radial", "integration")
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    # FP64 FMA rate measured here, with the clocks sampled during the probe
+    with ClockSampler(local_rank) as pclk:
+        fp64_meas, fp64_ms = B.pizza_fp64_fma_rate(40000)
+    pclk = pclk.summary()
+
+    # a dedicated stream: the library launches, the L2 flush and the timing events
+    # all go to it (torch's default stream handle is 0, which the library reads
+    # as "use your own stream")
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    nc = inputs.n_c_of(wl)
+    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"] + 1000 * rank, cfg=wl["cfg"], n_c=nc)
+    z, zu = inputs.zero_state(n_r, n_phi, n_c=nc)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def make(precision):
+        s = B.Solver(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"], radial=radial)
+        if precision == "mixed":
+            B.pizza_set_option(s.ctx, "precision", 1)
+        B.pizza_set_stream(s.ctx, stream.cuda_stream)
+        s.set_state(th, z, zu)
+        return s
+
+    sol = make(args.precision)
+    total_ms, kt, kn, clocks = measure_context(args, B, sol, stream, flush, world, dev, barrier, local_rank)
+    e2e = e2e_rate(args, B, sol, gp)
+    mixed = None
+    want_mixed = (args.precision == "fp64" and radial == "integration" and not wl.get("adjoint")
+                  and not args.no_mixed)
+    if want_mixed:
+        mix = make("mixed")
+        m_ms, m_kt, m_kn, m_clk = measure_context(args, B, mix, stream, flush, world, dev, barrier, local_rank)
+        m_e2e = e2e_rate(args, B, mix, gp)
+        err = mixed_error(args, B, wl, Ra, mix, th, z, zu)
+        mixed = {"value": job_value(gp, args.steps, world, m_ms), "unit": UNIT, "ms_per_step": m_ms / args.steps,
+                 "speedup_vs_fp64": total_ms / m_ms, "e2e": m_e2e, "error_vs_fp64": err, "clocks": m_clk,
+                 "precision": "FP32 explicit stage (radial transforms, azimuthal FFTs, products); FP64 state, "
+                              "history, linear couplings, boundary rows and solves",
+                 "kernels": {k: {"avg_us": 1e3 * float(m_kt[i]) / max(int(m_kn[i]), 1),
+                                 "share": float(m_kt[i]) / max(float(m_kt.sum()), 1e-30)}
+                             for i, k in enumerate(KERNELS)}}
+        mix.close()
     err = mixed_error(args, B, wl, Ra, sol, th, z, zu) if args.precision == "mixed" else None
     adj = adjoint_cost(args, B, wl, Ra, sol, th, z, zu) if wl.get("adjoint") else None
 
@@ -460,39 +573,54 @@ def run_native(args, wl, Ra, rank, world, local_rank):
         sol.close()
         return
     value = job_value(gp, args.steps, world, total_ms)
-    flops = algorithmic_flops(n_r, n_phi, wl["scheme"], wl.get("radial", "integration"))
-    share = {k: float(kt[i]) / max(float(kt.sum()), 1e-30) for i, k in enumerate(KERNELS)}
+    flops = algorithmic_flops(n_r, n_phi, wl["scheme"], radial)
+    nbytes = algorithmic_bytes(n_r, n_phi, wl["scheme"], radial)
+    kernels = kernel_table(kt, kn, flops, nbytes, hbm_peak)
     dom = max(range(4), key=lambda i: kt[i])
-    avg_ms = float(kt[dom]) / max(int(kn[dom]), 1)
-    achieved = flops[KERNELS[dom]] / (avg_ms / 1e3) / 1e12
+    kd = KERNELS[dom]
+    avg_s = float(kt[dom]) / max(int(kn[dom]), 1) / 1e3
+    achieved = flops[kd] / avg_s / 1e12
+    traffic = NCU_TRAFFIC.get((args.workload, kd), (None, None))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": config_of(args, wl, Ra),
-        "e2e": {"value": gp * k_e2e / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes, "steps": k_e2e},
+        "e2e": e2e,
         "gpu_launches": launches_per_step(wl["scheme"]) * args.steps,
-        "roofline": {"bound": "alu", "kernel": KERNELS[dom], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "kernel": kd, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": NCU_TRAFFIC.get((args.workload, KERNELS[dom]), (None, None))[0],
-                     "traffic_source": NCU_TRAFFIC.get((args.workload, KERNELS[dom]), (None, None))[1],
-                     "peak_source": "nominal FP64 rate of the profiling recipe (not in MEASURED_PEAKS)",
+                     "frac_of_measured_fp64": achieved / fp64_meas,
+                     "traffic": traffic[0], "traffic_source": traffic[1],
+                     "peak_source": "FP64 unit count x max SM clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
+                                    "MEASURED_PEAKS.json has no FP64 figure",
                      "timing": "CUDA events around each launch, second pass of the same K steps"},
-        "kernels": {k: {"launches": int(kn[i]), "avg_us": 1e3 * float(kt[i]) / max(int(kn[i]), 1),
-                        "share": share[k], "gflop_per_launch": flops[k] / 1e9} for i, k in enumerate(KERNELS)},
-        "clocks": clk.summary(),
+        "roofline_hbm": {"bound": "hbm", "kernel": kd, "achieved": nbytes[kd] / avg_s / 1e9, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": nbytes[kd] / avg_s / 1e9 / hbm_peak,
+                         "algorithmic_bytes": nbytes[kd], "peak_source": hbm_src + ", of measured"},
+        "fp64_peak_measured": {"tflops": fp64_meas, "ms": fp64_ms, "clocks": pclk,
+                               "tflops_at_max_clock": (fp64_meas * 2070.0 / pclk["sm_mhz"]
+                                                       if pclk.get("sm_mhz") else None),
+                               "how": "pizza_fp64_fma_rate: 8 independent FMA chains x 2048 threads per SM, "
+                                      "one launch timed with CUDA events"},
+        "kernels": kernels,
+        "clocks": clocks,
     }
+    if mixed is not None:
+        line["mixed"] = mixed
     if err is not None:
         line["error_vs_fp64"] = err
     if adj is not None:
         line["adjoint"] = adj
     if not args.no_cpu_baseline and world == 1:
-        n, t_cpu, _ = oracle_sample(wl, Ra, budget_s=args.cpu_budget, max_steps=1000)
-        line["cpu_baseline"] = {"value": gp * n / t_cpu / 1e6, "unit": UNIT, "cores": cores_used(),
+        n, t_cpu, setup, busy = oracle_sample(wl, Ra, budget_s=args.cpu_budget, max_steps=1000)
+        line["cpu_baseline"] = {"value": gp * n / t_cpu / 1e6, "unit": UNIT, "cores": busy,
                                 "kind": "oracle",
-                                "sample": "%d full steps of the workload on the host CPU (%.1f s)" % (n, t_cpu)}
+                                "sample": "%d full step(s) of the workload on the host CPU (%.1f s; set-up, "
+                                          "factorisation and first step %.1f s untimed; %s; cores = average "
+                                          "busy cores, of %d BLAS threads)" % (n, t_cpu, setup, oracle_kind(wl),
+                                                                              cores_used())}
     print(json.dumps(line), flush=True)
     sol.close()
 
@@ -503,14 +631,15 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="sparse_n257_p768", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default="large_n2049_p6144", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision record")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.steps_given = args.steps is not None
     if args.steps is None:
-        args.steps = 100
+        args.steps = 100 if inputs.WORKLOADS[args.workload]["n_r"] < 1025 else 20
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
