@@ -225,10 +225,10 @@ class SlabSolver:
             return 1
 
     def state(self):
-        """This rank's modes of (theta, Psi, u_bar); u_bar only on the rank of m = 0."""
-        th, ps, u = self.solver.get_state()
+        """This rank's modes of (Psi, theta, u_bar); u_bar only on the rank of m = 0."""
+        ps, th, u = self.solver.get_state()
         m0, m1 = self.plan.m_range
-        return th[m0:m1], ps[m0:m1], (u if m0 == 0 else None)
+        return ps[m0:m1], th[m0:m1], (u if m0 == 0 else None)
 
     def close(self):
         from . import binding as B

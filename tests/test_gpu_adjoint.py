@@ -120,6 +120,46 @@ def test_adjoint_gradient_matches_finite_differences_n257():
     assert abs(fdR - float(r.grad)) <= 1e-4 * abs(float(r.grad))
 
 
+def test_adjoint_workload_400_steps_checkpoint_20():
+    """The adjoint workload as specified: 400 CNAB2 steps at n_r = 257,
+    n_phi = 768, E = 1e-5, Pr = 1, Ra = 5 Ra_c, dt = 1e-7, checkpoints every 20
+    steps, seeded initial perturbation 1e-3 (seed 5): dJ/dtheta_0 along a seeded
+    direction against central finite differences with h = 1e-6 relative to
+    |theta_0|, and dJ/dRa with h = 1e-3 relative to Ra: J depends on Ra only
+    weakly here (Ra dJ/dRa ~ 2e-3 J), so at h = 1e-6 the difference J(Ra + h) -
+    J(Ra - h) is ~4e-9 J, a few thousand ulps of J, and the rounding differences
+    of two separate 400-step runs are a visible fraction of it (measured: 4e-3
+    off at h = 1e-6); at h = 1e-3 they are not, and the central difference's
+    O(h^2) error stays far below the bar."""
+    from paper_1902_07092_gb300.autograd import NusseltAverage
+    import torch
+    wl = inputs.WORKLOADS["adjoint_n257_p768"]
+    E = wl["E"]
+    Ra = wl["ra_factor"] * critical_rayleigh(E)
+    cfg = dict(n_r=wl["n_r"], n_phi=wl["n_phi"], E=E, Pr=1.0, radius_ratio=0.35, dt=wl["dt"], steps=wl["steps"],
+               checkpoint_every=wl["checkpoint_every"])
+    th0 = inputs.theta_init(wl["n_r"], wl["n_phi"], wl["amp"], wl["seed"], cfg=wl["cfg"], m_min=0)
+    t = torch.tensor(th0, requires_grad=True)
+    r = torch.tensor(Ra, dtype=torch.float64, requires_grad=True)
+    J = NusseltAverage.apply(t, r, cfg)
+    J.backward()
+    d = inputs.theta_init(wl["n_r"], wl["n_phi"], 1.0, 55, cfg=5, m_min=0)
+    h = 1e-6 * np.linalg.norm(th0) / np.linalg.norm(d)
+    with torch.no_grad():
+        Jp = float(NusseltAverage.apply(torch.tensor(th0 + h * d), r, cfg))
+        Jm = float(NusseltAverage.apply(torch.tensor(th0 - h * d), r, cfg))
+        JRp = float(NusseltAverage.apply(torch.tensor(th0), torch.tensor(Ra * (1 + 1e-3)), cfg))
+        JRm = float(NusseltAverage.apply(torch.tensor(th0), torch.tensor(Ra * (1 - 1e-3)), cfg))
+    fd = (Jp - Jm) / (2 * h)
+    ad = float(np.real(np.vdot(t.grad.numpy(), d)))
+    fdR = (JRp - JRm) / (2e-3 * Ra)
+    print("400-step adjoint: J %.12e  theta: fd %.12e adjoint %.12e (rel %.2e)  Ra: fd %.12e adjoint %.12e "
+          "(rel %.2e)" % (float(J.detach()), fd, ad, abs(fd - ad) / abs(ad), fdR, float(r.grad),
+                          abs(fdR - float(r.grad)) / abs(float(r.grad))))
+    assert abs(fd - ad) <= 1e-5 * abs(ad)
+    assert abs(fdR - float(r.grad)) <= 1e-4 * abs(float(r.grad))
+
+
 @pytest.mark.parametrize("dd", [1, 0])
 def test_adjoint_run_matches_oracle_n257(dd):
     """Three CNAB2 steps on the adjoint workload's grid (257, 768), E = 1e-5,

@@ -126,3 +126,45 @@ def test_option_change_forces_a_new_graph():
     assert not all(np.array_equal(x, y) for x, y in zip(got, fp64))
     a.close()
     ref.close()
+
+
+def test_batch64_members_in_the_graph_match_the_oracle():
+    """Four members of the 64-run batched workload -- the first run of each n_r,
+    and run 8, the n_r = 513 run with the smallest E (1.04e-6, where the
+    streamfunction solve leans on its refinement most) -- stepped twice inside
+    one batch graph, each against the oracle's banded Appendix A stepper.  Bars
+    as the single-run tests: 1e-12 (n_r <= 129), 2e-12 (257), 5e-12 (513; the
+    streamfunction systems' effective condition grows with N_c)."""
+    from oracle.banded import BandedIntegrationStepper
+    from paper_1902_07092_gb300.binding import Batch, Solver
+    from tests.parity_util import assert_state_close, critical_rayleigh_interp
+    runs = inputs.batch_runs(64)
+    pick = {}
+    for i, r in enumerate(runs):
+        pick.setdefault(r["n_r"], i)
+    idx = sorted(set(pick.values()) | {8})
+    assert runs[8]["n_r"] == 513 and runs[8]["E"] == min(r["E"] for r in runs)
+    sols, oras = [], []
+    for i in idx:
+        r = runs[i]
+        Ra = r["ra_factor"] * critical_rayleigh_interp(r["E"])
+        s = Solver(r["n_r"], r["n_phi"], r["E"], Ra, r["Pr"], r["eta"], r["scheme"], r["dt"])
+        o = BandedIntegrationStepper(r["n_r"], r["n_phi"], r["E"], Ra, r["Pr"], r["eta"], r["scheme"], r["dt"])
+        th = inputs.theta_init(r["n_r"], r["n_phi"], r["amp"], r["seed"], cfg=r["cfg"])
+        z, zu = inputs.zero_state(r["n_r"], r["n_phi"])
+        s.set_state(th, z, zu)
+        o.set_state(z, th, zu)
+        sols.append(s)
+        oras.append(o)
+    batch = Batch(sols)
+    batch.step(2)
+    tol = {65: 1e-12, 129: 1e-12, 257: 2e-12, 513: 5e-12}
+    for i, s, o in zip(idx, sols, oras):
+        o.step()
+        o.step()
+        e = assert_state_close(s.get_state(), o.y, tol[runs[i]["n_r"]], oracle=o)
+        print("batch64 run %d (n_r %d, n_phi %d, E %.3g): state %.2e psi %.2e theta %.2e u %.2e" % (
+            i, runs[i]["n_r"], runs[i]["n_phi"], runs[i]["E"], e["state"], e["psi"], e["theta"], e["u"]))
+    batch.close()
+    for s in sols:
+        s.close()
