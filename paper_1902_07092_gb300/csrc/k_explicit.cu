@@ -820,6 +820,276 @@ size_t smem_grid_to_spec(const StepParams& P) { return smem_spec_to_grid(P); }
 
 // The explicit stage runs on double2 (FP64) or float2 (option "precision" =
 // mixed) grid arrays; G1, G2 hold either type.
+// ---------------------------------------------------------------------------
+// Large radial grids in FP64 (K = n_r - 1 >= LEAN_K, the half-length DCT-I):
+// a1 and a3 with three shared arrays of K + 1 entries, X, C, Y (98 KB at
+// n_r = 2049), instead of the batched layout's 2 x 2K + 3 n_r entries (229 KB),
+// so that two CTAs share an SM and hide each other's barrier and shared-memory
+// latency (one CTA left the FP64 pipe ~50 % idle).  The fields of a mode go
+// through the transform one after another; the derivative scans run in place on
+// C with X as scratch; the DCT-I works in place on the pair (X, Y).  The same
+// equations, in the same precision, as k_spec_to_grid / k_grid_to_spec.
+// ---------------------------------------------------------------------------
+constexpr int LEAN_K = 1024;
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+__host__ __device__ inline bool lean_radial(const StepParams& P) {
+    return !P.fp32 && P.K >= LEAN_K && P.plan_h.L == P.K;
+}
+
+// DCT-I of x_0..x_K in X (K + 1 entries):
+//   C_k = x_0 + (-1)^k x_K + 2 sum_{j=1}^{K-1} x_j cos(pi j k / K),  k = 0..K,
+// by one complex FFT of length K, as dct1_batched: y_j = (x_j + x_{K-j})/2
+// - sin(pi j/K)(x_j - x_{K-j}) formed in place pair by pair (j, K - j),
+// F = FFT(y), C_{2k} = F_k + F_{K-k}, and the odd outputs from
+// C_1 = sum_j (x_j - x_{K-j}) cos(pi j/K) by C_{2k+1} = C_{2k-1} - i(F_k - F_{K-k}),
+// the prefix sum taken by the whole CTA in FP64.  The FFT ping-pongs between X
+// and Y; the outputs go to the buffer that does not hold F, which is returned.
+// Starts and ends with __syncthreads().
+__device__ double2* dct1_pair(double2* X, double2* Y, const StepParams& P) {
+    const int K = P.plan_h.L, H = K / 2;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+    const double2* tw = P.plan_r.tw;  // tw[j] = (cos(pi j/K), -sin(pi j/K))
+    __shared__ double2 wsum[NTHREADS_R / 32];
+    __shared__ double2 c1;
+    __syncthreads();
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = tid; j < H; j += nth) {
+        if (j == 0) {
+            const double2 a = X[0], b = X[K];
+            X[0] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y + b.y));
+            acc = csub(a, b);
+        } else {
+            const double2 a = X[j], b = X[K - j];
+            const double sn = -tw[j].y, cs = tw[j].x;
+            const double2 sum = cadd(a, b), dif = csub(a, b);
+            X[j] = make_double2(fma(-sn, dif.x, 0.5 * sum.x), fma(-sn, dif.y, 0.5 * sum.y));
+            X[K - j] = make_double2(fma(sn, dif.x, 0.5 * sum.x), fma(sn, dif.y, 0.5 * sum.y));
+            acc.x = fma(2.0 * cs, dif.x, acc.x);
+            acc.y = fma(2.0 * cs, dif.y, acc.y);
+        }
+    }
+    // (j = H: y_H = x_H, and its term of C_1 vanishes)
+    acc = warp_sum(acc);
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double2 t = wsum[0];
+        for (int w = 1; w < nw; ++w) t = cadd(t, wsum[w]);
+        c1 = t;
+    }
+    double2* F = fft_batched<+1>(X, Y, P.plan_h, 1);  // begins with a barrier
+    double2* O = (F == X) ? Y : X;
+    for (int k = tid; k <= H; k += nth) O[2 * k] = cadd(F[k], F[k == 0 ? 0 : K - k]);
+    // odd outputs: each thread a contiguous chunk of k in [0, H), its sum of
+    // d_k = -i (F_k - F_{K-k}) (d_0 = 0), a block-wide exclusive scan, then the chunk
+    const int chunk = (H + nth - 1) / nth;
+    const int lo = min(tid * chunk, H), hi = min(lo + chunk, H);
+    double2 tot = make_double2(0.0, 0.0);
+    for (int k = max(lo, 1); k < hi; ++k) {
+        const double2 df = csub(F[k], F[K - k]);
+        tot.x += df.y;
+        tot.y -= df.x;
+    }
+    double2 inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double ux = __shfl_up_sync(0xffffffffu, inc.x, o);
+        const double uy = __shfl_up_sync(0xffffffffu, inc.y, o);
+        if (lane >= o) {
+            inc.x += ux;
+            inc.y += uy;
+        }
+    }
+    __syncthreads();  // c1 and the even outputs are published; wsum is free again
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    double2 run = c1;
+    for (int w = 0; w < warp; ++w) run = cadd(run, wsum[w]);
+    run.x += inc.x - tot.x;
+    run.y += inc.y - tot.y;
+    for (int k = lo; k < hi; ++k) {
+        if (k > 0) {
+            const double2 df = csub(F[k], F[K - k]);
+            run.x += df.y;
+            run.y -= df.x;
+        }
+        O[2 * k + 1] = run;
+    }
+    __syncthreads();
+    return O;
+}
+
+__global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean(StepParams P, VecSet y, double2* __restrict__ G1) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int m = P.m_lo + blockIdx.x;
+    const int K = P.K, N = P.n_r, nc = P.nc, M = P.M;
+    double2* X = reinterpret_cast<double2*>(smraw);
+    double2* C = X + N;   // plain coefficients (Psi, then its derivatives; u_bar)
+    double2* Y = C + N;   // second DCT buffer (u_bar' for m = 0)
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const double Cw = P.cnorm, Cw0 = 0.5 * P.cnorm, dm = (double)m;
+
+    for (int n = tid; n < N; n += nth) {
+        double2 a = make_double2(0.0, 0.0);
+        if (n < nc) {
+            const double w = (n == 0) ? Cw0 : Cw;
+            a = (m > 0) ? cscale(y.psi[(size_t)m * nc + n], w) : make_double2(y.u[n] * w, 0.0);
+        }
+        C[n] = a;
+    }
+    __syncthreads();
+    double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
+    __shared__ double red[4 * 32], mx[4];
+    double lam = 1.0;
+    if (m == 0) {  // u_bar and lam u_bar' packed into one transform (lam a power of two)
+        cheb_derivative_scan(C, Y, X, N, P.inv_a);
+        block_max_abs(C, N, 2, N, mx, red);
+        lam = pow2_ratio(mx[0], mx[1]);
+    }
+    // fields: 0 Psi, 1 Psi', 2 Psi'', 3 theta (m >= 1); 4 packed u_bar, 3 theta (m = 0)
+    const int nf = (m > 0) ? 4 : 2;
+    for (int i = 0; i < nf; ++i) {
+        const int fid = (m > 0) ? i : (i == 0 ? 4 : 3);
+        if (m > 0 && (fid == 1 || fid == 2)) cheb_derivative_scan(C, C, X, N, P.inv_a);  // C <- dC/ds
+        for (int j = tid; j <= K; j += nth) {
+            double2 v;
+            if (fid <= 2)
+                v = C[j];
+            else if (fid == 3)
+                v = (j < nc) ? cscale(y.th[(size_t)m * nc + j], (j == 0) ? Cw0 : Cw) : make_double2(0.0, 0.0);
+            else
+                v = make_double2(C[j].x, lam * Y[j].x);
+            X[j] = (j == 0 || j == K) ? cscale(v, 2.0) : v;
+        }
+        double2* Z = dct1_pair(X, Y, P);
+        for (int k = tid; k < N; k += nth) {
+            const double2 g = cscale(Z[k], 0.5);  // value of the series at x_k
+            const double s = P.s[k], h2 = P.h2[k], is = P.inv_s[k];
+            double2* out = G1 + g_index(k, 0, m, M);
+            if (fid == 0) {
+                out[0] = cmul_i(g, dm);
+                out[M] = cscale(g, 3.0 * s);
+                out[2 * M] = cscale(g, 6.0 + dm * dm * h2 * is * is);
+                if (PF) {
+                    const double U = P.pump_ups[k];
+                    PF[k] = cadd(cscale(g, -U * (P.pump_cr[k] + dm * dm)), cmul_i(g, -U * dm * P.pump_ci[k]));
+                }
+            } else if (fid == 1) {
+                out[M] = csub(out[M], cscale(g, h2));
+                out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - 5.0 * s));
+                if (PF) PF[k] = cadd(PF[k], cscale(g, P.pump_ups[k] * 0.5 * s));
+            } else if (fid == 2) {
+                out[2 * M] = csub(out[2 * M], cscale(g, h2));
+                if (PF) PF[k] = csub(PF[k], cscale(out[2 * M], P.pump_ups[k]));
+            } else if (fid == 3) {
+                out[3 * M] = g;
+            } else {
+                out[0] = make_double2(0.0, 0.0);
+                out[M] = make_double2(g.x, 0.0);
+                out[2 * M] = make_double2(g.y / lam + g.x * is, 0.0);
+                if (PF) {
+                    const double w0 = g.y / lam + g.x * is;
+                    PF[k] = make_double2(P.pump_ups[k] * g.x * (1.0 + 0.5 * P.E * w0), 0.0);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean(StepParams P, const double2* __restrict__ G2,
+                                                                      VecSet y, VecSet e) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int m = P.m_lo + blockIdx.x;
+    const int K = P.K, N = P.n_r, nc = P.nc, M = P.M;
+    double2* X = reinterpret_cast<double2*>(smraw);
+    double2* C = X + N;
+    double2* Y = C + N;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const double dm = (double)m, iK = 1.0 / (double)K, hK = 0.5 / (double)K, hc = 0.5 * P.cnorm;
+    const double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
+    const double bfac = P.Ra / P.Pr * (double)m / P.s_o;
+    // field 0: N_omega (m >= 1) or N_u (m = 0); field 1: N_theta
+    for (int fld = 0; fld < 2; ++fld) {
+        double2* W = X;  // the buffer holding the grid values to analyse
+        if (fld == 1 || m > 0) {
+            // plain coefficients of F = h^2 [v omega]_m (or h^2 [v theta]_m), d/ds of them
+            const int f = (fld == 0) ? 0 : 2;
+            for (int j = tid; j <= K; j += nth) X[j] = cscale(G2[g_index(j, f, m, M)], P.h2[j]);
+            const double2* Z = dct1_pair(X, Y, P);
+            for (int n = tid; n <= K; n += nth) C[n] = cscale(Z[n], (n == 0 || n == K) ? hK : iK);
+            __syncthreads();
+            cheb_derivative_scan(C, C, X, N, P.inv_a);
+            for (int j = tid; j <= K; j += nth) X[j] = (j == 0 || j == K) ? cscale(C[j], 2.0) : C[j];
+            const double2* D = dct1_pair(X, Y, P);
+            W = (D == X) ? Y : X;
+            for (int k = tid; k <= K; k += nth) {
+                const double2 dF = cscale(D[k], 0.5);
+                const double is = P.inv_s[k];
+                double2 val;
+                if (fld == 0) {
+                    val = cscale(cadd(dF, cmul_i(G2[g_index(k, 1, m, M)], dm)), is);
+                    if (PF) val = csub(val, PF[k]);
+                } else {
+                    val = csub(cscale(cadd(dF, cmul_i(G2[g_index(k, 3, m, M)], dm)), is), G2[g_index(k, 2, m, M)]);
+                }
+                W[k] = val;
+            }
+        } else {  // N_u = (h^2/s) [v omega]_0 (+ pumping)
+            for (int k = tid; k <= K; k += nth) {
+                double2 val = cscale(G2[g_index(k, 0, m, M)], P.h2[k] * P.inv_s[k]);
+                if (PF) val = cadd(val, PF[k]);
+                W[k] = val;
+            }
+        }
+        // Eq. icheb of the grid values, truncated to n < nc
+        const double2* Z = dct1_pair(W, (W == X) ? Y : X, P);
+        for (int n = tid; n < nc; n += nth) C[n] = cscale(Z[n], hc);
+        __syncthreads();
+        // integrated right-hand sides; the linear couplings read the FP64 state
+        for (int k = tid; k < nc; k += nth) {
+            if (fld == 0) {
+                if (m > 0) {
+                    double2 ep = make_double2(0.0, 0.0);
+                    if (k >= 4) {
+                        ep = band_row<8>(P.ops.band[OP_C], C, k, nc);
+                        if (!P.buoy_imp)
+                            ep = cadd(ep, cmul_i(band_row<8>(P.ops.band[OP_C], y.th + (size_t)m * nc, k, nc), bfac));
+                    }
+                    e.psi[(size_t)m * nc + k] = ep;
+                } else {
+                    e.psi[k] = make_double2(0.0, 0.0);
+                    e.u[k] = (k >= 2) ? -band_row<4>(P.ops.band[OP_D], C, k, nc).x : 0.0;
+                }
+            } else {
+                double2 et = make_double2(0.0, 0.0);
+                if (k >= 2) {
+                    const double2 dn = band_row<4>(P.ops.band[OP_D], C, k, nc);
+                    if (m > 0) {
+                        const double2 gp = band_row<4>(P.ops.band[OP_G], y.psi + (size_t)m * nc, k, nc);
+                        et = csub(cmul_i(gp, -P.tc * dm), dn);
+                    } else {
+                        et = cscale(dn, -1.0);
+                    }
+                }
+                e.th[(size_t)m * nc + k] = et;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t smem_radial_lean(const StepParams& P) { return sizeof(double2) * 3 * (size_t)P.n_r; }
+
 template <class T>
 static cudaError_t spec_to_grid_t(const StepParams& P, VecSet y, void* G1, cudaStream_t st) {
     const size_t sm = smem_spec_to_grid(P);
@@ -862,6 +1132,13 @@ static cudaError_t grid_to_spec_t(const StepParams& P, const void* G2, VecSet y,
 }
 
 cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st) {
+    if (lean_radial(P)) {
+        const size_t sm = smem_radial_lean(P);
+        cudaError_t err = cudaFuncSetAttribute(k_spec_to_grid_lean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_spec_to_grid_lean<<<slab_modes(P), NTHREADS_R, sm, st>>>(P, y, G1);
+        return cudaGetLastError();
+    }
     return P.fp32 ? spec_to_grid_t<float2>(P, y, G1, st) : spec_to_grid_t<double2>(P, y, G1, st);
 }
 
@@ -884,6 +1161,13 @@ cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2*
 }
 
 cudaError_t launch_grid_to_spec(const StepParams& P, const double2* G2, VecSet y, VecSet e, cudaStream_t st) {
+    if (lean_radial(P)) {
+        const size_t sm = smem_radial_lean(P);
+        cudaError_t err = cudaFuncSetAttribute(k_grid_to_spec_lean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_grid_to_spec_lean<<<slab_modes(P), NTHREADS_R, sm, st>>>(P, G2, y, e);
+        return cudaGetLastError();
+    }
     return P.fp32 ? grid_to_spec_t<float2>(P, G2, y, e, st) : grid_to_spec_t<double2>(P, G2, y, e, st);
 }
 
