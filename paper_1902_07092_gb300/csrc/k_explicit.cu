@@ -83,8 +83,11 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
     if (m > 0) cheb_derivative_scan(cc1, cc2, bufA, N, P.inv_a);
 
     // field list: 0 Psi, 1 Psi', 2 Psi'', 3 theta, 4 packed u_bar + i lam u_bar'
-    // (lam a power of two balancing the two parts)
-    __shared__ double red[4 * 32], mx[4];
+    // (lam a power of two balancing the two parts).  The reduction scratch lives
+    // in bufB, unused until the first transform: without static shared memory two
+    // FP32 CTAs fit an SM at n_r = 2049.
+    double* red = reinterpret_cast<double*>(bufB);
+    double* mx = red + 4 * 32;
     RT lam = 1;
     if (m == 0) {
         block_max_abs(cc0, N, 2, N, mx, red);

@@ -544,14 +544,17 @@ struct SolveSmem {
 
 __host__ __device__ inline int round8(int n) { return (n + 7) / 8 * 8; }
 
-__host__ __device__ inline size_t solve_smem_doubles(int nc, int MB) {
+// DEEP (the FP32-refined temperature solve): the FP64 temperature chain scratch
+// tw is not used, so it is left out (at N_c = 1365 this lets the epilogue keep
+// the assembled right-hand sides in shared memory)
+__host__ __device__ inline size_t solve_smem_doubles(int nc, int MB, bool deep = false) {
     const int b = round8(nc);
-    return (size_t)MB * 2 * 7 * b + 2 * (size_t)b + 3 * (size_t)b;  // last: 3 b float2
+    return (size_t)MB * 2 * (deep ? 6 : 7) * b + 2 * (size_t)b + 3 * (size_t)b;  // last: 3 b float2
 }
 
 __host__ __device__ inline size_t keep_f_doubles(int nc) { return 3 * (size_t)round8(nc); }
 
-template <int MB>
+template <int MB, bool DEEP = false>
 __device__ SolveSmem carve(double2* base, int nc) {
     SolveSmem s;
     const int b = round8(nc);
@@ -562,7 +565,11 @@ __device__ SolveSmem carve(double2* base, int nc) {
         s.px[i] = p; p += b;
         s.pd[i] = p; p += b;
         s.tf[i] = p; p += b;
-        s.tw[i] = p; p += b;
+        if (DEEP) {
+            s.tw[i] = nullptr;
+        } else {
+            s.tw[i] = p; p += b;
+        }
         s.tx[i] = p; p += b;
     }
     double* d = reinterpret_cast<double*>(p);
@@ -708,7 +715,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     const int np = nc - 4, nt = nc - 2;
     const int nbp = (np + 7) / 8, nbt = (nt + 7) / 8;
     const int nA = 8 * (nbp / 2);  // first half of a split streamfunction block (F.psplit)
-    SolveSmem s = carve<MB>(sm, nc);
+    SolveSmem s = carve<MB, DEEP>(sm, nc);
     const bool has_u = (m0 == 0);
     constexpr int PP = DEEP ? PFB_DEEP_P : PFB, PT = DEEP ? PFB_DEEP_T : PFB;
 
@@ -1205,14 +1212,16 @@ __global__ void k_check_finite(VecSet y, size_t n2, int nu, int* __restrict__ fl
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
-size_t smem_solve_mb(const StepParams& P, int MB) { return sizeof(double) * solve_smem_doubles(P.nc, MB); }
+size_t smem_solve_mb(const StepParams& P, int MB, bool deep = false) {
+    return sizeof(double) * solve_smem_doubles(P.nc, MB, deep);
+}
 
 }  // namespace
 
 
 cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFactors& F, VecSet y_out,
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st) {
-    const size_t sm = smem_solve_mb(P, 1);
+    const size_t sm = smem_solve_mb(P, 1, F.ir_t > 0);
     if (F.gal) {
         // the FP64 solve arrays (16 round8(nc) doubles), the staging of the factors
         // (double2 x 2 GCH x 21, double x 2 GCH x 12 twice) and 3 pivot rows
