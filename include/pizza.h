@@ -140,6 +140,10 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            dt > alpha / max(rate) for a state evaluated since the previous
  *            pizza_synchronize, then clears the maxima.  0 (default) = off;
  *            negative: PIZZA_EINVAL;
+ *   "solve_roles" 1 (default) = from N_c > 600 with explicit buoyancy the
+ *            implicit solve runs one CTA per system (streamfunction; temperature
+ *            and zonal flow) instead of one per mode, two CTAs per SM; 0 = one
+ *            CTA per mode.  The same arithmetic either way;
  *   "radial_batch" radial transforms batched per shared-memory pass in the
  *            per-mode explicit kernels: 1, 2 or 4, 0 = the default rule (up to
  *            n_r = 513: 4 in FP64, 2 in mixed precision; else 1); "phi_threads" threads of the per-radius azimuthal

@@ -949,6 +949,248 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
 }
 
 // ---------------------------------------------------------------------------
+// The same solve split by system over two CTAs per mode (large N_c, FP32-refined
+// temperature, explicit buoyancy): role 0 the streamfunction system, role 1 the
+// temperature system (and, for m = 0, the zonal flow after it).  The systems are
+// independent when the buoyancy is explicit; each role holds only its own arrays
+// in shared memory (at N_c = 1365: 109 KB and 98 KB instead of 219 KB) and the
+// kernel is capped at 128 registers, so two CTAs share an SM and one's block
+// chains overlap the other's residual, Schur and epilogue phases.  Interleaved
+// roles (block 2m + role) give every SM a mix.  The same arithmetic as k_solve
+// with fuse_t = 0; chain prefetch depth 2.
+// ---------------------------------------------------------------------------
+__device__ void epilogue_row_psi(const StepParams& P, const RhsSpec& R, double gdt, int m, int k, const double2* xp,
+                                 VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp,
+                                 const double2* fps) {
+    const int nc = P.nc;
+    const double mu = (double)m * m;
+    double2 mp = make_double2(0.0, 0.0);
+    if (m > 0 && k >= 4) {
+        const double2 a0 = band_row_c<8>(P.ops.band[OP_A0], xp, k, nc);
+        const double2 a2 = band_row_c<8>(P.ops.band[OP_A2], xp, k, nc);
+        mp = make_double2(fma(mu, a2.x, a0.x), fma(mu, a2.y, a0.y));
+    }
+    const size_t idx = (size_t)m * nc + k;
+    if (want_imp) {  // before any store: an output may be one of the terms of f
+        const double2 fp = fps[k];
+        imp_out.psi[idx] = (m > 0 && k >= 4) ? cscale(csub(mp, fp), 1.0 / gdt) : make_double2(0.0, 0.0);
+    }
+    if (want_mass) mass_out.psi[idx] = mp;
+}
+
+__device__ void epilogue_row_theta(const StepParams& P, const RhsSpec& R, double gdt, int m, int k, const double2* xt,
+                                   const double* xu, VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp,
+                                   const double2* fts) {
+    const int nc = P.nc;
+    double2 mt = make_double2(0.0, 0.0);
+    double muu = 0.0;
+    if (k >= 2) {
+        mt = band_row_c<4>(P.ops.band[OP_D], xt, k, nc);
+        if (m == 0) {
+            const double* rd = P.ops.band[OP_D] + (size_t)k * 9;
+            for (int d = 0; d < 9; ++d) {
+                const int n = k - 4 + d;
+                if (n >= 0 && n < nc) muu = fma(__ldg(&rd[d]), xu[n], muu);
+            }
+        }
+    }
+    const size_t idx = (size_t)m * nc + k;
+    if (want_imp) {  // before any store: an output may be one of the terms of f
+        const double2 ft = fts[k];
+        double fu = 0.0;
+        if (m == 0)
+            for (int t = 0; t < R.nterms; ++t) fu = fma(R.t[t].c, R.t[t].v.u[k], fu);
+        const double ig = 1.0 / gdt;
+        imp_out.th[idx] = (k >= 2) ? cscale(csub(mt, ft), ig) : make_double2(0.0, 0.0);
+        if (m == 0) imp_out.u[k] = (k >= 2) ? (muu - fu) * ig : 0.0;
+    }
+    if (want_mass) {
+        mass_out.th[idx] = mt;
+        if (m == 0) mass_out.u[k] = muu;
+    }
+}
+
+__host__ __device__ inline size_t solve_roles_smem_doubles(int nc) {
+    const int b = round8(nc);
+    // role 0: pf, pw, px, pd, fp (double2); role 1: tf, tx (double2), tr, tq, td
+    // (float2), uf, ux (double) -- the larger of the two
+    return (size_t)2 * b * 5 > (size_t)2 * b * 2 + 3 * b + 2 * b ? (size_t)2 * b * 5 : (size_t)2 * b * 2 + 5 * b;
+}
+
+__global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, RhsSpec R, DevFactors F, VecSet y_out,
+                                                                VecSet mass_out, VecSet imp_out, int want_mass,
+                                                                int want_imp) {
+    extern __shared__ double2 sm[];
+    const int nc = P.nc;
+    const int m = P.m_lo + (int)(blockIdx.x >> 1), role = blockIdx.x & 1;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
+    const int np = nc - 4, nt = nc - 2;
+    const int nbp = (np + 7) / 8;
+    const int nA = 8 * (nbp / 2);
+    const int b = round8(nc);
+    SolveSmem s{};
+    if (role == 0) {
+        // ---------------------------------------------------- streamfunction
+        s.pf[0] = sm;
+        s.pw[0] = sm + b;
+        s.px[0] = sm + 2 * b;
+        s.pd[0] = sm + 3 * b;
+        s.fp = sm + 4 * b;
+        if (m == 0) {  // Psi_0 = 0
+            for (int n = tid; n < nc; n += nth) {
+                y_out.psi[n] = make_double2(0.0, 0.0);
+                if (want_mass) mass_out.psi[n] = make_double2(0.0, 0.0);
+                if (want_imp) imp_out.psi[n] = make_double2(0.0, 0.0);
+            }
+            return;
+        }
+        for (int n = tid; n < nc; n += nth) {
+            double2 ap = make_double2(0.0, 0.0);
+#pragma unroll 4
+            for (int t = 0; t < R.nterms; ++t) {
+                const double c = R.t[t].c;
+                const double2 vp = R.t[t].v.psi[(size_t)m * nc + n];
+                ap.x = fma(c, vp.x, ap.x);
+                ap.y = fma(c, vp.y, ap.y);
+            }
+            s.pf[0][n] = (n < 4) ? make_double2(0.0, 0.0) : ap;
+            s.fp[n] = s.pf[0][n];
+        }
+        __syncthreads();
+        const double2* blk = F.pBlk + (size_t)m * nbp * 192;
+        for (int it = 0; it < 2; ++it) {  // solve, then one refinement step
+            double2* x = it ? s.pd[0] : s.px[0];
+            if (warp < 2)
+                pair_block_solve<8, PFB>(s.pf[0] + 4, s.pw[0], x + 4, F.psplit ? nA : np, blk, true, warp, 1);
+            else if (warp >= 6 && F.psplit)
+                pair_block_solve<8, PFB>(s.pf[0] + 4 + nA, s.pw[0] + nA, x + 4 + nA, np - nA, blk + (size_t)(nbp / 2) * 192,
+                                         true, warp - 6, 4);
+            __syncthreads();
+            if (F.psplit)
+                split_join(x + 4, np, nA, F.pSpk + (size_t)m * np * 8, F.pRj + (size_t)m * 256, true);
+            if (warp == 0) warp_schur<4>(x, it ? s.pf[0] : nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
+            __syncthreads();
+            schur_update<4>(x, nc, F.pY + (size_t)m * np * 4, 0, nth);
+            __syncthreads();
+            if (it == 0) {
+                // residual r = f - L x over the assembled rows, and the tau rows
+                for (int k = 4 + tid; k < nc; k += nth) {
+                    const double2* row = F.pBand + ((size_t)m * np + (k - 4)) * 17;
+                    double2 acc = s.pf[0][k];
+#pragma unroll
+                    for (int d = 0; d < 17; ++d) {
+                        const int n = k - 8 + d;
+                        if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), s.px[0][n]);
+                    }
+                    s.pf[0][k] = acc;
+                }
+                if (warp == 0) {
+                    double2 t[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) t[r] = make_double2(0.0, 0.0);
+                    for (int j = lane; j < nc; j += 32) {
+                        const double2 xv = s.px[0][j];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const double bb = __ldg(&P.ops.tau_psi[(size_t)r * nc + j]);
+                            t[r].x = fma(bb, xv.x, t[r].x);
+                            t[r].y = fma(bb, xv.y, t[r].y);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) t[r] = warp_sum(t[r]);
+                    if (lane < 4) s.pf[0][lane] = csub(s.pf[0][lane], t[lane]);
+                }
+                __syncthreads();
+            }
+        }
+        for (int n = tid; n < nc; n += nth) s.px[0][n] = cadd(s.px[0][n], s.pd[0][n]);
+        __syncthreads();
+        for (int n = tid; n < nc; n += nth) {
+            y_out.psi[(size_t)m * nc + n] = s.px[0][n];
+            if (want_mass || want_imp)
+                epilogue_row_psi(P, R, F.gdt, m, n, s.px[0], mass_out, imp_out, want_mass, want_imp, s.fp);
+        }
+        return;
+    }
+    // ------------------------------------------- temperature (and zonal flow)
+    s.tf[0] = sm;
+    s.tx[0] = sm + b;
+    float2* f32 = reinterpret_cast<float2*>(sm + 2 * b);
+    s.tr = f32;
+    s.tq = f32 + b;
+    s.td = f32 + 2 * b;
+    double* d64 = reinterpret_cast<double*>(f32 + 3 * b);
+    s.uf = d64;
+    s.ux = d64 + b;
+    const int nbt = (nt + 7) / 8;
+    for (int n = tid; n < nc; n += nth) {
+        double2 at = make_double2(0.0, 0.0);
+        double au = 0.0;
+#pragma unroll 4
+        for (int t = 0; t < R.nterms; ++t) {
+            const double c = R.t[t].c;
+            const double2 vt = R.t[t].v.th[(size_t)m * nc + n];
+            at.x = fma(c, vt.x, at.x);
+            at.y = fma(c, vt.y, at.y);
+            if (m == 0) au = fma(c, R.t[t].v.u[n], au);
+        }
+        s.tf[0][n] = (n < 2) ? make_double2(0.0, 0.0) : at;
+        s.tr[n] = to_f2(s.tf[0][n]);
+        if (m == 0) s.uf[n] = (n < 2) ? 0.0 : au;
+    }
+    __syncthreads();
+    if (warp == 2 || warp == 3)
+        pair_block_solve<8, PFB>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192, true, warp - 2, 2);
+    __syncthreads();
+    if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
+    __syncthreads();
+    schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, 0, nth);
+    __syncthreads();
+    for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
+    __syncthreads();
+    temperature_corrections<1, false>(P, F, s, m, false, 0);
+    if (m == 0) {
+        // the zonal flow after the temperature, in its freed FP32 arrays (the
+        // same footprint in doubles): chain scratch in tq, correction in td, the
+        // refinement's chain scratch in tr
+        s.pd[0] = reinterpret_cast<double2*>(s.tq);
+        s.pw[0] = reinterpret_cast<double2*>(s.td);
+        s.pf[0] = reinterpret_cast<double2*>(s.tr);
+        if (warp == 4 || warp == 5)
+            pair_block_solve<8, PFB>(s.uf + 2, reinterpret_cast<double*>(s.pd[0]), s.ux + 2, nt, F.uBlk, true, warp - 4, 3);
+        __syncthreads();
+        if (warp == 4) {
+            double t0 = 0.0, t1 = 0.0;
+            for (int j = lane; j < nt; j += 32) {
+                t0 = fma(__ldg(&P.ops.tau_dir_B[j]), s.ux[2 + j], t0);
+                t1 = fma(__ldg(&P.ops.tau_dir_B[nt + j]), s.ux[2 + j], t1);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+                t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+            }
+            if (lane < 2) s.ux[lane] = -(F.uSinv[lane * 2] * t0 + F.uSinv[lane * 2 + 1] * t1);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const double u0 = s.ux[0], u1 = s.ux[1];
+            for (int j = tid; j < nt; j += nth) s.ux[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
+        }
+        __syncthreads();
+        refine_zonal_flow(P, F, s);
+    }
+    for (int n = tid; n < nc; n += nth) {
+        y_out.th[(size_t)m * nc + n] = s.tx[0][n];
+        if (m == 0) y_out.u[n] = s.ux[n];
+        if (want_mass || want_imp)
+            epilogue_row_theta(P, R, F.gdt, m, n, s.tx[0], s.ux, mass_out, imp_out, want_mass, want_imp, s.tf[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Galerkin-basis solve (Appendix B; option "radial" = 2).  Per mode the square
 // systems P_4 (A - g dt B) S_Psi x = P_4 r and P_2 (D - g dt F/Pr) S_D x = P_2 r
 // (and the zonal-flow one) are solved with their banded LU factors with partial
@@ -1233,8 +1475,17 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
                                                       want_imp ? 1 : 0);
         return cudaGetLastError();
     }
-    // the systems with FP32-refined temperature solves (N_c > 600) take the deep
-    // chain prefetch (one or two CTAs per SM by shared memory)
+    // the systems with FP32-refined temperature solves (N_c > 600): with explicit
+    // buoyancy one CTA per system (two per mode, two per SM), else the deep chain
+    // prefetch (one CTA per SM by shared memory)
+    if (F.ir_t && !P.buoy_imp && P.solve_roles) {
+        const size_t smr = sizeof(double) * solve_roles_smem_doubles(P.nc);
+        cudaError_t err = cudaFuncSetAttribute(k_solve_roles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        if (err != cudaSuccess) return err;
+        k_solve_roles<<<2 * slab_modes(P), NTHREADS_S, smr, st>>>(P, rhs, F, y_out, mass_out, imp_out,
+                                                                  want_mass ? 1 : 0, want_imp ? 1 : 0);
+        return cudaGetLastError();
+    }
     auto kern = F.ir_t ? k_solve<1, true> : k_solve<1, false>;
     // the epilogue reads the assembled right-hand sides from shared memory where
     // they fit (up to N_c ~ 1300), else sums the terms again

@@ -142,6 +142,9 @@ struct StepParams {
     // Courant guard (option "cfl_alpha", Eq. cfl): when cfl_max is set the
     // azimuthal kernel folds max |u_s|/ds_k and max |u_phi|/(s_k dphi) of the
     // synthesised state into cfl_max[0], cfl_max[1] (atomic maxima)
+    // large-N_c solve (FP32-refined temperature, explicit buoyancy) in one CTA
+    // per system (option "solve_roles", 1 = default) instead of one per mode
+    int solve_roles;
     double* cfl_max;
     const double* cfl_ds;  // [n_r] local Gauss-Lobatto spacing
     double cfl_dphi;       // 2 pi / n_phi
