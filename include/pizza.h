@@ -140,10 +140,16 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            dt > alpha / max(rate) for a state evaluated since the previous
  *            pizza_synchronize, then clears the maxima.  0 (default) = off;
  *            negative: PIZZA_EINVAL;
- *   "solve_roles" 1 (default) = from N_c > 600 with explicit buoyancy the
- *            implicit solve runs one CTA per system (streamfunction; temperature
- *            and zonal flow) instead of one per mode, two CTAs per SM; 0 = one
- *            CTA per mode.  The same arithmetic either way;
+ *   "radial_lean" the FP64 synthesis and analysis kernels in the layout of
+ *            three shared arrays of n_r values, the fields one after another (two
+ *            CTAs per SM at n_r = 2049) instead of the batched layout: 1 from
+ *            n_r = 129, 0 never, -1 (default) from n_r = 513.  Results agree to
+ *            rounding (the DCT-I sums in another order);
+ *   "solve_roles" with explicit buoyancy, the implicit solve in one CTA per
+ *            system (streamfunction; temperature, then the zonal flow for m = 0)
+ *            instead of one per mode: 1 always, 0 never, -1 (default) from
+ *            N_c > 600, where it fits two CTAs per SM.  The same arithmetic
+ *            either way (bitwise equal results);
  *   "radial_batch" radial transforms batched per shared-memory pass in the
  *            per-mode explicit kernels: 1, 2 or 4, 0 = the default rule (up to
  *            n_r = 513: 4 in FP64, 2 in mixed precision; else 1); "phi_threads" threads of the per-radius azimuthal

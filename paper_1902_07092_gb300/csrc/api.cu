@@ -1508,7 +1508,8 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         P.plan_p.twdd = dtw;
         P.phi_dd = 1;
     }
-    P.solve_roles = 1;
+    P.solve_roles = -1;
+    P.radial_lean = -1;
     // half-length radial plan: its twiddles exp(-2 pi i j/K) are plan_r's at stride 2
     if (!make_fft_plan(ctx->K, P.plan_h)) {
         ctx->err = "unsupported transform length";
@@ -1668,10 +1669,19 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
         ctx->P.phi_dd = (value == 1.0) ? 1 : 0;
         return PIZZA_OK;
     }
-    if (std::strcmp(key, "solve_roles") == 0) {
-        if (value != 0.0 && value != 1.0) return fail(ctx, PIZZA_EINVAL, "solve_roles must be 0 or 1");
+    if (std::strcmp(key, "radial_lean") == 0) {
+        if (value != 0.0 && value != 1.0 && value != -1.0)
+            return fail(ctx, PIZZA_EINVAL, "radial_lean must be -1 (by size), 0 or 1");
         cudaStreamSynchronize(ctx->stream);
-        ctx->P.solve_roles = (value == 1.0) ? 1 : 0;
+        ctx->P.radial_lean = (int)value;
+        ++ctx->epoch;
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "solve_roles") == 0) {
+        if (value != 0.0 && value != 1.0 && value != -1.0)
+            return fail(ctx, PIZZA_EINVAL, "solve_roles must be -1 (by size), 0 or 1");
+        cudaStreamSynchronize(ctx->stream);
+        ctx->P.solve_roles = (int)value;
         ++ctx->epoch;
         return PIZZA_OK;
     }

@@ -824,7 +824,8 @@ size_t smem_grid_to_spec(const StepParams& P) { return smem_spec_to_grid(P); }
 // The explicit stage runs on double2 (FP64) or float2 (option "precision" =
 // mixed) grid arrays; G1, G2 hold either type.
 // ---------------------------------------------------------------------------
-// Large radial grids in FP64 (K = n_r - 1 >= LEAN_K, the half-length DCT-I):
+// Large radial grids in FP64 (K = n_r - 1 >= LEAN_K, the half-length DCT-I;
+// measured faster than the batched layout from n_r = 513, slower at 257):
 // a1 and a3 with three shared arrays of K + 1 entries, X, C, Y (98 KB at
 // n_r = 2049), instead of the batched layout's 2 x 2K + 3 n_r entries (229 KB),
 // so that two CTAs share an SM and hide each other's barrier and shared-memory
@@ -833,7 +834,7 @@ size_t smem_grid_to_spec(const StepParams& P) { return smem_spec_to_grid(P); }
 // C with X as scratch; the DCT-I works in place on the pair (X, Y).  The same
 // equations, in the same precision, as k_spec_to_grid / k_grid_to_spec.
 // ---------------------------------------------------------------------------
-constexpr int LEAN_K = 1024;
+constexpr int LEAN_K = 512;
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
 #pragma unroll
@@ -845,7 +846,8 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
 }
 
 __host__ __device__ inline bool lean_radial(const StepParams& P) {
-    return !P.fp32 && P.K >= LEAN_K && P.plan_h.L == P.K;
+    if (P.fp32 || P.plan_h.L != P.K || P.K < 128 || P.radial_lean == 0) return false;
+    return P.radial_lean > 0 || P.K >= LEAN_K;
 }
 
 // DCT-I of x_0..x_K in X (K + 1 entries):

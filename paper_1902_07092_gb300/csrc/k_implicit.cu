@@ -1114,12 +1114,15 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
         return;
     }
     // ------------------------------------------- temperature (and zonal flow)
+    // FP32-refined (ir_t): tf, tx, then the FP32 tr, tq, td; otherwise FP64 blocks
+    // with tw as chain scratch in the place of tr
     s.tf[0] = sm;
     s.tx[0] = sm + b;
     float2* f32 = reinterpret_cast<float2*>(sm + 2 * b);
     s.tr = f32;
     s.tq = f32 + b;
     s.td = f32 + 2 * b;
+    s.tw[0] = reinterpret_cast<double2*>(f32);  // FP64 path: b double2 over tr and tq
     double* d64 = reinterpret_cast<double*>(f32 + 3 * b);
     s.uf = d64;
     s.ux = d64 + b;
@@ -1136,20 +1139,31 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
             if (m == 0) au = fma(c, R.t[t].v.u[n], au);
         }
         s.tf[0][n] = (n < 2) ? make_double2(0.0, 0.0) : at;
-        s.tr[n] = to_f2(s.tf[0][n]);
+        if (F.ir_t) s.tr[n] = to_f2(s.tf[0][n]);
         if (m == 0) s.uf[n] = (n < 2) ? 0.0 : au;
     }
     __syncthreads();
-    if (warp == 2 || warp == 3)
-        pair_block_solve<8, PFB>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192, true, warp - 2, 2);
-    __syncthreads();
-    if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
-    __syncthreads();
-    schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, 0, nth);
-    __syncthreads();
-    for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
-    __syncthreads();
-    temperature_corrections<1, false>(P, F, s, m, false, 0);
+    if (F.ir_t) {
+        if (warp == 2 || warp == 3)
+            pair_block_solve<8, PFB>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192, true, warp - 2, 2);
+        __syncthreads();
+        if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
+        __syncthreads();
+        schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, 0, nth);
+        __syncthreads();
+        for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
+        __syncthreads();
+        temperature_corrections<1, false>(P, F, s, m, false, 0);
+    } else {
+        if (warp == 2 || warp == 3)
+            pair_block_solve<8, PFB>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m * nbt * 192, true,
+                                     warp - 2, 2);
+        __syncthreads();
+        if (warp == 2) warp_schur<2>(s.tx[0], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m * 4);
+        __syncthreads();
+        schur_update<2>(s.tx[0], nc, F.tY + (size_t)m * nt * 2, 0, nth);
+        __syncthreads();
+    }
     if (m == 0) {
         // the zonal flow after the temperature, in its freed FP32 arrays (the
         // same footprint in doubles): chain scratch in tq, correction in td, the
@@ -1180,7 +1194,7 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
             for (int j = tid; j < nt; j += nth) s.ux[2 + j] -= F.uY[(size_t)j * 2] * u0 + F.uY[(size_t)j * 2 + 1] * u1;
         }
         __syncthreads();
-        refine_zonal_flow(P, F, s);
+        if (F.ir_t) refine_zonal_flow(P, F, s);
     }
     for (int n = tid; n < nc; n += nth) {
         y_out.th[(size_t)m * nc + n] = s.tx[0][n];
@@ -1478,7 +1492,7 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
     // the systems with FP32-refined temperature solves (N_c > 600): with explicit
     // buoyancy one CTA per system (two per mode, two per SM), else the deep chain
     // prefetch (one CTA per SM by shared memory)
-    if (F.ir_t && !P.buoy_imp && P.solve_roles) {
+    if (!P.buoy_imp && (P.solve_roles > 0 || (P.solve_roles < 0 && F.ir_t))) {
         const size_t smr = sizeof(double) * solve_roles_smem_doubles(P.nc);
         cudaError_t err = cudaFuncSetAttribute(k_solve_roles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
         if (err != cudaSuccess) return err;

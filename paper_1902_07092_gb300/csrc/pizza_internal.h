@@ -142,9 +142,12 @@ struct StepParams {
     // Courant guard (option "cfl_alpha", Eq. cfl): when cfl_max is set the
     // azimuthal kernel folds max |u_s|/ds_k and max |u_phi|/(s_k dphi) of the
     // synthesised state into cfl_max[0], cfl_max[1] (atomic maxima)
-    // large-N_c solve (FP32-refined temperature, explicit buoyancy) in one CTA
-    // per system (option "solve_roles", 1 = default) instead of one per mode
+    // the solve with explicit buoyancy in one CTA per system instead of one per
+    // mode (option "solve_roles"): 1 always, 0 never, -1 (default) from N_c > 600
     int solve_roles;
+    // FP64 radial kernels in the three-array layout (option "radial_lean"):
+    // 1 from n_r = 129 (the half-length DCT-I), 0 never, -1 (default) from n_r = 513
+    int radial_lean;
     double* cfl_max;
     const double* cfl_ds;  // [n_r] local Gauss-Lobatto spacing
     double cfl_dphi;       // 2 pi / n_phi

@@ -298,19 +298,20 @@ def test_steps_match_oracle_fp32_refined_temperature_solve(scheme):
     gpu.close()
 
 
-@pytest.mark.parametrize("scheme", ["CNAB2", "SBDF3"])
-def test_solve_in_one_cta_per_system_equals_one_cta_per_mode(scheme):
-    """Option solve_roles: at N_c > 600 with explicit buoyancy the solve runs one
-    CTA per system (streamfunction; temperature, then the zonal flow for m = 0)
-    instead of one per mode.  The arithmetic is the same, so three steps from a
-    state with every field nonzero agree bit for bit (n_r = 1025, n_phi = 768)."""
+@pytest.mark.parametrize("n_r,n_phi,E,scheme", [(1025, 768, 1e-6, "CNAB2"), (1025, 768, 1e-6, "SBDF3"),
+                                                (257, 768, 1e-5, "ARS443"), (65, 192, 1e-3, "BPR353")])
+def test_solve_in_one_cta_per_system_equals_one_cta_per_mode(n_r, n_phi, E, scheme):
+    """Option solve_roles: with explicit buoyancy the solve runs one CTA per
+    system (streamfunction; temperature, then the zonal flow for m = 0) instead of
+    one per mode -- by default from N_c > 600 (FP32-refined temperature), on
+    request below it (FP64 temperature blocks).  The arithmetic is the same, so
+    three steps from a state with every field nonzero agree bit for bit."""
     from paper_1902_07092_gb300.binding import Solver, pizza_set_option
-    n_r, n_phi, E = 1025, 768, 1e-6
     Ra = 5.0 * critical_rayleigh(E)
     psi, th, u = random_state(n_r, n_phi, 1e-2, 31, psi_amp=1e-4, u_amp=1e-3)
     out = []
     for roles in (1, 0):
-        s = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, scheme, 1e-9)
+        s = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, scheme, 1e-3 * E)
         pizza_set_option(s.ctx, "solve_roles", roles)
         s.set_state(th, psi, u)
         s.step(3)
@@ -318,3 +319,22 @@ def test_solve_in_one_cta_per_system_equals_one_cta_per_mode(scheme):
         s.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n_r,n_phi", [(129, 384), (257, 768), (513, 1536)])
+def test_lean_radial_layout_matches_oracle(n_r, n_phi):
+    """Option radial_lean = 1 below its default threshold: the three-array
+    synthesis and analysis kernels give the oracle's explicit terms to the same
+    bar as the batched layout."""
+    from paper_1902_07092_gb300.binding import pizza_set_option
+    gpu, ora = make_pair(n_r, n_phi, 1e-3, 2.0, "CNAB2", 1e-4)
+    pizza_set_option(gpu.ctx, "radial_lean", 1)
+    psi, th, u = random_state(n_r, n_phi, 1.0, 5, psi_amp=1.0, u_amp=1.0)
+    gpu.set_state(th, psi, u)
+    ep, et, eu = gpu.explicit_terms()
+    rp, rt, ru = explicit_terms(ora.g, psi, th, u)
+    tol = max(1e-12, 4 * n_r * n_r * 2.0 ** -53)
+    errs = (rel_l2(ep, rp), rel_l2(et, rt), rel_l2(eu, ru))
+    print("lean explicit terms n_r=%d: %.2e %.2e %.2e (tol %.1e)" % ((n_r,) + errs + (tol,)))
+    assert max(errs) <= tol
+    gpu.close()
