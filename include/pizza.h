@@ -278,10 +278,13 @@ int pizza_nusselt_end(pizza_ctx *ctx, double *sum, int *steps);
 
 /* Autotuner: times the explicit stage of the context (on its current state)
  * for each launch shape the device allows -- radial transforms batched one, two
- * or four per shared-memory pass, 128/256/512 threads in the azimuthal kernel -- and
- * keeps the fastest for later steps.  The shapes change the schedule, not the
- * arithmetic: results are bitwise the same.  *nb_r and *phi_threads (may be NULL)
- * receive the choice.  Integration formulation only. */
+ * or four per shared-memory pass, 128/256/512 threads in the azimuthal kernel --
+ * and, with explicit buoyancy and tau rows, the implicit solve with one CTA per
+ * mode and with one per system (option "solve_roles"), and keeps the fastest
+ * for later steps.  The choices change the schedule, not the arithmetic: results
+ * are bitwise the same.  *nb_r and *phi_threads (may be NULL) receive the
+ * explicit-stage choice.  Integration formulation only; builds the factored
+ * operators if the context has not stepped yet. */
 int pizza_autotune(pizza_ctx *ctx, int *nb_r, int *phi_threads);
 
 /* Batches of independent contexts (any sizes, parameters and schemes) advanced

@@ -2221,10 +2221,38 @@ int pizza_autotune(pizza_ctx* ctx, int* nb_r, int* phi_thr) {
             pick = c;
         }
     }
-    ctx->event_pool.push_back(a);
-    ctx->event_pool.push_back(b);
     ctx->P.nb_r = pick.first;
     ctx->P.phi_threads = pick.second;
+    // the solve: one CTA per mode or one per system (explicit buoyancy, tau rows),
+    // timed on a solve of the current state with the first implicit weight's
+    // factors into the scratch vector
+    if (!ctx->P.buoy_imp && !ctx->gal) {
+        int rc = ensure_factors(ctx);
+        if (rc) return rc;
+        RhsSpec R{};
+        R.t[R.nterms++] = {y, 1.0};
+        const DevFactors& F = ctx->factors[0];
+        const int keep_roles = ctx->P.solve_roles;
+        float best_s = 1e30f;
+        int pick_s = keep_roles;
+        for (int roles : {0, 1}) {
+            ctx->P.solve_roles = roles;
+            CK(launch_solve(ctx->P, R, F, e, e, e, true, false, ctx->stream));  // warm-up
+            CK(cudaEventRecord(a, ctx->stream));
+            for (int r = 0; r < 3; ++r) CK(launch_solve(ctx->P, R, F, e, e, e, true, false, ctx->stream));
+            CK(cudaEventRecord(b, ctx->stream));
+            CK(cudaEventSynchronize(b));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (ms < best_s) {
+                best_s = ms;
+                pick_s = roles;
+            }
+        }
+        ctx->P.solve_roles = pick_s;
+    }
+    ctx->event_pool.push_back(a);
+    ctx->event_pool.push_back(b);
     ctx->epoch++;  // launch shapes changed: batch graphs are captured anew
     if (nb_r) *nb_r = pick.first;
     if (phi_thr) *phi_thr = pick.second;

@@ -83,15 +83,35 @@ __global__ void __launch_bounds__(NTHREADS_R) k_spec_to_grid(StepParams P, VecSe
     if (m > 0) cheb_derivative_scan(cc1, cc2, bufA, N, P.inv_a);
 
     // field list: 0 Psi, 1 Psi', 2 Psi'', 3 theta, 4 packed u_bar + i lam u_bar'
-    // (lam a power of two balancing the two parts).  The reduction scratch lives
-    // in bufB, unused until the first transform: without static shared memory two
-    // FP32 CTAs fit an SM at n_r = 2049.
-    double* red = reinterpret_cast<double*>(bufB);
-    double* mx = red + 4 * 32;
+    // (lam a power of two balancing the two parts).  The reduction's 16 doubles
+    // live in bufB (at least 128 bytes: n_r >= 9), unused until the first
+    // transform: without static shared memory two FP32 CTAs fit an SM at
+    // n_r = 2049.
     RT lam = 1;
     if (m == 0) {
-        block_max_abs(cc0, N, 2, N, mx, red);
-        lam = (RT)pow2_ratio(mx[0], mx[1]);
+        double* red = reinterpret_cast<double*>(bufB);  // [warp][2]
+        double a0 = 0.0, a1 = 0.0;
+        for (int i = tid; i < N; i += nth) {
+            a0 = fmax(a0, (double)(fabs(cc0[i].x) + fabs(cc0[i].y)));
+            a1 = fmax(a1, (double)(fabs(cc1[i].x) + fabs(cc1[i].y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 = fmax(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+            a1 = fmax(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+        }
+        const int w = tid >> 5;
+        if ((tid & 31) == 0) {
+            red[2 * w] = a0;
+            red[2 * w + 1] = a1;
+        }
+        __syncthreads();
+        double r0 = 0.0, r1 = 0.0;
+        for (int q = 0; q < (nth >> 5); ++q) {
+            r0 = fmax(r0, red[2 * q]);
+            r1 = fmax(r1, red[2 * q + 1]);
+        }
+        lam = (RT)pow2_ratio(r0, r1);
     }
     int fields[4];
     int nf;
