@@ -19,7 +19,9 @@ library's stream, with a 256 MiB write between steps to flush the 129 MB L2
 kernel launch for the per-kernel (roofline) numbers.  The end-to-end figure
 times set_state (pinned host buffers) + step + get_state per step.
 Multi-GPU (torchrun): independent replicas, one per rank; value = all ranks'
-grid-point-steps / max time over ranks.
+grid-point-steps / max time over ranks.  --shard slabs instead splits one run
+over the ranks by the m-slab decomposition (NCCL all-to-alls inside the step;
+strong scaling), and checks the decomposed step bitwise against the whole one.
 """
 import argparse
 import json
@@ -625,6 +627,76 @@ def run_native(args, wl, Ra, rank, world, local_rank):
     sol.close()
 
 
+def run_slabs(args, wl, Ra, rank, world, local_rank):
+    """One run of the workload split over the ranks by the m-slab decomposition
+    (Section 5): each rank advances its slab of modes and transforms its slab of
+    radii, two NCCL all-to-alls per explicit evaluation.  Total work is fixed as
+    the rank count grows: strong scaling."""
+    import torch
+    import torch.distributed as dist
+    from paper_1902_07092_gb300 import binding as B
+    from paper_1902_07092_gb300.slabs import DistTransport, Plan, SlabSolver
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n_r, n_phi = wl["n_r"], wl["n_phi"]
+    gp = n_r * n_phi
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    nc = inputs.n_c_of(wl)
+    th = inputs.theta_init(n_r, n_phi, wl["amp"], wl["seed"], cfg=wl["cfg"], n_c=nc)
+    z, zu = inputs.zero_state(n_r, n_phi, n_c=nc)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def make():
+        s = B.Solver(n_r, n_phi, wl["E"], Ra, wl["Pr"], wl["eta"], wl["scheme"], wl["dt"])
+        B.pizza_set_stream(s.ctx, stream.cuda_stream)
+        s.set_state(th, z, zu)
+        return s
+
+    sol = make()
+    plan = Plan(sol.M, n_r, world, rank)
+    slab = SlabSolver(sol, plan, DistTransport(), dev)
+    total_ms, kt, kn, clocks = measure_context(args, B, sol, stream, flush, world, dev, dist.barrier, local_rank)
+    if slab.error:
+        raise RuntimeError(slab.error)
+    # the decomposed step against the whole step on one context: two steps from
+    # the initial state, this rank's modes compared bit for bit
+    sol.set_state(th, z, zu)
+    sol.step(2)
+    mine = sol.get_state()
+    ref = make()
+    ref.step(2)
+    whole = ref.get_state()
+    ref.close()
+    m0, m1 = plan.m_range
+    same = all(np.array_equal(a[m0:m1], b[m0:m1]) for a, b in zip(mine[:2], whole[:2]))
+    if m0 == 0:
+        same = same and np.array_equal(mine[2], whole[2])
+    ok = torch.tensor([1.0 if same else 0.0], device=dev)
+    dist.all_reduce(ok, op=dist.ReduceOp.MIN)
+    if rank == 0:
+        flops = algorithmic_flops(n_r, n_phi, wl["scheme"])
+        nbytes = algorithmic_bytes(n_r, n_phi, wl["scheme"])
+        peaks = measured_peaks()
+        line = {
+            "metric": METRIC, "value": gp * args.steps / (total_ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(config_of(args, wl, Ra), parallelism="m-slabs x%d" % world,
+                           slabs={"modes": plan.ms, "radii": plan.ks}),
+            "gpu_launches": launches_per_step(wl["scheme"]) * args.steps,
+            "kernels": kernel_table(kt, kn, flops, nbytes, float(peaks.get("hbm_gbs", 6800.0))),
+            "slabs": {"bitwise_equal_to_whole_step": bool(ok.item() == 1.0),
+                      "exchange": "torch.distributed all_to_all_single (NCCL), two per explicit evaluation, "
+                                  "inside the step through pizza_set_slab's callback",
+                      "rank0_kernels_note": "kernel times of rank 0's slab"},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    slab.close()
+    sol.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -636,6 +708,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "slabs"],
+                    help="replicas: one run per rank (weak scaling); slabs: one run split over the ranks "
+                         "by the m-slab decomposition (strong scaling)")
     args = ap.parse_args()
     args.steps_given = args.steps is not None
     if args.steps is None:
@@ -661,6 +736,15 @@ def main():
     Ra = wl["ra_factor"] * critical_rayleigh(wl["E"])
     if args.impl == "reference":
         run_reference(args, wl, Ra, rank)
+        return
+    if args.shard == "slabs":
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29541")
+        os.environ.setdefault("NCCL_DEBUG", "WARN")  # keep stdout to the one JSON line
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+        run_slabs(args, wl, Ra, rank, world, local_rank)
+        dist.destroy_process_group()
         return
     if world > 1:
         import torch.distributed as dist

@@ -108,3 +108,41 @@ def test_slab_option_limits():
     sl.close()
     s.diagnostics()                      # the whole step again
     s.close()
+
+
+def test_slab_ranks_through_nccl_all_to_all():
+    """The same exchange code over torch.distributed's NCCL backend (one rank on
+    this GPU: the all-to-alls run, each rank's share being everything): the
+    decomposed step equals the whole step bit for bit."""
+    import socket
+
+    import torch
+    import torch.distributed as dist
+    from paper_1902_07092_gb300 import binding as B
+    from paper_1902_07092_gb300.slabs import DistTransport, Plan, SlabSolver
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1)
+    try:
+        n_r, n_phi = 129, 384
+        Ra = 3.0 * critical_rayleigh(1e-3)
+        th = inputs.theta_init(n_r, n_phi, 1.0, 5, cfg=7, m_min=0)
+        z, zu = inputs.zero_state(n_r, n_phi)
+        whole = B.Solver(n_r, n_phi, 1e-3, Ra, 1.0, 0.35, "SBDF3", 1e-4)
+        whole.set_state(th, z, zu)
+        whole.step(3)
+        ref = whole.get_state()
+        whole.close()
+        s = B.Solver(n_r, n_phi, 1e-3, Ra, 1.0, 0.35, "SBDF3", 1e-4)
+        slab = SlabSolver(s, Plan(s.M, n_r, 1, 0), DistTransport(), torch.device("cuda", 0))
+        s.set_state(th, z, zu)
+        s.step(3)
+        assert slab.error is None
+        for a, b in zip(s.get_state(), ref):
+            assert np.array_equal(a, b)
+        slab.close()
+        s.close()
+    finally:
+        dist.destroy_process_group()
