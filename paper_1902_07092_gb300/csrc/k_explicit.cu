@@ -1078,18 +1078,20 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean(StepParams 
         }
         // Eq. icheb of the grid values, truncated to n < nc
         const double2* Z = dct1_pair(W, (W == X) ? Y : X, P);
-        for (int n = tid; n < nc; n += nth) C[n] = cscale(Z[n], hc);
+        // N_omega_hat, with the buoyancy (Ra/Pr)(i m/s_o) theta_hat added before the
+        // one C^I apply (Eq. psi_int applies C^I to their sum)
+        const bool buoy = (fld == 0 && m > 0 && !P.buoy_imp);
+        for (int n = tid; n < nc; n += nth) {
+            const double2 v = cscale(Z[n], hc);
+            C[n] = buoy ? cadd(v, cmul_i(y.th[(size_t)m * nc + n], bfac)) : v;
+        }
         __syncthreads();
         // integrated right-hand sides; the linear couplings read the FP64 state
         for (int k = tid; k < nc; k += nth) {
             if (fld == 0) {
                 if (m > 0) {
                     double2 ep = make_double2(0.0, 0.0);
-                    if (k >= 4) {
-                        ep = band_row<8>(P.ops.band[OP_C], C, k, nc);
-                        if (!P.buoy_imp)
-                            ep = cadd(ep, cmul_i(band_row<8>(P.ops.band[OP_C], y.th + (size_t)m * nc, k, nc), bfac));
-                    }
+                    if (k >= 4) ep = band_row<8>(P.ops.band[OP_C], C, k, nc);
                     e.psi[(size_t)m * nc + k] = ep;
                 } else {
                     e.psi[k] = make_double2(0.0, 0.0);
