@@ -150,6 +150,12 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            instead of one per mode: 1 always, 0 never, -1 (default) from
  *            N_c > 600, where it fits two CTAs per SM.  The same arithmetic
  *            either way (bitwise equal results);
+ *   "psi_chain_dd" in that kernel, the block chains of the streamfunction
+ *            solve (Appendix A's banded block) in double-float arithmetic on the
+ *            FP32 pipe (about 48 significant bits; the Schur step, residual and
+ *            refinement stay FP64): 1 always, 0 never (FP64 chains), -1
+ *            (default) from N_c > 600.  Results agree with the FP64 chains to the
+ *            accuracy of the refined solve, not bitwise;
  *   "radial_batch" radial transforms batched per shared-memory pass in the
  *            per-mode explicit kernels: 1, 2 or 4, 0 = the default rule (up to
  *            n_r = 513: 4 in FP64, 2 in mixed precision; else 1); "phi_threads" threads of the per-radius azimuthal

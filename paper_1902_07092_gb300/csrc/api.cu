@@ -441,6 +441,16 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         for (int d = 0; d < 9; ++d) bu8[(size_t)k * 17 + d + 4] = bu[(size_t)k * 9 + d];
     if (!block_lu_twisted(bu8, nc, 8, 2, ub)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
     UPLOAD(F.pBlk, double2, hpK);
+    {
+        // double-float copy: the nearest float and the float nearest the remainder
+        std::vector<float4> hpKd(hpK.size());
+        for (size_t i = 0; i < hpK.size(); ++i) {
+            const double re = hpK[i].x, im = hpK[i].y;
+            const float rh = (float)re, ih = (float)im;
+            hpKd[i] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+        }
+        UPLOAD(F.pBlkDD, float4, hpKd);
+    }
     F.psplit = psplit ? 1 : 0;
     if (psplit) {
         UPLOAD(F.pSpk, double2, hpSpk);
@@ -1510,6 +1520,7 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
     }
     P.solve_roles = -1;
     P.radial_lean = -1;
+    P.psi_dd = -1;
     // half-length radial plan: its twiddles exp(-2 pi i j/K) are plan_r's at stride 2
     if (!make_fft_plan(ctx->K, P.plan_h)) {
         ctx->err = "unsupported transform length";
@@ -1682,6 +1693,14 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
             return fail(ctx, PIZZA_EINVAL, "solve_roles must be -1 (by size), 0 or 1");
         cudaStreamSynchronize(ctx->stream);
         ctx->P.solve_roles = (int)value;
+        ++ctx->epoch;
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "psi_chain_dd") == 0) {
+        if (value != 0.0 && value != 1.0 && value != -1.0)
+            return fail(ctx, PIZZA_EINVAL, "psi_chain_dd must be -1 (by size), 0 or 1");
+        cudaStreamSynchronize(ctx->stream);
+        ctx->P.psi_dd = (int)value;
         ++ctx->epoch;
         return PIZZA_OK;
     }

@@ -101,6 +101,111 @@ __device__ __forceinline__ float2 fma_x(float a, float2 b, float2 acc) {
 __device__ __forceinline__ float2 sub_x(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
+// Accumulator, conversions and finalisation of a chain value: for FP64 and FP32
+// chains the accumulator is the value type itself and these are identities.
+__device__ __forceinline__ double2 sub_acc(double2 a, double2 b) { return csub(a, b); }
+__device__ __forceinline__ float2 sub_acc(float2 a, float2 b) { return sub_x(a, b); }
+__device__ __forceinline__ double sub_acc(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 fin(double2 v) { return v; }
+__device__ __forceinline__ float2 fin(float2 v) { return v; }
+__device__ __forceinline__ double fin(double v) { return v; }
+__device__ __forceinline__ double2 cvt_to(double2 v, const double2*) { return v; }
+__device__ __forceinline__ float2 cvt_to(float2 v, const float2*) { return v; }
+__device__ __forceinline__ double cvt_to(double v, const double*) { return v; }
+
+// Double-float chains of the streamfunction solve.  The block chains of the
+// Appendix A solve need about 44 significant bits: with the Schur step, the
+// residual and the refinement in FP64, chains in 44- to 48-bit arithmetic leave
+// the refined solution as close to the oracle's as FP64 chains do (measured on the
+// tau systems at n_r = 257, 1025 and 2049), while FP32 chains need two and more
+// corrections at n_r = 1025 and do not converge at 2049.  A double-float value
+// (ddfloat.cuh) carries 48 bits on the FP32 pipe, which issues 64 times the FP64
+// rate on GB300.
+//
+// Factors and chain values are complex double-floats (ddc, 16 bytes like a
+// double2).  A row sum runs in an accumulator dacc of leading sums s and trailing
+// sums e per component: every product a b of double-floats adds its leading part
+// p = a.hi b.hi to s by a two-sum and its trailing parts (the two-product error
+// fma(a.hi, b.hi, -p), a.hi b.lo + a.lo b.hi, and the two-sum's error) to e; the
+// value is s + e, renormalised once at the end of the row (Ogita, Rump and
+// Oishi's compensated dot product, applied to double-float inputs).
+struct __align__(16) dacc {
+    float xs, xe, ys, ye;
+};
+template <>
+__device__ __forceinline__ dacc zero<dacc>() { return dacc{0.f, 0.f, 0.f, 0.f}; }
+template <>
+__device__ __forceinline__ ddc zero<ddc>() { return ddc{ddf{0.f, 0.f}, ddf{0.f, 0.f}}; }
+
+// s + p = s' + t exactly (Knuth's two-sum)
+__device__ __forceinline__ float two_sum(float s, float p, float& t) {
+    const float r = __fadd_rn(s, p);
+    const float bb = __fsub_rn(r, s);
+    t = __fadd_rn(__fsub_rn(s, __fsub_rn(r, bb)), __fsub_rn(p, bb));
+    return r;
+}
+// (s, e) += (ah + al)(bh + bl)
+__device__ __forceinline__ void dd_acc(float& s, float& e, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    const float pe = __fmaf_rn(ah, bh, -p);
+    const float cr = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+    float t;
+    s = two_sum(s, p, t);
+    e = __fadd_rn(e, __fadd_rn(t, __fadd_rn(pe, cr)));
+}
+// acc + a b, complex
+__device__ __forceinline__ dacc fma_x(ddc a, ddc b, dacc acc) {
+    dd_acc(acc.xs, acc.xe, a.x.hi, a.x.lo, b.x.hi, b.x.lo);
+    dd_acc(acc.xs, acc.xe, -a.y.hi, -a.y.lo, b.y.hi, b.y.lo);
+    dd_acc(acc.ys, acc.ye, a.x.hi, a.x.lo, b.y.hi, b.y.lo);
+    dd_acc(acc.ys, acc.ye, a.y.hi, a.y.lo, b.x.hi, b.x.lo);
+    return acc;
+}
+// sum over the four lanes of a row; the two-sum's result and error do not depend
+// on the order of its operands, so every lane gets the same bits
+__device__ __forceinline__ void dd_pair_sum(float& s, float& e, int o) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), e2 = __shfl_xor_sync(0xffffffffu, e, o);
+    float t;
+    s = two_sum(s, s2, t);
+    e = __fadd_rn(__fadd_rn(e, e2), t);
+}
+__device__ __forceinline__ dacc reduce4(dacc v) {
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        dd_pair_sum(v.xs, v.xe, o);
+        dd_pair_sum(v.ys, v.ye, o);
+    }
+    return v;
+}
+// (s + e) as a normalised double-float: two-sum, since e may exceed a cancelled s
+__device__ __forceinline__ ddf dd_norm(float s, float e) {
+    float t;
+    const float h = two_sum(s, e, t);
+    return ddf{h, t};
+}
+__device__ __forceinline__ ddc fin(dacc v) { return ddc{dd_norm(v.xs, v.xe), dd_norm(v.ys, v.ye)}; }
+// b - p
+__device__ __forceinline__ ddf dd_sub1(ddf b, float s, float e) {
+    float t;
+    const float h = two_sum(b.hi, -s, t);
+    return dd_norm(h, __fadd_rn(__fsub_rn(b.lo, e), t));
+}
+__device__ __forceinline__ ddc sub_x(ddc b, dacc p) { return ddc{dd_sub1(b.x, p.xs, p.xe), dd_sub1(b.y, p.ys, p.ye)}; }
+__device__ __forceinline__ dacc sub_acc(dacc a, dacc b) {
+    float t, u;
+    const float xs = two_sum(a.xs, -b.xs, t);
+    const float ys = two_sum(a.ys, -b.ys, u);
+    return dacc{xs, __fadd_rn(__fsub_rn(a.xe, b.xe), t), ys, __fadd_rn(__fsub_rn(a.ye, b.ye), u)};
+}
+template <>
+__device__ __forceinline__ ddc shfl_idx<ddc>(ddc v, int src) {
+    return ddc{ddf{__shfl_sync(0xffffffffu, v.x.hi, src), __shfl_sync(0xffffffffu, v.x.lo, src)},
+               ddf{__shfl_sync(0xffffffffu, v.y.hi, src), __shfl_sync(0xffffffffu, v.y.lo, src)}};
+}
+// the right-hand side and the solution stay FP64 arrays
+__device__ __forceinline__ ddc cvt_to(double2 v, const ddc*) { return dd_from(v); }
+__device__ __forceinline__ double2 cvt_to(ddc v, const double2*) { return dd_to(v); }
+
 // Blocks of coefficients prefetched ahead in the chains.  With a few CTAs per SM
 // (N_c up to ~600) two blocks cover the L2 latency at little register cost; the
 // large systems run one CTA per SM (shared memory) with their factors streamed
@@ -122,8 +227,8 @@ __device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 6
 // (n entries); rows of b at or beyond n read as zero.  Both warps of the pair
 // must call it (bar: named barrier id); act = false skips all memory accesses.
 // On return the whole of x is visible to both warps.
-template <int H, int PF, class TF, class TX>
-__device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __restrict__ blk, bool act, int half,
+template <int H, int PF, class TF, class TX, class TA = TX, class TB = TX>
+__device__ void pair_block_solve(const TB* b, TX* Z, TB* x, int n, const TF* __restrict__ blk, bool act, int half,
                                  int bar) {
     constexpr int CPL = H / 4;
     constexpr int HH = H * H;
@@ -160,8 +265,8 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
                 if (i0 + i < len) {
                     const int k = k_fw + dir * (i0 + i);
                     const int row = k * H + r;
-                    const TX bv = (ra && row < n) ? b[row] : zero<TX>();
-                    TX p = zero<TX>();
+                    const TX bv = (ra && row < n) ? cvt_to(b[row], (const TX*)nullptr) : zero<TX>();
+                    TA p = zero<TA>();
 #pragma unroll
                     for (int q = 0; q < CPL; ++q) p = fma_x(cur[i][q], prev[q], p);
                     p = reduce4(p);
@@ -181,7 +286,7 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
     // middle block, by both warps: x_c = S^{-1}(b_c - L_c z_{c-1} - M_c w_{c+1})
     TX prev[CPL];
     {
-        TX t = zero<TX>();
+        TA t = zero<TA>();
 #pragma unroll
         for (int q = 0; q < CPL; ++q) {
             const int col = c + 4 * q;
@@ -190,16 +295,16 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
         }
         t = reduce4(t);
         const int row = cm * H + r;
-        const TX bv = (ra && row < n) ? b[row] : zero<TX>();
+        const TX bv = (ra && row < n) ? cvt_to(b[row], (const TX*)nullptr) : zero<TX>();
         const TX rv = sub_x(bv, t);
         TX rr[CPL];
 #pragma unroll
         for (int q = 0; q < CPL; ++q) rr[q] = shfl_idx(rv, 4 * (c + 4 * q));
-        TX xv = zero<TX>();
+        TA xa = zero<TA>();
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) xv = fma_x(coef(cm, 1, q), rr[q], xv);
-        xv = reduce4(xv);
-        if (half == 0 && ra && c == 0 && row < n) x[row] = xv;
+        for (int q = 0; q < CPL; ++q) xa = fma_x(coef(cm, 1, q), rr[q], xa);
+        const TX xv = fin(reduce4(xa));
+        if (half == 0 && ra && c == 0 && row < n) x[row] = cvt_to(xv, (const TB*)nullptr);
 #pragma unroll
         for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(xv, 4 * (c + 4 * q));
     }
@@ -227,16 +332,16 @@ __device__ void pair_block_solve(const TX* b, TX* Z, TX* x, int n, const TF* __r
             for (int i = 0; i < PF; ++i) {
                 if (i0 + i < len) {
                     const int k = k_bw + bdir * (i0 + i);
-                    TX pz = zero<TX>(), ph = zero<TX>();
+                    TA pz = zero<TA>(), ph = zero<TA>();
 #pragma unroll
                     for (int q = 0; q < CPL; ++q) {
                         const TX zq = ra ? Z[k * H + c + 4 * q] : zero<TX>();
                         pz = fma_x(cu[i][q], zq, pz);
                         ph = fma_x(ch[i][q], prev[q], ph);
                     }
-                    TX p = reduce4(sub_x(pz, ph));
+                    const TX p = fin(reduce4(sub_acc(pz, ph)));
                     const int row = k * H + r;
-                    if (ra && c == 0 && row < n) x[row] = p;
+                    if (ra && c == 0 && row < n) x[row] = cvt_to(p, (const TB*)nullptr);
 #pragma unroll
                     for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(p, 4 * (c + 4 * q));
                 }
@@ -1017,6 +1122,7 @@ __host__ __device__ inline size_t solve_roles_smem_doubles(int nc) {
     return (size_t)2 * b * 5 > (size_t)2 * b * 2 + 3 * b + 2 * b ? (size_t)2 * b * 5 : (size_t)2 * b * 2 + 5 * b;
 }
 
+template <bool DDP>
 __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, RhsSpec R, DevFactors F, VecSet y_out,
                                                                 VecSet mass_out, VecSet imp_out, int want_mass,
                                                                 int want_imp) {
@@ -1058,13 +1164,24 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
         }
         __syncthreads();
         const double2* blk = F.pBlk + (size_t)m * nbp * 192;
+        const ddc* blkd = reinterpret_cast<const ddc*>(F.pBlkDD) + (size_t)m * nbp * 192;
+        ddc* zd = reinterpret_cast<ddc*>(s.pw[0]);
         for (int it = 0; it < 2; ++it) {  // solve, then one refinement step
             double2* x = it ? s.pd[0] : s.px[0];
-            if (warp < 2)
-                pair_block_solve<8, PFB>(s.pf[0] + 4, s.pw[0], x + 4, F.psplit ? nA : np, blk, true, warp, 1);
-            else if (warp >= 6 && F.psplit)
-                pair_block_solve<8, PFB>(s.pf[0] + 4 + nA, s.pw[0] + nA, x + 4 + nA, np - nA, blk + (size_t)(nbp / 2) * 192,
-                                         true, warp - 6, 4);
+            if constexpr (DDP) {  // double-float chains
+                if (warp < 2)
+                    pair_block_solve<8, PFB, ddc, ddc, dacc>(s.pf[0] + 4, zd, x + 4, F.psplit ? nA : np, blkd, true, warp,
+                                                             1);
+                else if (warp >= 6 && F.psplit)
+                    pair_block_solve<8, PFB, ddc, ddc, dacc>(s.pf[0] + 4 + nA, zd + nA, x + 4 + nA, np - nA,
+                                                             blkd + (size_t)(nbp / 2) * 192, true, warp - 6, 4);
+            } else {
+                if (warp < 2)
+                    pair_block_solve<8, PFB>(s.pf[0] + 4, s.pw[0], x + 4, F.psplit ? nA : np, blk, true, warp, 1);
+                else if (warp >= 6 && F.psplit)
+                    pair_block_solve<8, PFB>(s.pf[0] + 4 + nA, s.pw[0] + nA, x + 4 + nA, np - nA,
+                                             blk + (size_t)(nbp / 2) * 192, true, warp - 6, 4);
+            }
             __syncthreads();
             if (F.psplit)
                 split_join(x + 4, np, nA, F.pSpk + (size_t)m * np * 8, F.pRj + (size_t)m * 256, true);
@@ -1494,10 +1611,14 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
     // prefetch (one CTA per SM by shared memory)
     if (!P.buoy_imp && (P.solve_roles > 0 || (P.solve_roles < 0 && F.ir_t))) {
         const size_t smr = sizeof(double) * solve_roles_smem_doubles(P.nc);
-        cudaError_t err = cudaFuncSetAttribute(k_solve_roles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        // double-float streamfunction chains: option psi_chain_dd, by default
+        // from N_c > 600 (where the roles kernel is the default)
+        const bool ddp = F.pBlkDD && (P.psi_dd > 0 || (P.psi_dd < 0 && F.ir_t));
+        auto kern = ddp ? k_solve_roles<true> : k_solve_roles<false>;
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
         if (err != cudaSuccess) return err;
-        k_solve_roles<<<2 * slab_modes(P), NTHREADS_S, smr, st>>>(P, rhs, F, y_out, mass_out, imp_out,
-                                                                  want_mass ? 1 : 0, want_imp ? 1 : 0);
+        kern<<<2 * slab_modes(P), NTHREADS_S, smr, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
+                                                         want_imp ? 1 : 0);
         return cudaGetLastError();
     }
     auto kern = F.ir_t ? k_solve<1, true> : k_solve<1, false>;

@@ -61,6 +61,9 @@ struct DevFactors {
     // the inverse of the interface system [[I, V_last], [W_first, I]]
     int psplit;
     double2 *pSpk, *pRj;
+    // the same blocks as complex double-floats [re.hi, re.lo, im.hi, im.lo] for
+    // the double-float chains (option psi_chain_dd)
+    float4* pBlkDD;
     // temperature, real, blocks of H = 8 rows (band half width 4, padded): blocks
     // [M][nb_t][3][64], nb_t = ceil(n_t/8), Y [M][n_t][2], Sinv [M][4],
     // assembled rows 2..nc-1 of D^I - gamma dt F^I_m/Pr [M][n_t][9]
@@ -148,6 +151,10 @@ struct StepParams {
     // FP64 radial kernels in the three-array layout (option "radial_lean"):
     // 1 from n_r = 129 (the half-length DCT-I), 0 never, -1 (default) from n_r = 513
     int radial_lean;
+    // streamfunction block chains of the solve in double-float arithmetic
+    // (option "psi_chain_dd"): 1 always, 0 never, -1 (default) from N_c > 600,
+    // in the kernel with one CTA per system
+    int psi_dd;
     double* cfl_max;
     const double* cfl_ds;  // [n_r] local Gauss-Lobatto spacing
     double cfl_dphi;       // 2 pi / n_phi

@@ -304,8 +304,9 @@ def test_solve_in_one_cta_per_system_equals_one_cta_per_mode(n_r, n_phi, E, sche
     """Option solve_roles: with explicit buoyancy the solve runs one CTA per
     system (streamfunction; temperature, then the zonal flow for m = 0) instead of
     one per mode -- by default from N_c > 600 (FP32-refined temperature), on
-    request below it (FP64 temperature blocks).  The arithmetic is the same, so
-    three steps from a state with every field nonzero agree bit for bit."""
+    request below it (FP64 temperature blocks).  With FP64 streamfunction chains
+    (option psi_chain_dd = 0) the arithmetic is the same, so three steps from a
+    state with every field nonzero agree bit for bit."""
     from paper_1902_07092_gb300.binding import Solver, pizza_set_option
     Ra = 5.0 * critical_rayleigh(E)
     psi, th, u = random_state(n_r, n_phi, 1e-2, 31, psi_amp=1e-4, u_amp=1e-3)
@@ -313,6 +314,7 @@ def test_solve_in_one_cta_per_system_equals_one_cta_per_mode(n_r, n_phi, E, sche
     for roles in (1, 0):
         s = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, scheme, 1e-3 * E)
         pizza_set_option(s.ctx, "solve_roles", roles)
+        pizza_set_option(s.ctx, "psi_chain_dd", 0)
         s.set_state(th, psi, u)
         s.step(3)
         out.append(s.get_state())
@@ -338,3 +340,38 @@ def test_lean_radial_layout_matches_oracle(n_r, n_phi):
     print("lean explicit terms n_r=%d: %.2e %.2e %.2e (tol %.1e)" % ((n_r,) + errs + (tol,)))
     assert max(errs) <= tol
     gpu.close()
+
+
+@pytest.mark.parametrize("n_r,n_phi,E,scheme,tol", [(65, 192, 1e-3, "BPR353", 1e-12), (257, 24, 1e-5, "ARS443", 2e-12),
+                                                    (513, 24, 1e-5, "CNAB2", 5e-12),
+                                                    (1025, 24, 1e-6, "SBDF3", 5e-12)])
+def test_double_float_streamfunction_chains_match_oracle(n_r, n_phi, E, scheme, tol):
+    """Option psi_chain_dd: the block chains of the streamfunction solve in
+    double-float arithmetic (48 bits; Schur step, residual and refinement in
+    FP64), forced on below its default threshold (n_r = 65, 257: one chain pair;
+    513: the split block) and the default at n_r = 1025.  Two steps against the
+    oracle at the bars of the FP64-chain tests of the same sizes, and against the
+    FP64 chains of the same kernel (option 0) to the same bar."""
+    from paper_1902_07092_gb300.binding import pizza_set_option
+    th = inputs.theta_init(n_r, n_phi, 1e-3, 51, cfg=1, m_min=0)
+    psi = inputs.theta_init(n_r, n_phi, 1e-5, 52, cfg=8)
+    psi[0] = 0.0
+    u = inputs.theta_init(n_r, n_phi, 1e-3, 53, cfg=9, m_min=0)[0].real.copy()
+    runs = {}
+    for dd in (1, 0):
+        gpu, ora = make_pair(n_r, n_phi, E, 5.0, scheme, 1e-3 * E)
+        pizza_set_option(gpu.ctx, "solve_roles", 1)
+        pizza_set_option(gpu.ctx, "psi_chain_dd", dd)
+        gpu.set_state(th, psi, u)
+        ora.set_state(psi, th, u)
+        for k in range(2):
+            gpu.step(1)
+            ora.step()
+            e = assert_state_close(gpu.get_state(), ora.y, tol, oracle=ora)
+            print("psi_chain_dd=%d n_r=%d %s step %d: state %.2e psi %.2e" % (dd, n_r, scheme, k + 1, e["state"],
+                                                                             e["psi"]))
+        runs[dd] = gpu.get_state()
+        gpu.close()
+    d = rel_l2(np.concatenate([np.ravel(x) for x in runs[1]]), np.concatenate([np.ravel(x) for x in runs[0]]))
+    print("double-float vs FP64 chains n_r=%d: %.2e" % (n_r, d))
+    assert d <= tol
