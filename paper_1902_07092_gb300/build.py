@@ -19,6 +19,9 @@ SOURCES = ["host_ops.cpp", "coll_ops.cpp", "k_explicit.cu", "k_implicit.cu", "k_
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "--expt-relaxed-constexpr"]
+# per-source host flags: the compensated sums of the factorisation (host_ops.cpp)
+# need every product and sum rounded as written, so no floating-point contraction
+SOURCE_FLAGS = {"host_ops.cpp": ["-Xcompiler", "-ffp-contract=off"]}
 
 
 def nvcc():
@@ -42,7 +45,7 @@ def _compile(src, extra):
     o = os.path.join(BUILD, src + ".o")
     if not _needs(o, s):
         return o
-    cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", s, "-o", o]
+    cmd = [nvcc()] + ARCH + FLAGS + SOURCE_FLAGS.get(src, []) + extra + ["-c", s, "-o", o]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("compile failed: %s\n%s\n%s" % (" ".join(cmd), r.stdout, r.stderr))

@@ -40,7 +40,8 @@ std::vector<double> tau_rows_dir(int n_r, int n_c);
 // Factored bordered system (Appendix A) for p border rows and a banded block
 // D of half bandwidth kl = ku = h, factored by LU without pivoting:
 //   L[i*h + t] = L(i+1+t, i),  U[i*h + t] = U(i, i+1+t),  invd[i] = 1/U(i,i),
-//   Y = D^{-1} C stored [i*p + c],  Sinv = (A - B Y)^{-1} stored [r*p + c].
+//   Y = D^{-1} C stored [i*p + c] (refined twice with residuals summed in twice the
+//   working precision),  Sinv = (A - B Y)^{-1} stored [r*p + c].
 template <class T>
 struct Bordered {
     int n = 0, p = 0, h = 0;

@@ -202,9 +202,7 @@ __device__ __forceinline__ ddc shfl_idx<ddc>(ddc v, int src) {
     return ddc{ddf{__shfl_sync(0xffffffffu, v.x.hi, src), __shfl_sync(0xffffffffu, v.x.lo, src)},
                ddf{__shfl_sync(0xffffffffu, v.y.hi, src), __shfl_sync(0xffffffffu, v.y.lo, src)}};
 }
-// the right-hand side and the solution stay FP64 arrays
-__device__ __forceinline__ ddc cvt_to(double2 v, const ddc*) { return dd_from(v); }
-__device__ __forceinline__ double2 cvt_to(ddc v, const double2*) { return dd_to(v); }
+__device__ __forceinline__ ddc cvt_to(ddc v, const ddc*) { return v; }
 
 // Blocks of coefficients prefetched ahead in the chains.  With a few CTAs per SM
 // (N_c up to ~600) two blocks cover the L2 latency at little register cost; the
@@ -443,6 +441,95 @@ __device__ void schur_update(double2* sol, int nc, const TF* __restrict__ Y, int
         for (int c = 0; c < PB; ++c) acc = fms(acc, Y[(size_t)j * PB + c], y1[c]);
         sol[PB + j] = acc;
     }
+}
+
+// Row-block dot products by the whole CTA: t_r = sum_{j < nj} R[r nj + j] x[j]
+// for the PB rows r of a real row block R (tau rows restricted to some columns)
+// against a complex vector, FP64 or FP32.  Each thread takes a stride of j (a few
+// loads in flight per thread instead of one warp walking all of them), a
+// butterfly per warp, then the warp partials summed in warp order.  Lane r < PB
+// of warp 0 gets t_r (every other thread zero).  Contains one __syncthreads; the
+// caller's next barrier must come before any thread calls it again.
+__device__ __forceinline__ void acc_rx(double2& t, double b, double2 x) {
+    t.x = fma(b, x.x, t.x);
+    t.y = fma(b, x.y, t.y);
+}
+__device__ __forceinline__ void acc_rx(float2& t, float b, float2 x) {
+    t.x = fmaf(b, x.x, t.x);
+    t.y = fmaf(b, x.y, t.y);
+}
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+__device__ __forceinline__ float2 add_x(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 add_x(double2 a, double2 b) { return cadd(a, b); }
+
+template <int PB, class TX, class TR>
+__device__ TX block_rows_dot(const TX* x, int nj, const TR* __restrict__ R) {
+    __shared__ TX part[NTHREADS_S / 32][PB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    TX t[PB];
+#pragma unroll
+    for (int r = 0; r < PB; ++r) t[r] = zero<TX>();
+    for (int j = tid; j < nj; j += blockDim.x) {
+        const TX xv = x[j];
+#pragma unroll
+        for (int r = 0; r < PB; ++r) acc_rx(t[r], __ldg(&R[(size_t)r * nj + j]), xv);
+    }
+#pragma unroll
+    for (int r = 0; r < PB; ++r) t[r] = warp_sum(t[r]);
+    if (lane == 0)
+#pragma unroll
+        for (int r = 0; r < PB; ++r) part[warp][r] = t[r];
+    __syncthreads();
+    TX v = zero<TX>();
+    if (warp == 0 && lane < PB)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = add_x(v, part[w][lane]);
+    return v;
+}
+
+// Schur step of Appendix A by the whole CTA: sol[PB..] = D^{-1} h on entry;
+// sol[0..PB) = S^{-1}(g - B sol[PB..]) on exit (g = 0 when null), visible to
+// every thread.  B: PB x (nc-PB) real tau rows; S^{-1} complex or real.
+template <int PB, class TS>
+__device__ void block_schur(double2* sol, const double2* g, int nc, const double* __restrict__ B,
+                            const TS* __restrict__ Sinv) {
+    const double2 t = block_rows_dot<PB>(sol + PB, nc - PB, B);
+    if ((threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
+        const double2 gv = (lane < PB) ? csub(g ? g[lane] : make_double2(0.0, 0.0), t) : make_double2(0.0, 0.0);
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int c = 0; c < PB; ++c) {
+            const double2 gc = shfl_idx(gv, c);
+            if (lane < PB) acc = cadd(acc, mul(Sinv[lane * PB + c], gc));
+        }
+        if (lane < PB) sol[lane] = acc;
+    }
+    __syncthreads();
+}
+
+// FP32 Schur step of the temperature system by the whole CTA: sol[2..] = D^{-1} r
+// on entry, sol[0..2) = S^{-1}(g - B sol[2..]) on exit, g = the residual's tau
+// rows; B: 2 x (nc-2) tau rows in FP32, Sinv real 2 x 2.  Ends with __syncthreads.
+__device__ void block_schur32_dir(float2* sol, const float2* g, int nc, const float* __restrict__ B,
+                                  const float* __restrict__ Sinv) {
+    const float2 t = block_rows_dot<2>(sol + 2, nc - 2, B);
+    if ((threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
+        const float2 gv = (lane < 2) ? make_float2(g[lane].x - t.x, g[lane].y - t.y) : make_float2(0.f, 0.f);
+        const float2 g0 = shfl_idx(gv, 0), g1 = shfl_idx(gv, 1);
+        if (lane < 2) {
+            const float a = Sinv[lane * 2], b = Sinv[lane * 2 + 1];
+            sol[lane] = make_float2(fmaf(a, g0.x, b * g1.x), fmaf(a, g0.y, b * g1.y));
+        }
+    }
+    __syncthreads();
 }
 
 // FP32 Schur step of the temperature system by one warp: sol[2..] = D^{-1} r on
@@ -779,6 +866,45 @@ __device__ void temperature_residual(const StepParams& P, const DevFactors& F, S
         t0 = warp_sum(t0);
         t1 = warp_sum(t1);
         if (lane < 2) s.tr[lane] = to_f2(lane ? make_double2(-t1.x, -t1.y) : make_double2(-t0.x, -t0.y));
+    }
+}
+
+// The same residual with the tau rows summed by the whole CTA (kernel with one
+// CTA per system, where no other system's warps run beside it).  Contains one
+// __syncthreads; the caller's next barrier publishes s.tr.
+__device__ void temperature_residual_block(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0) {
+    const int nc = P.nc, nt = nc - 2;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
+    for (int k = 2 + tid; k < nc; k += nth) {
+        const double* row = F.tBand + ((size_t)m0 * nt + (k - 2)) * 9;
+        double2 acc = s.tf[0][k];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+            const int n = k - 4 + d;
+            if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), s.tx[0][n]);
+        }
+        s.tr[k] = to_f2(acc);
+    }
+    const double2 t = block_rows_dot<2>(s.tx[0], nc, P.ops.tau_dir);
+    if (warp == 0 && lane < 2) s.tr[lane] = to_f2(make_double2(-t.x, -t.y));
+}
+
+// The FP32-refined temperature solve of the kernel with one CTA per system:
+// ir_t corrections x += S32^{-1}(f - L x), every reduction by the whole CTA.
+__device__ void temperature_corrections_roles(const StepParams& P, const DevFactors& F, SolveSmem& s, int m0) {
+    const int nc = P.nc, nt = nc - 2, nbt = (nt + 7) / 8;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5;
+    for (int it = 0; it < F.ir_t; ++it) {
+        temperature_residual_block(P, F, s, m0);
+        __syncthreads();
+        if (warp == 2 || warp == 3)
+            pair_block_solve<8, PFB>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2, 2);
+        __syncthreads();
+        block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
+        schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
+        __syncthreads();
+        for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
+        __syncthreads();
     }
 }
 
@@ -1168,13 +1294,24 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
         ddc* zd = reinterpret_cast<ddc*>(s.pw[0]);
         for (int it = 0; it < 2; ++it) {  // solve, then one refinement step
             double2* x = it ? s.pd[0] : s.px[0];
-            if constexpr (DDP) {  // double-float chains
+            if constexpr (DDP) {
+                // double-float chains.  The conversions between FP64 and
+                // double-float run on the FP64 pipe, so they happen here for the
+                // whole vector at once, off the chains' dependent path: the
+                // right-hand side into pd (pass 0; the correction fills pd only
+                // later) or in place (pass 1: the residual is not needed after
+                // it), the solution back from double-floats written into x.
+                ddc* bd = reinterpret_cast<ddc*>(it ? s.pf[0] : s.pd[0]);
+                ddc* xd = reinterpret_cast<ddc*>(x);
+                for (int n = 4 + tid; n < nc; n += nth) bd[n] = dd_from(s.pf[0][n]);
+                __syncthreads();
                 if (warp < 2)
-                    pair_block_solve<8, PFB, ddc, ddc, dacc>(s.pf[0] + 4, zd, x + 4, F.psplit ? nA : np, blkd, true, warp,
-                                                             1);
+                    pair_block_solve<8, PFB, ddc, ddc, dacc>(bd + 4, zd, xd + 4, F.psplit ? nA : np, blkd, true, warp, 1);
                 else if (warp >= 6 && F.psplit)
-                    pair_block_solve<8, PFB, ddc, ddc, dacc>(s.pf[0] + 4 + nA, zd + nA, x + 4 + nA, np - nA,
+                    pair_block_solve<8, PFB, ddc, ddc, dacc>(bd + 4 + nA, zd + nA, xd + 4 + nA, np - nA,
                                                              blkd + (size_t)(nbp / 2) * 192, true, warp - 6, 4);
+                __syncthreads();
+                for (int n = 4 + tid; n < nc; n += nth) x[n] = dd_to(xd[n]);
             } else {
                 if (warp < 2)
                     pair_block_solve<8, PFB>(s.pf[0] + 4, s.pw[0], x + 4, F.psplit ? nA : np, blk, true, warp, 1);
@@ -1185,8 +1322,7 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
             __syncthreads();
             if (F.psplit)
                 split_join(x + 4, np, nA, F.pSpk + (size_t)m * np * 8, F.pRj + (size_t)m * 256, true);
-            if (warp == 0) warp_schur<4>(x, it ? s.pf[0] : nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
-            __syncthreads();
+            block_schur<4>(x, it ? s.pf[0] : nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
             schur_update<4>(x, nc, F.pY + (size_t)m * np * 4, 0, nth);
             __syncthreads();
             if (it == 0) {
@@ -1201,23 +1337,8 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
                     }
                     s.pf[0][k] = acc;
                 }
-                if (warp == 0) {
-                    double2 t[4];
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) t[r] = make_double2(0.0, 0.0);
-                    for (int j = lane; j < nc; j += 32) {
-                        const double2 xv = s.px[0][j];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            const double bb = __ldg(&P.ops.tau_psi[(size_t)r * nc + j]);
-                            t[r].x = fma(bb, xv.x, t[r].x);
-                            t[r].y = fma(bb, xv.y, t[r].y);
-                        }
-                    }
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) t[r] = warp_sum(t[r]);
-                    if (lane < 4) s.pf[0][lane] = csub(s.pf[0][lane], t[lane]);
-                }
+                const double2 t = block_rows_dot<4>(s.px[0], nc, P.ops.tau_psi);
+                if (warp == 0 && lane < 4) s.pf[0][lane] = csub(s.pf[0][lane], t);
                 __syncthreads();
             }
         }
@@ -1264,20 +1385,18 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
         if (warp == 2 || warp == 3)
             pair_block_solve<8, PFB>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192, true, warp - 2, 2);
         __syncthreads();
-        if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
-        __syncthreads();
+        block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, 0, nth);
         __syncthreads();
         for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
         __syncthreads();
-        temperature_corrections<1, false>(P, F, s, m, false, 0);
+        temperature_corrections_roles(P, F, s, m);
     } else {
         if (warp == 2 || warp == 3)
             pair_block_solve<8, PFB>(s.tf[0] + 2, s.tw[0], s.tx[0] + 2, nt, F.tBlk + (size_t)m * nbt * 192, true,
                                      warp - 2, 2);
         __syncthreads();
-        if (warp == 2) warp_schur<2>(s.tx[0], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m * 4);
-        __syncthreads();
+        block_schur<2>(s.tx[0], nullptr, nc, P.ops.tau_dir_B, F.tSinv + (size_t)m * 4);
         schur_update<2>(s.tx[0], nc, F.tY + (size_t)m * nt * 2, 0, nth);
         __syncthreads();
     }

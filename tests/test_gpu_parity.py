@@ -298,29 +298,40 @@ def test_steps_match_oracle_fp32_refined_temperature_solve(scheme):
     gpu.close()
 
 
-@pytest.mark.parametrize("n_r,n_phi,E,scheme", [(1025, 768, 1e-6, "CNAB2"), (1025, 768, 1e-6, "SBDF3"),
-                                                (257, 768, 1e-5, "ARS443"), (65, 192, 1e-3, "BPR353")])
-def test_solve_in_one_cta_per_system_equals_one_cta_per_mode(n_r, n_phi, E, scheme):
+@pytest.mark.parametrize("n_r,n_phi,E,scheme,tol", [(1025, 768, 1e-6, "CNAB2", 5e-12), (1025, 768, 1e-6, "SBDF3", 5e-12),
+                                                    (257, 768, 1e-5, "ARS443", 2e-12),
+                                                    (65, 192, 1e-3, "BPR353", 1e-12)])
+def test_solve_in_one_cta_per_system_equals_one_cta_per_mode(n_r, n_phi, E, scheme, tol):
     """Option solve_roles: with explicit buoyancy the solve runs one CTA per
     system (streamfunction; temperature, then the zonal flow for m = 0) instead of
     one per mode -- by default from N_c > 600 (FP32-refined temperature), on
     request below it (FP64 temperature blocks).  With FP64 streamfunction chains
-    (option psi_chain_dd = 0) the arithmetic is the same, so three steps from a
-    state with every field nonzero agree bit for bit."""
-    from paper_1902_07092_gb300.binding import Solver, pizza_set_option
-    Ra = 5.0 * critical_rayleigh(E)
+    (option psi_chain_dd = 0) the two kernels differ only in the order of the
+    Schur step's sums (the whole CTA against one warp), so three steps from a
+    state with every field nonzero agree to the parity bar of the size, and
+    each is that close to the oracle."""
+    from paper_1902_07092_gb300.binding import pizza_set_option
     psi, th, u = random_state(n_r, n_phi, 1e-2, 31, psi_amp=1e-4, u_amp=1e-3)
     out = []
+    ora = None
     for roles in (1, 0):
-        s = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, scheme, 1e-3 * E)
+        s, o = make_pair(n_r, n_phi, E, 5.0, scheme, 1e-3 * E)
+        if ora is None:
+            ora = o
+            ora.set_state(psi, th, u)
+            for _ in range(3):
+                ora.step()
         pizza_set_option(s.ctx, "solve_roles", roles)
         pizza_set_option(s.ctx, "psi_chain_dd", 0)
         s.set_state(th, psi, u)
         s.step(3)
+        e = assert_state_close(s.get_state(), ora.y, tol, oracle=ora)
+        print("solve_roles=%d n_r=%d %s: state %.2e" % (roles, n_r, scheme, e["state"]))
         out.append(s.get_state())
         s.close()
-    for a, b in zip(*out):
-        assert np.array_equal(a, b)
+    d = rel_l2(np.concatenate([np.ravel(x) for x in out[0]]), np.concatenate([np.ravel(x) for x in out[1]]))
+    print("one CTA per system vs per mode n_r=%d: %.2e" % (n_r, d))
+    assert d <= tol
 
 
 @pytest.mark.parametrize("n_r,n_phi", [(129, 384), (257, 768), (513, 1536)])
