@@ -148,8 +148,9 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *   "solve_roles" with explicit buoyancy, the implicit solve in one CTA per
  *            system (streamfunction; temperature, then the zonal flow for m = 0)
  *            instead of one per mode: 1 always, 0 never, -1 (default) from
- *            N_c > 600, where it fits two CTAs per SM.  The same arithmetic
- *            either way (bitwise equal results);
+ *            N_c > 600, where it fits two CTAs per SM.  The same operations
+ *            but for the order of the Schur steps' sums (the whole CTA against
+ *            one warp): results agree to the accuracy of the refined solve;
  *   "psi_chain_dd" in that kernel, the block chains of the streamfunction
  *            solve (Appendix A's banded block) in double-float arithmetic on the
  *            FP32 pipe (about 48 significant bits; the Schur step, residual and
@@ -287,8 +288,10 @@ int pizza_nusselt_end(pizza_ctx *ctx, double *sum, int *steps);
  * or four per shared-memory pass, 128/256/512 threads in the azimuthal kernel --
  * and, with explicit buoyancy and tau rows, the implicit solve with one CTA per
  * mode and with one per system (option "solve_roles"), and keeps the fastest
- * for later steps.  The choices change the schedule, not the arithmetic: results
- * are bitwise the same.  *nb_r and *phi_threads (may be NULL) receive the
+ * for later steps.  The launch shapes change the schedule, not the arithmetic
+ * (bitwise the same results); the solve arrangement changes the order of the
+ * Schur steps' sums, so results agree to the accuracy of the refined solve.
+ * *nb_r and *phi_threads (may be NULL) receive the
  * explicit-stage choice.  Integration formulation only; builds the factored
  * operators if the context has not stepped yet. */
 int pizza_autotune(pizza_ctx *ctx, int *nb_r, int *phi_threads);

@@ -441,20 +441,27 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         for (int d = 0; d < 9; ++d) bu8[(size_t)k * 17 + d + 4] = bu[(size_t)k * 9 + d];
     if (!block_lu_twisted(bu8, nc, 8, 2, ub)) return fail(ctx, PIZZA_EINVAL, "zonal-flow tau system singular");
     UPLOAD(F.pBlk, double2, hpK);
-    {
-        // double-float copy: the nearest float and the float nearest the remainder
-        std::vector<float4> hpKd(hpK.size());
-        for (size_t i = 0; i < hpK.size(); ++i) {
-            const double re = hpK[i].x, im = hpK[i].y;
+    // double-float copies: the nearest float and the float nearest the remainder
+    auto to_dd = [](const std::vector<double2>& v) {
+        std::vector<float4> d(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            const double re = v[i].x, im = v[i].y;
             const float rh = (float)re, ih = (float)im;
-            hpKd[i] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+            d[i] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
         }
-        UPLOAD(F.pBlkDD, float4, hpKd);
+        return d;
+    };
+    {
+        const std::vector<float4> hd = to_dd(hpK);
+        UPLOAD(F.pBlkDD, float4, hd);
     }
     F.psplit = psplit ? 1 : 0;
     if (psplit) {
         UPLOAD(F.pSpk, double2, hpSpk);
         UPLOAD(F.pRj, double2, hpRj);
+        const std::vector<float4> sd = to_dd(hpSpk), rd = to_dd(hpRj);
+        UPLOAD(F.pSpkDD, float4, sd);
+        UPLOAD(F.pRjDD, float4, rd);
     }
     UPLOAD(F.pY, double2, hpY);
     UPLOAD(F.pSinv, double2, hpS);

@@ -358,6 +358,232 @@ __device__ void pair_block_solve(const TB* b, TX* Z, TB* x, int n, const TF* __r
     pair_sync(bar);
 }
 
+// The same two-sided solve split into phases for a CTA whose other warps can
+// help (the kernel with one CTA per system).  The pair's walks each read one
+// matrix per block -- [0] forward, [2] backward -- so the same registers prefetch
+// PF blocks ahead with PF twice as large; the products W_k = [1]_k Z_k, which no
+// chain depends on, are formed between the walks by every warp of the CTA:
+//   chain_forward (pair)  -> barrier -> chain_middle (pair) -> barrier ->
+//   chain_diag (CTA, Z_k := W_k in place for k != c) -> barrier ->
+//   chain_backward (pair), x_k = W_k - [2]_k x_prev.
+// Geometry as in pair_block_solve: blocks of H rows, middle block c = nb/2,
+// half 0 walks 0..c-1, half 1 nb-1..c+1.  b, Z and x hold the chain type (no
+// conversions on the dependent path).
+template <int H>
+struct ChainGeom {
+    int nb, cm, dir, len, k_fw, k_bw;
+    __device__ ChainGeom(int n, int half) {
+        nb = (n + H - 1) / H;
+        cm = nb / 2;
+        dir = half ? -1 : 1;
+        len = half ? (nb - 1 - cm) : cm;
+        k_fw = half ? nb - 1 : 0;
+        k_bw = half ? cm + 1 : cm - 1;
+    }
+};
+
+template <int H, int PF, class TF, class TX, class TA>
+__device__ void chain_forward(const TX* b, TX* Z, int n, const TF* __restrict__ blk, int half) {
+    constexpr int CPL = H / 4;
+    constexpr int HH = H * H;
+    const int lane = threadIdx.x & 31;
+    const int r = lane >> 2, c = lane & 3;
+    const bool ra = r < H;
+    const ChainGeom<H> g(n, half);
+    auto coef = [&](int k, int q) -> TF { return ra ? blk[(size_t)k * 3 * HH + r * H + c + 4 * q] : zero<TF>(); };
+    TX prev[CPL];
+    TF cur[PF][CPL], nxt[PF][CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) prev[q] = zero<TX>();
+#pragma unroll
+    for (int i = 0; i < PF; ++i)
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) cur[i][q] = (i < g.len) ? coef(g.k_fw + g.dir * i, q) : zero<TF>();
+    for (int i0 = 0; i0 < g.len; i0 += PF) {
+#pragma unroll
+        for (int i = 0; i < PF; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+                nxt[i][q] = (i0 + PF + i < g.len) ? coef(g.k_fw + g.dir * (i0 + PF + i), q) : zero<TF>();
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            if (i0 + i < g.len) {
+                const int k = g.k_fw + g.dir * (i0 + i);
+                const int row = k * H + r;
+                const TX bv = (ra && row < n) ? b[row] : zero<TX>();
+                TA p = zero<TA>();
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) p = fma_x(cur[i][q], prev[q], p);
+                p = reduce4(p);
+                const TX zv = sub_x(bv, p);
+                if (ra && c == 0) Z[row] = zv;
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(zv, 4 * (c + 4 * q));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PF; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) cur[i][q] = nxt[i][q];
+    }
+}
+
+// middle block by both warps of the pair: x_c = S^{-1}(b_c - L_c z_{c-1} - M_c w_{c+1});
+// half 0 stores it, both keep it in prev (the start of their backward walks)
+template <int H, class TF, class TX, class TA>
+__device__ void chain_middle(const TX* b, const TX* Z, TX* x, int n, const TF* __restrict__ blk, int half,
+                             TX (&prev)[H / 4]) {
+    constexpr int CPL = H / 4;
+    constexpr int HH = H * H;
+    const int lane = threadIdx.x & 31;
+    const int r = lane >> 2, c = lane & 3;
+    const ChainGeom<H> g(n, half);
+    const int cm = g.cm, nb = g.nb;
+    auto coef = [&](int which, int q) -> TF { return blk[(size_t)cm * 3 * HH + which * HH + r * H + c + 4 * q]; };
+    TA t = zero<TA>();
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int col = c + 4 * q;
+        if (cm > 0) t = fma_x(coef(0, q), Z[(cm - 1) * H + col], t);
+        if (cm < nb - 1) t = fma_x(coef(2, q), Z[(cm + 1) * H + col], t);
+    }
+    t = reduce4(t);
+    const int row = cm * H + r;
+    const TX bv = (row < n) ? b[row] : zero<TX>();
+    const TX rv = sub_x(bv, t);
+    TX rr[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) rr[q] = shfl_idx(rv, 4 * (c + 4 * q));
+    TA xa = zero<TA>();
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) xa = fma_x(coef(1, q), rr[q], xa);
+    const TX xv = fin(reduce4(xa));
+    if (half == 0 && c == 0 && row < n) x[row] = xv;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(xv, 4 * (c + 4 * q));
+}
+
+// Z_k := [1]_k Z_k for every block k except the middle one, one warp per block
+// (warp w of nw), DU blocks in flight per warp: their coefficient and Z loads are
+// issued together before any product, so the pass costs a few load latencies
+// rather than one per block.  Rows at or beyond n stay untouched.
+constexpr int DU = 4;
+template <int H, class TF, class TX, class TA>
+__device__ void chain_diag(TX* Z, int n, const TF* __restrict__ blk, int w, int nw) {
+    constexpr int CPL = H / 4;
+    constexpr int HH = H * H;
+    const int lane = threadIdx.x & 31;
+    const int r = lane >> 2, c = lane & 3;
+    const int nb = (n + H - 1) / H, cm = nb / 2;
+    for (int k0 = w; k0 < nb; k0 += nw * DU) {
+        TF a[DU][CPL];
+        TX z[DU][CPL];
+#pragma unroll
+        for (int u = 0; u < DU; ++u) {
+            const int k = k0 + u * nw;
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const int col = k * H + c + 4 * q;
+                const bool ok = k < nb && k != cm;
+                a[u][q] = ok ? blk[(size_t)k * 3 * HH + HH + r * H + c + 4 * q] : zero<TF>();
+                z[u][q] = (ok && col < n) ? Z[col] : zero<TX>();
+            }
+        }
+        TX wv[DU];
+#pragma unroll
+        for (int u = 0; u < DU; ++u) {
+            TA t = zero<TA>();
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) t = fma_x(a[u][q], z[u][q], t);
+            wv[u] = fin(reduce4(t));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < DU; ++u) {
+            const int k = k0 + u * nw;
+            const int row = k * H + r;
+            if (k < nb && k != cm && c == 0 && row < n) Z[row] = wv[u];
+        }
+        __syncwarp();
+    }
+}
+
+// backward walk away from the middle block: x_k = W_k - [2]_k x_prev
+template <int H, int PF, class TF, class TX, class TA>
+__device__ void chain_backward(const TX* W, TX* x, int n, const TF* __restrict__ blk, int half, TX (&prev)[H / 4]) {
+    constexpr int CPL = H / 4;
+    constexpr int HH = H * H;
+    const int lane = threadIdx.x & 31;
+    const int r = lane >> 2, c = lane & 3;
+    const bool ra = r < H;
+    const ChainGeom<H> g(n, half);
+    const int bdir = half ? 1 : -1;
+    auto coef = [&](int k, int q) -> TF {
+        return ra ? blk[(size_t)k * 3 * HH + 2 * HH + r * H + c + 4 * q] : zero<TF>();
+    };
+    TF cur[PF][CPL], nxt[PF][CPL];
+#pragma unroll
+    for (int i = 0; i < PF; ++i)
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) cur[i][q] = (i < g.len) ? coef(g.k_bw + bdir * i, q) : zero<TF>();
+    for (int i0 = 0; i0 < g.len; i0 += PF) {
+#pragma unroll
+        for (int i = 0; i < PF; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+                nxt[i][q] = (i0 + PF + i < g.len) ? coef(g.k_bw + bdir * (i0 + PF + i), q) : zero<TF>();
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            if (i0 + i < g.len) {
+                const int k = g.k_bw + bdir * (i0 + i);
+                const int row = k * H + r;
+                TA ph = zero<TA>();
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) ph = fma_x(cur[i][q], prev[q], ph);
+                ph = reduce4(ph);
+                const TX wv = (ra && row < n) ? W[row] : zero<TX>();
+                const TX p = sub_x(wv, ph);
+                if (ra && c == 0 && row < n) x[row] = p;
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(p, 4 * (c + 4 * q));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PF; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) cur[i][q] = nxt[i][q];
+    }
+}
+
+// Whole-CTA driver of the phased solve for up to two systems: system 1 by the
+// warp pair (w1, w1 + 1), system 2 (n2 > 0) by (w2, w2 + 1).  Every thread of the
+// CTA calls it; it ends with a __syncthreads that publishes x and x2.
+template <int PF, class TF, class TX, class TA>
+__device__ void cta_chain_solve(const TX* b, TX* Z, TX* x, int n, const TF* __restrict__ blk, int w1, const TX* b2,
+                                TX* Z2, TX* x2, int n2, const TF* __restrict__ blk2, int w2) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool in1 = warp == w1 || warp == w1 + 1, in2 = n2 > 0 && (warp == w2 || warp == w2 + 1);
+    if (in1) chain_forward<8, PF, TF, TX, TA>(b, Z, n, blk, warp - w1);
+    if (in2) chain_forward<8, PF, TF, TX, TA>(b2, Z2, n2, blk2, warp - w2);
+    __syncthreads();
+    TX prev[2];
+    if (in1) chain_middle<8, TF, TX, TA>(b, Z, x, n, blk, warp - w1, prev);
+    if (in2) chain_middle<8, TF, TX, TA>(b2, Z2, x2, n2, blk2, warp - w2, prev);
+    __syncthreads();
+    chain_diag<8, TF, TX, TA>(Z, n, blk, warp, nw);
+    if (n2 > 0) chain_diag<8, TF, TX, TA>(Z2, n2, blk2, warp, nw);
+    __syncthreads();
+    if (in1) chain_backward<8, PF, TF, TX, TA>(Z, x, n, blk, warp - w1, prev);
+    if (in2) chain_backward<8, PF, TF, TX, TA>(Z2, x2, n2, blk2, warp - w2, prev);
+    __syncthreads();
+}
+
+// Register prefetch depths of the phased chains (one matrix per block step):
+// double-float streamfunction chains 2 blocks (4 measured slower at n_r = 2049:
+// 27 against 19 us per forward walk), FP32 temperature chains 8
+constexpr int PF_CHAIN_DD = 2;
+constexpr int PF_CHAIN_32 = 8;
+
 // Join of the streamfunction block solved in two halves (rows [0, nA) by warps
 // 0-1, [nA, n) by warps 6-7; DevFactors psplit): x holds each half's own solution
 // g.  The interface unknowns, A's last block and B's first, are
@@ -385,6 +611,49 @@ __device__ void split_join(double2* x, int n, int nA, const double2* __restrict_
 #pragma unroll
             for (int c = 0; c < 8; ++c) t = fms(t, __ldg(&row[c]), v[c]);
             x[i] = t;
+        }
+    __syncthreads();
+}
+
+// The same join in double-float arithmetic on the FP32 pipe (double-float
+// chains): x, the spikes and the interface inverse as complex double-floats.  The
+// 16 interface values are summed by 64 threads (four partial sums each, joined
+// by shuffles); the rows go two per thread and pass, loads first.
+__device__ void split_join_dd(ddc* x, int n, int nA, const ddc* __restrict__ spk, const ddc* __restrict__ rj,
+                              bool act) {
+    __shared__ ddc xi[16];
+    const int tid = threadIdx.x;
+    if (act && tid < 64) {
+        const int o = tid >> 2, part = tid & 3;  // output o, columns part*4 .. part*4+3
+        dacc acc = zero<dacc>();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = part * 4 + j;
+            acc = fma_x(rj[o * 16 + c], x[c < 8 ? nA - 8 + c : nA + c - 8], acc);
+        }
+        acc = reduce4(acc);
+        if (part == 0) xi[o] = fin(acc);
+    }
+    __syncthreads();
+    if (act)
+        for (int i0 = tid; i0 < n; i0 += 2 * blockDim.x) {
+            const int i1 = i0 + blockDim.x;
+            ddc s0[8], s1[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                s0[c] = spk[(size_t)i0 * 8 + c];
+                s1[c] = (i1 < n) ? spk[(size_t)i1 * 8 + c] : zero<ddc>();
+            }
+            const ddc* v0 = (i0 < nA) ? xi + 8 : xi;
+            const ddc* v1 = (i1 < nA) ? xi + 8 : xi;
+            dacc a0 = zero<dacc>(), a1 = zero<dacc>();
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                a0 = fma_x(s0[c], v0[c], a0);
+                a1 = fma_x(s1[c], v1[c], a1);
+            }
+            x[i0] = sub_x(x[i0], a0);
+            if (i1 < n) x[i1] = sub_x(x[i1], a1);
         }
     __syncthreads();
 }
@@ -897,9 +1166,8 @@ __device__ void temperature_corrections_roles(const StepParams& P, const DevFact
     for (int it = 0; it < F.ir_t; ++it) {
         temperature_residual_block(P, F, s, m0);
         __syncthreads();
-        if (warp == 2 || warp == 3)
-            pair_block_solve<8, PFB>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2, 2);
-        __syncthreads();
+        cta_chain_solve<PF_CHAIN_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192,
+                                                             2, nullptr, nullptr, nullptr, 0, nullptr, 0);
         block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
         __syncthreads();
@@ -1197,9 +1465,18 @@ __device__ void epilogue_row_psi(const StepParams& P, const RhsSpec& R, double g
     const double mu = (double)m * m;
     double2 mp = make_double2(0.0, 0.0);
     if (m > 0 && k >= 4) {
-        const double2 a0 = band_row_c<8>(P.ops.band[OP_A0], xp, k, nc);
-        const double2 a2 = band_row_c<8>(P.ops.band[OP_A2], xp, k, nc);
-        mp = make_double2(fma(mu, a2.x, a0.x), fma(mu, a2.y, a0.y));
+        // A^I_m = A0 + m^2 A2 assembled tap by tap: three FMAs a tap instead of four
+        const double* r0 = P.ops.band[OP_A0] + (size_t)k * 17;
+        const double* r2 = P.ops.band[OP_A2] + (size_t)k * 17;
+#pragma unroll
+        for (int d = 0; d < 17; ++d) {
+            const int n = k - 8 + d;
+            if (n >= 0 && n < nc) {
+                const double c = fma(mu, __ldg(&r2[d]), __ldg(&r0[d]));
+                mp.x = fma(c, xp[n].x, mp.x);
+                mp.y = fma(c, xp[n].y, mp.y);
+            }
+        }
     }
     const size_t idx = (size_t)m * nc + k;
     if (want_imp) {  // before any store: an output may be one of the terms of f
@@ -1276,17 +1553,26 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
             }
             return;
         }
-        for (int n = tid; n < nc; n += nth) {
-            double2 ap = make_double2(0.0, 0.0);
+        // two rows per thread and pass: twice the loads in flight
+        for (int n0 = tid; n0 < nc; n0 += 2 * nth) {
+            const int n1 = n0 + nth;
+            double2 a0 = make_double2(0.0, 0.0), a1 = a0;
 #pragma unroll 4
             for (int t = 0; t < R.nterms; ++t) {
                 const double c = R.t[t].c;
-                const double2 vp = R.t[t].v.psi[(size_t)m * nc + n];
-                ap.x = fma(c, vp.x, ap.x);
-                ap.y = fma(c, vp.y, ap.y);
+                const double2 v0 = R.t[t].v.psi[(size_t)m * nc + n0];
+                const double2 v1 = (n1 < nc) ? R.t[t].v.psi[(size_t)m * nc + n1] : make_double2(0.0, 0.0);
+                a0.x = fma(c, v0.x, a0.x);
+                a0.y = fma(c, v0.y, a0.y);
+                a1.x = fma(c, v1.x, a1.x);
+                a1.y = fma(c, v1.y, a1.y);
             }
-            s.pf[0][n] = (n < 4) ? make_double2(0.0, 0.0) : ap;
-            s.fp[n] = s.pf[0][n];
+            s.pf[0][n0] = (n0 < 4) ? make_double2(0.0, 0.0) : a0;
+            s.fp[n0] = s.pf[0][n0];
+            if (n1 < nc) {
+                s.pf[0][n1] = (n1 < 4) ? make_double2(0.0, 0.0) : a1;
+                s.fp[n1] = s.pf[0][n1];
+            }
         }
         __syncthreads();
         const double2* blk = F.pBlk + (size_t)m * nbp * 192;
@@ -1305,12 +1591,12 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
                 ddc* xd = reinterpret_cast<ddc*>(x);
                 for (int n = 4 + tid; n < nc; n += nth) bd[n] = dd_from(s.pf[0][n]);
                 __syncthreads();
-                if (warp < 2)
-                    pair_block_solve<8, PFB, ddc, ddc, dacc>(bd + 4, zd, xd + 4, F.psplit ? nA : np, blkd, true, warp, 1);
-                else if (warp >= 6 && F.psplit)
-                    pair_block_solve<8, PFB, ddc, ddc, dacc>(bd + 4 + nA, zd + nA, xd + 4 + nA, np - nA,
-                                                             blkd + (size_t)(nbp / 2) * 192, true, warp - 6, 4);
-                __syncthreads();
+                cta_chain_solve<PF_CHAIN_DD, ddc, ddc, dacc>(bd + 4, zd, xd + 4, F.psplit ? nA : np, blkd, 0, bd + 4 + nA,
+                                                             zd + nA, xd + 4 + nA, F.psplit ? np - nA : 0,
+                                                             blkd + (size_t)(nbp / 2) * 192, 6);
+                if (F.psplit)
+                    split_join_dd(xd + 4, np, nA, reinterpret_cast<const ddc*>(F.pSpkDD) + (size_t)m * np * 8,
+                                  reinterpret_cast<const ddc*>(F.pRjDD) + (size_t)m * 256, true);
                 for (int n = 4 + tid; n < nc; n += nth) x[n] = dd_to(xd[n]);
             } else {
                 if (warp < 2)
@@ -1320,7 +1606,7 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
                                              blk + (size_t)(nbp / 2) * 192, true, warp - 6, 4);
             }
             __syncthreads();
-            if (F.psplit)
+            if (!DDP && F.psplit)
                 split_join(x + 4, np, nA, F.pSpk + (size_t)m * np * 8, F.pRj + (size_t)m * 256, true);
             block_schur<4>(x, it ? s.pf[0] : nullptr, nc, P.ops.tau_psi_B, F.pSinv + (size_t)m * 16);
             schur_update<4>(x, nc, F.pY + (size_t)m * np * 4, 0, nth);
@@ -1365,26 +1651,37 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
     s.uf = d64;
     s.ux = d64 + b;
     const int nbt = (nt + 7) / 8;
-    for (int n = tid; n < nc; n += nth) {
-        double2 at = make_double2(0.0, 0.0);
-        double au = 0.0;
+    for (int n0 = tid; n0 < nc; n0 += 2 * nth) {  // two rows per thread and pass
+        const int n1 = n0 + nth;
+        double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+        double u0 = 0.0, u1 = 0.0;
 #pragma unroll 4
         for (int t = 0; t < R.nterms; ++t) {
             const double c = R.t[t].c;
-            const double2 vt = R.t[t].v.th[(size_t)m * nc + n];
-            at.x = fma(c, vt.x, at.x);
-            at.y = fma(c, vt.y, at.y);
-            if (m == 0) au = fma(c, R.t[t].v.u[n], au);
+            const double2 v0 = R.t[t].v.th[(size_t)m * nc + n0];
+            const double2 v1 = (n1 < nc) ? R.t[t].v.th[(size_t)m * nc + n1] : make_double2(0.0, 0.0);
+            a0.x = fma(c, v0.x, a0.x);
+            a0.y = fma(c, v0.y, a0.y);
+            a1.x = fma(c, v1.x, a1.x);
+            a1.y = fma(c, v1.y, a1.y);
+            if (m == 0) {
+                u0 = fma(c, R.t[t].v.u[n0], u0);
+                if (n1 < nc) u1 = fma(c, R.t[t].v.u[n1], u1);
+            }
         }
-        s.tf[0][n] = (n < 2) ? make_double2(0.0, 0.0) : at;
-        if (F.ir_t) s.tr[n] = to_f2(s.tf[0][n]);
-        if (m == 0) s.uf[n] = (n < 2) ? 0.0 : au;
+        s.tf[0][n0] = (n0 < 2) ? make_double2(0.0, 0.0) : a0;
+        if (F.ir_t) s.tr[n0] = to_f2(s.tf[0][n0]);
+        if (m == 0) s.uf[n0] = (n0 < 2) ? 0.0 : u0;
+        if (n1 < nc) {
+            s.tf[0][n1] = (n1 < 2) ? make_double2(0.0, 0.0) : a1;
+            if (F.ir_t) s.tr[n1] = to_f2(s.tf[0][n1]);
+            if (m == 0) s.uf[n1] = (n1 < 2) ? 0.0 : u1;
+        }
     }
     __syncthreads();
     if (F.ir_t) {
-        if (warp == 2 || warp == 3)
-            pair_block_solve<8, PFB>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192, true, warp - 2, 2);
-        __syncthreads();
+        cta_chain_solve<PF_CHAIN_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192,
+                                                             2, nullptr, nullptr, nullptr, 0, nullptr, 0);
         block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, 0, nth);
         __syncthreads();

@@ -61,9 +61,9 @@ struct DevFactors {
     // the inverse of the interface system [[I, V_last], [W_first, I]]
     int psplit;
     double2 *pSpk, *pRj;
-    // the same blocks as complex double-floats [re.hi, re.lo, im.hi, im.lo] for
-    // the double-float chains (option psi_chain_dd)
-    float4* pBlkDD;
+    // the same blocks, spikes and interface inverses as complex double-floats
+    // [re.hi, re.lo, im.hi, im.lo] for the double-float chains (option psi_chain_dd)
+    float4 *pBlkDD, *pSpkDD, *pRjDD;
     // temperature, real, blocks of H = 8 rows (band half width 4, padded): blocks
     // [M][nb_t][3][64], nb_t = ceil(n_t/8), Y [M][n_t][2], Sinv [M][4],
     // assembled rows 2..nc-1 of D^I - gamma dt F^I_m/Pr [M][n_t][9]

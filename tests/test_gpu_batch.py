@@ -1,6 +1,8 @@
-"""Batches in one CUDA graph and the autotuner: both change the schedule, not
-the arithmetic, so the states must equal those of contexts stepped one by one,
-bit for bit."""
+"""Batches in one CUDA graph and the autotuner's explicit-stage launch shapes:
+both change the schedule, not the arithmetic, so the states must equal those of
+contexts stepped one by one, bit for bit.  The autotuner's other choice, the
+solve with one CTA per mode or per system, sums the Schur steps in another order:
+there the states agree to the accuracy of the solve."""
 import numpy as np
 import pytest
 
@@ -66,14 +68,16 @@ def test_autotuned_launch_shapes_do_not_change_results():
         a.step(4)
         ref.append(a.get_state())
         a.close()
+    from tests.parity_util import rel_l2
     for k, run in enumerate(RUNS[:3] + RUNS[4:]):
         a, st = _make(k, run)
         nb, th = a.autotune()
         assert nb in (1, 2, 4) and th in (128, 256, 512)
         a.set_state(*st)
         a.step(4)
-        for x, y in zip(a.get_state(), ref[k]):
-            assert np.array_equal(x, y)
+        got = a.get_state()
+        d = rel_l2(np.concatenate([np.ravel(x) for x in got]), np.concatenate([np.ravel(x) for x in ref[k]]))
+        assert d <= 1e-13, (k, d)
         a.close()
 
 
