@@ -204,6 +204,20 @@ __device__ __forceinline__ ddc shfl_idx<ddc>(ddc v, int src) {
 }
 __device__ __forceinline__ ddc cvt_to(ddc v, const ddc*) { return v; }
 
+// Asynchronous 16-byte copies global -> shared (cp.async), committed in groups;
+// cp_async_wait<N> returns when at most N of the calling thread's groups are
+// still in flight.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() { cp_async_wait<1>(); }
+
 // Blocks of coefficients prefetched ahead in the chains.  With a few CTAs per SM
 // (N_c up to ~600) two blocks cover the L2 latency at little register cost; the
 // large systems run one CTA per SM (shared memory) with their factors streamed
@@ -382,50 +396,57 @@ struct ChainGeom {
     }
 };
 
-template <int H, int PF, class TF, class TX, class TA>
-__device__ void chain_forward(const TX* b, TX* Z, int n, const TF* __restrict__ blk, int half) {
+// Coefficients of a walk come through a ring of D matrices in shared memory
+// (ring: D * H * H entries per warp), filled by asynchronous copies D blocks
+// ahead: a copy in flight holds no register and no scoreboard, so the walk keeps
+// D loads outstanding whatever its own latency.  Step i waits for its block's
+// group, reads the lane's coefficients, and refills the slot with block i + D
+// once every lane has read it.
+template <int H, int D, class TF>
+__device__ __forceinline__ void ring_issue(const TF* __restrict__ blk, TF* ring, int k, int which, int slot,
+                                           bool valid) {
+    constexpr int HH = H * H;
+    constexpr int CH = HH * (int)sizeof(TF) / 16;  // 16-byte chunks of one matrix
+    const int lane = threadIdx.x & 31;
+    if (valid) {
+        const char* src = reinterpret_cast<const char*>(blk + (size_t)k * 3 * HH + which * HH);
+        char* dst = reinterpret_cast<char*>(ring + slot * HH);
+        for (int j = lane; j < CH; j += 32) cp_async16(dst + 16 * j, src + 16 * j);
+    }
+    cp_async_commit();
+}
+
+template <int H, int D, class TF, class TX, class TA>
+__device__ void chain_forward(const TX* b, TX* Z, int n, const TF* __restrict__ blk, int half, TF* ring) {
     constexpr int CPL = H / 4;
     constexpr int HH = H * H;
     const int lane = threadIdx.x & 31;
     const int r = lane >> 2, c = lane & 3;
-    const bool ra = r < H;
     const ChainGeom<H> g(n, half);
-    auto coef = [&](int k, int q) -> TF { return ra ? blk[(size_t)k * 3 * HH + r * H + c + 4 * q] : zero<TF>(); };
+#pragma unroll
+    for (int i = 0; i < D; ++i) ring_issue<H, D>(blk, ring, g.k_fw + g.dir * i, 0, i, i < g.len);
     TX prev[CPL];
-    TF cur[PF][CPL], nxt[PF][CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) prev[q] = zero<TX>();
+    for (int i = 0; i < g.len; ++i) {
+        const int k = g.k_fw + g.dir * i;
+        const int row = k * H + r;
+        const TX bv = (row < n) ? b[row] : zero<TX>();
+        cp_async_wait<D - 1>();
+        __syncwarp();
+        const TF* mat = ring + (i % D) * HH;
+        TA p = zero<TA>();
 #pragma unroll
-    for (int i = 0; i < PF; ++i)
+        for (int q = 0; q < CPL; ++q) p = fma_x(mat[r * H + c + 4 * q], prev[q], p);
+        __syncwarp();  // every lane has read the slot
+        ring_issue<H, D>(blk, ring, g.k_fw + g.dir * (i + D), 0, i % D, i + D < g.len);
+        p = reduce4(p);
+        const TX zv = sub_x(bv, p);
+        if (c == 0) Z[row] = zv;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) cur[i][q] = (i < g.len) ? coef(g.k_fw + g.dir * i, q) : zero<TF>();
-    for (int i0 = 0; i0 < g.len; i0 += PF) {
-#pragma unroll
-        for (int i = 0; i < PF; ++i)
-#pragma unroll
-            for (int q = 0; q < CPL; ++q)
-                nxt[i][q] = (i0 + PF + i < g.len) ? coef(g.k_fw + g.dir * (i0 + PF + i), q) : zero<TF>();
-#pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            if (i0 + i < g.len) {
-                const int k = g.k_fw + g.dir * (i0 + i);
-                const int row = k * H + r;
-                const TX bv = (ra && row < n) ? b[row] : zero<TX>();
-                TA p = zero<TA>();
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) p = fma_x(cur[i][q], prev[q], p);
-                p = reduce4(p);
-                const TX zv = sub_x(bv, p);
-                if (ra && c == 0) Z[row] = zv;
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(zv, 4 * (c + 4 * q));
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PF; ++i)
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) cur[i][q] = nxt[i][q];
+        for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(zv, 4 * (c + 4 * q));
     }
+    cp_async_wait<0>();
 }
 
 // middle block by both warps of the pair: x_c = S^{-1}(b_c - L_c z_{c-1} - M_c w_{c+1});
@@ -509,62 +530,51 @@ __device__ void chain_diag(TX* Z, int n, const TF* __restrict__ blk, int w, int 
 }
 
 // backward walk away from the middle block: x_k = W_k - [2]_k x_prev
-template <int H, int PF, class TF, class TX, class TA>
-__device__ void chain_backward(const TX* W, TX* x, int n, const TF* __restrict__ blk, int half, TX (&prev)[H / 4]) {
+template <int H, int D, class TF, class TX, class TA>
+__device__ void chain_backward(const TX* W, TX* x, int n, const TF* __restrict__ blk, int half, TX (&prev)[H / 4],
+                               TF* ring) {
     constexpr int CPL = H / 4;
     constexpr int HH = H * H;
     const int lane = threadIdx.x & 31;
     const int r = lane >> 2, c = lane & 3;
-    const bool ra = r < H;
     const ChainGeom<H> g(n, half);
     const int bdir = half ? 1 : -1;
-    auto coef = [&](int k, int q) -> TF {
-        return ra ? blk[(size_t)k * 3 * HH + 2 * HH + r * H + c + 4 * q] : zero<TF>();
-    };
-    TF cur[PF][CPL], nxt[PF][CPL];
 #pragma unroll
-    for (int i = 0; i < PF; ++i)
+    for (int i = 0; i < D; ++i) ring_issue<H, D>(blk, ring, g.k_bw + bdir * i, 2, i, i < g.len);
+    for (int i = 0; i < g.len; ++i) {
+        const int k = g.k_bw + bdir * i;
+        const int row = k * H + r;
+        const TX wv = (row < n) ? W[row] : zero<TX>();
+        cp_async_wait<D - 1>();
+        __syncwarp();
+        const TF* mat = ring + (i % D) * HH;
+        TA ph = zero<TA>();
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) cur[i][q] = (i < g.len) ? coef(g.k_bw + bdir * i, q) : zero<TF>();
-    for (int i0 = 0; i0 < g.len; i0 += PF) {
+        for (int q = 0; q < CPL; ++q) ph = fma_x(mat[r * H + c + 4 * q], prev[q], ph);
+        __syncwarp();
+        ring_issue<H, D>(blk, ring, g.k_bw + bdir * (i + D), 2, i % D, i + D < g.len);
+        ph = reduce4(ph);
+        const TX p = sub_x(wv, ph);
+        if (c == 0 && row < n) x[row] = p;
 #pragma unroll
-        for (int i = 0; i < PF; ++i)
-#pragma unroll
-            for (int q = 0; q < CPL; ++q)
-                nxt[i][q] = (i0 + PF + i < g.len) ? coef(g.k_bw + bdir * (i0 + PF + i), q) : zero<TF>();
-#pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            if (i0 + i < g.len) {
-                const int k = g.k_bw + bdir * (i0 + i);
-                const int row = k * H + r;
-                TA ph = zero<TA>();
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) ph = fma_x(cur[i][q], prev[q], ph);
-                ph = reduce4(ph);
-                const TX wv = (ra && row < n) ? W[row] : zero<TX>();
-                const TX p = sub_x(wv, ph);
-                if (ra && c == 0 && row < n) x[row] = p;
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(p, 4 * (c + 4 * q));
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PF; ++i)
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) cur[i][q] = nxt[i][q];
+        for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(p, 4 * (c + 4 * q));
     }
+    cp_async_wait<0>();
 }
 
 // Whole-CTA driver of the phased solve for up to two systems: system 1 by the
-// warp pair (w1, w1 + 1), system 2 (n2 > 0) by (w2, w2 + 1).  Every thread of the
-// CTA calls it; it ends with a __syncthreads that publishes x and x2.
-template <int PF, class TF, class TX, class TA>
+// warp pair (w1, w1 + 1), system 2 (n2 > 0) by (w2, w2 + 1).  ring: shared memory
+// for 4 x D matrices (one ring per walking warp: system 1's pair first).  Every
+// thread of the CTA calls it; it ends with a __syncthreads that publishes x, x2.
+template <int D, class TF, class TX, class TA>
 __device__ void cta_chain_solve(const TX* b, TX* Z, TX* x, int n, const TF* __restrict__ blk, int w1, const TX* b2,
-                                TX* Z2, TX* x2, int n2, const TF* __restrict__ blk2, int w2) {
+                                TX* Z2, TX* x2, int n2, const TF* __restrict__ blk2, int w2, TF* ring) {
+    constexpr int HH = 64;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool in1 = warp == w1 || warp == w1 + 1, in2 = n2 > 0 && (warp == w2 || warp == w2 + 1);
-    if (in1) chain_forward<8, PF, TF, TX, TA>(b, Z, n, blk, warp - w1);
-    if (in2) chain_forward<8, PF, TF, TX, TA>(b2, Z2, n2, blk2, warp - w2);
+    TF* my_ring = ring + (in1 ? warp - w1 : 2 + warp - w2) * D * HH;
+    if (in1) chain_forward<8, D, TF, TX, TA>(b, Z, n, blk, warp - w1, my_ring);
+    if (in2) chain_forward<8, D, TF, TX, TA>(b2, Z2, n2, blk2, warp - w2, my_ring);
     __syncthreads();
     TX prev[2];
     if (in1) chain_middle<8, TF, TX, TA>(b, Z, x, n, blk, warp - w1, prev);
@@ -573,16 +583,15 @@ __device__ void cta_chain_solve(const TX* b, TX* Z, TX* x, int n, const TF* __re
     chain_diag<8, TF, TX, TA>(Z, n, blk, warp, nw);
     if (n2 > 0) chain_diag<8, TF, TX, TA>(Z2, n2, blk2, warp, nw);
     __syncthreads();
-    if (in1) chain_backward<8, PF, TF, TX, TA>(Z, x, n, blk, warp - w1, prev);
-    if (in2) chain_backward<8, PF, TF, TX, TA>(Z2, x2, n2, blk2, warp - w2, prev);
+    if (in1) chain_backward<8, D, TF, TX, TA>(Z, x, n, blk, warp - w1, prev, my_ring);
+    if (in2) chain_backward<8, D, TF, TX, TA>(Z2, x2, n2, blk2, warp - w2, prev, my_ring);
     __syncthreads();
 }
 
-// Register prefetch depths of the phased chains (one matrix per block step):
-// double-float streamfunction chains 2 blocks (4 measured slower at n_r = 2049:
-// 27 against 19 us per forward walk), FP32 temperature chains 8
-constexpr int PF_CHAIN_DD = 2;
-constexpr int PF_CHAIN_32 = 8;
+// Ring depths of the phased chains: double-float streamfunction chains 6
+// matrices (1 KB each) per walking warp, FP32 temperature chains 8 (256 bytes)
+constexpr int RD_DD = 6;
+constexpr int RD_32 = 8;
 
 // Join of the streamfunction block solved in two halves (rows [0, nA) by warps
 // 0-1, [nA, n) by warps 6-7; DevFactors psplit): x holds each half's own solution
@@ -996,6 +1005,7 @@ struct SolveSmem {
     double2 *pf[2], *pw[2], *px[2], *pd[2], *tf[2], *tw[2], *tx[2];
     double *uf, *ux;
     float2 *tr, *tq, *td;  // refined FP32 temperature solves: residual, chain scratch, correction (MB = 1)
+    float* ring32;         // coefficient rings of the FP32 temperature walks (one CTA per system)
     // the streamfunction and zonal-flow right-hand sides as assembled (pf and uf
     // become residuals), for the epilogue; past the end of solve_smem_doubles,
     // present when the launch adds keep_f_doubles (MB = 1)
@@ -1166,8 +1176,8 @@ __device__ void temperature_corrections_roles(const StepParams& P, const DevFact
     for (int it = 0; it < F.ir_t; ++it) {
         temperature_residual_block(P, F, s, m0);
         __syncthreads();
-        cta_chain_solve<PF_CHAIN_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192,
-                                                             2, nullptr, nullptr, nullptr, 0, nullptr, 0);
+        cta_chain_solve<RD_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, 2,
+                                                      nullptr, nullptr, nullptr, 0, nullptr, 0, s.ring32);
         block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
         __syncthreads();
@@ -1518,11 +1528,16 @@ __device__ void epilogue_row_theta(const StepParams& P, const RhsSpec& R, double
     }
 }
 
-__host__ __device__ inline size_t solve_roles_smem_doubles(int nc) {
-    const int b = round8(nc);
-    // role 0: pf, pw, px, pd, fp (double2); role 1: tf, tx (double2), tr, tq, td
-    // (float2), uf, ux (double) -- the larger of the two
-    return (size_t)2 * b * 5 > (size_t)2 * b * 2 + 3 * b + 2 * b ? (size_t)2 * b * 5 : (size_t)2 * b * 2 + 5 * b;
+// Shared memory of the kernel with one CTA per system, bytes: the larger role.
+// Role 0 with double-float chains: pf, pw, px, fp (double2) and the rings of its
+// four walking warps (RD_DD matrices of complex double-floats each); with FP64
+// chains pf, pw, px, pd, fp.  Role 1: tf, tx (double2), tr, tq, td (float2), uf,
+// ux (double) and the rings of its two walking warps (RD_32 FP32 matrices).
+__host__ __device__ inline size_t solve_roles_smem_bytes(int nc, bool ddp) {
+    const size_t b = (size_t)round8(nc);
+    const size_t psi = ddp ? 4 * b * 16 + 4 * (size_t)RD_DD * 64 * 16 : 5 * b * 16;
+    const size_t th = 2 * b * 16 + 3 * b * 8 + 2 * b * 8 + 2 * (size_t)RD_32 * 64 * 4;
+    return psi > th ? psi : th;
 }
 
 template <bool DDP>
@@ -1543,8 +1558,9 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
         s.pf[0] = sm;
         s.pw[0] = sm + b;
         s.px[0] = sm + 2 * b;
-        s.pd[0] = sm + 3 * b;
-        s.fp = sm + 4 * b;
+        s.pd[0] = DDP ? nullptr : sm + 3 * b;  // double-float chains: the correction in place of the residual
+        s.fp = DDP ? sm + 3 * b : sm + 4 * b;
+        ddc* ring = reinterpret_cast<ddc*>(sm + 4 * b);  // double-float chains only
         if (m == 0) {  // Psi_0 = 0
             for (int n = tid; n < nc; n += nth) {
                 y_out.psi[n] = make_double2(0.0, 0.0);
@@ -1579,21 +1595,23 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
         const ddc* blkd = reinterpret_cast<const ddc*>(F.pBlkDD) + (size_t)m * nbp * 192;
         ddc* zd = reinterpret_cast<ddc*>(s.pw[0]);
         for (int it = 0; it < 2; ++it) {  // solve, then one refinement step
-            double2* x = it ? s.pd[0] : s.px[0];
+            // double-float chains: pass 0 solves into px, pass 1 (the correction)
+            // into pf, over its own right-hand side (the residual): the walks read
+            // a block's right-hand side before they write its solution
+            double2* x = it ? (DDP ? s.pf[0] : s.pd[0]) : s.px[0];
             if constexpr (DDP) {
-                // double-float chains.  The conversions between FP64 and
-                // double-float run on the FP64 pipe, so they happen here for the
-                // whole vector at once, off the chains' dependent path: the
-                // right-hand side into pd (pass 0; the correction fills pd only
-                // later) or in place (pass 1: the residual is not needed after
-                // it), the solution back from double-floats written into x.
-                ddc* bd = reinterpret_cast<ddc*>(it ? s.pf[0] : s.pd[0]);
+                // The conversions between FP64 and double-float run on the FP64
+                // pipe, so they happen here for the whole vector at once, off the
+                // chains' dependent path: the right-hand side in place (f stays in
+                // fp for the residual and the epilogue), the solution back from
+                // double-floats in place.
+                ddc* bd = reinterpret_cast<ddc*>(s.pf[0]);
                 ddc* xd = reinterpret_cast<ddc*>(x);
                 for (int n = 4 + tid; n < nc; n += nth) bd[n] = dd_from(s.pf[0][n]);
                 __syncthreads();
-                cta_chain_solve<PF_CHAIN_DD, ddc, ddc, dacc>(bd + 4, zd, xd + 4, F.psplit ? nA : np, blkd, 0, bd + 4 + nA,
-                                                             zd + nA, xd + 4 + nA, F.psplit ? np - nA : 0,
-                                                             blkd + (size_t)(nbp / 2) * 192, 6);
+                cta_chain_solve<RD_DD, ddc, ddc, dacc>(bd + 4, zd, xd + 4, F.psplit ? nA : np, blkd, 0, bd + 4 + nA, zd + nA,
+                                                       xd + 4 + nA, F.psplit ? np - nA : 0,
+                                                       blkd + (size_t)(nbp / 2) * 192, 6, ring);
                 if (F.psplit)
                     split_join_dd(xd + 4, np, nA, reinterpret_cast<const ddc*>(F.pSpkDD) + (size_t)m * np * 8,
                                   reinterpret_cast<const ddc*>(F.pRjDD) + (size_t)m * 256, true);
@@ -1613,9 +1631,10 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
             __syncthreads();
             if (it == 0) {
                 // residual r = f - L x over the assembled rows, and the tau rows
+                // (whose f is zero)
                 for (int k = 4 + tid; k < nc; k += nth) {
                     const double2* row = F.pBand + ((size_t)m * np + (k - 4)) * 17;
-                    double2 acc = s.pf[0][k];
+                    double2 acc = s.fp[k];
 #pragma unroll
                     for (int d = 0; d < 17; ++d) {
                         const int n = k - 8 + d;
@@ -1624,11 +1643,14 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
                     s.pf[0][k] = acc;
                 }
                 const double2 t = block_rows_dot<4>(s.px[0], nc, P.ops.tau_psi);
-                if (warp == 0 && lane < 4) s.pf[0][lane] = csub(s.pf[0][lane], t);
+                if (warp == 0 && lane < 4) s.pf[0][lane] = make_double2(-t.x, -t.y);
                 __syncthreads();
             }
         }
-        for (int n = tid; n < nc; n += nth) s.px[0][n] = cadd(s.px[0][n], s.pd[0][n]);
+        {
+            const double2* d = DDP ? s.pf[0] : s.pd[0];
+            for (int n = tid; n < nc; n += nth) s.px[0][n] = cadd(s.px[0][n], d[n]);
+        }
         __syncthreads();
         for (int n = tid; n < nc; n += nth) {
             y_out.psi[(size_t)m * nc + n] = s.px[0][n];
@@ -1650,6 +1672,7 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
     double* d64 = reinterpret_cast<double*>(f32 + 3 * b);
     s.uf = d64;
     s.ux = d64 + b;
+    s.ring32 = reinterpret_cast<float*>(d64 + 2 * b);
     const int nbt = (nt + 7) / 8;
     for (int n0 = tid; n0 < nc; n0 += 2 * nth) {  // two rows per thread and pass
         const int n1 = n0 + nth;
@@ -1680,8 +1703,8 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
     }
     __syncthreads();
     if (F.ir_t) {
-        cta_chain_solve<PF_CHAIN_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192,
-                                                             2, nullptr, nullptr, nullptr, 0, nullptr, 0);
+        cta_chain_solve<RD_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192, 2,
+                                                      nullptr, nullptr, nullptr, 0, nullptr, 0, s.ring32);
         block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, 0, nth);
         __syncthreads();
@@ -1766,12 +1789,6 @@ __device__ __forceinline__ double2 shfl_down_x(double2 v) {
 
 // Asynchronous 16-byte global -> shared copies (cp.async): a lane's copies
 // complete at cp.async.wait_group; __syncwarp then publishes them to the warp.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 constexpr int GCH = 32;  // rows of factors staged per chunk
 
@@ -2026,12 +2043,16 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
     // buoyancy one CTA per system (two per mode, two per SM), else the deep chain
     // prefetch (one CTA per SM by shared memory)
     if (!P.buoy_imp && (P.solve_roles > 0 || (P.solve_roles < 0 && F.ir_t))) {
-        const size_t smr = sizeof(double) * solve_roles_smem_doubles(P.nc);
         // double-float streamfunction chains: option psi_chain_dd, by default
         // from N_c > 600 (where the roles kernel is the default)
         const bool ddp = F.pBlkDD && (P.psi_dd > 0 || (P.psi_dd < 0 && F.ir_t));
+        const size_t smr = solve_roles_smem_bytes(P.nc, ddp);
         auto kern = ddp ? k_solve_roles<true> : k_solve_roles<false>;
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        // two CTAs per SM need the largest shared-memory carveout
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
         if (err != cudaSuccess) return err;
         kern<<<2 * slab_modes(P), NTHREADS_S, smr, st>>>(P, rhs, F, y_out, mass_out, imp_out, want_mass ? 1 : 0,
                                                          want_imp ? 1 : 0);
