@@ -151,12 +151,18 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            N_c > 600, where it fits two CTAs per SM.  The same operations
  *            but for the order of the Schur steps' sums (the whole CTA against
  *            one warp): results agree to the accuracy of the refined solve;
- *   "psi_chain_dd" in that kernel, the block chains of the streamfunction
- *            solve (Appendix A's banded block) in double-float arithmetic on the
- *            FP32 pipe (about 48 significant bits; the Schur step, residual and
- *            refinement stay FP64): 1 always, 0 never (FP64 chains), -1
- *            (default) from N_c > 600.  Results agree with the FP64 chains to the
- *            accuracy of the refined solve, not bitwise;
+ *   "psi_chain_dd" the block chains of the streamfunction solve (Appendix
+ *            A's banded block) in double-float arithmetic on the FP32 pipe
+ *            (about 48 significant bits; the Schur step, residual and refinement
+ *            stay FP64), explicit buoyancy: 1 always, 0 never (FP64 chains), -1
+ *            (default) from N_c > 64 (at N_c <= 64 the conversions cost more
+ *            than the shorter chains save).  Results agree with the FP64 chains
+ *            to the accuracy of the refined solve, not bitwise;
+ *   "theta_fp32" the temperature systems solved by FP32 block chains and two
+ *            corrections from FP64 residuals (the zonal flow then refined once
+ *            in FP64): 1 always, 0 never (one FP64 solve), -1 (default) from
+ *            N_c > 600, where the FP64 solve alone loses digits.  Changing it
+ *            drops the factored operators (rebuilt at the next step);
  *   "radial_batch" radial transforms batched per shared-memory pass in the
  *            per-mode explicit kernels: 1, 2 or 4, 0 = the default rule (up to
  *            n_r = 513: 4 in FP64, 2 in mixed precision; else 1); "phi_threads" threads of the per-radius azimuthal

@@ -114,6 +114,9 @@ struct pizza_ctx {
     bool coll = false;
     // Galerkin bases for the integration formulation's solves (option "radial" = 2)
     bool gal = false;
+    // temperature solves with FP32 chains and FP64-residual corrections (option
+    // "theta_fp32"): 1 always, 0 never, -1 (default) from N_c > 600
+    int theta32 = -1;
     std::vector<void*> vec_allocs;     // state and work vectors (re-made when the formulation changes)
     std::vector<double> coll_d1_row0;  // d/ds at s_o on grid values
     double* grid_out = nullptr;        // pizza_get_grid staging, 4 x n_r x n_phi
@@ -335,7 +338,7 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
     // FP32 solves reach the accuracy of the FP64 solve there (1e-13 at N_c = 1365,
     // measured on the tau systems), with the chains on the FP32 pipe; the
     // zonal-flow system (one mode) keeps its FP64 refinement.
-    const int ir_t = (nc > 600) ? 2 : 0;
+    const int ir_t = (ctx->theta32 > 0 || (ctx->theta32 < 0 && nc > 600)) ? 2 : 0;
     auto work = [&](int m0, int m1) {
         std::vector<cplx> bp((size_t)nc * 17);
         std::vector<double> bt((size_t)nc * 9);
@@ -1700,6 +1703,16 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
             return fail(ctx, PIZZA_EINVAL, "solve_roles must be -1 (by size), 0 or 1");
         cudaStreamSynchronize(ctx->stream);
         ctx->P.solve_roles = (int)value;
+        ++ctx->epoch;
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "theta_fp32") == 0) {
+        if (value != 0.0 && value != 1.0 && value != -1.0)
+            return fail(ctx, PIZZA_EINVAL, "theta_fp32 must be -1 (by size), 0 or 1");
+        if ((int)value == ctx->theta32) return PIZZA_OK;
+        cudaStreamSynchronize(ctx->stream);
+        free_factors(ctx);  // the temperature factors change form
+        ctx->theta32 = (int)value;
         ++ctx->epoch;
         return PIZZA_OK;
     }

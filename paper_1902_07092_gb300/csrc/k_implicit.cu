@@ -450,10 +450,13 @@ __device__ void chain_forward(const TX* b, TX* Z, int n, const TF* __restrict__ 
 }
 
 // middle block by both warps of the pair: x_c = S^{-1}(b_c - L_c z_{c-1} - M_c w_{c+1});
-// half 0 stores it, both keep it in prev (the start of their backward walks)
+// both keep it in prev (the start of their backward walks) and return the lane's
+// row of it; the caller stores it after a barrier, since x may share its rows
+// with b (the correction solved in place of the residual) and the other warp of
+// the pair reads b_c here
 template <int H, class TF, class TX, class TA>
-__device__ void chain_middle(const TX* b, const TX* Z, TX* x, int n, const TF* __restrict__ blk, int half,
-                             TX (&prev)[H / 4]) {
+__device__ TX chain_middle(const TX* b, const TX* Z, int n, const TF* __restrict__ blk, int half,
+                           TX (&prev)[H / 4]) {
     constexpr int CPL = H / 4;
     constexpr int HH = H * H;
     const int lane = threadIdx.x & 31;
@@ -479,9 +482,19 @@ __device__ void chain_middle(const TX* b, const TX* Z, TX* x, int n, const TF* _
 #pragma unroll
     for (int q = 0; q < CPL; ++q) xa = fma_x(coef(1, q), rr[q], xa);
     const TX xv = fin(reduce4(xa));
-    if (half == 0 && c == 0 && row < n) x[row] = xv;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) prev[q] = shfl_idx(xv, 4 * (c + 4 * q));
+    return xv;
+}
+
+// the middle block's rows of x, by half 0 of the pair (after the barrier that
+// ends the middle phase)
+template <int H, class TX>
+__device__ __forceinline__ void chain_middle_store(TX* x, int n, int half, TX xv) {
+    const int lane = threadIdx.x & 31;
+    const int r = lane >> 2, c = lane & 3;
+    const int row = ((n + H - 1) / H / 2) * H + r;
+    if (half == 0 && c == 0 && row < n) x[row] = xv;
 }
 
 // Z_k := [1]_k Z_k for every block k except the middle one, one warp per block
@@ -577,9 +590,12 @@ __device__ void cta_chain_solve(const TX* b, TX* Z, TX* x, int n, const TF* __re
     if (in2) chain_forward<8, D, TF, TX, TA>(b2, Z2, n2, blk2, warp - w2, my_ring);
     __syncthreads();
     TX prev[2];
-    if (in1) chain_middle<8, TF, TX, TA>(b, Z, x, n, blk, warp - w1, prev);
-    if (in2) chain_middle<8, TF, TX, TA>(b2, Z2, x2, n2, blk2, warp - w2, prev);
+    TX xm = zero<TX>();
+    if (in1) xm = chain_middle<8, TF, TX, TA>(b, Z, n, blk, warp - w1, prev);
+    if (in2) xm = chain_middle<8, TF, TX, TA>(b2, Z2, n2, blk2, warp - w2, prev);
     __syncthreads();
+    if (in1) chain_middle_store<8>(x, n, warp - w1, xm);
+    if (in2) chain_middle_store<8>(x2, n2, warp - w2, xm);
     chain_diag<8, TF, TX, TA>(Z, n, blk, warp, nw);
     if (n2 > 0) chain_diag<8, TF, TX, TA>(Z2, n2, blk2, warp, nw);
     __syncthreads();
@@ -1213,7 +1229,7 @@ __device__ void temperature_corrections(const StepParams& P, const DevFactors& F
     }
 }
 
-template <int MB, bool DEEP>
+template <int MB, bool DEEP, bool DDP = false>
 __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, DevFactors F, VecSet y_out,
                                                       VecSet mass_out, VecSet imp_out, int want_mass,
                                                       int want_imp, int keep_f) {
@@ -1246,6 +1262,9 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
             if (m == 0) au = fma(c, R.t[t].v.u[n], au);
         }
         s.pf[mi][n] = (n < 4 || m == 0) ? make_double2(0.0, 0.0) : ap;
+        // double-float streamfunction chains (explicit buoyancy, MB = 1): the
+        // right-hand side as double-floats in pd, which the correction fills later
+        if (DDP && m > 0) reinterpret_cast<ddc*>(s.pd[0])[n] = dd_from(s.pf[0][n]);
         s.tf[mi][n] = (n < 2) ? make_double2(0.0, 0.0) : at;
         if (F.ir_t) s.tr[n] = to_f2(s.tf[mi][n]);  // MB == 1 with ir_t
         if (m == 0) s.uf[n] = (n < 2) ? 0.0 : au;
@@ -1278,14 +1297,27 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         if (warp < 2) {
             if (do_p) {
                 const bool act = m0 > 0;
-                pair_block_solve<8, PP>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, F.psplit ? nA : np,
-                                    F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
+                if constexpr (DDP)
+                    pair_block_solve<8, PP, ddc, ddc, dacc>(
+                        reinterpret_cast<ddc*>(s.pd[0]) + 4, reinterpret_cast<ddc*>(s.pw[0]),
+                        reinterpret_cast<ddc*>(s.px[0]) + 4, F.psplit ? nA : np,
+                        reinterpret_cast<const ddc*>(F.pBlkDD) + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
+                else
+                    pair_block_solve<8, PP>(s.pf[0] + 4, s.pw[0], s.px[0] + 4, F.psplit ? nA : np,
+                                            F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
             }
         } else if (warp >= 6) {
             if (do_p && F.psplit) {  // the second half of the streamfunction block
                 const bool act = m0 > 0;
-                pair_block_solve<8, PP>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.px[0] + 4 + nA, np - nA,
-                                    F.pBlk + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
+                if constexpr (DDP)
+                    pair_block_solve<8, PP, ddc, ddc, dacc>(
+                        reinterpret_cast<ddc*>(s.pd[0]) + 4 + nA, reinterpret_cast<ddc*>(s.pw[0]) + nA,
+                        reinterpret_cast<ddc*>(s.px[0]) + 4 + nA, np - nA,
+                        reinterpret_cast<const ddc*>(F.pBlkDD) + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act,
+                        warp - 6, 4);
+                else
+                    pair_block_solve<8, PP>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.px[0] + 4 + nA, np - nA,
+                                            F.pBlk + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
             }
         } else if (warp < 4) {
             if (do_t) {
@@ -1302,6 +1334,11 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
                                     3);
         }
         __syncthreads();
+        if (DDP && do_p && m0 > 0) {  // the solution back from double-floats
+            const ddc* xd = reinterpret_cast<const ddc*>(s.px[0]);
+            for (int n = 4 + tid; n < nc; n += nth) s.px[0][n] = dd_to(xd[n]);
+            __syncthreads();
+        }
         if (do_p && F.psplit)
             split_join(s.px[0] + 4, np, nA, F.pSpk + (size_t)(m0 > 0 ? m0 : 0) * np * 8,
                        F.pRj + (size_t)(m0 > 0 ? m0 : 0) * 256, m0 > 0);
@@ -1382,6 +1419,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
             if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), x[n]);
         }
         s.pf[mi][k] = acc;  // the residual replaces the right-hand side
+        if (DDP) reinterpret_cast<ddc*>(s.pf[0])[k] = dd_from(acc);  // in place, as double-floats
     }
     if (warp < MB) {  // tau rows: r = 0 - tau x
         const int m = m0 + warp;
@@ -1407,19 +1445,43 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     __syncthreads();
     if (warp < 2) {
         const bool act = m0 > 0;
-        pair_block_solve<8, PP>(s.pf[0] + 4, s.pw[0], s.pd[0] + 4, F.psplit ? nA : np,
-                            F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
-        if (!F.psplit && act && warp == 0)
-            warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
+        if constexpr (DDP) {
+            pair_block_solve<8, PP, ddc, ddc, dacc>(
+                reinterpret_cast<ddc*>(s.pf[0]) + 4, reinterpret_cast<ddc*>(s.pw[0]), reinterpret_cast<ddc*>(s.pd[0]) + 4,
+                F.psplit ? nA : np, reinterpret_cast<const ddc*>(F.pBlkDD) + (size_t)(act ? m0 : 0) * nbp * 192, act,
+                warp, 1);
+            if (!F.psplit && act) {  // the pair converts its solution back, then warp 0 takes the Schur step
+                const ddc* xd = reinterpret_cast<const ddc*>(s.pd[0]);
+                for (int n = 4 + (tid & 63); n < nc; n += 64) s.pd[0][n] = dd_to(xd[n]);
+                pair_sync(1);
+                if (warp == 0) warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
+            }
+        } else {
+            pair_block_solve<8, PP>(s.pf[0] + 4, s.pw[0], s.pd[0] + 4, F.psplit ? nA : np,
+                                    F.pBlk + (size_t)(act ? m0 : 0) * nbp * 192, act, warp, 1);
+            if (!F.psplit && act && warp == 0)
+                warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
+        }
     } else if (warp >= 6 && F.psplit) {
         const bool act = m0 > 0;
-        pair_block_solve<8, PP>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.pd[0] + 4 + nA, np - nA,
-                            F.pBlk + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
+        if constexpr (DDP)
+            pair_block_solve<8, PP, ddc, ddc, dacc>(
+                reinterpret_cast<ddc*>(s.pf[0]) + 4 + nA, reinterpret_cast<ddc*>(s.pw[0]) + nA,
+                reinterpret_cast<ddc*>(s.pd[0]) + 4 + nA, np - nA,
+                reinterpret_cast<const ddc*>(F.pBlkDD) + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
+        else
+            pair_block_solve<8, PP>(s.pf[0] + 4 + nA, s.pw[0] + nA, s.pd[0] + 4 + nA, np - nA,
+                                    F.pBlk + ((size_t)(act ? m0 : 0) * nbp + nbp / 2) * 192, act, warp - 6, 4);
     } else if (fuse_t && warp < 4) {
         pair_block_solve<8, PT>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, true, warp - 2, 2);
         if (warp == 2) warp_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
     }
     __syncthreads();
+    if (DDP && F.psplit && m0 > 0) {  // the split solution back from double-floats before the join
+        const ddc* xd = reinterpret_cast<const ddc*>(s.pd[0]);
+        for (int n = 4 + tid; n < nc; n += nth) s.pd[0][n] = dd_to(xd[n]);
+        __syncthreads();
+    }
     if (F.psplit) {
         split_join(s.pd[0] + 4, np, nA, F.pSpk + (size_t)(m0 > 0 ? m0 : 0) * np * 8,
                    F.pRj + (size_t)(m0 > 0 ? m0 : 0) * 256, m0 > 0);
@@ -2027,7 +2089,6 @@ size_t smem_solve_mb(const StepParams& P, int MB, bool deep = false) {
 
 cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFactors& F, VecSet y_out,
                          VecSet mass_out, VecSet imp_out, bool want_mass, bool want_imp, cudaStream_t st) {
-    const size_t sm = smem_solve_mb(P, 1, F.ir_t > 0);
     if (F.gal) {
         // the FP64 solve arrays (16 round8(nc) doubles), the staging of the factors
         // (double2 x 2 GCH x 21, double x 2 GCH x 12 twice) and 3 pivot rows
@@ -2042,10 +2103,11 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
     // the systems with FP32-refined temperature solves (N_c > 600): with explicit
     // buoyancy one CTA per system (two per mode, two per SM), else the deep chain
     // prefetch (one CTA per SM by shared memory)
-    if (!P.buoy_imp && (P.solve_roles > 0 || (P.solve_roles < 0 && F.ir_t))) {
+    const bool large = P.nc > 600;
+    if (!P.buoy_imp && (P.solve_roles > 0 || (P.solve_roles < 0 && large))) {
         // double-float streamfunction chains: option psi_chain_dd, by default
         // from N_c > 600 (where the roles kernel is the default)
-        const bool ddp = F.pBlkDD && (P.psi_dd > 0 || (P.psi_dd < 0 && F.ir_t));
+        const bool ddp = F.pBlkDD && (P.psi_dd > 0 || (P.psi_dd < 0 && large));
         const size_t smr = solve_roles_smem_bytes(P.nc, ddp);
         auto kern = ddp ? k_solve_roles<true> : k_solve_roles<false>;
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
@@ -2058,7 +2120,14 @@ cudaError_t launch_solve(const StepParams& P, const RhsSpec& rhs, const DevFacto
                                                          want_imp ? 1 : 0);
         return cudaGetLastError();
     }
-    auto kern = F.ir_t ? k_solve<1, true> : k_solve<1, false>;
+    // one CTA per mode: the deep chain prefetch for the large systems (one CTA per
+    // SM); below N_c = 600 double-float streamfunction chains (option
+    // psi_chain_dd, by default from N_c > 64 with explicit buoyancy: n_r = 129,
+    // 257, 513 solve 47.6 -> 45.4, 87.8 -> 74.2, 335.5 -> 279.3 us; at n_r = 33
+    // the conversions cost more than the chains save, 34.5 -> 36.5 us)
+    const bool ddp = !large && !P.buoy_imp && F.pBlkDD && (P.psi_dd > 0 || (P.psi_dd < 0 && P.nc > 64));
+    auto kern = large ? k_solve<1, true> : (ddp ? k_solve<1, false, true> : k_solve<1, false>);
+    const size_t sm = smem_solve_mb(P, 1, large);
     // the epilogue reads the assembled right-hand sides from shared memory where
     // they fit (up to N_c ~ 1300), else sums the terms again
     int dev = 0, smax = 0;

@@ -152,8 +152,8 @@ struct StepParams {
     // 1 from n_r = 129 (the half-length DCT-I), 0 never, -1 (default) from n_r = 513
     int radial_lean;
     // streamfunction block chains of the solve in double-float arithmetic
-    // (option "psi_chain_dd"): 1 always, 0 never, -1 (default) from N_c > 600,
-    // in the kernel with one CTA per system
+    // (option "psi_chain_dd", explicit buoyancy): 1 always, 0 never, -1
+    // (default) from N_c > 64
     int psi_dd;
     double* cfl_max;
     const double* cfl_ds;  // [n_r] local Gauss-Lobatto spacing

@@ -386,3 +386,58 @@ def test_double_float_streamfunction_chains_match_oracle(n_r, n_phi, E, scheme, 
     d = rel_l2(np.concatenate([np.ravel(x) for x in runs[1]]), np.concatenate([np.ravel(x) for x in runs[0]]))
     print("double-float vs FP64 chains n_r=%d: %.2e" % (n_r, d))
     assert d <= tol
+
+
+@pytest.mark.parametrize("dd,t32", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("n_r,n_phi,E,scheme,tol", [(129, 24, 1e-4, "CNAB2", 1e-12), (257, 24, 1e-5, "ARS443", 2e-12),
+                                                    (513, 24, 1e-5, "SBDF3", 5e-12)])
+def test_one_cta_per_mode_solve_options_match_oracle(n_r, n_phi, E, scheme, tol, dd, t32):
+    """The solve with one CTA per mode below N_c = 600 with options
+    psi_chain_dd = 1 (double-float streamfunction chains, the solution converted
+    back before the Schur steps and the join) and theta_fp32 = 1 (temperature by
+    FP32 chains and two FP64-residual corrections, the zonal flow refined in
+    FP64), alone and together: two steps with every field nonzero against the
+    oracle at the bars of the FP64 solve of the same sizes."""
+    from paper_1902_07092_gb300.binding import pizza_set_option
+    th = inputs.theta_init(n_r, n_phi, 1e-3, 61, cfg=1, m_min=0)
+    psi = inputs.theta_init(n_r, n_phi, 1e-5, 62, cfg=8)
+    psi[0] = 0.0
+    u = inputs.theta_init(n_r, n_phi, 1e-3, 63, cfg=9, m_min=0)[0].real.copy()
+    gpu, ora = make_pair(n_r, n_phi, E, 5.0, scheme, 1e-3 * E)
+    pizza_set_option(gpu.ctx, "solve_roles", 0)
+    pizza_set_option(gpu.ctx, "psi_chain_dd", dd)
+    pizza_set_option(gpu.ctx, "theta_fp32", t32)
+    gpu.set_state(th, psi, u)
+    ora.set_state(psi, th, u)
+    for k in range(2):
+        gpu.step(1)
+        ora.step()
+        e = assert_state_close(gpu.get_state(), ora.y, tol, oracle=ora)
+        print("per-mode solve dd=%d t32=%d n_r=%d %s step %d: %s" % (
+            dd, t32, n_r, scheme, k + 1, {a: "%.2e" % b for a, b in e.items() if a != "_norms"}))
+    gpu.close()
+
+
+def test_solve_with_one_cta_per_system_is_deterministic():
+    """The double-float path of the solve with one CTA per system (n_r = 1025:
+    split streamfunction block, the correction solved in place of its residual,
+    shared-memory coefficient rings; FP32-refined temperature) has no
+    nondeterministic reduction, so repeated runs from one state must agree bit
+    for bit; a race between the warps of a pair (a row read after the other warp
+    stored into it) shows up here as a mismatch."""
+    from paper_1902_07092_gb300.binding import Solver
+    n_r, n_phi, E = 1025, 768, 1e-6
+    Ra = 5.0 * critical_rayleigh(E)
+    psi, th, u = random_state(n_r, n_phi, 1e-2, 71, psi_amp=1e-4, u_amp=1e-3)
+    ref = None
+    for rep in range(4):
+        s = Solver(n_r, n_phi, E, Ra, 1.0, 0.35, "SBDF3", 1e-9)
+        s.set_state(th, psi, u)
+        s.step(3)
+        got = s.get_state()
+        s.close()
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b), rep
