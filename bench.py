@@ -274,11 +274,25 @@ def config_of(args, wl, Ra):
             "l2": "flushed (256 MiB write) between timed steps",
             "parallelism": "replicas" if args.gpus > 1 else "single",
             "precision": ("fp64 throughout (the oracle)" if getattr(args, "impl", "native") == "reference" else
-                          "fp64: radial transforms, state, history, linear couplings and solves in FP64; the "
-                          "azimuthal FFTs and products in double-float (pairs of FP32 words, ~48-bit significands) "
-                          "with the m = 0 means of the products in FP64"
-                          if getattr(args, "precision", "fp64") == "fp64"
+                          precision_label(wl) if getattr(args, "precision", "fp64") == "fp64"
                           else "mixed: FP32 explicit stage, FP64 state/history/couplings/solves")}
+
+
+def precision_label(wl):
+    """What the FP64 path computes in which arithmetic (double-float: pairs of
+    FP32 words, ~48-bit significands, on the FP32 pipe)."""
+    big = wl["n_r"] >= 513 and wl.get("radial", "integration") == "integration"
+    nc = inputs.n_c_of(wl)
+    parts = ["fp64: state, history, field products at each radius, linear couplings, banded applies, "
+             "Schur steps, residuals and refinements in FP64",
+             "azimuthal FFTs and products in double-float with the m = 0 means of the products in FP64"]
+    if big:
+        parts.append("radial DCT-I and derivative scans in double-float (lean layout, n_r >= 513)")
+    if wl.get("radial", "integration") == "integration" and nc > 64:
+        parts.append("block chains of the streamfunction solve in double-float (N_c > 64)")
+    if nc > 600:
+        parts.append("temperature solves by FP32 chains with two FP64-residual corrections (N_c > 600)")
+    return "; ".join(parts)
 
 
 # ------------------------------------------------------------ native arm ----
@@ -497,7 +511,9 @@ def kernel_table(kt, kn, flops, nbytes, hbm_peak):
     for i, k in enumerate(KERNELS):
         us = 1e3 * float(kt[i]) / max(int(kn[i]), 1)
         out[k] = {"launches": int(kn[i]), "avg_us": us, "share": share[k], "gflop_per_launch": flops[k] / 1e9,
-                  "fp64_tflops": flops[k] / (us * 1e-6) / 1e12 if us > 0 else None,
+                  # FP64-grade algorithmic flops per second, whichever pipe ran them
+                  # (the double-float transforms and chains run on the FP32 pipe)
+                  "tflops_algorithmic": flops[k] / (us * 1e-6) / 1e12 if us > 0 else None,
                   "mb_per_launch": nbytes[k] / 1e6,
                   "hbm_frac": nbytes[k] / (us * 1e-6) / 1e9 / hbm_peak if us > 0 else None}
     return out

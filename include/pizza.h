@@ -145,6 +145,13 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            CTAs per SM at n_r = 2049) instead of the batched layout: 1 from
  *            n_r = 129, 0 never, -1 (default) from n_r = 513.  Results agree to
  *            rounding (the DCT-I sums in another order);
+ *   "radial_dd" the DCT-I and Chebyshev derivative scans of the lean radial
+ *            kernels in double-float arithmetic on the FP32 pipe (about 48
+ *            significant bits; loads, stores, field products, banded applies and
+ *            couplings in FP64): 1 always (with the lean layout), 0 never, -1
+ *            (default) with the lean layout's default, from n_r = 513.  Results
+ *            agree with the FP64 transforms to well within the explicit terms'
+ *            FP64 bar, not bitwise;
  *   "solve_roles" with explicit buoyancy, the implicit solve in one CTA per
  *            system (streamfunction; temperature, then the zonal flow for m = 0)
  *            instead of one per mode: 1 always, 0 never, -1 (default) from

@@ -1539,6 +1539,27 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
     P.plan_h.tw = P.plan_r.tw;
     P.plan_h.twf = P.plan_r.twf;
     P.plan_h.tws = 2;
+    {
+        // the radial twiddles as double-float pairs (double-float lean transforms)
+        const int L = 2 * ctx->K;
+        std::vector<float4> dd(L);
+        const long double pi = 3.141592653589793238462643383279502884L;
+        for (int j = 0; j < L; ++j) {
+            const long double a = 2.0L * pi * (long double)j / (long double)L;
+            const long double c = cosl(a), sn = -sinl(a);
+            const float ch = (float)c, sh = (float)sn;
+            dd[j] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(sn - (long double)sh));
+        }
+        float4* dtw = dalloc<float4>(ctx, dd.size(), al);
+        if (!dtw) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(dtw, dd.data(), dd.size() * sizeof(float4));
+        P.plan_r.twdd = dtw;
+        P.plan_h.twdd = dtw;
+    }
+    P.radial_dd = -1;
 
     // m-independent banded operators and tau rows
     HostOps H = host_ops_of(ctx);
@@ -1703,6 +1724,14 @@ int set_option_impl(pizza_ctx* ctx, const char* key, double value) {
             return fail(ctx, PIZZA_EINVAL, "solve_roles must be -1 (by size), 0 or 1");
         cudaStreamSynchronize(ctx->stream);
         ctx->P.solve_roles = (int)value;
+        ++ctx->epoch;
+        return PIZZA_OK;
+    }
+    if (std::strcmp(key, "radial_dd") == 0) {
+        if (value != 0.0 && value != 1.0 && value != -1.0)
+            return fail(ctx, PIZZA_EINVAL, "radial_dd must be -1 (by size), 0 or 1");
+        cudaStreamSynchronize(ctx->stream);
+        ctx->P.radial_dd = (int)value;
         ++ctx->epoch;
         return PIZZA_OK;
     }

@@ -870,6 +870,13 @@ __host__ __device__ inline bool lean_radial(const StepParams& P) {
     return P.radial_lean > 0 || P.K >= LEAN_K;
 }
 
+// double-float radial transforms in the lean kernels (option "radial_dd"):
+// 1 always, 0 never, -1 (default) as the lean layout's own default
+__host__ __device__ inline bool radial_dd(const StepParams& P) {
+    if (!P.plan_r.twdd || P.radial_dd == 0) return false;
+    return P.radial_dd > 0 || P.K >= LEAN_K;
+}
+
 // DCT-I of x_0..x_K in X (K + 1 entries):
 //   C_k = x_0 + (-1)^k x_K + 2 sum_{j=1}^{K-1} x_j cos(pi j k / K),  k = 0..K,
 // by one complex FFT of length K, as dct1_batched: y_j = (x_j + x_{K-j})/2
@@ -951,6 +958,140 @@ __device__ double2* dct1_pair(double2* X, double2* Y, const StepParams& P) {
     }
     __syncthreads();
     return O;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float radial transforms (option "radial_dd", lean layout).  The same
+// DCT-I and derivative scan as dct1_pair and cheb_derivative_scan with complex
+// double-floats (ddfloat.cuh: about 48 significant bits) on the FP32 pipe, which
+// issues 64 times the FP64 rate on GB300; grid and coefficient values cross to
+// and from FP64 at the kernels' loads and stores only.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ ddf dd_shfl_xor(ddf v, int o) {
+    return ddf{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ ddf dd_shfl_up(ddf v, int o) {
+    return ddf{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ ddf dd_shfl_down(ddf v, int o) {
+    return ddf{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ ddc dd_warp_sum(ddc v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x = v.x + dd_shfl_xor(v.x, o);
+        v.y = v.y + dd_shfl_xor(v.y, o);
+    }
+    return v;
+}
+// an integer |k| < 2^24 as a double-float (exact)
+__device__ __forceinline__ ddf dd_int(int k) { return ddf{(float)k, 0.f}; }
+__device__ __forceinline__ ddc dd_scale2c(ddc a, float s) { return ddc{dd_scale2(a.x, s), dd_scale2(a.y, s)}; }
+
+// dct1_pair in double-float: X, Y hold K + 1 (resp. the FFT's K) complex
+// double-floats; the same steps, the C_1 sum and the prefix sums in double-float.
+__device__ ddc* dct1_pair_dd(ddc* X, ddc* Y, const StepParams& P) {
+    const int K = P.plan_h.L, H = K / 2;
+    const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+    const ddc* tw = reinterpret_cast<const ddc*>(P.plan_r.twdd);  // (cos(pi j/K), -sin(pi j/K))
+    __shared__ ddc wsum[NTHREADS_R / 32];
+    __shared__ ddc c1;
+    __syncthreads();
+    ddc acc = ddc{ddf{0.f, 0.f}, ddf{0.f, 0.f}};
+    for (int j = tid; j < H; j += nth) {
+        if (j == 0) {
+            const ddc a = X[0], b = X[K];
+            X[0] = dd_scale2c(cadd(a, b), 0.5f);
+            acc = csub(a, b);
+        } else {
+            const ddc a = X[j], b = X[K - j];
+            const ddc t = ldg_tw(tw + j);
+            const ddf sn = -t.y, cs2 = dd_scale2(t.x, 2.f);
+            const ddc hs = dd_scale2c(cadd(a, b), 0.5f), dif = csub(a, b);
+            X[j] = ddc{hs.x - sn * dif.x, hs.y - sn * dif.y};
+            X[K - j] = ddc{hs.x + sn * dif.x, hs.y + sn * dif.y};
+            acc = ddc{acc.x + cs2 * dif.x, acc.y + cs2 * dif.y};
+        }
+    }
+    acc = dd_warp_sum(acc);
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        ddc t = wsum[0];
+        for (int w = 1; w < nw; ++w) t = cadd(t, wsum[w]);
+        c1 = t;
+    }
+    ddc* F = fft_batched<+1>(X, Y, P.plan_h, 1);  // begins with a barrier
+    ddc* O = (F == X) ? Y : X;
+    for (int k = tid; k <= H; k += nth) O[2 * k] = cadd(F[k], F[k == 0 ? 0 : K - k]);
+    const int chunk = (H + nth - 1) / nth;
+    const int lo = min(tid * chunk, H), hi = min(lo + chunk, H);
+    ddc tot = ddc{ddf{0.f, 0.f}, ddf{0.f, 0.f}};
+    for (int k = max(lo, 1); k < hi; ++k) {
+        const ddc df = csub(F[k], F[K - k]);
+        tot = ddc{tot.x + df.y, tot.y - df.x};
+    }
+    ddc inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const ddf ux = dd_shfl_up(inc.x, o), uy = dd_shfl_up(inc.y, o);
+        if (lane >= o) inc = ddc{inc.x + ux, inc.y + uy};
+    }
+    __syncthreads();
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    ddc run = c1;
+    for (int w = 0; w < warp; ++w) run = cadd(run, wsum[w]);
+    run = cadd(run, csub(inc, tot));
+    for (int k = lo; k < hi; ++k) {
+        if (k > 0) {
+            const ddc df = csub(F[k], F[K - k]);
+            run = ddc{run.x + df.y, run.y - df.x};
+        }
+        O[2 * k + 1] = run;
+    }
+    __syncthreads();
+    return O;
+}
+
+// cheb_derivative_scan in double-float (scale: the x -> s factor, rounded to
+// double-float once)
+__device__ void cheb_derivative_scan_dd(const ddc* c, ddc* d, ddc* tmp, int n, double scale) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const ddc zero = ddc{ddf{0.f, 0.f}, ddf{0.f, 0.f}};
+    if (warp < 2) {
+        const int q = warp;
+        const int len = (n - q + 1) / 2;
+        const int per = (len + 31) / 32;
+        const int i0 = lane * per, i1 = min(i0 + per, len);
+        ddc acc = zero;
+        for (int i = i1 - 1; i >= i0; --i) {
+            const int k = 2 * i + q;
+            if (k > 0) {
+                const ddf f = dd_int(2 * k);
+                acc = ddc{acc.x + f * c[k].x, acc.y + f * c[k].y};
+            }
+            tmp[k] = acc;
+        }
+        ddc sfx = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const ddf x = dd_shfl_down(sfx.x, o), y = dd_shfl_down(sfx.y, o);
+            if (lane + o < 32) sfx = ddc{sfx.x + x, sfx.y + y};
+        }
+        const ddc off = csub(sfx, acc);
+        for (int i = i0; i < i1; ++i) {
+            const int k = 2 * i + q;
+            tmp[k] = cadd(tmp[k], off);
+        }
+    }
+    __syncthreads();
+    const ddf fs = dd_from(scale), f0 = dd_from(0.5 * scale);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const ddf f = (j == 0) ? f0 : fs;
+        d[j] = (j + 1 < n) ? cscale(tmp[j + 1], f) : zero;
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean(StepParams P, VecSet y, double2* __restrict__ G1) {
@@ -1115,6 +1256,192 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean(StepParams 
     }
 }
 
+// k_spec_to_grid_lean with double-float transforms: the coefficients become
+// double-floats when loaded, the series values FP64 again when stored; the
+// field arithmetic at each radius stays FP64.
+__global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean_dd(StepParams P, VecSet y,
+                                                                         double2* __restrict__ G1) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int m = P.m_lo + blockIdx.x;
+    const int K = P.K, N = P.n_r, nc = P.nc, M = P.M;
+    ddc* X = reinterpret_cast<ddc*>(smraw);
+    ddc* C = X + N;
+    ddc* Y = C + N;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const double Cw = P.cnorm, Cw0 = 0.5 * P.cnorm, dm = (double)m;
+    const ddc zero = ddc{ddf{0.f, 0.f}, ddf{0.f, 0.f}};
+    for (int n = tid; n < N; n += nth) {
+        double2 a = make_double2(0.0, 0.0);
+        if (n < nc) {
+            const double w = (n == 0) ? Cw0 : Cw;
+            a = (m > 0) ? cscale(y.psi[(size_t)m * nc + n], w) : make_double2(y.u[n] * w, 0.0);
+        }
+        C[n] = dd_from(a);
+    }
+    __syncthreads();
+    double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
+    __shared__ double red[4 * 32], mx[4];
+    float lam = 1.f;
+    if (m == 0) {  // u_bar and lam u_bar' packed into one transform (lam a power of two)
+        cheb_derivative_scan_dd(C, Y, X, N, P.inv_a);
+        double a0 = 0.0, a1 = 0.0;  // max |u_bar|, max |u_bar'| (leading parts)
+        for (int i = tid; i < N; i += nth) {
+            a0 = fmax(a0, fabs((double)C[i].x.hi) + fabs((double)C[i].y.hi));
+            a1 = fmax(a1, fabs((double)Y[i].x.hi) + fabs((double)Y[i].y.hi));
+        }
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 = fmax(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+            a1 = fmax(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+        }
+        if (lane == 0) {
+            red[warp] = a0;
+            red[32 + warp] = a1;
+        }
+        __syncthreads();
+        if (tid < 2) {
+            double r = 0.0;
+            for (int w = 0; w < (nth >> 5); ++w) r = fmax(r, red[tid * 32 + w]);
+            mx[tid] = r;
+        }
+        __syncthreads();
+        lam = (float)pow2_ratio(mx[0], mx[1]);
+    }
+    const int nf = (m > 0) ? 4 : 2;
+    for (int i = 0; i < nf; ++i) {
+        const int fid = (m > 0) ? i : (i == 0 ? 4 : 3);
+        if (m > 0 && (fid == 1 || fid == 2)) cheb_derivative_scan_dd(C, C, X, N, P.inv_a);  // C <- dC/ds
+        for (int j = tid; j <= K; j += nth) {
+            ddc v;
+            if (fid <= 2)
+                v = C[j];
+            else if (fid == 3)
+                v = (j < nc) ? dd_from(cscale(y.th[(size_t)m * nc + j], (j == 0) ? Cw0 : Cw)) : zero;
+            else
+                v = ddc{C[j].x, dd_scale2(Y[j].x, lam)};
+            X[j] = (j == 0 || j == K) ? dd_scale2c(v, 2.f) : v;
+        }
+        const ddc* Z = dct1_pair_dd(X, Y, P);
+        for (int k = tid; k < N; k += nth) {
+            const double2 g = cscale(dd_to(Z[k]), 0.5);  // value of the series at x_k
+            const double s = P.s[k], h2 = P.h2[k], is = P.inv_s[k];
+            double2* out = G1 + g_index(k, 0, m, M);
+            if (fid == 0) {
+                out[0] = cmul_i(g, dm);
+                out[M] = cscale(g, 3.0 * s);
+                out[2 * M] = cscale(g, 6.0 + dm * dm * h2 * is * is);
+                if (PF) {
+                    const double U = P.pump_ups[k];
+                    PF[k] = cadd(cscale(g, -U * (P.pump_cr[k] + dm * dm)), cmul_i(g, -U * dm * P.pump_ci[k]));
+                }
+            } else if (fid == 1) {
+                out[M] = csub(out[M], cscale(g, h2));
+                out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - 5.0 * s));
+                if (PF) PF[k] = cadd(PF[k], cscale(g, P.pump_ups[k] * 0.5 * s));
+            } else if (fid == 2) {
+                out[2 * M] = csub(out[2 * M], cscale(g, h2));
+                if (PF) PF[k] = csub(PF[k], cscale(out[2 * M], P.pump_ups[k]));
+            } else if (fid == 3) {
+                out[3 * M] = g;
+            } else {
+                out[0] = make_double2(0.0, 0.0);
+                out[M] = make_double2(g.x, 0.0);
+                out[2 * M] = make_double2(g.y / (double)lam + g.x * is, 0.0);
+                if (PF) {
+                    const double w0 = g.y / (double)lam + g.x * is;
+                    PF[k] = make_double2(P.pump_ups[k] * g.x * (1.0 + 0.5 * P.E * w0), 0.0);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// k_grid_to_spec_lean with double-float transforms: grid values become
+// double-floats when loaded, the flux divergence is formed in FP64 at each
+// radius from the double-float derivative, and the analysed coefficients are FP64
+// again (in C, over the double-float data) before the banded applies.
+__global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean_dd(StepParams P, const double2* __restrict__ G2,
+                                                                         VecSet y, VecSet e) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int m = P.m_lo + blockIdx.x;
+    const int K = P.K, N = P.n_r, nc = P.nc, M = P.M;
+    ddc* X = reinterpret_cast<ddc*>(smraw);
+    ddc* C = X + N;
+    ddc* Y = C + N;
+    double2* Cd = reinterpret_cast<double2*>(C);  // the analysed coefficients, FP64
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const double dm = (double)m, hc = 0.5 * P.cnorm;
+    const float iK = 1.f / (float)K, hK = 0.5f / (float)K;  // K a power of two: exact
+    const double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
+    const double bfac = P.Ra / P.Pr * (double)m / P.s_o;
+    for (int fld = 0; fld < 2; ++fld) {
+        ddc* W = X;
+        if (fld == 1 || m > 0) {
+            const int f = (fld == 0) ? 0 : 2;
+            for (int j = tid; j <= K; j += nth) X[j] = dd_from(cscale(G2[g_index(j, f, m, M)], P.h2[j]));
+            const ddc* Z = dct1_pair_dd(X, Y, P);
+            for (int n = tid; n <= K; n += nth) C[n] = dd_scale2c(Z[n], (n == 0 || n == K) ? hK : iK);
+            __syncthreads();
+            cheb_derivative_scan_dd(C, C, X, N, P.inv_a);
+            for (int j = tid; j <= K; j += nth) X[j] = (j == 0 || j == K) ? dd_scale2c(C[j], 2.f) : C[j];
+            const ddc* D = dct1_pair_dd(X, Y, P);
+            W = (D == X) ? Y : X;
+            for (int k = tid; k <= K; k += nth) {
+                const double2 dF = cscale(dd_to(D[k]), 0.5);
+                const double is = P.inv_s[k];
+                double2 val;
+                if (fld == 0) {
+                    val = cscale(cadd(dF, cmul_i(G2[g_index(k, 1, m, M)], dm)), is);
+                    if (PF) val = csub(val, PF[k]);
+                } else {
+                    val = csub(cscale(cadd(dF, cmul_i(G2[g_index(k, 3, m, M)], dm)), is), G2[g_index(k, 2, m, M)]);
+                }
+                W[k] = dd_from(val);
+            }
+        } else {  // N_u = (h^2/s) [v omega]_0 (+ pumping)
+            for (int k = tid; k <= K; k += nth) {
+                double2 val = cscale(G2[g_index(k, 0, m, M)], P.h2[k] * P.inv_s[k]);
+                if (PF) val = cadd(val, PF[k]);
+                W[k] = dd_from(val);
+            }
+        }
+        const ddc* Z = dct1_pair_dd(W, (W == X) ? Y : X, P);
+        const bool buoy = (fld == 0 && m > 0 && !P.buoy_imp);
+        // Z lives in X or Y, never in C: the FP64 coefficients overwrite C
+        for (int n = tid; n < nc; n += nth) {
+            const double2 v = cscale(dd_to(Z[n]), hc);
+            Cd[n] = buoy ? cadd(v, cmul_i(y.th[(size_t)m * nc + n], bfac)) : v;
+        }
+        __syncthreads();
+        for (int k = tid; k < nc; k += nth) {
+            if (fld == 0) {
+                if (m > 0) {
+                    double2 ep = make_double2(0.0, 0.0);
+                    if (k >= 4) ep = band_row<8>(P.ops.band[OP_C], Cd, k, nc);
+                    e.psi[(size_t)m * nc + k] = ep;
+                } else {
+                    e.psi[k] = make_double2(0.0, 0.0);
+                    e.u[k] = (k >= 2) ? -band_row<4>(P.ops.band[OP_D], Cd, k, nc).x : 0.0;
+                }
+            } else {
+                double2 et = make_double2(0.0, 0.0);
+                if (k >= 2) {
+                    const double2 dn = band_row<4>(P.ops.band[OP_D], Cd, k, nc);
+                    if (m > 0) {
+                        const double2 gp = band_row<4>(P.ops.band[OP_G], y.psi + (size_t)m * nc, k, nc);
+                        et = csub(cmul_i(gp, -P.tc * dm), dn);
+                    } else {
+                        et = cscale(dn, -1.0);
+                    }
+                }
+                e.th[(size_t)m * nc + k] = et;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 size_t smem_radial_lean(const StepParams& P) { return sizeof(double2) * 3 * (size_t)P.n_r; }
 
 template <class T>
@@ -1161,9 +1488,10 @@ static cudaError_t grid_to_spec_t(const StepParams& P, const void* G2, VecSet y,
 cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st) {
     if (lean_radial(P)) {
         const size_t sm = smem_radial_lean(P);
-        cudaError_t err = cudaFuncSetAttribute(k_spec_to_grid_lean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        auto kern = radial_dd(P) ? k_spec_to_grid_lean_dd : k_spec_to_grid_lean;
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (err != cudaSuccess) return err;
-        k_spec_to_grid_lean<<<slab_modes(P), NTHREADS_R, sm, st>>>(P, y, G1);
+        kern<<<slab_modes(P), NTHREADS_R, sm, st>>>(P, y, G1);
         return cudaGetLastError();
     }
     return P.fp32 ? spec_to_grid_t<float2>(P, y, G1, st) : spec_to_grid_t<double2>(P, y, G1, st);
@@ -1190,9 +1518,10 @@ cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2*
 cudaError_t launch_grid_to_spec(const StepParams& P, const double2* G2, VecSet y, VecSet e, cudaStream_t st) {
     if (lean_radial(P)) {
         const size_t sm = smem_radial_lean(P);
-        cudaError_t err = cudaFuncSetAttribute(k_grid_to_spec_lean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        auto kern = radial_dd(P) ? k_grid_to_spec_lean_dd : k_grid_to_spec_lean;
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (err != cudaSuccess) return err;
-        k_grid_to_spec_lean<<<slab_modes(P), NTHREADS_R, sm, st>>>(P, G2, y, e);
+        kern<<<slab_modes(P), NTHREADS_R, sm, st>>>(P, G2, y, e);
         return cudaGetLastError();
     }
     return P.fp32 ? grid_to_spec_t<float2>(P, G2, y, e, st) : grid_to_spec_t<double2>(P, G2, y, e, st);

@@ -151,6 +151,9 @@ struct StepParams {
     // FP64 radial kernels in the three-array layout (option "radial_lean"):
     // 1 from n_r = 129 (the half-length DCT-I), 0 never, -1 (default) from n_r = 513
     int radial_lean;
+    // double-float DCT-I and derivative scans in the lean radial kernels (option
+    // "radial_dd"): 1 always, 0 never, -1 (default) from n_r = 513
+    int radial_dd;
     // streamfunction block chains of the solve in double-float arithmetic
     // (option "psi_chain_dd", explicit buoyancy): 1 always, 0 never, -1
     // (default) from N_c > 64

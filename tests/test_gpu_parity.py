@@ -441,3 +441,43 @@ def test_solve_with_one_cta_per_system_is_deterministic():
         else:
             for a, b in zip(got, ref):
                 assert np.array_equal(a, b), rep
+
+
+@pytest.mark.parametrize("n_r,n_phi", [(129, 384), (257, 768), (513, 1536)])
+def test_double_float_lean_radial_transforms_match_oracle(n_r, n_phi):
+    """Option radial_dd = 1 with the lean layout forced: the DCT-I and derivative
+    scans of the synthesis and analysis kernels in double-float arithmetic (the
+    field arithmetic at each radius, the banded applies and the stored values in
+    FP64) give the oracle's explicit terms to the bar of the FP64 transforms,
+    max(1e-12, 4 n_r^2 eps), on states with O(1) fields; and two steps to the
+    step bars of the size."""
+    from paper_1902_07092_gb300.binding import pizza_set_option
+    gpu, ora = make_pair(n_r, n_phi, 1e-3, 2.0, "CNAB2", 1e-4)
+    pizza_set_option(gpu.ctx, "radial_lean", 1)
+    pizza_set_option(gpu.ctx, "radial_dd", 1)
+    psi, th, u = random_state(n_r, n_phi, 1.0, 5, psi_amp=1.0, u_amp=1.0)
+    gpu.set_state(th, psi, u)
+    ep, et, eu = gpu.explicit_terms()
+    rp, rt, ru = explicit_terms(ora.g, psi, th, u)
+    tol = max(1e-12, 4 * n_r * n_r * 2.0 ** -53)
+    errs = (rel_l2(ep, rp), rel_l2(et, rt), rel_l2(eu, ru))
+    print("double-float lean explicit terms n_r=%d: %.2e %.2e %.2e (tol %.1e)" % ((n_r,) + errs + (tol,)))
+    assert max(errs) <= tol
+    gpu.close()
+    # two steps from a small state, against the oracle
+    gpu, ora = make_pair(n_r, 24, 1e-5, 5.0, "SBDF3", 1e-8)
+    pizza_set_option(gpu.ctx, "radial_lean", 1)
+    pizza_set_option(gpu.ctx, "radial_dd", 1)
+    th = inputs.theta_init(n_r, 24, 1e-3, 81, cfg=1, m_min=0)
+    psi = inputs.theta_init(n_r, 24, 1e-5, 82, cfg=8)
+    psi[0] = 0.0
+    u = inputs.theta_init(n_r, 24, 1e-3, 83, cfg=9, m_min=0)[0].real.copy()
+    gpu.set_state(th, psi, u)
+    ora.set_state(psi, th, u)
+    bar = {129: 1e-12, 257: 2e-12, 513: 5e-12}[n_r]
+    for k in range(2):
+        gpu.step(1)
+        ora.step()
+        e = assert_state_close(gpu.get_state(), ora.y, bar, oracle=ora)
+        print("double-float lean n_r=%d step %d: state %.2e" % (n_r, k + 1, e["state"]))
+    gpu.close()
