@@ -339,6 +339,12 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
     // measured on the tau systems), with the chains on the FP32 pipe; the
     // zonal-flow system (one mode) keeps its FP64 refinement.
     const int ir_t = (ctx->theta32 > 0 || (ctx->theta32 < 0 && nc > 600)) ? 2 : 0;
+    // the FP32 temperature block split in two halves like the streamfunction one
+    // (the kernel with one CTA per system walks each half with its own warp pair)
+    const bool tsplit = ir_t && nbt >= 40;
+    const int ntA = 8 * (nbt / 2);
+    std::vector<double> htSpk(tsplit ? (size_t)M * nt * 8 : 0), htRj(tsplit ? (size_t)M * 256 : 0),
+        htKs(tsplit ? htK.size() : 0);
     auto work = [&](int m0, int m1) {
         std::vector<cplx> bp((size_t)nc * 17);
         std::vector<double> bt((size_t)nc * 9);
@@ -406,6 +412,19 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
                 continue;
             }
             std::copy(tb.begin(), tb.end(), htK.begin() + (size_t)m * nbt * 192);
+            if (tsplit) {  // and the halves (kept beside: the per-mode kernel walks the whole block)
+                std::vector<double> ta, tb2, V, Wm, Jinv;
+                if (!block_lu_twisted(bt8, 2 + ntA, 8, 2, ta) || !block_lu_twisted(bt8, nc, 8, 2 + ntA, tb2) ||
+                    !split_spikes(bt8, 8, 2, nt, ntA, V, Wm, Jinv)) {
+                    bad[m] = 1;
+                    continue;
+                }
+                std::copy(ta.begin(), ta.end(), htKs.begin() + (size_t)m * nbt * 192);
+                std::copy(tb2.begin(), tb2.end(), htKs.begin() + (size_t)m * nbt * 192 + ta.size());
+                std::copy(V.begin(), V.end(), htSpk.begin() + (size_t)m * nt * 8);
+                std::copy(Wm.begin(), Wm.end(), htSpk.begin() + ((size_t)m * nt + ntA) * 8);
+                std::copy(Jinv.begin(), Jinv.end(), htRj.begin() + (size_t)m * 256);
+            }
             std::copy(g.Y.begin(), g.Y.end(), htY.begin() + (size_t)m * nt * 2);
             std::copy(g.Sinv.begin(), g.Sinv.end(), htS.begin() + (size_t)m * 4);
         }
@@ -484,6 +503,14 @@ int build_factors(pizza_ctx* ctx, const HostOps& H, double gamma, DevFactors& F,
         UPLOAD(F.tBlk32, float, tK32);
         UPLOAD(F.tY32, float, tY32);
         UPLOAD(F.tSinv32, float, tS32);
+        F.tsplit = tsplit ? 1 : 0;
+        if (tsplit) {
+            const std::vector<float> ks32(htKs.begin(), htKs.end()), sp32(htSpk.begin(), htSpk.end()),
+                rj32(htRj.begin(), htRj.end());
+            UPLOAD(F.tBlk32S, float, ks32);
+            UPLOAD(F.tSpk32, float, sp32);
+            UPLOAD(F.tRj32, float, rj32);
+        }
     }
     UPLOAD(F.uBlk, double, ub);
     UPLOAD(F.uY, double, fu.Y);

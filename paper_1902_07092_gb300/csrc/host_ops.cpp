@@ -688,6 +688,8 @@ void band_lu_pivot_solve(int n, int kl, int ku, const std::vector<T>& Lm, const 
 
 template void band_lu_pivot_solve<cplx>(int, int, int, const std::vector<cplx>&, const std::vector<cplx>&,
                                         const std::vector<unsigned char>&, const std::vector<double>&, cplx*);
+template void band_lu_pivot_solve<double>(int, int, int, const std::vector<double>&, const std::vector<double>&,
+                                        const std::vector<unsigned char>&, const std::vector<double>&, double*);
 
 template bool band_lu_pivot<double>(int, int, int, const std::vector<double>&, std::vector<double>&,
                                     std::vector<double>&, std::vector<unsigned char>&, std::vector<double>&);

@@ -683,6 +683,38 @@ __device__ void split_join_dd(ddc* x, int n, int nA, const ddc* __restrict__ spk
     __syncthreads();
 }
 
+// The same join for the FP32 temperature block split in halves (real spikes
+// and interface inverse, complex FP32 values).
+__device__ void split_join32(float2* x, int n, int nA, const float* __restrict__ spk, const float* __restrict__ rj) {
+    __shared__ float2 xi[16];
+    const int tid = threadIdx.x;
+    if (tid < 16) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) {
+            const float r = __ldg(&rj[tid * 16 + c]);
+            const float2 v = x[c < 8 ? nA - 8 + c : nA + c - 8];
+            acc.x = fmaf(r, v.x, acc.x);
+            acc.y = fmaf(r, v.y, acc.y);
+        }
+        xi[tid] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+        const float* row = spk + (size_t)i * 8;
+        const float2* v = (i < nA) ? xi + 8 : xi;
+        float2 t = x[i];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float r = __ldg(&row[c]);
+            t.x = fmaf(-r, v[c].x, t.x);
+            t.y = fmaf(-r, v[c].y, t.y);
+        }
+        x[i] = t;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ double2 warp_sum(double2 v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1164,6 +1196,23 @@ __device__ void temperature_residual(const StepParams& P, const DevFactors& F, S
     }
 }
 
+// The FP32 temperature solve D td = tr of the kernel with one CTA per system:
+// one block walked by warps 2-3, or (tsplit) its two halves by warps 2-3 and 4-5
+// joined through the spikes.  Whole CTA; ends with a barrier.
+__device__ void theta32_chains(const DevFactors& F, SolveSmem& s, int m, int nt, int nbt) {
+    const float* tb = (F.tsplit ? F.tBlk32S : F.tBlk32) + (size_t)m * nbt * 192;
+    if (F.tsplit) {
+        const int ntA = 8 * (nbt / 2);
+        cta_chain_solve<RD_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, ntA, tb, 2, s.tr + 2 + ntA, s.tq + ntA,
+                                                      s.td + 2 + ntA, nt - ntA, tb + (size_t)(nbt / 2) * 192, 4,
+                                                      s.ring32);
+        split_join32(s.td + 2, nt, ntA, F.tSpk32 + (size_t)m * nt * 8, F.tRj32 + (size_t)m * 256);
+    } else {
+        cta_chain_solve<RD_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, tb, 2, nullptr, nullptr, nullptr, 0,
+                                                      nullptr, 0, s.ring32);
+    }
+}
+
 // The same residual with the tau rows summed by the whole CTA (kernel with one
 // CTA per system, where no other system's warps run beside it).  Contains one
 // __syncthreads; the caller's next barrier publishes s.tr.
@@ -1192,8 +1241,7 @@ __device__ void temperature_corrections_roles(const StepParams& P, const DevFact
     for (int it = 0; it < F.ir_t; ++it) {
         temperature_residual_block(P, F, s, m0);
         __syncthreads();
-        cta_chain_solve<RD_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m0 * nbt * 192, 2,
-                                                      nullptr, nullptr, nullptr, 0, nullptr, 0, s.ring32);
+        theta32_chains(F, s, m0, nt, nbt);
         block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
         __syncthreads();
@@ -1594,11 +1642,11 @@ __device__ void epilogue_row_theta(const StepParams& P, const RhsSpec& R, double
 // Role 0 with double-float chains: pf, pw, px, fp (double2) and the rings of its
 // four walking warps (RD_DD matrices of complex double-floats each); with FP64
 // chains pf, pw, px, pd, fp.  Role 1: tf, tx (double2), tr, tq, td (float2), uf,
-// ux (double) and the rings of its two walking warps (RD_32 FP32 matrices).
+// ux (double) and the rings of its (up to four) walking warps (RD_32 FP32 matrices).
 __host__ __device__ inline size_t solve_roles_smem_bytes(int nc, bool ddp) {
     const size_t b = (size_t)round8(nc);
     const size_t psi = ddp ? 4 * b * 16 + 4 * (size_t)RD_DD * 64 * 16 : 5 * b * 16;
-    const size_t th = 2 * b * 16 + 3 * b * 8 + 2 * b * 8 + 2 * (size_t)RD_32 * 64 * 4;
+    const size_t th = 2 * b * 16 + 3 * b * 8 + 2 * b * 8 + 4 * (size_t)RD_32 * 64 * 4;
     return psi > th ? psi : th;
 }
 
@@ -1765,8 +1813,7 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
     }
     __syncthreads();
     if (F.ir_t) {
-        cta_chain_solve<RD_32, float, float2, float2>(s.tr + 2, s.tq, s.td + 2, nt, F.tBlk32 + (size_t)m * nbt * 192, 2,
-                                                      nullptr, nullptr, nullptr, 0, nullptr, 0, s.ring32);
+        theta32_chains(F, s, m, nt, nbt);
         block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, 0, nth);
         __syncthreads();

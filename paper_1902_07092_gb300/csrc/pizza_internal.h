@@ -75,6 +75,13 @@ struct DevFactors {
     // ir_t times from FP64 residuals of the assembled system
     int ir_t;
     float *tBlk32, *tY32, *tSinv32;
+    // the FP32 temperature block split in two halves for the kernel with one CTA
+    // per system (tsplit = 1 from 40 blocks, with ir_t; rows [0, n_tA),
+    // n_tA = 8 floor(nb_t/2), and [n_tA, n_t)): tBlk32S each half's factors (A's
+    // first), tSpk32 [M][n_t][8] the spikes (V, then W) and tRj32 [M][16][16] the
+    // interface inverse, as for the streamfunction
+    int tsplit;
+    float *tBlk32S, *tSpk32, *tRj32;
     // Galerkin bases (option "radial" = 2, Appendix B): banded LU with partial
     // pivoting of the square integrated systems (host_ops.h, band_lu_pivot).
     // Streamfunction, complex, 8 diagonals below / 12 above: gpL [M][n_p][8],
