@@ -257,14 +257,15 @@ __device__ __forceinline__ void stockham_pass(const T* __restrict__ src, T* __re
 // Batched FFT of nb transforms stored contiguously in buf0 (each length pl.L);
 // buf1 is scratch of the same size.  Ends with __syncthreads(); returns the buffer
 // holding the result.
-template <int SIGN, class T>
+template <int SIGN, class T, bool R8 = false>
 __device__ __forceinline__ T* fft_batched(T* buf0, T* buf1, const FftPlan& pl, int nb) {
     T* a = buf0;
     T* b = buf1;
     int Ns = 1;
     const int tid = threadIdx.x, nth = blockDim.x;
     const T* tw = Cx<T>::tw(pl);
-    constexpr bool f32 = sizeof(typename Cx<T>::R) == sizeof(float);  // FP32: the radix-8 factorisation
+    // FP32 (and R8 callers): the radix-8 factorisation, fewer passes
+    constexpr bool f32 = R8 || sizeof(typename Cx<T>::R) == sizeof(float);
     const int npass = f32 ? pl.npass8 : pl.npass;
     __syncthreads();
     for (int p = 0; p < npass; ++p) {

@@ -1021,7 +1021,7 @@ __device__ ddc* dct1_pair_dd(ddc* X, ddc* Y, const StepParams& P) {
         for (int w = 1; w < nw; ++w) t = cadd(t, wsum[w]);
         c1 = t;
     }
-    ddc* F = fft_batched<+1>(X, Y, P.plan_h, 1);  // begins with a barrier
+    ddc* F = fft_batched<+1, ddc, true>(X, Y, P.plan_h, 1);  // begins with a barrier
     ddc* O = (F == X) ? Y : X;
     for (int k = tid; k <= H; k += nth) O[2 * k] = cadd(F[k], F[k == 0 ? 0 : K - k]);
     const int chunk = (H + nth - 1) / nth;
