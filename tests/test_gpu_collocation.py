@@ -7,7 +7,16 @@ integration path (derivatives of interpolated grid products); the physical-grid
 vorticity set from psi max(1e-12, n_r^4 eps / 4) (two derivatives); full steps
 1e-12 at n_r = 33 and 2e-12 at n_r = 257, where the inverses of the dense systems
 themselves carry ~3e-13 (the oracle solves by LU with one refinement step, the
-device multiplies by inverse columns built on the host the same way)."""
+device multiplies by inverse columns built on the host the same way).
+
+Where the dynamics themselves amplify rounding-size differences (the strongly
+nonlinear amp = 1 states: in the oracle alone a difference grows up to ~10x per
+ARS443 step at dt = 1e-4), the step-k bar
+is max(1e-12, 2^7 d_k), d_k the divergence after k steps of the oracle from
+itself with the initial state perturbed by 2^-52 relative (rounding_growth): each
+step of the device path differs from the oracle's by up to ~2^7 units of FP64
+rounding (the double-float azimuthal transforms, 2^-48 per operation over
+log2 n_phi levels), and those differences grow as d_k does."""
 import numpy as np
 import pytest
 
@@ -45,6 +54,31 @@ def coll_state(n_r, n_phi, amp, seed, psi_amp=None, u_amp=None):
     u = inputs.theta_init(n_r, n_phi, u_amp if u_amp is not None else amp, seed + 2, cfg=9, m_min=0,
                           n_c=n_r)[0].real.copy()
     return psi, th, u
+
+
+def rounding_growth(make_oracle, psi, th, u, nsteps, seed=7):
+    """d_k, k = 1..nsteps: relative L2 divergence (the larger of state and theta)
+    of the oracle from itself when every initial coefficient is perturbed by a
+    seeded relative 2^-52 (one FP64 rounding)."""
+    a, b = make_oracle(), make_oracle()
+    rng = np.random.default_rng(seed)
+
+    def pert(x):
+        return x * (1.0 + 2.0 ** -52 * rng.standard_normal(np.shape(x)))
+
+    set_both_oracle = lambda o, p, t, v: o.set_state(o.vorticity_from_psi(p), p, t, v)
+    set_both_oracle(a, psi, th, u)
+    set_both_oracle(b, pert(psi), pert(th), pert(u))
+    out = []
+    for _ in range(nsteps):
+        a.step()
+        b.step()
+        _, p1, t1, u1 = a.y
+        _, p2, t2, u2 = b.y
+        r = np.concatenate([p1.ravel(), t1.ravel(), u1.astype(complex)])
+        g = np.concatenate([p2.ravel(), t2.ravel(), u2.astype(complex)])
+        out.append(max(rel_l2(g, r), rel_l2(t2, t1)))
+    return out
 
 
 def set_both(gpu, ora, psi, th, u):
@@ -114,11 +148,13 @@ def test_collocation_steps_match_oracle_tiny(scheme, amp):
     n_r, n_phi = 33, 96
     gpu, ora = coll_pair(n_r, n_phi, 1e-3, 2.0, scheme, 1e-4)
     psi, th, u = coll_state(n_r, n_phi, amp, 1, psi_amp=amp, u_amp=amp)
+    d = rounding_growth(lambda: coll_pair(n_r, n_phi, 1e-3, 2.0, scheme, 1e-4)[1], psi, th, u, 4)
     set_both(gpu, ora, psi, th, u)
     for k in range(4):
         gpu.step(1)
         ora.step()
-        e = compare_state(gpu, ora, 1e-12, tol_w=max(1e-12, n_r ** 4 * EPS / 4))
+        tol = max(1e-12, 2.0 ** 7 * d[k])
+        e = compare_state(gpu, ora, tol, tol_w=max(tol, n_r ** 4 * EPS / 4))
         print("collocation %s amp %g step %d: %s" % (scheme, amp, k + 1, {a: "%.2e" % b for a, b in e.items()}))
     gpu.close()
 

@@ -20,7 +20,7 @@ from oracle.onset import leading_mode
 from oracle.stepper import IntegrationStepper
 from paper_1902_07092_gb300 import inputs
 from tests.parity_util import GOLDEN, assert_state_close, critical_rayleigh, rel_l2
-from tests.test_gpu_collocation import EPS, coll_state, compare_state, set_both
+from tests.test_gpu_collocation import EPS, coll_state, compare_state, rounding_growth, set_both
 from tests.test_gpu_parity import random_state
 
 pytestmark = pytest.mark.gpu
@@ -106,11 +106,17 @@ def test_pumping_collocation_steps_match_oracle(scheme, amp):
     n_r, n_phi = 33, 96
     gpu, ora = pair(n_r, n_phi, 1e-3, 2.0, scheme, 1e-4, "collocation")
     psi, th, u = coll_state(n_r, n_phi, amp, 1, psi_amp=amp, u_amp=amp)
+    # the step-k bar follows the oracle's own growth of a rounding-size difference
+    # (up to ~10x per step for the strongly nonlinear amp = 1 states)
+    Ra = 2.0 * critical_rayleigh(1e-3)
+    d = rounding_growth(lambda: CollocationStepper(n_r, n_phi, 1e-3, Ra, 1.0, 0.35, scheme, 1e-4, pumping=True),
+                        psi, th, u, 4)
     set_both(gpu, ora, psi, th, u)
     for k in range(4):
         gpu.step(1)
         ora.step()
-        e = compare_state(gpu, ora, 1e-12, tol_w=max(1e-12, n_r ** 4 * EPS / 4))
+        tol = max(1e-12, 2.0 ** 7 * d[k])
+        e = compare_state(gpu, ora, tol, tol_w=max(tol, n_r ** 4 * EPS / 4))
         print("pumping collocation %s amp %g step %d: %s" % (scheme, amp, k + 1, {a: "%.2e" % b for a, b in e.items()}))
     gpu.close()
 
