@@ -70,4 +70,61 @@ __device__ __forceinline__ ddc creflect(ddc a, ddc s) {                         
 __device__ __forceinline__ ddc dd_from(double2 v) { return ddc{dd_from(v.x), dd_from(v.y)}; }
 __device__ __forceinline__ double2 dd_to(ddc a) { return make_double2(dd_to(a.x), dd_to(a.y)); }
 
+// The same conversions taken apart on the IEEE 754 fields with integer and FP32
+// instructions.  On GB300 a conversion between float and double issues on the
+// FP64 unit (2 per clock per SM), which made the conversions of a transform's
+// inputs and outputs cost as much as a quarter of its time.
+//
+// v = (-1)^s 1.f 2^e (52 fraction bits f) splits into h = the first 24
+// significant bits (truncated) and the remainder r 2^(e-52), r = the low 29 bits
+// of f, rounded to a float; one fast two-sum renormalises (|h| >= |r 2^(e-52)|).
+// The pair holds v to 2^-48 relative.  |v| below float's normal range gives a
+// signed zero, |v| above it (and inf, NaN) a signed infinity.
+__device__ __forceinline__ ddf dd_from_bits(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+    const unsigned sign = hw & 0x80000000u;
+    const int E = (int)((hw >> 20) & 0x7ffu) - 896;  // biased float exponent of 2^e
+    if (E <= 0) return ddf{__uint_as_float(sign), 0.f};
+    if (E >= 255) return ddf{__uint_as_float(sign | 0x7f800000u), 0.f};
+    const float h = __uint_as_float(sign | ((unsigned)E << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    // r = 64 (r >> 6) + (r & 63), both parts exact floats by the 2^23 offset
+    const unsigned r = lw & 0x1fffffffu;
+    const float r1 = __fsub_rn(__uint_as_float(0x4b000000u | (r >> 6)), 8388608.f);
+    const float r0 = __fsub_rn(__uint_as_float(0x4b000000u | (r & 63u)), 8388608.f);
+    const float rf = __fmul_rn(__fmaf_rn(r1, 64.f, r0), 2.220446049250313e-16f);  // r 2^-52
+    const float l = __fmul_rn(rf, __uint_as_float((unsigned)E << 23));          // times 2^e
+    return dd_renorm(h, __uint_as_float(__float_as_uint(l) ^ sign));
+}
+__device__ __forceinline__ ddc dd_from_bits(double2 v) { return ddc{dd_from_bits(v.x), dd_from_bits(v.y)}; }
+
+// a float as the double of the same value (exact); subnormal floats give zero
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu, sign = b & 0x80000000u;
+    const unsigned ed = (e == 0xffu) ? 0x7ffu : e + 896u;
+    const unsigned hw = (e == 0u) ? sign : sign | (ed << 20) | ((b & 0x7fffffu) >> 3);
+    const unsigned lw = (e == 0u) ? 0u : b << 29;
+    return __hiloint2double((int)hw, (int)lw);
+}
+// the float nearest v (ties away from zero), by an integer rounding of the
+// fraction; below float's normal range a signed zero, above it a signed infinity
+__device__ __forceinline__ float f32_from_bits(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+    const unsigned sign = hw & 0x80000000u;
+    const int E = (int)((hw >> 20) & 0x7ffu) - 896;
+    if (E <= 0) return __uint_as_float(sign);
+    if (E >= 255) return __uint_as_float(sign | 0x7f800000u);
+    // exponent and leading 23 fraction bits (mod 2^32), plus the rounding bit;
+    // a carry out of the fraction steps the exponent, as rounding does
+    unsigned t = ((hw << 3) | (lw >> 29)) - (896u << 23);
+    t = (t & 0x7fffffffu) + ((lw >> 28) & 1u);
+    return __uint_as_float(sign | min(t, 0x7f800000u));
+}
+
+// hi + lo rounded to double: one FP64 add
+__device__ __forceinline__ double dd_to_bits(ddf a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+__device__ __forceinline__ double2 dd_to_bits(ddc a) { return make_double2(dd_to_bits(a.x), dd_to_bits(a.y)); }
+
 }  // namespace pz

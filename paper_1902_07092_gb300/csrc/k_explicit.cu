@@ -393,11 +393,11 @@ __device__ __forceinline__ void load_packed_spectrum_dd(ddc* Z, const double2* _
     // each spectral value converted once, written to m and to its mirror Pn - m
     for (int m = threadIdx.x; m <= n_m; m += blockDim.x) {
         if (m == 0) {
-            Z[0] = ddc{dd_from(src[0].x), dd_scale2(dd_from(src[M].x), sb)};
+            Z[0] = ddc{dd_from_bits(src[0].x), dd_scale2(dd_from_bits(src[M].x), sb)};
             continue;
         }
-        const ddc a = dd_from(src[m]);
-        ddc b = dd_from(src[M + m]);
+        const ddc a = dd_from_bits(src[m]);
+        ddc b = dd_from_bits(src[M + m]);
         b.x = dd_scale2(b.x, sb);
         b.y = dd_scale2(b.y, sb);
         Z[m] = ddc{a.x - b.y, a.y + b.x};        // a + i b
@@ -421,9 +421,20 @@ __device__ __forceinline__ void store_split_spectrum_dd(const ddc* Y, double2* _
             b.x = dd_scale2(y1.y + y2.y, 0.5f) * ib;
             b.y = -(dd_scale2(y1.x - y2.x, 0.5f) * ib);
         }
-        dst[m] = dd_to(a);
-        dst[M + m] = dd_to(b);
+        dst[m] = dd_to_bits(a);
+        dst[M + m] = dd_to_bits(b);
     }
+}
+
+// |x| as the high word of its bits (monotone in |x|: its biased exponent and
+// leading fraction bits), on the integer pipe
+__device__ __forceinline__ unsigned hi_word_abs(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+// the power of two a / b rounded down to exponents, from the high words of a and b,
+// clamped to [-lim, lim]; 0 where either is zero or subnormal
+__device__ __forceinline__ int pow2_exponent_words(unsigned wa, unsigned wb, int lim) {
+    const int ea = (int)(wa >> 20), eb = (int)(wb >> 20);
+    if (ea == 0 || eb == 0) return 0;
+    return max(-lim, min(lim, ea - eb));
 }
 
 __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const double2* __restrict__ G1,
@@ -436,33 +447,61 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
     ddc* Y = sm + Pn;
     const int tid = threadIdx.x, nth = blockDim.x;
     ddc reg[MAXPER];
-    __shared__ double red[4 * 32], mx[4];
-    block_max_abs(G1 + g_index(k, 0, 0, M), M, 4, n_m + 1, mx, red);
-    const int e1 = pow2_exponent(mx[0], mx[1], 40), e2 = pow2_exponent(mx[2], mx[3], 40);
+    __shared__ double red[4 * 32];
     const ddf iP = dd_from(P.inv_nphi);  // 1/n_phi
-    // FP64 means of the four products, pairs (v, omega), (u_phi, omega), (v, theta),
-    // (u_phi, theta), reduced per warp here and summed at the end
+    // One pass over the four fields (v, u_phi, omega, theta):
+    // * the FP64 means of the four products, pairs (v, omega), (u_phi, omega),
+    //   (v, theta), (u_phi, theta): a_0 b_0 + 2 sum_{m >= 1} Re(a_m conj(b_m)), with
+    //   the real parts only at m = 0 (the transforms read no more of mode 0);
+    // * the largest biased exponent of |Re|, |Im| of each field, from the high
+    //   words on the integer pipe: the powers of two that balance the packed pairs.
     __shared__ double msum[4][16];
+    __shared__ unsigned wmx[4][16];
     {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        double acc[4] = {0.0, 0.0, 0.0, 0.0}, a0[4] = {0.0, 0.0, 0.0, 0.0};
+        unsigned hx[4] = {0u, 0u, 0u, 0u};
         const double2* f = G1 + g_index(k, 0, 0, M);  // f[q * M + m]: v, u_phi, omega, theta
         for (int m = tid; m <= n_m; m += nth) {
-            // m = 0: the real parts only (the transforms read no more of mode 0)
-            const double w = (m == 0) ? 1.0 : 2.0, wi = (m == 0) ? 0.0 : 2.0;
             const double2 v = f[m], up = f[M + m], om = f[2 * M + m], th = f[3 * M + m];
-            acc[0] = fma(w, v.x * om.x, fma(wi, v.y * om.y, acc[0]));
-            acc[1] = fma(w, up.x * om.x, fma(wi, up.y * om.y, acc[1]));
-            acc[2] = fma(w, v.x * th.x, fma(wi, v.y * th.y, acc[2]));
-            acc[3] = fma(w, up.x * th.x, fma(wi, up.y * th.y, acc[3]));
+            hx[0] = max(hx[0], max(hi_word_abs(v.x), hi_word_abs(v.y)));
+            hx[1] = max(hx[1], max(hi_word_abs(up.x), hi_word_abs(up.y)));
+            hx[2] = max(hx[2], max(hi_word_abs(om.x), hi_word_abs(om.y)));
+            hx[3] = max(hx[3], max(hi_word_abs(th.x), hi_word_abs(th.y)));
+            if (m == 0) {
+                a0[0] = v.x * om.x;
+                a0[1] = up.x * om.x;
+                a0[2] = v.x * th.x;
+                a0[3] = up.x * th.x;
+            } else {
+                acc[0] = fma(v.x, om.x, fma(v.y, om.y, acc[0]));
+                acc[1] = fma(up.x, om.x, fma(up.y, om.y, acc[1]));
+                acc[2] = fma(v.x, th.x, fma(v.y, th.y, acc[2]));
+                acc[3] = fma(up.x, th.x, fma(up.y, th.y, acc[3]));
+            }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            acc[q] = fma(2.0, acc[q], a0[q]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            hx[q] = __reduce_max_sync(0xffffffffu, hx[q]);
         }
         if ((tid & 31) == 0)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) msum[q][tid >> 5] = acc[q];
+            for (int q = 0; q < 4; ++q) {
+                msum[q][tid >> 5] = acc[q];
+                wmx[q][tid >> 5] = hx[q];
+            }
+    }
+    __syncthreads();
+    int e1, e2;
+    {
+        unsigned w[4] = {0u, 0u, 0u, 0u};
+        for (int i = 0; i < (nth >> 5); ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = max(w[q], wmx[q][i]);
+        e1 = pow2_exponent_words(w[0], w[1], 40);
+        e2 = pow2_exponent_words(w[2], w[3], 40);
     }
 
     if (pair) {
@@ -1276,7 +1315,7 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean_dd(StepPara
             const double w = (n == 0) ? Cw0 : Cw;
             a = (m > 0) ? cscale(y.psi[(size_t)m * nc + n], w) : make_double2(y.u[n] * w, 0.0);
         }
-        C[n] = dd_from(a);
+        C[n] = dd_from_bits(a);
     }
     __syncthreads();
     double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
@@ -1316,14 +1355,14 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean_dd(StepPara
             if (fid <= 2)
                 v = C[j];
             else if (fid == 3)
-                v = (j < nc) ? dd_from(cscale(y.th[(size_t)m * nc + j], (j == 0) ? Cw0 : Cw)) : zero;
+                v = (j < nc) ? dd_from_bits(cscale(y.th[(size_t)m * nc + j], (j == 0) ? Cw0 : Cw)) : zero;
             else
                 v = ddc{C[j].x, dd_scale2(Y[j].x, lam)};
             X[j] = (j == 0 || j == K) ? dd_scale2c(v, 2.f) : v;
         }
         const ddc* Z = dct1_pair_dd(X, Y, P);
         for (int k = tid; k < N; k += nth) {
-            const double2 g = cscale(dd_to(Z[k]), 0.5);  // value of the series at x_k
+            const double2 g = dd_to_bits(dd_scale2c(Z[k], 0.5f));  // value of the series at x_k
             const double s = P.s[k], h2 = P.h2[k], is = P.inv_s[k];
             double2* out = G1 + g_index(k, 0, m, M);
             if (fid == 0) {
@@ -1379,7 +1418,7 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean_dd(StepPara
         ddc* W = X;
         if (fld == 1 || m > 0) {
             const int f = (fld == 0) ? 0 : 2;
-            for (int j = tid; j <= K; j += nth) X[j] = dd_from(cscale(G2[g_index(j, f, m, M)], P.h2[j]));
+            for (int j = tid; j <= K; j += nth) X[j] = dd_from_bits(cscale(G2[g_index(j, f, m, M)], P.h2[j]));
             const ddc* Z = dct1_pair_dd(X, Y, P);
             for (int n = tid; n <= K; n += nth) C[n] = dd_scale2c(Z[n], (n == 0 || n == K) ? hK : iK);
             __syncthreads();
@@ -1388,7 +1427,7 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean_dd(StepPara
             const ddc* D = dct1_pair_dd(X, Y, P);
             W = (D == X) ? Y : X;
             for (int k = tid; k <= K; k += nth) {
-                const double2 dF = cscale(dd_to(D[k]), 0.5);
+                const double2 dF = dd_to_bits(dd_scale2c(D[k], 0.5f));
                 const double is = P.inv_s[k];
                 double2 val;
                 if (fld == 0) {
@@ -1397,20 +1436,20 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean_dd(StepPara
                 } else {
                     val = csub(cscale(cadd(dF, cmul_i(G2[g_index(k, 3, m, M)], dm)), is), G2[g_index(k, 2, m, M)]);
                 }
-                W[k] = dd_from(val);
+                W[k] = dd_from_bits(val);
             }
         } else {  // N_u = (h^2/s) [v omega]_0 (+ pumping)
             for (int k = tid; k <= K; k += nth) {
                 double2 val = cscale(G2[g_index(k, 0, m, M)], P.h2[k] * P.inv_s[k]);
                 if (PF) val = cadd(val, PF[k]);
-                W[k] = dd_from(val);
+                W[k] = dd_from_bits(val);
             }
         }
         const ddc* Z = dct1_pair_dd(W, (W == X) ? Y : X, P);
         const bool buoy = (fld == 0 && m > 0 && !P.buoy_imp);
         // Z lives in X or Y, never in C: the FP64 coefficients overwrite C
         for (int n = tid; n < nc; n += nth) {
-            const double2 v = cscale(dd_to(Z[n]), hc);
+            const double2 v = cscale(dd_to_bits(Z[n]), hc);
             Cd[n] = buoy ? cadd(v, cmul_i(y.th[(size_t)m * nc + n], bfac)) : v;
         }
         __syncthreads();

@@ -99,7 +99,10 @@ __device__ __forceinline__ float2 fma_x(float a, float2 b, float2 acc) {
     return make_float2(fmaf(a, b.x, acc.x), fmaf(a, b.y, acc.y));
 }
 __device__ __forceinline__ float2 sub_x(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+// conversions between the FP32 chains and FP64 on the integer and FP32 pipes
+// (GB300 issues float <-> double conversions on its FP64 unit)
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2(f32_from_bits(v.x), f32_from_bits(v.y)); }
+__device__ __forceinline__ double2 to_d2_bits(float2 v) { return make_double2(f2d_bits(v.x), f2d_bits(v.y)); }
 
 // Accumulator, conversions and finalisation of a chain value: for FP64 and FP32
 // chains the accumulator is the value type itself and these are identities.
@@ -1245,7 +1248,7 @@ __device__ void temperature_corrections_roles(const StepParams& P, const DevFact
         block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m0 * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
         __syncthreads();
-        for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
+        for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2_bits(s.td[n]));
         __syncthreads();
     }
 }
@@ -1270,7 +1273,7 @@ __device__ void temperature_corrections(const StepParams& P, const DevFactors& F
             __syncthreads();
             schur_update32_dir(s.td, nc, F.tY32 + (size_t)m0 * nt * 2, 0, nth);
             __syncthreads();
-            for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
+            for (int n = tid; n < nc; n += nth) s.tx[0][n] = cadd(s.tx[0][n], to_d2_bits(s.td[n]));
             __syncthreads();
         }
         if (has_u) refine_zonal_flow(P, F, s);  // FP64
@@ -1312,7 +1315,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         s.pf[mi][n] = (n < 4 || m == 0) ? make_double2(0.0, 0.0) : ap;
         // double-float streamfunction chains (explicit buoyancy, MB = 1): the
         // right-hand side as double-floats in pd, which the correction fills later
-        if (DDP && m > 0) reinterpret_cast<ddc*>(s.pd[0])[n] = dd_from(s.pf[0][n]);
+        if (DDP && m > 0) reinterpret_cast<ddc*>(s.pd[0])[n] = dd_from_bits(s.pf[0][n]);
         s.tf[mi][n] = (n < 2) ? make_double2(0.0, 0.0) : at;
         if (F.ir_t) s.tr[n] = to_f2(s.tf[mi][n]);  // MB == 1 with ir_t
         if (m == 0) s.uf[n] = (n < 2) ? 0.0 : au;
@@ -1384,7 +1387,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         __syncthreads();
         if (DDP && do_p && m0 > 0) {  // the solution back from double-floats
             const ddc* xd = reinterpret_cast<const ddc*>(s.px[0]);
-            for (int n = 4 + tid; n < nc; n += nth) s.px[0][n] = dd_to(xd[n]);
+            for (int n = 4 + tid; n < nc; n += nth) s.px[0][n] = dd_to_bits(xd[n]);
             __syncthreads();
         }
         if (do_p && F.psplit)
@@ -1441,7 +1444,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         }
         __syncthreads();
         if (F.ir_t && do_t) {  // the FP32 temperature solve becomes the FP64 iterate
-            for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
+            for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2_bits(s.td[n]);
             __syncthreads();
         }
         if (P.buoy_imp && pass == 0) temperature_corrections<MB, DEEP>(P, F, s, m0, has_u, 0);
@@ -1467,7 +1470,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
             if (n >= 0 && n < nc) acc = fms(acc, __ldg(&row[d]), x[n]);
         }
         s.pf[mi][k] = acc;  // the residual replaces the right-hand side
-        if (DDP) reinterpret_cast<ddc*>(s.pf[0])[k] = dd_from(acc);  // in place, as double-floats
+        if (DDP) reinterpret_cast<ddc*>(s.pf[0])[k] = dd_from_bits(acc);  // in place, as double-floats
     }
     if (warp < MB) {  // tau rows: r = 0 - tau x
         const int m = m0 + warp;
@@ -1500,7 +1503,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
                 warp, 1);
             if (!F.psplit && act) {  // the pair converts its solution back, then warp 0 takes the Schur step
                 const ddc* xd = reinterpret_cast<const ddc*>(s.pd[0]);
-                for (int n = 4 + (tid & 63); n < nc; n += 64) s.pd[0][n] = dd_to(xd[n]);
+                for (int n = 4 + (tid & 63); n < nc; n += 64) s.pd[0][n] = dd_to_bits(xd[n]);
                 pair_sync(1);
                 if (warp == 0) warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
             }
@@ -1527,7 +1530,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     __syncthreads();
     if (DDP && F.psplit && m0 > 0) {  // the split solution back from double-floats before the join
         const ddc* xd = reinterpret_cast<const ddc*>(s.pd[0]);
-        for (int n = 4 + tid; n < nc; n += nth) s.pd[0][n] = dd_to(xd[n]);
+        for (int n = 4 + tid; n < nc; n += nth) s.pd[0][n] = dd_to_bits(xd[n]);
         __syncthreads();
     }
     if (F.psplit) {
@@ -1548,7 +1551,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         const int mi = idx / nc, n = idx - mi * nc, m = m0 + mi;
         if (m >= M) continue;
         s.px[mi][n] = (m == 0) ? make_double2(0.0, 0.0) : cadd(s.px[mi][n], s.pd[mi][n]);
-        if (fuse_t) s.tx[0][n] = cadd(s.tx[0][n], to_d2(s.td[n]));
+        if (fuse_t) s.tx[0][n] = cadd(s.tx[0][n], to_d2_bits(s.td[n]));
     }
     __syncthreads();
     }
@@ -1725,7 +1728,7 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
                 if (F.psplit)
                     split_join_dd(xd + 4, np, nA, reinterpret_cast<const ddc*>(F.pSpkDD) + (size_t)m * np * 8,
                                   reinterpret_cast<const ddc*>(F.pRjDD) + (size_t)m * 256, true);
-                for (int n = 4 + tid; n < nc; n += nth) x[n] = dd_to(xd[n]);
+                for (int n = 4 + tid; n < nc; n += nth) x[n] = dd_to_bits(xd[n]);
             } else {
                 if (warp < 2)
                     pair_block_solve<8, PFB>(s.pf[0] + 4, s.pw[0], x + 4, F.psplit ? nA : np, blk, true, warp, 1);
@@ -1817,7 +1820,7 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
         block_schur32_dir(s.td, s.tr, nc, P.ops.tau_dir_B32, F.tSinv32 + (size_t)m * 4);
         schur_update32_dir(s.td, nc, F.tY32 + (size_t)m * nt * 2, 0, nth);
         __syncthreads();
-        for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2(s.td[n]);
+        for (int n = tid; n < nc; n += nth) s.tx[0][n] = to_d2_bits(s.td[n]);
         __syncthreads();
         temperature_corrections_roles(P, F, s, m);
     } else {
