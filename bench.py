@@ -285,11 +285,13 @@ def precision_label(wl):
     FP32 words, ~48-bit significands, on the FP32 pipe)."""
     big = wl["n_r"] >= 513 and wl.get("radial", "integration") == "integration"
     nc = inputs.n_c_of(wl)
-    parts = ["fp64: state, history, field products at each radius, linear couplings, banded applies, "
-             "Schur steps, residuals and refinements in FP64",
+    parts = ["fp64: state, history, stored grid values, linear couplings, banded applies, "
+             "Schur steps, residuals and refinements in FP64" + ("" if big else "; field arithmetic at each "
+                                                                 "radius in FP64"),
              "azimuthal FFTs and products in double-float with the m = 0 means of the products in FP64"]
     if big:
-        parts.append("radial DCT-I and derivative scans in double-float (lean layout, n_r >= 513)")
+        parts.append("radial DCT-I, derivative scans and field arithmetic at each radius in double-float "
+                     "(lean layout, n_r >= 513)")
     if wl.get("radial", "integration") == "integration" and nc > 64:
         parts.append("block chains of the streamfunction solve in double-float (N_c > 64)")
     if nc > 600:

@@ -145,10 +145,11 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            CTAs per SM at n_r = 2049) instead of the batched layout: 1 from
  *            n_r = 129, 0 never, -1 (default) from n_r = 513.  Results agree to
  *            rounding (the DCT-I sums in another order);
- *   "radial_dd" the DCT-I and Chebyshev derivative scans of the lean radial
- *            kernels in double-float arithmetic on the FP32 pipe (about 48
- *            significant bits; loads, stores, field products, banded applies and
- *            couplings in FP64): 1 always (with the lean layout), 0 never, -1
+ *   "radial_dd" the DCT-I, the Chebyshev derivative scans and the field
+ *            arithmetic at each radius of the lean radial kernels in
+ *            double-float arithmetic on the FP32 pipe (about 48 significant bits;
+ *            stored values, banded applies and couplings in FP64): 1 always
+ *            (with the lean layout), 0 never, -1
  *            (default) with the lean layout's default, from n_r = 513.  Results
  *            agree with the FP64 transforms to well within the explicit terms'
  *            FP64 bar, not bitwise;

@@ -1503,6 +1503,30 @@ int pizza_init(pizza_ctx** out, int n_r, int n_phi, double E, double Ra, double 
         P.s_f = fs;
         P.h2_f = fh;
         P.inv_s_f = fi;
+        // double-float copies: hi the nearest float, lo the float nearest the rest
+        std::vector<float2> sd(n_r), hd(n_r), idd(n_r);
+        auto split = [](double v) {
+            const float h = (float)v;
+            return make_float2(h, (float)(v - (double)h));
+        };
+        for (int k = 0; k < n_r; ++k) {
+            sd[k] = split(s[k]);
+            hd[k] = split(h2[k]);
+            idd[k] = split(is[k]);
+        }
+        float2* ds2 = dalloc<float2>(ctx, n_r, al);
+        float2* dh2 = dalloc<float2>(ctx, n_r, al);
+        float2* di2 = dalloc<float2>(ctx, n_r, al);
+        if (!ds2 || !dh2 || !di2) {
+            ctx->err = "device allocation failed";
+            return bail(PIZZA_ENOMEM);
+        }
+        up(ds2, sd.data(), n_r * 8);
+        up(dh2, hd.data(), n_r * 8);
+        up(di2, idd.data(), n_r * 8);
+        P.s_dd = ds2;
+        P.h2_dd = dh2;
+        P.inv_s_dd = di2;
     }
 
     if (!make_fft_plan(2 * ctx->K, P.plan_r) || !make_fft_plan(n_phi, P.plan_p)) {

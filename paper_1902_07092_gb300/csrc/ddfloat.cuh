@@ -127,4 +127,37 @@ __device__ __forceinline__ float f32_from_bits(double v) {
 __device__ __forceinline__ double dd_to_bits(ddf a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 __device__ __forceinline__ double2 dd_to_bits(ddc a) { return make_double2(dd_to_bits(a.x), dd_to_bits(a.y)); }
 
+// hi + lo as a double with integer instructions only.  hi widened to double
+// leaves 29 zero fraction bits below its 24; a renormalised lo (|lo| <= ulp(hi)/2,
+// exponent at least 24 below hi's) is lo's significand shifted into them
+// (truncated past the double's last place), added to the bit pattern when the
+// signs agree and subtracted otherwise, at twice the shift when hi is a power of
+// two (the difference then lies in the binade below).  Within one unit in the
+// last place of the double nearest hi + lo; a subnormal lo counts as zero.
+__device__ __forceinline__ double dd_compose(ddf a) {
+    const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
+    const unsigned eh = (hb >> 23) & 0xffu, el = (lb >> 23) & 0xffu;
+    if (eh == 0u || eh == 0xffu || el == 0u) return f2d_bits(a.hi);
+    const int sh = 29 - (int)(eh - el);
+    if (sh > 5) return dd_to_bits(a);  // not a renormalised pair
+    const unsigned ml = (lb & 0x7fffffu) | 0x800000u;
+    const unsigned L = (sh >= 0) ? (ml << sh) : ((sh > -24) ? (ml >> -sh) : 0u);
+    unsigned long long H =
+        ((unsigned long long)(((eh + 896u) << 20) | ((hb & 0x7fffffu) >> 3)) << 32) | (unsigned long long)(hb << 29);
+    if ((hb ^ lb) & 0x80000000u)
+        H -= ((hb & 0x7fffffu) == 0u) ? 2ull * L : (unsigned long long)L;
+    else
+        H |= L;
+    return __longlong_as_double((long long)(H | ((unsigned long long)(hb & 0x80000000u) << 32)));
+}
+__device__ __forceinline__ double2 dd_compose(ddc a) { return make_double2(dd_compose(a.x), dd_compose(a.y)); }
+
+// a double-float times a float (two-product of the leading parts plus lo b)
+__device__ __forceinline__ ddf dd_mulf(ddf a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    return dd_renorm(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+// i t a for a complex double-float a and a float t
+__device__ __forceinline__ ddc cmul_if(ddc a, float t) { return ddc{-dd_mulf(a.y, t), dd_mulf(a.x, t)}; }
+
 }  // namespace pz

@@ -421,8 +421,8 @@ __device__ __forceinline__ void store_split_spectrum_dd(const ddc* Y, double2* _
             b.x = dd_scale2(y1.y + y2.y, 0.5f) * ib;
             b.y = -(dd_scale2(y1.x - y2.x, 0.5f) * ib);
         }
-        dst[m] = dd_to_bits(a);
-        dst[M + m] = dd_to_bits(b);
+        dst[m] = dd_compose(a);
+        dst[M + m] = dd_compose(b);
     }
 }
 
@@ -912,7 +912,7 @@ __host__ __device__ inline bool lean_radial(const StepParams& P) {
 // double-float radial transforms in the lean kernels (option "radial_dd"):
 // 1 always, 0 never, -1 (default) as the lean layout's own default
 __host__ __device__ inline bool radial_dd(const StepParams& P) {
-    if (!P.plan_r.twdd || P.radial_dd == 0) return false;
+    if (!P.plan_r.twdd || !P.s_dd || P.radial_dd == 0) return false;
     return P.radial_dd > 0 || P.K >= LEAN_K;
 }
 
@@ -1296,8 +1296,12 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean(StepParams 
 }
 
 // k_spec_to_grid_lean with double-float transforms: the coefficients become
-// double-floats when loaded, the series values FP64 again when stored; the
-// field arithmetic at each radius stays FP64.
+// double-floats when loaded (the Chebyshev weights applied in double-float), the
+// field arithmetic at each radius runs in double-float with double-float tables
+// of s, h^2 and 1/s, and each grid value becomes FP64 once, when it is final.
+// Between the passes over psi, dpsi/ds and d2psi/ds2 the partial sums of the
+// u_phi and omega columns wait in the grid array in double-float form (each CTA
+// owns its column m); the pumping flux and the m = 0 column stay FP64.
 __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean_dd(StepParams P, VecSet y,
                                                                          double2* __restrict__ G1) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1307,15 +1311,22 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean_dd(StepPara
     ddc* C = X + N;
     ddc* Y = C + N;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const double Cw = P.cnorm, Cw0 = 0.5 * P.cnorm, dm = (double)m;
+    const double dm = (double)m;
+    const ddf Cw = dd_from(P.cnorm), Cw0 = dd_scale2(Cw, 0.5f);
+    const float fm = (float)m;  // exact: m < 2^24
+    const ddf fm2 = dd_from(dm * dm);
+    const ddf* s_dd = reinterpret_cast<const ddf*>(P.s_dd);
+    const ddf* h2_dd = reinterpret_cast<const ddf*>(P.h2_dd);
+    const ddf* is_dd = reinterpret_cast<const ddf*>(P.inv_s_dd);
     const ddc zero = ddc{ddf{0.f, 0.f}, ddf{0.f, 0.f}};
     for (int n = tid; n < N; n += nth) {
-        double2 a = make_double2(0.0, 0.0);
+        ddc a = zero;
         if (n < nc) {
-            const double w = (n == 0) ? Cw0 : Cw;
-            a = (m > 0) ? cscale(y.psi[(size_t)m * nc + n], w) : make_double2(y.u[n] * w, 0.0);
+            const ddf w = (n == 0) ? Cw0 : Cw;
+            a = (m > 0) ? cscale(dd_from_bits(y.psi[(size_t)m * nc + n]), w)
+                        : ddc{dd_from_bits(y.u[n]) * w, ddf{0.f, 0.f}};
         }
-        C[n] = dd_from_bits(a);
+        C[n] = a;
     }
     __syncthreads();
     double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
@@ -1355,34 +1366,40 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean_dd(StepPara
             if (fid <= 2)
                 v = C[j];
             else if (fid == 3)
-                v = (j < nc) ? dd_from_bits(cscale(y.th[(size_t)m * nc + j], (j == 0) ? Cw0 : Cw)) : zero;
+                v = (j < nc) ? cscale(dd_from_bits(y.th[(size_t)m * nc + j]), (j == 0) ? Cw0 : Cw) : zero;
             else
                 v = ddc{C[j].x, dd_scale2(Y[j].x, lam)};
             X[j] = (j == 0 || j == K) ? dd_scale2c(v, 2.f) : v;
         }
         const ddc* Z = dct1_pair_dd(X, Y, P);
         for (int k = tid; k < N; k += nth) {
-            const double2 g = dd_to_bits(dd_scale2c(Z[k], 0.5f));  // value of the series at x_k
-            const double s = P.s[k], h2 = P.h2[k], is = P.inv_s[k];
+            const ddc gd = dd_scale2c(Z[k], 0.5f);  // value of the series at x_k
             double2* out = G1 + g_index(k, 0, m, M);
+            ddc* outd = reinterpret_cast<ddc*>(out);  // the partial sums, double-float
             if (fid == 0) {
-                out[0] = cmul_i(g, dm);
-                out[M] = cscale(g, 3.0 * s);
-                out[2 * M] = cscale(g, 6.0 + dm * dm * h2 * is * is);
+                const ddf h2 = h2_dd[k], is = is_dd[k];
+                out[0] = dd_compose(cmul_if(gd, fm));
+                outd[M] = cscale(gd, dd_mulf(s_dd[k], 3.f));
+                outd[2 * M] = cscale(gd, h2 * (is * is) * fm2 + ddf{6.f, 0.f});
                 if (PF) {
+                    const double2 g = dd_compose(gd);
                     const double U = P.pump_ups[k];
                     PF[k] = cadd(cscale(g, -U * (P.pump_cr[k] + dm * dm)), cmul_i(g, -U * dm * P.pump_ci[k]));
                 }
             } else if (fid == 1) {
-                out[M] = csub(out[M], cscale(g, h2));
-                out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - 5.0 * s));
-                if (PF) PF[k] = cadd(PF[k], cscale(g, P.pump_ups[k] * 0.5 * s));
+                const ddf s_ = s_dd[k], h2 = h2_dd[k];
+                out[M] = dd_compose(csub(outd[M], cscale(gd, h2)));
+                outd[2 * M] = csub(outd[2 * M], cscale(gd, h2 * is_dd[k] - dd_mulf(s_, 5.f)));
+                if (PF) PF[k] = cadd(PF[k], cscale(dd_compose(gd), P.pump_ups[k] * 0.5 * P.s[k]));
             } else if (fid == 2) {
-                out[2 * M] = csub(out[2 * M], cscale(g, h2));
-                if (PF) PF[k] = csub(PF[k], cscale(out[2 * M], P.pump_ups[k]));
+                const double2 o2 = dd_compose(csub(outd[2 * M], cscale(gd, h2_dd[k])));
+                out[2 * M] = o2;
+                if (PF) PF[k] = csub(PF[k], cscale(o2, P.pump_ups[k]));
             } else if (fid == 3) {
-                out[3 * M] = g;
+                out[3 * M] = dd_compose(gd);
             } else {
+                const double2 g = dd_compose(gd);
+                const double is = P.inv_s[k];
                 out[0] = make_double2(0.0, 0.0);
                 out[M] = make_double2(g.x, 0.0);
                 out[2 * M] = make_double2(g.y / (double)lam + g.x * is, 0.0);
@@ -1397,9 +1414,11 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean_dd(StepPara
 }
 
 // k_grid_to_spec_lean with double-float transforms: grid values become
-// double-floats when loaded, the flux divergence is formed in FP64 at each
-// radius from the double-float derivative, and the analysed coefficients are FP64
-// again (in C, over the double-float data) before the banded applies.
+// double-floats when loaded, the flux divergence is formed in double-float at
+// each radius from the double-float derivative (double-float tables of h^2 and
+// 1/s), and the analysed coefficients, with the explicit buoyancy added in
+// double-float, are FP64 again (in C, over the double-float data) before the
+// FP64 banded applies.  The pumping flux is read in FP64.
 __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean_dd(StepParams P, const double2* __restrict__ G2,
                                                                          VecSet y, VecSet e) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1410,15 +1429,19 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean_dd(StepPara
     ddc* Y = C + N;
     double2* Cd = reinterpret_cast<double2*>(C);  // the analysed coefficients, FP64
     const int tid = threadIdx.x, nth = blockDim.x;
-    const double dm = (double)m, hc = 0.5 * P.cnorm;
+    const double dm = (double)m;
+    const ddf hc = dd_from(0.5 * P.cnorm);
     const float iK = 1.f / (float)K, hK = 0.5f / (float)K;  // K a power of two: exact
+    const float fm = (float)m;                               // exact: m < 2^24
     const double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
-    const double bfac = P.Ra / P.Pr * (double)m / P.s_o;
+    const ddf bfac = dd_from(P.Ra / P.Pr * (double)m / P.s_o);
+    const ddf* h2_dd = reinterpret_cast<const ddf*>(P.h2_dd);
+    const ddf* is_dd = reinterpret_cast<const ddf*>(P.inv_s_dd);
     for (int fld = 0; fld < 2; ++fld) {
         ddc* W = X;
         if (fld == 1 || m > 0) {
             const int f = (fld == 0) ? 0 : 2;
-            for (int j = tid; j <= K; j += nth) X[j] = dd_from_bits(cscale(G2[g_index(j, f, m, M)], P.h2[j]));
+            for (int j = tid; j <= K; j += nth) X[j] = cscale(dd_from_bits(G2[g_index(j, f, m, M)]), h2_dd[j]);
             const ddc* Z = dct1_pair_dd(X, Y, P);
             for (int n = tid; n <= K; n += nth) C[n] = dd_scale2c(Z[n], (n == 0 || n == K) ? hK : iK);
             __syncthreads();
@@ -1427,30 +1450,36 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean_dd(StepPara
             const ddc* D = dct1_pair_dd(X, Y, P);
             W = (D == X) ? Y : X;
             for (int k = tid; k <= K; k += nth) {
-                const double2 dF = dd_to_bits(dd_scale2c(D[k], 0.5f));
-                const double is = P.inv_s[k];
-                double2 val;
+                const ddc dF = dd_scale2c(D[k], 0.5f);
+                const ddf is = is_dd[k];
+                ddc val;
                 if (fld == 0) {
-                    val = cscale(cadd(dF, cmul_i(G2[g_index(k, 1, m, M)], dm)), is);
-                    if (PF) val = csub(val, PF[k]);
+                    val = cscale(cadd(dF, cmul_if(dd_from_bits(G2[g_index(k, 1, m, M)]), fm)), is);
+                    if (PF) val = csub(val, dd_from_bits(PF[k]));
                 } else {
-                    val = csub(cscale(cadd(dF, cmul_i(G2[g_index(k, 3, m, M)], dm)), is), G2[g_index(k, 2, m, M)]);
+                    val = csub(cscale(cadd(dF, cmul_if(dd_from_bits(G2[g_index(k, 3, m, M)]), fm)), is),
+                               dd_from_bits(G2[g_index(k, 2, m, M)]));
                 }
-                W[k] = dd_from_bits(val);
+                W[k] = val;
             }
         } else {  // N_u = (h^2/s) [v omega]_0 (+ pumping)
             for (int k = tid; k <= K; k += nth) {
-                double2 val = cscale(G2[g_index(k, 0, m, M)], P.h2[k] * P.inv_s[k]);
-                if (PF) val = cadd(val, PF[k]);
-                W[k] = dd_from_bits(val);
+                ddc val = cscale(dd_from_bits(G2[g_index(k, 0, m, M)]), h2_dd[k] * is_dd[k]);
+                if (PF) val = cadd(val, dd_from_bits(PF[k]));
+                W[k] = val;
             }
         }
         const ddc* Z = dct1_pair_dd(W, (W == X) ? Y : X, P);
         const bool buoy = (fld == 0 && m > 0 && !P.buoy_imp);
         // Z lives in X or Y, never in C: the FP64 coefficients overwrite C
         for (int n = tid; n < nc; n += nth) {
-            const double2 v = cscale(dd_to_bits(Z[n]), hc);
-            Cd[n] = buoy ? cadd(v, cmul_i(y.th[(size_t)m * nc + n], bfac)) : v;
+            const ddc v = cscale(Z[n], hc);
+            if (buoy) {
+                const ddc t = dd_from_bits(y.th[(size_t)m * nc + n]);
+                Cd[n] = dd_compose(ddc{v.x - t.y * bfac, v.y + t.x * bfac});  // + i bfac theta
+            } else {
+                Cd[n] = dd_compose(v);
+            }
         }
         __syncthreads();
         for (int k = tid; k < nc; k += nth) {

@@ -1387,7 +1387,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
         __syncthreads();
         if (DDP && do_p && m0 > 0) {  // the solution back from double-floats
             const ddc* xd = reinterpret_cast<const ddc*>(s.px[0]);
-            for (int n = 4 + tid; n < nc; n += nth) s.px[0][n] = dd_to_bits(xd[n]);
+            for (int n = 4 + tid; n < nc; n += nth) s.px[0][n] = dd_compose(xd[n]);
             __syncthreads();
         }
         if (do_p && F.psplit)
@@ -1503,7 +1503,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
                 warp, 1);
             if (!F.psplit && act) {  // the pair converts its solution back, then warp 0 takes the Schur step
                 const ddc* xd = reinterpret_cast<const ddc*>(s.pd[0]);
-                for (int n = 4 + (tid & 63); n < nc; n += 64) s.pd[0][n] = dd_to_bits(xd[n]);
+                for (int n = 4 + (tid & 63); n < nc; n += 64) s.pd[0][n] = dd_compose(xd[n]);
                 pair_sync(1);
                 if (warp == 0) warp_schur<4>(s.pd[0], s.pf[0], nc, P.ops.tau_psi_B, F.pSinv + (size_t)m0 * 16);
             }
@@ -1530,7 +1530,7 @@ __global__ void __launch_bounds__(NTHREADS_S) k_solve(StepParams P, RhsSpec R, D
     __syncthreads();
     if (DDP && F.psplit && m0 > 0) {  // the split solution back from double-floats before the join
         const ddc* xd = reinterpret_cast<const ddc*>(s.pd[0]);
-        for (int n = 4 + tid; n < nc; n += nth) s.pd[0][n] = dd_to_bits(xd[n]);
+        for (int n = 4 + tid; n < nc; n += nth) s.pd[0][n] = dd_compose(xd[n]);
         __syncthreads();
     }
     if (F.psplit) {
@@ -1728,7 +1728,7 @@ __global__ void __launch_bounds__(NTHREADS_S, 2) k_solve_roles(StepParams P, Rhs
                 if (F.psplit)
                     split_join_dd(xd + 4, np, nA, reinterpret_cast<const ddc*>(F.pSpkDD) + (size_t)m * np * 8,
                                   reinterpret_cast<const ddc*>(F.pRjDD) + (size_t)m * 256, true);
-                for (int n = 4 + tid; n < nc; n += nth) x[n] = dd_to_bits(xd[n]);
+                for (int n = 4 + tid; n < nc; n += nth) x[n] = dd_compose(xd[n]);
             } else {
                 if (warp < 2)
                     pair_block_solve<8, PFB>(s.pf[0] + 4, s.pw[0], x + 4, F.psplit ? nA : np, blk, true, warp, 1);

@@ -115,6 +115,7 @@ struct StepParams {
     const double* h2;     // [n_r]
     const double* inv_s;  // [n_r]
     const float *s_f, *h2_f, *inv_s_f;  // the same in FP32 (mixed-precision explicit stage)
+    const float2 *s_dd, *h2_dd, *inv_s_dd;  // the same as double-floats (hi, lo): lean radial kernels
     FftPlan plan_r;       // length 2K (radial DCT-I as an FFT of the even extension)
     FftPlan plan_h;       // length K, plan_r's twiddles at stride 2 (radial DCT-I, dct1_batched)
     FftPlan plan_p;       // length n_phi (azimuthal)

@@ -445,10 +445,10 @@ def test_solve_with_one_cta_per_system_is_deterministic():
 
 @pytest.mark.parametrize("n_r,n_phi", [(129, 384), (257, 768), (513, 1536)])
 def test_double_float_lean_radial_transforms_match_oracle(n_r, n_phi):
-    """Option radial_dd = 1 with the lean layout forced: the DCT-I and derivative
-    scans of the synthesis and analysis kernels in double-float arithmetic (the
-    field arithmetic at each radius, the banded applies and the stored values in
-    FP64) give the oracle's explicit terms to the bar of the FP64 transforms,
+    """Option radial_dd = 1 with the lean layout forced: the DCT-I, the derivative
+    scans and the field arithmetic at each radius of the synthesis and analysis
+    kernels in double-float arithmetic (the banded applies and the stored values
+    in FP64) give the oracle's explicit terms to the bar of the FP64 transforms,
     max(1e-12, 4 n_r^2 eps), on states with O(1) fields; and two steps to the
     step bars of the size."""
     from paper_1902_07092_gb300.binding import pizza_set_option
