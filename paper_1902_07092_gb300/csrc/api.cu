@@ -55,8 +55,9 @@ static int fft_factors(int L, bool use8, int* radix) {
 }
 
 bool make_fft_plan(int L, FftPlan& pl) {
-    // FP64 / double-float transforms keep radix 4 (radix 8 measured slower there:
-    // its butterflies hold more registers); FP32 transforms take radix 8
+    // FP64 transforms keep radix 4 (radix 8 measured slower there: its
+    // butterflies hold more registers); FP32 transforms and the double-float
+    // azimuthal and radial transforms take radix 8 (fft_batched's R8)
     const int np = fft_factors(L, false, pl.radix), np8 = fft_factors(L, true, pl.radix8);
     if (np < 0 || np8 < 0) return false;
     pl.L = L;

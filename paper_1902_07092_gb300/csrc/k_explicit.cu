@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
         Y = X + 2 * Pn;
         load_packed_spectrum_dd(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, pow2f(e1));
         load_packed_spectrum_dd(X + Pn, G1 + g_index(k, 2, 0, M), M, Pn, n_m, pow2f(e2));
-        ddc* R = fft_batched<+1>(X, Y, P.plan_p, 2);
+        ddc* R = fft_batched<+1, ddc, true>(X, Y, P.plan_p, 2);
         if (P.cfl_max) cfl_rates(P, R, Pn, (double)pow2f(e1), k, red);
         ddc* O = (R == X) ? Y : X;
         for (int j = tid; j < Pn; j += nth) {
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
             O[j] = cscale(g1, g2.x);
             O[Pn + j] = cscale(g1, g2.y);
         }
-        ddc* S = fft_batched<-1>(O, R, P.plan_p, 2);
+        ddc* S = fft_batched<-1, ddc, true>(O, R, P.plan_p, 2);
         store_split_spectrum_dd(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, iP, dd_scale2(iP, pow2f(-e1)));
         store_split_spectrum_dd(S + Pn, G2 + g_index(k, 2, 0, M), M, Pn, n_m, dd_scale2(iP, pow2f(-e2)),
                                 dd_scale2(dd_scale2(iP, pow2f(-e1)), pow2f(-e2)));
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
         return;
     }
     load_packed_spectrum_dd(X, G1 + g_index(k, 0, 0, M), M, Pn, n_m, pow2f(e1));
-    ddc* R = fft_batched<+1>(X, Y, P.plan_p, 1);
+    ddc* R = fft_batched<+1, ddc, true>(X, Y, P.plan_p, 1);
     if (P.cfl_max) cfl_rates(P, R, Pn, (double)pow2f(e1), k, red);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
     }
     __syncthreads();
     load_packed_spectrum_dd(X, G1 + g_index(k, 2, 0, M), M, Pn, n_m, pow2f(e2));
-    R = fft_batched<+1>(X, Y, P.plan_p, 1);
+    R = fft_batched<+1, ddc, true>(X, Y, P.plan_p, 1);
 #pragma unroll
     for (int i = 0; i < MAXPER; ++i) {
         const int j = tid + i * nth;
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
         }
     }
     ddc* other = (R == X) ? Y : X;
-    ddc* S = fft_batched<-1>(R, other, P.plan_p, 1);
+    ddc* S = fft_batched<-1, ddc, true>(R, other, P.plan_p, 1);
     // g1 Re(g2) = v omega + i l1 u_phi omega
     store_split_spectrum_dd(S, G2 + g_index(k, 0, 0, M), M, Pn, n_m, iP, dd_scale2(iP, pow2f(-e1)));
     __syncthreads();
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(512, 1) k_phi_products_dd(StepParams P, const 
         const int j = tid + i * nth;
         if (j < Pn) X[j] = reg[i];
     }
-    S = fft_batched<-1>(X, Y, P.plan_p, 1);
+    S = fft_batched<-1, ddc, true>(X, Y, P.plan_p, 1);
     // g1 Im(g2) = l2 (v theta + i l1 u_phi theta)
     store_split_spectrum_dd(S, G2 + g_index(k, 2, 0, M), M, Pn, n_m, dd_scale2(iP, pow2f(-e2)),
                             dd_scale2(dd_scale2(iP, pow2f(-e1)), pow2f(-e2)));
