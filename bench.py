@@ -107,10 +107,10 @@ def algorithmic_flops(n_r, n_phi, scheme, radial="integration"):
 # of this workload (summaries under profiles/); null for kernels not captured.
 NCU_TRAFFIC = {
     ("sparse_n257_p768", "solve"): (44.36e6 + 0.03e6, "profiles/imex_step_kernels_n257_p768.md"),
-    ("large_n2049_p6144", "solve"): (5676.0e6 + 172.0e6, "profiles/imex_step_kernels_n2049_p6144.md"),
-    ("large_n2049_p6144", "spec_to_grid"): (107.0e6 + 227.2e6, "profiles/imex_step_kernels_n2049_p6144.md"),
-    ("large_n2049_p6144", "phi_products"): (269.0e6 + 216.6e6, "profiles/imex_step_kernels_n2049_p6144.md"),
-    ("large_n2049_p6144", "grid_to_spec"): (360.2e6 + 71.3e6, "profiles/imex_step_kernels_n2049_p6144.md"),
+    ("large_n2049_p6144", "solve"): (5672.7e6 + 171.6e6, "profiles/imex_step_kernels_n2049_p6144.md"),
+    ("large_n2049_p6144", "spec_to_grid"): (106.3e6 + 226.2e6, "profiles/imex_step_kernels_n2049_p6144.md"),
+    ("large_n2049_p6144", "phi_products"): (269.1e6 + 216.3e6, "profiles/imex_step_kernels_n2049_p6144.md"),
+    ("large_n2049_p6144", "grid_to_spec"): (360.1e6 + 71.0e6, "profiles/imex_step_kernels_n2049_p6144.md"),
     ("coll_n257_p768", "solve"): (735.4e6 + 6.9e6, "profiles/collocation_step_kernels_n257_p768.md"),
     ("galerkin_n257_p768", "solve"): (34.58e6 + 0.003e6, "profiles/galerkin_step_kernels_n257_p768.md"),
 }
