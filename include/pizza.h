@@ -144,7 +144,11 @@ int pizza_init(pizza_ctx **out, int n_r, int n_phi, double E, double Ra,
  *            three shared arrays of n_r values, the fields one after another (two
  *            CTAs per SM at n_r = 2049) instead of the batched layout: 1 from
  *            n_r = 129, 0 never, -1 (default) from n_r = 513.  Results agree to
- *            rounding (the DCT-I sums in another order);
+ *            rounding (the DCT-I sums in another order).  In mixed precision
+ *            ("precision" = 1) the FP32 kernels take this layout only with 1
+ *            (three CTAs per SM; faster at n_r = 2049, but the half-length DCT-I
+ *            accumulates the FP32 rounding of its outputs: about 20x the
+ *            batched layout's distance from FP64, still within the mixed bar);
  *   "radial_dd" the DCT-I, the Chebyshev derivative scans and the field
  *            arithmetic at each radius of the lean radial kernels in
  *            double-float arithmetic on the FP32 pipe (about 48 significant bits;

@@ -904,8 +904,15 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
     return v;
 }
 
+// The mixed-precision (FP32) stage takes the lean layout only when asked
+// (radial_lean = 1): at n_r = 2049 it ran the mixed step 5.99 against 6.53 ms,
+// but the half-length DCT-I builds its odd outputs from a prefix sum over the
+// FP32 transform's outputs, which accumulates their rounding: 2.2e-7 from the
+// FP64 path after 20 steps against 1.1e-8 with the batched layout's
+// even-extension transform.
 __host__ __device__ inline bool lean_radial(const StepParams& P) {
-    if (P.fp32 || P.plan_h.L != P.K || P.K < 128 || P.radial_lean == 0) return false;
+    if (P.plan_h.L != P.K || P.K < 128 || P.radial_lean == 0) return false;
+    if (P.fp32) return P.radial_lean > 0;
     return P.radial_lean > 0 || P.K >= LEAN_K;
 }
 
@@ -916,36 +923,62 @@ __host__ __device__ inline bool radial_dd(const StepParams& P) {
     return P.radial_dd > 0 || P.K >= LEAN_K;
 }
 
+// The FP64 accumulators of dct1_pair: exact widening of FP32 values by their
+// bits (no FP64-unit conversion), the nearest float on the way back
+__device__ __forceinline__ double acc_of(double v) { return v; }
+__device__ __forceinline__ double acc_of(float v) { return f2d_bits(v); }
+__device__ __forceinline__ double2 acc_of(double2 v) { return v; }
+__device__ __forceinline__ double2 acc_of(float2 v) { return make_double2(f2d_bits(v.x), f2d_bits(v.y)); }
+template <class T>
+__device__ __forceinline__ T from_acc(double2 v);
+template <>
+__device__ __forceinline__ double2 from_acc<double2>(double2 v) { return v; }
+template <>
+__device__ __forceinline__ float2 from_acc<float2>(double2 v) { return make_float2(f32_from_bits(v.x), f32_from_bits(v.y)); }
+
 // DCT-I of x_0..x_K in X (K + 1 entries):
 //   C_k = x_0 + (-1)^k x_K + 2 sum_{j=1}^{K-1} x_j cos(pi j k / K),  k = 0..K,
 // by one complex FFT of length K, as dct1_batched: y_j = (x_j + x_{K-j})/2
 // - sin(pi j/K)(x_j - x_{K-j}) formed in place pair by pair (j, K - j),
 // F = FFT(y), C_{2k} = F_k + F_{K-k}, and the odd outputs from
 // C_1 = sum_j (x_j - x_{K-j}) cos(pi j/K) by C_{2k+1} = C_{2k-1} - i(F_k - F_{K-k}),
-// the prefix sum taken by the whole CTA in FP64.  The FFT ping-pongs between X
-// and Y; the outputs go to the buffer that does not hold F, which is returned.
+// the prefix sum taken by the whole CTA in FP64 (also for FP32 data, whose
+// transform and pair arithmetic stay FP32).  The FFT ping-pongs between X and Y;
+// the outputs go to the buffer that does not hold F, which is returned.
 // Starts and ends with __syncthreads().
-__device__ double2* dct1_pair(double2* X, double2* Y, const StepParams& P) {
+template <class T>
+__device__ T* dct1_pair(T* X, T* Y, const StepParams& P) {
+    using RT = typename Cx<T>::R;
     const int K = P.plan_h.L, H = K / 2;
     const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
-    const double2* tw = P.plan_r.tw;  // tw[j] = (cos(pi j/K), -sin(pi j/K))
+    const T* tw = Cx<T>::tw(P.plan_r);  // tw[j] = (cos(pi j/K), -sin(pi j/K))
     __shared__ double2 wsum[NTHREADS_R / 32];
     __shared__ double2 c1;
     __syncthreads();
     double2 acc = make_double2(0.0, 0.0);
     for (int j = tid; j < H; j += nth) {
         if (j == 0) {
-            const double2 a = X[0], b = X[K];
-            X[0] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y + b.y));
-            acc = csub(a, b);
+            const T a = X[0], b = X[K];
+            T h = a;
+            h.x = (RT)0.5 * (a.x + b.x);
+            h.y = (RT)0.5 * (a.y + b.y);
+            X[0] = h;
+            acc = acc_of(csub(a, b));
         } else {
-            const double2 a = X[j], b = X[K - j];
-            const double sn = -tw[j].y, cs = tw[j].x;
-            const double2 sum = cadd(a, b), dif = csub(a, b);
-            X[j] = make_double2(fma(-sn, dif.x, 0.5 * sum.x), fma(-sn, dif.y, 0.5 * sum.y));
-            X[K - j] = make_double2(fma(sn, dif.x, 0.5 * sum.x), fma(sn, dif.y, 0.5 * sum.y));
-            acc.x = fma(2.0 * cs, dif.x, acc.x);
-            acc.y = fma(2.0 * cs, dif.y, acc.y);
+            const T a = X[j], b = X[K - j];
+            const RT sn = -tw[j].y, cs = tw[j].x;
+            const T sum = cadd(a, b), dif = csub(a, b);
+            T lo = sum, hi = sum;
+            lo.x = fmat(-sn, dif.x, (RT)0.5 * sum.x);
+            lo.y = fmat(-sn, dif.y, (RT)0.5 * sum.y);
+            hi.x = fmat(sn, dif.x, (RT)0.5 * sum.x);
+            hi.y = fmat(sn, dif.y, (RT)0.5 * sum.y);
+            X[j] = lo;
+            X[K - j] = hi;
+            const double2 dd = acc_of(dif);
+            const double c2 = 2.0 * acc_of(cs);
+            acc.x = fma(c2, dd.x, acc.x);
+            acc.y = fma(c2, dd.y, acc.y);
         }
     }
     // (j = H: y_H = x_H, and its term of C_1 vanishes)
@@ -957,8 +990,8 @@ __device__ double2* dct1_pair(double2* X, double2* Y, const StepParams& P) {
         for (int w = 1; w < nw; ++w) t = cadd(t, wsum[w]);
         c1 = t;
     }
-    double2* F = fft_batched<+1>(X, Y, P.plan_h, 1);  // begins with a barrier
-    double2* O = (F == X) ? Y : X;
+    T* F = fft_batched<+1>(X, Y, P.plan_h, 1);  // begins with a barrier
+    T* O = (F == X) ? Y : X;
     for (int k = tid; k <= H; k += nth) O[2 * k] = cadd(F[k], F[k == 0 ? 0 : K - k]);
     // odd outputs: each thread a contiguous chunk of k in [0, H), its sum of
     // d_k = -i (F_k - F_{K-k}) (d_0 = 0), a block-wide exclusive scan, then the chunk
@@ -966,7 +999,7 @@ __device__ double2* dct1_pair(double2* X, double2* Y, const StepParams& P) {
     const int lo = min(tid * chunk, H), hi = min(lo + chunk, H);
     double2 tot = make_double2(0.0, 0.0);
     for (int k = max(lo, 1); k < hi; ++k) {
-        const double2 df = csub(F[k], F[K - k]);
+        const double2 df = acc_of(csub(F[k], F[K - k]));
         tot.x += df.y;
         tot.y -= df.x;
     }
@@ -989,11 +1022,11 @@ __device__ double2* dct1_pair(double2* X, double2* Y, const StepParams& P) {
     run.y += inc.y - tot.y;
     for (int k = lo; k < hi; ++k) {
         if (k > 0) {
-            const double2 df = csub(F[k], F[K - k]);
+            const double2 df = acc_of(csub(F[k], F[K - k]));
             run.x += df.y;
             run.y -= df.x;
         }
-        O[2 * k + 1] = run;
+        O[2 * k + 1] = from_acc<T>(run);
     }
     __syncthreads();
     return O;
@@ -1133,15 +1166,37 @@ __device__ void cheb_derivative_scan_dd(const ddc* c, ddc* d, ddc* tmp, int n, d
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean(StepParams P, VecSet y, double2* __restrict__ G1) {
+// The FP64 coefficients as the lean kernels' element type: unchanged in FP64,
+// the nearest float in FP32 (bit-level, off the FP64 unit)
+template <class T>
+__device__ __forceinline__ T to_elem(double2 v);
+template <>
+__device__ __forceinline__ double2 to_elem<double2>(double2 v) { return v; }
+template <>
+__device__ __forceinline__ float2 to_elem<float2>(double2 v) { return make_float2(f32_from_bits(v.x), f32_from_bits(v.y)); }
+
+// CTAs per SM of the lean kernels: two in FP64 (98 KB of shared memory at
+// n_r = 2049), three in FP32 (the FP32 arrays and the FP64 coefficients of a3)
+template <class T>
+constexpr int lean_ctas() { return sizeof(T) == sizeof(double2) ? 2 : 3; }
+
+// T = double2: the FP64 stage; T = float2: the mixed-precision stage (FP32
+// transforms and field arithmetic, grid arrays in FP32, the FP64 state read and
+// the analysed coefficients widened to FP64 for the banded applies).
+template <class T>
+__global__ void __launch_bounds__(NTHREADS_R, lean_ctas<T>()) k_spec_to_grid_lean(StepParams P, VecSet y,
+                                                                                  T* __restrict__ G1) {
+    using RT = typename Cx<T>::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int m = P.m_lo + blockIdx.x;
     const int K = P.K, N = P.n_r, nc = P.nc, M = P.M;
-    double2* X = reinterpret_cast<double2*>(smraw);
-    double2* C = X + N;   // plain coefficients (Psi, then its derivatives; u_bar)
-    double2* Y = C + N;   // second DCT buffer (u_bar' for m = 0)
+    T* X = reinterpret_cast<T*>(smraw);
+    T* C = X + N;   // plain coefficients (Psi, then its derivatives; u_bar)
+    T* Y = C + N;   // second DCT buffer (u_bar' for m = 0)
     const int tid = threadIdx.x, nth = blockDim.x;
-    const double Cw = P.cnorm, Cw0 = 0.5 * P.cnorm, dm = (double)m;
+    const double Cw = P.cnorm, Cw0 = 0.5 * P.cnorm;
+    const RT dm = (RT)m;
+    const T zero = Cx<T>::make(0.0, 0.0);
 
     for (int n = tid; n < N; n += nth) {
         double2 a = make_double2(0.0, 0.0);
@@ -1149,16 +1204,16 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean(StepParams 
             const double w = (n == 0) ? Cw0 : Cw;
             a = (m > 0) ? cscale(y.psi[(size_t)m * nc + n], w) : make_double2(y.u[n] * w, 0.0);
         }
-        C[n] = a;
+        C[n] = to_elem<T>(a);
     }
     __syncthreads();
-    double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
+    T* PF = P.pump ? reinterpret_cast<T*>(P.pump_F) + (size_t)m * N : nullptr;
     __shared__ double red[4 * 32], mx[4];
-    double lam = 1.0;
+    RT lam = (RT)1;
     if (m == 0) {  // u_bar and lam u_bar' packed into one transform (lam a power of two)
         cheb_derivative_scan(C, Y, X, N, P.inv_a);
         block_max_abs(C, N, 2, N, mx, red);
-        lam = pow2_ratio(mx[0], mx[1]);
+        lam = (RT)pow2_ratio(mx[0], mx[1]);
     }
     // fields: 0 Psi, 1 Psi', 2 Psi'', 3 theta (m >= 1); 4 packed u_bar, 3 theta (m = 0)
     const int nf = (m > 0) ? 4 : 2;
@@ -1166,44 +1221,51 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean(StepParams 
         const int fid = (m > 0) ? i : (i == 0 ? 4 : 3);
         if (m > 0 && (fid == 1 || fid == 2)) cheb_derivative_scan(C, C, X, N, P.inv_a);  // C <- dC/ds
         for (int j = tid; j <= K; j += nth) {
-            double2 v;
-            if (fid <= 2)
+            T v;
+            if (fid <= 2) {
                 v = C[j];
-            else if (fid == 3)
-                v = (j < nc) ? cscale(y.th[(size_t)m * nc + j], (j == 0) ? Cw0 : Cw) : make_double2(0.0, 0.0);
-            else
-                v = make_double2(C[j].x, lam * Y[j].x);
-            X[j] = (j == 0 || j == K) ? cscale(v, 2.0) : v;
+            } else if (fid == 3) {
+                v = (j < nc) ? to_elem<T>(cscale(y.th[(size_t)m * nc + j], (j == 0) ? Cw0 : Cw)) : zero;
+            } else {
+                v = C[j];
+                v.y = lam * Y[j].x;
+            }
+            X[j] = (j == 0 || j == K) ? cscale(v, (RT)2) : v;
         }
-        double2* Z = dct1_pair(X, Y, P);
+        T* Z = dct1_pair(X, Y, P);
         for (int k = tid; k < N; k += nth) {
-            const double2 g = cscale(Z[k], 0.5);  // value of the series at x_k
-            const double s = P.s[k], h2 = P.h2[k], is = P.inv_s[k];
-            double2* out = G1 + g_index(k, 0, m, M);
+            const T g = cscale(Z[k], (RT)0.5);  // value of the series at x_k
+            const RT s = Tab<T>::s(P, k), h2 = Tab<T>::h2(P, k), is = Tab<T>::is(P, k);
+            T* out = G1 + g_index(k, 0, m, M);
             if (fid == 0) {
                 out[0] = cmul_i(g, dm);
-                out[M] = cscale(g, 3.0 * s);
-                out[2 * M] = cscale(g, 6.0 + dm * dm * h2 * is * is);
+                out[M] = cscale(g, (RT)3 * s);
+                out[2 * M] = cscale(g, (RT)6 + dm * dm * h2 * is * is);
                 if (PF) {
-                    const double U = P.pump_ups[k];
-                    PF[k] = cadd(cscale(g, -U * (P.pump_cr[k] + dm * dm)), cmul_i(g, -U * dm * P.pump_ci[k]));
+                    const RT U = (RT)P.pump_ups[k];
+                    PF[k] = cadd(cscale(g, -U * ((RT)P.pump_cr[k] + dm * dm)), cmul_i(g, -U * dm * (RT)P.pump_ci[k]));
                 }
             } else if (fid == 1) {
                 out[M] = csub(out[M], cscale(g, h2));
-                out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - 5.0 * s));
-                if (PF) PF[k] = cadd(PF[k], cscale(g, P.pump_ups[k] * 0.5 * s));
+                out[2 * M] = csub(out[2 * M], cscale(g, h2 * is - (RT)5 * s));
+                if (PF) PF[k] = cadd(PF[k], cscale(g, (RT)P.pump_ups[k] * (RT)0.5 * s));
             } else if (fid == 2) {
                 out[2 * M] = csub(out[2 * M], cscale(g, h2));
-                if (PF) PF[k] = csub(PF[k], cscale(out[2 * M], P.pump_ups[k]));
+                if (PF) PF[k] = csub(PF[k], cscale(out[2 * M], (RT)P.pump_ups[k]));
             } else if (fid == 3) {
                 out[3 * M] = g;
             } else {
-                out[0] = make_double2(0.0, 0.0);
-                out[M] = make_double2(g.x, 0.0);
-                out[2 * M] = make_double2(g.y / lam + g.x * is, 0.0);
+                T o = zero;
+                out[0] = o;
+                o.x = g.x;
+                out[M] = o;
+                o.x = g.y / lam + g.x * is;
+                out[2 * M] = o;
                 if (PF) {
-                    const double w0 = g.y / lam + g.x * is;
-                    PF[k] = make_double2(P.pump_ups[k] * g.x * (1.0 + 0.5 * P.E * w0), 0.0);
+                    const RT w0 = g.y / lam + g.x * is;
+                    T pf = zero;
+                    pf.x = (RT)P.pump_ups[k] * g.x * ((RT)1 + (RT)(0.5 * P.E) * w0);
+                    PF[k] = pf;
                 }
             }
         }
@@ -1211,36 +1273,47 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_spec_to_grid_lean(StepParams 
     }
 }
 
-__global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean(StepParams P, const double2* __restrict__ G2,
-                                                                      VecSet y, VecSet e) {
+// byte offset of a3's FP64 coefficient array behind the three T arrays (16-byte
+// aligned); in FP64 the coefficients overwrite C instead
+template <class T>
+__host__ __device__ inline size_t lean_cd_offset(int n_r) {
+    return sizeof(T) == sizeof(double2) ? sizeof(T) * (size_t)n_r : (sizeof(T) * 3 * (size_t)n_r + 15) / 16 * 16;
+}
+
+template <class T>
+__global__ void __launch_bounds__(NTHREADS_R, lean_ctas<T>()) k_grid_to_spec_lean(StepParams P, const T* __restrict__ G2,
+                                                                                  VecSet y, VecSet e) {
+    using RT = typename Cx<T>::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int m = P.m_lo + blockIdx.x;
     const int K = P.K, N = P.n_r, nc = P.nc, M = P.M;
-    double2* X = reinterpret_cast<double2*>(smraw);
-    double2* C = X + N;
-    double2* Y = C + N;
+    T* X = reinterpret_cast<T*>(smraw);
+    T* C = X + N;
+    T* Y = C + N;
+    double2* Cd = reinterpret_cast<double2*>(smraw + lean_cd_offset<T>(N));  // FP64 coefficients
     const int tid = threadIdx.x, nth = blockDim.x;
-    const double dm = (double)m, iK = 1.0 / (double)K, hK = 0.5 / (double)K, hc = 0.5 * P.cnorm;
-    const double2* PF = P.pump ? P.pump_F + (size_t)m * N : nullptr;
+    const RT dm = (RT)m, iK = (RT)(1.0 / (double)K), hK = (RT)(0.5 / (double)K);
+    const double dmd = (double)m, hc = 0.5 * P.cnorm;
+    const T* PF = P.pump ? reinterpret_cast<const T*>(P.pump_F) + (size_t)m * N : nullptr;
     const double bfac = P.Ra / P.Pr * (double)m / P.s_o;
     // field 0: N_omega (m >= 1) or N_u (m = 0); field 1: N_theta
     for (int fld = 0; fld < 2; ++fld) {
-        double2* W = X;  // the buffer holding the grid values to analyse
+        T* W = X;  // the buffer holding the grid values to analyse
         if (fld == 1 || m > 0) {
             // plain coefficients of F = h^2 [v omega]_m (or h^2 [v theta]_m), d/ds of them
             const int f = (fld == 0) ? 0 : 2;
-            for (int j = tid; j <= K; j += nth) X[j] = cscale(G2[g_index(j, f, m, M)], P.h2[j]);
-            const double2* Z = dct1_pair(X, Y, P);
+            for (int j = tid; j <= K; j += nth) X[j] = cscale(G2[g_index(j, f, m, M)], Tab<T>::h2(P, j));
+            const T* Z = dct1_pair(X, Y, P);
             for (int n = tid; n <= K; n += nth) C[n] = cscale(Z[n], (n == 0 || n == K) ? hK : iK);
             __syncthreads();
             cheb_derivative_scan(C, C, X, N, P.inv_a);
-            for (int j = tid; j <= K; j += nth) X[j] = (j == 0 || j == K) ? cscale(C[j], 2.0) : C[j];
-            const double2* D = dct1_pair(X, Y, P);
+            for (int j = tid; j <= K; j += nth) X[j] = (j == 0 || j == K) ? cscale(C[j], (RT)2) : C[j];
+            const T* D = dct1_pair(X, Y, P);
             W = (D == X) ? Y : X;
             for (int k = tid; k <= K; k += nth) {
-                const double2 dF = cscale(D[k], 0.5);
-                const double is = P.inv_s[k];
-                double2 val;
+                const T dF = cscale(D[k], (RT)0.5);
+                const RT is = Tab<T>::is(P, k);
+                T val;
                 if (fld == 0) {
                     val = cscale(cadd(dF, cmul_i(G2[g_index(k, 1, m, M)], dm)), is);
                     if (PF) val = csub(val, PF[k]);
@@ -1251,19 +1324,20 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean(StepParams 
             }
         } else {  // N_u = (h^2/s) [v omega]_0 (+ pumping)
             for (int k = tid; k <= K; k += nth) {
-                double2 val = cscale(G2[g_index(k, 0, m, M)], P.h2[k] * P.inv_s[k]);
+                T val = cscale(G2[g_index(k, 0, m, M)], Tab<T>::h2(P, k) * Tab<T>::is(P, k));
                 if (PF) val = cadd(val, PF[k]);
                 W[k] = val;
             }
         }
         // Eq. icheb of the grid values, truncated to n < nc
-        const double2* Z = dct1_pair(W, (W == X) ? Y : X, P);
+        const T* Z = dct1_pair(W, (W == X) ? Y : X, P);
         // N_omega_hat, with the buoyancy (Ra/Pr)(i m/s_o) theta_hat added before the
-        // one C^I apply (Eq. psi_int applies C^I to their sum)
+        // one C^I apply (Eq. psi_int applies C^I to their sum); Z lives in X or Y,
+        // never where the FP64 coefficients go
         const bool buoy = (fld == 0 && m > 0 && !P.buoy_imp);
         for (int n = tid; n < nc; n += nth) {
-            const double2 v = cscale(Z[n], hc);
-            C[n] = buoy ? cadd(v, cmul_i(y.th[(size_t)m * nc + n], bfac)) : v;
+            const double2 v = cscale(acc_of(Z[n]), hc);
+            Cd[n] = buoy ? cadd(v, cmul_i(y.th[(size_t)m * nc + n], bfac)) : v;
         }
         __syncthreads();
         // integrated right-hand sides; the linear couplings read the FP64 state
@@ -1271,19 +1345,19 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean(StepParams 
             if (fld == 0) {
                 if (m > 0) {
                     double2 ep = make_double2(0.0, 0.0);
-                    if (k >= 4) ep = band_row<8>(P.ops.band[OP_C], C, k, nc);
+                    if (k >= 4) ep = band_row<8>(P.ops.band[OP_C], Cd, k, nc);
                     e.psi[(size_t)m * nc + k] = ep;
                 } else {
                     e.psi[k] = make_double2(0.0, 0.0);
-                    e.u[k] = (k >= 2) ? -band_row<4>(P.ops.band[OP_D], C, k, nc).x : 0.0;
+                    e.u[k] = (k >= 2) ? -band_row<4>(P.ops.band[OP_D], Cd, k, nc).x : 0.0;
                 }
             } else {
                 double2 et = make_double2(0.0, 0.0);
                 if (k >= 2) {
-                    const double2 dn = band_row<4>(P.ops.band[OP_D], C, k, nc);
+                    const double2 dn = band_row<4>(P.ops.band[OP_D], Cd, k, nc);
                     if (m > 0) {
                         const double2 gp = band_row<4>(P.ops.band[OP_G], y.psi + (size_t)m * nc, k, nc);
-                        et = csub(cmul_i(gp, -P.tc * dm), dn);
+                        et = csub(cmul_i(gp, -P.tc * dmd), dn);
                     } else {
                         et = cscale(dn, -1.0);
                     }
@@ -1511,6 +1585,10 @@ __global__ void __launch_bounds__(NTHREADS_R, 2) k_grid_to_spec_lean_dd(StepPara
 }
 
 size_t smem_radial_lean(const StepParams& P) { return sizeof(double2) * 3 * (size_t)P.n_r; }
+// the FP32 lean kernels: three float2 arrays; a3 also the FP64 coefficients
+static size_t smem_radial_lean32(const StepParams& P, bool analysis) {
+    return analysis ? lean_cd_offset<float2>(P.n_r) + sizeof(double2) * (size_t)P.nc : sizeof(float2) * 3 * (size_t)P.n_r;
+}
 
 template <class T>
 static cudaError_t spec_to_grid_t(const StepParams& P, VecSet y, void* G1, cudaStream_t st) {
@@ -1554,9 +1632,17 @@ static cudaError_t grid_to_spec_t(const StepParams& P, const void* G2, VecSet y,
 }
 
 cudaError_t launch_spec_to_grid(const StepParams& P, VecSet y, double2* G1, cudaStream_t st) {
+    if (lean_radial(P) && P.fp32) {
+        const size_t sm = smem_radial_lean32(P, false);
+        cudaError_t err =
+            cudaFuncSetAttribute(k_spec_to_grid_lean<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_spec_to_grid_lean<float2><<<slab_modes(P), NTHREADS_R, sm, st>>>(P, y, reinterpret_cast<float2*>(G1));
+        return cudaGetLastError();
+    }
     if (lean_radial(P)) {
         const size_t sm = smem_radial_lean(P);
-        auto kern = radial_dd(P) ? k_spec_to_grid_lean_dd : k_spec_to_grid_lean;
+        auto kern = radial_dd(P) ? k_spec_to_grid_lean_dd : k_spec_to_grid_lean<double2>;
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (err != cudaSuccess) return err;
         kern<<<slab_modes(P), NTHREADS_R, sm, st>>>(P, y, G1);
@@ -1584,9 +1670,17 @@ cudaError_t launch_phi_products(const StepParams& P, const double2* G1, double2*
 }
 
 cudaError_t launch_grid_to_spec(const StepParams& P, const double2* G2, VecSet y, VecSet e, cudaStream_t st) {
+    if (lean_radial(P) && P.fp32) {
+        const size_t sm = smem_radial_lean32(P, true);
+        cudaError_t err =
+            cudaFuncSetAttribute(k_grid_to_spec_lean<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_grid_to_spec_lean<float2><<<slab_modes(P), NTHREADS_R, sm, st>>>(P, reinterpret_cast<const float2*>(G2), y, e);
+        return cudaGetLastError();
+    }
     if (lean_radial(P)) {
         const size_t sm = smem_radial_lean(P);
-        auto kern = radial_dd(P) ? k_grid_to_spec_lean_dd : k_grid_to_spec_lean;
+        auto kern = radial_dd(P) ? k_grid_to_spec_lean_dd : k_grid_to_spec_lean<double2>;
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (err != cudaSuccess) return err;
         kern<<<slab_modes(P), NTHREADS_R, sm, st>>>(P, G2, y, e);

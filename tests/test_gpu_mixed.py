@@ -56,6 +56,60 @@ def test_mixed_explicit_terms_error(n_r, n_phi):
     gpu.close()
 
 
+@pytest.mark.parametrize("n_r,n_phi", [(129, 384), (257, 768), (513, 1536)])
+def test_mixed_lean_radial_kernels_match_oracle(n_r, n_phi):
+    """Option radial_lean = 1 in mixed precision: the FP32 three-array radial
+    kernels (half-length DCT-I with the odd outputs' prefix sums in FP64, FP32
+    transforms and field arithmetic at each radius, FP32 grid arrays, the analysed
+    coefficients widened to FP64 for the banded applies) give the explicit terms
+    the streamfunction and temperature explicit terms within the mixed bar,
+    8 n_r log2(n_phi) u_32, of the FP64 oracle, and two steps within 1e-6 of it.
+    The zonal-flow term is forced by the m = 0 mean [v omega]_0, which the FP32
+    azimuthal kernel forms with the cancellation of its terms (to ~1e-4 of them)
+    whatever the radial layout: there the lean layout must stay within the batched
+    layout's own error plus the bar."""
+    from paper_1902_07092_gb300.binding import pizza_set_option
+    Ra = 2.0 * critical_rayleigh(1e-3)
+    ora = IntegrationStepper(n_r, n_phi, 1e-3, Ra, 1.0, 0.35, "CNAB2", 1e-4)
+    th = inputs.theta_init(n_r, n_phi, 1.0, 3, cfg=7, m_min=0)
+    psi = inputs.theta_init(n_r, n_phi, 1.0, 4, cfg=8)
+    psi[0] = 0.0
+    u = inputs.theta_init(n_r, n_phi, 1.0, 5, cfg=9, m_min=0)[0].real.copy()
+    rp, rt, ru = explicit_terms(ora.g, psi, th, u)
+    errs = {}
+    for lean in (0, 1):
+        gpu = mixed_solver(n_r, n_phi, 1e-3, Ra, "CNAB2", 1e-4)
+        pizza_set_option(gpu.ctx, "radial_lean", lean)
+        gpu.set_state(th, psi, u)
+        ep, et, eu = gpu.explicit_terms()
+        errs[lean] = (rel_l2(ep, rp), rel_l2(et, rt), rel_l2(eu, ru))
+        gpu.close()
+    tol = 8 * n_r * math.log2(n_phi) * U32
+    print("mixed explicit terms n_r=%d, lean: psi %.2e theta %.2e u %.2e; batched: u %.2e (tol %.1e)"
+          % ((n_r,) + errs[1] + (errs[0][2], tol)))
+    assert max(errs[1][:2]) <= tol
+    assert errs[1][2] <= errs[0][2] + tol
+    # two steps from a small state
+    E, dt = 1e-5, 1e-8
+    Ra = 5.0 * critical_rayleigh(E)
+    gpu = mixed_solver(n_r, 24, E, Ra, "SBDF3", dt)
+    pizza_set_option(gpu.ctx, "radial_lean", 1)
+    ora = IntegrationStepper(n_r, 24, E, Ra, 1.0, 0.35, "SBDF3", dt)
+    th = inputs.theta_init(n_r, 24, 1e-3, 81, cfg=1, m_min=0)
+    psi = inputs.theta_init(n_r, 24, 1e-5, 82, cfg=8)
+    psi[0] = 0.0
+    u = inputs.theta_init(n_r, 24, 1e-3, 83, cfg=9, m_min=0)[0].real.copy()
+    gpu.set_state(th, psi, u)
+    ora.set_state(psi, th, u)
+    for k in range(2):
+        gpu.step(1)
+        ora.step()
+        e = state_rel(gpu.get_state(), ora.y)
+        print("mixed lean n_r=%d step %d: state rel err %.2e" % (n_r, k + 1, e))
+        assert e <= 1e-6
+    gpu.close()
+
+
 def test_mixed_steps_sparse_workload():
     """n_r = 257, n_phi = 768, E = 1e-5, Ra = 10 Ra_c, ARS443, dt = 1e-7, seeded
     perturbation 1e-3: five steps against the FP64 oracle."""
