@@ -15,7 +15,7 @@ Bars (relative L2):
   measured 2.8e-12 after the first step.
 * FP64 u_bar: max(20, c_u) times the state bar, c_u the cancellation factor of
   its forcing (tests/parity_util.py).
-* mixed precision: 1e-6 of the whole state after every step (the benchmark spec's bar).
+* mixed precision: 1e-6 of the whole state after every step (the mixed-precision bar of the time step).
 """
 import numpy as np
 import pytest
